@@ -1,0 +1,174 @@
+"""DGSEM operators R^(1) (Eq. 12) and R^(2) (Eq. 16) on periodic, uniform
+Cartesian meshes in 1, 2 or 3 dimensions.  Test infrastructure only (see
+``oracle/__init__``).
+
+State layout (canonical, shared with the library's C-ABI):
+    w[e][v][k][j][i]   (i = x node index fastest; d = 1, 2, 3 keeps the last d
+                        node axes), e = ex + nx * (ey + ny * ez).
+
+On a Cartesian element of size h_m the transformation of Sec. 3.1.1 reduces to
+J_geo = prod h_m / 2, transformed flux (prod_{n != m} h_n/2) F^m and surface
+element of the same size, so Eq. 12 becomes, for every direction m,
+
+    R1 += -(2 / h_m) [ sum_l Dhat[i, l] F^m_l  +  f*_{+m} lhat_i(+1)
+                                               +  f*_{-m} lhat_i(-1) ]
+
+along the node index of direction m, where f*_{+-m} is the numerical flux of
+Eq. 13 with the outward normal of that face and w^L the element's own trace.
+Traces are the solution polynomial evaluated at the edge (Sec. 3.1.1).
+
+R^(2)(w, sigma) is the same operator with F^m(w) replaced by (dF^m/dw) sigma and
+the face flux f~* of Sec. 3.1.2, which uses the traces of w and sigma and the
+same dissipation coefficient (evaluated at w, not differentiated).
+"""
+import numpy as np
+
+from . import laws
+from .basis import Basis, LOBATTO
+
+
+class Mesh:
+    def __init__(self, dim, n, lo, hi):
+        self.dim = dim
+        self.n = tuple(int(x) for x in n[:dim])
+        self.lo = np.array(lo[:dim], dtype=np.float64)
+        self.hi = np.array(hi[:dim], dtype=np.float64)
+        self.h = (self.hi - self.lo) / np.array(self.n)
+        self.nE = int(np.prod(self.n))
+
+
+class Disc:
+    """A discretisation: mesh + basis + physics."""
+
+    def __init__(self, mesh, N, physics, family=LOBATTO):
+        self.mesh = mesh
+        self.basis = Basis(N, family)
+        self.ph = physics
+        self.d = mesh.dim
+        self.p = N + 1
+        self.nv = physics.nv
+        self.shape = (mesh.nE, self.nv) + (self.p,) * self.d
+        self.ndof = int(np.prod(self.shape))
+
+    # -- layout ---------------------------------------------------------
+    def to_grid(self, w):
+        """canonical (nE, nv, P..) -> (nv, n_{d-1}, .., n_0, P_{d-1}, .., P_0)."""
+        d = self.d
+        g = w.reshape(tuple(reversed(self.mesh.n)) + (self.nv,) + (self.p,) * d)
+        return np.moveaxis(g, d, 0)
+
+    def from_grid(self, g):
+        d = self.d
+        w = np.moveaxis(g, 0, d)
+        return w.reshape(self.shape)
+
+    def elem_axis(self, m):
+        return 1 + (self.d - 1 - m)
+
+    def node_axis(self, m):
+        return 1 + self.d + (self.d - 1 - m)
+
+    def node_coords(self):
+        """Physical coordinates of every node, list of d arrays in canonical
+        shape (nE, P..) (variable axis dropped)."""
+        d, mesh, xi = self.d, self.mesh, self.basis.nodes
+        coords = []
+        for m in range(d):
+            shp = [1] * (2 * d)
+            e = np.arange(mesh.n[m], dtype=np.float64)
+            shp_e = list(shp)
+            shp_e[d - 1 - m] = mesh.n[m]
+            shp_n = list(shp)
+            shp_n[d + d - 1 - m] = self.p
+            x = (mesh.lo[m] + mesh.h[m] * e.reshape(shp_e)
+                 + 0.5 * mesh.h[m] * (xi.reshape(shp_n) + 1.0))
+            full = np.broadcast_to(x, tuple(reversed(mesh.n)) + (self.p,) * d)
+            coords.append(np.ascontiguousarray(full).reshape((mesh.nE,) + (self.p,) * d))
+        return coords
+
+    # -- helpers ----------------------------------------------------------
+    @staticmethod
+    def _apply(M, A, axis):
+        """(M A) along `axis`: out[..i..] = sum_l M[i, l] A[..l..]."""
+        return np.moveaxis(np.tensordot(M, A, axes=([1], [axis])), 0, axis)
+
+    @staticmethod
+    def _trace(vec, A, axis):
+        """Evaluate the polynomial along `axis` with the weights `vec` (removes axis)."""
+        return np.tensordot(A, vec, axes=([axis], [0]))
+
+    def _lift(self, f, lhat, axis):
+        shp = [1] * (2 * self.d + 1)
+        shp[axis] = self.p
+        return np.expand_dims(f, axis) * lhat.reshape(shp)
+
+
+def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False):
+    """R^(1)(w) if mode == "R1"; R^(2)(w, sigma) if mode == "R2".
+
+    frozen_neighbor (R2 only): the neighbours' sigma traces are taken as zero,
+    which gives the element-local linearisation used by the block
+    preconditioners of Sec. 3.2.3 (neighbour dependencies neglected)."""
+    ph, b = disc.ph, disc.basis
+    W = disc.to_grid(w)
+    S = disc.to_grid(sigma) if sigma is not None else None
+    out = np.zeros(W.shape, dtype=np.result_type(W, S) if S is not None else W.dtype)
+    for m in range(disc.d):
+        ea, na = disc.elem_axis(m), disc.node_axis(m)
+        # nodal flux and volume term
+        if mode == "R1":
+            F = laws.flux(W, m, ph)
+        else:
+            F = laws.flux_jvp(W, S, m, ph)
+        vol = Disc._apply(b.Dhat, F, na)
+        # traces: own + face (right trace) and own - face (left trace)
+        wp = Disc._trace(b.l_p, W, na)
+        wm = Disc._trace(b.l_m, W, na)
+        # neighbour e+1 seen from element e: its minus trace
+        wR = np.roll(wm, -1, axis=ea)
+        kappa = laws.dissipation(wp, wR, m, ph)
+        if mode == "R1":
+            fface = 0.5 * (laws.flux(wp, m, ph) + laws.flux(wR, m, ph)) + kappa * (wp - wR)
+            fplus = fface
+            fminus = -np.roll(fface, 1, axis=ea)
+        else:
+            sp = Disc._trace(b.l_p, S, na)
+            sm = Disc._trace(b.l_m, S, na)
+            sR = np.roll(sm, -1, axis=ea)
+            if not frozen_neighbor:
+                fface = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wR, sR, m, ph))
+                         + kappa * (sp - sR))
+                fplus = fface
+                fminus = -np.roll(fface, 1, axis=ea)
+            else:
+                # element's + face: neighbour sigma trace set to zero
+                fplus = 0.5 * laws.flux_jvp(wp, sp, m, ph) + kappa * sp
+                # element's - face: the face (e-1, e) seen from e, with the
+                # neighbour (e-1) sigma trace zero; outward normal is -e_m
+                kappa_prev = np.roll(kappa, 1, axis=ea)
+                fminus = -(0.5 * laws.flux_jvp(wm, sm, m, ph) - kappa_prev * sm)
+        surf = disc._lift(fplus, b.lhat_p, na) + disc._lift(fminus, b.lhat_m, na)
+        out = out - (2.0 / disc.mesh.h[m]) * (vol + surf)
+    return disc.from_grid(out)
+
+
+def R1(disc, w):
+    """R^(1)_h(w), Eq. 12 (with Eq. 13 at the faces)."""
+    return operator(disc, w, mode="R1")
+
+
+def R2(disc, w, sigma):
+    """R^(2)_h(w, sigma), Eq. 16."""
+    return operator(disc, w, sigma, mode="R2")
+
+
+def cell_integral(disc, w):
+    """Integral of each variable over the domain with the collocated quadrature:
+    sum_e sum_nodes (prod_m omega * h_m / 2) w.  Shape (nv,)."""
+    wq = disc.basis.weights
+    W = w.reshape((disc.mesh.nE, disc.nv) + (disc.p,) * disc.d)
+    tot = W
+    for _ in range(disc.d):
+        tot = np.tensordot(tot, wq, axes=([tot.ndim - 1], [0]))
+    jac = np.prod(disc.mesh.h / 2.0)
+    return jac * tot.sum(axis=0)

@@ -1,0 +1,140 @@
+"""Physical fluxes F^m(w) and their directional derivatives (dF^m/dw) s for the
+conservation laws of the paper.  Test infrastructure only (see
+``oracle/__init__``).
+
+Arrays carry the conserved variables on axis 0; every function is written with
+plain arithmetic so that it also runs on complex arrays (complex-step tests).
+
+  advection   F^m = a_m w                                   (Sec. 4.1.1)
+  burgers     F^m = w^2 / 2 in every direction (inviscid part of the Burgers
+              workload; the viscous part is not in the oracle)
+  euler       Eq. 21: F^m = (rho v_m, rho v_m v + p/eps^2 e_m, v_m (E + p)),
+              p = (gamma - 1)(E - eps^2/2 rho |v|^2)
+
+Numerical-flux dissipation (Eq. 13 and its parameters in Sec. 4.1):
+  global Lax-Friedrichs: lambda is a constant per variable; advection
+  lambda = |a . n|, Euler lambda = diag(1/eps, 1, .., 1, 1/eps) (Sec. 4.1.2).
+  Rusanov: lambda = 1/2 max(|v_n^L| + c^L, |v_n^R| + c^R), the usual local
+  choice (the Euler workload asks for it); c = sqrt(gamma p / rho) / eps.
+"""
+import numpy as np
+
+ADVECTION = "advection"
+BURGERS = "burgers"
+EULER = "euler"
+
+
+class Physics:
+    def __init__(self, law, dim, a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0,
+                 flux="lf", lf_scale=1.0):
+        self.law = law
+        self.dim = dim
+        self.a = np.array(a[:dim], dtype=np.float64)
+        self.gamma = gamma
+        self.eps = eps
+        self.flux = flux            # "lf" (global Lax-Friedrichs) or "rusanov"
+        self.lf_scale = lf_scale    # multiplies the paper's lambda in "lf"
+        self.nv = {ADVECTION: 1, BURGERS: 1, EULER: dim + 2}[law]
+        self.linear = law == ADVECTION
+
+
+def _re(x):
+    return np.real(x)
+
+
+def cs_abs(x):
+    """|x| that keeps the derivative for complex-step use (sign of the real part)."""
+    return np.where(_re(x) >= 0, x, -x)
+
+
+def cs_max(x, y):
+    return np.where(_re(x) >= _re(y), x, y)
+
+
+def euler_primitives(w, ph):
+    d = ph.dim
+    rho = w[0]
+    v = [w[1 + k] / rho for k in range(d)]
+    E = w[d + 1]
+    v2 = sum(vk * vk for vk in v)
+    p = (ph.gamma - 1.0) * (E - 0.5 * ph.eps ** 2 * rho * v2)
+    return rho, v, E, p
+
+
+def flux(w, m, ph):
+    """F^m(w), direction m (0 = x)."""
+    if ph.law == ADVECTION:
+        return ph.a[m] * w
+    if ph.law == BURGERS:
+        return 0.5 * w * w
+    d = ph.dim
+    rho, v, E, p = euler_primitives(w, ph)
+    F = np.empty_like(w)
+    F[0] = w[1 + m]
+    for k in range(d):
+        F[1 + k] = w[1 + m] * v[k]
+        if k == m:
+            F[1 + k] = F[1 + k] + p / ph.eps ** 2
+    F[d + 1] = v[m] * (E + p)
+    return F
+
+
+def flux_jvp(w, s, m, ph):
+    """(dF^m/dw)(w) s, the directional derivative of the flux along s."""
+    if ph.law == ADVECTION:
+        return ph.a[m] * s
+    if ph.law == BURGERS:
+        return w * s
+    d = ph.dim
+    g, e2 = ph.gamma, ph.eps ** 2
+    rho, v, E, p = euler_primitives(w, ph)
+    srho, sE = s[0], s[d + 1]
+    smom = [s[1 + k] for k in range(d)]
+    # derivative of v_k = m_k / rho and of p
+    dv = [(smom[k] - v[k] * srho) / rho for k in range(d)]
+    v2 = sum(vk * vk for vk in v)
+    vdots = sum(v[k] * smom[k] for k in range(d))
+    dp = (g - 1.0) * (sE - e2 * vdots + 0.5 * e2 * v2 * srho)
+    J = np.empty_like(s)
+    J[0] = smom[m]
+    for k in range(d):
+        J[1 + k] = v[m] * smom[k] + v[k] * smom[m] - v[m] * v[k] * srho
+        if k == m:
+            J[1 + k] = J[1 + k] + dp / e2
+    J[d + 1] = dv[m] * (E + p) + v[m] * (sE + dp)
+    return J
+
+
+def lf_lambda(ph, m):
+    """Constant dissipation coefficient per variable (global LF, Eq. 13)."""
+    if ph.law == ADVECTION:
+        lam = np.array([abs(ph.a[m])])
+    elif ph.law == BURGERS:
+        lam = np.array([1.0])
+    else:
+        lam = np.ones(ph.nv)
+        lam[0] = 1.0 / ph.eps
+        lam[-1] = 1.0 / ph.eps
+    return ph.lf_scale * lam
+
+
+def max_speed(w, m, ph):
+    """Largest |eigenvalue| of dF^m/dw at w (per point)."""
+    if ph.law == ADVECTION:
+        return np.full(w.shape[1:], abs(ph.a[m]))
+    if ph.law == BURGERS:
+        return cs_abs(w[0])
+    rho, v, E, p = euler_primitives(w, ph)
+    c = np.sqrt(ph.gamma * p / rho) / ph.eps
+    return cs_abs(v[m]) + c
+
+
+def dissipation(wL, wR, m, ph):
+    """The coefficient kappa multiplying (w^L - w^R) in the numerical flux;
+    broadcastable against a state array with variables on axis 0."""
+    if ph.flux == "lf":
+        lam = lf_lambda(ph, m)
+        return lam.reshape((-1,) + (1,) * (wL.ndim - 1))
+    if ph.flux == "rusanov":
+        return 0.5 * cs_max(max_speed(wL, m, ph), max_speed(wR, m, ph))[None]
+    raise ValueError(ph.flux)

@@ -1,0 +1,339 @@
+"""Benchmark of the HBPC-DGSEM hot path on one GB300.
+
+Workload (default): 2-D linear advection u_t + div((1, 1) u) = 0 on the periodic
+unit square, 64 x 64 elements, N = 5 (Gauss-Lobatto), u0 = sin(2 pi x) sin(2 pi y),
+HBPC(8, 4) (the highest order of the paper), CFL 8 -> dt = 1/96, matrix-free
+Newton-GMRES with the paper's BJ_ext preconditioner, eps_Newton = 1e-12 with
+the absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5, FP64.  One bench step = one HBPC time step (15 implicit
+stage solves).  Metric: DOF-timesteps/s = n_dof x steps / device seconds.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the path has no data-path collective), value = sum over ranks / max time.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host on
+a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-timesteps/s per HBPC step at fixed L2 error; learned vs plain GMRES"
+UNIT = "DOF-timesteps/s"
+
+WL = dict(dim=2, n=(64, 64), lo=(0.0, 0.0), hi=(1.0, 1.0), N=5, a=(1.0, 1.0), q=8, kmax=4,
+          cfl=8.0, t_end=1.0, tol_newton_rel=1e-12, tol_newton_abs=1e-12, tol_gmres_rel=1e-5,
+          gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50)
+
+
+def workload_dt():
+    # dt_raw = CFL / sum_m(|a_m| p / h_m), rounded to T_end / ceil(T_end / dt_raw)
+    p = WL["N"] + 1
+    s = sum(abs(WL["a"][m]) * p / ((WL["hi"][m] - WL["lo"][m]) / WL["n"][m]) for m in range(WL["dim"]))
+    raw = WL["cfl"] / s
+    return WL["t_end"] / np.ceil(WL["t_end"] / raw - 1e-12)
+
+
+def config_dict(dt, extra=None):
+    c = {"workload": "2d_linear_advection_64x64_N5_HBPC(8,4)_CFL8_BJext_GMRES",
+         "mesh": "64x64 periodic [0,1]^2", "N": 5, "nodes": "Gauss-Lobatto", "hbpc": "q=8,kmax=4",
+         "dt": dt, "eps_newton": WL["tol_newton_rel"], "newton_abs_dW": WL["tol_newton_abs"],
+         "eps_gmres": WL["tol_gmres_rel"],
+         "gmres_restart": WL["gmres_restart"], "preconditioner": "BJ_ext (Sec. 3.2.3)",
+         "l2_between_steps": "flushed (256 MB write) between timed steps"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def exact_solution(coords, t):
+    from paper_2109_04804_gb300 import inputs
+    sh = [c - a * t for c, a in zip(coords, WL["a"])]
+    return inputs.sine_product(sh)
+
+
+# -- algorithmic work per launch (bytes, flops per W-DOF) ----------------------
+def jv_work_per_dof():
+    """Linear Jv (Eq. 24): reads dW, dS and writes the two outputs: 32 B per
+    W-DOF.  Flops: two R1 passes, each 2*d*p (volume) + 2*d/p face points x 7
+    (flux 5, lifting 2), plus 3 FMAs to combine."""
+    d, p = WL["dim"], WL["N"] + 1
+    r1 = 2 * d * p + (2 * d / p) * 7
+    return 32.0, 2 * r1 + 6
+
+
+def pc_work_per_dof():
+    """BJ_ext apply: per element it reads M_i and J_i (2 n_b^2 doubles), the two
+    input halves and writes the two output halves: (16 n_b + 32) B per W-DOF;
+    four n_b x n_b matrix-vector products: 8 n_b flops per W-DOF (+ 4)."""
+    nb = (WL["N"] + 1) ** WL["dim"]
+    return 16.0 * nb + 32.0, 8.0 * nb + 4.0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    dt = workload_dt()
+    stream = torch.cuda.Stream()
+    ctx = hbpc.Context(WL["dim"], WL["n"], WL["lo"], WL["hi"], WL["N"], law=hbpc.LAW_ADVECTION,
+                       a=WL["a"], q=WL["q"], kmax=WL["kmax"], dt=dt,
+                       tol_newton_rel=WL["tol_newton_rel"], tol_newton_abs=WL["tol_newton_abs"],
+                       tol_gmres_rel=WL["tol_gmres_rel"], gmres_restart=WL["gmres_restart"],
+                       gmres_max_iter=WL["gmres_max_iter"], newton_max_iter=WL["newton_max_iter"],
+                       pc=hbpc.PC_BJEXT, stream=stream.cuda_stream)
+    coords = ctx.node_coords()
+    w0 = inputs.sine_product(coords)
+    ctx.set_state(w0)
+    ndof = ctx.ndof
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)             # L2 flush outside the timed window
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats = ctx.stats()
+    t_sec = total_ms / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_sec], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sec = float(tt.item())
+        torch.distributed.barrier()
+    value = ndof * args.steps * world / t_sec
+    r1_per_s = (stats["r1_evals"] + stats["r2_evals"]) / t_sec
+    # accuracy: L2 error vs the exact solution at the final time
+    w = ctx.get_state()
+    t_fin = (args.warmup + args.steps) * dt
+    err = float(np.sqrt(np.mean((w - exact_solution(coords, t_fin)) ** 2)))
+
+    # per-phase device time from a separate profiled step (events around launches)
+    ctx.profile(True)
+    ctx.step(1)
+    prof = ctx.profile_get()
+    pstats = ctx.stats()
+    ctx.profile(False)
+    # roofline of the dominant kernel phase (FP64 on GB300 is ALU-bound: the
+    # denominator is the measured FP64 FMA throughput; HBM fraction alongside)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    fp64_peak = hbpc.fp64_fma_peak()          # measured live on this GPU
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kernels = {"jv": ("dg_operator_kernel<advection,2D,P=6,JobJvLinear> (Eq. 24)", jv_work_per_dof()),
+               "pc_apply": ("k_pc_apply (BJ_ext, Sec. 3.2.3)", pc_work_per_dof())}
+    entries = {}
+    for ph, (name, (bpd, fpd)) in kernels.items():
+        ms, n = prof[ph]
+        if n == 0:
+            continue
+        avg = ms / 1000.0 / n
+        gf = fpd * ndof / avg / 1e9
+        gb = bpd * ndof / avg / 1e9
+        entries[ph] = {"kernel": name, "bound": "alu", "achieved": round(gf / 1000.0, 4),
+                       "peak": fp64_peak / 1000.0, "unit": "TFLOP/s", "frac": round(gf / fp64_peak, 4),
+                       "traffic": None, "hbm_achieved_gbs": round(gb, 1),
+                       "hbm_frac_of_measured": round(gb / hbm, 4), "avg_launch_us": round(avg * 1e6, 2),
+                       "launches_profiled": n, "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3)}
+    dom = max(entries, key=lambda k: prof[k][0])
+    roofline = dict(entries[dom])
+    roofline["peak_source"] = "FP64 FMA throughput measured in this run (hbpc_fp64_fma_peak)"
+    roofline["phase_ms_one_step"] = {k: round(v[0], 3) for k, v in prof.items()}
+    roofline["phase_launches_one_step"] = {k: v[1] for k, v in prof.items()}
+    roofline["other_kernels"] = {k: v for k, v in entries.items() if k != dom}
+
+    # e2e: the public API with host buffers, copies inside the timed region
+    host_in = torch.from_numpy(w0.copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state_host_ptr(host_in.data_ptr())
+        ctx.step(1)
+        ctx.get_state_host_ptr(host_out.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
+    ctx.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(dt, {"parallelism": "replicas" if world > 1 else "single"}),
+            "r1_evals_per_s": r1_per_s, "l2_error_vs_exact": err,
+            "gmres_its_per_step": stats["gmres_its"] / args.steps,
+            "newton_its_per_step": stats["newton_its"] / args.steps,
+            "gpu_launches": int(stats["launches"]), "roofline": roofline, "e2e": e2e, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(dt)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(dt, budget_s=20.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload: the first predictor stage solve of one HBPC(8,4) step (one of
+    its 15 stage solves), scaled to a full step."""
+    from oracle import dgsem, laws, newton
+    from paper_2109_04804_gb300 import inputs
+    ph = laws.Physics(laws.ADVECTION, 2, a=WL["a"])
+    disc = dgsem.Disc(dgsem.Mesh(2, WL["n"], WL["lo"], WL["hi"]), WL["N"], ph)
+    w0 = inputs.sine_product(disc.node_coords())
+    opts = newton.NewtonOptions(tol_rel=WL["tol_newton_rel"], tol_abs=WL["tol_newton_abs"],
+                                gmres_tol=WL["tol_gmres_rel"], restart=WL["gmres_restart"],
+                                jv="linear", pc="bjext")
+    dc = 1.0 / 3.0
+    a1, a2 = dc / 2.0, dc * dc / 6.0
+    r1 = dgsem.R1(disc, w0)
+    b = w0 + a1 * dt * r1 + (a2 * dt * dt / 2.0) * dgsem.R2(disc, w0, r1)
+    t0 = time.perf_counter()
+    _, _, st = newton.newton_solve(disc, b, a1, a2, dt, w0, opts)
+    t1 = time.perf_counter() - t0
+    solves_per_step = (4 - 1) * (1 + 4)
+    step_s = t1 * solves_per_step
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    return {"value": disc.ndof / step_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "first predictor stage solve of one HBPC(8,4) step on the full 64x64 N=5 "
+                      "mesh (%d GMRES its, %.1f s), scaled x%d stage solves per step"
+                      % (st.gmres_its, t1, solves_per_step)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    dt = workload_dt()
+    vals = []
+    sample = None
+    t_all = time.perf_counter()
+    for _ in range(max(1, args.warmup) + max(1, args.steps)):
+        cb = cpu_baseline(dt)
+        vals.append(cb["value"])
+        sample = cb
+        if time.perf_counter() - t_all > 240:
+            break
+    timed = vals[-max(1, args.steps):]
+    value = float(np.mean(timed))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * 147456 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(dt), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
+                             "sample": sample["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

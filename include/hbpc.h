@@ -1,0 +1,212 @@
+/*
+ * hbpc.h -- C-ABI of libhbpc, a GB300 (sm_103a) implementation of the implicit
+ * two-derivative deferred-correction time discretisation HBPC(q, k_max) for the
+ * discontinuous Galerkin spectral element method (Zeifang & Schuetz, "Two-
+ * derivative deferred correction time discretization for the discontinuous
+ * Galerkin method").
+ *
+ * Conventions
+ *  - Every function returns hbpc_status (0 = HBPC_OK) and never aborts or exits;
+ *    hbpc_last_error() returns a message for the last failure of a context.
+ *  - State layout (host and device): canonical FP64 array w[e][v][k][j][i] --
+ *    element e = ex + nx*(ey + ny*ez), variable v, node indices (only the last
+ *    `dim` of k, j, i exist), i fastest.  n_dof = n_E * n_var * (N+1)^dim.
+ *  - Pointers documented as "device" must be device memory of the context's
+ *    device (cudaMalloc, cudaMallocManaged or a framework allocator); "host"
+ *    pointers are ordinary host memory.  The caller owns every buffer it passes;
+ *    the library copies what it keeps.  All device work is enqueued on the
+ *    stream given at creation (NULL = legacy default stream) and the calls
+ *    return after that stream has finished the call's work.
+ *  - Meshes are uniform, Cartesian and periodic in every direction.
+ *  - Invalid arguments are rejected before anything is allocated or launched.
+ */
+#ifndef HBPC_H
+#define HBPC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HBPC_OK = 0,
+  HBPC_ERR_INVALID_ARG = 1,    /* bad parameter; nothing was done */
+  HBPC_ERR_OOM = 2,            /* a device allocation failed */
+  HBPC_ERR_CUDA = 3,           /* a CUDA call failed (message has the CUDA error) */
+  HBPC_ERR_NO_CONVERGENCE = 4, /* Newton or GMRES iteration cap reached */
+  HBPC_ERR_NONFINITE = 5,      /* a residual or update norm is NaN or Inf */
+  HBPC_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+  HBPC_ERR_UNSUPPORTED = 7     /* valid request that this build does not cover */
+} hbpc_status;
+
+/* Conservation laws.  ADVECTION: w_t + div(a w) = 0 (Sec. 4.1.1).
+ * BURGERS: w_t + div((w^2/2)(1,..,1)) = 0 (inviscid part of the Burgers workload).
+ * EULER: compressible Euler with reference Mach number eps (Eq. 21). */
+typedef enum { HBPC_LAW_ADVECTION = 0, HBPC_LAW_BURGERS = 1, HBPC_LAW_EULER = 2 } hbpc_law;
+
+/* Numerical flux of Eq. 13: f* = 1/2 (F(wL) + F(wR)) . n + kappa (wL - wR).
+ * GLOBAL_LF: kappa is a global constant per variable, lf_scale times the paper's
+ *   lambda: |a.n| (advection), 1 (Burgers), diag(1/eps, 1, .., 1, 1/eps) (Euler).
+ * RUSANOV: kappa = 1/2 max(|v_n| + c) over the two traces (frozen, i.e. not
+ *   differentiated, in R2 and in the linearised operator). */
+typedef enum { HBPC_FLUX_GLOBAL_LF = 0, HBPC_FLUX_RUSANOV = 1 } hbpc_flux;
+
+/* Node family of the 1-D basis (Sec. 3.1.1). */
+typedef enum { HBPC_NODES_LOBATTO = 0, HBPC_NODES_GAUSS = 1 } hbpc_nodes;
+
+/* Preconditioner of the extended linear system (Sec. 3.2.3).  NONE: plain
+ * GMRES.  BJEXT: the BJ_ext block preconditioner, right preconditioning; needs
+ * n_var (N+1)^dim <= 160 and 2 n_E (n_var (N+1)^dim)^2 doubles of device memory. */
+typedef enum { HBPC_PC_NONE = 0, HBPC_PC_BJEXT = 1 } hbpc_pc;
+
+/* Arithmetic of the Krylov loop.  FP64: everything in FP64, Jv by the
+ * difference quotients of Eq. 23 (Eq. 24 for a linear flux).  MIXED: the
+ * Newton residual, the update and the stage logic stay FP64; the Krylov basis
+ * and the Jacobian-vector products use FP32 with the analytic linearised
+ * operator dR1/dw v = R2(w, v) (Sec. 3.2.1). */
+typedef enum { HBPC_PREC_FP64 = 0, HBPC_PREC_MIXED = 1 } hbpc_precision;
+
+typedef struct {
+  int dim;          /* 1, 2 or 3 */
+  int n[3];         /* elements per direction (n[m] >= 1 for m < dim) */
+  double lo[3];     /* domain [lo, hi] per direction */
+  double hi[3];
+} hbpc_mesh;
+
+typedef struct {
+  int law;          /* hbpc_law */
+  int flux;         /* hbpc_flux */
+  double a[3];      /* advection velocity */
+  double gamma;     /* ratio of specific heats (Euler) */
+  double eps;       /* reference Mach number eps (Euler, Eq. 21); also enters
+                       eps_FD of Eq. 23 for every law (use 1 for advection) */
+  double lf_scale;  /* multiplies the global-LF lambda; 1 = Eq. 13 as printed */
+} hbpc_physics;
+
+typedef struct {
+  int q;                 /* order of the quadrature: 4, 6 or 8 (Eq. A.1-A.3) */
+  int kmax;              /* corrector sweeps, >= 0 */
+  double dt;             /* time step, > 0 */
+  double tol_newton_rel; /* ||G(X^r)|| <= tol * ||G(X^0)|| (Sec. 3.2.1) */
+  double tol_newton_abs; /* or ||dW||_2 <= tol_abs (Sec. 5.2); 0 disables */
+  double tol_gmres_rel;  /* GMRES relative tolerance */
+  int gmres_restart;     /* Krylov dimension per cycle, 1..1000 */
+  int gmres_max_iter;    /* GMRES iterations per Newton step (cap), >= 1 */
+  int newton_max_iter;   /* Newton iterations per stage solve (cap), >= 1 */
+  int pc;                /* hbpc_pc */
+  int precision;         /* hbpc_precision */
+} hbpc_solver;
+
+typedef struct {
+  long long steps;        /* HBPC steps taken */
+  long long newton_solves;
+  long long newton_its;
+  long long gmres_its;
+  long long r1_evals;     /* full-mesh operator passes (R1, R2 or linearised) */
+  long long r2_evals;
+  long long launches;     /* kernel launches issued by the library */
+  double t;               /* simulated time */
+} hbpc_stats;
+
+/* Phases of the per-launch device timing (hbpc_profile_*). */
+enum {
+  HBPC_PHASE_JV = 0,        /* Jacobian-vector product passes (Eq. 23/24) */
+  HBPC_PHASE_OPERATOR = 1,  /* residual, R1, R2 passes outside the Krylov loop */
+  HBPC_PHASE_DOT = 2,       /* Arnoldi multi-dot passes */
+  HBPC_PHASE_UPDATE = 3,    /* Arnoldi update + norm passes */
+  HBPC_PHASE_VECTOR = 4,    /* norms, solution update, stage combinations */
+  HBPC_PHASE_PC = 5,        /* BJ_ext apply */
+  HBPC_PHASE_PC_BUILD = 6,  /* BJ_ext assembly, S = I - c1 J + c2 J^2, inverse */
+  HBPC_NPHASES = 7
+};
+
+typedef struct hbpc_ctx hbpc_ctx;
+
+/* Create a context: computes the basis (Sec. 3.1.1) on the host, allocates all
+ * device memory the method needs and binds to the current CUDA device and the
+ * given stream (cudaStream_t, NULL = default).  N >= 1 and (N+1) <= 8. */
+hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
+                        const hbpc_physics* phys, const hbpc_solver* solver,
+                        void* cuda_stream);
+
+/* Free all device memory of the context.  Accepts NULL. */
+void hbpc_destroy(hbpc_ctx* ctx);
+
+/* Number of state values n_dof and of variables per node. */
+long long hbpc_ndof(const hbpc_ctx* ctx);
+int hbpc_nvar(const hbpc_ctx* ctx);
+
+/* Physical node coordinates, host output x[dim][n_E][(N+1)^dim] (FP64). */
+hbpc_status hbpc_node_coords(const hbpc_ctx* ctx, double* x);
+
+/* 1-D basis of degree N (Sec. 3.1.1), host outputs: nodes xi[N+1], weights
+ * w[N+1], Dhat[(N+1)*(N+1)] row-major with Dhat[i][j] = -(w_j/w_i) l_i'(xi_j),
+ * lm[N+1] = l_i(-1), lp[N+1] = l_i(+1).  Any output may be NULL. */
+hbpc_status hbpc_basis(int N, int nodes, double* xi, double* w, double* Dhat,
+                       double* lm, double* lp);
+
+/* Copy the state w^n in (out): `w` has n_dof FP64 values, on the device if
+ * on_device != 0, else on the host. */
+hbpc_status hbpc_set_state(hbpc_ctx* ctx, const double* w, int on_device);
+hbpc_status hbpc_get_state(const hbpc_ctx* ctx, double* w, int on_device);
+hbpc_status hbpc_set_time(hbpc_ctx* ctx, double t);
+
+/* Advance the state by n_steps HBPC(q, k_max) steps (Algorithm 1, Sec. 2.1).
+ * On non-convergence the state stays at the last completed step and
+ * HBPC_ERR_NO_CONVERGENCE is returned. */
+hbpc_status hbpc_step(hbpc_ctx* ctx, int n_steps);
+
+/* r = R1(w), Eq. 12 with the flux of Eq. 13.  w, r: device, n_dof FP64. */
+hbpc_status hbpc_eval_R1(hbpc_ctx* ctx, const double* w, double* r);
+
+/* r = R2(w, s), Eq. 16.  w, s, r: device, n_dof FP64. */
+hbpc_status hbpc_eval_R2(hbpc_ctx* ctx, const double* w, const double* s, double* r);
+
+/* Extended residual of one implicit stage (Sec. 3.2.1):
+ *   G = (W - b - alpha1 dt R1(W) + alpha2 dt^2/2 R2(W, S),  S - R1(W)).
+ * X = (W, S) and G are device arrays of 2 n_dof FP64, b of n_dof. */
+hbpc_status hbpc_eval_G(hbpc_ctx* ctx, const double* b, double alpha1, double alpha2,
+                        const double* X, double* G);
+
+/* Jacobian-vector product of the stage system at X applied to dX (Eq. 23, or
+ * Eq. 24 for a linear flux; the context's precision selects the form).
+ * X, dX, out: device, 2 n_dof FP64. */
+hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
+                         const double* dX, double* out);
+
+/* BJ_ext preconditioner (Sec. 3.2.3) built at the state W of X = (W, S) for the
+ * stage coefficients alpha1, alpha2, applied to `in`: out = P^-1 in.  Needs a
+ * context created with pc = HBPC_PC_BJEXT.  X, in, out: device, 2 n_dof FP64. */
+hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
+                         const double* in, double* out);
+
+/* Solve one implicit stage G(X) = 0 (Eq. 7-9) by Newton-GMRES from
+ * X^0 = (W0, R1(W0)).  b, W0: device n_dof; W_out, S_out: device n_dof (S_out
+ * may be NULL). */
+hbpc_status hbpc_newton_solve(hbpc_ctx* ctx, const double* b, double alpha1, double alpha2,
+                              const double* W0, double* W_out, double* S_out);
+
+hbpc_status hbpc_get_stats(const hbpc_ctx* ctx, hbpc_stats* out);
+hbpc_status hbpc_reset_stats(hbpc_ctx* ctx);
+
+/* Per-launch device timing: while enabled, every kernel launch of the context
+ * is bracketed by CUDA events on its stream (this adds a little host overhead;
+ * use it in a separate measurement pass).  hbpc_profile_get writes, per phase
+ * (HBPC_PHASE_*), the summed device milliseconds and the number of launches
+ * into host arrays of n_phases entries; hbpc_profile_enable(ctx, 1) clears. */
+hbpc_status hbpc_profile_enable(hbpc_ctx* ctx, int enable);
+hbpc_status hbpc_profile_get(hbpc_ctx* ctx, double* ms, long long* launches, int n_phases);
+
+/* FP64 FMA throughput of the current device in GFLOP/s (a few milliseconds of
+ * independent FMA chains on every SM, best of three, CUDA events).  Used as the
+ * arithmetic roofline of the FP64 kernels.  Allocates and frees a small buffer. */
+hbpc_status hbpc_fp64_fma_peak(double* gflops);
+
+/* Message of the last failure on this context (static storage owned by the
+ * context; "" if none).  Accepts NULL (returns the message of the last failed
+ * hbpc_create). */
+const char* hbpc_last_error(const hbpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HBPC_H */

@@ -1,0 +1,135 @@
+// BJ_ext block preconditioner (Sec. 3.2.3) on the device.
+//
+//   J_i = dR1/dW restricted to element i with the neighbours' traces frozen
+//   S_i = A_i - B_i C_i = I - c1 J_i + c2 J_i^2        (c1 = a1 dt, c2 = a2 dt^2/2)
+//   M_i = S_i^-1
+//   P^-1 (w, s) = (D w + E s, F w + G s) with D = M, E = -B M, F = -C M, G = A M,
+//   A = I - c1 J, B = c2 J, C = -J; because J commutes with M this is applied as
+//     u = M w, v = M s,  top = u - c2 J v,  bottom = J u + v - c1 J v.
+//
+// Storage: per element an n_b x n_b block, column-major (entry (r, c) at
+// c * n_b + r), n_b = n_var (N+1)^dim, so that the threads of one element, one
+// per row, read consecutive addresses.
+#pragma once
+#include "dg_common.cuh"
+#include "krylov_common.cuh"
+
+namespace hbpc {
+
+// Assembly of J_i from the structure of Eq. 12: the column of node q, variable
+// u has, for every direction m, the volume entries Dvol[m][r_m][q_m] A^m(w_q)
+// along the line of q, and the face entries of the lifted numerical flux's
+// derivative with respect to the element's own trace (the neighbour is frozen).
+template <int LAW, int DIM, int P, bool LGL>
+__global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ W,
+                                                     double* __restrict__ Jout,
+                                                     const DGParams<double> prm) {
+  using L = typename LawOf<LAW, DIM, double>::type;
+  constexpr int NV = L::NV, NN = ipow(P, DIM), NB = NV * NN;
+  const int e = blockIdx.x;
+  if (e >= prm.nE) return;
+  double* J = Jout + size_t(e) * NB * NB;
+  __shared__ double sw[NB];
+  for (int t = threadIdx.x; t < NB; t += blockDim.x) sw[t] = W[size_t(e) * NB + t];
+  for (size_t t = threadIdx.x; t < size_t(NB) * NB; t += blockDim.x) J[t] = 0.0;
+  __syncthreads();
+  int ec[3];
+  ec[0] = e % prm.n[0];
+  ec[1] = (e / prm.n[0]) % prm.n[1];
+  ec[2] = e / (prm.n[0] * prm.n[1]);
+  for (int col = threadIdx.x; col < NB; col += blockDim.x) {
+    const int u = col / NN, q = col - u * NN;
+    double* Jc = J + size_t(col) * NB;
+    int qi[3] = {q % P, (q / P) % P, q / (P * P)};
+    double wq[NV], eu[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { wq[v] = sw[v * NN + q]; eu[v] = (v == u) ? 1.0 : 0.0; }
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
+      const int b0 = q - qi[m] * st;
+      double a[NV];
+      if constexpr (L::LINEAR) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a[v] = eu[v];      // a_m is folded into Dvol
+      } else {
+        L::jvp(wq, eu, m, a, prm);
+      }
+      // volume: output node r = b0 + l*st receives Dvol[m][l][q_m] * a
+      for (int l = 0; l < P; ++l)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Jc[v * NN + b0 + l * st] += prm.Dvol[m][l][qi[m]] * a[v];
+      // faces: own traces at the - and + face of the line through q
+      double Ap[NV];
+      L::jvp(wq, eu, m, Ap, prm);   // dF^m/dw at w_q applied to e_u (used for Lobatto)
+      for (int side = 0; side < 2; ++side) {
+        const double lq = side ? prm.lp[qi[m]] : prm.lm[qi[m]];   // d(own trace)/d(w_q)
+        if (lq == 0.0) continue;
+        // own trace t_o and neighbour trace t_n at this face point
+        double to[NV], tn[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { to[v] = 0.0; tn[v] = 0.0; }
+        int nc[3] = {ec[0], ec[1], ec[2]};
+        nc[m] += side ? 1 : -1;
+        if (nc[m] < 0) nc[m] += prm.n[m];
+        if (nc[m] >= prm.n[m]) nc[m] -= prm.n[m];
+        const int en = nc[0] + prm.n[0] * (nc[1] + prm.n[1] * nc[2]);
+        for (int i = 0; i < P; ++i) {
+          const double lo = side ? prm.lp[i] : prm.lm[i];
+          const double ln = side ? prm.lm[i] : prm.lp[i];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            to[v] += lo * sw[v * NN + b0 + i * st];
+            tn[v] += ln * W[(size_t(en) * NV + v) * NN + b0 + i * st];
+          }
+        }
+        double A[NV], kap[NV];
+        if (LGL) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) A[v] = Ap[v];
+        } else {
+          L::jvp(to, eu, m, A, prm);
+        }
+        if (prm.rusanov) {
+          const double c = 0.5 * fmax(L::speed(to, m, prm), L::speed(tn, m, prm));
+#pragma unroll
+          for (int v = 0; v < NV; ++v) kap[v] = c;
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) kap[v] = prm.lam[m][v];
+        }
+        // + face: f = 1/2 (F(t_o) + F(t_n)) + kap (t_o - t_n)      -> df/dt_o = A/2 + kap
+        // - face: f = -(1/2 (F(t_n) + F(t_o)) + kap (t_n - t_o))  -> df/dt_o = -A/2 + kap
+        for (int l = 0; l < P; ++l) {
+          const double lift = side ? prm.sp[m][l] : prm.sm[m][l];
+          if (lift == 0.0) continue;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const double d = (side ? 0.5 : -0.5) * A[v] + kap[v] * eu[v];
+            Jc[v * NN + b0 + l * st] += lift * lq * d;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Apply P^-1 to x = scale * (xW, xS) (element blocks of n_b values), result to
+// (oW, oS) (added when accumulate != 0), and the norms of the result's halves
+// (unscaled, square-rooted) to zn[0..2] (total, W, S) through the last block.
+// EPB elements per block, one thread per row.
+struct PcApply {
+  const double* M; const double* J;
+  const double* xW; const double* xS;
+  const double* scale;          // device scalar or null (1)
+  const int* jidx;              // column index for xW/xS (stride ld), null -> 0
+  size_t ld;
+  double* oW; double* oS;
+  const double* c12;            // device c1, c2
+  const int* skip;
+  int accumulate;
+  double* zn;
+  int nb, nE;
+};
+
+}  // namespace hbpc

@@ -1,0 +1,187 @@
+// BJ_ext kernels that do not depend on the conservation law: S = I - c1 J +
+// c2 J^2, the batched Gauss-Jordan inverse and the apply P^-1 (Sec. 3.2.3).
+// Included by exactly one translation unit.
+#pragma once
+#include "bjext.cuh"
+
+namespace hbpc {
+
+// S = I - c1 J + c2 J^2 for one element per block (J staged in shared memory),
+// written to `S` (same layout).  Dynamic shared memory: nb * nb doubles.
+__global__ void __launch_bounds__(256) k_pc_form_S(const double* __restrict__ Jall,
+                                                   double* __restrict__ Sall, int nb, int nE,
+                                                   const double* c12) {
+  const int e = blockIdx.x;
+  if (e >= nE) return;
+  extern __shared__ double sJ[];
+  const double* J = Jall + size_t(e) * nb * nb;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) sJ[t] = J[t];
+  __syncthreads();
+  const double c1 = c12[0], c2 = c12[1];
+  double* S = Sall + size_t(e) * nb * nb;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int c = t / nb, r = t - c * nb;          // entry (r, c)
+    double jj = 0.0;
+    for (int k = 0; k < nb; ++k) jj += sJ[k * nb + r] * sJ[c * nb + k];   // (J J)(r, c)
+    S[t] = (r == c ? 1.0 : 0.0) - c1 * sJ[t] + c2 * jj;
+  }
+}
+
+// In-place inverse of one n_b x n_b block per thread block by Gauss-Jordan
+// elimination with partial (row) pivoting; the column exchanges implied by the
+// row pivots are undone at the end.  A zero pivot leaves the block unchanged and
+// sets *singular (the preconditioner is then skipped by the host).
+// Dynamic shared memory: (nb * nb + nb) doubles + nb ints.
+__global__ void __launch_bounds__(256) k_pc_invert(double* __restrict__ Mall, int nb, int nE,
+                                                   int* singular) {
+  const int e = blockIdx.x;
+  if (e >= nE) return;
+  extern __shared__ double smem[];
+  double* A = smem;                  // column-major nb x nb
+  double* colk = A + nb * nb;        // copy of the pivot column
+  int* perm = reinterpret_cast<int*>(colk + nb);
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  double* M = Mall + size_t(e) * nb * nb;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) A[t] = M[t];
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    // pivot: largest |A(i, k)|, i >= k (warp 0)
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < nb; i += 32) {
+        const double a = fabs(A[k * nb + i]);
+        if (a > best) { best = a; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        s_piv = bi;
+        perm[k] = bi;
+        if (!(best > 0.0)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_piv;
+    if (p != k)
+      for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        const double t = A[c * nb + k];
+        A[c * nb + k] = A[c * nb + p];
+        A[c * nb + p] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[k * nb + k];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) colk[i] = A[k * nb + i];
+    __syncthreads();
+    // row k scaled; column k becomes e_k scaled
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) A[c * nb + k] = (c == k ? 1.0 : A[c * nb + k]) * inv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+      const int c = t / nb, i = t - c * nb;
+      if (i == k) continue;
+      const double f = colk[i];
+      const double rk = A[c * nb + k];
+      A[t] = (c == k ? 0.0 : A[t]) - f * rk;
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) atomicExch(singular, 1);
+    return;
+  }
+  // undo the column interchanges in reverse order
+  for (int k = nb - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double t = A[k * nb + i];
+        A[k * nb + i] = A[p * nb + i];
+        A[p * nb + i] = t;
+      }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) M[t] = A[t];
+}
+
+__global__ void __launch_bounds__(256) k_pc_apply(PcApply a, Krylov K) {
+  if (a.skip && *a.skip) return;
+  const int nb = a.nb;
+  const int epb = blockDim.x / nb;
+  const int le = threadIdx.x / nb, r = threadIdx.x - le * nb;
+  const int e = blockIdx.x * epb + le;
+  const bool live = le < epb && e < a.nE;
+  extern __shared__ double sm[];
+  double* xw = sm + le * 4 * nb;
+  double* xs = xw + nb;
+  double* su = xs + nb;
+  double* sv = su + nb;
+  const size_t off = (a.jidx ? size_t(*a.jidx) * a.ld : 0) + size_t(e) * nb;
+  const double sc = a.scale ? (a.jidx ? a.scale[*a.jidx] : *a.scale) : 1.0;
+  if (live) {
+    xw[r] = sc * a.xW[off + r];
+    xs[r] = sc * a.xS[off + r];
+  }
+  __syncthreads();
+  double u = 0.0, v = 0.0;
+  if (live) {
+    const double* Me = a.M + size_t(e) * nb * nb;
+    for (int c = 0; c < nb; ++c) {
+      const double m = Me[size_t(c) * nb + r];
+      u += m * xw[c];
+      v += m * xs[c];
+    }
+    su[r] = u;
+    sv[r] = v;
+  }
+  __syncthreads();
+  double aw = 0.0, as = 0.0;
+  if (live) {
+    const double* Je = a.J + size_t(e) * nb * nb;
+    double ju = 0.0, jv = 0.0;
+    for (int c = 0; c < nb; ++c) {
+      const double j = Je[size_t(c) * nb + r];
+      ju += j * su[c];
+      jv += j * sv[c];
+    }
+    const double c1 = a.c12[0], c2 = a.c12[1];
+    double top = u - c2 * jv;
+    double bot = ju + v - c1 * jv;
+    const size_t o = size_t(e) * nb + r;
+    if (a.accumulate) { top += a.oW[o]; bot += a.oS[o]; }
+    a.oW[o] = top;
+    a.oS[o] = bot;
+    aw = top * top;
+    as = bot * bot;
+  }
+  // norms of the result through the last block
+  __shared__ double s2[2][kVecWarps];
+  aw = warp_sum(aw);
+  as = warp_sum(as);
+  if ((threadIdx.x & 31) == 0) { s2[0][threadIdx.x >> 5] = aw; s2[1][threadIdx.x >> 5] = as; }
+  __syncthreads();
+  const int stride = K.m + 3;
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { ta += s2[0][w]; tb += s2[1][w]; }
+    K.partial[size_t(blockIdx.x) * stride + 0] = ta;
+    K.partial[size_t(blockIdx.x) * stride + 1] = tb;
+  }
+  if (!last_block(K.ticket, gridDim.x)) return;
+  __shared__ double rr[2];
+  reduce_partials(K.partial, stride, gridDim.x, 2, rr);
+  __syncthreads();
+  if (threadIdx.x == 0 && a.zn) {
+    a.zn[0] = sqrt(rr[0] + rr[1]);
+    a.zn[1] = sqrt(rr[0]);
+    a.zn[2] = sqrt(rr[1]);
+  }
+}
+
+}  // namespace hbpc

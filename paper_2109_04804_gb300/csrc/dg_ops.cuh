@@ -1,0 +1,453 @@
+// Element-batched DGSEM operator kernel (Eq. 12 for R1, Eq. 16 for R2).
+//
+// One thread per volume node; EPB elements per block.  Per operator evaluation:
+//   1. every node loads its state (and direction for R2), evaluates the nodal
+//      flux F^m(w) (R1) or (dF^m/dw) s (R2) for all directions and stores it in
+//      shared memory;
+//   2. the element's 2*DIM*P^(DIM-1) face points compute the numerical flux of
+//      Eq. 13 (R1) or the flux f~* of Sec. 3.1.2 (R2) from the element's own
+//      trace (shared memory) and the neighbour's trace (global memory, L2) and
+//      store it in shared memory -- each face is evaluated by both of its
+//      elements, which keeps the pass free of any grid-wide dependency;
+//   3. every node contracts the fluxes with Dvol along each direction and adds
+//      the lifted face fluxes.
+// A Job supplies how node values are loaded (so that perturbed states W + eps dW
+// are formed on the fly) and what is done with the results (the epilogue), so
+// Jacobian-vector products and residuals are single passes over memory.
+#pragma once
+#include "dg_common.cuh"
+
+namespace hbpc {
+
+enum EvalKind { EV_R1 = 0, EV_R2 = 1 };
+
+template <int DIM, int P>
+struct Geo {
+  static constexpr int NN = ipow(P, DIM);        // nodes per element
+  static constexpr int NF = ipow(P, DIM - 1);    // nodes per face
+  static constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
+  static constexpr int THREADS = EPB * NN;
+};
+
+template <int LAW, int DIM, int P>
+struct KernelShape {
+  static constexpr int NV = (LAW == LAW_EULER) ? DIM + 2 : 1;
+  static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF, EPB = Geo<DIM, P>::EPB;
+  // shared values per element: state + direction + DIM fluxes + 2*DIM faces
+  static constexpr int PER_ELEM = 2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF;
+  static constexpr int MATS = DIM * P * P + 2 * DIM * P;
+  template <typename T>
+  static constexpr size_t smem_bytes() { return (size_t(EPB) * PER_ELEM + MATS) * sizeof(T); }
+};
+
+// Numerical flux at one face point of direction M and side SIDE (0: -, 1: +)
+// of the thread's element: Eq. 13 for R1, the flux f~* of Sec. 3.1.2 for R2.
+// Direction and side are compile-time so that every array stays in registers.
+template <int LAW, int DIM, int P, bool LGL, typename T, class Job>
+struct FaceFlux {
+  using L = typename LawOf<LAW, DIM, T>::type;
+  static constexpr int NV = L::NV, NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
+  template <int M, int SIDE>
+  __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, int k, bool r2,
+                                             const int* ec, int pt, const T* sst, const T* sdir,
+                                             T* sface) {
+    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    const int base = (pt % st) + (pt / st) * st * P;   // face point -> node with idx_M = 0
+    // neighbour element across this face (periodic)
+    int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
+    int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
+    c += SIDE ? 1 : -1;
+    if (c < 0) c += prm.n[M];
+    if (c >= prm.n[M]) c -= prm.n[M];
+    const int en = nc0 + prm.n[0] * (nc1 + prm.n[1] * nc2);
+    T wo[NV], wn[NV], so[NV], sn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { wo[v] = T(0); wn[v] = T(0); so[v] = T(0); sn[v] = T(0); }
+    if constexpr (LGL) {
+      const int own_node = base + (SIDE ? (P - 1) * st : 0);
+      const int nb_node = base + (SIDE ? 0 : (P - 1) * st);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wo[v] = sst[v * NN + own_node];
+        if (r2) so[v] = sdir[v * NN + own_node];
+      }
+      job.load_state(k, en, nb_node, wn);
+      if (r2) job.load_dir(k, en, nb_node, sn);
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int node = base + i * st;
+        const T lo = SIDE ? prm.lp[i] : prm.lm[i];   // own trace at this face
+        const T ln = SIDE ? prm.lm[i] : prm.lp[i];   // neighbour's trace at this face
+        T tw[NV], ts[NV];
+        job.load_state(k, en, node, tw);
+        if (r2) job.load_dir(k, en, node, ts);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          wo[v] += lo * sst[v * NN + node];
+          wn[v] += ln * tw[v];
+          if (r2) { so[v] += lo * sdir[v * NN + node]; sn[v] += ln * ts[v]; }
+        }
+      }
+    }
+    // (L, R) = (own, neighbour) on the + face, (neighbour, own) on the - face
+    T wL[NV], wR[NV], sL[NV], sR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wL[v] = SIDE ? wo[v] : wn[v];
+      wR[v] = SIDE ? wn[v] : wo[v];
+      sL[v] = SIDE ? so[v] : sn[v];
+      sR[v] = SIDE ? sn[v] : so[v];
+    }
+    T FL[NV], FR[NV], kap[NV];
+    if (prm.rusanov) {
+      const T cmax = T(0.5) * fmax(L::speed(wL, M, prm), L::speed(wR, M, prm));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) kap[v] = cmax;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) kap[v] = prm.lam[M][v];
+    }
+    if (r2) { L::jvp(wL, sL, M, FL, prm); L::jvp(wR, sR, M, FR, prm); }
+    else { L::flux(wL, M, FL, prm); L::flux(wR, M, FR, prm); }
+    const T sgn = SIDE ? T(1) : T(-1);     // outward normal of the element
+    const int f = 2 * M + SIDE;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T jump = r2 ? (sL[v] - sR[v]) : (wL[v] - wR[v]);
+      sface[(f * NV + v) * NF + pt] = sgn * (T(0.5) * (FL[v] + FR[v]) + kap[v] * jump);
+    }
+  }
+};
+
+template <int LAW, int DIM, int P, bool LGL, typename T, class Job>
+__global__ void __launch_bounds__(Geo<DIM, P>::THREADS)
+dg_operator_kernel(const Job job, const DGParams<T> prm) {
+  using L = typename LawOf<LAW, DIM, T>::type;
+  using G = Geo<DIM, P>;
+  constexpr int NV = L::NV, NN = G::NN, NF = G::NF, EPB = G::EPB;
+  constexpr int PER_ELEM = KernelShape<LAW, DIM, P>::PER_ELEM;
+
+  if (!job.active()) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // operator matrices first (indexed by node, so kept out of the constant bank)
+  T* const sD = reinterpret_cast<T*>(smem_raw);              // [DIM][P][P]
+  T* const sSp = sD + DIM * P * P;                           // [DIM][P]
+  T* const sSm = sSp + DIM * P;                              // [DIM][P]
+  for (int t = threadIdx.x; t < DIM * P * P; t += blockDim.x) {
+    const int m = t / (P * P), r = t - m * P * P;
+    sD[t] = prm.Dvol[m][r / P][r % P];
+  }
+  for (int t = threadIdx.x; t < DIM * P; t += blockDim.x) {
+    sSp[t] = prm.sp[t / P][t % P];
+    sSm[t] = prm.sm[t / P][t % P];
+  }
+  T* const smem = sSm + DIM * P;
+  const int le = threadIdx.x / NN;
+  const int n = threadIdx.x - le * NN;
+  const int e = blockIdx.x * EPB + le;
+  const bool live = e < prm.nE;
+  T* const sst = smem + le * PER_ELEM;     // [NV][NN] state
+  T* const sdir = sst + NV * NN;           // [NV][NN] direction (R2)
+  T* const sG = sdir + NV * NN;            // [DIM][NV][NN] nodal fluxes
+  T* const sface = sG + DIM * NV * NN;     // [2*DIM][NV][NF] face fluxes
+
+  int ec[3] = {0, 0, 0};
+  if (live) {
+    ec[0] = e % prm.n[0];
+    ec[1] = (e / prm.n[0]) % prm.n[1];
+    ec[2] = e / (prm.n[0] * prm.n[1]);
+  }
+  int idx[3] = {0, 0, 0};
+  idx[0] = n % P;
+  if (DIM > 1) idx[1] = (n / P) % P;
+  if (DIM > 2) idx[2] = n / (P * P);
+
+  T res[Job::K][NV];
+
+#pragma unroll
+  for (int k = 0; k < Job::K; ++k) {
+    const bool r2 = Job::kind(k) == EV_R2;
+    // -- 1. node values and nodal fluxes --------------------------------
+    if (live) {
+      T w[NV], s[NV];
+      job.load_state(k, e, n, w);
+      if (r2) job.load_dir(k, e, n, s);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        sst[v * NN + n] = w[v];
+        if (r2) sdir[v * NN + n] = s[v];
+      }
+      if constexpr (!L::LINEAR) {
+        T F[DIM][NV];
+        if (r2) L::jvp_all(w, s, F, prm); else L::flux_all(w, F, prm);
+#pragma unroll
+        for (int m = 0; m < DIM; ++m)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) sG[(m * NV + v) * NN + n] = F[m][v];
+      }
+    }
+    __syncthreads();
+    // -- 2. face fluxes ------------------------------------------------------
+    if (live) {
+      for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
+        const int f = fp / NF, pt = fp - f * NF;
+        using FF = FaceFlux<LAW, DIM, P, LGL, T, Job>;
+        switch (f) {
+          case 0: FF::template run<0, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 1: FF::template run<0, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 2: if constexpr (DIM > 1) FF::template run<1, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 3: if constexpr (DIM > 1) FF::template run<1, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 4: if constexpr (DIM > 2) FF::template run<2, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 5: if constexpr (DIM > 2) FF::template run<2, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          default: break;
+        }
+      }
+    }
+    __syncthreads();
+    // -- 3. volume contraction + lifting ---------------------------------------
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T acc = 0;
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
+          const int i = idx[m];
+          const int b0 = n - i * st;
+          const T* g;
+          if constexpr (L::LINEAR) g = (r2 ? sdir : sst) + v * NN;
+          else g = sG + (m * NV + v) * NN;
+          const T* Drow = sD + (m * P + i) * P;
+#pragma unroll
+          for (int l = 0; l < P; ++l) acc += Drow[l] * g[b0 + l * st];
+          const int pt = (n % st) + (n / (st * P)) * st;
+          const T* fm = sface + ((2 * m) * NV + v) * NF;
+          const T* fpl = sface + ((2 * m + 1) * NV + v) * NF;
+          if constexpr (LGL) {
+            if (i == P - 1) acc += sSp[m * P + P - 1] * fpl[pt];
+            if (i == 0) acc += sSm[m * P] * fm[pt];
+          } else {
+            acc += sSp[m * P + i] * fpl[pt] + sSm[m * P + i] * fm[pt];
+          }
+        }
+        res[k][v] = acc;
+      }
+    }
+    if (k + 1 < Job::K) __syncthreads();
+  }
+  if (live) job.epilogue(e, n, res);
+}
+
+// ---------------------------------------------------------------------------
+// Jobs.  Index of (element e, variable v, node n): (e * NV + v) * NN + n.
+// ---------------------------------------------------------------------------
+template <int NV, int NN, typename T>
+struct JobR1 {
+  static constexpr int K = 1;
+  const double* w; double* out;
+  __device__ static constexpr int kind(int) { return EV_R1; }
+  __device__ bool active() const { return true; }
+  __device__ void load_state(int, int e, int n, T* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = T(w[(size_t(e) * NV + v) * NN + n]);
+  }
+  __device__ void load_dir(int, int, int, T*) const {}
+  __device__ void epilogue(int e, int n, const T (*r)[NV]) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[(size_t(e) * NV + v) * NN + n] = double(r[0][v]);
+  }
+};
+
+template <int NV, int NN, typename T>
+struct JobR2 {
+  static constexpr int K = 1;
+  const double* w; const double* s; double* out;
+  __device__ static constexpr int kind(int) { return EV_R2; }
+  __device__ bool active() const { return true; }
+  __device__ void load_state(int, int e, int n, T* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = T(w[(size_t(e) * NV + v) * NN + n]);
+  }
+  __device__ void load_dir(int, int e, int n, T* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = T(s[(size_t(e) * NV + v) * NN + n]);
+  }
+  __device__ void epilogue(int e, int n, const T (*r)[NV]) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[(size_t(e) * NV + v) * NN + n] = double(r[0][v]);
+  }
+};
+
+// Extended residual of a stage (Sec. 3.2.1) from X = (W, S):
+//   r1 = R1(W), r2 = R2(W, S), G1 = W - b - c1 r1 + c2 r2, G2 = S - r1.
+template <int NV, int NN>
+struct JobResidual {
+  static constexpr int K = 2;
+  const double* W; const double* S; const double* b;
+  double c1, c2;
+  double* G1; double* G2; double* r1; double* r2;
+  __device__ static constexpr int kind(int k) { return k == 0 ? EV_R1 : EV_R2; }
+  __device__ bool active() const { return true; }
+  __device__ void load_state(int, int e, int n, double* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = W[(size_t(e) * NV + v) * NN + n];
+  }
+  __device__ void load_dir(int, int e, int n, double* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = S[(size_t(e) * NV + v) * NN + n];
+  }
+  __device__ void epilogue(int e, int n, const double (*r)[NV]) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      const double a = r[0][v], c = r[1][v];
+      r1[i] = a;
+      r2[i] = c;
+      G1[i] = W[i] - b[i] - c1 * a + c2 * c;
+      G2[i] = S[i] - a;
+    }
+  }
+};
+
+// Device-side description of the vector z a Jacobian-vector product acts on:
+// z = scale * V[:, col] where col = *jidx (device scalar; 0 if jidx is null),
+// scale = vscale[col] (1 if vscale is null) and nrmW[col], nrmS[col] are the
+// Euclidean norms of the unscaled W and sigma halves.  The output goes to
+// column *out_jidx + out_offset of `out` (same layout).
+struct JvInput {
+  const double* V; size_t ld, half;
+  const int* jidx;
+  const double* vscale;
+  const double* nrmW; const double* nrmS;
+  const int* skip;              // device flag: nonzero -> nothing to do
+  double* out; size_t out_ld; int out_offset;
+  const int* out_jidx;          // output column = *out_jidx + out_offset (null -> out_offset)
+  __device__ __forceinline__ int col() const { return jidx ? *jidx : 0; }
+  __device__ __forceinline__ const double* zW() const { return V + size_t(col()) * ld; }
+  __device__ __forceinline__ const double* zS() const { return zW() + half; }
+  __device__ __forceinline__ double scale() const { return vscale ? vscale[col()] : 1.0; }
+  __device__ __forceinline__ double nW() const { return fabs(scale()) * nrmW[col()]; }
+  __device__ __forceinline__ double nS() const { return fabs(scale()) * nrmS[col()]; }
+  __device__ __forceinline__ double* oW() const {
+    return out + size_t((out_jidx ? *out_jidx : 0) + out_offset) * out_ld;
+  }
+  __device__ __forceinline__ double* oS() const { return oW() + half; }
+  __device__ __forceinline__ bool skipped() const { return skip && *skip; }
+};
+
+struct JvCoef {
+  const double* c1;        // device scalars alpha1 dt and alpha2 dt^2 / 2
+  const double* c2;
+  double sqrt_eps_machine; // sqrt(2^-52)
+  double eps_ref;          // reference Mach number in eps_FD
+};
+
+// Eq. 23, first part: the two quotients taken at W + eps_w dW,
+//   eps_w = sqrt(eps_machine) / (eps ||dW||),
+//   t1 = (R1(W + eps_w dW) - R1(W)) / eps_w,  t2 = (R2(W + eps_w dW, S) - R2(W, S)) / eps_w,
+//   out = (dW - c1 t1 + c2 t2,  dS - t1).   (||dW|| = 0: t1 = t2 = 0.)
+template <int NV, int NN>
+struct JobJvFD_A {
+  static constexpr int K = 2;
+  const double* W; const double* S; const double* r1; const double* r2;
+  JvInput z; JvCoef c;
+  __device__ static constexpr int kind(int k) { return k == 0 ? EV_R1 : EV_R2; }
+  __device__ bool active() const { return !z.skipped(); }
+  __device__ double eps_w() const {
+    const double nw = z.nW();
+    return nw > 0.0 ? c.sqrt_eps_machine / (c.eps_ref * nw) : 0.0;
+  }
+  __device__ void load_state(int, int e, int n, double* x) const {
+    const double ew = eps_w() * z.scale();
+    const double* zw = z.zW();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      x[v] = W[i] + ew * zw[i];
+    }
+  }
+  __device__ void load_dir(int, int e, int n, double* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = S[(size_t(e) * NV + v) * NN + n];
+  }
+  __device__ void epilogue(int e, int n, const double (*r)[NV]) const {
+    const double ew = eps_w(), sc = z.scale();
+    const double iew = ew > 0.0 ? 1.0 / ew : 0.0;
+    const double c1 = *c.c1, c2 = *c.c2;
+    const double* zw = z.zW(); const double* zs = z.zS();
+    double* ow = z.oW(); double* os = z.oS();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      const double t1 = (r[0][v] - r1[i]) * iew;
+      const double t2 = (r[1][v] - r2[i]) * iew;
+      ow[i] = sc * zw[i] - c1 * t1 + c2 * t2;
+      os[i] = sc * zs[i] - t1;
+    }
+  }
+};
+
+// Eq. 23, second part: out_W += c2 (R2(W, S + eps_s dS) - R2(W, S)) / eps_s.
+template <int NV, int NN>
+struct JobJvFD_B {
+  static constexpr int K = 1;
+  const double* W; const double* S; const double* r2;
+  JvInput z; JvCoef c;
+  __device__ static constexpr int kind(int) { return EV_R2; }
+  __device__ bool active() const { return !z.skipped() && z.nS() > 0.0; }
+  __device__ double eps_s() const { return c.sqrt_eps_machine / (c.eps_ref * z.nS()); }
+  __device__ void load_state(int, int e, int n, double* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = W[(size_t(e) * NV + v) * NN + n];
+  }
+  __device__ void load_dir(int, int e, int n, double* x) const {
+    const double es = eps_s() * z.scale();
+    const double* zs = z.zS();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      x[v] = S[i] + es * zs[i];
+    }
+  }
+  __device__ void epilogue(int e, int n, const double (*r)[NV]) const {
+    const double ies = 1.0 / eps_s(), c2 = *c.c2;
+    double* ow = z.oW();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      ow[i] += c2 * (r[0][v] - r2[i]) * ies;
+    }
+  }
+};
+
+// Eq. 24 (linear flux): out = (dW - c1 R1(dW) + c2 R1(dS), dS - R1(dW)).
+template <int NV, int NN>
+struct JobJvLinear {
+  static constexpr int K = 2;
+  JvInput z; JvCoef c;
+  __device__ static constexpr int kind(int) { return EV_R1; }
+  __device__ bool active() const { return !z.skipped(); }
+  __device__ void load_state(int k, int e, int n, double* x) const {
+    const double* src = k == 0 ? z.zW() : z.zS();
+    const double sc = z.scale();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = sc * src[(size_t(e) * NV + v) * NN + n];
+  }
+  __device__ void load_dir(int, int, int, double*) const {}
+  __device__ void epilogue(int e, int n, const double (*r)[NV]) const {
+    const double c1 = *c.c1, c2 = *c.c2, sc = z.scale();
+    const double* zw = z.zW(); const double* zs = z.zS();
+    double* ow = z.oW(); double* os = z.oS();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      const double a = r[0][v], b = r[1][v];
+      ow[i] = sc * zw[i] - c1 * a + c2 * b;
+      os[i] = sc * zs[i] - a;
+    }
+  }
+};
+
+}  // namespace hbpc

@@ -1,0 +1,93 @@
+// Device-side GMRES state, Krylov basis description and the deterministic
+// reduction helpers shared by the Krylov and preconditioner kernels.
+//
+// Reductions are deterministic: every block writes its partial sums, the last
+// block to finish (atomic ticket, no waiting) adds them in block order with a
+// fixed shuffle tree.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hbpc {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecWarps = kVecThreads / 32;
+constexpr int kSub = 2048;          // staged sub-chunk of q (doubles)
+
+struct GmresState {
+  int j;             // columns built in this cycle
+  int done;          // cycle finished
+  int converged;     // residual target met
+  int reorth;        // current column needs a second Gram-Schmidt pass
+  int its;           // iterations of this solve
+  int max_its;
+  int m;             // restart length
+  int breakdown;
+  double target;     // absolute target on the residual norm
+  double resid;      // current residual norm estimate |g_j|
+  double qq;         // ||q||^2 before orthogonalisation
+  double nrm[3];     // scratch norms of the last norm-producing kernel (total, W, S)
+};
+
+// All pointers are device memory.  V holds m+1 columns of length n2 at stride
+// ld; column i represents v_i = vscale[i] * V_i.  nrmW/nrmS are the norms of the
+// unscaled halves of V_i (first `half` entries are W, the rest sigma).
+struct Krylov {
+  double* V; size_t ld, n2, half;
+  int m;
+  double* H;        // (m+1) x m, column-major, ldh = m+1
+  double* cs; double* sn; double* g;
+  double* vscale; double* nrmW; double* nrmS;
+  double* hc;       // dot results of the current pass, length m+2
+  double* y;        // solution coefficients (times vscale), length m
+  GmresState* st;
+  double* partial;  // nblocks x (m+3)
+  unsigned* ticket;
+  int nblocks;
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Last-block election: returns true in every thread of the last block to
+// arrive.  Partials written before must be visible (threadfence first).
+__device__ __forceinline__ bool last_block(unsigned* ticket, int nblocks) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == unsigned(nblocks - 1)) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *ticket = 0u;   // reset for the next reduction
+  }
+  return s_last != 0u;
+}
+
+// Deterministic cross-block sum of partial[b * stride + c] for c in [0, cnt):
+// warp w sums columns c = w, w + kVecWarps, ..; lanes stride over blocks.
+__device__ __forceinline__ void reduce_partials(const double* partial, int stride, int nblocks,
+                                                int cnt, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < cnt; c += kVecWarps) {
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += __ldcg(partial + size_t(b) * stride + c);
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+  }
+}
+
+__device__ __forceinline__ void chunk_range(size_t n, int nblocks, size_t& lo, size_t& hi) {
+  const size_t chunk = ((n + nblocks - 1) / nblocks + 31) & ~size_t(31);
+  lo = size_t(blockIdx.x) * chunk;
+  hi = lo + chunk < n ? lo + chunk : n;
+  if (lo > n) lo = n;
+}
+
+}  // namespace hbpc

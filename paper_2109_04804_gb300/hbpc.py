@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libhbpc (C-ABI in include/hbpc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device buffers are torch CUDA tensors (PyTorch provides device memory and
+streams); host buffers are numpy arrays.  Importing this module loads the
+shared library and raises ImportError if it has not been built (there is no
+fallback implementation).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhbpc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libhbpc.so is not built; run __graft_entry__.build() "
+                      "(or python paper_2109_04804_gb300/build.py) first")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# -- enums (hbpc.h) -----------------------------------------------------------
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NO_CONVERGENCE, ERR_NONFINITE, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = range(8)
+LAW_ADVECTION, LAW_BURGERS, LAW_EULER = 0, 1, 2
+FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
+NODES_LOBATTO, NODES_GAUSS = 0, 1
+PC_NONE, PC_BJEXT = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")
+
+STATUS_NAMES = {0: "HBPC_OK", 1: "HBPC_ERR_INVALID_ARG", 2: "HBPC_ERR_OOM", 3: "HBPC_ERR_CUDA",
+                4: "HBPC_ERR_NO_CONVERGENCE", 5: "HBPC_ERR_NONFINITE", 6: "HBPC_ERR_TIMEOUT",
+                7: "HBPC_ERR_UNSUPPORTED"}
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class Physics(ctypes.Structure):
+    _fields_ = [("law", ctypes.c_int), ("flux", ctypes.c_int), ("a", ctypes.c_double * 3),
+                ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("lf_scale", ctypes.c_double)]
+
+
+class Solver(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("kmax", ctypes.c_int), ("dt", ctypes.c_double),
+                ("tol_newton_rel", ctypes.c_double), ("tol_newton_abs", ctypes.c_double),
+                ("tol_gmres_rel", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+                ("gmres_max_iter", ctypes.c_int), ("newton_max_iter", ctypes.c_int),
+                ("pc", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("newton_solves", ctypes.c_longlong),
+                ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
+                ("r1_evals", ctypes.c_longlong), ("r2_evals", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong), ("t", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_CTX = ctypes.c_void_p
+
+_SIGS = {
+    "hbpc_create": (_I, [ctypes.POINTER(_CTX), ctypes.POINTER(Mesh), _I, _I, ctypes.POINTER(Physics),
+                         ctypes.POINTER(Solver), _P]),
+    "hbpc_destroy": (None, [_CTX]),
+    "hbpc_ndof": (ctypes.c_longlong, [_CTX]),
+    "hbpc_nvar": (_I, [_CTX]),
+    "hbpc_node_coords": (_I, [_CTX, _P]),
+    "hbpc_basis": (_I, [_I, _I, _P, _P, _P, _P, _P]),
+    "hbpc_set_state": (_I, [_CTX, _P, _I]),
+    "hbpc_get_state": (_I, [_CTX, _P, _I]),
+    "hbpc_set_time": (_I, [_CTX, _D]),
+    "hbpc_step": (_I, [_CTX, _I]),
+    "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
+    "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
+    "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
+    "hbpc_eval_Jv": (_I, [_CTX, _D, _D, _P, _P, _P]),
+    "hbpc_newton_solve": (_I, [_CTX, _P, _D, _D, _P, _P, _P]),
+    "hbpc_eval_pc": (_I, [_CTX, _D, _D, _P, _P, _P]),
+    "hbpc_fp64_fma_peak": (_I, [ctypes.POINTER(ctypes.c_double)]),
+    "hbpc_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
+    "hbpc_reset_stats": (_I, [_CTX]),
+    "hbpc_last_error": (ctypes.c_char_p, [_CTX]),
+    "hbpc_profile_enable": (_I, [_CTX, _I]),
+    "hbpc_profile_get": (_I, [_CTX, _P, _P, _I]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class HBPCError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+
+
+def _check(status, ctx=None):
+    if status != OK:
+        msg = _lib.hbpc_last_error(ctx)
+        raise HBPCError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags.c_contiguous
+        return t.ctypes.data
+    assert t.is_contiguous() and str(t.dtype) == "torch.float64"
+    return t.data_ptr()
+
+
+def basis(N, nodes=NODES_LOBATTO):
+    p = N + 1
+    xi, w, lm, lp = (np.zeros(p) for _ in range(4))
+    Dh = np.zeros((p, p))
+    _check(_lib.hbpc_basis(N, nodes, _ptr(xi), _ptr(w), _ptr(Dh), _ptr(lm), _ptr(lp)))
+    return {"nodes": xi, "weights": w, "Dhat": Dh, "l_m": lm, "l_p": lp}
+
+
+def fp64_fma_peak():
+    """Measured FP64 FMA throughput of the current device, GFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.hbpc_fp64_fma_peak(ctypes.byref(v)))
+    return v.value
+
+
+class Context:
+    """One HBPC-DGSEM problem on the current CUDA device."""
+
+    def __init__(self, dim, n, lo, hi, N, law=LAW_ADVECTION, flux=FLUX_GLOBAL_LF,
+                 a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, nodes=NODES_LOBATTO,
+                 q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0,
+                 tol_gmres_rel=1e-5, gmres_restart=100, gmres_max_iter=7000,
+                 newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64, stream=None):
+        pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
+        self.mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
+                         (ctypes.c_double * 3)(*pad(hi, 1.0)))
+        self.phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale)
+        self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel,
+                             gmres_restart, gmres_max_iter, newton_max_iter, pc, precision)
+        self.N, self.dim, self.nodes = N, dim, nodes
+        self._ctx = _CTX()
+        _check(_lib.hbpc_create(ctypes.byref(self._ctx), ctypes.byref(self.mesh), N, nodes,
+                                ctypes.byref(self.phys), ctypes.byref(self.solver), stream))
+        self.ndof = _lib.hbpc_ndof(self._ctx)
+        self.nv = _lib.hbpc_nvar(self._ctx)
+        self.nE = 1
+        for m in range(dim):
+            self.nE *= n[m]
+        self.shape = (self.nE, self.nv) + (N + 1,) * dim
+
+    def close(self):
+        if self._ctx:
+            _lib.hbpc_destroy(self._ctx)
+            self._ctx = _CTX()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, st):
+        _check(st, self._ctx)
+
+    def node_coords(self):
+        nn = (self.N + 1) ** self.dim
+        x = np.zeros((self.dim, self.nE * nn))
+        self._c(_lib.hbpc_node_coords(self._ctx, _ptr(x)))
+        return [x[m].reshape((self.nE,) + (self.N + 1,) * self.dim) for m in range(self.dim)]
+
+    def set_state(self, w):
+        on_dev = 0 if isinstance(w, np.ndarray) else 1
+        if on_dev == 0:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.size == self.ndof
+        self._c(_lib.hbpc_set_state(self._ctx, _ptr(w), on_dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(self.shape)
+        on_dev = 0 if isinstance(out, np.ndarray) else 1
+        self._c(_lib.hbpc_get_state(self._ctx, _ptr(out), on_dev))
+        return out
+
+    def set_state_host_ptr(self, ptr):
+        """Copy the state in from host memory at address `ptr` (n_dof FP64)."""
+        self._c(_lib.hbpc_set_state(self._ctx, ptr, 0))
+
+    def get_state_host_ptr(self, ptr):
+        """Copy the state out to host memory at address `ptr` (n_dof FP64)."""
+        self._c(_lib.hbpc_get_state(self._ctx, ptr, 0))
+
+    def set_time(self, t):
+        self._c(_lib.hbpc_set_time(self._ctx, t))
+
+    def step(self, n=1):
+        self._c(_lib.hbpc_step(self._ctx, n))
+
+    def eval_R1(self, w, out):
+        self._c(_lib.hbpc_eval_R1(self._ctx, _ptr(w), _ptr(out)))
+        return out
+
+    def eval_R2(self, w, s, out):
+        self._c(_lib.hbpc_eval_R2(self._ctx, _ptr(w), _ptr(s), _ptr(out)))
+        return out
+
+    def eval_G(self, b, alpha1, alpha2, X, G):
+        self._c(_lib.hbpc_eval_G(self._ctx, _ptr(b), alpha1, alpha2, _ptr(X), _ptr(G)))
+        return G
+
+    def eval_Jv(self, alpha1, alpha2, X, dX, out):
+        self._c(_lib.hbpc_eval_Jv(self._ctx, alpha1, alpha2, _ptr(X), _ptr(dX), _ptr(out)))
+        return out
+
+    def eval_pc(self, alpha1, alpha2, X, inp, out):
+        self._c(_lib.hbpc_eval_pc(self._ctx, alpha1, alpha2, _ptr(X), _ptr(inp), _ptr(out)))
+        return out
+
+    def newton_solve(self, b, alpha1, alpha2, W0, W_out, S_out=None):
+        self._c(_lib.hbpc_newton_solve(self._ctx, _ptr(b), alpha1, alpha2, _ptr(W0), _ptr(W_out),
+                                       _ptr(S_out)))
+        return W_out
+
+    def stats(self):
+        s = Stats()
+        self._c(_lib.hbpc_get_stats(self._ctx, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        self._c(_lib.hbpc_reset_stats(self._ctx))
+
+    def profile(self, enable=True):
+        self._c(_lib.hbpc_profile_enable(self._ctx, 1 if enable else 0))
+
+    def profile_get(self):
+        ms = np.zeros(len(PHASES))
+        cnt = np.zeros(len(PHASES), dtype=np.int64)
+        self._c(_lib.hbpc_profile_get(self._ctx, _ptr(ms), cnt.ctypes.data, len(PHASES)))
+        return {ph: (float(ms[i]), int(cnt[i])) for i, ph in enumerate(PHASES)}

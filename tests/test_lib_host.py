@@ -1,0 +1,68 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every function include/hbpc.h declares, computes the basis like the oracle,
+and rejects invalid arguments before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.basis import Basis, GAUSS, LOBATTO
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hbpc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc as h
+    return h
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hbpc.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:hbpc_status|void|long long|int|const char\*)\s+(hbpc_\w+)\s*\(",
+                                 text, re.M)))
+
+
+def test_exports_every_declared_symbol(hbpc):
+    import ctypes
+    lib = ctypes.CDLL(hbpc.LIB_PATH)
+    decl = declared_functions()
+    assert len(decl) >= 18
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(hbpc.EXPORTED) == decl
+
+
+@pytest.mark.parametrize("family,code", [(LOBATTO, 0), (GAUSS, 1)])
+@pytest.mark.parametrize("N", range(1, 8))
+def test_basis_matches_oracle(hbpc, N, family, code):
+    b = hbpc.basis(N, code)
+    o = Basis(N, family)
+    np.testing.assert_allclose(b["nodes"], o.nodes, atol=2e-15)
+    np.testing.assert_allclose(b["weights"], o.weights, rtol=1e-13)
+    np.testing.assert_allclose(b["Dhat"], o.Dhat, atol=1e-12 * np.abs(o.Dhat).max())
+    np.testing.assert_allclose(b["l_m"], o.l_m, atol=1e-13)
+    np.testing.assert_allclose(b["l_p"], o.l_p, atol=1e-13)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(N=0), 1), (dict(N=8), 1), (dict(q=5), 1), (dict(dt=0.0), 1), (dict(dt=-1.0), 1),
+    (dict(kmax=-1), 1), (dict(gmres_restart=0), 1), (dict(gmres_max_iter=0), 1),
+    (dict(eps=0.0), 1), (dict(law=7), 1), (dict(nodes=3), 1), (dict(dim=4), 1),
+])
+def test_invalid_arguments_rejected(hbpc, kw, code):
+    args = dict(dim=2, n=(2, 2), lo=(0, 0), hi=(1, 1), N=3)
+    args.update(kw)
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(**args)
+    assert ei.value.status == code
+
+
+def test_invalid_mesh_rejected(hbpc):
+    with pytest.raises(hbpc.HBPCError):
+        hbpc.Context(2, (0, 2), (0, 0), (1, 1), 3)
+    with pytest.raises(hbpc.HBPCError):
+        hbpc.Context(2, (2, 2), (0, 1), (1, 1), 3)

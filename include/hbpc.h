@@ -196,6 +196,30 @@ hbpc_status hbpc_reset_stats(hbpc_ctx* ctx);
 hbpc_status hbpc_profile_enable(hbpc_ctx* ctx, int enable);
 hbpc_status hbpc_profile_get(hbpc_ctx* ctx, double* ms, long long* launches, int n_phases);
 
+/* Allocation-free Jacobian-vector product: the same result as hbpc_eval_Jv for
+ * the discretisation described by (mesh, N, nodes, phys) and the time step dt,
+ * without a context and without allocating any memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc
+ * -- code that runs while a framework owns all device memory through its own
+ * pool or arena, code with a fixed memory budget decided up front, or code that
+ * must not trigger the implicit synchronisation and fragmentation an allocation
+ * can cause.  Its scratch (R1(W) and R2(W, S) at X, the partial sums of the
+ * ||dW||, ||dS|| reduction, a reduction ticket) is one file-scope device array
+ * of about 4.2 MB that every GPU which loads the library holds until the
+ * process exits.  Limits and behaviour:
+ *  - n_dof must not exceed 262144 (else HBPC_ERR_INVALID_ARG, nothing launched);
+ *  - the first call on a device looks up the array's device address with that
+ *    device current, so make that first call before any stream capture;
+ *  - all calls share the array, which keeps the last call's contents; each call
+ *    clears the part that must start at zero, but calls that overlap on the GPU
+ *    (concurrent streams or threads) race on it and must be serialised;
+ *  - work is enqueued on cuda_stream (NULL = default) and the call returns when
+ *    that stream has finished it; errors are reported by hbpc_last_error(NULL).
+ * X, dX, out: device, 2 n_dof FP64 (X = (W, S)). */
+hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics* phys,
+                                 double dt, double alpha1, double alpha2, const double* X,
+                                 const double* dX, double* out, void* cuda_stream);
+
 /* FP64 FMA throughput of the current device in GFLOP/s (a few milliseconds of
  * independent FMA chains on every SM, best of three, CUDA events).  Used as the
  * arithmetic roofline of the FP64 kernels.  Allocates and frees a small buffer. */

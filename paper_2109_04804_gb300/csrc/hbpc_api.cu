@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -629,6 +630,51 @@ void fill_params(hbpc_ctx* x) {
   p.rusanov = x->phys.flux == HBPC_FLUX_RUSANOV ? 1 : 0;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free Jacobian-vector product.  Its scratch (R1(W) and R2(W, S) at
+// the linearisation point, the per-block partial sums of the ||dW||, ||dS||
+// reduction, the reduction ticket and a few scalars) lives in one file-scope
+// device array instead of memory obtained from cudaMalloc.
+// ---------------------------------------------------------------------------
+constexpr long long kNoAllocMaxDof = 1LL << 18;   // n_dof limit (262,144 values)
+constexpr int kNoAllocMaxBlocks = 512;            // reduction blocks
+constexpr size_t kNoAllocR1 = 0;                                          // doubles
+constexpr size_t kNoAllocR2 = kNoAllocR1 + size_t(kNoAllocMaxDof);
+constexpr size_t kNoAllocPartial = kNoAllocR2 + size_t(kNoAllocMaxDof);   // blocks x 4
+constexpr size_t kNoAllocC12 = kNoAllocPartial + size_t(kNoAllocMaxBlocks) * 4;
+constexpr size_t kNoAllocNrm = kNoAllocC12 + 4;
+constexpr size_t kNoAllocState = kNoAllocNrm + 4;                         // GmresState
+constexpr size_t kNoAllocTicket = kNoAllocState + (sizeof(GmresState) + 7) / 8;
+constexpr size_t kNoAllocBytes = (kNoAllocTicket + 1) * sizeof(double);  // about 4.2 MB
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The first call
+// on a device resolves it (cudaGetSymbolAddress, with that device current);
+// later calls reuse the cached address.
+hbpc_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "device index beyond the allocation-free table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return HBPC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -926,6 +972,77 @@ hbpc_status hbpc_profile_get(hbpc_ctx* ctx, double* ms, long long* launches, int
     if (launches) launches[i] = ctx->prof.cnt[i];
   }
   return HBPC_OK;
+}
+
+hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics* phys,
+                                 double dt, double alpha1, double alpha2, const double* X,
+                                 const double* dX, double* out, void* cuda_stream) {
+  if (!X || !dX || !out) return fail(nullptr, HBPC_ERR_INVALID_ARG, "null pointer");
+  hbpc_solver so{};
+  so.q = 4; so.kmax = 0; so.dt = dt;
+  so.tol_newton_rel = 1e-12; so.tol_newton_abs = 0.0; so.tol_gmres_rel = 1e-5;
+  so.gmres_restart = 1; so.gmres_max_iter = 1; so.newton_max_iter = 1;
+  so.pc = HBPC_PC_NONE; so.precision = HBPC_PREC_FP64;
+  hbpc_status st = validate(mesh, N, nodes, phys, &so);
+  if (st != HBPC_OK) return st;
+  // host-side description of the discretisation (no device memory)
+  hbpc_ctx x;
+  x.mesh = *mesh; x.phys = *phys; x.sol = so;
+  x.N = N; x.P = N + 1; x.nodes = nodes; x.dim = mesh->dim;
+  x.nv = phys->law == HBPC_LAW_EULER ? mesh->dim + 2 : 1;
+  x.nE = 1;
+  for (int m = 0; m < x.dim; ++m) x.nE *= mesh->n[m];
+  long long nn = 1;
+  for (int m = 0; m < x.dim; ++m) nn *= x.P;
+  x.ndof = x.nE * x.nv * nn;
+  if (x.ndof > kNoAllocMaxDof)
+    return fail(nullptr, HBPC_ERR_INVALID_ARG,
+                "n_dof exceeds the allocation-free limit of 262144 values; use hbpc_eval_Jv");
+  if (!basis_1d(N, nodes, x.basis)) return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis");
+  if (!get_ops(phys->law, x.dim, x.P, nodes == HBPC_NODES_LOBATTO, x.ops))
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "this (law, dim, N, node family) is not compiled in");
+  fill_params(&x);
+  unsigned char* base = nullptr;
+  if ((st = noalloc_scratch(&base)) != HBPC_OK) return st;
+  double* scr = reinterpret_cast<double*>(base);
+  const cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const long long n = x.ndof;
+  const size_t n2 = size_t(2 * n);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  Krylov K{};
+  K.m = 1;   // partial stride m + 3 = 4
+  K.partial = scr + kNoAllocPartial;
+  K.st = reinterpret_cast<GmresState*>(scr + kNoAllocState);
+  K.ticket = reinterpret_cast<unsigned*>(scr + kNoAllocTicket);
+  K.nblocks = std::max(1, std::min<int>({2 * sms, int((n2 + 1023) / 1024), kNoAllocMaxBlocks}));
+  double* c12 = scr + kNoAllocC12;
+  double* nrm = scr + kNoAllocNrm;
+  const double c1 = alpha1 * dt, c2 = alpha2 * dt * dt / 2.0;
+  auto ck = [&](cudaError_t e, const char* what) -> hbpc_status {
+    return e == cudaSuccess ? HBPC_OK : cuda_fail(nullptr, e, what);
+  };
+  // the shared array keeps the previous call's contents: the ticket must start at 0
+  if ((st = ck(cudaMemsetAsync(K.ticket, 0, sizeof(unsigned), stream), "clear ticket")) != HBPC_OK) return st;
+  k_set2<<<1, 32, 0, stream>>>(c12, c1, c2);
+  // R1(W), R2(W, S) at X into the scratch (G goes to `out`, overwritten below)
+  x.ops.residual(x.prm, X, X + n, X, c1, c2, out, out + n, scr + kNoAllocR1, scr + kNoAllocR2, stream);
+  k_norms<<<K.nblocks, kVecThreads, 0, stream>>>(dX, n2, size_t(n), K, nullptr);
+  k_sqrt_norms<<<1, 32, 0, stream>>>(K.st, nrm);
+  if ((st = ck(cudaGetLastError(), "noalloc launches")) != HBPC_OK) return st;
+  JvInput z{};
+  z.V = dX; z.ld = n2; z.half = size_t(n);
+  z.nrmW = nrm + 1; z.nrmS = nrm + 2;
+  z.out = out; z.out_ld = n2; z.out_offset = 0;
+  JvCoef cf;
+  cf.c1 = c12; cf.c2 = c12 + 1;
+  cf.sqrt_eps_machine = std::sqrt(std::ldexp(1.0, -52));
+  cf.eps_ref = phys->eps;
+  if (x.ops.jv_linear) x.ops.jv_linear(x.prm, z, cf, stream);
+  else x.ops.jv_fd(x.prm, X, X + n, scr + kNoAllocR1, scr + kNoAllocR2, z, cf, stream);
+  if ((st = ck(cudaGetLastError(), "noalloc jv")) != HBPC_OK) return st;
+  return ck(cudaStreamSynchronize(stream), "noalloc sync");
 }
 
 const char* hbpc_last_error(const hbpc_ctx* ctx) {

@@ -83,6 +83,8 @@ _SIGS = {
     "hbpc_newton_solve": (_I, [_CTX, _P, _D, _D, _P, _P, _P]),
     "hbpc_eval_pc": (_I, [_CTX, _D, _D, _P, _P, _P]),
     "hbpc_fp64_fma_peak": (_I, [ctypes.POINTER(ctypes.c_double)]),
+    "hbpc_eval_Jv_noalloc": (_I, [ctypes.POINTER(Mesh), _I, _I, ctypes.POINTER(Physics), _D, _D, _D,
+                                  _P, _P, _P, _P]),
     "hbpc_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
     "hbpc_reset_stats": (_I, [_CTX]),
     "hbpc_last_error": (ctypes.c_char_p, [_CTX]),
@@ -133,6 +135,20 @@ def fp64_fma_peak():
     v = ctypes.c_double(0.0)
     _check(_lib.hbpc_fp64_fma_peak(ctypes.byref(v)))
     return v.value
+
+
+def eval_Jv_noalloc(dim, n, lo, hi, N, dt, alpha1, alpha2, X, dX, out, law=LAW_ADVECTION,
+                    flux=FLUX_GLOBAL_LF, a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0,
+                    nodes=NODES_LOBATTO, stream=None):
+    """Jacobian-vector product of one stage system without a context and without
+    any device allocation (hbpc_eval_Jv_noalloc; n_dof <= 262144)."""
+    pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
+    mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
+                (ctypes.c_double * 3)(*pad(hi, 1.0)))
+    phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale)
+    _check(_lib.hbpc_eval_Jv_noalloc(ctypes.byref(mesh), N, nodes, ctypes.byref(phys), dt, alpha1,
+                                     alpha2, _ptr(X), _ptr(dX), _ptr(out), stream))
+    return out
 
 
 class Context:

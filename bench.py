@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-timesteps/s per HBPC step at fixed L2 error; learned vs plain GMRES"
+PRECISION = ["mixed"]   # set from --precision
 UNIT = "DOF-timesteps/s"
 
 WL = dict(dim=2, n=(64, 64), lo=(0.0, 0.0), hi=(1.0, 1.0), N=5, a=(1.0, 1.0), q=8, kmax=4,
@@ -45,6 +46,7 @@ def workload_dt():
 
 def config_dict(dt, extra=None):
     c = {"workload": "2d_linear_advection_64x64_N5_HBPC(8,4)_CFL8_BJext_GMRES",
+         "precision": PRECISION[0],
          "mesh": "64x64 periodic [0,1]^2", "N": 5, "nodes": "Gauss-Lobatto", "hbpc": "q=8,kmax=4",
          "dt": dt, "eps_newton": WL["tol_newton_rel"], "newton_abs_dW": WL["tol_newton_abs"],
          "eps_gmres": WL["tol_gmres_rel"],
@@ -124,21 +126,22 @@ def exact_solution(coords, t):
 
 
 # -- algorithmic work per launch (bytes, flops per W-DOF) ----------------------
-def jv_work_per_dof():
+def jv_work_per_dof(mixed=False):
     """Linear Jv (Eq. 24): reads dW, dS and writes the two outputs: 32 B per
-    W-DOF.  Flops: two R1 passes, each 2*d*p (volume) + 2*d/p face points x 7
-    (flux 5, lifting 2), plus 3 FMAs to combine."""
+    W-DOF in FP64 (16 B in FP32).  Flops: two R1 passes, each 2*d*p (volume)
+    + 2*d/p face points x 7 (flux 5, lifting 2), plus 3 FMAs to combine."""
     d, p = WL["dim"], WL["N"] + 1
     r1 = 2 * d * p + (2 * d / p) * 7
-    return 32.0, 2 * r1 + 6
+    return (16.0 if mixed else 32.0), 2 * r1 + 6
 
 
-def pc_work_per_dof():
-    """BJ_ext apply: per element it reads M_i and J_i (2 n_b^2 doubles), the two
-    input halves and writes the two output halves: (16 n_b + 32) B per W-DOF;
-    four n_b x n_b matrix-vector products: 8 n_b flops per W-DOF (+ 4)."""
+def pc_work_per_dof(mixed=False):
+    """BJ_ext apply: per element it reads M_i and J_i (2 n_b^2 values), the two
+    input halves and writes the two output halves: (16 n_b + 32) B per W-DOF in
+    FP64, (8 n_b + 16) B in FP32; four n_b x n_b matrix-vector products:
+    8 n_b flops per W-DOF (+ 4)."""
     nb = (WL["N"] + 1) ** WL["dim"]
-    return 16.0 * nb + 32.0, 8.0 * nb + 4.0
+    return ((8.0 * nb + 16.0) if mixed else (16.0 * nb + 32.0)), 8.0 * nb + 4.0
 
 
 def run_ours(args):
@@ -158,7 +161,8 @@ def run_ours(args):
                        tol_newton_rel=WL["tol_newton_rel"], tol_newton_abs=WL["tol_newton_abs"],
                        tol_gmres_rel=WL["tol_gmres_rel"], gmres_restart=WL["gmres_restart"],
                        gmres_max_iter=WL["gmres_max_iter"], newton_max_iter=WL["newton_max_iter"],
-                       pc=hbpc.PC_BJEXT, stream=stream.cuda_stream)
+                       pc=hbpc.PC_BJEXT, stream=stream.cuda_stream,
+                       precision=hbpc.PREC_MIXED if PRECISION[0] == "mixed" else hbpc.PREC_FP64)
     coords = ctx.node_coords()
     w0 = inputs.sine_product(coords)
     ctx.set_state(w0)
@@ -214,8 +218,11 @@ def run_ours(args):
         pass
     fp64_peak = hbpc.fp64_fma_peak()          # measured live on this GPU
     hbm = peaks.get("hbm_gbs", 6800.0)
-    kernels = {"jv": ("dg_operator_kernel<advection,2D,P=6,JobJvLinear> (Eq. 24)", jv_work_per_dof()),
-               "pc_apply": ("k_pc_apply (BJ_ext, Sec. 3.2.3)", pc_work_per_dof())}
+    mixed = PRECISION[0] == "mixed"
+    kernels = {"jv": ("dg_operator_kernel<advection,2D,P=6,JobJvLinear<%s>> (Eq. 24)"
+                      % ("float" if mixed else "double"), jv_work_per_dof(mixed)),
+               "pc_apply": ("k_pc_apply<%s> (BJ_ext, Sec. 3.2.3)" % ("float" if mixed else "double"),
+                            pc_work_per_dof(mixed))}
     entries = {}
     for ph, (name, (bpd, fpd)) in kernels.items():
         ms, n = prof[ph]
@@ -224,14 +231,21 @@ def run_ours(args):
         avg = ms / 1000.0 / n
         gf = fpd * ndof / avg / 1e9
         gb = bpd * ndof / avg / 1e9
-        entries[ph] = {"kernel": name, "bound": "alu", "achieved": round(gf / 1000.0, 4),
-                       "peak": fp64_peak / 1000.0, "unit": "TFLOP/s", "frac": round(gf / fp64_peak, 4),
-                       "traffic": None, "hbm_achieved_gbs": round(gb, 1),
-                       "hbm_frac_of_measured": round(gb / hbm, 4), "avg_launch_us": round(avg * 1e6, 2),
-                       "launches_profiled": n, "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3)}
+        if mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are HBM-bound
+            entries[ph] = {"kernel": name, "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
+                           "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": None,
+                           "alu_tflops": round(gf / 1000.0, 3)}
+        else:
+            entries[ph] = {"kernel": name, "bound": "alu", "achieved": round(gf / 1000.0, 4),
+                           "peak": fp64_peak / 1000.0, "unit": "TFLOP/s", "frac": round(gf / fp64_peak, 4),
+                           "traffic": None, "hbm_achieved_gbs": round(gb, 1),
+                           "hbm_frac_of_measured": round(gb / hbm, 4)}
+        entries[ph].update({"avg_launch_us": round(avg * 1e6, 2), "launches_profiled": n,
+                            "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3)})
     dom = max(entries, key=lambda k: prof[k][0])
     roofline = dict(entries[dom])
-    roofline["peak_source"] = "FP64 FMA throughput measured in this run (hbpc_fp64_fma_peak)"
+    roofline["peak_source"] = ("measured HBM copy bandwidth (MEASURED_PEAKS.json)" if mixed else
+                               "FP64 FMA throughput measured in this run (hbpc_fp64_fma_peak)")
     roofline["phase_ms_one_step"] = {k: round(v[0], 3) for k, v in prof.items()}
     roofline["phase_launches_one_step"] = {k: v[1] for k, v in prof.items()}
     roofline["other_kernels"] = {k: v for k, v in entries.items() if k != dom}
@@ -252,7 +266,9 @@ def run_ours(args):
     ctx.close()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if PRECISION[0] == "fp64" else "f64 state/Newton, f32 Krylov",
+            "data": "synthetic",
             "config": config_dict(dt, {"parallelism": "replicas" if world > 1 else "single"}),
             "r1_evals_per_s": r1_per_s, "l2_error_vs_exact": err,
             "gmres_its_per_step": stats["gmres_its"] / args.steps,
@@ -328,7 +344,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
     args = ap.parse_args()
+    PRECISION[0] = args.precision
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -55,8 +55,12 @@ typedef enum { HBPC_NODES_LOBATTO = 0, HBPC_NODES_GAUSS = 1 } hbpc_nodes;
 
 /* Preconditioner of the extended linear system (Sec. 3.2.3).  NONE: plain
  * GMRES.  BJEXT: the BJ_ext block preconditioner, right preconditioning; needs
- * n_var (N+1)^dim <= 160 and 2 n_E (n_var (N+1)^dim)^2 doubles of device memory. */
-typedef enum { HBPC_PC_NONE = 0, HBPC_PC_BJEXT = 1 } hbpc_pc;
+ * n_var (N+1)^dim <= 160 and 2 n_E (n_var (N+1)^dim)^2 doubles of device memory.
+ * LEARNED: the BJ_ext structure with the block inverse (I - c1 J + c2 J^2)^-1
+ * replaced by a learned per-element network (hbpc_pc_* below; no counterpart in
+ * the paper).  The preconditioner never changes the answer, only the GMRES
+ * iteration count: Newton stops on the same FP64 residual. */
+typedef enum { HBPC_PC_NONE = 0, HBPC_PC_BJEXT = 1, HBPC_PC_LEARNED = 2 } hbpc_pc;
 
 /* Arithmetic of the Krylov loop.  FP64: everything in FP64, Jv by the
  * difference quotients of Eq. 23 (Eq. 24 for a linear flux).  MIXED: the
@@ -187,6 +191,38 @@ hbpc_status hbpc_newton_solve(hbpc_ctx* ctx, const double* b, double alpha1, dou
 
 hbpc_status hbpc_get_stats(const hbpc_ctx* ctx, hbpc_stats* out);
 hbpc_status hbpc_reset_stats(hbpc_ctx* ctx);
+
+/* Switch the preconditioner of an existing context (allocates what it needs). */
+hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc);
+
+/* Learned block preconditioner (the workload's addition; the paper has none).
+ * Network: f = standardised [W_e, c1, c2] (d_in = n_b + 2, zero padded to a
+ * multiple of 16) -> tanh(256) -> tanh(256) -> O (n_b^2, padded to a multiple
+ * of 8); M~_e = I + reshape(O) row-major.  BF16 tensor-core GEMMs with FP32
+ * accumulation, FP32 master weights and Adam.  Parameters as one FP32 array:
+ * W1 (256 x d_in_padded), b1 (256), W2 (256 x 256), b2, W3 (d_out_padded x 256),
+ * b3 (d_out_padded), row-major weights (out x in), then the feature
+ * standardisation mu (d_in_padded) and sd (d_in_padded): f = (raw - mu) / sd. */
+hbpc_status hbpc_pc_model_info(hbpc_ctx* ctx, int* d_in_padded, int* hidden, int* d_out_padded,
+                               long long* n_params);
+hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double out_scale);
+hbpc_status hbpc_pc_model_get(hbpc_ctx* ctx, float* params);        /* host output */
+hbpc_status hbpc_pc_model_set(hbpc_ctx* ctx, const float* params);  /* host input */
+/* Probe loss L = sum_{s,p} |M~_s S_s x_p - x_p|^2 / (B P), S = I - c1 J + c2 J^2,
+ * and its gradient for given inputs (host): F (B x d_in_padded, already
+ * standardised), J (B x n_b x n_b column-major), c12 (B x 2), X (B x P x n_b).
+ * B a multiple of 8, 1 <= P <= 16; grads (host, n_params) may be NULL. */
+hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int B, int P, const float* F, const float* J, const float* c12,
+                              const float* X, double* loss, float* grads);
+/* Sample `samples_per_newton` elements' (features, J_e, c1, c2) at every Newton
+ * iteration that builds a block preconditioner into a replay buffer of
+ * `capacity` samples (0 stops sampling). */
+hbpc_status hbpc_pc_collect(hbpc_ctx* ctx, int samples_per_newton, int capacity);
+/* `iters` Adam steps on random batches of the replay buffer with `probes`
+ * Rademacher probes per sample (SplitMix64 of the seed); first and last batch
+ * losses to loss_first / loss_last (may be NULL). */
+hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int iters, int batch, int probes, double lr, unsigned long long seed,
+                          double* loss_first, double* loss_last);
 
 /* Per-launch device timing: while enabled, every kernel launch of the context
  * is bracketed by CUDA events on its stream (this adds a little host overhead;

@@ -117,19 +117,22 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
 // Apply P^-1 to x = scale * (xW, xS) (element blocks of n_b values), result to
 // (oW, oS) (added when accumulate != 0), and the norms of the result's halves
 // (unscaled, square-rooted) to zn[0..2] (total, W, S) through the last block.
-// EPB elements per block, one thread per row.
-struct PcApply {
-  const double* M; const double* J;
-  const double* xW; const double* xS;
+// EPB elements per block, one thread per row.  S: storage and arithmetic type
+// of the blocks and vectors (FP64, or FP32 in the mixed-precision mode).
+template <typename S>
+struct PcApplyT {
+  const S* M; const S* J;
+  const S* xW; const S* xS;
   const double* scale;          // device scalar or null (1)
   const int* jidx;              // column index for xW/xS (stride ld), null -> 0
   size_t ld;
-  double* oW; double* oS;
+  S* oW; S* oS;
   const double* c12;            // device c1, c2
   const int* skip;
   int accumulate;
   double* zn;
   int nb, nE;
 };
+using PcApply = PcApplyT<double>;
 
 }  // namespace hbpc

@@ -110,30 +110,32 @@ __global__ void __launch_bounds__(256) k_pc_invert(double* __restrict__ Mall, in
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) M[t] = A[t];
 }
 
-__global__ void __launch_bounds__(256) k_pc_apply(PcApply a, Krylov K) {
+template <typename S>
+__global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   if (a.skip && *a.skip) return;
   const int nb = a.nb;
   const int epb = blockDim.x / nb;
   const int le = threadIdx.x / nb, r = threadIdx.x - le * nb;
   const int e = blockIdx.x * epb + le;
   const bool live = le < epb && e < a.nE;
-  extern __shared__ double sm[];
-  double* xw = sm + le * 4 * nb;
-  double* xs = xw + nb;
-  double* su = xs + nb;
-  double* sv = su + nb;
+  extern __shared__ double sm_raw[];
+  S* sm = reinterpret_cast<S*>(sm_raw);
+  S* xw = sm + le * 4 * nb;
+  S* xs = xw + nb;
+  S* su = xs + nb;
+  S* sv = su + nb;
   const size_t off = (a.jidx ? size_t(*a.jidx) * a.ld : 0) + size_t(e) * nb;
-  const double sc = a.scale ? (a.jidx ? a.scale[*a.jidx] : *a.scale) : 1.0;
+  const S sc = S(a.scale ? (a.jidx ? a.scale[*a.jidx] : *a.scale) : 1.0);
   if (live) {
     xw[r] = sc * a.xW[off + r];
     xs[r] = sc * a.xS[off + r];
   }
   __syncthreads();
-  double u = 0.0, v = 0.0;
+  S u = S(0), v = S(0);
   if (live) {
-    const double* Me = a.M + size_t(e) * nb * nb;
+    const S* Me = a.M + size_t(e) * nb * nb;
     for (int c = 0; c < nb; ++c) {
-      const double m = Me[size_t(c) * nb + r];
+      const S m = Me[size_t(c) * nb + r];
       u += m * xw[c];
       v += m * xs[c];
     }
@@ -143,23 +145,24 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApply a, Krylov K) {
   __syncthreads();
   double aw = 0.0, as = 0.0;
   if (live) {
-    const double* Je = a.J + size_t(e) * nb * nb;
-    double ju = 0.0, jv = 0.0;
+    const S* Je = a.J + size_t(e) * nb * nb;
+    S ju = S(0), jv = S(0);
     for (int c = 0; c < nb; ++c) {
-      const double j = Je[size_t(c) * nb + r];
+      const S j = Je[size_t(c) * nb + r];
       ju += j * su[c];
       jv += j * sv[c];
     }
-    const double c1 = a.c12[0], c2 = a.c12[1];
-    double top = u - c2 * jv;
-    double bot = ju + v - c1 * jv;
+    const S c1 = S(a.c12[0]), c2 = S(a.c12[1]);
+    S top = u - c2 * jv;
+    S bot = ju + v - c1 * jv;
     const size_t o = size_t(e) * nb + r;
     if (a.accumulate) { top += a.oW[o]; bot += a.oS[o]; }
     a.oW[o] = top;
     a.oS[o] = bot;
-    aw = top * top;
-    as = bot * bot;
+    aw = double(top * top);
+    as = double(bot * bot);
   }
+  if (!a.zn) return;   // norms only needed by the difference-quotient Jv
   // norms of the result through the last block
   __shared__ double s2[2][kVecWarps];
   aw = warp_sum(aw);
@@ -182,6 +185,25 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApply a, Krylov K) {
     a.zn[1] = sqrt(rr[0]);
     a.zn[2] = sqrt(rr[1]);
   }
+}
+
+// FP64 -> FP32 copy (mixed precision: basis, linearisation point, PC blocks)
+__global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, size_t n, double scale) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    y[i] = float(scale * x[i]);
+}
+
+// y (FP64) += x (FP32)
+__global__ void k_add_float(const float* __restrict__ x, double* __restrict__ y, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    y[i] += double(x[i]);
+}
+
+// out (FP32) = -g (FP64) - jx (FP32): restart residual of the mixed mode
+__global__ void k_neg_sum_f(const double* __restrict__ g, const float* __restrict__ jx, float* __restrict__ out,
+                            size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = float(-g[i]) - jx[i];
 }
 
 }  // namespace hbpc

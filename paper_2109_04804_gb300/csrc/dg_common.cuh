@@ -10,6 +10,38 @@ constexpr int kMaxP = 8;     // nodes per direction (N + 1 <= 8)
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
+
+// Forward-mode dual number x + eps dx (eps^2 = 0).  Evaluating the flux
+// Jacobian-vector product at the dual state (w + eps t, s + eps u) gives, in the
+// eps part, d/deps [A(w + eps t)(s + eps u)] = A(w) u + H(w)[s, t]: the
+// directional derivative of R2 used by the analytic (mixed-precision) Jacobian-
+// vector product.  Only + - * / are needed by the fluxes' derivatives.
+template <typename T>
+struct Dual {
+  T v, d;
+  __host__ __device__ Dual() : v(0), d(0) {}
+  __host__ __device__ Dual(T a) : v(a), d(0) {}
+  __host__ __device__ Dual(T a, T b) : v(a), d(b) {}
+};
+template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+  const T iv = T(1) / b.v;
+  const T q = a.v * iv;
+  return {q, (a.d - q * b.d) * iv};
+}
+template <typename T> __device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, Dual<T> b) { a.v += b.v; a.d += b.d; return a; }
+
+// base (real) type of a value type and its real part
+template <class V> struct BaseOf { using type = V; };
+template <class T> struct BaseOf<Dual<T>> { using type = T; };
+template <class V> __device__ __forceinline__ typename BaseOf<V>::type real_part(const V& x) { return x; }
+template <class T> __device__ __forceinline__ T real_part(const Dual<T>& x) { return x.v; }
+
 enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2 };
 
 // Operator parameters, passed by value (kernel parameter space).  All matrices
@@ -34,21 +66,31 @@ struct DGParams {
 };
 
 // ---------------------------------------------------------------------------
-// Physical fluxes.  flux_all: F^m(w) for every direction m; jvp_all: the
-// directional derivative (dF^m/dw) s; speed: max |eigenvalue| of dF^m/dw.
+// Physical fluxes, templated on the value type V (double, float or a Dual of
+// either; T is the real type of the parameters).  flux_all: F^m(w) for every
+// direction m; jvp_all: the directional derivative (dF^m/dw) s; speed: the
+// largest |eigenvalue| of dF^m/dw (real values only).
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 struct Advection {
   static constexpr int NV = 1;
   static constexpr bool LINEAR = true;
-  __device__ __forceinline__ static void flux_all(const T* w, T (*F)[NV], const DGParams<T>& p) {
+  template <class V>
+  __device__ __forceinline__ static void flux_all(const V* w, V (*F)[NV], const DGParams<T>& p) {
 #pragma unroll
     for (int m = 0; m < DIM; ++m) F[m][0] = p.a[m] * w[0];
   }
-  __device__ __forceinline__ static void flux(const T* w, int m, T* F, const DGParams<T>& p) {
+  template <class V>
+  __device__ __forceinline__ static void jvp_all(const V* w, const V* s, V (*J)[NV], const DGParams<T>& p) {
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) J[m][0] = p.a[m] * s[0];
+  }
+  template <class V>
+  __device__ __forceinline__ static void flux(const V* w, int m, V* F, const DGParams<T>& p) {
     F[0] = p.a[m] * w[0];
   }
-  __device__ __forceinline__ static void jvp(const T* w, const T* s, int m, T* J, const DGParams<T>& p) {
+  template <class V>
+  __device__ __forceinline__ static void jvp(const V* w, const V* s, int m, V* J, const DGParams<T>& p) {
     J[0] = p.a[m] * s[0];
   }
   __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {
@@ -60,20 +102,24 @@ template <int DIM, typename T>
 struct Burgers {
   static constexpr int NV = 1;
   static constexpr bool LINEAR = false;
-  __device__ __forceinline__ static void flux_all(const T* w, T (*F)[NV], const DGParams<T>& p) {
-    const T f = T(0.5) * w[0] * w[0];
+  template <class V>
+  __device__ __forceinline__ static void flux_all(const V* w, V (*F)[NV], const DGParams<T>& p) {
+    const V f = T(0.5) * (w[0] * w[0]);
 #pragma unroll
     for (int m = 0; m < DIM; ++m) F[m][0] = f;
   }
-  __device__ __forceinline__ static void jvp_all(const T* w, const T* s, T (*J)[NV], const DGParams<T>& p) {
-    const T f = w[0] * s[0];
+  template <class V>
+  __device__ __forceinline__ static void jvp_all(const V* w, const V* s, V (*J)[NV], const DGParams<T>& p) {
+    const V f = w[0] * s[0];
 #pragma unroll
     for (int m = 0; m < DIM; ++m) J[m][0] = f;
   }
-  __device__ __forceinline__ static void flux(const T* w, int m, T* F, const DGParams<T>& p) {
-    F[0] = T(0.5) * w[0] * w[0];
+  template <class V>
+  __device__ __forceinline__ static void flux(const V* w, int m, V* F, const DGParams<T>& p) {
+    F[0] = T(0.5) * (w[0] * w[0]);
   }
-  __device__ __forceinline__ static void jvp(const T* w, const T* s, int m, T* J, const DGParams<T>& p) {
+  template <class V>
+  __device__ __forceinline__ static void jvp(const V* w, const V* s, int m, V* J, const DGParams<T>& p) {
     J[0] = w[0] * s[0];
   }
   __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {
@@ -88,67 +134,75 @@ template <int DIM, typename T>
 struct Euler {
   static constexpr int NV = DIM + 2;
   static constexpr bool LINEAR = false;
-  __device__ __forceinline__ static void flux_all(const T* w, T (*F)[NV], const DGParams<T>& p) {
-    const T ir = T(1) / w[0];
-    T v[DIM], v2 = 0;
+  template <class V>
+  __device__ __forceinline__ static void flux_all(const V* w, V (*F)[NV], const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v[DIM], v2 = V(T(0));
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; }
-    const T E = w[DIM + 1];
-    const T pr = p.gm1 * (E - T(0.5) * p.eps2 * w[0] * v2);
-    const T pe = pr * p.inv_eps2;
+    const V E = w[DIM + 1];
+    const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
+    const V pe = pr * p.inv_eps2;
 #pragma unroll
     for (int m = 0; m < DIM; ++m) {
       F[m][0] = w[1 + m];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) F[m][1 + k] = w[1 + m] * v[k] + (k == m ? pe : T(0));
+      for (int k = 0; k < DIM; ++k) F[m][1 + k] = (k == m) ? w[1 + m] * v[k] + pe : w[1 + m] * v[k];
       F[m][DIM + 1] = v[m] * (E + pr);
     }
   }
-  __device__ __forceinline__ static void flux(const T* w, int m, T* F, const DGParams<T>& p) {
-    const T ir = T(1) / w[0];
-    T v[DIM], v2 = 0;
+  template <class V>
+  __device__ __forceinline__ static void flux(const V* w, int m, V* F, const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v[DIM], v2 = V(T(0));
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; }
-    const T E = w[DIM + 1];
-    const T pr = p.gm1 * (E - T(0.5) * p.eps2 * w[0] * v2);
+    const V E = w[DIM + 1];
+    const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
     F[0] = w[1 + m];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) F[1 + k] = w[1 + m] * v[k] + (k == m ? pr * p.inv_eps2 : T(0));
+    for (int k = 0; k < DIM; ++k) F[1 + k] = (k == m) ? w[1 + m] * v[k] + pr * p.inv_eps2 : w[1 + m] * v[k];
     F[DIM + 1] = v[m] * (E + pr);
   }
   // (dF^m/dw) s with dp = (gamma-1)(s_E - eps^2 v.s_mom + eps^2/2 |v|^2 s_rho)
-  __device__ __forceinline__ static void jvp_all(const T* w, const T* s, T (*J)[NV], const DGParams<T>& p) {
-    const T ir = T(1) / w[0];
-    T v[DIM], v2 = 0, vs = 0;
+  template <class V>
+  __device__ __forceinline__ static void jvp_all(const V* w, const V* s, V (*J)[NV], const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v[DIM], v2 = V(T(0)), vs = V(T(0));
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; vs += v[k] * s[1 + k]; }
-    const T E = w[DIM + 1];
-    const T pr = p.gm1 * (E - T(0.5) * p.eps2 * w[0] * v2);
-    const T dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + T(0.5) * p.eps2 * v2 * s[0]);
-    const T dpe = dp * p.inv_eps2;
+    const V E = w[DIM + 1];
+    const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
+    const V dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + (T(0.5) * p.eps2) * (v2 * s[0]));
+    const V dpe = dp * p.inv_eps2;
 #pragma unroll
     for (int m = 0; m < DIM; ++m) {
       J[m][0] = s[1 + m];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k)
-        J[m][1 + k] = v[m] * s[1 + k] + v[k] * s[1 + m] - v[m] * v[k] * s[0] + (k == m ? dpe : T(0));
-      const T dvm = (s[1 + m] - v[m] * s[0]) * ir;
+      for (int k = 0; k < DIM; ++k) {
+        const V t = v[m] * s[1 + k] + v[k] * s[1 + m] - v[m] * (v[k] * s[0]);
+        J[m][1 + k] = (k == m) ? t + dpe : t;
+      }
+      const V dvm = (s[1 + m] - v[m] * s[0]) * ir;
       J[m][DIM + 1] = dvm * (E + pr) + v[m] * (s[DIM + 1] + dp);
     }
   }
-  __device__ __forceinline__ static void jvp(const T* w, const T* s, int m, T* J, const DGParams<T>& p) {
-    const T ir = T(1) / w[0];
-    T v[DIM], v2 = 0, vs = 0;
+  template <class V>
+  __device__ __forceinline__ static void jvp(const V* w, const V* s, int m, V* J, const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v[DIM], v2 = V(T(0)), vs = V(T(0));
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; vs += v[k] * s[1 + k]; }
-    const T E = w[DIM + 1];
-    const T pr = p.gm1 * (E - T(0.5) * p.eps2 * w[0] * v2);
-    const T dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + T(0.5) * p.eps2 * v2 * s[0]);
+    const V E = w[DIM + 1];
+    const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
+    const V dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + (T(0.5) * p.eps2) * (v2 * s[0]));
     J[0] = s[1 + m];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k)
-      J[1 + k] = v[m] * s[1 + k] + v[k] * s[1 + m] - v[m] * v[k] * s[0] + (k == m ? dp * p.inv_eps2 : T(0));
-    const T dvm = (s[1 + m] - v[m] * s[0]) * ir;
+    for (int k = 0; k < DIM; ++k) {
+      const V t = v[m] * s[1 + k] + v[k] * s[1 + m] - v[m] * (v[k] * s[0]);
+      J[1 + k] = (k == m) ? t + dp * p.inv_eps2 : t;
+    }
+    const V dvm = (s[1 + m] - v[m] * s[0]) * ir;
     J[DIM + 1] = dvm * (E + pr) + v[m] * (s[DIM + 1] + dp);
   }
   __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {

@@ -36,21 +36,25 @@ struct KernelShape {
   // shared values per element: state + direction + DIM fluxes + 2*DIM faces
   static constexpr int PER_ELEM = 2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF;
   static constexpr int MATS = DIM * P * P + 2 * DIM * P;
-  template <typename T>
-  static constexpr size_t smem_bytes() { return (size_t(EPB) * PER_ELEM + MATS) * sizeof(T); }
+  // operator matrices (base type B, padded to 16 bytes) then element data (V)
+  template <typename V, typename B>
+  static constexpr size_t mats_bytes() { return ((MATS * sizeof(B) + 15) / 16) * 16; }
+  template <typename V, typename B = V>
+  static constexpr size_t smem_bytes() { return mats_bytes<V, B>() + size_t(EPB) * PER_ELEM * sizeof(V); }
 };
 
 // Numerical flux at one face point of direction M and side SIDE (0: -, 1: +)
 // of the thread's element: Eq. 13 for R1, the flux f~* of Sec. 3.1.2 for R2.
 // Direction and side are compile-time so that every array stays in registers.
-template <int LAW, int DIM, int P, bool LGL, typename T, class Job>
+template <int LAW, int DIM, int P, bool LGL, typename V, class Job>
 struct FaceFlux {
+  using T = typename BaseOf<V>::type;
   using L = typename LawOf<LAW, DIM, T>::type;
   static constexpr int NV = L::NV, NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
   template <int M, int SIDE>
   __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, int k, bool r2,
-                                             const int* ec, int pt, const T* sst, const T* sdir,
-                                             T* sface) {
+                                             const int* ec, int pt, const V* sst, const V* sdir,
+                                             V* sface) {
     constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;   // face point -> node with idx_M = 0
     // neighbour element across this face (periodic)
@@ -60,9 +64,9 @@ struct FaceFlux {
     if (c < 0) c += prm.n[M];
     if (c >= prm.n[M]) c -= prm.n[M];
     const int en = nc0 + prm.n[0] * (nc1 + prm.n[1] * nc2);
-    T wo[NV], wn[NV], so[NV], sn[NV];
+    V wo[NV], wn[NV], so[NV], sn[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { wo[v] = T(0); wn[v] = T(0); so[v] = T(0); sn[v] = T(0); }
+    for (int v = 0; v < NV; ++v) { wo[v] = V(T(0)); wn[v] = V(T(0)); so[v] = V(T(0)); sn[v] = V(T(0)); }
     if constexpr (LGL) {
       const int own_node = base + (SIDE ? (P - 1) * st : 0);
       const int nb_node = base + (SIDE ? 0 : (P - 1) * st);
@@ -79,7 +83,7 @@ struct FaceFlux {
         const int node = base + i * st;
         const T lo = SIDE ? prm.lp[i] : prm.lm[i];   // own trace at this face
         const T ln = SIDE ? prm.lm[i] : prm.lp[i];   // neighbour's trace at this face
-        T tw[NV], ts[NV];
+        V tw[NV], ts[NV];
         job.load_state(k, en, node, tw);
         if (r2) job.load_dir(k, en, node, ts);
 #pragma unroll
@@ -91,7 +95,7 @@ struct FaceFlux {
       }
     }
     // (L, R) = (own, neighbour) on the + face, (neighbour, own) on the - face
-    T wL[NV], wR[NV], sL[NV], sR[NV];
+    V wL[NV], wR[NV], sL[NV], sR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       wL[v] = SIDE ? wo[v] : wn[v];
@@ -99,9 +103,14 @@ struct FaceFlux {
       sL[v] = SIDE ? so[v] : sn[v];
       sR[v] = SIDE ? sn[v] : so[v];
     }
-    T FL[NV], FR[NV], kap[NV];
+    V FL[NV], FR[NV];
+    T kap[NV];
     if (prm.rusanov) {
-      const T cmax = T(0.5) * fmax(L::speed(wL, M, prm), L::speed(wR, M, prm));
+      // dissipation from the real parts of the traces: frozen in derivatives
+      T wLr[NV], wRr[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { wLr[v] = real_part(wL[v]); wRr[v] = real_part(wR[v]); }
+      const T cmax = T(0.5) * fmax(L::speed(wLr, M, prm), L::speed(wRr, M, prm));
 #pragma unroll
       for (int v = 0; v < NV; ++v) kap[v] = cmax;
     } else {
@@ -114,15 +123,16 @@ struct FaceFlux {
     const int f = 2 * M + SIDE;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const T jump = r2 ? (sL[v] - sR[v]) : (wL[v] - wR[v]);
+      const V jump = r2 ? (sL[v] - sR[v]) : (wL[v] - wR[v]);
       sface[(f * NV + v) * NF + pt] = sgn * (T(0.5) * (FL[v] + FR[v]) + kap[v] * jump);
     }
   }
 };
 
-template <int LAW, int DIM, int P, bool LGL, typename T, class Job>
+template <int LAW, int DIM, int P, bool LGL, typename V, class Job>
 __global__ void __launch_bounds__(Geo<DIM, P>::THREADS)
-dg_operator_kernel(const Job job, const DGParams<T> prm) {
+dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) {
+  using T = typename BaseOf<V>::type;
   using L = typename LawOf<LAW, DIM, T>::type;
   using G = Geo<DIM, P>;
   constexpr int NV = L::NV, NN = G::NN, NF = G::NF, EPB = G::EPB;
@@ -143,15 +153,15 @@ dg_operator_kernel(const Job job, const DGParams<T> prm) {
     sSp[t] = prm.sp[t / P][t % P];
     sSm[t] = prm.sm[t / P][t % P];
   }
-  T* const smem = sSm + DIM * P;
+  V* const smem = reinterpret_cast<V*>(smem_raw + KernelShape<LAW, DIM, P>::template mats_bytes<V, T>());
   const int le = threadIdx.x / NN;
   const int n = threadIdx.x - le * NN;
   const int e = blockIdx.x * EPB + le;
   const bool live = e < prm.nE;
-  T* const sst = smem + le * PER_ELEM;     // [NV][NN] state
-  T* const sdir = sst + NV * NN;           // [NV][NN] direction (R2)
-  T* const sG = sdir + NV * NN;            // [DIM][NV][NN] nodal fluxes
-  T* const sface = sG + DIM * NV * NN;     // [2*DIM][NV][NF] face fluxes
+  V* const sst = smem + le * PER_ELEM;     // [NV][NN] state
+  V* const sdir = sst + NV * NN;           // [NV][NN] direction (R2)
+  V* const sG = sdir + NV * NN;            // [DIM][NV][NN] nodal fluxes
+  V* const sface = sG + DIM * NV * NN;     // [2*DIM][NV][NF] face fluxes
 
   int ec[3] = {0, 0, 0};
   if (live) {
@@ -164,14 +174,14 @@ dg_operator_kernel(const Job job, const DGParams<T> prm) {
   if (DIM > 1) idx[1] = (n / P) % P;
   if (DIM > 2) idx[2] = n / (P * P);
 
-  T res[Job::K][NV];
+  V res[Job::K][NV];
 
 #pragma unroll
   for (int k = 0; k < Job::K; ++k) {
     const bool r2 = Job::kind(k) == EV_R2;
     // -- 1. node values and nodal fluxes --------------------------------
     if (live) {
-      T w[NV], s[NV];
+      V w[NV], s[NV];
       job.load_state(k, e, n, w);
       if (r2) job.load_dir(k, e, n, s);
 #pragma unroll
@@ -180,7 +190,7 @@ dg_operator_kernel(const Job job, const DGParams<T> prm) {
         if (r2) sdir[v * NN + n] = s[v];
       }
       if constexpr (!L::LINEAR) {
-        T F[DIM][NV];
+        V F[DIM][NV];
         if (r2) L::jvp_all(w, s, F, prm); else L::flux_all(w, F, prm);
 #pragma unroll
         for (int m = 0; m < DIM; ++m)
@@ -193,7 +203,7 @@ dg_operator_kernel(const Job job, const DGParams<T> prm) {
     if (live) {
       for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
         const int f = fp / NF, pt = fp - f * NF;
-        using FF = FaceFlux<LAW, DIM, P, LGL, T, Job>;
+        using FF = FaceFlux<LAW, DIM, P, LGL, V, Job>;
         switch (f) {
           case 0: FF::template run<0, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
           case 1: FF::template run<0, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
@@ -210,21 +220,21 @@ dg_operator_kernel(const Job job, const DGParams<T> prm) {
     if (live) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T acc = 0;
+        V acc = V(T(0));
 #pragma unroll
         for (int m = 0; m < DIM; ++m) {
           const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
           const int i = idx[m];
           const int b0 = n - i * st;
-          const T* g;
+          const V* g;
           if constexpr (L::LINEAR) g = (r2 ? sdir : sst) + v * NN;
           else g = sG + (m * NV + v) * NN;
           const T* Drow = sD + (m * P + i) * P;
 #pragma unroll
           for (int l = 0; l < P; ++l) acc += Drow[l] * g[b0 + l * st];
           const int pt = (n % st) + (n / (st * P)) * st;
-          const T* fm = sface + ((2 * m) * NV + v) * NF;
-          const T* fpl = sface + ((2 * m + 1) * NV + v) * NF;
+          const V* fm = sface + ((2 * m) * NV + v) * NF;
+          const V* fpl = sface + ((2 * m + 1) * NV + v) * NF;
           if constexpr (LGL) {
             if (i == P - 1) acc += sSp[m * P + P - 1] * fpl[pt];
             if (i == 0) acc += sSm[m * P] * fm[pt];
@@ -315,27 +325,29 @@ struct JobResidual {
 // z = scale * V[:, col] where col = *jidx (device scalar; 0 if jidx is null),
 // scale = vscale[col] (1 if vscale is null) and nrmW[col], nrmS[col] are the
 // Euclidean norms of the unscaled W and sigma halves.  The output goes to
-// column *out_jidx + out_offset of `out` (same layout).
-struct JvInput {
-  const double* V; size_t ld, half;
+// column *out_jidx + out_offset of `out` (same layout).  S is the storage type.
+template <typename S>
+struct JvInputT {
+  const S* V; size_t ld, half;
   const int* jidx;
   const double* vscale;
   const double* nrmW; const double* nrmS;
   const int* skip;              // device flag: nonzero -> nothing to do
-  double* out; size_t out_ld; int out_offset;
+  S* out; size_t out_ld; int out_offset;
   const int* out_jidx;          // output column = *out_jidx + out_offset (null -> out_offset)
   __device__ __forceinline__ int col() const { return jidx ? *jidx : 0; }
-  __device__ __forceinline__ const double* zW() const { return V + size_t(col()) * ld; }
-  __device__ __forceinline__ const double* zS() const { return zW() + half; }
+  __device__ __forceinline__ const S* zW() const { return V + size_t(col()) * ld; }
+  __device__ __forceinline__ const S* zS() const { return zW() + half; }
   __device__ __forceinline__ double scale() const { return vscale ? vscale[col()] : 1.0; }
   __device__ __forceinline__ double nW() const { return fabs(scale()) * nrmW[col()]; }
   __device__ __forceinline__ double nS() const { return fabs(scale()) * nrmS[col()]; }
-  __device__ __forceinline__ double* oW() const {
+  __device__ __forceinline__ S* oW() const {
     return out + size_t((out_jidx ? *out_jidx : 0) + out_offset) * out_ld;
   }
-  __device__ __forceinline__ double* oS() const { return oW() + half; }
+  __device__ __forceinline__ S* oS() const { return oW() + half; }
   __device__ __forceinline__ bool skipped() const { return skip && *skip; }
 };
+using JvInput = JvInputT<double>;
 
 struct JvCoef {
   const double* c1;        // device scalars alpha1 dt and alpha2 dt^2 / 2
@@ -422,30 +434,78 @@ struct JobJvFD_B {
   }
 };
 
-// Eq. 24 (linear flux): out = (dW - c1 R1(dW) + c2 R1(dS), dS - R1(dW)).
-template <int NV, int NN>
+// Eq. 24 (linear flux): out = (dW - c1 R1(dW) + c2 R1(dS), dS - R1(dW)),
+// arithmetic in T, vectors stored as S (FP64, or FP32 in the mixed mode).
+template <int NV, int NN, typename T = double, typename S = double>
 struct JobJvLinear {
   static constexpr int K = 2;
-  JvInput z; JvCoef c;
+  JvInputT<S> z; JvCoef c;
   __device__ static constexpr int kind(int) { return EV_R1; }
   __device__ bool active() const { return !z.skipped(); }
-  __device__ void load_state(int k, int e, int n, double* x) const {
-    const double* src = k == 0 ? z.zW() : z.zS();
-    const double sc = z.scale();
+  __device__ void load_state(int k, int e, int n, T* x) const {
+    const S* src = k == 0 ? z.zW() : z.zS();
+    const T sc = T(z.scale());
 #pragma unroll
-    for (int v = 0; v < NV; ++v) x[v] = sc * src[(size_t(e) * NV + v) * NN + n];
+    for (int v = 0; v < NV; ++v) x[v] = sc * T(src[(size_t(e) * NV + v) * NN + n]);
   }
-  __device__ void load_dir(int, int, int, double*) const {}
-  __device__ void epilogue(int e, int n, const double (*r)[NV]) const {
-    const double c1 = *c.c1, c2 = *c.c2, sc = z.scale();
-    const double* zw = z.zW(); const double* zs = z.zS();
-    double* ow = z.oW(); double* os = z.oS();
+  __device__ void load_dir(int, int, int, T*) const {}
+  __device__ void epilogue(int e, int n, const T (*r)[NV]) const {
+    const T c1 = T(*c.c1), c2 = T(*c.c2), sc = T(z.scale());
+    const S* zw = z.zW(); const S* zs = z.zS();
+    S* ow = z.oW(); S* os = z.oS();
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const size_t i = (size_t(e) * NV + v) * NN + n;
-      const double a = r[0][v], b = r[1][v];
-      ow[i] = sc * zw[i] - c1 * a + c2 * b;
-      os[i] = sc * zs[i] - a;
+      const T a = r[0][v], b = r[1][v];
+      ow[i] = S(sc * T(zw[i]) - c1 * a + c2 * b);
+      os[i] = S(sc * T(zs[i]) - a);
+    }
+  }
+};
+
+// Analytic Jacobian-vector product of the stage system (Eq. 18) in FP32 with
+// dual numbers, used by the mixed-precision mode for a nonlinear flux:
+//   eval 0: R1 at the dual state W + eps dW          -> eps part R2(W, dW)
+//   eval 1: R2 at (W + eps dW, S + eps dS)            -> eps part R2(W, dS) + dR2/dW[dW]
+//   out = (dW - c1 R2(W, dW) + c2 (R2(W, dS) + dR2/dW[dW]),  dS - R2(W, dW)),
+// i.e. Eq. 18 with dR1/dW = R2(W, .) (Sec. 3.2.1) and the Hessian block taken
+// exactly (the dissipation coefficient of a Rusanov flux is frozen).
+template <int NV, int NN>
+struct JobJvMixed {
+  static constexpr int K = 2;
+  using V = Dual<float>;
+  const float* W; const float* Sg;   // FP32 copies of the linearisation point (W, sigma)
+  JvInputT<float> z; JvCoef c;
+  __device__ static constexpr int kind(int k) { return k == 0 ? EV_R1 : EV_R2; }
+  __device__ bool active() const { return !z.skipped(); }
+  __device__ void load_state(int, int e, int n, V* x) const {
+    const float sc = float(z.scale());
+    const float* zw = z.zW();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      x[v] = V(W[i], sc * zw[i]);
+    }
+  }
+  __device__ void load_dir(int, int e, int n, V* x) const {
+    const float sc = float(z.scale());
+    const float* zs = z.zS();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      x[v] = V(Sg[i], sc * zs[i]);
+    }
+  }
+  __device__ void epilogue(int e, int n, const V (*r)[NV]) const {
+    const float c1 = float(*c.c1), c2 = float(*c.c2), sc = float(z.scale());
+    const float* zw = z.zW(); const float* zs = z.zS();
+    float* ow = z.oW(); float* os = z.oS();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t i = (size_t(e) * NV + v) * NN + n;
+      const float d0 = r[0][v].d, d1 = r[1][v].d;
+      ow[i] = sc * zw[i] - c1 * d0 + c2 * d1;
+      os[i] = sc * zs[i] - d0;
     }
   }
 };

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,7 @@
 #include "hbpc_internal.h"
 #include "krylov.cuh"
 #include "bjext_kernels.cuh"
+#include "mlp.cuh"
 
 namespace hbpc {
 
@@ -132,6 +134,36 @@ struct hbpc_ctx {
   size_t pc_smem = 0;
   bool pc_built = false;
   double pc_c1 = 0.0, pc_c2 = 0.0;
+  // mixed precision (FP32 Krylov loop, FP64 Newton)
+  DGParams<float> prmf{};
+  KrylovT<float> Kf{};
+  float* Vf = nullptr;      // FP32 Krylov basis
+  float* Zf = nullptr;      // FP32 preconditioned vector / scratch, 2 n_dof
+  float* Zf2 = nullptr;     // FP32 scratch, 2 n_dof
+  float* Wf = nullptr;      // FP32 copy of the linearisation point (W, sigma)
+  float* Mf = nullptr;      // FP32 copies of the BJ_ext blocks
+  float* Jf = nullptr;
+  // learned block preconditioner (network, replay buffer, scratch)
+  struct Learned {
+    bool alloc = false;
+    int nb = 0, din = 0, dinp = 0, H = kMlpHidden, dout = 0, doutp = 0;
+    size_t np = 0, np_train = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+    float* P = nullptr; float* G = nullptr; float* Mo = nullptr; float* Ve = nullptr;
+    __nv_bfloat16* W1h = nullptr; __nv_bfloat16* W2h = nullptr; __nv_bfloat16* W3h = nullptr;
+    __nv_bfloat16* W2T = nullptr; __nv_bfloat16* W3T = nullptr;
+    float* mu = nullptr; float* sd = nullptr;
+    bool stats = false;
+    int adam_t = 0;
+    int cap = 0, count = 0, next = 0, per_newton = 0, offset = 0;
+    float* featbuf = nullptr; float* Jbuf = nullptr; float* cbuf = nullptr;
+    __nv_bfloat16* Fi = nullptr; __nv_bfloat16* H1i = nullptr; __nv_bfloat16* H2i = nullptr;
+    int Bmax = 0;
+    __nv_bfloat16 *Fb = nullptr, *H1b = nullptr, *H2b = nullptr, *dOb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    __nv_bfloat16 *dOT = nullptr, *H2T = nullptr, *dZ2T = nullptr, *H1T = nullptr, *dZ1T = nullptr, *FT = nullptr;
+    float *Jb = nullptr, *cb = nullptr, *Ob = nullptr, *Xb = nullptr;
+    double* lpart = nullptr;
+    int* idx = nullptr;
+  } lp;
   Krylov K{};
   hbpc_stats stats{};
   std::string err;
@@ -267,7 +299,7 @@ hbpc_status read_state(hbpc_ctx* x) {
 
 // squared norms of a 2 n_dof vector into st->nrm (and sqrt into out3 if given)
 hbpc_status norms(hbpc_ctx* x, const double* v, size_t n, double* out3 = nullptr) {
-  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<<<x->nblocks, kVecThreads, 0, x->stream>>>(v, n, size_t(x->ndof), x->K, nullptr));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, double><<<x->nblocks, kVecThreads, 0, x->stream>>>(v, n, size_t(x->ndof), x->K, nullptr));
   HBPC_LAUNCH_CK(x, "k_norms");
   if (out3) {
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sqrt_norms<<<1, 32, 0, x->stream>>>(x->st, out3));
@@ -307,7 +339,7 @@ JvInput krylov_input(hbpc_ctx* x) {
   z.skip = &x->st->done;
   z.out = x->V; z.out_ld = size_t(2 * x->ndof); z.out_offset = 1;
   z.out_jidx = &x->st->j;
-  if (x->sol.pc == HBPC_PC_BJEXT) {   // Jv acts on z = P^-1 v_j, kept in Z
+  if (x->sol.pc != HBPC_PC_NONE) {   // Jv acts on z = P^-1 v_j, kept in Z
     z.V = x->Z; z.jidx = nullptr; z.vscale = nullptr;
     z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
   }
@@ -322,19 +354,245 @@ hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const doubl
   a.xW = in; a.xS = in + x->ndof;
   a.scale = scale; a.jidx = jidx; a.ld = size_t(2 * x->ndof);
   a.oW = out; a.oS = out + x->ndof;
-  a.c12 = x->c12; a.skip = skip; a.accumulate = accumulate; a.zn = x->zn;
+  a.c12 = x->c12; a.skip = skip; a.accumulate = accumulate;
+  a.zn = x->ops.jv_linear ? nullptr : x->zn;   // ||z|| halves feed eps_FD of Eq. 23 only
   a.nb = x->nb; a.nE = int(x->nE);
-  HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
+  HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<double><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply");
+  return HBPC_OK;
+}
+
+// FP32 version for the mixed mode (blocks in Mf, Jf)
+hbpc_status pc_apply_f(hbpc_ctx* x, const float* in, const int* jidx, const double* scale, float* out,
+                       int accumulate, const int* skip) {
+  PcApplyT<float> a{};
+  a.M = x->Mf; a.J = x->Jf;
+  a.xW = in; a.xS = in + x->ndof;
+  a.scale = scale; a.jidx = jidx; a.ld = size_t(2 * x->ndof);
+  a.oW = out; a.oS = out + x->ndof;
+  a.c12 = x->c12; a.skip = skip; a.accumulate = accumulate;
+  a.zn = nullptr;   // the analytic FP32 Jv needs no norms
+  a.nb = x->nb; a.nE = int(x->nE);
+  HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<float><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
+  HBPC_LAUNCH_CK(x, "k_pc_apply<float>");
+  return HBPC_OK;
+}
+
+hbpc_status to_float(hbpc_ctx* x, const double* in, float* out, size_t n) {
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_to_float<<<grid_for(n), 256, 0, x->stream>>>(in, out, n, 1.0));
+  HBPC_LAUNCH_CK(x, "k_to_float");
+  return HBPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned block preconditioner (mlp.cuh): allocation, inference, training.
+// ---------------------------------------------------------------------------
+template <typename Tp>
+hbpc_status dalloc_any(hbpc_ctx* x, Tp** p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(Tp));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(x, HBPC_ERR_OOM, std::string("cudaMalloc (learned preconditioner): ") + cudaGetErrorString(e));
+  }
+  return HBPC_OK;
+}
+
+template <class Epi>
+hbpc_status gemm(hbpc_ctx* x, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                 int K, Epi epi) {
+  if (K % 8 || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+    return fail(x, HBPC_ERR_INVALID_ARG, "GEMM operands must be 16-byte aligned with K, ld multiples of 8");
+  const dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_gemm_bf16_nt<Epi><<<grid, kGemmThreads, 0, x->stream>>>(A, lda, B, ldb, M, N, K, epi));
+  HBPC_LAUNCH_CK(x, "k_gemm_bf16_nt");
+  return HBPC_OK;
+}
+
+hbpc_status lp_transpose(hbpc_ctx* x, const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols) {
+  const dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_transpose_bf16<<<grid, block, 0, x->stream>>>(in, out, rows, cols));
+  HBPC_LAUNCH_CK(x, "k_transpose_bf16");
+  return HBPC_OK;
+}
+
+// Allocate the network, its optimiser state and the inference scratch.
+hbpc_status lp_alloc(hbpc_ctx* x) {
+  auto& L = x->lp;
+  if (L.alloc) return HBPC_OK;
+  L.nb = x->nb;
+  L.din = L.nb + 2;
+  L.dinp = ((L.din + 15) / 16) * 16;
+  L.dout = L.nb * L.nb;
+  L.doutp = ((L.dout + 7) / 8) * 8;
+  const size_t H = size_t(L.H);
+  L.oW1 = 0; L.ob1 = L.oW1 + H * L.dinp; L.oW2 = L.ob1 + H; L.ob2 = L.oW2 + H * H;
+  L.oW3 = L.ob2 + H; L.ob3 = L.oW3 + size_t(L.doutp) * H; L.np_train = L.ob3 + L.doutp;
+  L.np = L.np_train + 2 * size_t(L.dinp);   // + feature standardisation (mu, sd)
+  hbpc_status e;
+  if ((e = dalloc_any(x, &L.P, L.np)) || (e = dalloc_any(x, &L.G, L.np)) || (e = dalloc_any(x, &L.Mo, L.np)) ||
+      (e = dalloc_any(x, &L.Ve, L.np)) || (e = dalloc_any(x, &L.W1h, H * L.dinp)) ||
+      (e = dalloc_any(x, &L.W2h, H * H)) || (e = dalloc_any(x, &L.W3h, size_t(L.doutp) * H)) ||
+      (e = dalloc_any(x, &L.W2T, H * H)) || (e = dalloc_any(x, &L.W3T, size_t(L.doutp) * H)) ||
+      (e = dalloc_any(x, &L.Fi, size_t(x->nE) * L.dinp)) || (e = dalloc_any(x, &L.H1i, size_t(x->nE) * H)) ||
+      (e = dalloc_any(x, &L.H2i, size_t(x->nE) * H)))
+    return e;
+  L.mu = L.P + L.np_train;
+  L.sd = L.mu + L.dinp;
+  HBPC_CK(x, cudaMemsetAsync(L.P, 0, L.np * sizeof(float), x->stream));
+  HBPC_CK(x, cudaMemsetAsync(L.Mo, 0, L.np * sizeof(float), x->stream));
+  HBPC_CK(x, cudaMemsetAsync(L.Ve, 0, L.np * sizeof(float), x->stream));
+  std::vector<float> ones(L.dinp, 1.0f);
+  HBPC_CK(x, cudaStreamSynchronize(x->stream));
+  HBPC_CK(x, cudaMemcpy(L.sd, ones.data(), L.dinp * sizeof(float), cudaMemcpyHostToDevice));
+  L.alloc = true;
+  return HBPC_OK;
+}
+
+hbpc_status lp_alloc_train(hbpc_ctx* x, int B, int P) {
+  auto& L = x->lp;
+  hbpc_status e;
+  if ((e = lp_alloc(x)) != HBPC_OK) return e;
+  if (B <= L.Bmax && L.Xb && P * L.nb * B <= L.Bmax * 16 * L.nb) return HBPC_OK;
+  const size_t Bs = size_t(B), H = size_t(L.H);
+  for (void* q : {(void*)L.Fb, (void*)L.H1b, (void*)L.H2b, (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1,
+                  (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T, (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT,
+                  (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb, (void*)L.lpart, (void*)L.idx})
+    cudaFree(q);
+  if ((e = dalloc_any(x, &L.Fb, Bs * L.dinp)) || (e = dalloc_any(x, &L.H1b, Bs * H)) ||
+      (e = dalloc_any(x, &L.H2b, Bs * H)) || (e = dalloc_any(x, &L.dOb, Bs * L.doutp)) ||
+      (e = dalloc_any(x, &L.dZ2, Bs * H)) || (e = dalloc_any(x, &L.dZ1, Bs * H)) ||
+      (e = dalloc_any(x, &L.dOT, Bs * L.doutp)) || (e = dalloc_any(x, &L.H2T, Bs * H)) ||
+      (e = dalloc_any(x, &L.dZ2T, Bs * H)) || (e = dalloc_any(x, &L.H1T, Bs * H)) ||
+      (e = dalloc_any(x, &L.dZ1T, Bs * H)) || (e = dalloc_any(x, &L.FT, Bs * L.dinp)) ||
+      (e = dalloc_any(x, &L.Jb, Bs * L.dout)) || (e = dalloc_any(x, &L.cb, Bs * 2)) ||
+      (e = dalloc_any(x, &L.Ob, Bs * L.doutp)) || (e = dalloc_any(x, &L.Xb, Bs * 16 * L.nb)) ||
+      (e = dalloc_any(x, &L.lpart, Bs)) || (e = dalloc_any(x, &L.idx, Bs)))
+    return e;
+  HBPC_CK(x, cudaMemsetAsync(L.dOb, 0, Bs * L.doutp * sizeof(__nv_bfloat16), x->stream));
+  L.Bmax = B;
+  return HBPC_OK;
+}
+
+void lp_free(hbpc_ctx* x) {
+  auto& L = x->lp;
+  for (void* q : {(void*)L.P, (void*)L.G, (void*)L.Mo, (void*)L.Ve, (void*)L.W1h, (void*)L.W2h, (void*)L.W3h,
+                  (void*)L.W2T, (void*)L.W3T, (void*)L.featbuf, (void*)L.Jbuf,
+                  (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
+                  (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
+                  (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
+                  (void*)L.lpart, (void*)L.idx})
+    cudaFree(q);
+  L = hbpc_ctx::Learned{};
+}
+
+// BF16 copies of the weights (and the transposes used by the backward pass)
+hbpc_status lp_refresh(hbpc_ctx* x) {
+  auto& L = x->lp;
+  const size_t H = size_t(L.H);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(H * L.dinp), 256, 0, x->stream>>>(L.P + L.oW1, L.W1h, H * L.dinp));
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(H * H), 256, 0, x->stream>>>(L.P + L.oW2, L.W2h, H * H));
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(size_t(L.doutp) * H), 256, 0, x->stream>>>(L.P + L.oW3, L.W3h, size_t(L.doutp) * H));
+  HBPC_LAUNCH_CK(x, "lp_refresh");
+  hbpc_status s;
+  if ((s = lp_transpose(x, L.W2h, L.W2T, L.H, L.H)) != HBPC_OK) return s;
+  return lp_transpose(x, L.W3h, L.W3T, L.doutp, L.H);
+}
+
+// M~_e for every element from the current network (replaces the LU of BJ_ext).
+hbpc_status lp_infer(hbpc_ctx* x, const double* W, double c1, double c2) {
+  auto& L = x->lp;
+  if (!L.alloc) return fail(x, HBPC_ERR_INVALID_ARG, "learned preconditioner has no network");
+  hbpc_status s;
+  const size_t nf = size_t(x->nE) * L.dinp;
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_features<<<grid_for(nf), 256, 0, x->stream>>>(W, int(x->nE), L.nb, c1, c2, L.mu, L.sd, L.dinp, L.Fi));
+  HBPC_LAUNCH_CK(x, "k_mlp_features");
+  const int nE = int(x->nE);
+  if ((s = gemm(x, L.Fi, L.dinp, L.W1h, L.dinp, nE, L.H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1i, L.H})) != HBPC_OK) return s;
+  if ((s = gemm(x, L.H1i, L.H, L.W2h, L.H, nE, L.H, L.H, EpiBiasTanh{L.P + L.ob2, L.H2i, L.H})) != HBPC_OK) return s;
+  if (x->sol.precision == HBPC_PREC_MIXED)
+    return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.P + L.ob3, x->Mf, L.nb});
+  return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<double>{L.P + L.ob3, x->Mpc, L.nb});
+}
+
+// One forward/backward pass on the batch already in Fb, Jb, cb, Xb: loss and
+// gradients (in L.G).
+hbpc_status lp_loss_grad(hbpc_ctx* x, int B, int P, double* loss) {
+  auto& L = x->lp;
+  hbpc_status s;
+  const int H = L.H;
+  // forward
+  if ((s = gemm(x, L.Fb, L.dinp, L.W1h, L.dinp, B, H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1b, H})) != HBPC_OK) return s;
+  if ((s = gemm(x, L.H1b, H, L.W2h, H, B, H, H, EpiBiasTanh{L.P + L.ob2, L.H2b, H})) != HBPC_OK) return s;
+  if ((s = gemm(x, L.H2b, H, L.W3h, H, B, L.doutp, H, EpiBiasF32{L.P + L.ob3, L.Ob, L.doutp})) != HBPC_OK) return s;
+  // probe loss and dO (dO keeps the n_b^2-wide row layout inside its doutp-wide rows)
+  const size_t shm = size_t(2 * P + 2) * L.nb * sizeof(float);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_probe_loss<<<B, 256, shm, x->stream>>>(L.Jb, L.cb, L.Ob, L.Xb, B, P, L.nb, L.doutp, L.dOb, L.lpart));
+  HBPC_LAUNCH_CK(x, "k_mlp_probe_loss");
+  // backward: W3, b3
+  if ((s = lp_transpose(x, L.dOb, L.dOT, B, L.doutp)) != HBPC_OK) return s;
+  if ((s = lp_transpose(x, L.H2b, L.H2T, B, H)) != HBPC_OK) return s;
+  if ((s = gemm(x, L.dOT, B, L.H2T, B, L.doutp, H, B, EpiStore{L.G + L.oW3, H})) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_colsum_bf16<<<(L.doutp + 255) / 256, 256, 0, x->stream>>>(L.dOb, B, L.doutp, L.G + L.ob3));
+  // dZ2 = (dO W3) * (1 - h2^2)
+  if ((s = gemm(x, L.dOb, L.doutp, L.W3T, L.doutp, B, H, L.doutp, EpiDtanh{L.H2b, L.dZ2, H})) != HBPC_OK) return s;
+  if ((s = lp_transpose(x, L.dZ2, L.dZ2T, B, H)) != HBPC_OK) return s;
+  if ((s = lp_transpose(x, L.H1b, L.H1T, B, H)) != HBPC_OK) return s;
+  if ((s = gemm(x, L.dZ2T, B, L.H1T, B, H, H, B, EpiStore{L.G + L.oW2, H})) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_colsum_bf16<<<(H + 255) / 256, 256, 0, x->stream>>>(L.dZ2, B, H, L.G + L.ob2));
+  // dZ1 = (dZ2 W2) * (1 - h1^2)
+  if ((s = gemm(x, L.dZ2, H, L.W2T, H, B, H, H, EpiDtanh{L.H1b, L.dZ1, H})) != HBPC_OK) return s;
+  if ((s = lp_transpose(x, L.dZ1, L.dZ1T, B, H)) != HBPC_OK) return s;
+  if ((s = lp_transpose(x, L.Fb, L.FT, B, L.dinp)) != HBPC_OK) return s;
+  if ((s = gemm(x, L.dZ1T, B, L.FT, B, H, L.dinp, B, EpiStore{L.G + L.oW1, L.dinp})) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_colsum_bf16<<<(H + 255) / 256, 256, 0, x->stream>>>(L.dZ1, B, H, L.G + L.ob1));
+  HBPC_LAUNCH_CK(x, "lp backward");
+  if (loss) {
+    std::vector<double> lp(B);
+    HBPC_CK(x, cudaMemcpyAsync(lp.data(), L.lpart, B * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+    if ((s = sync(x, "lp loss")) != HBPC_OK) return s;
+    double t = 0.0;
+    for (int i = 0; i < B; ++i) t += lp[i];
+    *loss = t;
+  }
+  return HBPC_OK;
+}
+
+// Sample the current Newton iteration's element Jacobians into the replay buffer.
+hbpc_status lp_collect(hbpc_ctx* x, const double* W, double c1, double c2) {
+  auto& L = x->lp;
+  if (L.per_newton <= 0 || !L.featbuf) return HBPC_OK;
+  const int count = std::min<int>(L.per_newton, int(x->nE));
+  const int stride = std::max<int>(1, int(x->nE) / count);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+           k_mlp_collect<<<count, 128, 0, x->stream>>>(W, x->Jpc, int(x->nE), L.nb, c1, c2, count, stride, L.offset,
+                                                        L.next, L.cap, L.featbuf, L.Jbuf, L.cbuf));
+  HBPC_LAUNCH_CK(x, "k_mlp_collect");
+  L.offset = (L.offset + 1) % std::max(1, stride);
+  L.next = (L.next + count) % L.cap;
+  L.count = std::min(L.cap, L.count + count);
   return HBPC_OK;
 }
 
 // Build J_i, S_i and M_i = S_i^-1 at the state W for the current c1, c2.
 hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   const bool linear = x->phys.law == HBPC_LAW_ADVECTION;
-  if (linear && x->pc_built && x->pc_c1 == c1 && x->pc_c2 == c2) return HBPC_OK;
+  const bool collecting = x->lp.per_newton > 0;
+  if (linear && !collecting && x->sol.pc != HBPC_PC_LEARNED && x->pc_built && x->pc_c1 == c1 &&
+      x->pc_c2 == c2)
+    return HBPC_OK;
   const size_t nb = size_t(x->nb);
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(x->prm, W, x->Jpc, x->stream));
+  hbpc_status s0;
+  if (collecting && (s0 = lp_collect(x, W, c1, c2)) != HBPC_OK) return s0;
+  if (x->sol.pc == HBPC_PC_LEARNED) {   // M~ from the network instead of the LU
+    if ((s0 = lp_infer(x, W, c1, c2)) != HBPC_OK) return s0;
+    if (x->sol.precision == HBPC_PREC_MIXED &&
+        (s0 = to_float(x, x->Jpc, x->Jf, size_t(x->nE) * nb * nb)) != HBPC_OK) return s0;
+    x->pc_built = true;
+    x->pc_c1 = c1;
+    x->pc_c2 = c2;
+    return HBPC_OK;
+  }
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
            k_pc_form_S<<<int(x->nE), 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb,
                                                                                    int(x->nE), x->c12));
@@ -347,25 +605,37 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   hbpc_status s = sync(x, "pc build");
   if (s != HBPC_OK) return s;
   if (sing) return fail(x, HBPC_ERR_NONFINITE, "BJ_ext block is singular");
+  if (x->sol.precision == HBPC_PREC_MIXED) {
+    const size_t blk = size_t(x->nE) * nb * nb;
+    if ((s = to_float(x, x->Mpc, x->Mf, blk)) != HBPC_OK) return s;
+    if ((s = to_float(x, x->Jpc, x->Jf, blk)) != HBPC_OK) return s;
+  }
   x->pc_built = true;
   x->pc_c1 = c1;
   x->pc_c2 = c2;
   return HBPC_OK;
 }
 
+// The four launches of one Gram-Schmidt (CGS2) column: dot, update + second
+// dot, update + norms, finalisation (krylov.cuh).
+template <typename S>
+void cgs_launch(hbpc_ctx* x, const KrylovT<S>& K) {
+  const size_t m1 = size_t(K.m + 1);
+  HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_cgs_dot<S><<<x->nblocks, kVecThreads, m1 * kVecWarps * sizeof(double), x->stream>>>(K));
+  HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_cgs_update_dot<S><<<x->nblocks, kVecThreads, m1 * (kVecWarps + 1) * sizeof(double), x->stream>>>(K));
+  HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_cgs_update<S><<<x->nblocks, kVecThreads, m1 * sizeof(double), x->stream>>>(K));
+  HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_cgs_finalize<S><<<1, kVecThreads, 3 * (m1 + 1) * sizeof(double), x->stream>>>(K));
+}
+
 hbpc_status arnoldi_step(hbpc_ctx* x) {
   hbpc_status s;
-  if (x->sol.pc == HBPC_PC_BJEXT) {
+  if (x->sol.pc != HBPC_PC_NONE) {
     s = pc_apply(x, x->V, &x->st->j, x->K.vscale, x->Z, 0, &x->st->done);
     if (s != HBPC_OK) return s;
   }
   s = apply_jv(x, krylov_input(x));
   if (s != HBPC_OK) return s;
-  const size_t sm = sizeof(double) * size_t(x->K.m + 3);
-  HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_arnoldi_dot<<<x->nblocks, kVecThreads, sm, x->stream>>>(x->K, 0));
-  HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_arnoldi_update<<<x->nblocks, kVecThreads, sm, x->stream>>>(x->K, 0));
-  HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_arnoldi_dot<<<x->nblocks, kVecThreads, sm, x->stream>>>(x->K, 1));
-  HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_arnoldi_update<<<x->nblocks, kVecThreads, sm, x->stream>>>(x->K, 1));
+  cgs_launch<double>(x, x->K);
   HBPC_LAUNCH_CK(x, "arnoldi");
   return HBPC_OK;
 }
@@ -376,7 +646,7 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const size_t n2 = size_t(2 * x->ndof);
   HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
   HBPC_CK(x, cudaMemcpyAsync(x->V, x->G, n2 * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
-  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<<<1, 32, 0, x->stream>>>(x->K, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
   HBPC_LAUNCH_CK(x, "k_cycle_init");
   const int batch = 4;
   for (;;) {
@@ -391,13 +661,13 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
       return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
     if (!h.done) continue;
     // end of a cycle: dX += V y
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<<<1, 32, 0, x->stream>>>(x->K));
-    if (x->sol.pc == HBPC_PC_BJEXT) {   // dX += P^-1 (V y)
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->Z, 0));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<double><<<1, 32, 0, x->stream>>>(x->K));
+    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->Z, 0));
       s = pc_apply(x, x->Z, nullptr, nullptr, x->dX, 1, nullptr);
       if (s != HBPC_OK) return s;
     } else {
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->dX, 1));
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->dX, 1));
     }
     HBPC_LAUNCH_CK(x, "gmres update");
     if (h.converged || h.its >= h.max_its) {
@@ -419,8 +689,94 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->V + n2, x->V, n2));
     s = norms(x, x->V, n2);
     if (s != HBPC_OK) return s;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
     HBPC_LAUNCH_CK(x, "k_cycle_init");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: the Krylov loop in FP32 (basis, Jacobian-vector product
+// with the analytic linearised operator, BJ_ext apply), the Newton residual,
+// update and stage logic in FP64.  Hessenberg, Givens rotations and the
+// cross-thread / cross-block sums of the Arnoldi reductions stay FP64.
+// ---------------------------------------------------------------------------
+JvInputT<float> krylov_input_f(hbpc_ctx* x) {
+  JvInputT<float> z{};
+  z.V = x->Vf; z.ld = size_t(2 * x->ndof); z.half = size_t(x->ndof);
+  z.jidx = &x->st->j;
+  z.vscale = x->Kf.vscale;
+  z.nrmW = x->Kf.nrmW; z.nrmS = x->Kf.nrmS;
+  z.skip = &x->st->done;
+  z.out = x->Vf; z.out_ld = size_t(2 * x->ndof); z.out_offset = 1;
+  z.out_jidx = &x->st->j;
+  if (x->sol.pc != HBPC_PC_NONE) {
+    z.V = x->Zf; z.jidx = nullptr; z.vscale = nullptr;
+    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
+  }
+  return z;
+}
+
+hbpc_status apply_jv_f(hbpc_ctx* x, const JvInputT<float>& z) {
+  HBPC_RUN(x, HBPC_PHASE_JV, 1,
+           x->ops.jv_f(x->prmf, z, jv_coef(x), x->Wf, x->Wf + x->ndof, x->stream));
+  HBPC_LAUNCH_CK(x, "jv_f");
+  return HBPC_OK;
+}
+
+hbpc_status arnoldi_step_f(hbpc_ctx* x) {
+  hbpc_status s;
+  if (x->sol.pc != HBPC_PC_NONE) {
+    s = pc_apply_f(x, x->Vf, &x->st->j, x->Kf.vscale, x->Zf, 0, &x->st->done);
+    if (s != HBPC_OK) return s;
+  }
+  if ((s = apply_jv_f(x, krylov_input_f(x))) != HBPC_OK) return s;
+  cgs_launch<float>(x, x->Kf);
+  HBPC_LAUNCH_CK(x, "arnoldi<float>");
+  return HBPC_OK;
+}
+
+hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
+  const size_t n2 = size_t(2 * x->ndof);
+  hbpc_status s;
+  HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
+  if ((s = to_float(x, x->G, x->Vf, n2)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
+  HBPC_LAUNCH_CK(x, "k_cycle_init<float>");
+  const int batch = 4;
+  for (;;) {
+    for (int b = 0; b < batch; ++b)
+      if ((s = arnoldi_step_f(x)) != HBPC_OK) return s;
+    if ((s = read_state(x)) != HBPC_OK) return s;
+    const GmresState& h = *x->st_host;
+    if (!(h.resid == h.resid) || std::isinf(h.resid))
+      return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
+    if (!h.done) continue;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<float><<<1, 32, 0, x->stream>>>(x->Kf));
+    const size_t smy = sizeof(double) * size_t(x->Kf.m + 1);
+    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, float><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->Zf, 0));
+      if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
+    } else {
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, double><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->dX, 1));
+    }
+    HBPC_LAUNCH_CK(x, "gmres<float> update");
+    if (h.converged || h.its >= h.max_its) {
+      *its_out = h.its;
+      *conv_out = h.converged != 0;
+      return HBPC_OK;
+    }
+    // restart: V_0 = -G - J dX (FP32 Jacobian-vector product of the FP32 copy of dX)
+    if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
+    JvInputT<float> z{};
+    z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
+    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
+    z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
+    if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, float><<<x->nblocks, kVecThreads, 0, x->stream>>>(x->Vf, n2, size_t(x->ndof), x->K, nullptr));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
+    HBPC_LAUNCH_CK(x, "gmres<float> restart");
   }
 }
 
@@ -455,8 +811,13 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
   for (int r = 0; r < x->sol.newton_max_iter; ++r) {
     int its = 0;
     bool conv = false;
-    if (x->sol.pc == HBPC_PC_BJEXT && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
-    if ((s = gmres(x, &its, &conv)) != HBPC_OK) return s;
+    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    if (x->sol.precision == HBPC_PREC_MIXED) {
+      if ((s = to_float(x, x->X, x->Wf, size_t(2 * n))) != HBPC_OK) return s;
+      if ((s = gmres_f(x, &its, &conv)) != HBPC_OK) return s;
+    } else {
+      if ((s = gmres(x, &its, &conv)) != HBPC_OK) return s;
+    }
     x->stats.gmres_its += its;
     x->stats.newton_its += 1;
     const int per = x->ops.jv_linear ? 2 : 3;
@@ -562,7 +923,41 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->dX); cudaFree(x->bvec); cudaFree(x->stage); cudaFree(x->V); cudaFree(x->small);
   cudaFree(x->partial); cudaFree(x->ticket); cudaFree(x->st);
   cudaFree(x->Jpc); cudaFree(x->Mpc); cudaFree(x->Z); cudaFree(x->singular);
+  cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
+  lp_free(x);
   if (x->st_host) cudaFreeHost(x->st_host);
+}
+
+// Launch shape of the BJ_ext apply (depends only on the block size)
+void pc_launch_config(hbpc_ctx* x) {
+  const int epb = std::max(1, 256 / x->nb);
+  x->pc_threads = ((epb * x->nb + 31) / 32) * 32;
+  x->pc_grid = int((x->nE + epb - 1) / epb);
+  x->pc_smem = size_t(epb) * 4 * x->nb * sizeof(double);
+}
+
+// Device memory of the block preconditioners (BJ_ext and learned).
+hbpc_status pc_alloc(hbpc_ctx* x) {
+  if (x->Jpc) return HBPC_OK;
+  const size_t blk = size_t(x->nE) * x->nb * x->nb, n2 = size_t(2 * x->ndof);
+  hbpc_status e;
+  if ((e = dmalloc(x, &x->Jpc, blk)) || (e = dmalloc(x, &x->Mpc, blk)) || (e = dmalloc(x, &x->Z, n2)) ||
+      (e = dmalloc(x, &x->singular, 1)))
+    return e;
+  HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
+  const size_t nbz = size_t(x->nb);
+  cudaFuncSetAttribute(k_pc_form_S, cudaFuncAttributeMaxDynamicSharedMemorySize, int(nbz * nbz * sizeof(double)));
+  cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int((nbz * nbz + nbz) * sizeof(double) + nbz * sizeof(int)));
+  return HBPC_OK;
+}
+
+hbpc_status pc_alloc_f(hbpc_ctx* x) {
+  if (x->Mf) return HBPC_OK;
+  const size_t blk = size_t(x->nE) * x->nb * x->nb;
+  hbpc_status e;
+  if ((e = dmalloc(x, &x->Mf, blk)) || (e = dmalloc(x, &x->Jf, blk))) return e;
+  return HBPC_OK;
 }
 
 hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics* ph,
@@ -587,14 +982,15 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   if (so->gmres_max_iter < 1 || so->newton_max_iter < 1) return bad("iteration caps must be >= 1");
   if (!(so->tol_gmres_rel > 0.0) || !(so->tol_newton_rel >= 0.0) || !(so->tol_newton_abs >= 0.0))
     return bad("tolerances must be positive");
-  if (so->pc != HBPC_PC_NONE && so->pc != HBPC_PC_BJEXT) return bad("unknown preconditioner");
-  if (so->pc == HBPC_PC_BJEXT) {
+  if (so->pc != HBPC_PC_NONE && so->pc != HBPC_PC_BJEXT && so->pc != HBPC_PC_LEARNED)
+    return bad("unknown preconditioner");
+  if (so->pc != HBPC_PC_NONE) {
     int nb = (ph->law == HBPC_LAW_EULER) ? mesh->dim + 2 : 1;
     for (int m = 0; m < mesh->dim; ++m) nb *= (N + 1);
     if (nb > kMaxPcBlock)
       return fail(nullptr, HBPC_ERR_UNSUPPORTED, "BJ_ext block n_var (N+1)^dim exceeds the supported size");
   }
-  if (so->precision != HBPC_PREC_FP64) return fail(nullptr, HBPC_ERR_UNSUPPORTED, "precision not available");
+  if (so->precision != HBPC_PREC_FP64 && so->precision != HBPC_PREC_MIXED) return bad("unknown precision");
   return HBPC_OK;
 }
 
@@ -628,6 +1024,24 @@ void fill_params(hbpc_ctx* x) {
   p.inv_eps2 = 1.0 / p.eps2;
   p.inv_eps = 1.0 / x->phys.eps;
   p.rusanov = x->phys.flux == HBPC_FLUX_RUSANOV ? 1 : 0;
+  // FP32 copy for the mixed-precision Jacobian-vector product
+  DGParams<float>& f = x->prmf;
+  std::memset(&f, 0, sizeof(f));
+  for (int m = 0; m < 3; ++m) f.n[m] = p.n[m];
+  f.nE = p.nE;
+  for (int m = 0; m < 3; ++m) {
+    for (int i = 0; i < kMaxP; ++i) {
+      for (int l = 0; l < kMaxP; ++l) f.Dvol[m][i][l] = float(p.Dvol[m][i][l]);
+      f.sp[m][i] = float(p.sp[m][i]);
+      f.sm[m][i] = float(p.sm[m][i]);
+    }
+    for (int v = 0; v < 5; ++v) f.lam[m][v] = float(p.lam[m][v]);
+    f.a[m] = float(p.a[m]);
+  }
+  for (int i = 0; i < kMaxP; ++i) { f.lp[i] = float(p.lp[i]); f.lm[i] = float(p.lm[i]); }
+  f.gm1 = float(p.gm1); f.gamma = float(p.gamma); f.eps2 = float(p.eps2);
+  f.inv_eps2 = float(p.inv_eps2); f.inv_eps = float(p.inv_eps);
+  f.rusanov = p.rusanov;
 }
 
 
@@ -726,12 +1140,7 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   x->nblocks = std::max(1, std::min<int>(2 * sms, int((n2 + 1023) / 1024)));
   x->nb = int(x->ndof / x->nE);
-  if (solver->pc == HBPC_PC_BJEXT) {
-    const int epb = std::max(1, 256 / x->nb);
-    x->pc_threads = ((epb * x->nb + 31) / 32) * 32;
-    x->pc_grid = int((x->nE + epb - 1) / epb);
-    x->pc_smem = size_t(epb) * 4 * x->nb * sizeof(double);
-  }
+  pc_launch_config(x);
   const int prows = std::max(x->nblocks, x->pc_grid);
   hbpc_status e = HBPC_OK;
   if ((e = dmalloc(x, &x->Wn, n)) || (e = dmalloc(x, &x->X, n2)) || (e = dmalloc(x, &x->G, n2)) ||
@@ -741,20 +1150,27 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
     g_create_error = x->err;
     free_all(x); delete x; return e;
   }
-  const size_t nsmall = size_t(m + 1) * m + 3 * m + 8 * (m + 3) + 24;
-  if (solver->pc == HBPC_PC_BJEXT) {
-    const size_t blk = size_t(x->nE) * x->nb * x->nb;
-    if ((e = dmalloc(x, &x->Jpc, blk)) || (e = dmalloc(x, &x->Mpc, blk)) || (e = dmalloc(x, &x->Z, n2)) ||
-        (e = dmalloc(x, &x->singular, 1))) {
+  const size_t nsmall = size_t(m + 1) * m + 3 * m + 9 * (m + 3) + 24;
+  if (solver->pc != HBPC_PC_NONE && (e = pc_alloc(x)) != HBPC_OK) {
+    g_create_error = x->err;
+    free_all(x); delete x; return e;
+  }
+  if (solver->pc == HBPC_PC_LEARNED && (e = lp_alloc(x)) != HBPC_OK) {
+    g_create_error = x->err;
+    free_all(x); delete x; return e;
+  }
+  if (solver->precision == HBPC_PREC_MIXED) {
+    if ((e = dmalloc(x, &x->Vf, size_t(m + 1) * n2)) || (e = dmalloc(x, &x->Zf, n2)) ||
+        (e = dmalloc(x, &x->Zf2, n2)) || (e = dmalloc(x, &x->Wf, n2))) {
       g_create_error = x->err;
       free_all(x); delete x; return e;
     }
-    const size_t nbz = size_t(x->nb);
-    cudaFuncSetAttribute(k_pc_form_S, cudaFuncAttributeMaxDynamicSharedMemorySize, int(nbz * nbz * sizeof(double)));
-    cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int((nbz * nbz + nbz) * sizeof(double) + nbz * sizeof(int)));
+    if (solver->pc != HBPC_PC_NONE && (e = pc_alloc_f(x)) != HBPC_OK) {
+      g_create_error = x->err;
+      free_all(x); delete x; return e;
+    }
   }
-  if ((e = dmalloc(x, &x->small, nsmall)) || (e = dmalloc(x, &x->partial, size_t(prows) * (m + 3))) ||
+  if ((e = dmalloc(x, &x->small, nsmall)) || (e = dmalloc(x, &x->partial, size_t(prows) * (2 * m + 4))) ||
       (e = dmalloc(x, &x->ticket, 1)) || (e = dmalloc(x, &x->st, 1))) {
     g_create_error = x->err;
     free_all(x); delete x; return e;
@@ -774,11 +1190,16 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
   K.vscale = q; q += m + 3;
   K.nrmW = q; q += m + 3;
   K.nrmS = q; q += m + 3;
-  K.hc = q; q += m + 3;
+  K.hc = q; q += 2 * (m + 3);
   x->c12 = q; q += 4;
   x->dxn = q; q += 4;
   x->zn = q; q += 4;
   K.st = x->st; K.partial = x->partial; K.ticket = x->ticket; K.nblocks = x->nblocks;
+  // the FP32 basis shares the small device arrays and the iteration state
+  x->Kf.V = x->Vf; x->Kf.ld = K.ld; x->Kf.n2 = K.n2; x->Kf.half = K.half; x->Kf.m = K.m;
+  x->Kf.H = K.H; x->Kf.cs = K.cs; x->Kf.sn = K.sn; x->Kf.g = K.g; x->Kf.vscale = K.vscale;
+  x->Kf.nrmW = K.nrmW; x->Kf.nrmS = K.nrmS; x->Kf.hc = K.hc; x->Kf.y = K.y; x->Kf.st = K.st;
+  x->Kf.partial = K.partial; x->Kf.ticket = K.ticket; x->Kf.nblocks = K.nblocks;
   cudaError_t ce = cudaMemsetAsync(x->small, 0, nsmall * sizeof(double), x->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(x->ticket, 0, sizeof(unsigned), x->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(x->st, 0, sizeof(GmresState), x->stream);
@@ -912,7 +1333,7 @@ hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const doub
 hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
                          const double* in, double* out) {
   if (!ctx || !X || !in || !out) return HBPC_ERR_INVALID_ARG;
-  if (ctx->sol.pc != HBPC_PC_BJEXT) return fail(ctx, HBPC_ERR_INVALID_ARG, "context has no preconditioner");
+  if (ctx->sol.pc == HBPC_PC_NONE) return fail(ctx, HBPC_ERR_INVALID_ARG, "context has no preconditioner");
   const long long n = ctx->ndof;
   const size_t n2 = size_t(2 * n);
   const double dt = ctx->sol.dt;
@@ -952,6 +1373,176 @@ hbpc_status hbpc_reset_stats(hbpc_ctx* ctx) {
   ctx->stats = hbpc_stats{};
   ctx->stats.t = t;
   return HBPC_OK;
+}
+
+hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  if (pc != HBPC_PC_NONE && pc != HBPC_PC_BJEXT && pc != HBPC_PC_LEARNED)
+    return fail(ctx, HBPC_ERR_INVALID_ARG, "unknown preconditioner");
+  if (pc != HBPC_PC_NONE) {
+    if (ctx->nb > kMaxPcBlock)
+      return fail(ctx, HBPC_ERR_UNSUPPORTED, "block n_var (N+1)^dim exceeds the supported size");
+    hbpc_status s;
+    if ((s = pc_alloc(ctx)) != HBPC_OK) return s;
+    if (ctx->sol.precision == HBPC_PREC_MIXED && (s = pc_alloc_f(ctx)) != HBPC_OK) return s;
+    if (pc == HBPC_PC_LEARNED && (s = lp_alloc(ctx)) != HBPC_OK) return s;
+  }
+  ctx->sol.pc = pc;
+  ctx->pc_built = false;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_pc_model_info(hbpc_ctx* ctx, int* d_in_padded, int* hidden, int* d_out_padded,
+                               long long* n_params) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  if (ctx->nb > kMaxPcBlock) return fail(ctx, HBPC_ERR_UNSUPPORTED, "block too large for the learned preconditioner");
+  const int din = ctx->nb + 2, dinp = ((din + 15) / 16) * 16;
+  const int doutp = ((ctx->nb * ctx->nb + 7) / 8) * 8, H = kMlpHidden;
+  if (d_in_padded) *d_in_padded = dinp;
+  if (hidden) *hidden = H;
+  if (d_out_padded) *d_out_padded = doutp;
+  if (n_params) *n_params = (long long)H * dinp + H + (long long)H * H + H + (long long)doutp * H + doutp + 2LL * dinp;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double out_scale) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  hbpc_status s;
+  if ((s = pc_alloc(ctx)) != HBPC_OK || (s = lp_alloc(ctx)) != HBPC_OK) return s;
+  auto& L = ctx->lp;
+  std::vector<float> h(L.np, 0.0f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<float> nd(0.0f, 1.0f);
+  const size_t H = size_t(L.H);
+  const float s1 = 1.0f / std::sqrt(float(L.din)), s2 = 1.0f / std::sqrt(float(H));
+  for (size_t r = 0; r < H; ++r)
+    for (int c = 0; c < L.din; ++c) h[L.oW1 + r * L.dinp + c] = s1 * nd(rng);
+  for (size_t i = 0; i < H * H; ++i) h[L.oW2 + i] = s2 * nd(rng);
+  for (int r = 0; r < L.dout; ++r)
+    for (size_t c = 0; c < H; ++c) h[L.oW3 + size_t(r) * H + c] = float(out_scale) * s2 * nd(rng);
+  for (int k = 0; k < L.dinp; ++k) h[L.np_train + L.dinp + k] = 1.0f;   // sd = 1, mu = 0
+  HBPC_CK(ctx, cudaMemcpy(L.P, h.data(), L.np * sizeof(float), cudaMemcpyHostToDevice));
+  HBPC_CK(ctx, cudaMemset(L.Mo, 0, L.np * sizeof(float)));
+  HBPC_CK(ctx, cudaMemset(L.Ve, 0, L.np * sizeof(float)));
+  L.adam_t = 0;
+  L.stats = false;
+  if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
+  return sync(ctx, "pc_model_init");
+}
+
+hbpc_status hbpc_pc_model_get(hbpc_ctx* ctx, float* params) {
+  if (!ctx || !params || !ctx->lp.alloc) return HBPC_ERR_INVALID_ARG;
+  HBPC_CK(ctx, cudaMemcpyAsync(params, ctx->lp.P, ctx->lp.np * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx, "pc_model_get");
+}
+
+hbpc_status hbpc_pc_model_set(hbpc_ctx* ctx, const float* params) {
+  if (!ctx || !params) return HBPC_ERR_INVALID_ARG;
+  hbpc_status s;
+  if ((s = pc_alloc(ctx)) != HBPC_OK || (s = lp_alloc(ctx)) != HBPC_OK) return s;
+  HBPC_CK(ctx, cudaMemcpyAsync(ctx->lp.P, params, ctx->lp.np * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->lp.stats = true;   // the standardisation comes with the parameters
+  if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
+  return sync(ctx, "pc_model_set");
+}
+
+hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int B, int P, const float* F, const float* J, const float* c12,
+                              const float* X, double* loss, float* grads) {
+  if (!ctx || !F || !J || !c12 || !X || B < 8 || B % 8 || P < 1 || P > 16) return HBPC_ERR_INVALID_ARG;
+  if (!ctx->lp.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
+  hbpc_status s;
+  if ((s = lp_alloc_train(ctx, B, P)) != HBPC_OK) return s;
+  auto& L = ctx->lp;
+  const size_t nf = size_t(B) * L.dinp;
+  std::vector<float> ftmp(F, F + nf);
+  float* dF = nullptr;
+  HBPC_CK(ctx, cudaMalloc(&dF, nf * sizeof(float)));
+  cudaMemcpy(dF, ftmp.data(), nf * sizeof(float), cudaMemcpyHostToDevice);
+  k_f32_to_bf16<<<grid_for(nf), 256, 0, ctx->stream>>>(dF, L.Fb, nf);
+  HBPC_CK(ctx, cudaMemcpyAsync(L.Jb, J, size_t(B) * L.dout * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  HBPC_CK(ctx, cudaMemcpyAsync(L.cb, c12, size_t(B) * 2 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  HBPC_CK(ctx, cudaMemcpyAsync(L.Xb, X, size_t(B) * P * L.nb * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  double l = 0.0;
+  s = lp_loss_grad(ctx, B, P, &l);
+  cudaFree(dF);
+  if (s != HBPC_OK) return s;
+  if (loss) *loss = l;
+  if (grads) {
+    HBPC_CK(ctx, cudaMemcpyAsync(grads, L.G, L.np_train * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    std::fill(grads + L.np_train, grads + L.np, 0.0f);
+  }
+  return sync(ctx, "pc_loss_grad");
+}
+
+hbpc_status hbpc_pc_collect(hbpc_ctx* ctx, int samples_per_newton, int capacity) {
+  if (!ctx || samples_per_newton < 0 || capacity < 0) return HBPC_ERR_INVALID_ARG;
+  hbpc_status s;
+  if ((s = pc_alloc(ctx)) != HBPC_OK || (s = lp_alloc(ctx)) != HBPC_OK) return s;
+  auto& L = ctx->lp;
+  if (samples_per_newton > 0 && capacity > 0 && capacity != L.cap) {
+    cudaFree(L.featbuf); cudaFree(L.Jbuf); cudaFree(L.cbuf);
+    L.featbuf = L.Jbuf = L.cbuf = nullptr;
+    if ((s = dalloc_any(ctx, &L.featbuf, size_t(capacity) * L.din)) ||
+        (s = dalloc_any(ctx, &L.Jbuf, size_t(capacity) * L.dout)) ||
+        (s = dalloc_any(ctx, &L.cbuf, size_t(capacity) * 2)))
+      return s;
+    L.cap = capacity; L.count = 0; L.next = 0;
+  }
+  if (samples_per_newton > 0 && L.cap == 0) return fail(ctx, HBPC_ERR_INVALID_ARG, "capacity must be > 0");
+  L.per_newton = samples_per_newton;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int iters, int batch, int probes, double lr, unsigned long long seed,
+                          double* loss_first, double* loss_last) {
+  if (!ctx || iters < 1 || batch < 8 || batch % 8 || probes < 1 || probes > 16 || !(lr > 0.0))
+    return HBPC_ERR_INVALID_ARG;
+  auto& L = ctx->lp;
+  if (!L.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
+  if (L.count < batch) return fail(ctx, HBPC_ERR_INVALID_ARG, "replay buffer holds fewer samples than a batch");
+  hbpc_status s;
+  if ((s = lp_alloc_train(ctx, batch, probes)) != HBPC_OK) return s;
+  if (!L.stats) {   // feature standardisation from the replay buffer
+    std::vector<float> f(size_t(L.count) * L.din);
+    HBPC_CK(ctx, cudaMemcpy(f.data(), L.featbuf, f.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    std::vector<float> mu(L.dinp, 0.0f), sd(L.dinp, 1.0f);
+    for (int k = 0; k < L.din; ++k) {
+      double m = 0.0, q = 0.0;
+      for (int i = 0; i < L.count; ++i) m += f[size_t(i) * L.din + k];
+      m /= L.count;
+      for (int i = 0; i < L.count; ++i) { const double d = f[size_t(i) * L.din + k] - m; q += d * d; }
+      const double sdv = std::sqrt(q / L.count);
+      mu[k] = float(m);
+      sd[k] = sdv > 1e-6 * (std::fabs(m) + 1e-30) && sdv > 0.0 ? float(sdv) : 1.0f;
+    }
+    HBPC_CK(ctx, cudaMemcpy(L.mu, mu.data(), L.dinp * sizeof(float), cudaMemcpyHostToDevice));
+    HBPC_CK(ctx, cudaMemcpy(L.sd, sd.data(), L.dinp * sizeof(float), cudaMemcpyHostToDevice));
+    L.stats = true;
+  }
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int it = 0; it < iters; ++it) {
+    const unsigned long long sd = seed * 1000003ull + unsigned(it);
+    HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_rand_idx<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(L.idx, batch, L.count, sd));
+    HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1,
+             k_mlp_gather<<<batch, 128, 0, ctx->stream>>>(L.featbuf, L.Jbuf, L.cbuf, L.idx, batch, L.din, L.dinp, L.nb,
+                                                           L.mu, L.sd, L.Fb, L.Jb, L.cb));
+    const size_t nx = size_t(batch) * probes * L.nb;
+    HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_rademacher<<<grid_for(nx), 256, 0, ctx->stream>>>(L.Xb, nx, sd + 17));
+    HBPC_LAUNCH_CK(ctx, "pc_train sample");
+    double l = 0.0;
+    const bool want = (it == 0 && loss_first) || (it == iters - 1 && loss_last);
+    if ((s = lp_loss_grad(ctx, batch, probes, want ? &l : nullptr)) != HBPC_OK) return s;
+    if (it == 0 && loss_first) *loss_first = l;
+    if (it == iters - 1 && loss_last) *loss_last = l;
+    L.adam_t += 1;
+    const float bc1 = 1.0f - std::pow(b1, float(L.adam_t)), bc2 = 1.0f - std::pow(b2, float(L.adam_t));
+    HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1,
+             k_adam<<<grid_for(L.np_train), 256, 0, ctx->stream>>>(L.P, L.G, L.Mo, L.Ve, L.np_train, float(lr), b1, b2, eps, bc1, bc2));
+    HBPC_LAUNCH_CK(ctx, "k_adam");
+    if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
+  }
+  ctx->pc_built = false;
+  return sync(ctx, "pc_train");
 }
 
 hbpc_status hbpc_profile_enable(hbpc_ctx* ctx, int enable) {
@@ -1028,7 +1619,7 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   k_set2<<<1, 32, 0, stream>>>(c12, c1, c2);
   // R1(W), R2(W, S) at X into the scratch (G goes to `out`, overwritten below)
   x.ops.residual(x.prm, X, X + n, X, c1, c2, out, out + n, scr + kNoAllocR1, scr + kNoAllocR2, stream);
-  k_norms<<<K.nblocks, kVecThreads, 0, stream>>>(dX, n2, size_t(n), K, nullptr);
+  k_norms<double, double><<<K.nblocks, kVecThreads, 0, stream>>>(dX, n2, size_t(n), K, nullptr);
   k_sqrt_norms<<<1, 32, 0, stream>>>(K.st, nrm);
   if ((st = ck(cudaGetLastError(), "noalloc launches")) != HBPC_OK) return st;
   JvInput z{};

@@ -15,7 +15,8 @@ struct Basis1D {
 };
 bool basis_1d(int N, int family, Basis1D& b);
 
-struct JvInput;
+template <typename S> struct JvInputT;
+using JvInput = JvInputT<double>;
 struct JvCoef;
 
 // Launchers of the element operator for one (law, dim, P, node family).
@@ -31,6 +32,9 @@ struct OpsTable {
   void (*jv_fd)(const DGParams<double>&, const double* W, const double* S, const double* r1,
                 const double* r2, const JvInput&, const JvCoef&, cudaStream_t) = nullptr;
   void (*jv_linear)(const DGParams<double>&, const JvInput&, const JvCoef&, cudaStream_t) = nullptr;
+  // mixed precision: FP32 Jacobian-vector product at the FP32 copy (Wf, Sf)
+  void (*jv_f)(const DGParams<float>&, const JvInputT<float>&, const JvCoef&, const float* Wf,
+               const float* Sf, cudaStream_t) = nullptr;
   // BJ_ext element Jacobians J_i (Sec. 3.2.3), column-major n_b x n_b per element
   void (*pc_assemble)(const DGParams<double>&, const double* W, double* J, cudaStream_t) = nullptr;
 };

@@ -12,12 +12,13 @@ namespace hbpc {
 
 // Squared norms (total, first `half`, rest) of x; result in st->nrm and, if
 // given, written to out3.  One launch of nblocks blocks.
-__global__ void k_norms(const double* x, size_t n, size_t half, Krylov K, double* out3) {
+template <typename S, typename V>
+__global__ void k_norms(const V* x, size_t n, size_t half, KrylovT<S> K, double* out3) {
   size_t lo, hi;
   chunk_range(n, K.nblocks, lo, hi);
   double a = 0.0, b = 0.0;
   for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const double v = x[i];
+    const double v = double(x[i]);
     if (i < half) a += v * v; else b += v * v;
   }
   __shared__ double s[2][kVecWarps];
@@ -45,7 +46,8 @@ __global__ void k_norms(const double* x, size_t n, size_t half, Krylov K, double
 // Start a cycle from V_0 (already holding the unscaled residual r) with
 // v_0 = sign * V_0 / ||V_0||.  Norms come from st->nrm (k_norms on V_0).
 // first != 0 also fixes the target tol * ||rhs|| and clears the counters.
-__global__ void k_cycle_init(Krylov K, double sign, double tol, int first, int max_its) {
+template <typename S>
+__global__ void k_cycle_init(KrylovT<S> K, double sign, double tol, int first, int max_its) {
   if (threadIdx.x != 0) return;
   GmresState* st = K.st;
   const double beta = sqrt(st->nrm[0]);
@@ -63,157 +65,303 @@ __global__ void k_cycle_init(Krylov K, double sign, double tol, int first, int m
   st->done = (st->converged || st->its >= st->max_its) ? 1 : 0;
 }
 
-// Column finalisation (one thread): H(j+1, j) = ||q||, rotations, residual,
-// stopping decision.  q = V_{j+1}; nq2/nw2/ns2 are its squared norms.
-__device__ __forceinline__ void finalize_column(const Krylov& K, double nq2, double nw2, double ns2) {
+// Column finalisation: H(j+1, j) = ||q||, rotations, residual, stopping
+// decision.  q = V_{j+1}; nq2/nw2/ns2 are its squared norms.  Called by every
+// thread of the last block: the column and the rotations are staged in shared
+// memory in parallel, thread 0 applies the rotations there (the chain is
+// sequential by nature) and the column is written back in parallel.
+template <typename S>
+__device__ __forceinline__ void finalize_column(const KrylovT<S>& K, double nq2, double nw2, double ns2,
+                                                double* sh /* >= 3 (m+2) doubles */) {
   GmresState* st = K.st;
   const int j = st->j, ldh = K.m + 1;
   double* Hj = K.H + size_t(j) * ldh;
-  const double hnext = sqrt(nq2);
-  Hj[j + 1] = hnext;
-  K.vscale[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
-  K.nrmW[j + 1] = sqrt(nw2);
-  K.nrmS[j + 1] = sqrt(ns2);
-  for (int i = 0; i < j; ++i) {           // previous rotations
-    const double t = K.cs[i] * Hj[i] + K.sn[i] * Hj[i + 1];
-    Hj[i + 1] = -K.sn[i] * Hj[i] + K.cs[i] * Hj[i + 1];
-    Hj[i] = t;
+  double* hcol = sh;
+  double* scs = sh + (K.m + 2);
+  double* ssn = scs + (K.m + 2);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    hcol[i] = Hj[i];
+    scs[i] = K.cs[i];
+    ssn[i] = K.sn[i];
   }
-  const double den = hypot(Hj[j], Hj[j + 1]);
-  const double c = den > 0.0 ? Hj[j] / den : 1.0, s = den > 0.0 ? Hj[j + 1] / den : 0.0;
-  K.cs[j] = c; K.sn[j] = s;
-  Hj[j] = den; Hj[j + 1] = 0.0;
-  K.g[j + 1] = -s * K.g[j];
-  K.g[j] = c * K.g[j];
-  st->resid = fabs(K.g[j + 1]);
-  st->its += 1;
-  st->j = j + 1;
-  st->reorth = 0;
-  const bool ok = st->resid <= st->target;
-  const bool brk = !(hnext > 0.0);
-  st->breakdown = brk ? 1 : 0;
-  st->converged = (ok || brk) ? 1 : 0;
-  st->done = (ok || brk || st->j >= K.m || st->its >= st->max_its) ? 1 : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hnext = sqrt(nq2);
+    hcol[j + 1] = hnext;
+    K.vscale[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+    K.nrmW[j + 1] = sqrt(nw2);
+    K.nrmS[j + 1] = sqrt(ns2);
+    for (int i = 0; i < j; ++i) {           // previous rotations
+      const double t = scs[i] * hcol[i] + ssn[i] * hcol[i + 1];
+      hcol[i + 1] = -ssn[i] * hcol[i] + scs[i] * hcol[i + 1];
+      hcol[i] = t;
+    }
+    const double den = hypot(hcol[j], hcol[j + 1]);
+    const double c = den > 0.0 ? hcol[j] / den : 1.0, s = den > 0.0 ? hcol[j + 1] / den : 0.0;
+    K.cs[j] = c; K.sn[j] = s;
+    hcol[j] = den; hcol[j + 1] = 0.0;
+    const double gj = K.g[j];
+    K.g[j + 1] = -s * gj;
+    K.g[j] = c * gj;
+    st->resid = fabs(K.g[j + 1]);
+    st->its += 1;
+    st->j = j + 1;
+    st->reorth = 0;
+    const bool ok = st->resid <= st->target;
+    const bool brk = !(hnext > 0.0);
+    st->breakdown = brk ? 1 : 0;
+    st->converged = (ok || brk) ? 1 : 0;
+    st->done = (ok || brk || st->j >= K.m || st->its >= st->max_its) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hj[i] = hcol[i];
 }
 
-// Dot products d_i = <q, V_i>, i = 0..j, with q = V_{j+1}; h_i = vscale_i d_i is
-// stored in K.hc.  pass 0: first Gram-Schmidt pass, also ||q||^2 -> st->qq.
-// pass 1: re-orthogonalisation pass, runs only if st->reorth.
-__global__ void __launch_bounds__(kVecThreads) k_arnoldi_dot(Krylov K, int pass) {
-  GmresState* st = K.st;
-  if (st->done || (pass == 1 && !st->reorth)) return;
-  const int j = st->j;
-  const int cnt = j + 1 + (pass == 0 ? 1 : 0);     // + ||q||^2 in the first pass
-  const double* q = K.V + size_t(j + 1) * K.ld;
-  __shared__ double sq[kSub];
-  extern __shared__ double s_acc[];                 // cnt accumulators
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_acc[i] = 0.0;
-  size_t lo, hi;
-  chunk_range(K.n2, K.nblocks, lo, hi);
+// ---------------------------------------------------------------------------
+// Classical Gram-Schmidt with re-orthogonalisation (CGS2) in three passes and a
+// finalisation, without single-block tails: every pass writes per-block partial
+// sums; the next pass's blocks all reduce them redundantly in their prologue
+// (same data, same order, hence the same value in every block).
+//   pass A  k_cgs_dot:        P0[b][i]  = <q, V_i>_b                         i <= j
+//   pass B  k_cgs_update_dot: h_i = vscale_i sum_b P0[b][i];  q1 = q - sum h_i v_i;
+//                             P2[b][i]  = <q1, V_i>_b
+//   pass C  k_cgs_update:     c_i = vscale_i sum_b P2[b][i];  q2 = q1 - sum c_i v_i;
+//                             P3[b]     = (|q2_W|^2, |q2_S|^2)_b
+//   k_cgs_finalize (1 block): H(:, j) = h + c, H(j+1, j) = |q2|, Givens rotation,
+//                             residual and stopping decision.
+// Partial layout: row b of K.partial holds P0 / P2 in columns [0, m+1) and
+// [m+1, 2m+2), P3 in the two columns after.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cgs_stride(int m) { return 2 * (m + 1) + 2; }
+
+// Block-redundant reduction of partial columns [col0, col0 + cnt) into shared
+// s_out (times vscale when given).  Warp w handles columns w, w + 8, ..
+__device__ __forceinline__ void cgs_reduce_cols(const double* partial, int stride, int nb, int col0, int cnt,
+                                                const double* vscale, double* s_out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (size_t c0 = lo; c0 < hi; c0 += kSub) {
-    const int len = int(hi - c0 < size_t(kSub) ? hi - c0 : size_t(kSub));
-    __syncthreads();
-    for (int t = threadIdx.x; t < len; t += blockDim.x) sq[t] = q[c0 + t];
-    __syncthreads();
-    for (int i = warp; i < cnt; i += kVecWarps) {
-      const double* Vi = (i <= j) ? K.V + size_t(i) * K.ld + c0 : nullptr;
-      double a = 0.0;
-      if (Vi) { for (int t = lane; t < len; t += 32) a += sq[t] * Vi[t]; }
-      else { for (int t = lane; t < len; t += 32) a += sq[t] * sq[t]; }
-      a = warp_sum(a);
-      if (lane == 0) s_acc[i] += a;
-    }
-  }
-  __syncthreads();
-  const int stride = K.m + 3;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) K.partial[size_t(blockIdx.x) * stride + i] = s_acc[i];
-  if (!last_block(K.ticket, K.nblocks)) return;
-  reduce_partials(K.partial, stride, K.nblocks, cnt, K.hc);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i <= j; ++i) K.hc[i] *= K.vscale[i];
-    if (pass == 0) {
-      st->qq = K.hc[j + 1];
-      double* Hj = K.H + size_t(j) * (K.m + 1);
-      for (int i = 0; i <= j; ++i) Hj[i] = K.hc[i];
-    } else {
-      double* Hj = K.H + size_t(j) * (K.m + 1);
-      for (int i = 0; i <= j; ++i) Hj[i] += K.hc[i];
-    }
+  for (int c = warp; c < cnt; c += kVecWarps) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(partial + size_t(b) * stride + col0 + c);
+    s = warp_sum(s);
+    if (lane == 0) s_out[c] = vscale ? s * vscale[c] : s;
   }
 }
 
-// q <- q - sum_i hc_i vscale_i V_i and the squared norms of q.  pass 0: decide
-// on re-orthogonalisation (||q_new|| < ||q_old|| / sqrt(2)) or finalise the
-// column; pass 1 (only if st->reorth): finalise.
-__global__ void __launch_bounds__(kVecThreads) k_arnoldi_update(Krylov K, int pass) {
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_dot(KrylovT<S> K) {
+  using A = typename AccOf<S>::type;
   GmresState* st = K.st;
-  if (st->done || (pass == 1 && !st->reorth)) return;
-  const int j = st->j;
-  double* q = K.V + size_t(j + 1) * K.ld;
-  extern __shared__ double s_coef[];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) s_coef[i] = K.hc[i] * K.vscale[i];
+  if (st->done) return;
+  const int j = st->j, cnt = j + 1;
+  const S* q = K.V + size_t(j + 1) * K.ld;
+  extern __shared__ double s_red[];                 // [cnt][kVecWarps]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
   __syncthreads();
-  size_t lo, hi;
-  chunk_range(K.n2, K.nblocks, lo, hi);
-  double aw = 0.0, as = 0.0;
-  for (size_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-    double x = q[t];
-    for (int i = 0; i <= j; ++i) x -= s_coef[i] * K.V[size_t(i) * K.ld + t];
-    q[t] = x;
-    if (t < K.half) aw += x * x; else as += x * x;
-  }
-  __shared__ double s[2][kVecWarps];
-  aw = warp_sum(aw); as = warp_sum(as);
-  if ((threadIdx.x & 31) == 0) { s[0][threadIdx.x >> 5] = aw; s[1][threadIdx.x >> 5] = as; }
-  __syncthreads();
-  const int stride = K.m + 3;
-  if (threadIdx.x == 0) {
-    double ta = 0.0, tb = 0.0;
-    for (int w = 0; w < kVecWarps; ++w) { ta += s[0][w]; tb += s[1][w]; }
-    K.partial[size_t(blockIdx.x) * stride + 0] = ta;
-    K.partial[size_t(blockIdx.x) * stride + 1] = tb;
-  }
-  if (!last_block(K.ticket, K.nblocks)) return;
-  __shared__ double r[2];
-  reduce_partials(K.partial, stride, K.nblocks, 2, r);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const double nq2 = r[0] + r[1];
-    if (pass == 0 && nq2 < 0.5 * st->qq) {
-      st->reorth = 1;
-    } else {
-      finalize_column(K, nq2, r[0], r[1]);
+  const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kTile + threadIdx.x;
+    A qv[kRows];
+    bool in[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      in[r] = row < K.n2;
+      qv[r] = in[r] ? A(q[row]) : A(0);
     }
+    int i = 0;
+    for (; i + 1 < cnt; i += 2) {
+      const S* V0 = K.V + size_t(i) * K.ld;
+      const S* V1 = V0 + K.ld;
+      A a0 = A(0), a1 = A(0);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        if (in[r]) { a0 += qv[r] * A(V0[row]); a1 += qv[r] * A(V1[row]); }
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      if (lane == 0) { s_red[i * kVecWarps + warp] += double(a0); s_red[(i + 1) * kVecWarps + warp] += double(a1); }
+    }
+    if (i < cnt) {
+      const S* V0 = K.V + size_t(i) * K.ld;
+      A a0 = A(0);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        if (in[r]) a0 += qv[r] * A(V0[row]);
+      }
+      a0 = warp_sum(a0);
+      if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
+    }
+  }
+  __syncthreads();
+  const int stride = cgs_stride(K.m);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) s += s_red[i * kVecWarps + w];
+    K.partial[size_t(blockIdx.x) * stride + i] = s;
   }
 }
 
-// y = R^-1 g over the j columns of the finished cycle; y_i *= vscale_i.
-__global__ void k_solve_y(Krylov K) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int jn = K.st->j, ldh = K.m + 1;
-  for (int i = jn - 1; i >= 0; --i) {
-    double t = K.g[i];
-    for (int k = i + 1; k < jn; ++k) t -= K.H[size_t(k) * ldh + i] * K.y[k];
-    const double d = K.H[size_t(i) * ldh + i];
-    K.y[i] = d != 0.0 ? t / d : 0.0;
+// q <- q - sum_i c_i vscale_i V_i for the rows of this block, with c from the
+// partials at column col0 (prologue), then either the next pass's dot partials
+// (with_dot) or the squared norms of the result.
+template <typename S, bool WITH_DOT>
+__device__ __forceinline__ void cgs_update_body(const KrylovT<S>& K, int j, int col_in, int col_out,
+                                                double* s_h, double* s_red) {
+  using A = typename AccOf<S>::type;
+  const int cnt = j + 1;
+  const int stride = cgs_stride(K.m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  S* q = K.V + size_t(j + 1) * K.ld;
+  // prologue: this pass's coefficients, reduced redundantly by every block
+  cgs_reduce_cols(K.partial, stride, K.nblocks, col_in, cnt, K.vscale, s_h);
+  if (WITH_DOT)
+    for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
+  __syncthreads();
+  A aw = A(0), as = A(0);
+  const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kTile + threadIdx.x;
+    A x[kRows];
+    bool in[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      in[r] = row < K.n2;
+      x[r] = in[r] ? A(q[row]) : A(0);
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const S* Vi = K.V + size_t(i) * K.ld;
+      const A c = A(s_h[i] * K.vscale[i]);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        if (in[r]) x[r] -= c * A(Vi[row]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      if (in[r]) {
+        q[row] = S(x[r]);
+        if (row < K.half) aw += x[r] * x[r]; else as += x[r] * x[r];
+      }
+    }
+    if (WITH_DOT) {
+      for (int i = 0; i < cnt; ++i) {
+        const S* Vi = K.V + size_t(i) * K.ld;
+        A a0 = A(0);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const size_t row = base + size_t(r) * kVecThreads;
+          if (in[r]) a0 += x[r] * A(Vi[row]);
+        }
+        a0 = warp_sum(a0);
+        if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
+      }
+    }
   }
-  for (int i = 0; i < jn; ++i) K.y[i] *= K.vscale[i];
+  if (WITH_DOT) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      double s = 0.0;
+      for (int w = 0; w < kVecWarps; ++w) s += s_red[i * kVecWarps + w];
+      K.partial[size_t(blockIdx.x) * stride + col_out + i] = s;
+    }
+  } else {
+    __shared__ double s2[2][kVecWarps];
+    aw = warp_sum(aw); as = warp_sum(as);
+    if (lane == 0) { s2[0][warp] = double(aw); s2[1][warp] = double(as); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ta = 0.0, tb = 0.0;
+      for (int w = 0; w < kVecWarps; ++w) { ta += s2[0][w]; tb += s2[1][w]; }
+      K.partial[size_t(blockIdx.x) * stride + col_out] = ta;
+      K.partial[size_t(blockIdx.x) * stride + col_out + 1] = tb;
+    }
+  }
+  if (blockIdx.x == 0)   // the coefficients of this pass for the Hessenberg column
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) (WITH_DOT ? K.hc : K.hc + (K.m + 2))[i] = s_h[i];
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_update_dot(KrylovT<S> K) {
+  if (K.st->done) return;
+  extern __shared__ double sm[];          // s_h [m+1] | s_red [(m+1) kVecWarps]
+  cgs_update_body<S, true>(K, K.st->j, 0, K.m + 1, sm, sm + (K.m + 1));
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_update(KrylovT<S> K) {
+  if (K.st->done) return;
+  extern __shared__ double sm[];
+  cgs_update_body<S, false>(K, K.st->j, K.m + 1, 2 * (K.m + 1), sm, nullptr);
+}
+
+// One block: norms of q2, Hessenberg column h + c, rotation, stopping decision.
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
+  GmresState* st = K.st;
+  if (st->done) return;
+  const int j = st->j;
+  extern __shared__ double sm[];          // >= 3 (m+2) doubles
+  __shared__ double nrm[2];
+  cgs_reduce_cols(K.partial, cgs_stride(K.m), K.nblocks, 2 * (K.m + 1), 2, nullptr, nrm);
+  double* Hj = K.H + size_t(j) * (K.m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = K.hc[i] + K.hc[(K.m + 2) + i];
+  __syncthreads();
+  finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
+}
+
+// y = R^-1 g over the j columns of the finished cycle; y_i *= vscale_i.  One
+// warp, column-oriented back substitution (lane k owns y_k).
+template <typename S>
+__global__ void k_solve_y(KrylovT<S> K) {
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int jn = K.st->j, ldh = K.m + 1, lane = threadIdx.x;
+  for (int i = lane; i < jn; i += 32) K.y[i] = K.g[i];
+  __syncwarp();
+  for (int i = jn - 1; i >= 0; --i) {
+    const double d = K.H[size_t(i) * ldh + i];
+    const double yi = d != 0.0 ? K.y[i] / d : 0.0;
+    __syncwarp();
+    if (lane == 0) K.y[i] = yi;
+    for (int k2 = lane; k2 < i; k2 += 32) K.y[k2] -= K.H[size_t(i) * ldh + k2] * yi;
+    __syncwarp();
+  }
+  for (int i = lane; i < jn; i += 32) K.y[i] *= K.vscale[i];
 }
 
 // x (+)= sum_i y_i V_i over the cycle's columns (accumulate != 0 adds to x).
-__global__ void __launch_bounds__(kVecThreads) k_combine(Krylov K, double* x, int accumulate) {
+template <typename S, typename X>
+__global__ void __launch_bounds__(kVecThreads) k_combine(KrylovT<S> K, X* x, int accumulate) {
+  using A = typename AccOf<S>::type;
   const int jn = K.st->j;
   extern __shared__ double s_y[];
   for (int i = threadIdx.x; i < jn; i += blockDim.x) s_y[i] = K.y[i];
   __syncthreads();
-  size_t lo, hi;
-  chunk_range(K.n2, K.nblocks, lo, hi);
-  for (size_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
-    double a = accumulate ? x[t] : 0.0;
-    for (int i = 0; i < jn; ++i) a += s_y[i] * K.V[size_t(i) * K.ld + t];
-    x[t] = a;
+  const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kTile + threadIdx.x;
+    A a[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) a[r] = A(0);
+    for (int i = 0; i < jn; ++i) {
+      const S* Vi = K.V + size_t(i) * K.ld;
+      const A y = A(s_y[i]);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        if (row < K.n2) a[r] += y * A(Vi[row]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      if (row < K.n2) x[row] = accumulate ? X(double(x[row]) + double(a[r])) : X(a[r]);
+    }
   }
 }
 

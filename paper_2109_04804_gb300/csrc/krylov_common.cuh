@@ -12,7 +12,8 @@ namespace hbpc {
 
 constexpr int kVecThreads = 256;
 constexpr int kVecWarps = kVecThreads / 32;
-constexpr int kSub = 2048;          // staged sub-chunk of q (doubles)
+constexpr int kRows = 4;            // rows of a vector per thread and tile
+constexpr int kTile = kVecThreads * kRows;
 
 struct GmresState {
   int j;             // columns built in this cycle
@@ -31,22 +32,32 @@ struct GmresState {
 
 // All pointers are device memory.  V holds m+1 columns of length n2 at stride
 // ld; column i represents v_i = vscale[i] * V_i.  nrmW/nrmS are the norms of the
-// unscaled halves of V_i (first `half` entries are W, the rest sigma).
-struct Krylov {
-  double* V; size_t ld, n2, half;
+// unscaled halves of V_i (first `half` entries are W, the rest sigma).  S is the
+// storage type of the basis (double, or float in the mixed-precision mode).
+template <typename S>
+struct KrylovT {
+  S* V; size_t ld, n2, half;
   int m;
   double* H;        // (m+1) x m, column-major, ldh = m+1
   double* cs; double* sn; double* g;
   double* vscale; double* nrmW; double* nrmS;
-  double* hc;       // dot results of the current pass, length m+2
+  double* hc;       // Gram-Schmidt coefficients of the two passes: [0, m+2) and [m+2, 2m+4)
   double* y;        // solution coefficients (times vscale), length m
   GmresState* st;
   double* partial;  // nblocks x (m+3)
   unsigned* ticket;
   int nblocks;
 };
+using Krylov = KrylovT<double>;
 
-__device__ __forceinline__ double warp_sum(double x) {
+// Accumulation type of per-thread sums over a basis of storage type S: FP64
+// for an FP64 basis; FP32 for an FP32 basis (the per-warp sums are then added
+// in FP64 across warps and blocks).
+template <typename S> struct AccOf { using type = double; };
+template <> struct AccOf<float> { using type = float; };
+
+template <typename A>
+__device__ __forceinline__ A warp_sum(A x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;

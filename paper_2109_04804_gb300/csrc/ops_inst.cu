@@ -19,12 +19,12 @@
 namespace hbpc {
 namespace {
 
-template <int LAW, int DIM, int P, bool LGL, class Job>
-void launch(const Job& job, const DGParams<double>& prm, cudaStream_t s) {
+template <int LAW, int DIM, int P, bool LGL, class Job, typename V = double>
+void launch(const Job& job, const DGParams<typename BaseOf<V>::type>& prm, cudaStream_t s) {
   using KS = KernelShape<LAW, DIM, P>;
   using Gm = Geo<DIM, P>;
-  constexpr size_t smem = KS::template smem_bytes<double>();
-  auto kern = &dg_operator_kernel<LAW, DIM, P, LGL, double, Job>;
+  constexpr size_t smem = KS::template smem_bytes<V, typename BaseOf<V>::type>();
+  auto kern = &dg_operator_kernel<LAW, DIM, P, LGL, V, Job>;
   if (smem > 48 * 1024) {
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -68,12 +68,25 @@ struct Inst {
     JobJvLinear<NV, NN> j{z, c};
     launch<LAW, DIM, P, LGL>(j, p, s);
   }
+  // mixed precision: FP32 Jacobian-vector product (Eq. 24 for a linear flux,
+  // analytic dual-number form of Eq. 18 otherwise)
+  static void jv_f(const DGParams<float>& p, const JvInputT<float>& z, const JvCoef& c, const float* Wf,
+                   const float* Sf, cudaStream_t s) {
+    if constexpr (LINEAR) {
+      JobJvLinear<NV, NN, float, float> j{z, c};
+      launch<LAW, DIM, P, LGL, JobJvLinear<NV, NN, float, float>, float>(j, p, s);
+    } else {
+      JobJvMixed<NV, NN> j{Wf, Sf, z, c};
+      launch<LAW, DIM, P, LGL, JobJvMixed<NV, NN>, Dual<float>>(j, p, s);
+    }
+  }
   static void pc_assemble(const DGParams<double>& p, const double* W, double* J, cudaStream_t s) {
     k_pc_assemble<LAW, DIM, P, LGL><<<p.nE, 128, 0, s>>>(W, J, p);
   }
   static void fill(OpsTable& t) {
     t.nv = NV;
     t.pc_assemble = &pc_assemble;
+    t.jv_f = &jv_f;
     t.r1 = &r1;
     t.r2 = &r2;
     t.residual = &residual;

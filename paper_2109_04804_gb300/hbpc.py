@@ -25,7 +25,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NO_CONVERGENCE, ERR_NONFINITE, ERR_T
 LAW_ADVECTION, LAW_BURGERS, LAW_EULER = 0, 1, 2
 FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
-PC_NONE, PC_BJEXT = 0, 1
+PC_NONE, PC_BJEXT, PC_LEARNED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")
 
@@ -82,6 +82,14 @@ _SIGS = {
     "hbpc_eval_Jv": (_I, [_CTX, _D, _D, _P, _P, _P]),
     "hbpc_newton_solve": (_I, [_CTX, _P, _D, _D, _P, _P, _P]),
     "hbpc_eval_pc": (_I, [_CTX, _D, _D, _P, _P, _P]),
+    "hbpc_set_pc": (_I, [_CTX, _I]),
+    "hbpc_pc_model_info": (_I, [_CTX, _P, _P, _P, _P]),
+    "hbpc_pc_model_init": (_I, [_CTX, ctypes.c_ulonglong, _D]),
+    "hbpc_pc_model_get": (_I, [_CTX, _P]),
+    "hbpc_pc_model_set": (_I, [_CTX, _P]),
+    "hbpc_pc_loss_grad": (_I, [_CTX, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "hbpc_pc_collect": (_I, [_CTX, _I, _I]),
+    "hbpc_pc_train": (_I, [_CTX, _I, _I, _I, _D, ctypes.c_ulonglong, _P, _P]),
     "hbpc_fp64_fma_peak": (_I, [ctypes.POINTER(ctypes.c_double)]),
     "hbpc_eval_Jv_noalloc": (_I, [ctypes.POINTER(Mesh), _I, _I, ctypes.POINTER(Physics), _D, _D, _D,
                                   _P, _P, _P, _P]),
@@ -243,6 +251,46 @@ class Context:
     def eval_pc(self, alpha1, alpha2, X, inp, out):
         self._c(_lib.hbpc_eval_pc(self._ctx, alpha1, alpha2, _ptr(X), _ptr(inp), _ptr(out)))
         return out
+
+    # -- learned block preconditioner ---------------------------------------
+    def set_pc(self, pc):
+        self._c(_lib.hbpc_set_pc(self._ctx, pc))
+
+    def pc_model_info(self):
+        v = [ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0)]
+        self._c(_lib.hbpc_pc_model_info(self._ctx, *[ctypes.addressof(t) for t in v]))
+        return {"d_in_padded": v[0].value, "hidden": v[1].value, "d_out_padded": v[2].value,
+                "n_params": v[3].value}
+
+    def pc_model_init(self, seed=0, out_scale=1e-2):
+        self._c(_lib.hbpc_pc_model_init(self._ctx, seed, out_scale))
+
+    def pc_model_get(self):
+        out = np.zeros(self.pc_model_info()["n_params"], dtype=np.float32)
+        self._c(_lib.hbpc_pc_model_get(self._ctx, out.ctypes.data))
+        return out
+
+    def pc_model_set(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        self._c(_lib.hbpc_pc_model_set(self._ctx, params.ctypes.data))
+
+    def pc_loss_grad(self, F, J, c12, X):
+        F, J, c12, X = (np.ascontiguousarray(a, dtype=np.float32) for a in (F, J, c12, X))
+        B, P = X.shape[0], X.shape[1]
+        loss = ctypes.c_double(0.0)
+        grads = np.zeros(self.pc_model_info()["n_params"], dtype=np.float32)
+        self._c(_lib.hbpc_pc_loss_grad(self._ctx, B, P, F.ctypes.data, J.ctypes.data, c12.ctypes.data,
+                                       X.ctypes.data, ctypes.addressof(loss), grads.ctypes.data))
+        return loss.value, grads
+
+    def pc_collect(self, samples_per_newton, capacity):
+        self._c(_lib.hbpc_pc_collect(self._ctx, samples_per_newton, capacity))
+
+    def pc_train(self, iters, batch=256, probes=4, lr=1e-3, seed=0):
+        l0, l1 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._c(_lib.hbpc_pc_train(self._ctx, iters, batch, probes, lr, seed, ctypes.addressof(l0),
+                                   ctypes.addressof(l1)))
+        return l0.value, l1.value
 
     def newton_solve(self, b, alpha1, alpha2, W0, W_out, S_out=None):
         self._c(_lib.hbpc_newton_solve(self._ctx, _ptr(b), alpha1, alpha2, _ptr(W0), _ptr(W_out),

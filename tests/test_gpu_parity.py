@@ -274,3 +274,68 @@ def test_c2_full_size_step_vs_exact(hb):
     ref = exact.fourier_hbpc(disc, inputs.sine_product(disc.node_coords()), dt, 8, 4, 1)
     assert rel(w, ref) <= 1e-11
     ctx.close()
+
+
+@pytest.mark.parametrize("law,dim,flux,pc", [
+    (laws.ADVECTION, 2, "lf", "bjext"), (laws.ADVECTION, 2, "lf", "none"),
+    (laws.EULER, 2, "rusanov", "bjext"), (laws.EULER, 2, "lf", "none"),
+    (laws.BURGERS, 2, "rusanov", "bjext"), (laws.EULER, 3, "rusanov", "none")])
+def test_mixed_precision_stage_solve_matches_oracle(hb, law, dim, flux, pc):
+    """Mixed precision (FP32 Krylov loop with the analytic dual-number Jv, FP64
+    Newton residual and update) reaches the same root as the FP64 oracle: the
+    answer is fixed by G(X) = 0, which is evaluated in FP64."""
+    N, dt = 3, 0.05
+    n = {2: (5, 4), 3: (3, 2, 2)}[dim]
+    ctx, disc = pair(hb, law, dim, N, n, LOBATTO, flux, lo=(-1, -1, -1), hi=(1, 1, 1), dt=dt,
+                     tol_newton_rel=1e-13, tol_newton_abs=1e-13, tol_gmres_rel=1e-5, gmres_restart=80,
+                     precision=hb.PREC_MIXED, pc=hb.PC_BJEXT if pc == "bjext" else hb.PC_NONE)
+    X = disc.node_coords()
+    if law == laws.EULER:
+        W0 = inputs.density_wave(X)
+    elif law == laws.BURGERS:
+        W0 = 0.5 + 0.25 * inputs.sine_product(X, k=1.0)
+    else:
+        W0 = inputs.sine_product(X, k=1.0)
+    b = W0 + dt * 0.1 * np.cos(3.0 * W0)
+    opts = newton.NewtonOptions(tol_rel=1e-13, tol_abs=1e-13, gmres_tol=1e-9, restart=80,
+                                jv="linear" if disc.ph.linear else "fd")
+    Wr, Sr, st = newton.newton_solve(disc, b, 1.0, 1.0, dt, W0, opts)
+    Wd = torch.empty(disc.ndof, dtype=torch.float64, device="cuda")
+    ctx.newton_solve(dev(b), 1.0, 1.0, dev(W0), Wd)
+    assert rel(host(Wd), Wr.ravel()) <= 1e-11
+    ctx.close()
+
+
+def test_mixed_precision_c2_full_size_step_vs_exact(hb):
+    """The bench workload in mixed precision: one HBPC(8,4) step of the 64x64,
+    N=5 advection problem equals the exact per-Fourier-mode result."""
+    dt = 1.0 / 96
+    ctx, disc = pair(hb, laws.ADVECTION, 2, 5, (64, 64), a=(1.0, 1.0), q=8, kmax=4, dt=dt,
+                     tol_newton_rel=1e-12, tol_newton_abs=1e-12, tol_gmres_rel=1e-5, gmres_restart=100,
+                     pc=hb.PC_BJEXT, precision=hb.PREC_MIXED)
+    w0 = inputs.sine_product(ctx.node_coords())
+    ctx.set_state(w0)
+    ctx.step(1)
+    w = ctx.get_state()
+    ref = exact.fourier_hbpc(disc, inputs.sine_product(disc.node_coords()), dt, 8, 4, 1)
+    assert rel(w, ref) <= 1e-11
+    ctx.close()
+
+
+@pytest.mark.parametrize("flux", ["lf", "rusanov"])
+def test_mixed_precision_euler_steps_vs_oracle(hb, flux):
+    dt = 0.04
+    ctx, disc = pair(hb, laws.EULER, 2, 3, (4, 3), LOBATTO, flux, lo=(-1, -1), hi=(1, 1), q=6, kmax=1,
+                     dt=dt, tol_newton_rel=1e-13, tol_newton_abs=1e-13, tol_gmres_rel=1e-5,
+                     gmres_restart=100, precision=hb.PREC_MIXED, pc=hb.PC_BJEXT)
+    w0 = inputs.density_wave(ctx.node_coords())
+    ctx.set_state(w0)
+    ctx.step(2)
+    w = ctx.get_state()
+    opts = newton.NewtonOptions(tol_rel=1e-13, tol_abs=1e-13, gmres_tol=1e-8, restart=100, jv="fd")
+    adv = ohbpc.dg_stepper(disc, dt, 6, 1, opts)
+    ref = inputs.density_wave(disc.node_coords())
+    for _ in range(2):
+        ref = adv(ref)
+    assert rel(w, ref) <= 1e-11
+    ctx.close()

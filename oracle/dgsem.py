@@ -20,6 +20,11 @@ Traces are the solution polynomial evaluated at the edge (Sec. 3.1.1).
 R^(2)(w, sigma) is the same operator with F^m(w) replaced by (dF^m/dw) sigma and
 the face flux f~* of Sec. 3.1.2, which uses the traces of w and sigma and the
 same dissipation coefficient (evaluated at w, not differentiated).
+
+Scalar laws may carry a viscous term nu Laplace(w), discretised with the BR2
+lifting of Sec. 5.1.1 (``viscous``).  Its flux F^v = nu d does not depend on w,
+so it adds nu L_h(w) to R^(1) and, by Eq. 31-33 with dF^v/dw = 0 and
+eta = d_t, nu L_h(sigma) to R^(2).
 """
 import numpy as np
 
@@ -149,6 +154,87 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False):
                 fminus = -(0.5 * laws.flux_jvp(wm, sm, m, ph) - kappa_prev * sm)
         surf = disc._lift(fplus, b.lhat_p, na) + disc._lift(fminus, b.lhat_m, na)
         out = out - (2.0 / disc.mesh.h[m]) * (vol + surf)
+    res = disc.from_grid(out)
+    if ph.nu != 0.0:
+        res = res + viscous(disc, w if mode == "R1" else sigma, frozen_neighbor and mode == "R2")
+    return res
+
+
+def br2_traces(disc, U, m, frozen_neighbor=False):
+    """Face quantities of the BR2 lifting along direction m (Sec. 5.1.1) for a
+    scalar grid array U: the common value u* of Eq. 30 at the element's + and
+    - faces and the face gradients d^L, d^R of the face-local liftings.
+
+    The face-local lifting of a face f (strong form; equal to the weak form on
+    the collocated nodes) keeps only f's surface term, scaled by eta:
+        d_f = (2/h) D u + eta r_f,   (r_f, phi) = <(u* - u) n, phi>_f,
+    evaluated at f.  On the element's + face (n = +e_m) this gives
+    d = (2/h)[u'(+1) + eta c_p (u* - u(+1))], on its - face (n = -e_m)
+    d = (2/h)[u'(-1) + eta c_m (u(-1) - u*)], with c_pm = sum_i l_i(pm1)^2 / omega_i.
+    frozen_neighbor: the neighbours' values are taken as zero.
+    Returns (ustar_p, ustar_m, fp_grad, fm_grad): u* at the + and - faces and the
+    averages 1/2 (d^L + d^R) at the + and - faces (gradient along +e_m)."""
+    ph, b = disc.ph, disc.basis
+    ea, na = disc.elem_axis(m), disc.node_axis(m)
+    H = 2.0 / disc.mesh.h[m]
+    eta = ph.eta_br2
+    c_p = float(np.sum(b.l_p * b.lhat_p))
+    c_m = float(np.sum(b.l_m * b.lhat_m))
+    dl_p = b.l_p @ b.D      # l_j'(+1): derivative of the interpolant at +1
+    dl_m = b.l_m @ b.D
+    up = Disc._trace(b.l_p, U, na)
+    um = Disc._trace(b.l_m, U, na)
+    gp = H * Disc._trace(dl_p, U, na)
+    gm = H * Disc._trace(dl_m, U, na)
+    if not frozen_neighbor:
+        uR = np.roll(um, -1, axis=ea)          # right neighbour's - trace
+        gR = np.roll(gm, -1, axis=ea)
+        ustar_p = 0.5 * (up + uR)
+        dL = gp + H * eta * c_p * (ustar_p - up)
+        dR = gR + H * eta * c_m * (uR - ustar_p)
+        fp_grad = 0.5 * (dL + dR)
+        ustar_m = np.roll(ustar_p, 1, axis=ea)
+        fm_grad = np.roll(fp_grad, 1, axis=ea)
+    else:
+        ustar_p = 0.5 * up
+        fp_grad = 0.5 * ((gp + H * eta * c_p * (ustar_p - up)) + H * eta * c_m * (0.0 - ustar_p))
+        ustar_m = 0.5 * um
+        fm_grad = 0.5 * (H * eta * c_p * (ustar_m - 0.0) + (gm + H * eta * c_m * (um - ustar_m)))
+    return ustar_p, ustar_m, fp_grad, fm_grad
+
+
+def br2_gradient(disc, u, m, frozen_neighbor=False):
+    """The lifted gradient component d^m of Eq. 29 (weak form, collocated):
+    d_i = (2/h_m) [ sum_j Dhat[i, j] u_j + lhat_i(+1) u*_+ - lhat_i(-1) u*_- ]."""
+    b = disc.basis
+    U = disc.to_grid(u)
+    na = disc.node_axis(m)
+    ustar_p, ustar_m, _, _ = br2_traces(disc, U, m, frozen_neighbor)
+    H = 2.0 / disc.mesh.h[m]
+    d = H * (Disc._apply(b.Dhat, U, na) + disc._lift(ustar_p, b.lhat_p, na)
+             - disc._lift(ustar_m, b.lhat_m, na))
+    return disc.from_grid(d)
+
+
+def viscous(disc, u, frozen_neighbor=False):
+    """nu L_h(u): the viscous part of the weak form of Sec. 5.1.1 for the flux
+    F^v = nu d (scalar law, constant viscosity), with the central viscous face
+    flux of Eq. 30:
+        out_i = sum_m (2/h_m) [ sum_j Dhat[i, j] nu d^m_j
+                                + lhat_i(+1) F^v*_+ - lhat_i(-1) F^v*_- ],
+    F^v*_pm = nu 1/2 (d^L + d^R) at the element's + and - faces (along +e_m).
+    frozen_neighbor: neighbours' values zero (the element-diagonal block)."""
+    ph, b = disc.ph, disc.basis
+    U = disc.to_grid(u)
+    out = np.zeros(U.shape, dtype=U.dtype)
+    for m in range(disc.d):
+        na = disc.node_axis(m)
+        H = 2.0 / disc.mesh.h[m]
+        _, _, fp_grad, fm_grad = br2_traces(disc, U, m, frozen_neighbor)
+        d = disc.to_grid(br2_gradient(disc, u, m, frozen_neighbor))
+        out = out + H * (Disc._apply(b.Dhat, ph.nu * d, na)
+                         + disc._lift(ph.nu * fp_grad, b.lhat_p, na)
+                         - disc._lift(ph.nu * fm_grad, b.lhat_m, na))
     return disc.from_grid(out)
 
 

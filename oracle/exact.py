@@ -7,7 +7,8 @@ Test infrastructure only (see ``oracle/__init__``).
   linear_matrix     the dense matrix of R1 for a linear flux.
   dense_stepper     Algorithm 1 for a linear flux with every stage solved by a
                     dense direct solve of (I - a1 dt L + a2 dt^2/2 L^2) W = b.
-  fourier_*         for linear advection on a uniform periodic Cartesian mesh
+  fourier_*         for linear advection (with or without the BR2 viscous
+                    term) on a uniform periodic Cartesian mesh
                     R1 is block circulant; per Fourier mode it is a small
                     matrix L(theta) (Kronecker sum of the 1-D symbols), so one
                     HBPC step and the time-exact semi-discrete solution
@@ -80,10 +81,14 @@ def dense_stepper(L, dt, q, kmax):
     return lambda w: hbpc.step(w, dt, q, kmax, R1, R2, solve)
 
 
-def _blocks_1d(N, h, a, family=LOBATTO, flux="lf", lf_scale=1.0):
-    """Neighbour blocks A_{-1}, A_0, A_{+1} of the 1-D advection operator,
-    (R1 w)_e = sum_d A_d w_{e+d}, read off the oracle's R1 on 3 elements."""
-    ph = laws.Physics(laws.ADVECTION, 1, a=(a,), flux=flux, lf_scale=lf_scale)
+def _blocks_1d(N, h, a, family=LOBATTO, flux="lf", lf_scale=1.0, nu=0.0, eta_br2=2.0):
+    """Neighbour blocks A_{-1}, A_0, A_{+1} of the 1-D advection(-diffusion)
+    operator, (R1 w)_e = sum_d A_d w_{e+d}, read off the oracle's R1 on 3
+    elements.  The BR2 viscous term acts along each direction separately, so the
+    d-dimensional symbol is the Kronecker sum of these 1-D ones when eta_br2 is
+    the d-dimensional value."""
+    ph = laws.Physics(laws.ADVECTION, 1, a=(a,), flux=flux, lf_scale=lf_scale, nu=nu,
+                      eta_br2=eta_br2)
     disc = dgsem.Disc(dgsem.Mesh(1, (3,), (0.0,), (3 * h,)), N, ph, family)
     p = N + 1
     A = {d: np.zeros((p, p)) for d in (-1, 0, 1)}
@@ -104,7 +109,8 @@ def fourier_symbols(disc):
     p, d = disc.p, disc.d
     sym1 = []
     for m in range(d):
-        A = _blocks_1d(N, mesh.h[m], ph.a[m], disc.basis.family, ph.flux, ph.lf_scale)
+        A = _blocks_1d(N, mesh.h[m], ph.a[m], disc.basis.family, ph.flux, ph.lf_scale,
+                       ph.nu, ph.eta_br2)
         th = 2.0 * np.pi * np.arange(mesh.n[m]) / mesh.n[m]
         S = (A[-1][None] * np.exp(-1j * th)[:, None, None] + A[0][None]
              + A[1][None] * np.exp(1j * th)[:, None, None])

@@ -6,8 +6,9 @@ Arrays carry the conserved variables on axis 0; every function is written with
 plain arithmetic so that it also runs on complex arrays (complex-step tests).
 
   advection   F^m = a_m w                                   (Sec. 4.1.1)
-  burgers     F^m = w^2 / 2 in every direction (inviscid part of the Burgers
-              workload; the viscous part is not in the oracle)
+  burgers     F^m = w^2 / 2 in every direction (the inviscid part; the viscous
+              term nu Laplace(u) of the viscous Burgers workload is the BR2
+              operator of ``dgsem.viscous``)
   euler       Eq. 21: F^m = (rho v_m, rho v_m v + p/eps^2 e_m, v_m (E + p)),
               p = (gamma - 1)(E - eps^2/2 rho |v|^2)
 
@@ -26,7 +27,7 @@ EULER = "euler"
 
 class Physics:
     def __init__(self, law, dim, a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0,
-                 flux="lf", lf_scale=1.0):
+                 flux="lf", lf_scale=1.0, nu=0.0, eta_br2=None):
         self.law = law
         self.dim = dim
         self.a = np.array(a[:dim], dtype=np.float64)
@@ -36,6 +37,13 @@ class Physics:
         self.lf_scale = lf_scale    # multiplies the paper's lambda in "lf"
         self.nv = {ADVECTION: 1, BURGERS: 1, EULER: dim + 2}[law]
         self.linear = law == ADVECTION
+        # viscous term nu Laplace(w) (scalar laws only) with the BR2 lifting of
+        # Sec. 6.1; eta_br2 scales the face-local liftings (the paper leaves its
+        # value open; default: the number of faces of an element, 2 dim)
+        if nu != 0.0 and law == EULER:
+            raise ValueError("the viscous term is implemented for scalar laws only")
+        self.nu = float(nu)
+        self.eta_br2 = float(2 * dim if eta_br2 is None else eta_br2)
 
 
 def _re(x):

@@ -8,6 +8,7 @@ the absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5, FP64.  One bench step = one
 stage solves).  Metric: DOF-timesteps/s = n_dof x steps / device seconds.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+  python bench.py --workload burgers_batch   (256 viscous Burgers instances, below)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path has no data-path collective), value = sum over ranks / max time.
@@ -311,6 +312,120 @@ def cpu_baseline(dt, budget_s=20.0):
                       % (st.gmres_its, t1, solves_per_step)}
 
 
+BATCH = dict(n_inst=256, n_range=(16, 96), N_range=(3, 7), nu_range=(1e-3, 1e-2), seed=2024,
+             q=6, kmax=2, cfl_finest=2.0, tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3,
+             gmres_restart=30, gmres_max_iter=3000, newton_max_iter=30)
+
+
+def batch_instances(n_inst):
+    """The seeded instance list of the batched viscous Burgers workload: square
+    periodic meshes n x n on [0, 1]^2 with n uniform in 16..96, N uniform in
+    3..7, nu uniform in [1e-3, 1e-2]; initial data: 8 random Fourier modes,
+    max |u0| = 1 (seed per instance)."""
+    rng = np.random.default_rng(BATCH["seed"])
+    out = []
+    for i in range(n_inst):
+        n = int(rng.integers(BATCH["n_range"][0], BATCH["n_range"][1] + 1))
+        N = int(rng.integers(BATCH["N_range"][0], BATCH["N_range"][1] + 1))
+        nu = float(rng.uniform(*BATCH["nu_range"]))
+        out.append(((n, n), N, nu, 1000 + i))
+    return out
+
+
+def run_batch(args):
+    """Batched workload: independent 2-D viscous Burgers instances
+    u_t + div(u^2/2 (1, 1)) = nu Laplace(u) (BR2, Sec. 5.1.1), one batch
+    (hbpc_batch_*) advanced by HBPC(6, 2) with a common dt (CFL 2 on the finest
+    instance), mixed precision (FP32 Krylov and R1 linearisation, FP64 Newton
+    residual), BJ_ext.  One step = one HBPC step of every instance."""
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    inst = batch_instances(args.instances)
+    h_min = min(1.0 / n[0] / (N + 1) for n, N, _, _ in inst)
+    dt = BATCH["cfl_finest"] * h_min        # max |u0| = 1
+    b = hbpc.Batch(2, [(n, (0.0, 0.0), (1.0, 1.0)) for n, _, _, _ in inst], [N for _, N, _, _ in inst],
+                   nus=[nu for _, _, nu, _ in inst], law=hbpc.LAW_BURGERS, flux=hbpc.FLUX_RUSANOV,
+                   q=BATCH["q"], kmax=BATCH["kmax"], dt=dt, tol_newton_rel=BATCH["tol_newton_rel"],
+                   tol_newton_abs=BATCH["tol_newton_abs"], tol_gmres_rel=BATCH["tol_gmres_rel"],
+                   gmres_restart=BATCH["gmres_restart"], gmres_max_iter=BATCH["gmres_max_iter"],
+                   newton_max_iter=BATCH["newton_max_iter"], pc=hbpc.PC_BJEXT, precision=hbpc.PREC_MIXED)
+    ndof = 0
+    w0s = []
+    for i, (n, N, nu, seed) in enumerate(inst):
+        w0 = inputs.burgers_fourier(b.node_coords(i), seed=seed)
+        b.set_state(i, w0)
+        w0s.append(w0)
+        ndof += w0.size
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    st0 = b.stats()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(1)                 # every group's stream synchronised before it returns
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+    clk = clocks.stop()
+    st = b.stats()
+    t_sec = total
+    if world > 1:
+        tt = torch.tensor([t_sec], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sec = float(tt.item())
+    value = ndof * args.steps * world / t_sec
+    d = {k: st[k] - st0[k] for k in ("newton_its", "gmres_its", "r1_evals", "r2_evals", "launches")}
+    # e2e: host buffers copied in and out of every instance every step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for i in range(len(inst)):
+            b.set_state(i, w0s[i])
+        b.step(1)
+        for i in range(len(inst)):
+            b.get_state(i)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    groups = b.groups()
+    b.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov", "data": "synthetic",
+            "config": {"workload": "batched_viscous_burgers_%d_instances_HBPC(6,2)_BR2_BJext" % len(inst),
+                       "instances": len(inst), "groups_by_N": groups, "total_dof": ndof,
+                       "mesh": "n x n periodic [0,1]^2, n uniform in 16..96", "N": "uniform in 3..7",
+                       "nu": "uniform in [1e-3, 1e-2]", "dt": dt, "cfl_finest": BATCH["cfl_finest"],
+                       "flux": "Rusanov", "eps_newton": BATCH["tol_newton_rel"], "eps_gmres": BATCH["tol_gmres_rel"],
+                       "gmres_restart": BATCH["gmres_restart"], "precision": "mixed",
+                       "timing": "host clock between device synchronisations (groups run on their own streams)",
+                       "l2_between_steps": "flushed (256 MB write) between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "r1_evals_per_s": (d["r1_evals"] + d["r2_evals"]) / t_sec,
+            "gmres_its_per_step": d["gmres_its"] / args.steps, "newton_its_per_step": d["newton_its"] / args.steps,
+            "gpu_launches": int(d["launches"]),
+            "e2e": {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -346,10 +461,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
+    ap.add_argument("--workload", default="advection2d", choices=["advection2d", "burgers_batch"],
+                    help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
+                         "viscous Burgers instances")
+    ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
     args = ap.parse_args()
     PRECISION[0] = args.precision
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "burgers_batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -84,6 +84,15 @@ typedef struct {
   double eps;       /* reference Mach number eps (Euler, Eq. 21); also enters
                        eps_FD of Eq. 23 for every law (use 1 for advection) */
   double lf_scale;  /* multiplies the global-LF lambda; 1 = Eq. 13 as printed */
+  double nu;        /* viscosity of a term nu Laplace(w) added to a scalar law
+                       (advection or Burgers), discretised by the BR2 lifting of
+                       Sec. 5.1.1 (Eqs. 26-30 with F^v = nu grad w, central
+                       face fluxes, face-local liftings).  0 = inviscid; < 0 is
+                       HBPC_ERR_INVALID_ARG; > 0 with Euler is
+                       HBPC_ERR_UNSUPPORTED. */
+  double eta_br2;   /* BR2 stabilisation factor of the face-local liftings (the
+                       paper leaves its value open); <= 0 selects 2 * dim, the
+                       number of faces of an element */
 } hbpc_physics;
 
 typedef struct {
@@ -177,9 +186,12 @@ hbpc_status hbpc_eval_G(hbpc_ctx* ctx, const double* b, double alpha1, double al
 hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
                          const double* dX, double* out);
 
-/* BJ_ext preconditioner (Sec. 3.2.3) built at the state W of X = (W, S) for the
- * stage coefficients alpha1, alpha2, applied to `in`: out = P^-1 in.  Needs a
- * context created with pc = HBPC_PC_BJEXT.  X, in, out: device, 2 n_dof FP64. */
+/* Block preconditioner (BJ_ext of Sec. 3.2.3, or the learned blocks) built at
+ * the state W of X = (W, S) for the stage coefficients alpha1, alpha2, applied
+ * to `in`: out = P^-1 in.  Needs a context with pc != HBPC_PC_NONE.  In the
+ * MIXED precision mode the blocks S_e, their inverses and the apply are FP32
+ * (what the Krylov loop uses); in FP64 mode everything is FP64.
+ * X, in, out: device, 2 n_dof FP64. */
 hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
                          const double* in, double* out);
 
@@ -205,24 +217,39 @@ hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc);
  * standardisation mu (d_in_padded) and sd (d_in_padded): f = (raw - mu) / sd. */
 hbpc_status hbpc_pc_model_info(hbpc_ctx* ctx, int* d_in_padded, int* hidden, int* d_out_padded,
                                long long* n_params);
+/* Random weights (normal, scaled by 1/sqrt(fan-in); W3 further by out_scale),
+ * zero biases, Adam state cleared.  If the replay buffer holds exact block
+ * inverses (data collected with BJ_ext), b3 starts at their mean minus I, so
+ * the untrained network returns the mean block inverse. */
 hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double out_scale);
 hbpc_status hbpc_pc_model_get(hbpc_ctx* ctx, float* params);        /* host output */
 hbpc_status hbpc_pc_model_set(hbpc_ctx* ctx, const float* params);  /* host input */
-/* Probe loss L = sum_{s,p} |M~_s S_s x_p - x_p|^2 / (B P), S = I - c1 J + c2 J^2,
- * and its gradient for given inputs (host): F (B x d_in_padded, already
- * standardised), J (B x n_b x n_b column-major), c12 (B x 2), X (B x P x n_b).
- * B a multiple of 8, 1 <= P <= 16; grads (host, n_params) may be NULL. */
-hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int B, int P, const float* F, const float* J, const float* c12,
-                              const float* X, double* loss, float* grads);
+/* Training losses of the learned preconditioner.
+ * PROBE: L = sum_{s,p} |M~_s S_s x_p - x_p|^2 / (B P), S = I - c1 J + c2 J^2,
+ *        with Rademacher probes x_p (what a preconditioner should achieve).
+ * INVERSE: L = sum_s |M~_s - T_s|_F^2 / B against the exact block inverses
+ *        T_s = S_s^-1 computed by the BJ_ext path during data collection (a
+ *        well-conditioned regression, used to start training). */
+typedef enum { HBPC_PC_LOSS_PROBE = 0, HBPC_PC_LOSS_INVERSE = 1 } hbpc_pc_loss;
+/* Loss and gradient for given inputs (host): F (B x d_in_padded, already
+ * standardised), J (B x n_b x n_b column-major: the element Jacobian for
+ * PROBE, the target inverse for INVERSE), c12 (B x 2), X (B x P x n_b probes;
+ * PROBE only, may be NULL for INVERSE).  B a multiple of 8, 1 <= P <= 16;
+ * grads (host, n_params) may be NULL. */
+hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int loss_kind, int B, int P, const float* F, const float* J,
+                              const float* c12, const float* X, double* loss, float* grads);
 /* Sample `samples_per_newton` elements' (features, J_e, c1, c2) at every Newton
  * iteration that builds a block preconditioner into a replay buffer of
- * `capacity` samples (0 stops sampling). */
+ * `capacity` samples (0 stops sampling); with the BJ_ext preconditioner the
+ * exact block inverses S_e^-1 are stored too (targets of the INVERSE loss). */
 hbpc_status hbpc_pc_collect(hbpc_ctx* ctx, int samples_per_newton, int capacity);
-/* `iters` Adam steps on random batches of the replay buffer with `probes`
- * Rademacher probes per sample (SplitMix64 of the seed); first and last batch
- * losses to loss_first / loss_last (may be NULL). */
-hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int iters, int batch, int probes, double lr, unsigned long long seed,
-                          double* loss_first, double* loss_last);
+/* `iters` Adam steps of the given loss (hbpc_pc_loss) on random batches of the
+ * replay buffer, `probes` Rademacher probes per sample for PROBE (SplitMix64 of
+ * the seed); first and last batch losses to loss_first / loss_last (may be
+ * NULL).  INVERSE needs every buffered sample to have its target
+ * (HBPC_ERR_INVALID_ARG otherwise). */
+hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int loss_kind, int iters, int batch, int probes, double lr,
+                          unsigned long long seed, double* loss_first, double* loss_last);
 
 /* Per-launch device timing: while enabled, every kernel launch of the context
  * is bracketed by CUDA events on its stream (this adds a little host overhead;
@@ -260,6 +287,41 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
  * independent FMA chains on every SM, best of three, CUDA events).  Used as the
  * arithmetic roofline of the FP64 kernels.  Allocates and frees a small buffer. */
 hbpc_status hbpc_fp64_fma_peak(double* gflops);
+
+/* ---- Batches of independent instances (no counterpart in the paper) -----
+ * n_inst problems that share dim, law, flux, gamma, eps, lf_scale, a, eta_br2,
+ * the node family and the solver settings (HBPC(q, k_max), dt, tolerances,
+ * preconditioner NONE or BJEXT, precision), each with its own mesh (n, lo, hi),
+ * degree N[i] and viscosity phys[i].nu.  Instances with the same N form one
+ * group: one element numbering (each instance's elements contiguous, padded to
+ * the operator kernel's elements per block), so every kernel launch of the
+ * group covers all its instances; the Jacobian and the block preconditioner are
+ * block diagonal over instances.  Newton stops per instance (Sec. 3.2.1 tests
+ * applied to each instance's residual; converged instances are frozen), one
+ * GMRES per Newton iteration covers the group's active instances.  Groups run
+ * concurrently, each on its own stream driven by its own host thread. */
+typedef struct hbpc_batch hbpc_batch;
+hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* meshes, const int* N, int nodes,
+                              const hbpc_physics* phys, const hbpc_solver* solver);
+void hbpc_batch_destroy(hbpc_batch* b);                       /* accepts NULL */
+int hbpc_batch_groups(const hbpc_batch* b);                   /* number of distinct N */
+long long hbpc_batch_ndof(const hbpc_batch* b, int inst);     /* -1 for a bad index */
+/* State of instance `inst` (canonical layout of that instance alone); host
+ * memory unless on_device != 0. */
+hbpc_status hbpc_batch_set_state(hbpc_batch* b, int inst, const double* w, int on_device);
+hbpc_status hbpc_batch_get_state(hbpc_batch* b, int inst, double* w, int on_device);
+/* Node coordinates of instance `inst`, host x[dim][n_E][(N+1)^dim]. */
+hbpc_status hbpc_batch_node_coords(hbpc_batch* b, int inst, double* x);
+/* R1 (Eq. 12, with the viscous term) of the current state of inst's group,
+ * instance `inst`'s part copied to host r. */
+hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r);
+/* n_steps HBPC steps of every instance. */
+hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps);
+/* Counters summed over groups (steps, t: the maximum). */
+hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out);
+hbpc_status hbpc_batch_profile_enable(hbpc_batch* b, int enable);
+/* Message of the last failure of the batch (NULL: of the last failed create). */
+const char* hbpc_batch_last_error(const hbpc_batch* b);
 
 /* Message of the last failure on this context (static storage owned by the
  * context; "" if none).  Accepts NULL (returns the message of the last failed

@@ -9,7 +9,9 @@ inverse M~ = I + reshape(O) of the BJ_ext block S = I - c1 J + c2 J^2
 
     L = sum_samples sum_p || M~ u_p - x_p ||^2 / (n_samples n_probes),   u_p = S x_p,
 
-i.e. M~ S x_p should reproduce the probe x_p.
+i.e. M~ S x_p should reproduce the probe x_p, or, to start training, with the
+inverse regression L = sum_samples |M~ - S^-1|_F^2 / n_samples against exact
+block inverses.
 
 Network: two tanh hidden layers,
     z1 = W1 f + b1, h1 = tanh(z1), z2 = W2 h1 + b2, h2 = tanh(z2), O = W3 h2 + b3,
@@ -56,6 +58,15 @@ def probe_loss(O, U, X, nb):
     L = np.sum(R * R) / (B * P)
     dM = 2.0 * np.einsum("bpi,bpj->bij", R, U) / (B * P)
     return L, dM.reshape(B, nb * nb)
+
+
+def inverse_loss(O, T, nb):
+    """Regression of M~ on the exact block inverses T (B, nb, nb):
+    L = sum_s |M~_s - T_s|_F^2 / B and dL/dO (B, nb^2)."""
+    B = T.shape[0]
+    R = mtilde(O, nb) - T
+    L = np.sum(R * R) / B
+    return L, (2.0 * R / B).reshape(B, nb * nb)
 
 
 def backward(p, act, dO):

@@ -20,6 +20,8 @@ namespace hbpc {
 // u has, for every direction m, the volume entries Dvol[m][r_m][q_m] A^m(w_q)
 // along the line of q, and the face entries of the lifted numerical flux's
 // derivative with respect to the element's own trace (the neighbour is frozen).
+// A BR2 viscous term adds nu times its element-diagonal block along the line
+// (a constant table, the same for every element).
 template <int LAW, int DIM, int P, bool LGL>
 __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ W,
                                                      double* __restrict__ Jout,
@@ -33,10 +35,15 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
   for (int t = threadIdx.x; t < NB; t += blockDim.x) sw[t] = W[size_t(e) * NB + t];
   for (size_t t = threadIdx.x; t < size_t(NB) * NB; t += blockDim.x) J[t] = 0.0;
   __syncthreads();
+  // the instance of this element (batches): its mesh and scales; padding
+  // elements between instances keep J = 0
+  const InstGeo<double> geo = inst_geo(prm, e / Geo<DIM, P>::EPB);
+  const int el = e - geo.e0;
+  if (el >= geo.nE) return;
   int ec[3];
-  ec[0] = e % prm.n[0];
-  ec[1] = (e / prm.n[0]) % prm.n[1];
-  ec[2] = e / (prm.n[0] * prm.n[1]);
+  ec[0] = el % geo.n[0];
+  ec[1] = (el / geo.n[0]) % geo.n[1];
+  ec[2] = el / (geo.n[0] * geo.n[1]);
   for (int col = threadIdx.x; col < NB; col += blockDim.x) {
     const int u = col / NN, q = col - u * NN;
     double* Jc = J + size_t(col) * NB;
@@ -50,15 +57,24 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
       const int b0 = q - qi[m] * st;
       double a[NV];
       if constexpr (L::LINEAR) {
+        // a_m is folded into Dvol unless a viscous term is present
+        const double am = prm.visc ? prm.a[m] : 1.0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a[v] = eu[v];      // a_m is folded into Dvol
+        for (int v = 0; v < NV; ++v) a[v] = am * eu[v];
       } else {
         L::jvp(wq, eu, m, a, prm);
       }
+      const double hs = geo.hs[m];
       // volume: output node r = b0 + l*st receives Dvol[m][l][q_m] * a
       for (int l = 0; l < P; ++l)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Jc[v * NN + b0 + l * st] += prm.Dvol[m][l][qi[m]] * a[v];
+        for (int v = 0; v < NV; ++v) Jc[v * NN + b0 + l * st] += hs * prm.Dvol[m][l][qi[m]] * a[v];
+      // BR2 viscous term (scalar laws): its element-diagonal block along the line
+      // (a second-derivative operator: two factors 2/h)
+      if constexpr (NV == 1) {
+        if (prm.visc)
+          for (int l = 0; l < P; ++l) Jc[b0 + l * st] += geo.nu * hs * hs * prm.vloc[(m * P + l) * P + qi[m]];
+      }
       // faces: own traces at the - and + face of the line through q
       double Ap[NV];
       L::jvp(wq, eu, m, Ap, prm);   // dF^m/dw at w_q applied to e_u (used for Lobatto)
@@ -71,9 +87,9 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
         for (int v = 0; v < NV; ++v) { to[v] = 0.0; tn[v] = 0.0; }
         int nc[3] = {ec[0], ec[1], ec[2]};
         nc[m] += side ? 1 : -1;
-        if (nc[m] < 0) nc[m] += prm.n[m];
-        if (nc[m] >= prm.n[m]) nc[m] -= prm.n[m];
-        const int en = nc[0] + prm.n[0] * (nc[1] + prm.n[1] * nc[2]);
+        if (nc[m] < 0) nc[m] += geo.n[m];
+        if (nc[m] >= geo.n[m]) nc[m] -= geo.n[m];
+        const int en = geo.e0 + nc[0] + geo.n[0] * (nc[1] + geo.n[1] * nc[2]);
         for (int i = 0; i < P; ++i) {
           const double lo = side ? prm.lp[i] : prm.lm[i];
           const double ln = side ? prm.lm[i] : prm.lp[i];
@@ -101,7 +117,7 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
         // + face: f = 1/2 (F(t_o) + F(t_n)) + kap (t_o - t_n)      -> df/dt_o = A/2 + kap
         // - face: f = -(1/2 (F(t_n) + F(t_o)) + kap (t_n - t_o))  -> df/dt_o = -A/2 + kap
         for (int l = 0; l < P; ++l) {
-          const double lift = side ? prm.sp[m][l] : prm.sm[m][l];
+          const double lift = hs * (side ? prm.sp[m][l] : prm.sm[m][l]);
           if (lift == 0.0) continue;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {

@@ -7,23 +7,25 @@
 namespace hbpc {
 
 // S = I - c1 J + c2 J^2 for one element per block (J staged in shared memory),
-// written to `S` (same layout).  Dynamic shared memory: nb * nb doubles.
-__global__ void __launch_bounds__(256) k_pc_form_S(const double* __restrict__ Jall,
-                                                   double* __restrict__ Sall, int nb, int nE,
-                                                   const double* c12) {
+// written to `S` (same layout), in T (FP64, or FP32 for the mixed-precision
+// mode, where the blocks only precondition).  Dynamic shared memory: nb * nb T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T* __restrict__ Sall, int nb,
+                                                   int nE, const double* c12) {
   const int e = blockIdx.x;
   if (e >= nE) return;
-  extern __shared__ double sJ[];
-  const double* J = Jall + size_t(e) * nb * nb;
+  extern __shared__ __align__(16) unsigned char sJ_raw[];
+  T* sJ = reinterpret_cast<T*>(sJ_raw);
+  const T* J = Jall + size_t(e) * nb * nb;
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) sJ[t] = J[t];
   __syncthreads();
-  const double c1 = c12[0], c2 = c12[1];
-  double* S = Sall + size_t(e) * nb * nb;
+  const T c1 = T(c12[0]), c2 = T(c12[1]);
+  T* S = Sall + size_t(e) * nb * nb;
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
     const int c = t / nb, r = t - c * nb;          // entry (r, c)
-    double jj = 0.0;
+    T jj = T(0);
     for (int k = 0; k < nb; ++k) jj += sJ[k * nb + r] * sJ[c * nb + k];   // (J J)(r, c)
-    S[t] = (r == c ? 1.0 : 0.0) - c1 * sJ[t] + c2 * jj;
+    S[t] = (r == c ? T(1) : T(0)) - c1 * sJ[t] + c2 * jj;
   }
 }
 
@@ -31,40 +33,40 @@ __global__ void __launch_bounds__(256) k_pc_form_S(const double* __restrict__ Ja
 // elimination with partial (row) pivoting; the column exchanges implied by the
 // row pivots are undone at the end.  A zero pivot leaves the block unchanged and
 // sets *singular (the preconditioner is then skipped by the host).
-// Dynamic shared memory: (nb * nb + nb) doubles + nb ints.
-__global__ void __launch_bounds__(256) k_pc_invert(double* __restrict__ Mall, int nb, int nE,
-                                                   int* singular) {
+// Dynamic shared memory: (nb * nb + nb) T + nb ints.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pc_invert(T* __restrict__ Mall, int nb, int nE, int* singular) {
   const int e = blockIdx.x;
   if (e >= nE) return;
-  extern __shared__ double smem[];
-  double* A = smem;                  // column-major nb x nb
-  double* colk = A + nb * nb;        // copy of the pivot column
+  extern __shared__ __align__(16) unsigned char inv_raw[];
+  T* A = reinterpret_cast<T*>(inv_raw);   // column-major nb x nb
+  T* colk = A + nb * nb;                  // copy of the pivot column
   int* perm = reinterpret_cast<int*>(colk + nb);
   __shared__ int s_piv;
   __shared__ int s_bad;
-  double* M = Mall + size_t(e) * nb * nb;
+  T* M = Mall + size_t(e) * nb * nb;
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) A[t] = M[t];
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   for (int k = 0; k < nb; ++k) {
     // pivot: largest |A(i, k)|, i >= k (warp 0)
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      T best = T(-1);
       int bi = k;
       for (int i = k + threadIdx.x; i < nb; i += 32) {
-        const double a = fabs(A[k * nb + i]);
+        const T a = fabs(A[k * nb + i]);
         if (a > best) { best = a; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (threadIdx.x == 0) {
         s_piv = bi;
         perm[k] = bi;
-        if (!(best > 0.0)) s_bad = 1;
+        if (!(best > T(0))) s_bad = 1;
       }
     }
     __syncthreads();
@@ -72,23 +74,23 @@ __global__ void __launch_bounds__(256) k_pc_invert(double* __restrict__ Mall, in
     const int p = s_piv;
     if (p != k)
       for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-        const double t = A[c * nb + k];
+        const T t = A[c * nb + k];
         A[c * nb + k] = A[c * nb + p];
         A[c * nb + p] = t;
       }
     __syncthreads();
-    const double inv = 1.0 / A[k * nb + k];
+    const T inv = T(1) / A[k * nb + k];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) colk[i] = A[k * nb + i];
     __syncthreads();
     // row k scaled; column k becomes e_k scaled
-    for (int c = threadIdx.x; c < nb; c += blockDim.x) A[c * nb + k] = (c == k ? 1.0 : A[c * nb + k]) * inv;
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) A[c * nb + k] = (c == k ? T(1) : A[c * nb + k]) * inv;
     __syncthreads();
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
       const int c = t / nb, i = t - c * nb;
       if (i == k) continue;
-      const double f = colk[i];
-      const double rk = A[c * nb + k];
-      A[t] = (c == k ? 0.0 : A[t]) - f * rk;
+      const T f = colk[i];
+      const T rk = A[c * nb + k];
+      A[t] = (c == k ? T(0) : A[t]) - f * rk;
     }
     __syncthreads();
   }
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256) k_pc_invert(double* __restrict__ Mall, in
     const int p = perm[k];
     if (p != k)
       for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        const double t = A[k * nb + i];
+        const T t = A[k * nb + i];
         A[k * nb + i] = A[p * nb + i];
         A[p * nb + i] = t;
       }

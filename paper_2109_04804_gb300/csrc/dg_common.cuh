@@ -35,6 +35,7 @@ template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Du
   return {q, (a.d - q * b.d) * iv};
 }
 template <typename T> __device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, Dual<T> b) { a.v += b.v; a.d += b.d; return a; }
+template <typename T> __device__ __forceinline__ Dual<T>& operator-=(Dual<T>& a, Dual<T> b) { a.v -= b.v; a.d -= b.d; return a; }
 
 // base (real) type of a value type and its real part
 template <class V> struct BaseOf { using type = V; };
@@ -49,6 +50,29 @@ enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2 };
 // transformation (Sec. 3.1.1), so the element operator of Eq. 12 is
 //   R1_i = sum_m [ sum_l Dvol[m][i][l] G^m_l + sp[m][i] f*_{+m} + sm[m][i] f*_{-m} ]
 // with G^m the nodal flux (for advection the state itself, a_m folded in Dvol).
+// Launch shape of the element operator kernel: one thread per node, EPB
+// elements per block.
+template <int DIM, int P>
+struct Geo {
+  static constexpr int NN = ipow(P, DIM);        // nodes per element
+  static constexpr int NF = ipow(P, DIM - 1);    // nodes per face
+  static constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
+  static constexpr int THREADS = EPB * NN;
+};
+
+// Geometry of one instance of a batch of independent problems that share the
+// law, the node family and N: one element numbering in which every instance's
+// elements are contiguous and start at a multiple of the operator kernel's
+// elements per block, so that a block never spans two instances.
+template <typename T>
+struct InstGeo {
+  int n[3];   // elements per direction
+  int e0;     // first element of the instance
+  int nE;     // elements of the instance
+  T hs[3];    // 2 / h_m; the matrices of DGParams are then those of h_m = 2
+  T nu;       // viscosity of the instance
+};
+
 template <typename T>
 struct DGParams {
   int n[3];                 // elements per direction (1 for unused directions)
@@ -63,7 +87,31 @@ struct DGParams {
   T eps2, inv_eps2, inv_eps;
   T lam[3][5];              // global-LF kappa per direction and variable
   int rusanov;
+  // BR2 viscous term nu Laplace(w) of a scalar law (Sec. 5.1.1); visc = 0: none.
+  // With visc != 0 Dvol does not carry a_m (the advective flux goes through
+  // the nodal-flux path like a nonlinear flux).
+  int visc;
+  T nu;
+  T bp[3], bm[3];           // (2/h_m) eta c_+, (2/h_m) eta c_-
+  const T* vtab;            // device: Dg[DIM][P][P] = (2/h) D, gp[DIM][P], gm[DIM][P] = (2/h) l_j'(+-1)
+  const double* vloc;       // device: element-diagonal viscous block per direction [DIM][P][P], unit nu
+  // batch of instances (null for a single problem): per-instance geometry and,
+  // per block of the operator kernel, the instance it belongs to
+  const InstGeo<T>* inst;
+  const int* blk_inst;
 };
+
+// Geometry of the instance that operator block `blk` works on.
+template <typename T>
+__device__ __forceinline__ InstGeo<T> inst_geo(const DGParams<T>& p, int blk) {
+  if (p.inst) return p.inst[p.blk_inst[blk]];
+  InstGeo<T> g;
+  g.n[0] = p.n[0]; g.n[1] = p.n[1]; g.n[2] = p.n[2];
+  g.e0 = 0; g.nE = p.nE;
+  g.hs[0] = T(1); g.hs[1] = T(1); g.hs[2] = T(1);
+  g.nu = p.nu;
+  return g;
+}
 
 // ---------------------------------------------------------------------------
 // Physical fluxes, templated on the value type V (double, float or a Dual of

@@ -11,6 +11,12 @@
 //      elements, which keeps the pass free of any grid-wide dependency;
 //   3. every node contracts the fluxes with Dvol along each direction and adds
 //      the lifted face fluxes.
+// With a BR2 viscous term (scalar laws, Sec. 5.1.1) pass 2 also forms, per face
+// point, the common value u* and the average of the two face-local lifted
+// gradients (the neighbour's line is read in full for its derivative at the
+// face); a pass 2b then forms the lifted gradient d at every node and folds
+// -nu d into the nodal flux, and the viscous face flux into the face flux, so
+// pass 3 is unchanged.
 // A Job supplies how node values are loaded (so that perturbed states W + eps dW
 // are formed on the fly) and what is done with the results (the epilogue), so
 // Jacobian-vector products and residuals are single passes over memory.
@@ -21,21 +27,18 @@ namespace hbpc {
 
 enum EvalKind { EV_R1 = 0, EV_R2 = 1 };
 
-template <int DIM, int P>
-struct Geo {
-  static constexpr int NN = ipow(P, DIM);        // nodes per element
-  static constexpr int NF = ipow(P, DIM - 1);    // nodes per face
-  static constexpr int EPB = NN >= 256 ? 1 : 256 / NN;
-  static constexpr int THREADS = EPB * NN;
-};
 
 template <int LAW, int DIM, int P>
 struct KernelShape {
   static constexpr int NV = (LAW == LAW_EULER) ? DIM + 2 : 1;
+  static constexpr bool VISC = NV == 1;          // BR2 viscous term available
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF, EPB = Geo<DIM, P>::EPB;
   // shared values per element: state + direction + DIM fluxes + 2*DIM faces
-  static constexpr int PER_ELEM = 2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF;
-  static constexpr int MATS = DIM * P * P + 2 * DIM * P;
+  // (+ 2*DIM faces of u* - u for the viscous term)
+  static constexpr int PER_ELEM =
+      2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF + (VISC ? 2 * DIM * NF : 0);
+  // Dvol, sp, sm (+ Dg, gp, gm)
+  static constexpr int MATS = DIM * P * P + 2 * DIM * P + (VISC ? DIM * P * P + 2 * DIM * P : 0);
   // operator matrices (base type B, padded to 16 bytes) then element data (V)
   template <typename V, typename B>
   static constexpr size_t mats_bytes() { return ((MATS * sizeof(B) + 15) / 16) * 16; }
@@ -52,18 +55,18 @@ struct FaceFlux {
   using L = typename LawOf<LAW, DIM, T>::type;
   static constexpr int NV = L::NV, NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
   template <int M, int SIDE>
-  __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, int k, bool r2,
-                                             const int* ec, int pt, const V* sst, const V* sdir,
-                                             V* sface) {
+  __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, const InstGeo<T>& g,
+                                             int k, bool r2, const int* ec, int pt, const V* sst,
+                                             const V* sdir, V* sface) {
     constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;   // face point -> node with idx_M = 0
-    // neighbour element across this face (periodic)
+    // neighbour element across this face (periodic within the instance)
     int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
     int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
     c += SIDE ? 1 : -1;
-    if (c < 0) c += prm.n[M];
-    if (c >= prm.n[M]) c -= prm.n[M];
-    const int en = nc0 + prm.n[0] * (nc1 + prm.n[1] * nc2);
+    if (c < 0) c += g.n[M];
+    if (c >= g.n[M]) c -= g.n[M];
+    const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
     V wo[NV], wn[NV], so[NV], sn[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { wo[v] = V(T(0)); wn[v] = V(T(0)); so[v] = V(T(0)); sn[v] = V(T(0)); }
@@ -129,6 +132,59 @@ struct FaceFlux {
   }
 };
 
+// BR2 viscous part at one face point (scalar law): the common value
+// u* = (u_own + u_nb)/2 (Eq. 30) and the face-local lifted gradients
+//   element left of the face:  d^L = u'(+1) + eta c_+ (u* - u^L(+1)),
+//   element right of the face: d^R = u'(-1) + eta c_- (u^R(-1) - u*)   (times 2/h),
+// (strong-form liftings keeping only this face's surface term, scaled by eta).
+// The viscous face flux nu (d^L + d^R)/2 along +e_M enters sface with the sign
+// that makes pass 3 add +(2/h)[lhat(+1) F^v*_+ - lhat(-1) F^v*_-]; u* - u_own is
+// kept for the lifted volume gradient of pass 2b.  u: the element's values of
+// the viscous input (state for R1, direction for R2) in shared memory.
+template <int DIM, int P, typename V, class Job>
+struct FaceVisc {
+  using T = typename BaseOf<V>::type;
+  static constexpr int NF = Geo<DIM, P>::NF;
+  template <int M, int SIDE>
+  __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, const InstGeo<T>& g,
+                                             int k, bool r2, const int* ec, int pt, const V* u,
+                                             const T* sgp, const T* sgm, V* sface, V* sjump) {
+    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    const int base = (pt % st) + (pt / st) * st * P;
+    int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
+    int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
+    c += SIDE ? 1 : -1;
+    if (c < 0) c += g.n[M];
+    if (c >= g.n[M]) c -= g.n[M];
+    const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
+    V uo = V(T(0)), go = V(T(0)), un = V(T(0)), gn = V(T(0));
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const int node = base + i * st;
+      V y[1];
+      if (r2) job.load_dir(k, en, node, y); else job.load_state(k, en, node, y);
+      const V x = u[node];
+      uo += (SIDE ? prm.lp[i] : prm.lm[i]) * x;
+      go += (SIDE ? sgp[M * P + i] : sgm[M * P + i]) * x;
+      un += (SIDE ? prm.lm[i] : prm.lp[i]) * y[0];
+      gn += (SIDE ? sgm[M * P + i] : sgp[M * P + i]) * y[0];
+    }
+    const V us = T(0.5) * (uo + un);
+    V dL, dR;
+    if (SIDE) {
+      dL = go + prm.bp[M] * (us - uo);
+      dR = gn + prm.bm[M] * (un - us);
+    } else {
+      dL = gn + prm.bp[M] * (us - un);
+      dR = go + prm.bm[M] * (uo - us);
+    }
+    const int f = 2 * M + SIDE;
+    const T sg = SIDE ? T(-0.5) : T(0.5);
+    sface[f * NF + pt] += (sg * g.nu * g.hs[M]) * (dL + dR);
+    sjump[f * NF + pt] = us - uo;
+  }
+};
+
 template <int LAW, int DIM, int P, bool LGL, typename V, class Job>
 __global__ void __launch_bounds__(Geo<DIM, P>::THREADS)
 dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) {
@@ -137,6 +193,7 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
   using G = Geo<DIM, P>;
   constexpr int NV = L::NV, NN = G::NN, NF = G::NF, EPB = G::EPB;
   constexpr int PER_ELEM = KernelShape<LAW, DIM, P>::PER_ELEM;
+  constexpr bool VISC = KernelShape<LAW, DIM, P>::VISC;
 
   if (!job.active()) return;
 
@@ -153,21 +210,31 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
     sSp[t] = prm.sp[t / P][t % P];
     sSm[t] = prm.sm[t / P][t % P];
   }
+  const bool visc = VISC && prm.visc;
+  T* const sDg = sSm + DIM * P;                              // [DIM][P][P] (viscous)
+  T* const sgp = sDg + DIM * P * P;                          // [DIM][P]
+  T* const sgm = sgp + DIM * P;                              // [DIM][P]
+  if (visc) {
+    for (int t = threadIdx.x; t < DIM * P * P + 2 * DIM * P; t += blockDim.x) sDg[t] = prm.vtab[t];
+  }
   V* const smem = reinterpret_cast<V*>(smem_raw + KernelShape<LAW, DIM, P>::template mats_bytes<V, T>());
   const int le = threadIdx.x / NN;
   const int n = threadIdx.x - le * NN;
-  const int e = blockIdx.x * EPB + le;
-  const bool live = e < prm.nE;
+  const int e = blockIdx.x * EPB + le;               // element in the (batch) numbering
+  const InstGeo<T> geo = inst_geo(prm, blockIdx.x);  // its instance's mesh and scales
+  const int el = e - geo.e0;                         // element within the instance
+  const bool live = e < prm.nE && el < geo.nE;
   V* const sst = smem + le * PER_ELEM;     // [NV][NN] state
   V* const sdir = sst + NV * NN;           // [NV][NN] direction (R2)
   V* const sG = sdir + NV * NN;            // [DIM][NV][NN] nodal fluxes
   V* const sface = sG + DIM * NV * NN;     // [2*DIM][NV][NF] face fluxes
+  V* const sjump = sface + 2 * DIM * NV * NF;   // [2*DIM][NF] u* - u_own (viscous)
 
   int ec[3] = {0, 0, 0};
   if (live) {
-    ec[0] = e % prm.n[0];
-    ec[1] = (e / prm.n[0]) % prm.n[1];
-    ec[2] = e / (prm.n[0] * prm.n[1]);
+    ec[0] = el % geo.n[0];
+    ec[1] = (el / geo.n[0]) % geo.n[1];
+    ec[2] = el / (geo.n[0] * geo.n[1]);
   }
   int idx[3] = {0, 0, 0};
   idx[0] = n % P;
@@ -189,7 +256,7 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
         sst[v * NN + n] = w[v];
         if (r2) sdir[v * NN + n] = s[v];
       }
-      if constexpr (!L::LINEAR) {
+      if (!L::LINEAR || visc) {
         V F[DIM][NV];
         if (r2) L::jvp_all(w, s, F, prm); else L::flux_all(w, F, prm);
 #pragma unroll
@@ -205,17 +272,62 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
         const int f = fp / NF, pt = fp - f * NF;
         using FF = FaceFlux<LAW, DIM, P, LGL, V, Job>;
         switch (f) {
-          case 0: FF::template run<0, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
-          case 1: FF::template run<0, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
-          case 2: if constexpr (DIM > 1) FF::template run<1, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
-          case 3: if constexpr (DIM > 1) FF::template run<1, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
-          case 4: if constexpr (DIM > 2) FF::template run<2, 0>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
-          case 5: if constexpr (DIM > 2) FF::template run<2, 1>(job, prm, k, r2, ec, pt, sst, sdir, sface); break;
+          case 0: FF::template run<0, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
+          case 1: FF::template run<0, 1>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
+          case 2: if constexpr (DIM > 1) FF::template run<1, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
+          case 3: if constexpr (DIM > 1) FF::template run<1, 1>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
+          case 4: if constexpr (DIM > 2) FF::template run<2, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
+          case 5: if constexpr (DIM > 2) FF::template run<2, 1>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
           default: break;
+        }
+        if constexpr (VISC) {
+          if (visc) {
+            using FV = FaceVisc<DIM, P, V, Job>;
+            const V* u = r2 ? sdir : sst;
+            switch (f) {
+              case 0: FV::template run<0, 0>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              case 1: FV::template run<0, 1>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              case 2: if constexpr (DIM > 1) FV::template run<1, 0>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              case 3: if constexpr (DIM > 1) FV::template run<1, 1>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              case 4: if constexpr (DIM > 2) FV::template run<2, 0>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              case 5: if constexpr (DIM > 2) FV::template run<2, 1>(job, prm, geo, k, r2, ec, pt, u, sgp, sgm, sface, sjump); break;
+              default: break;
+            }
+          }
         }
       }
     }
     __syncthreads();
+    // -- 2b. viscous: lifted gradient (Eq. 29, strong form) folded into sG -----
+    //   d^m_i = (2/h)(D u)_i + (2/h) lhat_i(+1)(u*_+ - u_+) - (2/h) lhat_i(-1)(u*_- - u_-)
+    if constexpr (VISC) {
+      if (visc) {
+        if (live) {
+          const V* u = r2 ? sdir : sst;
+#pragma unroll
+          for (int m = 0; m < DIM; ++m) {
+            const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
+            const int i = idx[m];
+            const int b0 = n - i * st;
+            const T* Grow = sDg + (m * P + i) * P;
+            V d = V(T(0));
+#pragma unroll
+            for (int l = 0; l < P; ++l) d += Grow[l] * u[b0 + l * st];
+            const int pt = (n % st) + (n / (st * P)) * st;
+            const V jp = sjump[(2 * m + 1) * NF + pt], jm = sjump[(2 * m) * NF + pt];
+            // sp = -(2/h) lhat(+1), sm = -(2/h) lhat(-1)
+            if constexpr (LGL) {
+              if (i == P - 1) d -= sSp[m * P + P - 1] * jp;
+              if (i == 0) d += sSm[m * P] * jm;
+            } else {
+              d += sSm[m * P + i] * jm - sSp[m * P + i] * jp;
+            }
+            sG[m * NN + n] -= (geo.nu * geo.hs[m]) * d;
+          }
+        }
+        __syncthreads();
+      }
+    }
     // -- 3. volume contraction + lifting ---------------------------------------
     if (live) {
 #pragma unroll
@@ -227,20 +339,22 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
           const int i = idx[m];
           const int b0 = n - i * st;
           const V* g;
-          if constexpr (L::LINEAR) g = (r2 ? sdir : sst) + v * NN;
+          if (L::LINEAR && !visc) g = (r2 ? sdir : sst) + v * NN;
           else g = sG + (m * NV + v) * NN;
           const T* Drow = sD + (m * P + i) * P;
+          V am = V(T(0));
 #pragma unroll
-          for (int l = 0; l < P; ++l) acc += Drow[l] * g[b0 + l * st];
+          for (int l = 0; l < P; ++l) am += Drow[l] * g[b0 + l * st];
           const int pt = (n % st) + (n / (st * P)) * st;
           const V* fm = sface + ((2 * m) * NV + v) * NF;
           const V* fpl = sface + ((2 * m + 1) * NV + v) * NF;
           if constexpr (LGL) {
-            if (i == P - 1) acc += sSp[m * P + P - 1] * fpl[pt];
-            if (i == 0) acc += sSm[m * P] * fm[pt];
+            if (i == P - 1) am += sSp[m * P + P - 1] * fpl[pt];
+            if (i == 0) am += sSm[m * P] * fm[pt];
           } else {
-            acc += sSp[m * P + i] * fpl[pt] + sSm[m * P + i] * fm[pt];
+            am += sSp[m * P + i] * fpl[pt] + sSm[m * P + i] * fm[pt];
           }
+          acc += geo.hs[m] * am;
         }
         res[k][v] = acc;
       }

@@ -15,6 +15,7 @@
 #include <new>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hbpc.h"
@@ -69,11 +70,59 @@ __global__ void k_sqrt_norms(const GmresState* st, double* out) {
   if (threadIdx.x < 3) out[threadIdx.x] = sqrt(st->nrm[threadIdx.x]);
 }
 
+// Batches: per-instance squared norms of a 2 n_dof vector v = (vW, vS), one
+// block per instance (fixed-order reduction): out[2 i] = |v_i|^2 over both
+// halves, out[2 i + 1] = |vW_i|^2.  range[2 i], range[2 i + 1]: first value and
+// count of instance i in a half.
+constexpr int kInstThreads = 512;
+__global__ void __launch_bounds__(kInstThreads) k_inst_sqnorms(const double* __restrict__ v, size_t half,
+                                                             const long long* __restrict__ range,
+                                                             double* __restrict__ out) {
+  const int i = blockIdx.x;
+  const long long a = range[2 * i], cnt = range[2 * i + 1];
+  double sw = 0.0, ss = 0.0;
+  for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const double x = v[a + t], y = v[half + a + t];
+    sw += x * x;
+    ss += y * y;
+  }
+  __shared__ double rw[kInstThreads / 32], rs[kInstThreads / 32];
+  sw = warp_sum(sw);
+  ss = warp_sum(ss);
+  if ((threadIdx.x & 31) == 0) { rw[threadIdx.x >> 5] = sw; rs[threadIdx.x >> 5] = ss; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tw = 0.0, ts = 0.0;
+    for (int w = 0; w < kInstThreads / 32; ++w) { tw += rw[w]; ts += rs[w]; }
+    out[2 * i] = tw + ts;
+    out[2 * i + 1] = tw;
+  }
+}
+
+// Batches: zero both halves of v on the instances whose active flag is 0
+// (their Newton iteration has converged; blockIdx.y = instance).
+__global__ void k_inst_mask(double* __restrict__ v, size_t half, const long long* __restrict__ range,
+                            const int* __restrict__ active) {
+  const int i = blockIdx.y;
+  if (active[i]) return;
+  const long long a = range[2 * i], cnt = range[2 * i + 1];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
+    v[a + t] = 0.0;
+    v[half + a + t] = 0.0;
+  }
+}
+
 }  // namespace hbpc
 
 using namespace hbpc;
 
 static thread_local std::string g_create_error;
+
+struct hbpc_batch {
+  std::vector<hbpc_ctx*> g;       // groups (one per N)
+  std::vector<int> ig, il;        // instance -> group, index within the group
+  std::string err;
+};
 
 namespace {
 // Per-launch device timing with CUDA events (enabled by hbpc_profile_enable).
@@ -123,6 +172,23 @@ struct hbpc_ctx {
   GmresState* st_host = nullptr;   // pinned mirror
   double* c12 = nullptr;    // device c1, c2
   double* dxn = nullptr;    // device norms of dX (total, W, S)
+  // BR2 viscous term: derivative tables (FP64 and FP32) and element blocks
+  double* vtab_d = nullptr;
+  float* vtab_f = nullptr;
+  double* vloc_d = nullptr;
+  // batch of instances sharing N (hbpc_batch_*); ninst = 0 for one problem
+  int ninst = 0;
+  std::vector<long long> ie0, inE;         // element range of every instance
+  std::vector<hbpc_mesh> imesh;
+  std::vector<double> inu;
+  InstGeo<double>* d_inst = nullptr;
+  InstGeo<float>* d_instf = nullptr;
+  int* d_blk = nullptr;                    // operator block -> instance
+  long long* d_irange = nullptr;           // per instance: first value, count (one half)
+  double* d_inrm = nullptr;                // per-instance squared norms
+  int* d_active = nullptr;                 // per-instance Newton activity
+  std::vector<double> h_inrm;
+  std::vector<int> h_active;
   // BJ_ext preconditioner (Sec. 3.2.3)
   int nb = 0;               // block size n_var (N+1)^dim
   double* Jpc = nullptr;    // element Jacobians, n_E x n_b x n_b
@@ -156,6 +222,9 @@ struct hbpc_ctx {
     int adam_t = 0;
     int cap = 0, count = 0, next = 0, per_newton = 0, offset = 0;
     float* featbuf = nullptr; float* Jbuf = nullptr; float* cbuf = nullptr;
+    float* Tbuf = nullptr;          // exact block inverses of the BJ_ext path (targets)
+    bool targets = true;            // every collected row has a target
+    int last_off = 0, last_row = 0, last_count = 0;
     __nv_bfloat16* Fi = nullptr; __nv_bfloat16* H1i = nullptr; __nv_bfloat16* H2i = nullptr;
     int Bmax = 0;
     __nv_bfloat16 *Fb = nullptr, *H1b = nullptr, *H2b = nullptr, *dOb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
@@ -476,7 +545,7 @@ hbpc_status lp_alloc_train(hbpc_ctx* x, int B, int P) {
 void lp_free(hbpc_ctx* x) {
   auto& L = x->lp;
   for (void* q : {(void*)L.P, (void*)L.G, (void*)L.Mo, (void*)L.Ve, (void*)L.W1h, (void*)L.W2h, (void*)L.W3h,
-                  (void*)L.W2T, (void*)L.W3T, (void*)L.featbuf, (void*)L.Jbuf,
+                  (void*)L.W2T, (void*)L.W3T, (void*)L.featbuf, (void*)L.Jbuf, (void*)L.Tbuf,
                   (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
                   (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
                   (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
@@ -516,7 +585,7 @@ hbpc_status lp_infer(hbpc_ctx* x, const double* W, double c1, double c2) {
 
 // One forward/backward pass on the batch already in Fb, Jb, cb, Xb: loss and
 // gradients (in L.G).
-hbpc_status lp_loss_grad(hbpc_ctx* x, int B, int P, double* loss) {
+hbpc_status lp_loss_grad(hbpc_ctx* x, int B, int P, double* loss, int kind) {
   auto& L = x->lp;
   hbpc_status s;
   const int H = L.H;
@@ -524,10 +593,16 @@ hbpc_status lp_loss_grad(hbpc_ctx* x, int B, int P, double* loss) {
   if ((s = gemm(x, L.Fb, L.dinp, L.W1h, L.dinp, B, H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1b, H})) != HBPC_OK) return s;
   if ((s = gemm(x, L.H1b, H, L.W2h, H, B, H, H, EpiBiasTanh{L.P + L.ob2, L.H2b, H})) != HBPC_OK) return s;
   if ((s = gemm(x, L.H2b, H, L.W3h, H, B, L.doutp, H, EpiBiasF32{L.P + L.ob3, L.Ob, L.doutp})) != HBPC_OK) return s;
-  // probe loss and dO (dO keeps the n_b^2-wide row layout inside its doutp-wide rows)
-  const size_t shm = size_t(2 * P + 2) * L.nb * sizeof(float);
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_probe_loss<<<B, 256, shm, x->stream>>>(L.Jb, L.cb, L.Ob, L.Xb, B, P, L.nb, L.doutp, L.dOb, L.lpart));
-  HBPC_LAUNCH_CK(x, "k_mlp_probe_loss");
+  // loss and dO (dO keeps the n_b^2-wide row layout inside its doutp-wide rows);
+  // Jb holds J (probe loss) or the target inverse (inverse regression)
+  if (kind == HBPC_PC_LOSS_INVERSE) {
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_inverse_loss<<<B, 256, 0, x->stream>>>(L.Jb, L.Ob, B, L.nb, L.doutp, L.dOb, L.lpart));
+    HBPC_LAUNCH_CK(x, "k_mlp_inverse_loss");
+  } else {
+    const size_t shm = size_t(2 * P + 2) * L.nb * sizeof(float);
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_probe_loss<<<B, 256, shm, x->stream>>>(L.Jb, L.cb, L.Ob, L.Xb, B, P, L.nb, L.doutp, L.dOb, L.lpart));
+    HBPC_LAUNCH_CK(x, "k_mlp_probe_loss");
+  }
   // backward: W3, b3
   if ((s = lp_transpose(x, L.dOb, L.dOT, B, L.doutp)) != HBPC_OK) return s;
   if ((s = lp_transpose(x, L.H2b, L.H2T, B, H)) != HBPC_OK) return s;
@@ -567,6 +642,7 @@ hbpc_status lp_collect(hbpc_ctx* x, const double* W, double c1, double c2) {
            k_mlp_collect<<<count, 128, 0, x->stream>>>(W, x->Jpc, int(x->nE), L.nb, c1, c2, count, stride, L.offset,
                                                         L.next, L.cap, L.featbuf, L.Jbuf, L.cbuf));
   HBPC_LAUNCH_CK(x, "k_mlp_collect");
+  L.last_off = L.offset; L.last_row = L.next; L.last_count = count;
   L.offset = (L.offset + 1) % std::max(1, stride);
   L.next = (L.next + count) % L.cap;
   L.count = std::min(L.cap, L.count + count);
@@ -585,6 +661,7 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   hbpc_status s0;
   if (collecting && (s0 = lp_collect(x, W, c1, c2)) != HBPC_OK) return s0;
   if (x->sol.pc == HBPC_PC_LEARNED) {   // M~ from the network instead of the LU
+    if (collecting) x->lp.targets = false;   // no exact inverse for these rows
     if ((s0 = lp_infer(x, W, c1, c2)) != HBPC_OK) return s0;
     if (x->sol.precision == HBPC_PREC_MIXED &&
         (s0 = to_float(x, x->Jpc, x->Jf, size_t(x->nE) * nb * nb)) != HBPC_OK) return s0;
@@ -593,23 +670,43 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
     x->pc_c2 = c2;
     return HBPC_OK;
   }
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-           k_pc_form_S<<<int(x->nE), 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb,
-                                                                                   int(x->nE), x->c12));
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-           k_pc_invert<<<int(x->nE), 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
-               x->Mpc, x->nb, int(x->nE), x->singular));
+  const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
+  const size_t blk = size_t(x->nE) * nb * nb;
+  if (mixed) {
+    // the blocks only precondition the FP32 Krylov loop: S and its inverse in FP32
+    if ((s0 = to_float(x, x->Jpc, x->Jf, blk)) != HBPC_OK) return s0;
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+             k_pc_form_S<float><<<int(x->nE), 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb,
+                                                                                         int(x->nE), x->c12));
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+             k_pc_invert<float><<<int(x->nE), 256, (nb * nb + nb) * sizeof(float) + nb * sizeof(int), x->stream>>>(
+                 x->Mf, x->nb, int(x->nE), x->singular));
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+             k_pc_form_S<double><<<int(x->nE), 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb,
+                                                                                           int(x->nE), x->c12));
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+             k_pc_invert<double><<<int(x->nE), 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
+                 x->Mpc, x->nb, int(x->nE), x->singular));
+  }
+  if (collecting && x->lp.Tbuf) {   // the block inverses as training targets
+    auto& L = x->lp;
+    const int stride = std::max<int>(1, int(x->nE) / std::max(1, L.last_count));
+    if (mixed)
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_mlp_collect_target<float><<<L.last_count, 128, 0, x->stream>>>(
+                   x->Mf, int(x->nE), L.nb, L.last_count, stride, L.last_off, L.last_row, L.cap, L.Tbuf));
+    else
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_mlp_collect_target<double><<<L.last_count, 128, 0, x->stream>>>(
+                   x->Mpc, int(x->nE), L.nb, L.last_count, stride, L.last_off, L.last_row, L.cap, L.Tbuf));
+  }
   HBPC_LAUNCH_CK(x, "pc build");
   int sing = 0;
   HBPC_CK(x, cudaMemcpyAsync(&sing, x->singular, sizeof(int), cudaMemcpyDeviceToHost, x->stream));
   hbpc_status s = sync(x, "pc build");
   if (s != HBPC_OK) return s;
   if (sing) return fail(x, HBPC_ERR_NONFINITE, "BJ_ext block is singular");
-  if (x->sol.precision == HBPC_PREC_MIXED) {
-    const size_t blk = size_t(x->nE) * nb * nb;
-    if ((s = to_float(x, x->Mpc, x->Mf, blk)) != HBPC_OK) return s;
-    if ((s = to_float(x, x->Jpc, x->Jf, blk)) != HBPC_OK) return s;
-  }
   x->pc_built = true;
   x->pc_c1 = c1;
   x->pc_c2 = c2;
@@ -791,7 +888,10 @@ hbpc_status residual(hbpc_ctx* x, const double* b, double c1, double c2) {
 }
 
 // Newton on G(X) = 0 from X^0 = (W0, R1(W0)).  Result in x->X.
+hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, const double* W0);
+
 hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const double* W0) {
+  if (x->ninst > 0) return newton_batch(x, b, a1, a2, W0);
   const long long n = x->ndof;
   const double dt = x->sol.dt;
   const double c1 = a1 * dt, c2 = a2 * dt * dt / 2.0;
@@ -839,6 +939,88 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
     if (gn <= x->sol.tol_newton_rel * g0 || dW <= x->sol.tol_newton_abs) return HBPC_OK;
   }
   return fail(x, HBPC_ERR_NO_CONVERGENCE, "Newton did not converge within newton_max_iter");
+}
+
+// Per-instance squared norms of a 2 n_dof vector into x->h_inrm.
+hbpc_status inst_norms(hbpc_ctx* x, const double* v) {
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1,
+           k_inst_sqnorms<<<x->ninst, kInstThreads, 0, x->stream>>>(v, size_t(x->ndof), x->d_irange, x->d_inrm));
+  HBPC_LAUNCH_CK(x, "k_inst_sqnorms");
+  HBPC_CK(x, cudaMemcpyAsync(x->h_inrm.data(), x->d_inrm, 2 * x->ninst * sizeof(double), cudaMemcpyDeviceToHost,
+                             x->stream));
+  return sync(x, "instance norms");
+}
+
+// Newton for a batch of independent instances: one extended system, one GMRES
+// per Newton iteration over all still-active instances (the Jacobian and the
+// block preconditioner are block diagonal over instances, so a zero
+// right-hand side keeps an instance's update exactly zero), and the stopping
+// tests of Sec. 3.2.1 applied to every instance separately: ||G_i|| <=
+// tol ||G_i^0|| or ||dW_i|| <= tol_abs.  A converged instance is frozen.
+hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, const double* W0) {
+  const long long n = x->ndof;
+  const int ni = x->ninst;
+  const double dt = x->sol.dt;
+  const double c1 = a1 * dt, c2 = a2 * dt * dt / 2.0;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_set2<<<1, 32, 0, x->stream>>>(x->c12, c1, c2));
+  if (W0 != x->X) HBPC_CK(x, cudaMemcpyAsync(x->X, W0, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+  HBPC_RUN(x, HBPC_PHASE_OPERATOR, 1, x->ops.r1(x->prm, x->X, x->X + n, x->stream));
+  HBPC_LAUNCH_CK(x, "r1");
+  x->stats.r1_evals += 1;
+  hbpc_status s = residual(x, b, c1, c2);
+  if (s != HBPC_OK) return s;
+  if ((s = inst_norms(x, x->G)) != HBPC_OK) return s;
+  std::vector<double> g0(ni);
+  int nact = 0;
+  for (int i = 0; i < ni; ++i) {
+    g0[i] = std::sqrt(x->h_inrm[2 * i]);
+    if (!std::isfinite(g0[i])) return fail(x, HBPC_ERR_NONFINITE, "initial Newton residual is not finite");
+    x->h_active[i] = g0[i] > 0.0 ? 1 : 0;
+    nact += x->h_active[i];
+  }
+  x->stats.newton_solves += 1;
+  const dim3 mgrid(64, ni);
+  for (int r = 0; nact > 0; ++r) {
+    if (r >= x->sol.newton_max_iter)
+      return fail(x, HBPC_ERR_NO_CONVERGENCE, "Newton did not converge within newton_max_iter (batch)");
+    HBPC_CK(x, cudaMemcpyAsync(x->d_active, x->h_active.data(), ni * sizeof(int), cudaMemcpyHostToDevice, x->stream));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_inst_mask<<<mgrid, 256, 0, x->stream>>>(x->G, size_t(n), x->d_irange, x->d_active));
+    HBPC_LAUNCH_CK(x, "k_inst_mask");
+    int its = 0;
+    bool conv = false;
+    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    if (x->sol.precision == HBPC_PREC_MIXED) {
+      if ((s = to_float(x, x->X, x->Wf, size_t(2 * n))) != HBPC_OK) return s;
+      if ((s = gmres_f(x, &its, &conv)) != HBPC_OK) return s;
+    } else {
+      if ((s = gmres(x, &its, &conv)) != HBPC_OK) return s;
+    }
+    x->stats.gmres_its += its;
+    x->stats.newton_its += 1;
+    const int per = x->ops.jv_linear ? 2 : 3;
+    x->stats.r1_evals += (long long)its * (x->ops.jv_linear ? 2 : 1);
+    x->stats.r2_evals += (long long)its * (per - (x->ops.jv_linear ? 2 : 1));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add<<<grid_for(size_t(2 * n)), 256, 0, x->stream>>>(x->dX, x->X, size_t(2 * n)));
+    HBPC_LAUNCH_CK(x, "newton update");
+    if ((s = inst_norms(x, x->dX)) != HBPC_OK) return s;
+    std::vector<double> dW(ni);
+    for (int i = 0; i < ni; ++i) dW[i] = std::sqrt(x->h_inrm[2 * i + 1]);
+    if ((s = residual(x, b, c1, c2)) != HBPC_OK) return s;
+    if ((s = inst_norms(x, x->G)) != HBPC_OK) return s;
+    nact = 0;
+    for (int i = 0; i < ni; ++i) {
+      if (!x->h_active[i]) continue;
+      const double gn = std::sqrt(x->h_inrm[2 * i]);
+      if (!std::isfinite(gn) || !std::isfinite(dW[i]))
+        return fail(x, HBPC_ERR_NONFINITE, "Newton residual is not finite (batch)");
+      if (x->verbose)
+        std::fprintf(stderr, "[hbpc] batch it %d inst %d gmres %d ||G||=%.6e rel %.3e ||dW||=%.3e\n", r, i, its, gn,
+                     gn / g0[i], dW[i]);
+      if (gn <= x->sol.tol_newton_rel * g0[i] || dW[i] <= x->sol.tol_newton_abs) x->h_active[i] = 0;
+      nact += x->h_active[i];
+    }
+  }
+  return HBPC_OK;
 }
 
 hbpc_status eval_r1r2(hbpc_ctx* x, const double* w, double* r1, double* r2) {
@@ -924,6 +1106,9 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->partial); cudaFree(x->ticket); cudaFree(x->st);
   cudaFree(x->Jpc); cudaFree(x->Mpc); cudaFree(x->Z); cudaFree(x->singular);
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
+  cudaFree(x->vtab_d); cudaFree(x->vtab_f); cudaFree(x->vloc_d);
+  cudaFree(x->d_inst); cudaFree(x->d_instf); cudaFree(x->d_blk); cudaFree(x->d_irange);
+  cudaFree(x->d_inrm); cudaFree(x->d_active);
   lp_free(x);
   if (x->st_host) cudaFreeHost(x->st_host);
 }
@@ -946,9 +1131,14 @@ hbpc_status pc_alloc(hbpc_ctx* x) {
     return e;
   HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
   const size_t nbz = size_t(x->nb);
-  cudaFuncSetAttribute(k_pc_form_S, cudaFuncAttributeMaxDynamicSharedMemorySize, int(nbz * nbz * sizeof(double)));
-  cudaFuncSetAttribute(k_pc_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_pc_form_S<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(nbz * nbz * sizeof(double)));
+  cudaFuncSetAttribute(k_pc_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int((nbz * nbz + nbz) * sizeof(double) + nbz * sizeof(int)));
+  cudaFuncSetAttribute(k_pc_form_S<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(nbz * nbz * sizeof(float)));
+  cudaFuncSetAttribute(k_pc_invert<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int((nbz * nbz + nbz) * sizeof(float) + nbz * sizeof(int)));
   return HBPC_OK;
 }
 
@@ -975,6 +1165,10 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   if (ph->flux != HBPC_FLUX_GLOBAL_LF && ph->flux != HBPC_FLUX_RUSANOV) return bad("unknown flux");
   if (!(ph->eps > 0.0)) return bad("eps must be > 0");
   if (ph->law == HBPC_LAW_EULER && !(ph->gamma > 1.0)) return bad("gamma must be > 1");
+  if (!(ph->nu >= 0.0) || !std::isfinite(ph->nu)) return bad("nu must be finite and >= 0");
+  if (std::isnan(ph->eta_br2) || std::isinf(ph->eta_br2)) return bad("eta_br2 must be finite");
+  if (ph->nu > 0.0 && ph->law == HBPC_LAW_EULER)
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "the viscous term is implemented for scalar laws only");
   if (so->q != 4 && so->q != 6 && so->q != 8) return bad("q must be 4, 6 or 8");
   if (so->kmax < 0) return bad("kmax must be >= 0");
   if (!(so->dt > 0.0)) return bad("dt must be > 0");
@@ -1001,9 +1195,12 @@ void fill_params(hbpc_ctx* x) {
   for (int m = 0; m < 3; ++m) p.n[m] = m < x->dim ? x->mesh.n[m] : 1;
   p.nE = int(x->nE);
   for (int m = 0; m < x->dim; ++m) {
-    const double h = (x->mesh.hi[m] - x->mesh.lo[m]) / x->mesh.n[m];
+    // a batch keeps the matrices of h = 2 and scales by 2/h per instance
+    const double h = x->ninst > 0 ? 2.0 : (x->mesh.hi[m] - x->mesh.lo[m]) / x->mesh.n[m];
     const double sc = -2.0 / h;
-    const double av = x->phys.law == HBPC_LAW_ADVECTION ? x->phys.a[m] : 1.0;
+    // a_m folds into Dvol for inviscid advection; with a viscous term the
+    // advective flux a_m w goes through the nodal-flux path instead
+    const double av = (x->phys.law == HBPC_LAW_ADVECTION && !(x->phys.nu > 0.0)) ? x->phys.a[m] : 1.0;
     for (int i = 0; i < P; ++i) {
       for (int l = 0; l < P; ++l) p.Dvol[m][i][l] = sc * av * x->basis.Dhat[i * P + l];
       p.sp[m][i] = sc * x->basis.lp[i] / x->basis.w[i];
@@ -1024,6 +1221,9 @@ void fill_params(hbpc_ctx* x) {
   p.inv_eps2 = 1.0 / p.eps2;
   p.inv_eps = 1.0 / x->phys.eps;
   p.rusanov = x->phys.flux == HBPC_FLUX_RUSANOV ? 1 : 0;
+  // BR2 viscous term (tables on the device are attached by visc_setup)
+  p.visc = x->phys.nu > 0.0 ? 1 : 0;
+  p.nu = x->phys.nu;
   // FP32 copy for the mixed-precision Jacobian-vector product
   DGParams<float>& f = x->prmf;
   std::memset(&f, 0, sizeof(f));
@@ -1042,6 +1242,41 @@ void fill_params(hbpc_ctx* x) {
   f.gm1 = float(p.gm1); f.gamma = float(p.gamma); f.eps2 = float(p.eps2);
   f.inv_eps2 = float(p.inv_eps2); f.inv_eps = float(p.inv_eps);
   f.rusanov = p.rusanov;
+  f.visc = p.visc;
+  f.nu = float(p.nu);
+}
+
+// Tables of the BR2 viscous term on the device (Sec. 5.1.1): per direction the
+// derivative matrix and edge derivatives scaled by 2/h (FP64 and FP32 copies)
+// and the element-diagonal block used by the preconditioner assembly.
+hbpc_status visc_setup(hbpc_ctx* x) {
+  if (!x->prm.visc) return HBPC_OK;
+  const int P = x->P, d = x->dim;
+  const double eta = x->phys.eta_br2 > 0.0 ? x->phys.eta_br2 : 2.0 * d;
+  const size_t ntab = size_t(d) * P * P + 2 * size_t(d) * P;
+  std::vector<double> tab(ntab), vloc(size_t(d) * P * P);
+  for (int m = 0; m < d; ++m) {
+    const double h = x->ninst > 0 ? 2.0 : (x->mesh.hi[m] - x->mesh.lo[m]) / x->mesh.n[m];
+    double bp = 0.0, bm = 0.0;
+    br2_tables(x->basis, h, eta, tab.data() + size_t(m) * P * P, tab.data() + size_t(d) * P * P + m * P,
+               tab.data() + size_t(d) * P * P + size_t(d) * P + m * P, &bp, &bm,
+               vloc.data() + size_t(m) * P * P);
+    x->prm.bp[m] = bp; x->prm.bm[m] = bm;
+    x->prmf.bp[m] = float(bp); x->prmf.bm[m] = float(bm);
+  }
+  std::vector<float> tabf(tab.begin(), tab.end());
+  hbpc_status e;
+  if ((e = dmalloc(x, &x->vtab_d, ntab)) || (e = dmalloc(x, &x->vtab_f, ntab)) ||
+      (e = dmalloc(x, &x->vloc_d, vloc.size())))
+    return e;
+  HBPC_CK(x, cudaMemcpy(x->vtab_d, tab.data(), ntab * sizeof(double), cudaMemcpyHostToDevice));
+  HBPC_CK(x, cudaMemcpy(x->vtab_f, tabf.data(), ntab * sizeof(float), cudaMemcpyHostToDevice));
+  HBPC_CK(x, cudaMemcpy(x->vloc_d, vloc.data(), vloc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  x->prm.vtab = x->vtab_d;
+  x->prm.vloc = x->vloc_d;
+  x->prmf.vtab = x->vtab_f;
+  x->prmf.vloc = x->vloc_d;
+  return HBPC_OK;
 }
 
 
@@ -1089,50 +1324,11 @@ hbpc_status noalloc_scratch(unsigned char** out) {
   return HBPC_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-hbpc_status hbpc_basis(int N, int nodes, double* xi, double* w, double* Dhat, double* lm, double* lp) {
-  Basis1D b;
-  if (nodes != HBPC_NODES_LOBATTO && nodes != HBPC_NODES_GAUSS)
-    return fail(nullptr, HBPC_ERR_INVALID_ARG, "unknown node family");
-  if (!basis_1d(N, nodes, b)) return fail(nullptr, HBPC_ERR_INVALID_ARG, "N must satisfy 1 <= N <= 7");
-  const int p = N + 1;
-  if (xi) std::memcpy(xi, b.xi.data(), p * sizeof(double));
-  if (w) std::memcpy(w, b.w.data(), p * sizeof(double));
-  if (Dhat) std::memcpy(Dhat, b.Dhat.data(), p * p * sizeof(double));
-  if (lm) std::memcpy(lm, b.lm.data(), p * sizeof(double));
-  if (lp) std::memcpy(lp, b.lp.data(), p * sizeof(double));
-  return HBPC_OK;
-}
-
-hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
-                        const hbpc_physics* phys, const hbpc_solver* solver, void* cuda_stream) {
-  if (!out) return fail(nullptr, HBPC_ERR_INVALID_ARG, "out is null");
-  *out = nullptr;
-  hbpc_status s = validate(mesh, N, nodes, phys, solver);
-  if (s != HBPC_OK) return s;
-  hbpc_ctx* x = new (std::nothrow) hbpc_ctx();
-  if (!x) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
-  x->mesh = *mesh; x->phys = *phys; x->sol = *solver;
-  x->N = N; x->P = N + 1; x->nodes = nodes; x->dim = mesh->dim;
-  x->nv = phys->law == HBPC_LAW_EULER ? mesh->dim + 2 : 1;
-  x->nE = 1;
-  for (int m = 0; m < x->dim; ++m) x->nE *= mesh->n[m];
-  long long nn = 1;
-  for (int m = 0; m < x->dim; ++m) nn *= x->P;
-  x->ndof = x->nE * x->nv * nn;
-  x->stream = static_cast<cudaStream_t>(cuda_stream);
-  if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
-  if (!basis_1d(N, nodes, x->basis)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis"); }
-  if (!get_ops(phys->law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
-    delete x;
-    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "this (law, dim, N, node family) is not compiled in");
-  }
-  if (x->nE > (1LL << 30)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "mesh too large"); }
-  tableau(solver->q, x);
-  fill_params(x);
+// Device memory and initial state of a context whose host description (sizes,
+// basis, operator table, tableau, parameters) is filled in.  On failure frees
+// the context and returns the error (message in g_create_error).
+hbpc_status ctx_finish(hbpc_ctx* x) {
+  const hbpc_solver* solver = &x->sol;
   const size_t n = size_t(x->ndof), n2 = 2 * n;
   const int m = solver->gmres_restart;
   int dev = 0, sms = 152;
@@ -1151,6 +1347,10 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
     free_all(x); delete x; return e;
   }
   const size_t nsmall = size_t(m + 1) * m + 3 * m + 9 * (m + 3) + 24;
+  if ((e = visc_setup(x)) != HBPC_OK) {
+    g_create_error = x->err;
+    free_all(x); delete x; return e;
+  }
   if (solver->pc != HBPC_PC_NONE && (e = pc_alloc(x)) != HBPC_OK) {
     g_create_error = x->err;
     free_all(x); delete x; return e;
@@ -1210,6 +1410,157 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
     g_create_error = std::string("initialisation: ") + cudaGetErrorString(ce);
     free_all(x); delete x; return HBPC_ERR_CUDA;
   }
+  return HBPC_OK;
+}
+
+// One group of a batch: the instances with the same N in one context (element
+// numbering padded so that each instance starts at a multiple of the operator's
+// elements per block; padding elements stay zero in every vector).
+hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, int N, int nodes,
+                         const hbpc_physics* phys, const hbpc_solver* solver, hbpc_ctx** out) {
+  *out = nullptr;
+  hbpc_ctx* x = new (std::nothrow) hbpc_ctx();
+  if (!x) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
+  const hbpc_mesh& m0 = meshes[ids[0]];
+  x->mesh = m0; x->phys = phys[ids[0]]; x->sol = *solver;
+  double numax = 0.0;
+  for (int id : ids) numax = std::max(numax, phys[id].nu);
+  x->phys.nu = numax;   // the viscous passes run if any instance is viscous
+  x->N = N; x->P = N + 1; x->nodes = nodes; x->dim = m0.dim;
+  x->nv = x->phys.law == HBPC_LAW_EULER ? x->dim + 2 : 1;
+  long long nn = 1;
+  for (int m = 0; m < x->dim; ++m) nn *= x->P;
+  const int epb = nn >= 256 ? 1 : int(256 / nn);   // Geo<DIM, P>::EPB
+  x->ninst = int(ids.size());
+  long long e = 0;
+  for (int id : ids) {
+    long long ne = 1;
+    for (int m = 0; m < x->dim; ++m) ne *= meshes[id].n[m];
+    x->ie0.push_back(e);
+    x->inE.push_back(ne);
+    x->imesh.push_back(meshes[id]);
+    x->inu.push_back(phys[id].nu);
+    e += ((ne + epb - 1) / epb) * epb;
+  }
+  x->nE = e;
+  x->ndof = x->nE * x->nv * nn;
+  if (x->nE > (1LL << 30)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "batch too large"); }
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete x;
+    return fail(nullptr, HBPC_ERR_CUDA, "cudaStreamCreate failed");
+  }
+  x->stream = st;
+  if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
+  if (!basis_1d(N, nodes, x->basis) ||
+      !get_ops(x->phys.law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
+    cudaStreamDestroy(st);
+    delete x;
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "this (law, dim, N, node family) is not compiled in");
+  }
+  tableau(solver->q, x);
+  fill_params(x);
+  hbpc_status s = ctx_finish(x);
+  if (s != HBPC_OK) { cudaStreamDestroy(st); return s; }
+  // instance tables
+  const int ni = x->ninst;
+  std::vector<InstGeo<double>> gd(ni);
+  std::vector<InstGeo<float>> gf(ni);
+  std::vector<long long> rng(2 * ni);
+  std::vector<int> blk(size_t(x->nE / epb), 0);
+  for (int i = 0; i < ni; ++i) {
+    InstGeo<double>& g = gd[i];
+    for (int m = 0; m < 3; ++m) g.n[m] = m < x->dim ? x->imesh[i].n[m] : 1;
+    g.e0 = int(x->ie0[i]);
+    g.nE = int(x->inE[i]);
+    for (int m = 0; m < 3; ++m)
+      g.hs[m] = m < x->dim ? 2.0 * x->imesh[i].n[m] / (x->imesh[i].hi[m] - x->imesh[i].lo[m]) : 1.0;
+    g.nu = x->inu[i];
+    InstGeo<float>& f = gf[i];
+    for (int m = 0; m < 3; ++m) { f.n[m] = g.n[m]; f.hs[m] = float(g.hs[m]); }
+    f.e0 = g.e0; f.nE = g.nE; f.nu = float(g.nu);
+    rng[2 * i] = x->ie0[i] * x->nv * nn;
+    rng[2 * i + 1] = x->inE[i] * x->nv * nn;
+    const long long b0 = x->ie0[i] / epb, b1 = (x->ie0[i] + x->inE[i] + epb - 1) / epb;
+    for (long long bb = b0; bb < b1; ++bb) blk[size_t(bb)] = i;
+  }
+  auto bail = [&](hbpc_status code) {
+    g_create_error = x->err;
+    cudaStreamDestroy(st);
+    free_all(x);
+    delete x;
+    return code;
+  };
+  if ((s = dmalloc(x, &x->d_inst, ni)) || (s = dmalloc(x, &x->d_instf, ni)) || (s = dmalloc(x, &x->d_blk, blk.size())) ||
+      (s = dmalloc(x, &x->d_irange, 2 * ni)) || (s = dmalloc(x, &x->d_inrm, 2 * ni)) ||
+      (s = dmalloc(x, &x->d_active, ni)))
+    return bail(s);
+  cudaError_t ce = cudaMemcpy(x->d_inst, gd.data(), ni * sizeof(InstGeo<double>), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(x->d_instf, gf.data(), ni * sizeof(InstGeo<float>), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(x->d_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(x->d_irange, rng.data(), rng.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  // every vector starts at zero so that the padding elements stay zero
+  const size_t n = size_t(x->ndof), n2 = 2 * n, m1 = size_t(solver->gmres_restart + 1);
+  auto z = [&](void* p, size_t bytes) { if (ce == cudaSuccess && p) ce = cudaMemsetAsync(p, 0, bytes, st); };
+  z(x->X, n2 * 8); z(x->G, n2 * 8); z(x->r1, n * 8); z(x->r2, n * 8); z(x->dX, n2 * 8); z(x->bvec, n * 8);
+  z(x->stage, size_t(2) * x->s * 3 * n * 8); z(x->V, m1 * n2 * 8); z(x->Z, n2 * 8);
+  z(x->Vf, m1 * n2 * 4); z(x->Zf, n2 * 4); z(x->Zf2, n2 * 4); z(x->Wf, n2 * 4);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) { x->err = std::string("batch tables: ") + cudaGetErrorString(ce); return bail(HBPC_ERR_CUDA); }
+  x->prm.inst = x->d_inst; x->prm.blk_inst = x->d_blk;
+  x->prmf.inst = x->d_instf; x->prmf.blk_inst = x->d_blk;
+  x->h_inrm.assign(2 * ni, 0.0);
+  x->h_active.assign(ni, 0);
+  *out = x;
+  return HBPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hbpc_status hbpc_basis(int N, int nodes, double* xi, double* w, double* Dhat, double* lm, double* lp) {
+  Basis1D b;
+  if (nodes != HBPC_NODES_LOBATTO && nodes != HBPC_NODES_GAUSS)
+    return fail(nullptr, HBPC_ERR_INVALID_ARG, "unknown node family");
+  if (!basis_1d(N, nodes, b)) return fail(nullptr, HBPC_ERR_INVALID_ARG, "N must satisfy 1 <= N <= 7");
+  const int p = N + 1;
+  if (xi) std::memcpy(xi, b.xi.data(), p * sizeof(double));
+  if (w) std::memcpy(w, b.w.data(), p * sizeof(double));
+  if (Dhat) std::memcpy(Dhat, b.Dhat.data(), p * p * sizeof(double));
+  if (lm) std::memcpy(lm, b.lm.data(), p * sizeof(double));
+  if (lp) std::memcpy(lp, b.lp.data(), p * sizeof(double));
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
+                        const hbpc_physics* phys, const hbpc_solver* solver, void* cuda_stream) {
+  if (!out) return fail(nullptr, HBPC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  hbpc_status s = validate(mesh, N, nodes, phys, solver);
+  if (s != HBPC_OK) return s;
+  hbpc_ctx* x = new (std::nothrow) hbpc_ctx();
+  if (!x) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
+  x->mesh = *mesh; x->phys = *phys; x->sol = *solver;
+  x->N = N; x->P = N + 1; x->nodes = nodes; x->dim = mesh->dim;
+  x->nv = phys->law == HBPC_LAW_EULER ? mesh->dim + 2 : 1;
+  x->nE = 1;
+  for (int m = 0; m < x->dim; ++m) x->nE *= mesh->n[m];
+  long long nn = 1;
+  for (int m = 0; m < x->dim; ++m) nn *= x->P;
+  x->ndof = x->nE * x->nv * nn;
+  x->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
+  if (!basis_1d(N, nodes, x->basis)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis"); }
+  if (!get_ops(phys->law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
+    delete x;
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "this (law, dim, N, node family) is not compiled in");
+  }
+  if (x->nE > (1LL << 30)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "mesh too large"); }
+  tableau(solver->q, x);
+  fill_params(x);
+  hbpc_status e = ctx_finish(x);
+  if (e != HBPC_OK) return e;   // ctx_finish freed x
   *out = x;
   return HBPC_OK;
 }
@@ -1343,6 +1694,14 @@ hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const doub
   ctx->pc_built = false;
   hbpc_status s = pc_build(ctx, ctx->X, c1, c2);
   if (s != HBPC_OK) return s;
+  if (ctx->sol.precision == HBPC_PREC_MIXED) {   // the FP32 blocks and apply of the Krylov loop
+    if ((s = to_float(ctx, in, ctx->Zf, n2)) != HBPC_OK) return s;
+    if ((s = pc_apply_f(ctx, ctx->Zf, nullptr, nullptr, ctx->Zf2, 0, nullptr)) != HBPC_OK) return s;
+    HBPC_CK(ctx, cudaMemsetAsync(out, 0, n2 * sizeof(double), ctx->stream));
+    HBPC_RUN(ctx, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, ctx->stream>>>(ctx->Zf2, out, n2));
+    HBPC_LAUNCH_CK(ctx, "eval_pc (mixed)");
+    return sync(ctx, "eval_pc");
+  }
   HBPC_CK(ctx, cudaMemcpyAsync(ctx->Z, in, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   if ((s = pc_apply(ctx, ctx->Z, nullptr, nullptr, out, 0, nullptr)) != HBPC_OK) return s;
   return sync(ctx, "eval_pc");
@@ -1426,6 +1785,10 @@ hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double ou
   HBPC_CK(ctx, cudaMemset(L.Ve, 0, L.np * sizeof(float)));
   L.adam_t = 0;
   L.stats = false;
+  if (L.Tbuf && L.targets && L.count > 0) {   // start from the mean block inverse
+    k_mlp_target_mean<<<(L.dout + 255) / 256, 256, 0, ctx->stream>>>(L.Tbuf, L.count, L.nb, L.P + L.ob3);
+    HBPC_LAUNCH_CK(ctx, "k_mlp_target_mean");
+  }
   if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
   return sync(ctx, "pc_model_init");
 }
@@ -1446,9 +1809,11 @@ hbpc_status hbpc_pc_model_set(hbpc_ctx* ctx, const float* params) {
   return sync(ctx, "pc_model_set");
 }
 
-hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int B, int P, const float* F, const float* J, const float* c12,
-                              const float* X, double* loss, float* grads) {
-  if (!ctx || !F || !J || !c12 || !X || B < 8 || B % 8 || P < 1 || P > 16) return HBPC_ERR_INVALID_ARG;
+hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int loss_kind, int B, int P, const float* F, const float* J,
+                              const float* c12, const float* X, double* loss, float* grads) {
+  if (loss_kind != HBPC_PC_LOSS_PROBE && loss_kind != HBPC_PC_LOSS_INVERSE) return HBPC_ERR_INVALID_ARG;
+  if (!ctx || !F || !J || !c12 || B < 8 || B % 8 || P < 1 || P > 16) return HBPC_ERR_INVALID_ARG;
+  if (loss_kind == HBPC_PC_LOSS_PROBE && !X) return HBPC_ERR_INVALID_ARG;
   if (!ctx->lp.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
   hbpc_status s;
   if ((s = lp_alloc_train(ctx, B, P)) != HBPC_OK) return s;
@@ -1461,9 +1826,10 @@ hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int B, int P, const float* F, const
   k_f32_to_bf16<<<grid_for(nf), 256, 0, ctx->stream>>>(dF, L.Fb, nf);
   HBPC_CK(ctx, cudaMemcpyAsync(L.Jb, J, size_t(B) * L.dout * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   HBPC_CK(ctx, cudaMemcpyAsync(L.cb, c12, size_t(B) * 2 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-  HBPC_CK(ctx, cudaMemcpyAsync(L.Xb, X, size_t(B) * P * L.nb * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  if (X)
+    HBPC_CK(ctx, cudaMemcpyAsync(L.Xb, X, size_t(B) * P * L.nb * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   double l = 0.0;
-  s = lp_loss_grad(ctx, B, P, &l);
+  s = lp_loss_grad(ctx, B, P, &l, loss_kind);
   cudaFree(dF);
   if (s != HBPC_OK) return s;
   if (loss) *loss = l;
@@ -1480,26 +1846,30 @@ hbpc_status hbpc_pc_collect(hbpc_ctx* ctx, int samples_per_newton, int capacity)
   if ((s = pc_alloc(ctx)) != HBPC_OK || (s = lp_alloc(ctx)) != HBPC_OK) return s;
   auto& L = ctx->lp;
   if (samples_per_newton > 0 && capacity > 0 && capacity != L.cap) {
-    cudaFree(L.featbuf); cudaFree(L.Jbuf); cudaFree(L.cbuf);
-    L.featbuf = L.Jbuf = L.cbuf = nullptr;
+    cudaFree(L.featbuf); cudaFree(L.Jbuf); cudaFree(L.cbuf); cudaFree(L.Tbuf);
+    L.featbuf = L.Jbuf = L.cbuf = L.Tbuf = nullptr;
     if ((s = dalloc_any(ctx, &L.featbuf, size_t(capacity) * L.din)) ||
         (s = dalloc_any(ctx, &L.Jbuf, size_t(capacity) * L.dout)) ||
+        (s = dalloc_any(ctx, &L.Tbuf, size_t(capacity) * L.dout)) ||
         (s = dalloc_any(ctx, &L.cbuf, size_t(capacity) * 2)))
       return s;
-    L.cap = capacity; L.count = 0; L.next = 0;
+    L.cap = capacity; L.count = 0; L.next = 0; L.targets = true;
   }
   if (samples_per_newton > 0 && L.cap == 0) return fail(ctx, HBPC_ERR_INVALID_ARG, "capacity must be > 0");
   L.per_newton = samples_per_newton;
   return HBPC_OK;
 }
 
-hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int iters, int batch, int probes, double lr, unsigned long long seed,
-                          double* loss_first, double* loss_last) {
+hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int loss_kind, int iters, int batch, int probes, double lr,
+                          unsigned long long seed, double* loss_first, double* loss_last) {
   if (!ctx || iters < 1 || batch < 8 || batch % 8 || probes < 1 || probes > 16 || !(lr > 0.0))
     return HBPC_ERR_INVALID_ARG;
+  if (loss_kind != HBPC_PC_LOSS_PROBE && loss_kind != HBPC_PC_LOSS_INVERSE) return HBPC_ERR_INVALID_ARG;
   auto& L = ctx->lp;
   if (!L.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
   if (L.count < batch) return fail(ctx, HBPC_ERR_INVALID_ARG, "replay buffer holds fewer samples than a batch");
+  if (loss_kind == HBPC_PC_LOSS_INVERSE && !(L.Tbuf && L.targets))
+    return fail(ctx, HBPC_ERR_INVALID_ARG, "inverse regression needs data collected with the BJ_ext preconditioner");
   hbpc_status s;
   if ((s = lp_alloc_train(ctx, batch, probes)) != HBPC_OK) return s;
   if (!L.stats) {   // feature standardisation from the replay buffer
@@ -1524,14 +1894,15 @@ hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int iters, int batch, int probes, doubl
     const unsigned long long sd = seed * 1000003ull + unsigned(it);
     HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_rand_idx<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(L.idx, batch, L.count, sd));
     HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1,
-             k_mlp_gather<<<batch, 128, 0, ctx->stream>>>(L.featbuf, L.Jbuf, L.cbuf, L.idx, batch, L.din, L.dinp, L.nb,
+             k_mlp_gather<<<batch, 128, 0, ctx->stream>>>(L.featbuf, loss_kind == HBPC_PC_LOSS_INVERSE ? L.Tbuf : L.Jbuf,
+                                                           L.cbuf, L.idx, batch, L.din, L.dinp, L.nb,
                                                            L.mu, L.sd, L.Fb, L.Jb, L.cb));
     const size_t nx = size_t(batch) * probes * L.nb;
     HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_rademacher<<<grid_for(nx), 256, 0, ctx->stream>>>(L.Xb, nx, sd + 17));
     HBPC_LAUNCH_CK(ctx, "pc_train sample");
     double l = 0.0;
     const bool want = (it == 0 && loss_first) || (it == iters - 1 && loss_last);
-    if ((s = lp_loss_grad(ctx, batch, probes, want ? &l : nullptr)) != HBPC_OK) return s;
+    if ((s = lp_loss_grad(ctx, batch, probes, want ? &l : nullptr, loss_kind)) != HBPC_OK) return s;
     if (it == 0 && loss_first) *loss_first = l;
     if (it == iters - 1 && loss_last) *loss_last = l;
     L.adam_t += 1;
@@ -1576,6 +1947,8 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   so.pc = HBPC_PC_NONE; so.precision = HBPC_PREC_FP64;
   hbpc_status st = validate(mesh, N, nodes, phys, &so);
   if (st != HBPC_OK) return st;
+  if (phys->nu != 0.0)
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "the allocation-free Jv has no viscous term; use hbpc_eval_Jv");
   // host-side description of the discretisation (no device memory)
   hbpc_ctx x;
   x.mesh = *mesh; x.phys = *phys; x.sol = so;
@@ -1634,6 +2007,172 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   else x.ops.jv_fd(x.prm, X, X + n, scr + kNoAllocR1, scr + kNoAllocR2, z, cf, stream);
   if ((st = ck(cudaGetLastError(), "noalloc jv")) != HBPC_OK) return st;
   return ck(cudaStreamSynchronize(stream), "noalloc sync");
+}
+
+/* ---- batches of independent instances ---------------------------------- */
+hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* meshes, const int* N, int nodes,
+                              const hbpc_physics* phys, const hbpc_solver* solver) {
+  if (!out || n_inst < 1 || !meshes || !N || !phys || !solver)
+    return fail(nullptr, HBPC_ERR_INVALID_ARG, "invalid batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n_inst; ++i) {
+    hbpc_status s = validate(&meshes[i], N[i], nodes, &phys[i], solver);
+    if (s != HBPC_OK) return s;
+    const hbpc_physics& a = phys[0];
+    const hbpc_physics& b = phys[i];
+    if (b.law != a.law || b.flux != a.flux || b.gamma != a.gamma || b.eps != a.eps || b.lf_scale != a.lf_scale ||
+        b.a[0] != a.a[0] || b.a[1] != a.a[1] || b.a[2] != a.a[2] || b.eta_br2 != a.eta_br2 ||
+        meshes[i].dim != meshes[0].dim)
+      return fail(nullptr, HBPC_ERR_INVALID_ARG,
+                  "batch instances must share dim, law, flux, gamma, eps, lf_scale, a and eta_br2");
+  }
+  if (solver->pc == HBPC_PC_LEARNED)
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "the learned preconditioner is not available for batches");
+  hbpc_batch* b = new (std::nothrow) hbpc_batch();
+  if (!b) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
+  b->ig.assign(n_inst, -1);
+  b->il.assign(n_inst, -1);
+  for (int Nv = 1; Nv <= kMaxP - 1; ++Nv) {
+    std::vector<int> ids;
+    for (int i = 0; i < n_inst; ++i)
+      if (N[i] == Nv) ids.push_back(i);
+    if (ids.empty()) continue;
+    hbpc_ctx* x = nullptr;
+    hbpc_status s = create_group(ids, meshes, Nv, nodes, phys, solver, &x);
+    if (s != HBPC_OK) { hbpc_batch_destroy(b); return s; }
+    for (size_t k = 0; k < ids.size(); ++k) { b->ig[ids[k]] = int(b->g.size()); b->il[ids[k]] = int(k); }
+    b->g.push_back(x);
+  }
+  *out = b;
+  return HBPC_OK;
+}
+
+void hbpc_batch_destroy(hbpc_batch* b) {
+  if (!b) return;
+  for (hbpc_ctx* x : b->g) {
+    cudaStreamSynchronize(x->stream);
+    cudaStream_t st = x->stream;
+    hbpc_destroy(x);
+    cudaStreamDestroy(st);
+  }
+  delete b;
+}
+
+int hbpc_batch_groups(const hbpc_batch* b) { return b ? int(b->g.size()) : 0; }
+
+long long hbpc_batch_ndof(const hbpc_batch* b, int inst) {
+  if (!b || inst < 0 || inst >= int(b->ig.size())) return -1;
+  const hbpc_ctx* x = b->g[b->ig[inst]];
+  return x->inE[b->il[inst]] * (x->ndof / x->nE);
+}
+
+static hbpc_status batch_inst(hbpc_batch* b, int inst, hbpc_ctx** x, size_t* off, size_t* cnt) {
+  if (!b || inst < 0 || inst >= int(b->ig.size())) return HBPC_ERR_INVALID_ARG;
+  *x = b->g[b->ig[inst]];
+  const int k = b->il[inst];
+  const size_t per = size_t((*x)->ndof / (*x)->nE);
+  *off = size_t((*x)->ie0[k]) * per;
+  *cnt = size_t((*x)->inE[k]) * per;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_batch_set_state(hbpc_batch* b, int inst, const double* w, int on_device) {
+  hbpc_ctx* x; size_t off, cnt;
+  if (!w || batch_inst(b, inst, &x, &off, &cnt) != HBPC_OK) return HBPC_ERR_INVALID_ARG;
+  HBPC_CK(x, cudaMemcpyAsync(x->Wn + off, w, cnt * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, x->stream));
+  return sync(x, "batch set_state");
+}
+
+hbpc_status hbpc_batch_get_state(hbpc_batch* b, int inst, double* w, int on_device) {
+  hbpc_ctx* x; size_t off, cnt;
+  if (!w || batch_inst(b, inst, &x, &off, &cnt) != HBPC_OK) return HBPC_ERR_INVALID_ARG;
+  HBPC_CK(x, cudaMemcpyAsync(w, x->Wn + off, cnt * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, x->stream));
+  return sync(x, "batch get_state");
+}
+
+hbpc_status hbpc_batch_node_coords(hbpc_batch* b, int inst, double* xo) {
+  hbpc_ctx* x; size_t off, cnt;
+  if (!xo || batch_inst(b, inst, &x, &off, &cnt) != HBPC_OK) return HBPC_ERR_INVALID_ARG;
+  const int k = b->il[inst];
+  const hbpc_mesh& mesh = x->imesh[k];
+  const int d = x->dim, P = x->P;
+  long long nn = 1;
+  for (int m = 0; m < d; ++m) nn *= P;
+  const long long nE = x->inE[k], per = nE * nn;
+  for (long long e = 0; e < nE; ++e) {
+    long long ec[3] = {0, 0, 0};
+    ec[0] = e % mesh.n[0];
+    if (d > 1) ec[1] = (e / mesh.n[0]) % mesh.n[1];
+    if (d > 2) ec[2] = e / (mesh.n[0] * (long long)mesh.n[1]);
+    for (long long node = 0; node < nn; ++node) {
+      long long id[3] = {node % P, (node / P) % P, node / (P * P)};
+      for (int m = 0; m < d; ++m) {
+        const double h = (mesh.hi[m] - mesh.lo[m]) / mesh.n[m];
+        xo[m * per + e * nn + node] = mesh.lo[m] + h * ec[m] + 0.5 * h * (x->basis.xi[id[m]] + 1.0);
+      }
+    }
+  }
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r) {
+  hbpc_ctx* x; size_t off, cnt;
+  if (!r || batch_inst(b, inst, &x, &off, &cnt) != HBPC_OK) return HBPC_ERR_INVALID_ARG;
+  HBPC_RUN(x, HBPC_PHASE_OPERATOR, 1, x->ops.r1(x->prm, x->Wn, x->r1, x->stream));
+  HBPC_LAUNCH_CK(x, "batch eval_R1");
+  HBPC_CK(x, cudaMemcpyAsync(r, x->r1 + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
+  return sync(x, "batch eval_R1");
+}
+
+hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps) {
+  if (!b || n_steps < 0) return HBPC_ERR_INVALID_ARG;
+  const size_t G = b->g.size();
+  std::vector<hbpc_status> st(G, HBPC_OK);
+  if (G == 1) {
+    st[0] = hbpc_step(b->g[0], n_steps);
+  } else {
+    // one host thread per group, each on its group's stream
+    std::vector<std::thread> th;
+    th.reserve(G);
+    for (size_t k = 0; k < G; ++k) th.emplace_back([&, k]() { st[k] = hbpc_step(b->g[k], n_steps); });
+    for (auto& t : th) t.join();
+  }
+  for (size_t k = 0; k < G; ++k)
+    if (st[k] != HBPC_OK) { b->err = b->g[k]->err; return st[k]; }
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out) {
+  if (!b || !out) return HBPC_ERR_INVALID_ARG;
+  hbpc_stats t{};
+  for (const hbpc_ctx* x : b->g) {
+    t.steps = std::max(t.steps, x->stats.steps);
+    t.newton_solves += x->stats.newton_solves;
+    t.newton_its += x->stats.newton_its;
+    t.gmres_its += x->stats.gmres_its;
+    t.r1_evals += x->stats.r1_evals;
+    t.r2_evals += x->stats.r2_evals;
+    t.launches += x->stats.launches;
+    t.t = std::max(t.t, x->stats.t);
+  }
+  *out = t;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_batch_profile_enable(hbpc_batch* b, int enable) {
+  if (!b) return HBPC_ERR_INVALID_ARG;
+  for (hbpc_ctx* x : b->g) {
+    hbpc_status s = hbpc_profile_enable(x, enable);
+    if (s != HBPC_OK) return s;
+  }
+  return HBPC_OK;
+}
+
+const char* hbpc_batch_last_error(const hbpc_batch* b) {
+  if (!b) return g_create_error.c_str();
+  return b->err.c_str();
 }
 
 const char* hbpc_last_error(const hbpc_ctx* ctx) {

@@ -81,6 +81,7 @@ bool basis_1d(int N, int family, Basis1D& b) {
     }
     D[i * p + i] = diag;
   }
+  b.D = D;
   // Dhat[i][j] = -(w_j / w_i) l_i'(xi_j) = -(w_j / w_i) D[j][i]
   b.Dhat.assign(p * p, 0.0);
   for (int i = 0; i < p; ++i)
@@ -99,7 +100,56 @@ bool basis_1d(int N, int family, Basis1D& b) {
     for (int j = 0; j < p; ++j) den += bw[j] / (x - b.xi[j]);
     for (int j = 0; j < p; ++j) out[j] = (bw[j] / (x - b.xi[j])) / den;
   }
+  // derivative of the interpolant at the edges: l_j'(+-1) = sum_i l_i(+-1) D[i][j]
+  // (l_j' has degree N - 1, so its interpolant through the nodes is exact)
+  b.dm.assign(p, 0.0);
+  b.dp.assign(p, 0.0);
+  for (int j = 0; j < p; ++j)
+    for (int i = 0; i < p; ++i) {
+      b.dm[j] += b.lm[i] * D[i * p + j];
+      b.dp[j] += b.lp[i] * D[i * p + j];
+    }
   return true;
+}
+
+void br2_tables(const Basis1D& b, double h, double eta, double* Dg, double* gp, double* gm,
+                double* bp, double* bm, double* Vloc) {
+  const int p = b.N + 1;
+  const double H = 2.0 / h;
+  double cp = 0.0, cm = 0.0;
+  for (int i = 0; i < p; ++i) {
+    cp += b.lp[i] * b.lp[i] / b.w[i];
+    cm += b.lm[i] * b.lm[i] / b.w[i];
+  }
+  for (int i = 0; i < p; ++i) {
+    for (int j = 0; j < p; ++j) Dg[i * p + j] = H * b.D[i * p + j];
+    gp[i] = H * b.dp[i];
+    gm[i] = H * b.dm[i];
+  }
+  *bp = H * eta * cp;
+  *bm = H * eta * cm;
+  // element-diagonal block of the viscous operator along one line (neighbours'
+  // values zero), per unit viscosity: column j is the response to u = e_j.
+  //   u*_+ = u(+1)/2, u*_- = u(-1)/2
+  //   face gradients (averages of the two face-local liftings):
+  //     + face: 1/2 [u'(+1) + eta c_p (u*_+ - u(+1)) + eta c_m (0 - u*_+)]
+  //     - face: 1/2 [eta c_p (u*_- - 0) + u'(-1) + eta c_m (u(-1) - u*_-)]   (times H)
+  //   lifted gradient d_l = H [ (D u)_l + lhat_l(+1)(u*_+ - u(+1)) - lhat_l(-1)(u*_- - u(-1)) ]
+  //   V_ij = H [ sum_l Dhat_il d_l + lhat_i(+1) fgrad_+ - lhat_i(-1) fgrad_- ]
+  std::vector<double> d(p);
+  for (int j = 0; j < p; ++j) {
+    const double up = b.lp[j], um = b.lm[j];
+    const double usp = 0.5 * up, usm = 0.5 * um;
+    const double fgp = 0.5 * (H * b.dp[j] + H * eta * cp * (usp - up) + H * eta * cm * (0.0 - usp));
+    const double fgm = 0.5 * (H * eta * cp * (usm - 0.0) + H * b.dm[j] + H * eta * cm * (um - usm));
+    for (int l = 0; l < p; ++l)
+      d[l] = H * (b.D[l * p + j] + (b.lp[l] / b.w[l]) * (usp - up) - (b.lm[l] / b.w[l]) * (usm - um));
+    for (int i = 0; i < p; ++i) {
+      double acc = 0.0;
+      for (int l = 0; l < p; ++l) acc += b.Dhat[i * p + l] * d[l];
+      Vloc[i * p + j] = H * (acc + (b.lp[i] / b.w[i]) * fgp - (b.lm[i] / b.w[i]) * fgm);
+    }
+  }
 }
 
 }  // namespace hbpc

@@ -11,9 +11,18 @@ constexpr int kMaxNodes = kMaxP;
 
 struct Basis1D {
   int N = 0;
-  std::vector<double> xi, w, Dhat, lm, lp;
+  std::vector<double> xi, w, D, Dhat, lm, lp;
+  std::vector<double> dm, dp;   // l_j'(-1), l_j'(+1)
 };
 bool basis_1d(int N, int family, Basis1D& b);
+
+// Tables of the BR2 viscous term (Sec. 5.1.1) for one direction with element
+// size h: Dg = (2/h) D (p x p, row-major), gp/gm = (2/h) l_j'(+-1),
+// bp/bm = (2/h) eta c_pm with c_pm = sum_i l_i(+-1)^2 / omega_i, and Vloc, the
+// element-diagonal block of the viscous operator along one line per unit
+// viscosity (p x p, row-major; neighbours' values zero).
+void br2_tables(const Basis1D& b, double h, double eta, double* Dg, double* gp, double* gm,
+                double* bp, double* bm, double* Vloc);
 
 template <typename S> struct JvInputT;
 using JvInput = JvInputT<double>;

@@ -161,6 +161,45 @@ __global__ void k_mlp_probe_loss(const float* __restrict__ J, const float* __res
   }
 }
 
+// Inverse-regression loss with the exact block inverses T = S^-1 of the BJ_ext
+// path as targets (n_b x n_b column-major FP32 per sample):
+//   loss = sum_s |I + O_s - T_s|_F^2 / B,   dO = 2 (I + O - T) / B,
+// O, dO in the same row layout as the probe loss.
+__global__ void k_mlp_inverse_loss(const float* __restrict__ T, const float* __restrict__ O, int B, int nb,
+                                   int ldo, __nv_bfloat16* __restrict__ dO, double* __restrict__ loss_part) {
+  const int s = blockIdx.x;
+  if (s >= B) return;
+  const float* Ts = T + size_t(s) * nb * nb;
+  const float* Os = O + size_t(s) * ldo;
+  const float norm = 2.f / float(B);
+  double lsum = 0.0;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int r = t / nb, c = t - r * nb;
+    const float d = (r == c ? 1.f : 0.f) + Os[t] - Ts[size_t(c) * nb + r];
+    dO[size_t(s) * ldo + t] = __float2bfloat16(norm * d);
+    lsum += double(d) * double(d);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x); ++i) t += red[i];
+    loss_part[s] = t / double(B);
+  }
+}
+
+// Output bias from the targets: b3[r nb + c] = mean_i T_i(r, c) - delta_rc, so
+// that an untrained network already returns the mean block inverse.
+__global__ void k_mlp_target_mean(const float* __restrict__ Tbuf, int count, int nb, float* __restrict__ b3) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * nb) return;
+  const int r = t / nb, c = t - r * nb;
+  double a = 0.0;
+  for (int i = 0; i < count; ++i) a += Tbuf[size_t(i) * nb * nb + size_t(c) * nb + r];
+  b3[t] = float(a / count) - (r == c ? 1.f : 0.f);
+}
+
 // Rademacher probes from SplitMix64 (Steele, Lea & Flood 2014) of (seed, index).
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -210,6 +249,20 @@ __global__ void k_mlp_collect(const double* __restrict__ W, const double* __rest
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
     Jbuf[row * nb * nb + t] = float(Jpc[size_t(e) * nb * nb + t]);
   if (threadIdx.x == 0) { cbuf[row * 2] = float(c1); cbuf[row * 2 + 1] = float(c2); }
+}
+
+// Store the block inverses M_e = S_e^-1 (column-major; FP64, or FP32 in the
+// mixed mode) of the elements that k_mlp_collect sampled with the same (count,
+// stride, offset, row0) as FP32 training targets.
+template <typename T>
+__global__ void k_mlp_collect_target(const T* __restrict__ Mpc, int nE, int nb, int count, int stride,
+                                     int offset, int row0, int cap, float* __restrict__ Tbuf) {
+  const int s = blockIdx.x;
+  if (s >= count) return;
+  const int e = (offset + s * stride) % nE;
+  const size_t row = size_t((row0 + s) % cap);
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
+    Tbuf[row * nb * nb + t] = float(Mpc[size_t(e) * nb * nb + t]);
 }
 
 // Adam (Kingma & Ba 2015) on FP32 parameters.

@@ -27,6 +27,7 @@ FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
 PC_NONE, PC_BJEXT, PC_LEARNED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+PC_LOSS = {"probe": 0, "inverse": 1}
 PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")
 
 STATUS_NAMES = {0: "HBPC_OK", 1: "HBPC_ERR_INVALID_ARG", 2: "HBPC_ERR_OOM", 3: "HBPC_ERR_CUDA",
@@ -41,7 +42,8 @@ class Mesh(ctypes.Structure):
 
 class Physics(ctypes.Structure):
     _fields_ = [("law", ctypes.c_int), ("flux", ctypes.c_int), ("a", ctypes.c_double * 3),
-                ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("lf_scale", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("lf_scale", ctypes.c_double),
+                ("nu", ctypes.c_double), ("eta_br2", ctypes.c_double)]
 
 
 class Solver(ctypes.Structure):
@@ -87,9 +89,9 @@ _SIGS = {
     "hbpc_pc_model_init": (_I, [_CTX, ctypes.c_ulonglong, _D]),
     "hbpc_pc_model_get": (_I, [_CTX, _P]),
     "hbpc_pc_model_set": (_I, [_CTX, _P]),
-    "hbpc_pc_loss_grad": (_I, [_CTX, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "hbpc_pc_loss_grad": (_I, [_CTX, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "hbpc_pc_collect": (_I, [_CTX, _I, _I]),
-    "hbpc_pc_train": (_I, [_CTX, _I, _I, _I, _D, ctypes.c_ulonglong, _P, _P]),
+    "hbpc_pc_train": (_I, [_CTX, _I, _I, _I, _I, _D, ctypes.c_ulonglong, _P, _P]),
     "hbpc_fp64_fma_peak": (_I, [ctypes.POINTER(ctypes.c_double)]),
     "hbpc_eval_Jv_noalloc": (_I, [ctypes.POINTER(Mesh), _I, _I, ctypes.POINTER(Physics), _D, _D, _D,
                                   _P, _P, _P, _P]),
@@ -98,6 +100,18 @@ _SIGS = {
     "hbpc_last_error": (ctypes.c_char_p, [_CTX]),
     "hbpc_profile_enable": (_I, [_CTX, _I]),
     "hbpc_profile_get": (_I, [_CTX, _P, _P, _I]),
+    "hbpc_batch_create": (_I, [ctypes.POINTER(_CTX), _I, _P, _P, _I, _P, ctypes.POINTER(Solver)]),
+    "hbpc_batch_destroy": (None, [_CTX]),
+    "hbpc_batch_groups": (_I, [_CTX]),
+    "hbpc_batch_ndof": (ctypes.c_longlong, [_CTX, _I]),
+    "hbpc_batch_set_state": (_I, [_CTX, _I, _P, _I]),
+    "hbpc_batch_get_state": (_I, [_CTX, _I, _P, _I]),
+    "hbpc_batch_node_coords": (_I, [_CTX, _I, _P]),
+    "hbpc_batch_eval_R1": (_I, [_CTX, _I, _P]),
+    "hbpc_batch_step": (_I, [_CTX, _I]),
+    "hbpc_batch_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
+    "hbpc_batch_profile_enable": (_I, [_CTX, _I]),
+    "hbpc_batch_last_error": (ctypes.c_char_p, [_CTX]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -163,14 +177,16 @@ class Context:
     """One HBPC-DGSEM problem on the current CUDA device."""
 
     def __init__(self, dim, n, lo, hi, N, law=LAW_ADVECTION, flux=FLUX_GLOBAL_LF,
-                 a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, nodes=NODES_LOBATTO,
+                 a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, nu=0.0, eta_br2=0.0,
+                 nodes=NODES_LOBATTO,
                  q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0,
                  tol_gmres_rel=1e-5, gmres_restart=100, gmres_max_iter=7000,
                  newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64, stream=None):
         pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
         self.mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                          (ctypes.c_double * 3)(*pad(hi, 1.0)))
-        self.phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale)
+        self.phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
+                            nu, eta_br2)
         self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel,
                              gmres_restart, gmres_max_iter, newton_max_iter, pc, precision)
         self.N, self.dim, self.nodes = N, dim, nodes
@@ -274,22 +290,31 @@ class Context:
         params = np.ascontiguousarray(params, dtype=np.float32)
         self._c(_lib.hbpc_pc_model_set(self._ctx, params.ctypes.data))
 
-    def pc_loss_grad(self, F, J, c12, X):
-        F, J, c12, X = (np.ascontiguousarray(a, dtype=np.float32) for a in (F, J, c12, X))
-        B, P = X.shape[0], X.shape[1]
-        loss = ctypes.c_double(0.0)
+    def pc_loss_grad(self, F, J, c12, X=None, loss="probe"):
+        # loss and gradients for host inputs; J is the element Jacobian for the
+        # probe loss and the target block inverse for the inverse loss
+        kind = PC_LOSS[loss]
+        F, J, c12 = (np.ascontiguousarray(a, dtype=np.float32) for a in (F, J, c12))
+        B = F.shape[0]
+        P = 1
+        xp = None
+        if X is not None:
+            X = np.ascontiguousarray(X, dtype=np.float32)
+            P = X.shape[1]
+            xp = X.ctypes.data
+        out = ctypes.c_double(0.0)
         grads = np.zeros(self.pc_model_info()["n_params"], dtype=np.float32)
-        self._c(_lib.hbpc_pc_loss_grad(self._ctx, B, P, F.ctypes.data, J.ctypes.data, c12.ctypes.data,
-                                       X.ctypes.data, ctypes.addressof(loss), grads.ctypes.data))
-        return loss.value, grads
+        self._c(_lib.hbpc_pc_loss_grad(self._ctx, kind, B, P, F.ctypes.data, J.ctypes.data, c12.ctypes.data,
+                                       xp, ctypes.addressof(out), grads.ctypes.data))
+        return out.value, grads
 
     def pc_collect(self, samples_per_newton, capacity):
         self._c(_lib.hbpc_pc_collect(self._ctx, samples_per_newton, capacity))
 
-    def pc_train(self, iters, batch=256, probes=4, lr=1e-3, seed=0):
+    def pc_train(self, iters, batch=256, probes=4, lr=1e-3, seed=0, loss="probe"):
         l0, l1 = ctypes.c_double(0.0), ctypes.c_double(0.0)
-        self._c(_lib.hbpc_pc_train(self._ctx, iters, batch, probes, lr, seed, ctypes.addressof(l0),
-                                   ctypes.addressof(l1)))
+        self._c(_lib.hbpc_pc_train(self._ctx, PC_LOSS[loss], iters, batch, probes, lr, seed,
+                                   ctypes.addressof(l0), ctypes.addressof(l1)))
         return l0.value, l1.value
 
     def newton_solve(self, b, alpha1, alpha2, W0, W_out, S_out=None):
@@ -313,3 +338,93 @@ class Context:
         cnt = np.zeros(len(PHASES), dtype=np.int64)
         self._c(_lib.hbpc_profile_get(self._ctx, _ptr(ms), cnt.ctypes.data, len(PHASES)))
         return {ph: (float(ms[i]), int(cnt[i])) for i, ph in enumerate(PHASES)}
+
+
+class Batch:
+    """A batch of independent instances (own mesh, degree N and viscosity each)
+    advanced together; see hbpc_batch_create in include/hbpc.h."""
+
+    def __init__(self, dim, meshes, Ns, nus=None, law=LAW_BURGERS, flux=FLUX_GLOBAL_LF,
+                 a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, eta_br2=0.0, nodes=NODES_LOBATTO,
+                 q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0, tol_gmres_rel=1e-5,
+                 gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64):
+        """meshes: list of (n, lo, hi) per instance."""
+        pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
+        k = len(meshes)
+        nus = [0.0] * k if nus is None else list(nus)
+        self.M = (Mesh * k)()
+        self.Ph = (Physics * k)()
+        for i, (n, lo, hi) in enumerate(meshes):
+            self.M[i] = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
+                             (ctypes.c_double * 3)(*pad(hi, 1.0)))
+            self.Ph[i] = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
+                                 float(nus[i]), eta_br2)
+        self.Nv = (ctypes.c_int * k)(*Ns)
+        self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel, gmres_restart,
+                             gmres_max_iter, newton_max_iter, pc, precision)
+        self.dim, self.n_inst, self.Ns = dim, k, list(Ns)
+        self.nv = (dim + 2) if law == LAW_EULER else 1
+        self.meshes = [tuple(m) for m in meshes]
+        self._b = _CTX()
+        st = _lib.hbpc_batch_create(ctypes.byref(self._b), k, ctypes.addressof(self.M), ctypes.addressof(self.Nv),
+                                    nodes, ctypes.addressof(self.Ph), ctypes.byref(self.solver))
+        if st != OK:
+            raise HBPCError(st, (_lib.hbpc_batch_last_error(None) or b"").decode())
+
+    def _c(self, st):
+        if st != OK:
+            raise HBPCError(st, (_lib.hbpc_batch_last_error(self._b) or b"").decode())
+
+    def close(self):
+        if self._b:
+            _lib.hbpc_batch_destroy(self._b)
+            self._b = _CTX()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def groups(self):
+        return _lib.hbpc_batch_groups(self._b)
+
+    def shape(self, i):
+        n = self.meshes[i][0]
+        nE = int(np.prod(n[:self.dim]))
+        return (nE, self.nv) + (self.Ns[i] + 1,) * self.dim
+
+    def ndof(self, i):
+        return int(_lib.hbpc_batch_ndof(self._b, i))
+
+    def node_coords(self, i):
+        shp = self.shape(i)
+        out = np.zeros((self.dim, shp[0]) + shp[2:])
+        self._c(_lib.hbpc_batch_node_coords(self._b, i, out.ctypes.data))
+        return [out[m] for m in range(self.dim)]
+
+    def set_state(self, i, w):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        assert w.size == self.ndof(i)
+        self._c(_lib.hbpc_batch_set_state(self._b, i, w.ctypes.data, 0))
+
+    def get_state(self, i):
+        out = np.zeros(self.shape(i))
+        self._c(_lib.hbpc_batch_get_state(self._b, i, out.ctypes.data, 0))
+        return out
+
+    def eval_R1(self, i):
+        out = np.zeros(self.shape(i))
+        self._c(_lib.hbpc_batch_eval_R1(self._b, i, out.ctypes.data))
+        return out
+
+    def step(self, n=1):
+        self._c(_lib.hbpc_batch_step(self._b, n))
+
+    def stats(self):
+        s = Stats()
+        self._c(_lib.hbpc_batch_get_stats(self._b, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def profile(self, enable=True):
+        self._c(_lib.hbpc_batch_profile_enable(self._b, 1 if enable else 0))

@@ -91,6 +91,42 @@ def test_learned_pc_loss_and_gradients_match_oracle(hb):
     ctx.close()
 
 
+def test_learned_pc_inverse_loss_matches_oracle(hb):
+    """The inverse-regression loss |M~ - T|_F^2 / B and its gradients against
+    the FP64 oracle (same BF16-exact parameters as the probe-loss test)."""
+    ctx = hb.Context(2, (4, 4), (-1, -1), (1, 1), 2, law=hb.LAW_EULER, flux=hb.FLUX_RUSANOV, dt=0.05,
+                     pc=hb.PC_LEARNED)
+    info = ctx.pc_model_info()
+    nb = 36
+    din, dout = nb + 2, nb * nb
+    rng = np.random.default_rng(17)
+    p = mlp.init_params(info["d_in_padded"], info["hidden"], dout, seed=4, out_scale=0.5)
+    p["b1"] = 0.1 * rng.standard_normal(info["hidden"])
+    p["b2"] = 0.1 * rng.standard_normal(info["hidden"])
+    p["b3"] = 0.01 * rng.standard_normal(dout)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        p[k] = torch.from_numpy(p[k]).to(torch.bfloat16).to(torch.float64).numpy()
+    p["W1"][:, din:] = 0.0
+    ctx.pc_model_set(layout(info, p, info["d_in_padded"]))
+    B = 16
+    F = np.zeros((B, info["d_in_padded"]))
+    F[:, :din] = rng.standard_normal((B, din))
+    F = torch.from_numpy(F).to(torch.bfloat16).to(torch.float64).numpy()
+    T = np.eye(nb)[None] + 0.2 * rng.standard_normal((B, nb, nb))
+    c12 = np.zeros((B, 2))
+    act = mlp.forward(p, F)
+    L_ref, dO = mlp.inverse_loss(act["O"], T, nb)
+    g_ref = mlp.backward(p, act, dO)
+    L_gpu, g_flat = ctx.pc_loss_grad(F, T.transpose(0, 2, 1), c12, None, loss="inverse")
+    g_gpu = unlayout(info, g_flat, info["d_in_padded"], dout)
+    assert abs(L_gpu - L_ref) <= 5e-2 * abs(L_ref), (L_gpu, L_ref)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = g_ref[k] if k != "W1" else g_ref[k][:, :info["d_in_padded"]]
+        err = np.linalg.norm(g_gpu[k] - ref) / np.linalg.norm(ref)
+        assert err <= 5e-2, (k, err)
+    ctx.close()
+
+
 def euler_stage(hb, pc, precision, dt=0.08, n=(6, 5)):
     ctx = hb.Context(2, n, (-1, -1), (1, 1), 2, law=hb.LAW_EULER, flux=hb.FLUX_RUSANOV, dt=dt,
                      tol_newton_rel=1e-13, tol_newton_abs=1e-13, tol_gmres_rel=1e-6, gmres_restart=200,

@@ -169,6 +169,31 @@ def test_bjext_apply_parity(hb, law, dim, N, family, flux):
     ctx.close()
 
 
+@pytest.mark.parametrize("law,dim,N,flux", [(laws.ADVECTION, 2, 5, "lf"), (laws.EULER, 2, 4, "rusanov"),
+                                            (laws.BURGERS, 2, 3, "lf")])
+def test_bjext_apply_parity_mixed(hb, law, dim, N, flux):
+    """In the mixed mode the blocks S_e, their Gauss-Jordan inverses and the
+    apply are FP32: the result against the oracle's FP64 construction is within
+    FP32 rounding amplified by the blocks' condition numbers (1e-4 here)."""
+    dt = 0.04
+    ctx, disc = pair(hb, law, dim, N, mesh_for(dim), LOBATTO, flux, lo=(-1, -1, -1), hi=(1, 1, 1), dt=dt,
+                     pc=hb.PC_BJEXT, precision=hb.PREC_MIXED)
+    rng = np.random.default_rng(32)
+    if law == laws.EULER:
+        W = euler_field(disc, 6, amp=0.02)
+    else:
+        W = 0.5 + 0.2 * rng.standard_normal(disc.shape)
+    X = np.concatenate([W.ravel(), dgsem.R1(disc, W).ravel()])
+    v = rng.standard_normal(2 * disc.ndof)
+    sysm = newton.StageSystem(disc, W, 1.0, 1.0, dt)
+    ref = newton.BJExt(sysm, W)(v)
+    out = torch.empty(2 * disc.ndof, dtype=torch.float64, device="cuda")
+    ctx.eval_pc(1.0, 1.0, dev(X), dev(v), out)
+    err = rel(host(out), ref)
+    assert err <= 1e-4, err
+    ctx.close()
+
+
 @pytest.mark.parametrize("law,dim,flux,alphas,pc", [
     (laws.ADVECTION, 2, "lf", (0.5, 1.0 / 6.0), "none"), (laws.ADVECTION, 1, "lf", (1.0, 1.0), "none"),
     (laws.BURGERS, 1, "rusanov", (1.0, 1.0), "none"), (laws.EULER, 2, "rusanov", (1.0 / 6.0, 1.0 / 54.0), "none"),

@@ -52,6 +52,8 @@ def test_basis_matches_oracle(hbpc, N, family, code):
     (dict(N=0), 1), (dict(N=8), 1), (dict(q=5), 1), (dict(dt=0.0), 1), (dict(dt=-1.0), 1),
     (dict(kmax=-1), 1), (dict(gmres_restart=0), 1), (dict(gmres_max_iter=0), 1),
     (dict(eps=0.0), 1), (dict(law=7), 1), (dict(nodes=3), 1), (dict(dim=4), 1),
+    (dict(nu=-0.1), 1), (dict(nu=float("nan")), 1), (dict(nu=0.01, eta_br2=float("inf")), 1),
+    (dict(nu=0.01, law=2), 7),
 ])
 def test_invalid_arguments_rejected(hbpc, kw, code):
     args = dict(dim=2, n=(2, 2), lo=(0, 0), hi=(1, 1), N=3)
@@ -66,3 +68,17 @@ def test_invalid_mesh_rejected(hbpc):
         hbpc.Context(2, (0, 2), (0, 0), (1, 1), 3)
     with pytest.raises(hbpc.HBPCError):
         hbpc.Context(2, (2, 2), (0, 1), (1, 1), 3)
+
+
+def test_batch_invalid_arguments_rejected(hbpc):
+    """Batch creation checks its arguments before touching the device."""
+    meshes = [((4, 4), (0, 0), (1, 1)), ((5, 3), (0, 0), (1, 1))]
+    with pytest.raises(hbpc.HBPCError) as ei:          # a bad N in one instance
+        hbpc.Batch(2, meshes, [3, 0], nus=[0.01, 0.02])
+    assert ei.value.status == 1
+    with pytest.raises(hbpc.HBPCError) as ei:          # negative viscosity
+        hbpc.Batch(2, meshes, [3, 4], nus=[0.01, -0.02])
+    assert ei.value.status == 1
+    with pytest.raises(hbpc.HBPCError) as ei:          # the learned preconditioner
+        hbpc.Batch(2, meshes, [3, 4], nus=[0.01, 0.02], pc=hbpc.PC_LEARNED)
+    assert ei.value.status == 7

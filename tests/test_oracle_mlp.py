@@ -71,3 +71,33 @@ def test_training_reduces_probe_loss():
         L, dO = mlp.probe_loss(act["O"], U, X, nb)
         p = opt.step(p, mlp.backward(p, act, dO))
     assert loss_of(p, F, U, X, nb) < 0.2 * L0
+
+
+def test_inverse_loss_zero_at_target_and_fd_gradient():
+    rng = np.random.default_rng(11)
+    B, nb = 4, 3
+    T = np.eye(nb)[None] + 0.4 * rng.standard_normal((B, nb, nb))
+    L, dO = mlp.inverse_loss((T - np.eye(nb)[None]).reshape(B, nb * nb), T, nb)
+    assert L < 1e-28 and np.abs(dO).max() < 1e-14
+    O = rng.standard_normal((B, nb * nb))
+    L, dO = mlp.inverse_loss(O, T, nb)
+    h = 1e-6
+    for _ in range(8):
+        i, j = rng.integers(0, B), rng.integers(0, nb * nb)
+        Op, Om = O.copy(), O.copy()
+        Op[i, j] += h
+        Om[i, j] -= h
+        fd = (mlp.inverse_loss(Op, T, nb)[0] - mlp.inverse_loss(Om, T, nb)[0]) / (2 * h)
+        assert abs(fd - dO[i, j]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_inverse_loss_equals_probe_loss_with_unit_probes():
+    """With S = I the probe loss over the complete set of unit probes is
+    |M~ - I|_F^2 / (B nb), the inverse loss against T = I divided by nb."""
+    rng = np.random.default_rng(12)
+    B, nb = 3, 4
+    O = rng.standard_normal((B, nb * nb))
+    X = np.broadcast_to(np.eye(nb)[None], (B, nb, nb)).copy()     # probes p = unit vectors
+    Lp, _ = mlp.probe_loss(O, X, X, nb)
+    Li, _ = mlp.inverse_loss(O, np.broadcast_to(np.eye(nb)[None], (B, nb, nb)), nb)
+    assert abs(Lp * nb - Li) <= 1e-12 * Li

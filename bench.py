@@ -9,6 +9,7 @@ stage solves).  Metric: DOF-timesteps/s = n_dof x steps / device seconds.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
   python bench.py --workload burgers_batch   (256 viscous Burgers instances, below)
+  python bench.py --workload euler_vortex    (learned vs BJ_ext vs plain GMRES, below)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path has no data-path collective), value = sum over ranks / max time.
@@ -171,6 +172,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         ctx.step(1)
+    tuning = ctx.autotune()        # launch shapes of the Krylov reductions and the PC apply
     torch.cuda.synchronize()
     ctx.reset_stats()
     clocks = Clocks(local)
@@ -270,7 +272,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if PRECISION[0] == "fp64" else "f64 state/Newton, f32 Krylov",
             "data": "synthetic",
-            "config": config_dict(dt, {"parallelism": "replicas" if world > 1 else "single"}),
+            "config": config_dict(dt, {"parallelism": "replicas" if world > 1 else "single",
+                                       "autotuned": tuning}),
             "r1_evals_per_s": r1_per_s, "l2_error_vs_exact": err,
             "gmres_its_per_step": stats["gmres_its"] / args.steps,
             "newton_its_per_step": stats["newton_its"] / args.steps,
@@ -366,6 +369,7 @@ def run_batch(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         b.step(1)
+    tuning = b.autotune()          # launch shapes per group, on the warmed-up state
     torch.cuda.synchronize()
     st0 = b.stats()
     clocks = Clocks(local)
@@ -411,6 +415,7 @@ def run_batch(args):
                        "flux": "Rusanov", "eps_newton": BATCH["tol_newton_rel"], "eps_gmres": BATCH["tol_gmres_rel"],
                        "gmres_restart": BATCH["gmres_restart"], "precision": "mixed",
                        "timing": "host clock between device synchronisations (groups run on their own streams)",
+                       "autotuned": tuning,
                        "l2_between_steps": "flushed (256 MB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "r1_evals_per_s": (d["r1_evals"] + d["r2_evals"]) / t_sec,
@@ -424,6 +429,129 @@ def run_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+VORTEX = dict(n=(128, 128), lo=(-10.0, -10.0), hi=(10.0, 10.0), N=4, q=6, kmax=2, cfl=10.0,
+              tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3, gmres_restart=100,
+              gmres_max_iter=3000, newton_max_iter=30, collect_per_newton=1024, collect_capacity=32768,
+              train_inverse_its=20000, train_lr=1e-3, train_batch=256,
+              train_probe=((8000, 1e-5), (8000, 1e-5), (8000, 5e-6), (8000, 2e-6)), train_probes=8)
+
+
+def vortex_dt():
+    """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v| + c of the
+    free stream plus the vortex's peak velocity (about 0.5 c_inf)."""
+    g = 1.4
+    lam = (0.5 * np.sqrt(g) + np.sqrt(g), np.sqrt(g))
+    h = [(VORTEX["hi"][m] - VORTEX["lo"][m]) / VORTEX["n"][m] for m in range(2)]
+    return VORTEX["cfl"] / sum(lam[m] * (VORTEX["N"] + 1) / h[m] for m in range(2))
+
+
+def run_vortex(args):
+    """2-D Euler isentropic vortex (strength 5, Mach 0.5) on [-10, 10]^2, 128 x 128
+    elements, N = 4, Rusanov, HBPC(6, 2), CFL 10, Newton tol 1e-10, mixed
+    precision.  The learned block preconditioner is trained on the GPU on
+    (features, exact block inverse) samples of the method's own BJ_ext Newton
+    iterations during the warm-up steps; then the same time step is taken with
+    the learned preconditioner, with BJ_ext, and with plain GMRES (no
+    preconditioner), each against the FP64-state BJ_ext result."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    dt = vortex_dt()
+
+    def ctx(pc):
+        return hbpc.Context(2, VORTEX["n"], VORTEX["lo"], VORTEX["hi"], VORTEX["N"], law=hbpc.LAW_EULER,
+                            flux=hbpc.FLUX_RUSANOV, q=VORTEX["q"], kmax=VORTEX["kmax"], dt=dt,
+                            tol_newton_rel=VORTEX["tol_newton_rel"], tol_newton_abs=VORTEX["tol_newton_abs"],
+                            tol_gmres_rel=VORTEX["tol_gmres_rel"], gmres_restart=VORTEX["gmres_restart"],
+                            gmres_max_iter=VORTEX["gmres_max_iter"], newton_max_iter=VORTEX["newton_max_iter"],
+                            pc=pc, precision=hbpc.PREC_MIXED)
+    gen = ctx(hbpc.PC_BJEXT)
+    gen.pc_collect(VORTEX["collect_per_newton"], VORTEX["collect_capacity"])
+    gen.set_state(inputs.isentropic_vortex(gen.node_coords()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gen.step(max(1, args.warmup))
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    w_start = gen.get_state()
+    gen.pc_collect(0, 0)
+    gen.pc_model_init(seed=1, out_scale=1e-2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l0, l1 = gen.pc_train(iters=VORTEX["train_inverse_its"], batch=VORTEX["train_batch"], probes=4,
+                          lr=VORTEX["train_lr"], seed=11, loss="inverse")
+    # then the probe loss |M~ S x - x|^2, what the preconditioner has to achieve
+    probe_losses = []
+    for k, (its, lr) in enumerate(VORTEX["train_probe"]):
+        pa, pb = gen.pc_train(iters=its, batch=VORTEX["train_batch"], probes=VORTEX["train_probes"], lr=lr,
+                              seed=50 + k, loss="probe")
+        probe_losses.append((pa, pb))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    params = gen.pc_model_get()
+    ndof = gen.ndof
+    gen.close()
+
+    def timed(pc, steps, params=None):
+        c = ctx(pc)
+        if params is not None:
+            c.pc_model_set(params)
+        c.set_state(w_start)
+        ok, ms = True, 0.0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            try:
+                c.step(1)
+            except hbpc.HBPCError as e:
+                ok = str(e)[:80]
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            if ok is not True:
+                break
+        st = c.stats()
+        w = c.get_state()
+        c.close()
+        return {"ok": ok, "ms_per_step": ms / steps, "value": ndof * steps / (ms / 1000.0) if ok is True else 0.0,
+                "gmres_its_per_step": st["gmres_its"] / steps, "newton_its_per_step": st["newton_its"] / steps,
+                "launches": int(st["launches"])}, w
+
+    r_bj, w_bj = timed(hbpc.PC_BJEXT, args.steps)
+    r_ln, w_ln = timed(hbpc.PC_LEARNED, args.steps, params)
+    r_pl, w_pl = timed(hbpc.PC_NONE, 1)
+    # every result against the BJ_ext run (the same Newton tolerance fixes the answer)
+    for r, w in ((r_ln, w_ln), (r_pl, w_pl)):
+        if r["ok"] is True:
+            ref = w_bj if r is r_ln else None
+            if ref is not None:
+                r["rel_l2_vs_bjext"] = float(np.linalg.norm(w - ref) / np.linalg.norm(ref))
+    head = r_ln if r_ln["ok"] is True else r_bj
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov, bf16 network",
+            "data": "synthetic",
+            "config": {"workload": "2d_euler_isentropic_vortex_128x128_N4_HBPC(6,2)_CFL10_Rusanov",
+                       "value_is": "learned preconditioner" if r_ln["ok"] is True else
+                                   "BJ_ext (the learned preconditioner did not converge)",
+                       "dt": dt, "eps_newton": VORTEX["tol_newton_rel"], "eps_gmres": VORTEX["tol_gmres_rel"],
+                       "gmres_restart": VORTEX["gmres_restart"], "gmres_max_iter": VORTEX["gmres_max_iter"],
+                       "newton_max_iter": VORTEX["newton_max_iter"], "precision": "mixed",
+                       "training": {"data_steps": max(1, args.warmup), "data_s": round(t_data, 2),
+                                    "samples_per_newton": VORTEX["collect_per_newton"],
+                                    "inverse_regression": {"iters": VORTEX["train_inverse_its"],
+                                                           "loss_first": l0, "loss_last": l1},
+                                    "probe": {"rounds": [list(r) for r in VORTEX["train_probe"]],
+                                              "probes": VORTEX["train_probes"],
+                                              "loss_first_last": probe_losses},
+                                    "train_s": round(t_train, 2)}},
+            "gpu_launches": head["launches"], "learned": r_ln, "bjext": r_bj, "plain_gmres": r_pl}
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -461,7 +589,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
-    ap.add_argument("--workload", default="advection2d", choices=["advection2d", "burgers_batch"],
+    ap.add_argument("--workload", default="advection2d", choices=["advection2d", "burgers_batch", "euler_vortex"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances")
     ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
@@ -471,6 +599,8 @@ def main():
         run_reference(args)
     elif args.workload == "burgers_batch":
         run_batch(args)
+    elif args.workload == "euler_vortex":
+        run_vortex(args)
     else:
         run_ours(args)
 

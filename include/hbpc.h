@@ -288,6 +288,24 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
  * arithmetic roofline of the FP64 kernels.  Allocates and frees a small buffer. */
 hbpc_status hbpc_fp64_fma_peak(double* gflops);
 
+/* Launch-shape autotuner (no counterpart in the paper): times, on the
+ * context's own buffers, the candidate shapes of the Krylov reductions (blocks
+ * = 1..4 x SMs; the CGS2 column at j = m/2) and of the block-preconditioner
+ * apply (1, 2, 4, 8 or 16 elements per block, at most 256 threads), median of
+ * 7 launches each, and
+ * keeps the fastest.  Call it before stepping or between steps; the result
+ * changes only the summation order of the reductions.  out may be NULL. */
+typedef struct {
+  int krylov_blocks;        /* chosen blocks of the Krylov reductions */
+  double krylov_us;         /* its time per CGS2 column (microseconds) */
+  double krylov_us_default; /* the same at the creation-time shape */
+  int pc_elems_per_block;   /* chosen elements per block of the apply */
+  double pc_us;             /* its time per apply (0 without a block preconditioner) */
+  double pc_us_default;
+  int cooperative_cgs;      /* 1: CGS2 runs as one cooperative launch */
+} hbpc_tuning;
+hbpc_status hbpc_autotune(hbpc_ctx* ctx, hbpc_tuning* out);
+
 /* ---- Batches of independent instances (no counterpart in the paper) -----
  * n_inst problems that share dim, law, flux, gamma, eps, lf_scale, a, eta_br2,
  * the node family and the solver settings (HBPC(q, k_max), dt, tolerances,
@@ -320,6 +338,8 @@ hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps);
 /* Counters summed over groups (steps, t: the maximum). */
 hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out);
 hbpc_status hbpc_batch_profile_enable(hbpc_batch* b, int enable);
+/* hbpc_autotune for every group; out: n_out >= hbpc_batch_groups entries or NULL. */
+hbpc_status hbpc_batch_autotune(hbpc_batch* b, hbpc_tuning* out, int n_out);
 /* Message of the last failure of the batch (NULL: of the last failed create). */
 const char* hbpc_batch_last_error(const hbpc_batch* b);
 

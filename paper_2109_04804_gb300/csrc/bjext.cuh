@@ -22,22 +22,21 @@ namespace hbpc {
 // derivative with respect to the element's own trace (the neighbour is frozen).
 // A BR2 viscous term adds nu times its element-diagonal block along the line
 // (a constant table, the same for every element).
-template <int LAW, int DIM, int P, bool LGL>
-__global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ W,
-                                                     double* __restrict__ Jout,
-                                                     const DGParams<double> prm) {
-  using L = typename LawOf<LAW, DIM, double>::type;
+template <int LAW, int DIM, int P, bool LGL, typename T = double>
+__global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ W, T* __restrict__ Jout,
+                                                     const DGParams<T> prm) {
+  using L = typename LawOf<LAW, DIM, T>::type;
   constexpr int NV = L::NV, NN = ipow(P, DIM), NB = NV * NN;
   const int e = blockIdx.x;
   if (e >= prm.nE) return;
-  double* J = Jout + size_t(e) * NB * NB;
-  __shared__ double sw[NB];
-  for (int t = threadIdx.x; t < NB; t += blockDim.x) sw[t] = W[size_t(e) * NB + t];
-  for (size_t t = threadIdx.x; t < size_t(NB) * NB; t += blockDim.x) J[t] = 0.0;
+  T* J = Jout + size_t(e) * NB * NB;
+  __shared__ T sw[NB];
+  for (int t = threadIdx.x; t < NB; t += blockDim.x) sw[t] = T(W[size_t(e) * NB + t]);
+  for (size_t t = threadIdx.x; t < size_t(NB) * NB; t += blockDim.x) J[t] = T(0);
   __syncthreads();
   // the instance of this element (batches): its mesh and scales; padding
   // elements between instances keep J = 0
-  const InstGeo<double> geo = inst_geo(prm, e / Geo<DIM, P>::EPB);
+  const InstGeo<T> geo = inst_geo(prm, e / Geo<DIM, P>::EPB);
   const int el = e - geo.e0;
   if (el >= geo.nE) return;
   int ec[3];
@@ -46,25 +45,25 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
   ec[2] = el / (geo.n[0] * geo.n[1]);
   for (int col = threadIdx.x; col < NB; col += blockDim.x) {
     const int u = col / NN, q = col - u * NN;
-    double* Jc = J + size_t(col) * NB;
+    T* Jc = J + size_t(col) * NB;
     int qi[3] = {q % P, (q / P) % P, q / (P * P)};
-    double wq[NV], eu[NV];
+    T wq[NV], eu[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { wq[v] = sw[v * NN + q]; eu[v] = (v == u) ? 1.0 : 0.0; }
+    for (int v = 0; v < NV; ++v) { wq[v] = sw[v * NN + q]; eu[v] = (v == u) ? T(1) : T(0); }
 #pragma unroll
     for (int m = 0; m < DIM; ++m) {
       const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
       const int b0 = q - qi[m] * st;
-      double a[NV];
+      T a[NV];
       if constexpr (L::LINEAR) {
         // a_m is folded into Dvol unless a viscous term is present
-        const double am = prm.visc ? prm.a[m] : 1.0;
+        const T am = prm.visc ? prm.a[m] : T(1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) a[v] = am * eu[v];
       } else {
         L::jvp(wq, eu, m, a, prm);
       }
-      const double hs = geo.hs[m];
+      const T hs = geo.hs[m];
       // volume: output node r = b0 + l*st receives Dvol[m][l][q_m] * a
       for (int l = 0; l < P; ++l)
 #pragma unroll
@@ -73,33 +72,33 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
       // (a second-derivative operator: two factors 2/h)
       if constexpr (NV == 1) {
         if (prm.visc)
-          for (int l = 0; l < P; ++l) Jc[b0 + l * st] += geo.nu * hs * hs * prm.vloc[(m * P + l) * P + qi[m]];
+          for (int l = 0; l < P; ++l) Jc[b0 + l * st] += geo.nu * hs * hs * T(prm.vloc[(m * P + l) * P + qi[m]]);
       }
       // faces: own traces at the - and + face of the line through q
-      double Ap[NV];
+      T Ap[NV];
       L::jvp(wq, eu, m, Ap, prm);   // dF^m/dw at w_q applied to e_u (used for Lobatto)
       for (int side = 0; side < 2; ++side) {
-        const double lq = side ? prm.lp[qi[m]] : prm.lm[qi[m]];   // d(own trace)/d(w_q)
-        if (lq == 0.0) continue;
+        const T lq = side ? prm.lp[qi[m]] : prm.lm[qi[m]];   // d(own trace)/d(w_q)
+        if (lq == T(0)) continue;
         // own trace t_o and neighbour trace t_n at this face point
-        double to[NV], tn[NV];
+        T to[NV], tn[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { to[v] = 0.0; tn[v] = 0.0; }
+        for (int v = 0; v < NV; ++v) { to[v] = T(0); tn[v] = T(0); }
         int nc[3] = {ec[0], ec[1], ec[2]};
         nc[m] += side ? 1 : -1;
         if (nc[m] < 0) nc[m] += geo.n[m];
         if (nc[m] >= geo.n[m]) nc[m] -= geo.n[m];
         const int en = geo.e0 + nc[0] + geo.n[0] * (nc[1] + geo.n[1] * nc[2]);
         for (int i = 0; i < P; ++i) {
-          const double lo = side ? prm.lp[i] : prm.lm[i];
-          const double ln = side ? prm.lm[i] : prm.lp[i];
+          const T lo = side ? prm.lp[i] : prm.lm[i];
+          const T ln = side ? prm.lm[i] : prm.lp[i];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             to[v] += lo * sw[v * NN + b0 + i * st];
-            tn[v] += ln * W[(size_t(en) * NV + v) * NN + b0 + i * st];
+            tn[v] += ln * T(W[(size_t(en) * NV + v) * NN + b0 + i * st]);
           }
         }
-        double A[NV], kap[NV];
+        T A[NV], kap[NV];
         if (LGL) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) A[v] = Ap[v];
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
           L::jvp(to, eu, m, A, prm);
         }
         if (prm.rusanov) {
-          const double c = 0.5 * fmax(L::speed(to, m, prm), L::speed(tn, m, prm));
+          const T c = T(0.5) * fmax(L::speed(to, m, prm), L::speed(tn, m, prm));
 #pragma unroll
           for (int v = 0; v < NV; ++v) kap[v] = c;
         } else {
@@ -117,11 +116,11 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
         // + face: f = 1/2 (F(t_o) + F(t_n)) + kap (t_o - t_n)      -> df/dt_o = A/2 + kap
         // - face: f = -(1/2 (F(t_n) + F(t_o)) + kap (t_n - t_o))  -> df/dt_o = -A/2 + kap
         for (int l = 0; l < P; ++l) {
-          const double lift = hs * (side ? prm.sp[m][l] : prm.sm[m][l]);
-          if (lift == 0.0) continue;
+          const T lift = hs * (side ? prm.sp[m][l] : prm.sm[m][l]);
+          if (lift == T(0)) continue;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            const double d = (side ? 0.5 : -0.5) * A[v] + kap[v] * eu[v];
+            const T d = (side ? T(0.5) : T(-0.5)) * A[v] + kap[v] * eu[v];
             Jc[v * NN + b0 + l * st] += lift * lq * d;
           }
         }

@@ -99,16 +99,21 @@ __global__ void __launch_bounds__(kInstThreads) k_inst_sqnorms(const double* __r
   }
 }
 
-// Batches: zero both halves of v on the instances whose active flag is 0
-// (their Newton iteration has converged; blockIdx.y = instance).
-__global__ void k_inst_mask(double* __restrict__ v, size_t half, const long long* __restrict__ range,
-                            const int* __restrict__ active) {
+// Batches: scale both halves of instance i's entries of a vector by scale[i]
+// (blockIdx.y = instance).  The vector is column *col + col_offset of v with
+// stride ld (v itself if col is null); nothing is done when *skip != 0.
+template <typename T>
+__global__ void k_inst_scale(T* __restrict__ v, size_t half, const long long* __restrict__ range,
+                             const double* __restrict__ scale, const int* col, int col_offset, size_t ld,
+                             const int* skip) {
+  if (skip && *skip) return;
+  T* base = col ? v + size_t(*col + col_offset) * ld : v;
   const int i = blockIdx.y;
-  if (active[i]) return;
+  const T sc = T(scale[i]);
   const long long a = range[2 * i], cnt = range[2 * i + 1];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < cnt; t += (long long)gridDim.x * blockDim.x) {
-    v[a + t] = 0.0;
-    v[half + a + t] = 0.0;
+    base[a + t] *= sc;
+    base[half + a + t] *= sc;
   }
 }
 
@@ -186,7 +191,8 @@ struct hbpc_ctx {
   int* d_blk = nullptr;                    // operator block -> instance
   long long* d_irange = nullptr;           // per instance: first value, count (one half)
   double* d_inrm = nullptr;                // per-instance squared norms
-  int* d_active = nullptr;                 // per-instance Newton activity
+  double* d_iscale = nullptr;              // per-instance row scaling of the GMRES system
+  std::vector<double> h_iscale;
   std::vector<double> h_inrm;
   std::vector<int> h_active;
   // BJ_ext preconditioner (Sec. 3.2.3)
@@ -237,6 +243,9 @@ struct hbpc_ctx {
   hbpc_stats stats{};
   std::string err;
   int nblocks = 0;
+  bool coop = false;        // CGS2 as one cooperative launch (all blocks resident)
+  int coop_max_blocks = 0;  // resident blocks of the cooperative kernel
+  int sms = 0;
   int verbose = 0;          // HBPC_VERBOSE=1: Newton/GMRES trace on stderr
   Prof prof;
 };
@@ -639,8 +648,13 @@ hbpc_status lp_collect(hbpc_ctx* x, const double* W, double c1, double c2) {
   const int count = std::min<int>(L.per_newton, int(x->nE));
   const int stride = std::max<int>(1, int(x->nE) / count);
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-           k_mlp_collect<<<count, 128, 0, x->stream>>>(W, x->Jpc, int(x->nE), L.nb, c1, c2, count, stride, L.offset,
-                                                        L.next, L.cap, L.featbuf, L.Jbuf, L.cbuf));
+           x->sol.precision == HBPC_PREC_MIXED
+               ? k_mlp_collect<float><<<count, 128, 0, x->stream>>>(W, x->Jf, int(x->nE), L.nb, c1, c2, count,
+                                                                     stride, L.offset, L.next, L.cap, L.featbuf,
+                                                                     L.Jbuf, L.cbuf)
+               : k_mlp_collect<double><<<count, 128, 0, x->stream>>>(W, x->Jpc, int(x->nE), L.nb, c1, c2, count,
+                                                                      stride, L.offset, L.next, L.cap, L.featbuf,
+                                                                      L.Jbuf, L.cbuf));
   HBPC_LAUNCH_CK(x, "k_mlp_collect");
   L.last_off = L.offset; L.last_row = L.next; L.last_count = count;
   L.offset = (L.offset + 1) % std::max(1, stride);
@@ -657,24 +671,23 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
       x->pc_c2 == c2)
     return HBPC_OK;
   const size_t nb = size_t(x->nb);
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(x->prm, W, x->Jpc, x->stream));
+  const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
+  // J_i in the precision of the apply: FP32 in the mixed mode (the blocks only
+  // precondition the FP32 Krylov loop), FP64 otherwise
+  if (mixed) HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble_f(x->prmf, W, x->Jf, x->stream));
+  else HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(x->prm, W, x->Jpc, x->stream));
   hbpc_status s0;
   if (collecting && (s0 = lp_collect(x, W, c1, c2)) != HBPC_OK) return s0;
   if (x->sol.pc == HBPC_PC_LEARNED) {   // M~ from the network instead of the LU
     if (collecting) x->lp.targets = false;   // no exact inverse for these rows
     if ((s0 = lp_infer(x, W, c1, c2)) != HBPC_OK) return s0;
-    if (x->sol.precision == HBPC_PREC_MIXED &&
-        (s0 = to_float(x, x->Jpc, x->Jf, size_t(x->nE) * nb * nb)) != HBPC_OK) return s0;
     x->pc_built = true;
     x->pc_c1 = c1;
     x->pc_c2 = c2;
     return HBPC_OK;
   }
-  const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
-  const size_t blk = size_t(x->nE) * nb * nb;
   if (mixed) {
-    // the blocks only precondition the FP32 Krylov loop: S and its inverse in FP32
-    if ((s0 = to_float(x, x->Jpc, x->Jf, blk)) != HBPC_OK) return s0;
+    // S and its inverse in FP32 as well
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
              k_pc_form_S<float><<<int(x->nE), 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb,
                                                                                          int(x->nE), x->c12));
@@ -717,11 +730,36 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
 // dot, update + norms, finalisation (krylov.cuh).
 template <typename S>
 void cgs_launch(hbpc_ctx* x, const KrylovT<S>& K) {
+  if (x->coop) {   // one cooperative launch (k_cgs_coop) instead of four
+    const size_t m1 = size_t(K.m + 1);
+    const size_t shm = std::max(m1 * (kVecWarps + 1), 3 * (m1 + 1)) * sizeof(double);
+    void* args[] = {const_cast<KrylovT<S>*>(&K)};
+    HBPC_RUN(x, HBPC_PHASE_DOT, 1,
+             cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cgs_coop<S>), dim3(x->nblocks),
+                                         dim3(kVecThreads), args, shm, x->stream));
+    return;
+  }
   const size_t m1 = size_t(K.m + 1);
   HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_cgs_dot<S><<<x->nblocks, kVecThreads, m1 * kVecWarps * sizeof(double), x->stream>>>(K));
   HBPC_RUN(x, HBPC_PHASE_DOT, 1, k_cgs_update_dot<S><<<x->nblocks, kVecThreads, m1 * (kVecWarps + 1) * sizeof(double), x->stream>>>(K));
   HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_cgs_update<S><<<x->nblocks, kVecThreads, m1 * sizeof(double), x->stream>>>(K));
   HBPC_RUN(x, HBPC_PHASE_UPDATE, 1, k_cgs_finalize<S><<<1, kVecThreads, 3 * (m1 + 1) * sizeof(double), x->stream>>>(K));
+}
+
+// Batches: the GMRES system of a group is scaled row-wise per instance,
+// D J dX = -D G with D_i = 1 / ||G_i|| (0 for converged instances), so that
+// its global relative tolerance asks the same relative accuracy of every
+// instance (J is block diagonal over instances: dX is unchanged).  Applied to
+// G before GMRES and to every Jacobian-vector product.
+template <typename T>
+hbpc_status inst_scale(hbpc_ctx* x, T* v, const int* col, int col_offset, const int* skip) {
+  if (x->ninst == 0) return HBPC_OK;
+  const dim3 grid(64, x->ninst);
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1,
+           k_inst_scale<T><<<grid, 256, 0, x->stream>>>(v, size_t(x->ndof), x->d_irange, x->d_iscale, col,
+                                                       col_offset, size_t(2 * x->ndof), skip));
+  HBPC_LAUNCH_CK(x, "k_inst_scale");
+  return HBPC_OK;
 }
 
 hbpc_status arnoldi_step(hbpc_ctx* x) {
@@ -732,6 +770,7 @@ hbpc_status arnoldi_step(hbpc_ctx* x) {
   }
   s = apply_jv(x, krylov_input(x));
   if (s != HBPC_OK) return s;
+  if ((s = inst_scale<double>(x, x->V, &x->st->j, 1, &x->st->done)) != HBPC_OK) return s;
   cgs_launch<double>(x, x->K);
   HBPC_LAUNCH_CK(x, "arnoldi");
   return HBPC_OK;
@@ -783,6 +822,7 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
     z.out = x->V + n2; z.out_ld = n2; z.out_offset = 0; z.out_jidx = nullptr;
     s = apply_jv(x, z);
     if (s != HBPC_OK) return s;
+    if ((s = inst_scale<double>(x, x->V + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->V + n2, x->V, n2));
     s = norms(x, x->V, n2);
     if (s != HBPC_OK) return s;
@@ -827,6 +867,7 @@ hbpc_status arnoldi_step_f(hbpc_ctx* x) {
     if (s != HBPC_OK) return s;
   }
   if ((s = apply_jv_f(x, krylov_input_f(x))) != HBPC_OK) return s;
+  if ((s = inst_scale<float>(x, x->Vf, &x->st->j, 1, &x->st->done)) != HBPC_OK) return s;
   cgs_launch<float>(x, x->Kf);
   HBPC_LAUNCH_CK(x, "arnoldi<float>");
   return HBPC_OK;
@@ -870,6 +911,7 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
     z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
     z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
     if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+    if ((s = inst_scale<float>(x, x->Vf + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, float><<<x->nblocks, kVecThreads, 0, x->stream>>>(x->Vf, n2, size_t(x->ndof), x->K, nullptr));
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
@@ -979,13 +1021,15 @@ hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, con
     nact += x->h_active[i];
   }
   x->stats.newton_solves += 1;
-  const dim3 mgrid(64, ni);
   for (int r = 0; nact > 0; ++r) {
     if (r >= x->sol.newton_max_iter)
       return fail(x, HBPC_ERR_NO_CONVERGENCE, "Newton did not converge within newton_max_iter (batch)");
-    HBPC_CK(x, cudaMemcpyAsync(x->d_active, x->h_active.data(), ni * sizeof(int), cudaMemcpyHostToDevice, x->stream));
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_inst_mask<<<mgrid, 256, 0, x->stream>>>(x->G, size_t(n), x->d_irange, x->d_active));
-    HBPC_LAUNCH_CK(x, "k_inst_mask");
+    for (int i = 0; i < ni; ++i)
+      x->h_iscale[i] = x->h_active[i] ? 1.0 / std::sqrt(x->h_inrm[2 * i]) : 0.0;
+    HBPC_CK(x, cudaMemcpyAsync(x->d_iscale, x->h_iscale.data(), ni * sizeof(double), cudaMemcpyHostToDevice,
+                               x->stream));
+    if ((s = inst_scale<double>(x, x->G, nullptr, 0, nullptr)) != HBPC_OK) return s;
+    if ((s = norms(x, x->G, size_t(2 * n))) != HBPC_OK) return s;   // of the scaled right-hand side
     int its = 0;
     bool conv = false;
     if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
@@ -1108,7 +1152,7 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
   cudaFree(x->vtab_d); cudaFree(x->vtab_f); cudaFree(x->vloc_d);
   cudaFree(x->d_inst); cudaFree(x->d_instf); cudaFree(x->d_blk); cudaFree(x->d_irange);
-  cudaFree(x->d_inrm); cudaFree(x->d_active);
+  cudaFree(x->d_inrm); cudaFree(x->d_iscale);
   lp_free(x);
   if (x->st_host) cudaFreeHost(x->st_host);
 }
@@ -1337,7 +1381,24 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
   x->nblocks = std::max(1, std::min<int>(2 * sms, int((n2 + 1023) / 1024)));
   x->nb = int(x->ndof / x->nE);
   pc_launch_config(x);
-  const int prows = std::max(x->nblocks, x->pc_grid);
+  {   // the fused CGS2 kernel needs every block resident at once
+    int coop_attr = 0, per_sm_d = 0, per_sm_f = 0;
+    cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev);
+    const size_t m1 = size_t(solver->gmres_restart + 1);
+    const size_t shm = std::max(m1 * (kVecWarps + 1), 3 * (m1 + 1)) * sizeof(double);
+    if (shm > 48 * 1024) {
+      cudaFuncSetAttribute(k_cgs_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+      cudaFuncSetAttribute(k_cgs_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, k_cgs_coop<double>, kVecThreads, shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_cgs_coop<float>, kVecThreads, shm);
+    cudaGetLastError();
+    x->coop_max_blocks = std::min(per_sm_d, per_sm_f) * sms;
+    x->coop = coop_attr && x->coop_max_blocks >= x->nblocks;
+    x->sms = sms;
+  }
+  // partial-sum rows for every launch shape the autotuner may pick
+  const int prows = std::max({x->nblocks, 4 * sms, int(x->nE)});
   hbpc_status e = HBPC_OK;
   if ((e = dmalloc(x, &x->Wn, n)) || (e = dmalloc(x, &x->X, n2)) || (e = dmalloc(x, &x->G, n2)) ||
       (e = dmalloc(x, &x->r1, n)) || (e = dmalloc(x, &x->r2, n)) || (e = dmalloc(x, &x->dX, n2)) ||
@@ -1409,6 +1470,116 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
   if (ce != cudaSuccess) {
     g_create_error = std::string("initialisation: ") + cudaGetErrorString(ce);
     free_all(x); delete x; return HBPC_ERR_CUDA;
+  }
+  return HBPC_OK;
+}
+
+// Launch-shape autotuner: times the candidates of the two runtime-shaped hot
+// kernels on the context's own buffers and keeps the fastest.
+//   Krylov reductions: blocks in {1, 2, 3, 4} x SMs (at most one row tile per
+//     block, and resident all at once for the cooperative CGS2 kernel); timed
+//     on a CGS2 column at j = m/2 (the state is restored afterwards).
+//   Block preconditioner apply: elements per block in {1, 2, 4, 8, 16} (one
+//     thread per block row, at most the 256 threads the kernel is built for).
+// Every timing is the median of 7 launches after 2 warm-ups (CUDA events on
+// the context's stream).  The arithmetic does not depend on the shapes except
+// for the summation order of the reductions.
+template <class F>
+double median_us(hbpc_ctx* x, F launch) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  std::vector<float> t;
+  for (int r = 0; r < 9; ++r) {
+    cudaEventRecord(a, x->stream);
+    launch();
+    cudaEventRecord(b, x->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (r >= 2) t.push_back(ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::sort(t.begin(), t.end());
+  return 1000.0 * t[t.size() / 2];
+}
+
+hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
+  hbpc_status s = sync(x, "autotune");
+  if (s != HBPC_OK) return s;
+  const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
+  GmresState saved{};
+  HBPC_CK(x, cudaMemcpy(&saved, x->st, sizeof(GmresState), cudaMemcpyDeviceToHost));
+  GmresState probe = saved;
+  probe.j = std::max(1, x->sol.gmres_restart / 2);
+  probe.done = 0; probe.its = 0; probe.max_its = 1 << 30; probe.m = x->sol.gmres_restart;
+  probe.target = 0.0; probe.reorth = 0;
+  GmresState* hprobe = x->st_host;           // pinned
+  *hprobe = probe;
+  const size_t n2 = size_t(2 * x->ndof);
+  const int tiles = int((n2 + kTile - 1) / kTile);
+  const int old_blocks = x->nblocks;
+  double best_k = 1e300;
+  int best_b = old_blocks;
+  double first_k = 0.0;
+  for (int c = 1; c <= 4; ++c) {
+    int nbk = std::min(c * x->sms, std::max(1, tiles));
+    if (x->coop) nbk = std::min(nbk, x->coop_max_blocks);
+    if (c > 1 && nbk <= std::min((c - 1) * x->sms, std::max(1, tiles))) continue;
+    x->nblocks = nbk; x->K.nblocks = nbk; x->Kf.nblocks = nbk;
+    const double us = median_us(x, [&]() {
+      cudaMemcpyAsync(x->st, hprobe, sizeof(GmresState), cudaMemcpyHostToDevice, x->stream);
+      if (mixed) cgs_launch<float>(x, x->Kf); else cgs_launch<double>(x, x->K);
+    });
+    if (cudaGetLastError() != cudaSuccess) continue;   // a shape that cannot launch is no candidate
+    if (nbk == old_blocks) first_k = us;
+    if (us < best_k) { best_k = us; best_b = nbk; }
+  }
+  x->nblocks = best_b; x->K.nblocks = best_b; x->Kf.nblocks = best_b;
+  HBPC_LAUNCH_CK(x, "autotune krylov");
+  // block preconditioner apply
+  double best_p = 0.0, first_p = 0.0;
+  int best_e = std::max(1, x->pc_threads / std::max(1, x->nb));
+  if (x->sol.pc != HBPC_PC_NONE && (mixed ? x->Mf != nullptr : x->Mpc != nullptr)) {
+    const int old_threads = x->pc_threads, old_grid = x->pc_grid;
+    const size_t old_smem = x->pc_smem;
+    best_p = 1e300;
+    int bt = old_threads, bg = old_grid;
+    size_t bs = old_smem;
+    // candidates: powers of two and the creation-time shape (as many elements
+    // as fit 256 threads, the kernel's launch bound)
+    std::vector<int> cand = {1, 2, 4, 8, 16, std::max(1, 256 / x->nb)};
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (int epb : cand) {
+      const int threads = ((epb * x->nb + 31) / 32) * 32;
+      const size_t smem = size_t(epb) * 4 * x->nb * sizeof(double);
+      if (threads > 256 || smem > 48 * 1024) continue;
+      const int grid = int((x->nE + epb - 1) / epb);
+      x->pc_threads = threads; x->pc_grid = grid; x->pc_smem = smem;
+      const double us = median_us(x, [&]() {
+        if (mixed) pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr);
+        else pc_apply(x, x->Z, nullptr, nullptr, x->G, 0, nullptr);
+      });
+      if (cudaGetLastError() != cudaSuccess) continue;
+      if (threads == old_threads) first_p = us;
+      if (us < best_p) { best_p = us; bt = threads; bg = grid; bs = smem; best_e = epb; }
+    }
+    x->pc_threads = bt; x->pc_grid = bg; x->pc_smem = bs;
+    HBPC_LAUNCH_CK(x, "autotune pc");
+  }
+  *hprobe = saved;
+  HBPC_CK(x, cudaMemcpyAsync(x->st, hprobe, sizeof(GmresState), cudaMemcpyHostToDevice, x->stream));
+  if ((s = sync(x, "autotune")) != HBPC_OK) return s;
+  if (out) {
+    out->krylov_blocks = best_b;
+    out->krylov_us = best_k;
+    out->krylov_us_default = first_k;
+    out->pc_elems_per_block = best_e;
+    out->pc_us = best_p;
+    out->pc_us_default = first_p;
+    out->cooperative_cgs = x->coop ? 1 : 0;
   }
   return HBPC_OK;
 }
@@ -1493,7 +1664,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   };
   if ((s = dmalloc(x, &x->d_inst, ni)) || (s = dmalloc(x, &x->d_instf, ni)) || (s = dmalloc(x, &x->d_blk, blk.size())) ||
       (s = dmalloc(x, &x->d_irange, 2 * ni)) || (s = dmalloc(x, &x->d_inrm, 2 * ni)) ||
-      (s = dmalloc(x, &x->d_active, ni)))
+      (s = dmalloc(x, &x->d_iscale, ni)))
     return bail(s);
   cudaError_t ce = cudaMemcpy(x->d_inst, gd.data(), ni * sizeof(InstGeo<double>), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(x->d_instf, gf.data(), ni * sizeof(InstGeo<float>), cudaMemcpyHostToDevice);
@@ -1511,6 +1682,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   x->prmf.inst = x->d_instf; x->prmf.blk_inst = x->d_blk;
   x->h_inrm.assign(2 * ni, 0.0);
   x->h_active.assign(ni, 0);
+  x->h_iscale.assign(ni, 0.0);
   *out = x;
   return HBPC_OK;
 }
@@ -2158,6 +2330,20 @@ hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out) {
     t.t = std::max(t.t, x->stats.t);
   }
   *out = t;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_autotune(hbpc_ctx* ctx, hbpc_tuning* out) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  return autotune(ctx, out);
+}
+
+hbpc_status hbpc_batch_autotune(hbpc_batch* b, hbpc_tuning* out, int n_out) {
+  if (!b || (out && n_out < int(b->g.size()))) return HBPC_ERR_INVALID_ARG;
+  for (size_t k = 0; k < b->g.size(); ++k) {
+    hbpc_status s = autotune(b->g[k], out ? out + k : nullptr);
+    if (s != HBPC_OK) { b->err = b->g[k]->err; return s; }
+  }
   return HBPC_OK;
 }
 

@@ -46,6 +46,7 @@ struct OpsTable {
                const float* Sf, cudaStream_t) = nullptr;
   // BJ_ext element Jacobians J_i (Sec. 3.2.3), column-major n_b x n_b per element
   void (*pc_assemble)(const DGParams<double>&, const double* W, double* J, cudaStream_t) = nullptr;
+  void (*pc_assemble_f)(const DGParams<float>&, const double* W, float* J, cudaStream_t) = nullptr;
 };
 
 // Returns false if the combination was not compiled.

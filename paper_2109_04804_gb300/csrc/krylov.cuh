@@ -6,6 +6,8 @@
 // can be replayed from a CUDA graph; every kernel returns at once when the
 // cycle is finished.  Included by exactly one translation unit.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "krylov_common.cuh"
 
 namespace hbpc {
@@ -309,6 +311,91 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
   extern __shared__ double sm[];          // >= 3 (m+2) doubles
   __shared__ double nrm[2];
   cgs_reduce_cols(K.partial, cgs_stride(K.m), K.nblocks, 2 * (K.m + 1), 2, nullptr, nrm);
+  double* Hj = K.H + size_t(j) * (K.m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = K.hc[i] + K.hc[(K.m + 2) + i];
+  __syncthreads();
+  finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
+}
+
+// The three CGS2 passes and the finalisation in one cooperative launch, the
+// kernel boundaries replaced by grid-wide barriers (the same arithmetic in the
+// same order as k_cgs_dot, k_cgs_update_dot, k_cgs_update, k_cgs_finalize).
+// Launched with cudaLaunchCooperativeKernel, which refuses a grid whose blocks
+// cannot all be resident, so every barrier is reached by every block.  The
+// early exit reads st->done before any block writes the state (the state is
+// written only by block 0 after the last barrier), so it is grid-uniform.
+// Dynamic shared memory: max((m+1)(kVecWarps+1), 3(m+2)) doubles.
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
+  using A = typename AccOf<S>::type;
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  GmresState* st = K.st;
+  if (st->done) return;
+  const int j = st->j, cnt = j + 1;
+  const int stride = cgs_stride(K.m);
+  extern __shared__ double sm[];
+  {   // pass A: partial dots <q, V_i>_b
+    const S* q = K.V + size_t(j + 1) * K.ld;
+    double* s_red = sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
+    __syncthreads();
+    const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const size_t base = tile * kTile + threadIdx.x;
+      A qv[kRows];
+      bool in[kRows];
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        in[r] = row < K.n2;
+        qv[r] = in[r] ? A(q[row]) : A(0);
+      }
+      int i = 0;
+      for (; i + 1 < cnt; i += 2) {
+        const S* V0 = K.V + size_t(i) * K.ld;
+        const S* V1 = V0 + K.ld;
+        A a0 = A(0), a1 = A(0);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const size_t row = base + size_t(r) * kVecThreads;
+          if (in[r]) { a0 += qv[r] * A(V0[row]); a1 += qv[r] * A(V1[row]); }
+        }
+        a0 = warp_sum(a0);
+        a1 = warp_sum(a1);
+        if (lane == 0) { s_red[i * kVecWarps + warp] += double(a0); s_red[(i + 1) * kVecWarps + warp] += double(a1); }
+      }
+      if (i < cnt) {
+        const S* V0 = K.V + size_t(i) * K.ld;
+        A a0 = A(0);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const size_t row = base + size_t(r) * kVecThreads;
+          if (in[r]) a0 += qv[r] * A(V0[row]);
+        }
+        a0 = warp_sum(a0);
+        if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < kVecWarps; ++w) t += s_red[i * kVecWarps + w];
+      K.partial[size_t(blockIdx.x) * stride + i] = t;
+    }
+  }
+  __threadfence();
+  grid.sync();
+  cgs_update_body<S, true>(K, j, 0, K.m + 1, sm, sm + (K.m + 1));     // pass B
+  __threadfence();
+  grid.sync();
+  cgs_update_body<S, false>(K, j, K.m + 1, 2 * (K.m + 1), sm, nullptr);   // pass C
+  __threadfence();
+  grid.sync();
+  if (blockIdx.x != 0) return;
+  __shared__ double nrm[2];
+  cgs_reduce_cols(K.partial, stride, K.nblocks, 2 * (K.m + 1), 2, nullptr, nrm);
   double* Hj = K.H + size_t(j) * (K.m + 1);
   for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = K.hc[i] + K.hc[(K.m + 2) + i];
   __syncthreads();

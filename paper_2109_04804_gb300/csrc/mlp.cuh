@@ -234,7 +234,8 @@ __global__ void k_mlp_gather(const float* __restrict__ featbuf, const float* __r
 
 // Store the features (raw, FP32), the element Jacobian (FP32) and c1, c2 of a
 // set of elements into the replay buffer at rows [row0, row0 + count) (mod cap).
-__global__ void k_mlp_collect(const double* __restrict__ W, const double* __restrict__ Jpc, int nE, int nb,
+template <typename T>
+__global__ void k_mlp_collect(const double* __restrict__ W, const T* __restrict__ Jpc, int nE, int nb,
                               double c1, double c2, int count, int stride, int offset, int row0, int cap,
                               float* __restrict__ featbuf, float* __restrict__ Jbuf, float* __restrict__ cbuf) {
   const int s = blockIdx.x;

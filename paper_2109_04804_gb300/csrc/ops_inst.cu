@@ -81,11 +81,16 @@ struct Inst {
     }
   }
   static void pc_assemble(const DGParams<double>& p, const double* W, double* J, cudaStream_t s) {
-    k_pc_assemble<LAW, DIM, P, LGL><<<p.nE, 128, 0, s>>>(W, J, p);
+    k_pc_assemble<LAW, DIM, P, LGL, double><<<p.nE, 128, 0, s>>>(W, J, p);
+  }
+  // FP32 assembly for the mixed-precision mode (the blocks only precondition)
+  static void pc_assemble_f(const DGParams<float>& p, const double* W, float* J, cudaStream_t s) {
+    k_pc_assemble<LAW, DIM, P, LGL, float><<<p.nE, 128, 0, s>>>(W, J, p);
   }
   static void fill(OpsTable& t) {
     t.nv = NV;
     t.pc_assemble = &pc_assemble;
+    t.pc_assemble_f = &pc_assemble_f;
     t.jv_f = &jv_f;
     t.r1 = &r1;
     t.r2 = &r2;

@@ -54,6 +54,12 @@ class Solver(ctypes.Structure):
                 ("pc", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("krylov_blocks", ctypes.c_int), ("krylov_us", ctypes.c_double),
+                ("krylov_us_default", ctypes.c_double), ("pc_elems_per_block", ctypes.c_int),
+                ("pc_us", ctypes.c_double), ("pc_us_default", ctypes.c_double), ("cooperative_cgs", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("newton_solves", ctypes.c_longlong),
                 ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
@@ -112,6 +118,8 @@ _SIGS = {
     "hbpc_batch_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
     "hbpc_batch_profile_enable": (_I, [_CTX, _I]),
     "hbpc_batch_last_error": (ctypes.c_char_p, [_CTX]),
+    "hbpc_autotune": (_I, [_CTX, _P]),
+    "hbpc_batch_autotune": (_I, [_CTX, _P, _I]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -333,6 +341,11 @@ class Context:
     def profile(self, enable=True):
         self._c(_lib.hbpc_profile_enable(self._ctx, 1 if enable else 0))
 
+    def autotune(self):
+        t = Tuning()
+        self._c(_lib.hbpc_autotune(self._ctx, ctypes.addressof(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
     def profile_get(self):
         ms = np.zeros(len(PHASES))
         cnt = np.zeros(len(PHASES), dtype=np.int64)
@@ -428,3 +441,9 @@ class Batch:
 
     def profile(self, enable=True):
         self._c(_lib.hbpc_batch_profile_enable(self._b, 1 if enable else 0))
+
+    def autotune(self):
+        k = self.groups()
+        arr = (Tuning * k)()
+        self._c(_lib.hbpc_batch_autotune(self._b, ctypes.addressof(arr), k))
+        return [{f: getattr(arr[i], f) for f, _ in Tuning._fields_} for i in range(k)]

@@ -214,13 +214,18 @@ hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc);
  * accumulation, FP32 master weights and Adam.  Parameters as one FP32 array:
  * W1 (256 x d_in_padded), b1 (256), W2 (256 x 256), b2, W3 (d_out_padded x 256),
  * b3 (d_out_padded), row-major weights (out x in), then the feature
- * standardisation mu (d_in_padded) and sd (d_in_padded): f = (raw - mu) / sd. */
+ * standardisation mu (d_in_padded) and sd (d_in_padded): f = (raw - mu) / sd,
+ * then 4 stage classes: keys (c1, c2) x 4 (c1 <= 0: unused) and their fixed
+ * mean inverses minus I (4 x d_out_padded, row-major blocks); the block of
+ * stage coefficients (c1, c2) is M~ = I + C_k + reshape(O), k the class with
+ * equal keys, else the nearest.  Keys, means and standardisation are computed
+ * from the replay buffer at the first hbpc_pc_train after hbpc_pc_model_init
+ * (means from the stored exact inverses, zero without them). */
 hbpc_status hbpc_pc_model_info(hbpc_ctx* ctx, int* d_in_padded, int* hidden, int* d_out_padded,
                                long long* n_params);
 /* Random weights (normal, scaled by 1/sqrt(fan-in); W3 further by out_scale),
- * zero biases, Adam state cleared.  If the replay buffer holds exact block
- * inverses (data collected with BJ_ext), b3 starts at their mean minus I, so
- * the untrained network returns the mean block inverse. */
+ * zero biases, Adam state cleared; standardisation and stage classes are
+ * recomputed at the next hbpc_pc_train. */
 hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double out_scale);
 hbpc_status hbpc_pc_model_get(hbpc_ctx* ctx, float* params);        /* host output */
 hbpc_status hbpc_pc_model_set(hbpc_ctx* ctx, const float* params);  /* host input */

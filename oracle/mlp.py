@@ -15,7 +15,9 @@ block inverses.
 
 Network: two tanh hidden layers,
     z1 = W1 f + b1, h1 = tanh(z1), z2 = W2 h1 + b2, h2 = tanh(z2), O = W3 h2 + b3,
-weights W (out x in).  Adam (Kingma & Ba 2015) updates every parameter with
+weights W (out x in); M~ = I + C_k + reshape(O) with C_k a fixed per-class
+matrix (the mean block inverse minus I of the samples whose stage
+coefficients (c1, c2) form class k; computed from the data, not trained).  Adam (Kingma & Ba 2015) updates every parameter with
 m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2, p -= lr m^/(sqrt(v^) + eps),
 m^ = m / (1 - b1^t), v^ = v / (1 - b2^t).
 """
@@ -45,26 +47,29 @@ def forward(p, F):
     return {"F": F, "h1": h1, "h2": h2, "O": O}
 
 
-def mtilde(O, nb):
-    """M~ = I + reshape(O), row-major blocks (B, nb, nb)."""
+def mtilde(O, nb, C=None):
+    """M~ = I + C + reshape(O), row-major blocks (B, nb, nb); C (B, nb^2) is the
+    fixed mean inverse (minus I) of each sample's stage class (None: 0)."""
+    if C is not None:
+        O = O + C
     return np.eye(nb)[None] + O.reshape(-1, nb, nb)
 
 
-def probe_loss(O, U, X, nb):
+def probe_loss(O, U, X, nb, C=None):
     """L and dL/dO for probes X (B, P, nb) with U = S X (B, P, nb)."""
     B, P, _ = X.shape
-    M = mtilde(O, nb)
+    M = mtilde(O, nb, C)
     R = np.einsum("bij,bpj->bpi", M, U) - X          # residual M~ u_p - x_p
     L = np.sum(R * R) / (B * P)
     dM = 2.0 * np.einsum("bpi,bpj->bij", R, U) / (B * P)
     return L, dM.reshape(B, nb * nb)
 
 
-def inverse_loss(O, T, nb):
+def inverse_loss(O, T, nb, C=None):
     """Regression of M~ on the exact block inverses T (B, nb, nb):
     L = sum_s |M~_s - T_s|_F^2 / B and dL/dO (B, nb^2)."""
     B = T.shape[0]
-    R = mtilde(O, nb) - T
+    R = mtilde(O, nb, C) - T
     L = np.sum(R * R) / B
     return L, (2.0 * R / B).reshape(B, nb * nb)
 

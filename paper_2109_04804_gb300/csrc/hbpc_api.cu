@@ -224,6 +224,8 @@ struct hbpc_ctx {
     __nv_bfloat16* W1h = nullptr; __nv_bfloat16* W2h = nullptr; __nv_bfloat16* W3h = nullptr;
     __nv_bfloat16* W2T = nullptr; __nv_bfloat16* W3T = nullptr;
     float* mu = nullptr; float* sd = nullptr;
+    float* ckey = nullptr; float* cmean = nullptr;   // stage classes and their mean inverses
+    int* cls = nullptr;                               // class of every training sample
     bool stats = false;
     int adam_t = 0;
     int cap = 0, count = 0, next = 0, per_newton = 0, offset = 0;
@@ -505,7 +507,8 @@ hbpc_status lp_alloc(hbpc_ctx* x) {
   const size_t H = size_t(L.H);
   L.oW1 = 0; L.ob1 = L.oW1 + H * L.dinp; L.oW2 = L.ob1 + H; L.ob2 = L.oW2 + H * H;
   L.oW3 = L.ob2 + H; L.ob3 = L.oW3 + size_t(L.doutp) * H; L.np_train = L.ob3 + L.doutp;
-  L.np = L.np_train + 2 * size_t(L.dinp);   // + feature standardisation (mu, sd)
+  // + feature standardisation (mu, sd), stage-class keys and mean inverses
+  L.np = L.np_train + 2 * size_t(L.dinp) + 2 * kMlpClasses + size_t(kMlpClasses) * L.doutp;
   hbpc_status e;
   if ((e = dalloc_any(x, &L.P, L.np)) || (e = dalloc_any(x, &L.G, L.np)) || (e = dalloc_any(x, &L.Mo, L.np)) ||
       (e = dalloc_any(x, &L.Ve, L.np)) || (e = dalloc_any(x, &L.W1h, H * L.dinp)) ||
@@ -516,6 +519,8 @@ hbpc_status lp_alloc(hbpc_ctx* x) {
     return e;
   L.mu = L.P + L.np_train;
   L.sd = L.mu + L.dinp;
+  L.ckey = L.sd + L.dinp;
+  L.cmean = L.ckey + 2 * kMlpClasses;
   HBPC_CK(x, cudaMemsetAsync(L.P, 0, L.np * sizeof(float), x->stream));
   HBPC_CK(x, cudaMemsetAsync(L.Mo, 0, L.np * sizeof(float), x->stream));
   HBPC_CK(x, cudaMemsetAsync(L.Ve, 0, L.np * sizeof(float), x->stream));
@@ -534,7 +539,7 @@ hbpc_status lp_alloc_train(hbpc_ctx* x, int B, int P) {
   const size_t Bs = size_t(B), H = size_t(L.H);
   for (void* q : {(void*)L.Fb, (void*)L.H1b, (void*)L.H2b, (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1,
                   (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T, (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT,
-                  (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb, (void*)L.lpart, (void*)L.idx})
+                  (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb, (void*)L.lpart, (void*)L.idx, (void*)L.cls})
     cudaFree(q);
   if ((e = dalloc_any(x, &L.Fb, Bs * L.dinp)) || (e = dalloc_any(x, &L.H1b, Bs * H)) ||
       (e = dalloc_any(x, &L.H2b, Bs * H)) || (e = dalloc_any(x, &L.dOb, Bs * L.doutp)) ||
@@ -544,7 +549,7 @@ hbpc_status lp_alloc_train(hbpc_ctx* x, int B, int P) {
       (e = dalloc_any(x, &L.dZ1T, Bs * H)) || (e = dalloc_any(x, &L.FT, Bs * L.dinp)) ||
       (e = dalloc_any(x, &L.Jb, Bs * L.dout)) || (e = dalloc_any(x, &L.cb, Bs * 2)) ||
       (e = dalloc_any(x, &L.Ob, Bs * L.doutp)) || (e = dalloc_any(x, &L.Xb, Bs * 16 * L.nb)) ||
-      (e = dalloc_any(x, &L.lpart, Bs)) || (e = dalloc_any(x, &L.idx, Bs)))
+      (e = dalloc_any(x, &L.lpart, Bs)) || (e = dalloc_any(x, &L.idx, Bs)) || (e = dalloc_any(x, &L.cls, Bs)))
     return e;
   HBPC_CK(x, cudaMemsetAsync(L.dOb, 0, Bs * L.doutp * sizeof(__nv_bfloat16), x->stream));
   L.Bmax = B;
@@ -558,7 +563,7 @@ void lp_free(hbpc_ctx* x) {
                   (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
                   (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
                   (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
-                  (void*)L.lpart, (void*)L.idx})
+                  (void*)L.lpart, (void*)L.idx, (void*)L.cls})
     cudaFree(q);
   L = hbpc_ctx::Learned{};
 }
@@ -587,9 +592,14 @@ hbpc_status lp_infer(hbpc_ctx* x, const double* W, double c1, double c2) {
   const int nE = int(x->nE);
   if ((s = gemm(x, L.Fi, L.dinp, L.W1h, L.dinp, nE, L.H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1i, L.H})) != HBPC_OK) return s;
   if ((s = gemm(x, L.H1i, L.H, L.W2h, L.H, nE, L.H, L.H, EpiBiasTanh{L.P + L.ob2, L.H2i, L.H})) != HBPC_OK) return s;
+  // the stage class of (c1, c2) from the keys (host copy of the parameters' keys)
+  float keys[2 * kMlpClasses];
+  HBPC_CK(x, cudaMemcpyAsync(keys, L.ckey, sizeof(keys), cudaMemcpyDeviceToHost, x->stream));
+  if ((s = sync(x, "class keys")) != HBPC_OK) return s;
+  const float* cm = L.cmean + size_t(mlp_class(keys, float(c1), float(c2))) * L.doutp;
   if (x->sol.precision == HBPC_PREC_MIXED)
-    return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.P + L.ob3, x->Mf, L.nb});
-  return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<double>{L.P + L.ob3, x->Mpc, L.nb});
+    return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.P + L.ob3, cm, x->Mf, L.nb});
+  return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<double>{L.P + L.ob3, cm, x->Mpc, L.nb});
 }
 
 // One forward/backward pass on the batch already in Fb, Jb, cb, Xb: loss and
@@ -604,12 +614,13 @@ hbpc_status lp_loss_grad(hbpc_ctx* x, int B, int P, double* loss, int kind) {
   if ((s = gemm(x, L.H2b, H, L.W3h, H, B, L.doutp, H, EpiBiasF32{L.P + L.ob3, L.Ob, L.doutp})) != HBPC_OK) return s;
   // loss and dO (dO keeps the n_b^2-wide row layout inside its doutp-wide rows);
   // Jb holds J (probe loss) or the target inverse (inverse regression)
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_classify<<<(B + 255) / 256, 256, 0, x->stream>>>(L.cb, B, L.ckey, L.cls));
   if (kind == HBPC_PC_LOSS_INVERSE) {
-    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_inverse_loss<<<B, 256, 0, x->stream>>>(L.Jb, L.Ob, B, L.nb, L.doutp, L.dOb, L.lpart));
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_inverse_loss<<<B, 256, 0, x->stream>>>(L.Jb, L.Ob, B, L.nb, L.doutp, L.cmean, L.cls, L.dOb, L.lpart));
     HBPC_LAUNCH_CK(x, "k_mlp_inverse_loss");
   } else {
     const size_t shm = size_t(2 * P + 2) * L.nb * sizeof(float);
-    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_probe_loss<<<B, 256, shm, x->stream>>>(L.Jb, L.cb, L.Ob, L.Xb, B, P, L.nb, L.doutp, L.dOb, L.lpart));
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_mlp_probe_loss<<<B, 256, shm, x->stream>>>(L.Jb, L.cb, L.Ob, L.Xb, B, P, L.nb, L.doutp, L.cmean, L.cls, L.dOb, L.lpart));
     HBPC_LAUNCH_CK(x, "k_mlp_probe_loss");
   }
   // backward: W3, b3
@@ -1552,10 +1563,16 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
     std::vector<int> cand = {1, 2, 4, 8, 16, std::max(1, 256 / x->nb)};
     std::sort(cand.begin(), cand.end());
     cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-    for (int epb : cand) {
-      const int threads = ((epb * x->nb + 31) / 32) * 32;
+    int last_eff = 0;
+    for (int want : cand) {
+      // k_pc_apply takes blockDim.x / n_b elements per block: size the grid
+      // and the shared memory for that count (the thread count is rounded up
+      // to whole warps)
+      const int threads = ((want * x->nb + 31) / 32) * 32;
+      const int epb = threads / x->nb;
       const size_t smem = size_t(epb) * 4 * x->nb * sizeof(double);
-      if (threads > 256 || smem > 48 * 1024) continue;
+      if (threads > 256 || smem > 48 * 1024 || epb == last_eff) continue;
+      last_eff = epb;
       const int grid = int((x->nE + epb - 1) / epb);
       x->pc_threads = threads; x->pc_grid = grid; x->pc_smem = smem;
       const double us = median_us(x, [&]() {
@@ -1957,10 +1974,6 @@ hbpc_status hbpc_pc_model_init(hbpc_ctx* ctx, unsigned long long seed, double ou
   HBPC_CK(ctx, cudaMemset(L.Ve, 0, L.np * sizeof(float)));
   L.adam_t = 0;
   L.stats = false;
-  if (L.Tbuf && L.targets && L.count > 0) {   // start from the mean block inverse
-    k_mlp_target_mean<<<(L.dout + 255) / 256, 256, 0, ctx->stream>>>(L.Tbuf, L.count, L.nb, L.P + L.ob3);
-    HBPC_LAUNCH_CK(ctx, "k_mlp_target_mean");
-  }
   if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
   return sync(ctx, "pc_model_init");
 }
@@ -2059,6 +2072,23 @@ hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int loss_kind, int iters, int batch, in
     }
     HBPC_CK(ctx, cudaMemcpy(L.mu, mu.data(), L.dinp * sizeof(float), cudaMemcpyHostToDevice));
     HBPC_CK(ctx, cudaMemcpy(L.sd, sd.data(), L.dinp * sizeof(float), cudaMemcpyHostToDevice));
+    // stage classes: the first kMlpClasses distinct (c1, c2) pairs of the buffer
+    std::vector<float> cb(size_t(L.count) * 2);
+    HBPC_CK(ctx, cudaMemcpy(cb.data(), L.cbuf, cb.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    std::vector<float> keys(2 * kMlpClasses, -1.0f);
+    int nk = 0;
+    for (int i = 0; i < L.count && nk < kMlpClasses; ++i) {
+      bool seen = false;
+      for (int k = 0; k < nk; ++k) seen = seen || (keys[2 * k] == cb[2 * i] && keys[2 * k + 1] == cb[2 * i + 1]);
+      if (!seen) { keys[2 * nk] = cb[2 * i]; keys[2 * nk + 1] = cb[2 * i + 1]; ++nk; }
+    }
+    HBPC_CK(ctx, cudaMemcpy(L.ckey, keys.data(), keys.size() * sizeof(float), cudaMemcpyHostToDevice));
+    HBPC_CK(ctx, cudaMemset(L.cmean, 0, size_t(kMlpClasses) * L.doutp * sizeof(float)));
+    if (L.Tbuf && L.targets)   // each class starts from its mean block inverse
+      for (int k = 0; k < nk; ++k)
+        k_mlp_class_mean<<<(L.dout + 255) / 256, 256, 0, ctx->stream>>>(L.Tbuf, L.cbuf, L.count, L.nb, keys[2 * k],
+                                                                        keys[2 * k + 1], L.cmean + size_t(k) * L.doutp);
+    HBPC_LAUNCH_CK(ctx, "class means");
     L.stats = true;
   }
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;

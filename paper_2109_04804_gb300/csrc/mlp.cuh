@@ -19,6 +19,22 @@
 namespace hbpc {
 
 constexpr int kMlpHidden = 256;
+constexpr int kMlpClasses = 4;   // stage classes: distinct (c1, c2) pairs with their own mean inverse
+
+// Class of a stage coefficient pair: the key equal to (c1, c2), else the
+// nearest in relative distance (keys with c1 <= 0 are unused).
+__device__ __host__ inline int mlp_class(const float* keys, float c1, float c2) {
+  int best = 0;
+  float bd = 3.0e38f;
+  for (int k = 0; k < kMlpClasses; ++k) {
+    const float k1 = keys[2 * k], k2 = keys[2 * k + 1];
+    if (!(k1 > 0.f)) continue;
+    if (k1 == c1 && k2 == c2) return k;
+    const float d = fabsf(c1 - k1) / k1 + fabsf(c2 - k2) / fmaxf(fabsf(k2), 1e-30f);
+    if (d < bd) { bd = d; best = k; }
+  }
+  return best;
+}
 
 // ---- epilogues ---------------------------------------------------------------
 struct EpiBiasTanh {            // out = bf16(tanh(acc + b[n]))
@@ -42,14 +58,15 @@ struct EpiDtanh {               // out = bf16(acc * (1 - h^2)), h the layer's ac
     out[size_t(m) * ld + n] = __float2bfloat16(acc * (1.f - h * h));
   }
 };
-// M~ of element m = I + reshape(acc + b): entry (r, c) = O[r nb + c], stored
+// M~ of element m = I + C_k + reshape(acc + b), C_k the mean block inverse
+// (minus I) of the stage class k: entry (r, c) = O[r nb + c], stored
 // column-major per element for the BJ_ext apply.
 template <typename S>
 struct EpiPcBlock {
-  const float* b; S* M; int nb;
+  const float* b; const float* cm; S* M; int nb;
   __device__ void operator()(int m, int n, float acc) const {
     const int r = n / nb, c = n - r * nb;
-    M[size_t(m) * nb * nb + size_t(c) * nb + r] = S(acc + b[n] + (r == c ? 1.f : 0.f));
+    M[size_t(m) * nb * nb + size_t(c) * nb + r] = S(acc + b[n] + cm[n] + (r == c ? 1.f : 0.f));
   }
 };
 
@@ -108,9 +125,11 @@ __global__ void k_colsum_bf16(const __nv_bfloat16* __restrict__ in, int rows, in
 // Dynamic shared memory: (2 P + 2) n_b floats.
 __global__ void k_mlp_probe_loss(const float* __restrict__ J, const float* __restrict__ c12,
                                  const float* __restrict__ O, const float* __restrict__ X, int B, int P,
-                                 int nb, int ldo, __nv_bfloat16* __restrict__ dO, double* __restrict__ loss_part) {
+                                 int nb, int ldo, const float* __restrict__ cmean, const int* __restrict__ cls,
+                                 __nv_bfloat16* __restrict__ dO, double* __restrict__ loss_part) {
   const int s = blockIdx.x;
   if (s >= B) return;
+  const float* Cs = cmean + size_t(cls[s]) * ldo;   // the sample's class mean (minus I)
   extern __shared__ float sh[];
   float* su = sh;                 // P x nb
   float* sr = su + P * nb;        // P x nb
@@ -137,7 +156,7 @@ __global__ void k_mlp_probe_loss(const float* __restrict__ J, const float* __res
     __syncthreads();
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {     // r_p = u + O u - x
       float a = 0.f;
-      for (int c = 0; c < nb; ++c) a += Os[size_t(r) * nb + c] * su[p * nb + c];
+      for (int c = 0; c < nb; ++c) a += (Os[size_t(r) * nb + c] + Cs[size_t(r) * nb + c]) * su[p * nb + c];
       const float rr = su[p * nb + r] + a - x[r];
       sr[p * nb + r] = rr;
       lsum += double(rr) * double(rr);
@@ -166,16 +185,18 @@ __global__ void k_mlp_probe_loss(const float* __restrict__ J, const float* __res
 //   loss = sum_s |I + O_s - T_s|_F^2 / B,   dO = 2 (I + O - T) / B,
 // O, dO in the same row layout as the probe loss.
 __global__ void k_mlp_inverse_loss(const float* __restrict__ T, const float* __restrict__ O, int B, int nb,
-                                   int ldo, __nv_bfloat16* __restrict__ dO, double* __restrict__ loss_part) {
+                                   int ldo, const float* __restrict__ cmean, const int* __restrict__ cls,
+                                   __nv_bfloat16* __restrict__ dO, double* __restrict__ loss_part) {
   const int s = blockIdx.x;
   if (s >= B) return;
   const float* Ts = T + size_t(s) * nb * nb;
   const float* Os = O + size_t(s) * ldo;
+  const float* Cs = cmean + size_t(cls[s]) * ldo;
   const float norm = 2.f / float(B);
   double lsum = 0.0;
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
     const int r = t / nb, c = t - r * nb;
-    const float d = (r == c ? 1.f : 0.f) + Os[t] - Ts[size_t(c) * nb + r];
+    const float d = (r == c ? 1.f : 0.f) + Os[t] + Cs[t] - Ts[size_t(c) * nb + r];
     dO[size_t(s) * ldo + t] = __float2bfloat16(norm * d);
     lsum += double(d) * double(d);
   }
@@ -189,15 +210,26 @@ __global__ void k_mlp_inverse_loss(const float* __restrict__ T, const float* __r
   }
 }
 
-// Output bias from the targets: b3[r nb + c] = mean_i T_i(r, c) - delta_rc, so
-// that an untrained network already returns the mean block inverse.
-__global__ void k_mlp_target_mean(const float* __restrict__ Tbuf, int count, int nb, float* __restrict__ b3) {
+// Class means from the targets: cm[r nb + c] = mean over the samples of class
+// (k1, k2) of T_i(r, c) - delta_rc, so that an untrained network already
+// returns the class's mean block inverse.
+__global__ void k_mlp_class_mean(const float* __restrict__ Tbuf, const float* __restrict__ cbuf, int count,
+                                 int nb, float k1, float k2, float* __restrict__ cm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb * nb) return;
   const int r = t / nb, c = t - r * nb;
   double a = 0.0;
-  for (int i = 0; i < count; ++i) a += Tbuf[size_t(i) * nb * nb + size_t(c) * nb + r];
-  b3[t] = float(a / count) - (r == c ? 1.f : 0.f);
+  int n = 0;
+  for (int i = 0; i < count; ++i)
+    if (cbuf[2 * i] == k1 && cbuf[2 * i + 1] == k2) { a += Tbuf[size_t(i) * nb * nb + size_t(c) * nb + r]; ++n; }
+  cm[t] = n ? float(a / n) - (r == c ? 1.f : 0.f) : 0.f;
+}
+
+// Class of every sample from its (c1, c2).
+__global__ void k_mlp_classify(const float* __restrict__ c12, int B, const float* __restrict__ keys,
+                               int* __restrict__ cls) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B) cls[s] = mlp_class(keys, c12[2 * s], c12[2 * s + 1]);
 }
 
 // Rademacher probes from SplitMix64 (Steele, Lea & Flood 2014) of (seed, index).

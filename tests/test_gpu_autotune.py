@@ -44,6 +44,7 @@ def test_autotune_keeps_the_answer(hb, prec):
 def test_batch_autotune_per_group(hb):
     b = hb.Batch(2, [((6, 5), (0, 0), (1, 1)), ((4, 4), (0, 0), (1, 1)), ((5, 3), (0, 0), (1, 1))], [3, 4, 3],
                  nus=[0.01, 0.0, 0.005], law=hb.LAW_BURGERS, q=4, kmax=1, dt=0.01, tol_newton_rel=1e-12,
+                 tol_newton_abs=1e-13,
                  tol_gmres_rel=1e-8, gmres_restart=40, pc=hb.PC_BJEXT)
     t = b.autotune()
     assert len(t) == b.groups() == 2

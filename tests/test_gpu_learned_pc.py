@@ -28,14 +28,24 @@ def hb():
     return hbpc
 
 
-def layout(info, p, din):
-    """oracle params -> the library's flat FP32 parameter vector."""
+def layout(info, p, din, classes=None):
+    """oracle params (and optional stage classes [((c1, c2), mean minus I)])
+    -> the library's flat FP32 parameter vector."""
     H, dinp, doutp = info["hidden"], info["d_in_padded"], info["d_out_padded"]
     W1 = np.zeros((H, dinp)); W1[:, :din] = p["W1"][:, :din]
     W3 = np.zeros((doutp, H)); W3[:p["W3"].shape[0]] = p["W3"]
     b3 = np.zeros(doutp); b3[:p["b3"].shape[0]] = p["b3"]
     mu, sd = np.zeros(dinp), np.ones(dinp)
-    return np.concatenate([W1.ravel(), p["b1"], p["W2"].ravel(), p["b2"], W3.ravel(), b3, mu, sd]).astype(np.float32)
+    flat = np.concatenate([W1.ravel(), p["b1"], p["W2"].ravel(), p["b2"], W3.ravel(), b3, mu, sd])
+    # stage-class keys (c1, c2 per class; c1 <= 0: unused) and class means (minus I)
+    keys = np.full(2 * 4, -1.0)
+    means = np.zeros((4, doutp))
+    for k, (key, cm) in enumerate(classes or []):
+        keys[2 * k:2 * k + 2] = key
+        means[k, :cm.size] = cm
+    flat = np.concatenate([flat, keys, means.ravel()])
+    assert flat.size == info["n_params"]
+    return flat.astype(np.float32)
 
 
 def unlayout(info, g, din, dout):
@@ -124,6 +134,49 @@ def test_learned_pc_inverse_loss_matches_oracle(hb):
         ref = g_ref[k] if k != "W1" else g_ref[k][:, :info["d_in_padded"]]
         err = np.linalg.norm(g_gpu[k] - ref) / np.linalg.norm(ref)
         assert err <= 5e-2, (k, err)
+    ctx.close()
+
+
+def test_learned_pc_class_means_in_losses(hb):
+    """Per-sample stage-class means C_k enter M~ = I + C_k + O in both losses."""
+    ctx = hb.Context(2, (4, 4), (-1, -1), (1, 1), 2, law=hb.LAW_EULER, flux=hb.FLUX_RUSANOV, dt=0.05,
+                     pc=hb.PC_LEARNED)
+    info = ctx.pc_model_info()
+    nb = 36
+    din, dout = nb + 2, nb * nb
+    rng = np.random.default_rng(27)
+    p = mlp.init_params(info["d_in_padded"], info["hidden"], dout, seed=5, out_scale=0.5)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        p[k] = torch.from_numpy(p[k]).to(torch.bfloat16).to(torch.float64).numpy()
+    p["W1"][:, din:] = 0.0
+    keys = [(0.05, 0.002), (0.2, 0.015)]
+    cms = [np.float32(0.1 * rng.standard_normal(dout)).astype(np.float64) for _ in keys]
+    ctx.pc_model_set(layout(info, p, info["d_in_padded"], list(zip(keys, cms))))
+    B, P = 16, 3
+    F = np.zeros((B, info["d_in_padded"]))
+    F[:, :din] = rng.standard_normal((B, din))
+    F = torch.from_numpy(F).to(torch.bfloat16).to(torch.float64).numpy()
+    cls = rng.integers(0, 2, B)
+    c12 = np.array([keys[c] for c in cls], dtype=np.float32).astype(np.float64)
+    C = np.stack([cms[c] for c in cls])
+    act = mlp.forward(p, F)
+    # inverse loss
+    T = np.eye(nb)[None] + 0.2 * rng.standard_normal((B, nb, nb))
+    L_ref, _ = mlp.inverse_loss(act["O"], T, nb, C)
+    L_gpu, _ = ctx.pc_loss_grad(F, T.transpose(0, 2, 1), c12, None, loss="inverse")
+    assert abs(L_gpu - L_ref) <= 5e-2 * abs(L_ref), (L_gpu, L_ref)
+    # probe loss
+    J = 0.3 * rng.standard_normal((B, nb, nb))
+    X = np.sign(rng.standard_normal((B, P, nb)))
+    S = np.eye(nb)[None] - c12[:, 0, None, None] * J + c12[:, 1, None, None] * (J @ J)
+    U = np.einsum("bij,bpj->bpi", S, X)
+    L_ref, dO = mlp.probe_loss(act["O"], U, X, nb, C)
+    g_ref = mlp.backward(p, act, dO)
+    L_gpu, g_flat = ctx.pc_loss_grad(F, J.transpose(0, 2, 1), c12, X)
+    g_gpu = unlayout(info, g_flat, info["d_in_padded"], dout)
+    assert abs(L_gpu - L_ref) <= 5e-2 * abs(L_ref), (L_gpu, L_ref)
+    err = np.linalg.norm(g_gpu["W3"] - g_ref["W3"]) / np.linalg.norm(g_ref["W3"])
+    assert err <= 5e-2, err
     ctx.close()
 
 

@@ -118,6 +118,8 @@ typedef struct {
   long long r2_evals;
   long long launches;     /* kernel launches issued by the library */
   double t;               /* simulated time */
+  long long arnoldi_cols; /* sum over Arnoldi iterations of the columns
+                             orthogonalised against (j + 1 at column j) */
 } hbpc_stats;
 
 /* Phases of the per-launch device timing (hbpc_profile_*). */
@@ -315,17 +317,19 @@ hbpc_status hbpc_autotune(hbpc_ctx* ctx, hbpc_tuning* out);
  * n_inst problems that share dim, law, flux, gamma, eps, lf_scale, a, eta_br2,
  * the node family and the solver settings (HBPC(q, k_max), dt, tolerances,
  * preconditioner NONE or BJEXT, precision), each with its own mesh (n, lo, hi),
- * degree N[i] and viscosity phys[i].nu.  Instances with the same N form one
- * group: one element numbering (each instance's elements contiguous, padded to
- * the operator kernel's elements per block), so every kernel launch of the
- * group covers all its instances; the Jacobian and the block preconditioner are
- * block diagonal over instances.  Newton stops per instance (Sec. 3.2.1 tests
- * applied to each instance's residual; converged instances are frozen), one
- * GMRES per Newton iteration covers the group's active instances.  Groups run
- * concurrently, each on its own stream driven by its own host thread. */
+ * degree N[i] and viscosity phys[i].nu.  Instances with the same N form
+ * groups of at most max_per_group instances (<= 0: one group per N), formed
+ * in order of size: one element numbering per group (each instance's elements
+ * contiguous, padded to the operator kernel's elements per block), so every
+ * kernel launch of the group covers all its instances; the Jacobian and the
+ * block preconditioner are block diagonal over instances.  Newton stops per
+ * instance (Sec. 3.2.1 tests applied to each instance's residual; converged
+ * instances are frozen); one GMRES per Newton iteration covers the group's
+ * active instances, row-scaled per instance.  Groups run concurrently, each on
+ * its own stream driven by its own host thread. */
 typedef struct hbpc_batch hbpc_batch;
 hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* meshes, const int* N, int nodes,
-                              const hbpc_physics* phys, const hbpc_solver* solver);
+                              const hbpc_physics* phys, const hbpc_solver* solver, int max_per_group);
 void hbpc_batch_destroy(hbpc_batch* b);                       /* accepts NULL */
 int hbpc_batch_groups(const hbpc_batch* b);                   /* number of distinct N */
 long long hbpc_batch_ndof(const hbpc_batch* b, int inst);     /* -1 for a bad index */

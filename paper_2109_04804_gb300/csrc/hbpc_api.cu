@@ -245,6 +245,7 @@ struct hbpc_ctx {
   hbpc_stats stats{};
   std::string err;
   int nblocks = 0;
+  int vcols = 0;            // columns of the FP64 basis V
   bool coop = false;        // CGS2 as one cooperative launch (all blocks resident)
   int coop_max_blocks = 0;  // resident blocks of the cooperative kernel
   int sms = 0;
@@ -773,6 +774,13 @@ hbpc_status inst_scale(hbpc_ctx* x, T* v, const int* col, int col_offset, const 
   return HBPC_OK;
 }
 
+// Columns orthogonalised against by the Arnoldi iterations that took the
+// cycle from column j0 to j1: sum_{j = j0}^{j1 - 1} (j + 1).
+long long arnoldi_cols(int j0, int j1) {
+  if (j1 <= j0) return 0;
+  return (long long)(j1 - j0) * (j0 + j1 + 1) / 2;
+}
+
 hbpc_status arnoldi_step(hbpc_ctx* x) {
   hbpc_status s;
   if (x->sol.pc != HBPC_PC_NONE) {
@@ -796,6 +804,7 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
   HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
   HBPC_LAUNCH_CK(x, "k_cycle_init");
   const int batch = 4;
+  int j_prev = 0;
   for (;;) {
     for (int b = 0; b < batch; ++b) {
       hbpc_status s = arnoldi_step(x);
@@ -804,6 +813,8 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
     hbpc_status s = read_state(x);
     if (s != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
+    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
+    j_prev = h.j;
     if (!(h.resid == h.resid) || std::isinf(h.resid))
       return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
     if (!h.done) continue;
@@ -839,6 +850,7 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
     if (s != HBPC_OK) return s;
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
     HBPC_LAUNCH_CK(x, "k_cycle_init");
+    j_prev = 0;
   }
 }
 
@@ -892,11 +904,14 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
   HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
   HBPC_LAUNCH_CK(x, "k_cycle_init<float>");
   const int batch = 4;
+  int j_prev = 0;
   for (;;) {
     for (int b = 0; b < batch; ++b)
       if ((s = arnoldi_step_f(x)) != HBPC_OK) return s;
     if ((s = read_state(x)) != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
+    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
+    j_prev = h.j;
     if (!(h.resid == h.resid) || std::isinf(h.resid))
       return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
     if (!h.done) continue;
@@ -927,6 +942,7 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, float><<<x->nblocks, kVecThreads, 0, x->stream>>>(x->Vf, n2, size_t(x->ndof), x->K, nullptr));
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
     HBPC_LAUNCH_CK(x, "gmres<float> restart");
+    j_prev = 0;
   }
 }
 
@@ -1410,11 +1426,14 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
   }
   // partial-sum rows for every launch shape the autotuner may pick
   const int prows = std::max({x->nblocks, 4 * sms, int(x->nE)});
+  // the FP64 Krylov basis only exists in the FP64 mode (the mixed mode keeps
+  // two FP64 columns as scratch and its basis in FP32)
+  x->vcols = solver->precision == HBPC_PREC_MIXED ? 2 : m + 1;
   hbpc_status e = HBPC_OK;
   if ((e = dmalloc(x, &x->Wn, n)) || (e = dmalloc(x, &x->X, n2)) || (e = dmalloc(x, &x->G, n2)) ||
       (e = dmalloc(x, &x->r1, n)) || (e = dmalloc(x, &x->r2, n)) || (e = dmalloc(x, &x->dX, n2)) ||
       (e = dmalloc(x, &x->bvec, n)) || (e = dmalloc(x, &x->stage, size_t(2) * x->s * 3 * n)) ||
-      (e = dmalloc(x, &x->V, size_t(m + 1) * n2))) {
+      (e = dmalloc(x, &x->V, size_t(x->vcols) * n2))) {
     g_create_error = x->err;
     free_all(x); delete x; return e;
   }
@@ -1691,7 +1710,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   const size_t n = size_t(x->ndof), n2 = 2 * n, m1 = size_t(solver->gmres_restart + 1);
   auto z = [&](void* p, size_t bytes) { if (ce == cudaSuccess && p) ce = cudaMemsetAsync(p, 0, bytes, st); };
   z(x->X, n2 * 8); z(x->G, n2 * 8); z(x->r1, n * 8); z(x->r2, n * 8); z(x->dX, n2 * 8); z(x->bvec, n * 8);
-  z(x->stage, size_t(2) * x->s * 3 * n * 8); z(x->V, m1 * n2 * 8); z(x->Z, n2 * 8);
+  z(x->stage, size_t(2) * x->s * 3 * n * 8); z(x->V, size_t(x->vcols) * n2 * 8); z(x->Z, n2 * 8);
   z(x->Vf, m1 * n2 * 4); z(x->Zf, n2 * 4); z(x->Zf2, n2 * 4); z(x->Wf, n2 * 4);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) { x->err = std::string("batch tables: ") + cudaGetErrorString(ce); return bail(HBPC_ERR_CUDA); }
@@ -1949,7 +1968,10 @@ hbpc_status hbpc_pc_model_info(hbpc_ctx* ctx, int* d_in_padded, int* hidden, int
   if (d_in_padded) *d_in_padded = dinp;
   if (hidden) *hidden = H;
   if (d_out_padded) *d_out_padded = doutp;
-  if (n_params) *n_params = (long long)H * dinp + H + (long long)H * H + H + (long long)doutp * H + doutp + 2LL * dinp;
+  // the layout of lp_alloc: weights and biases, standardisation, class keys and means
+  if (n_params)
+    *n_params = (long long)H * dinp + H + (long long)H * H + H + (long long)doutp * H + doutp + 2LL * dinp +
+                2LL * kMlpClasses + (long long)kMlpClasses * doutp;
   return HBPC_OK;
 }
 
@@ -2213,7 +2235,7 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
 
 /* ---- batches of independent instances ---------------------------------- */
 hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* meshes, const int* N, int nodes,
-                              const hbpc_physics* phys, const hbpc_solver* solver) {
+                              const hbpc_physics* phys, const hbpc_solver* solver, int max_per_group) {
   if (!out || n_inst < 1 || !meshes || !N || !phys || !solver)
     return fail(nullptr, HBPC_ERR_INVALID_ARG, "invalid batch arguments");
   *out = nullptr;
@@ -2234,16 +2256,26 @@ hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* mes
   if (!b) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
   b->ig.assign(n_inst, -1);
   b->il.assign(n_inst, -1);
+  const int cap = max_per_group > 0 ? max_per_group : n_inst;
   for (int Nv = 1; Nv <= kMaxP - 1; ++Nv) {
-    std::vector<int> ids;
+    std::vector<int> all;
     for (int i = 0; i < n_inst; ++i)
-      if (N[i] == Nv) ids.push_back(i);
-    if (ids.empty()) continue;
-    hbpc_ctx* x = nullptr;
-    hbpc_status s = create_group(ids, meshes, Nv, nodes, phys, solver, &x);
-    if (s != HBPC_OK) { hbpc_batch_destroy(b); return s; }
-    for (size_t k = 0; k < ids.size(); ++k) { b->ig[ids[k]] = int(b->g.size()); b->il[ids[k]] = int(k); }
-    b->g.push_back(x);
+      if (N[i] == Nv) all.push_back(i);
+    // instances of one N in groups of at most `cap`, sizes sorted so that a
+    // group holds instances of similar size
+    std::stable_sort(all.begin(), all.end(), [&](int a, int c) {
+      long long na = 1, nc = 1;
+      for (int m = 0; m < meshes[a].dim; ++m) { na *= meshes[a].n[m]; nc *= meshes[c].n[m]; }
+      return na < nc;
+    });
+    for (size_t g0 = 0; g0 < all.size(); g0 += size_t(cap)) {
+      std::vector<int> ids(all.begin() + g0, all.begin() + std::min(all.size(), g0 + size_t(cap)));
+      hbpc_ctx* x = nullptr;
+      hbpc_status s = create_group(ids, meshes, Nv, nodes, phys, solver, &x);
+      if (s != HBPC_OK) { hbpc_batch_destroy(b); return s; }
+      for (size_t k = 0; k < ids.size(); ++k) { b->ig[ids[k]] = int(b->g.size()); b->il[ids[k]] = int(k); }
+      b->g.push_back(x);
+    }
   }
   *out = b;
   return HBPC_OK;
@@ -2357,6 +2389,7 @@ hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out) {
     t.r1_evals += x->stats.r1_evals;
     t.r2_evals += x->stats.r2_evals;
     t.launches += x->stats.launches;
+    t.arnoldi_cols += x->stats.arnoldi_cols;
     t.t = std::max(t.t, x->stats.t);
   }
   *out = t;

@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("newton_solves", ctypes.c_longlong),
                 ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
                 ("r1_evals", ctypes.c_longlong), ("r2_evals", ctypes.c_longlong),
-                ("launches", ctypes.c_longlong), ("t", ctypes.c_double)]
+                ("launches", ctypes.c_longlong), ("t", ctypes.c_double), ("arnoldi_cols", ctypes.c_longlong)]
 
 
 _P = ctypes.c_void_p
@@ -106,7 +106,7 @@ _SIGS = {
     "hbpc_last_error": (ctypes.c_char_p, [_CTX]),
     "hbpc_profile_enable": (_I, [_CTX, _I]),
     "hbpc_profile_get": (_I, [_CTX, _P, _P, _I]),
-    "hbpc_batch_create": (_I, [ctypes.POINTER(_CTX), _I, _P, _P, _I, _P, ctypes.POINTER(Solver)]),
+    "hbpc_batch_create": (_I, [ctypes.POINTER(_CTX), _I, _P, _P, _I, _P, ctypes.POINTER(Solver), _I]),
     "hbpc_batch_destroy": (None, [_CTX]),
     "hbpc_batch_groups": (_I, [_CTX]),
     "hbpc_batch_ndof": (ctypes.c_longlong, [_CTX, _I]),
@@ -360,8 +360,9 @@ class Batch:
     def __init__(self, dim, meshes, Ns, nus=None, law=LAW_BURGERS, flux=FLUX_GLOBAL_LF,
                  a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, eta_br2=0.0, nodes=NODES_LOBATTO,
                  q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0, tol_gmres_rel=1e-5,
-                 gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64):
-        """meshes: list of (n, lo, hi) per instance."""
+                 gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64,
+                 max_per_group=0):
+        """meshes: list of (n, lo, hi) per instance; max_per_group <= 0: one group per N."""
         pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
         k = len(meshes)
         nus = [0.0] * k if nus is None else list(nus)
@@ -380,7 +381,7 @@ class Batch:
         self.meshes = [tuple(m) for m in meshes]
         self._b = _CTX()
         st = _lib.hbpc_batch_create(ctypes.byref(self._b), k, ctypes.addressof(self.M), ctypes.addressof(self.Nv),
-                                    nodes, ctypes.addressof(self.Ph), ctypes.byref(self.solver))
+                                    nodes, ctypes.addressof(self.Ph), ctypes.byref(self.solver), max_per_group)
         if st != OK:
             raise HBPCError(st, (_lib.hbpc_batch_last_error(None) or b"").decode())
 

@@ -232,7 +232,7 @@ def run_ours(args):
     cgs_b = (3.0 * cavg + 5.0) * 2.0 * vb       # bytes per W-DOF per launch
     cgs_f = (6.0 * cavg + 8.0) * 2.0            # flops per W-DOF per launch
     prof_cgs = (prof["arnoldi_dot"][0] + prof["arnoldi_update"][0], its_p)
-    kernels = {"jv": ("dg_operator_kernel<advection,2D,P=6,JobJvLinear<%s>> (Eq. 24)"
+    kernels = {"jv": ("dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)"
                       % ("float" if mixed else "double"), jv_work_per_dof(mixed), prof["jv"]),
                "pc_apply": ("k_pc_apply<%s> (BJ_ext, Sec. 3.2.3)" % ("float" if mixed else "double"),
                             pc_work_per_dof(mixed), prof["pc_apply"]),
@@ -328,7 +328,7 @@ def cpu_baseline(dt, budget_s=20.0):
 
 BATCH = dict(n_inst=256, n_range=(16, 96), N_range=(3, 7), nu_range=(1e-3, 1e-2), seed=2024,
              q=6, kmax=2, cfl_finest=2.0, tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3,
-             gmres_restart=30, gmres_max_iter=3000, newton_max_iter=50)
+             gmres_restart=100, gmres_max_iter=3000, newton_max_iter=50, max_per_group=1)
 
 
 def batch_instances(n_inst):
@@ -369,7 +369,8 @@ def run_batch(args):
                    q=BATCH["q"], kmax=BATCH["kmax"], dt=dt, tol_newton_rel=BATCH["tol_newton_rel"],
                    tol_newton_abs=BATCH["tol_newton_abs"], tol_gmres_rel=BATCH["tol_gmres_rel"],
                    gmres_restart=BATCH["gmres_restart"], gmres_max_iter=BATCH["gmres_max_iter"],
-                   newton_max_iter=BATCH["newton_max_iter"], pc=hbpc.PC_BJEXT, precision=hbpc.PREC_MIXED)
+                   newton_max_iter=BATCH["newton_max_iter"], pc=hbpc.PC_BJEXT, precision=hbpc.PREC_MIXED,
+                   max_per_group=args.max_per_group)
     ndof = 0
     w0s = []
     for i, (n, N, nu, seed) in enumerate(inst):
@@ -420,7 +421,8 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_sec / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov", "data": "synthetic",
             "config": {"workload": "batched_viscous_burgers_%d_instances_HBPC(6,2)_BR2_BJext" % len(inst),
-                       "instances": len(inst), "groups_by_N": groups, "total_dof": ndof,
+                       "instances": len(inst), "groups": groups, "max_per_group": args.max_per_group,
+                       "total_dof": ndof,
                        "mesh": "n x n periodic [0,1]^2, n uniform in 16..96", "N": "uniform in 3..7",
                        "nu": "uniform in [1e-3, 1e-2]", "dt": dt, "cfl_finest": BATCH["cfl_finest"],
                        "flux": "global Lax-Friedrichs (lambda = 1 = max |u0|; constant dissipation, so the "
@@ -606,6 +608,8 @@ def main():
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances")
     ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
+    ap.add_argument("--max-per-group", type=int, default=BATCH["max_per_group"],
+                    help="instances sharing one context and one GMRES (<= 0: all of one N)")
     args = ap.parse_args()
     PRECISION[0] = args.precision
     if args.impl == "reference":

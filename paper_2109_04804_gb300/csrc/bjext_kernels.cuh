@@ -136,7 +136,16 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   S u = S(0), v = S(0);
   if (live) {
     const S* Me = a.M + size_t(e) * nb * nb;
-    for (int c = 0; c < nb; ++c) {
+    int c = 0;
+    for (; c + 3 < nb; c += 4) {   // four columns' loads in flight, sums in column order
+      const S m0 = Me[size_t(c) * nb + r], m1 = Me[size_t(c + 1) * nb + r];
+      const S m2 = Me[size_t(c + 2) * nb + r], m3 = Me[size_t(c + 3) * nb + r];
+      u += m0 * xw[c]; v += m0 * xs[c];
+      u += m1 * xw[c + 1]; v += m1 * xs[c + 1];
+      u += m2 * xw[c + 2]; v += m2 * xs[c + 2];
+      u += m3 * xw[c + 3]; v += m3 * xs[c + 3];
+    }
+    for (; c < nb; ++c) {
       const S m = Me[size_t(c) * nb + r];
       u += m * xw[c];
       v += m * xs[c];
@@ -149,7 +158,16 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   if (live) {
     const S* Je = a.J + size_t(e) * nb * nb;
     S ju = S(0), jv = S(0);
-    for (int c = 0; c < nb; ++c) {
+    int c = 0;
+    for (; c + 3 < nb; c += 4) {
+      const S j0 = Je[size_t(c) * nb + r], j1 = Je[size_t(c + 1) * nb + r];
+      const S j2 = Je[size_t(c + 2) * nb + r], j3 = Je[size_t(c + 3) * nb + r];
+      ju += j0 * su[c]; jv += j0 * sv[c];
+      ju += j1 * su[c + 1]; jv += j1 * sv[c + 1];
+      ju += j2 * su[c + 2]; jv += j2 * sv[c + 2];
+      ju += j3 * su[c + 3]; jv += j3 * sv[c + 3];
+    }
+    for (; c < nb; ++c) {
       const S j = Je[size_t(c) * nb + r];
       ju += j * su[c];
       jv += j * sv[c];

@@ -43,7 +43,8 @@ template <class T> struct BaseOf<Dual<T>> { using type = T; };
 template <class V> __device__ __forceinline__ typename BaseOf<V>::type real_part(const V& x) { return x; }
 template <class T> __device__ __forceinline__ T real_part(const Dual<T>& x) { return x.v; }
 
-enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2 };
+enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2,
+           LAW_ADV2 = 3 };   // internal: two advected components (both halves of a Krylov vector)
 
 // Operator parameters, passed by value (kernel parameter space).  All matrices
 // already carry the Cartesian metric -(2/h_m) of the reference-element
@@ -140,6 +141,38 @@ struct Advection {
   template <class V>
   __device__ __forceinline__ static void jvp(const V* w, const V* s, int m, V* J, const DGParams<T>& p) {
     J[0] = p.a[m] * s[0];
+  }
+  __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {
+    return fabs(p.a[m]);
+  }
+};
+
+// Two independent components advected with the same velocity: the linear
+// operator of Eq. 24 applied to both halves (dW, dsigma) of a Krylov vector in
+// one element pass instead of two.
+template <int DIM, typename T>
+struct AdvectionPair {
+  static constexpr int NV = 2;
+  static constexpr bool LINEAR = true;
+  template <class V>
+  __device__ __forceinline__ static void flux_all(const V* w, V (*F)[NV], const DGParams<T>& p) {
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) { F[m][0] = p.a[m] * w[0]; F[m][1] = p.a[m] * w[1]; }
+  }
+  template <class V>
+  __device__ __forceinline__ static void jvp_all(const V* w, const V* s, V (*J)[NV], const DGParams<T>& p) {
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) { J[m][0] = p.a[m] * s[0]; J[m][1] = p.a[m] * s[1]; }
+  }
+  template <class V>
+  __device__ __forceinline__ static void flux(const V* w, int m, V* F, const DGParams<T>& p) {
+    F[0] = p.a[m] * w[0];
+    F[1] = p.a[m] * w[1];
+  }
+  template <class V>
+  __device__ __forceinline__ static void jvp(const V* w, const V* s, int m, V* J, const DGParams<T>& p) {
+    J[0] = p.a[m] * s[0];
+    J[1] = p.a[m] * s[1];
   }
   __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {
     return fabs(p.a[m]);
@@ -267,5 +300,6 @@ template <int LAW, int DIM, typename T> struct LawOf;
 template <int DIM, typename T> struct LawOf<LAW_ADV, DIM, T> { using type = Advection<DIM, T>; };
 template <int DIM, typename T> struct LawOf<LAW_BURGERS, DIM, T> { using type = Burgers<DIM, T>; };
 template <int DIM, typename T> struct LawOf<LAW_EULER, DIM, T> { using type = Euler<DIM, T>; };
+template <int DIM, typename T> struct LawOf<LAW_ADV2, DIM, T> { using type = AdvectionPair<DIM, T>; };
 
 }  // namespace hbpc

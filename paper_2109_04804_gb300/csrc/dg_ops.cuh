@@ -30,7 +30,7 @@ enum EvalKind { EV_R1 = 0, EV_R2 = 1 };
 
 template <int LAW, int DIM, int P>
 struct KernelShape {
-  static constexpr int NV = (LAW == LAW_EULER) ? DIM + 2 : 1;
+  static constexpr int NV = (LAW == LAW_EULER) ? DIM + 2 : (LAW == LAW_ADV2 ? 2 : 1);
   static constexpr bool VISC = NV == 1;          // BR2 viscous term available
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF, EPB = Geo<DIM, P>::EPB;
   // shared values per element: state + direction + DIM fluxes + 2*DIM faces
@@ -574,6 +574,31 @@ struct JobJvLinear {
       ow[i] = S(sc * T(zw[i]) - c1 * a + c2 * b);
       os[i] = S(sc * T(zs[i]) - a);
     }
+  }
+};
+
+// Eq. 24 with both operator passes in one: the two halves (dW, dS) of the input
+// are the two components of an AdvectionPair evaluation,
+//   out = (dW - c1 R1(dW) + c2 R1(dS), dS - R1(dW))   (inviscid linear advection).
+template <int NN, typename T = double, typename S = double>
+struct JobJvLinearPair {
+  static constexpr int K = 1;
+  JvInputT<S> z; JvCoef c;
+  __device__ static constexpr int kind(int) { return EV_R1; }
+  __device__ bool active() const { return !z.skipped(); }
+  __device__ void load_state(int, int e, int n, T* x) const {
+    const T sc = T(z.scale());
+    const size_t i = size_t(e) * NN + n;
+    x[0] = sc * T(z.zW()[i]);
+    x[1] = sc * T(z.zS()[i]);
+  }
+  __device__ void load_dir(int, int, int, T*) const {}
+  __device__ void epilogue(int e, int n, const T (*r)[2]) const {
+    const T c1 = T(*c.c1), c2 = T(*c.c2), sc = T(z.scale());
+    const size_t i = size_t(e) * NN + n;
+    const T a = r[0][0], b = r[0][1];
+    z.oW()[i] = S(sc * T(z.zW()[i]) - c1 * a + c2 * b);
+    z.oS()[i] = S(sc * T(z.zS()[i]) - a);
   }
 };
 

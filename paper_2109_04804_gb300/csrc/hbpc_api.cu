@@ -22,6 +22,7 @@
 #include "dg_ops.cuh"
 #include "hbpc_internal.h"
 #include "krylov.cuh"
+#include "batch_krylov.cuh"
 #include "bjext_kernels.cuh"
 #include "mlp.cuh"
 
@@ -193,6 +194,11 @@ struct hbpc_ctx {
   double* d_inrm = nullptr;                // per-instance squared norms
   double* d_iscale = nullptr;              // per-instance row scaling of the GMRES system
   std::vector<double> h_iscale;
+  // per-instance GMRES of the mixed mode (batch_krylov.cuh)
+  bool bk = false;
+  int bk_grid = 0;
+  BKrylovT<float> BK{};
+  void* bk_mem = nullptr;                  // one allocation for all of BK's device arrays
   std::vector<double> h_inrm;
   std::vector<int> h_active;
   // BJ_ext preconditioner (Sec. 3.2.3)
@@ -946,6 +952,78 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
   }
 }
 
+// Per-instance GMRES of a batch group in the mixed mode: J dX = -G for every
+// active instance with its own Krylov space (batch_krylov.cuh); converged
+// instances (zero right-hand side after the Newton freeze) take no step.
+hbpc_status gmres_bf(hbpc_ctx* x, int* its_out, bool* conv_out) {
+  const size_t n2 = size_t(2 * x->ndof);
+  BKrylovT<float>& K = x->BK;
+  const int grid = x->bk_grid;
+  const size_t shm = size_t(K.m + 1) * kVecWarps * sizeof(double);
+  hbpc_status s;
+  HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
+  if ((s = to_float(x, x->G, x->Vf, n2)) != HBPC_OK) return s;
+  auto start = [&](double sign, int first) -> hbpc_status {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_btile_sqnorm<float><<<grid, kVecThreads, 0, x->stream>>>(K));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcycle_init<float><<<1, 256, 0, x->stream>>>(K, sign, x->sol.tol_gmres_rel, first, x->sol.gmres_max_iter));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bscale0<float><<<grid, kVecThreads, 0, x->stream>>>(K));
+    HBPC_LAUNCH_CK(x, "batched cycle start");
+    return HBPC_OK;
+  };
+  if ((s = start(-1.0, 1)) != HBPC_OK) return s;
+  const int batch = 4;
+  int j_prev = 0;
+  for (;;) {
+    for (int b = 0; b < batch; ++b) {
+      if (x->sol.pc != HBPC_PC_NONE &&
+          (s = pc_apply_f(x, x->Vf, &x->st->j, nullptr, x->Zf, 0, &x->st->done)) != HBPC_OK)
+        return s;
+      JvInputT<float> z{};
+      z.V = x->sol.pc != HBPC_PC_NONE ? x->Zf : x->Vf;
+      z.ld = n2; z.half = size_t(x->ndof);
+      z.jidx = x->sol.pc != HBPC_PC_NONE ? nullptr : &x->st->j;
+      z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;   // not read by the FP32 products
+      z.skip = &x->st->done;
+      z.out = x->Vf; z.out_ld = n2; z.out_offset = 1; z.out_jidx = &x->st->j;
+      if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+      void* args[] = {&K};
+      HBPC_RUN(x, HBPC_PHASE_DOT, 1,
+               cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_bcgs_coop<float>), dim3(grid),
+                                           dim3(kVecThreads), args, shm, x->stream));
+      HBPC_LAUNCH_CK(x, "k_bcgs_coop");
+    }
+    if ((s = read_state(x)) != HBPC_OK) return s;
+    const GmresState& h = *x->st_host;
+    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
+    j_prev = h.j;
+    if (!h.done) continue;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bsolve_y<float><<<(K.ninst + 7) / 8, 256, 0, x->stream>>>(K));
+    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, float><<<grid, kVecThreads, 0, x->stream>>>(K, x->Zf, 0));
+      if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
+    } else {
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, double><<<grid, kVecThreads, 0, x->stream>>>(K, x->dX, 1));
+    }
+    HBPC_LAUNCH_CK(x, "batched gmres update");
+    if (h.converged || h.its >= h.max_its) {
+      *its_out = h.its;
+      *conv_out = h.converged != 0;
+      return HBPC_OK;
+    }
+    // restart: V_0 = -G - J dX, every instance from its own residual
+    if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
+    JvInputT<float> z{};
+    z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
+    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
+    z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
+    if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
+    if ((s = start(1.0, 0)) != HBPC_OK) return s;
+    j_prev = 0;
+  }
+}
+
 hbpc_status residual(hbpc_ctx* x, const double* b, double c1, double c2) {
   const long long n = x->ndof;
   HBPC_RUN(x, HBPC_PHASE_OPERATOR, 1,
@@ -1051,8 +1129,10 @@ hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, con
   for (int r = 0; nact > 0; ++r) {
     if (r >= x->sol.newton_max_iter)
       return fail(x, HBPC_ERR_NO_CONVERGENCE, "Newton did not converge within newton_max_iter (batch)");
+    // per-instance GMRES (x->bk): active instances as they are, converged ones
+    // with a zero right-hand side; the shared GMRES: rows scaled by 1 / ||G_i||
     for (int i = 0; i < ni; ++i)
-      x->h_iscale[i] = x->h_active[i] ? 1.0 / std::sqrt(x->h_inrm[2 * i]) : 0.0;
+      x->h_iscale[i] = !x->h_active[i] ? 0.0 : x->bk ? 1.0 : 1.0 / std::sqrt(x->h_inrm[2 * i]);
     HBPC_CK(x, cudaMemcpyAsync(x->d_iscale, x->h_iscale.data(), ni * sizeof(double), cudaMemcpyHostToDevice,
                                x->stream));
     if ((s = inst_scale<double>(x, x->G, nullptr, 0, nullptr)) != HBPC_OK) return s;
@@ -1062,7 +1142,7 @@ hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, con
     if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
     if (x->sol.precision == HBPC_PREC_MIXED) {
       if ((s = to_float(x, x->X, x->Wf, size_t(2 * n))) != HBPC_OK) return s;
-      if ((s = gmres_f(x, &its, &conv)) != HBPC_OK) return s;
+      if ((s = (x->bk ? gmres_bf(x, &its, &conv) : gmres_f(x, &its, &conv))) != HBPC_OK) return s;
     } else {
       if ((s = gmres(x, &its, &conv)) != HBPC_OK) return s;
     }
@@ -1179,7 +1259,7 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
   cudaFree(x->vtab_d); cudaFree(x->vtab_f); cudaFree(x->vloc_d);
   cudaFree(x->d_inst); cudaFree(x->d_instf); cudaFree(x->d_blk); cudaFree(x->d_irange);
-  cudaFree(x->d_inrm); cudaFree(x->d_iscale);
+  cudaFree(x->d_inrm); cudaFree(x->d_iscale); cudaFree(x->bk_mem);
   lp_free(x);
   if (x->st_host) cudaFreeHost(x->st_host);
 }
@@ -1620,6 +1700,74 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
   return HBPC_OK;
 }
 
+// Tiles and per-instance arrays of the mixed mode's per-instance GMRES
+// (batch_krylov.cuh).  Uses it when its cooperative kernel can be resident
+// with a useful grid; otherwise the group keeps the shared, row-scaled GMRES.
+hbpc_status bk_setup(hbpc_ctx* x) {
+  const int ni = x->ninst, m = x->sol.gmres_restart;
+  const long long per = x->ndof / x->nE;
+  std::vector<long long> trow;
+  std::vector<int> tcnt, tinst, itile;
+  for (int i = 0; i < ni; ++i) {
+    itile.push_back(int(tcnt.size()));
+    const long long a = x->ie0[i] * per, cnt = x->inE[i] * per;
+    for (int h = 0; h < 2; ++h)
+      for (long long r = 0; r < cnt; r += kTile) {
+        trow.push_back(h * x->ndof + a + r);
+        tcnt.push_back(int(std::min<long long>(kTile, cnt - r)));
+        tinst.push_back(i);
+      }
+  }
+  itile.push_back(int(tcnt.size()));
+  const int nt = int(tcnt.size());
+  int per_sm = 0;
+  const size_t shm = size_t(m + 1) * kVecWarps * sizeof(double);
+  if (shm > 48 * 1024)
+    cudaFuncSetAttribute(k_bcgs_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcgs_coop<float>, kVecThreads, shm);
+  int coop_attr = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev);
+  cudaGetLastError();
+  const int grid = std::min({nt, 2 * x->sms, per_sm * x->sms});
+  if (!coop_attr || grid < 1) return HBPC_OK;
+  // one allocation: doubles first, then the integer tables
+  const size_t nd = size_t(ni) * ((m + 1) * m + 2 * m + 2 * (m + 1) + 2 * (m + 2) + 3) + size_t(nt) * (m + 3);
+  const size_t bytes = nd * 8 + size_t(nt) * 8 + (size_t(nt) * 2 + (ni + 1) + 2 * ni) * 4 + 64;
+  if (cudaMalloc(&x->bk_mem, bytes) != cudaSuccess) {
+    x->bk_mem = nullptr;
+    return fail(x, HBPC_ERR_OOM, "cudaMalloc (batched GMRES)");
+  }
+  char* p = static_cast<char*>(x->bk_mem);
+  auto takeD = [&](size_t n) { double* r = reinterpret_cast<double*>(p); p += n * 8; return r; };
+  BKrylovT<float>& K = x->BK;
+  K.V = x->Vf; K.ld = size_t(2 * x->ndof); K.half = size_t(x->ndof);
+  K.m = m; K.ninst = ni; K.ntiles = nt;
+  K.H = takeD(size_t(ni) * (m + 1) * m);
+  K.cs = takeD(size_t(ni) * m); K.sn = takeD(size_t(ni) * m);
+  K.g = takeD(size_t(ni) * (m + 1)); K.y = takeD(size_t(ni) * (m + 1));
+  K.hc = takeD(size_t(ni) * 2 * (m + 2));
+  K.inv = takeD(ni); K.resid = takeD(ni); K.target = takeD(ni);
+  K.part = takeD(size_t(nt) * (m + 3));
+  long long* trow_d = reinterpret_cast<long long*>(p); p += size_t(nt) * 8;
+  int* ip = reinterpret_cast<int*>(p);
+  int* tcnt_d = ip; ip += nt;
+  int* tinst_d = ip; ip += nt;
+  int* itile_d = ip; ip += ni + 1;
+  K.conv = ip; ip += ni;
+  K.jn = ip; ip += ni;
+  K.trow = trow_d; K.tcnt = tcnt_d; K.tinst = tinst_d; K.itile = itile_d;
+  K.st = x->st;
+  HBPC_CK(x, cudaMemset(x->bk_mem, 0, bytes));
+  HBPC_CK(x, cudaMemcpy(trow_d, trow.data(), size_t(nt) * 8, cudaMemcpyHostToDevice));
+  HBPC_CK(x, cudaMemcpy(tcnt_d, tcnt.data(), size_t(nt) * 4, cudaMemcpyHostToDevice));
+  HBPC_CK(x, cudaMemcpy(tinst_d, tinst.data(), size_t(nt) * 4, cudaMemcpyHostToDevice));
+  HBPC_CK(x, cudaMemcpy(itile_d, itile.data(), size_t(ni + 1) * 4, cudaMemcpyHostToDevice));
+  x->bk = true;
+  x->bk_grid = grid;
+  return HBPC_OK;
+}
+
 // One group of a batch: the instances with the same N in one context (element
 // numbering padded so that each instance starts at a multiple of the operator's
 // elements per block; padding elements stay zero in every vector).
@@ -1716,6 +1864,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   if (ce != cudaSuccess) { x->err = std::string("batch tables: ") + cudaGetErrorString(ce); return bail(HBPC_ERR_CUDA); }
   x->prm.inst = x->d_inst; x->prm.blk_inst = x->d_blk;
   x->prmf.inst = x->d_instf; x->prmf.blk_inst = x->d_blk;
+  if (solver->precision == HBPC_PREC_MIXED && (s = bk_setup(x)) != HBPC_OK) return bail(s);
   x->h_inrm.assign(2 * ni, 0.0);
   x->h_active.assign(ni, 0);
   x->h_iscale.assign(ni, 0.0);

@@ -142,10 +142,8 @@ __device__ __forceinline__ void cgs_reduce_cols(const double* partial, int strid
                                                 const double* vscale, double* s_out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = warp; c < cnt; c += kVecWarps) {
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += __ldcg(partial + size_t(b) * stride + col0 + c);
-    s = warp_sum(s);
-    if (lane == 0) s_out[c] = vscale ? s * vscale[c] : s;
+    const double t = strided_sum(partial + col0 + c, stride, lane, nb);
+    if (lane == 0) s_out[c] = vscale ? t * vscale[c] : t;
   }
 }
 
@@ -171,31 +169,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_dot(KrylovT<S> K) {
       in[r] = row < K.n2;
       qv[r] = in[r] ? A(q[row]) : A(0);
     }
-    int i = 0;
-    for (; i + 1 < cnt; i += 2) {
-      const S* V0 = K.V + size_t(i) * K.ld;
-      const S* V1 = V0 + K.ld;
-      A a0 = A(0), a1 = A(0);
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const size_t row = base + size_t(r) * kVecThreads;
-        if (in[r]) { a0 += qv[r] * A(V0[row]); a1 += qv[r] * A(V1[row]); }
-      }
-      a0 = warp_sum(a0);
-      a1 = warp_sum(a1);
-      if (lane == 0) { s_red[i * kVecWarps + warp] += double(a0); s_red[(i + 1) * kVecWarps + warp] += double(a1); }
-    }
-    if (i < cnt) {
-      const S* V0 = K.V + size_t(i) * K.ld;
-      A a0 = A(0);
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const size_t row = base + size_t(r) * kVecThreads;
-        if (in[r]) a0 += qv[r] * A(V0[row]);
-      }
-      a0 = warp_sum(a0);
-      if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
-    }
+    col_dots<true>(K.V, K.ld, base, qv, in, cnt, s_red);
   }
   __syncthreads();
   const int stride = cgs_stride(K.m);
@@ -211,14 +185,15 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_dot(KrylovT<S> K) {
 // (with_dot) or the squared norms of the result.
 template <typename S, bool WITH_DOT>
 __device__ __forceinline__ void cgs_update_body(const KrylovT<S>& K, int j, int col_in, int col_out,
-                                                double* s_h, double* s_red) {
+                                                double* s_h, double* s_red, bool reduce = true) {
   using A = typename AccOf<S>::type;
   const int cnt = j + 1;
   const int stride = cgs_stride(K.m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   S* q = K.V + size_t(j + 1) * K.ld;
   // prologue: this pass's coefficients, reduced redundantly by every block
-  cgs_reduce_cols(K.partial, stride, K.nblocks, col_in, cnt, K.vscale, s_h);
+  // (unless the caller has them in s_h already)
+  if (reduce) cgs_reduce_cols(K.partial, stride, K.nblocks, col_in, cnt, K.vscale, s_h);
   if (WITH_DOT)
     for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
   __syncthreads();
@@ -234,15 +209,7 @@ __device__ __forceinline__ void cgs_update_body(const KrylovT<S>& K, int j, int 
       in[r] = row < K.n2;
       x[r] = in[r] ? A(q[row]) : A(0);
     }
-    for (int i = 0; i < cnt; ++i) {
-      const S* Vi = K.V + size_t(i) * K.ld;
-      const A c = A(s_h[i] * K.vscale[i]);
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const size_t row = base + size_t(r) * kVecThreads;
-        if (in[r]) x[r] -= c * A(Vi[row]);
-      }
-    }
+    col_axpy(K.V, K.ld, base, x, in, cnt, s_h, K.vscale);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const size_t row = base + size_t(r) * kVecThreads;
@@ -251,19 +218,7 @@ __device__ __forceinline__ void cgs_update_body(const KrylovT<S>& K, int j, int 
         if (row < K.half) aw += x[r] * x[r]; else as += x[r] * x[r];
       }
     }
-    if (WITH_DOT) {
-      for (int i = 0; i < cnt; ++i) {
-        const S* Vi = K.V + size_t(i) * K.ld;
-        A a0 = A(0);
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const size_t row = base + size_t(r) * kVecThreads;
-          if (in[r]) a0 += x[r] * A(Vi[row]);
-        }
-        a0 = warp_sum(a0);
-        if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
-      }
-    }
+    if (WITH_DOT) col_dots<true>(K.V, K.ld, base, x, in, cnt, s_red);
   }
   if (WITH_DOT) {
     __syncthreads();
@@ -317,9 +272,9 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
   finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
 }
 
-// The three CGS2 passes and the finalisation in one cooperative launch, the
-// kernel boundaries replaced by grid-wide barriers (the same arithmetic in the
-// same order as k_cgs_dot, k_cgs_update_dot, k_cgs_update, k_cgs_finalize).
+// The CGS2 passes and the finalisation in one cooperative launch, the kernel
+// boundaries replaced by grid-wide barriers; the second Gram-Schmidt pass runs
+// only when the DGKS test asks for it (the four-kernel form always runs it).
 // Launched with cudaLaunchCooperativeKernel, which refuses a grid whose blocks
 // cannot all be resident, so every barrier is reached by every block.  The
 // early exit reads st->done before any block writes the state (the state is
@@ -335,10 +290,13 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
   const int j = st->j, cnt = j + 1;
   const int stride = cgs_stride(K.m);
   extern __shared__ double sm[];
-  {   // pass A: partial dots <q, V_i>_b
+  __shared__ double s_qq[kVecWarps];
+  __shared__ int s_flag;
+  {   // pass A: partial dots <q, V_i>_b and |q|^2
     const S* q = K.V + size_t(j + 1) * K.ld;
     double* s_red = sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double qq_b = 0.0;
     for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
     __syncthreads();
     const size_t ntiles = (K.n2 + kTile - 1) / kTile;
@@ -352,45 +310,53 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
         in[r] = row < K.n2;
         qv[r] = in[r] ? A(q[row]) : A(0);
       }
-      int i = 0;
-      for (; i + 1 < cnt; i += 2) {
-        const S* V0 = K.V + size_t(i) * K.ld;
-        const S* V1 = V0 + K.ld;
-        A a0 = A(0), a1 = A(0);
+      col_dots<true>(K.V, K.ld, base, qv, in, cnt, s_red);
+      A qq = A(0);
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const size_t row = base + size_t(r) * kVecThreads;
-          if (in[r]) { a0 += qv[r] * A(V0[row]); a1 += qv[r] * A(V1[row]); }
-        }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        if (lane == 0) { s_red[i * kVecWarps + warp] += double(a0); s_red[(i + 1) * kVecWarps + warp] += double(a1); }
-      }
-      if (i < cnt) {
-        const S* V0 = K.V + size_t(i) * K.ld;
-        A a0 = A(0);
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const size_t row = base + size_t(r) * kVecThreads;
-          if (in[r]) a0 += qv[r] * A(V0[row]);
-        }
-        a0 = warp_sum(a0);
-        if (lane == 0) s_red[i * kVecWarps + warp] += double(a0);
-      }
+      for (int r = 0; r < kRows; ++r) qq += qv[r] * qv[r];
+      qq_b += double(warp_sum(qq));
     }
+    if (lane == 0) s_qq[warp] = qq_b;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       double t = 0.0;
       for (int w = 0; w < kVecWarps; ++w) t += s_red[i * kVecWarps + w];
       K.partial[size_t(blockIdx.x) * stride + i] = t;
     }
+    if (threadIdx.x == 0) {   // |q|^2 of this block's rows; column 2m+1 is free until pass C
+      double t = 0.0;
+      for (int w = 0; w < kVecWarps; ++w) t += s_qq[w];
+      K.partial[size_t(blockIdx.x) * stride + 2 * K.m + 1] = t;
+    }
   }
   __threadfence();
   grid.sync();
-  cgs_update_body<S, true>(K, j, 0, K.m + 1, sm, sm + (K.m + 1));     // pass B
-  __threadfence();
-  grid.sync();
-  cgs_update_body<S, false>(K, j, K.m + 1, 2 * (K.m + 1), sm, nullptr);   // pass C
+  // first-pass coefficients h_i = <q, v_i> and |q|^2, reduced redundantly (and
+  // identically) by every block; a second Gram-Schmidt pass only when the
+  // projection removed more than half of |q|^2 (the DGKS criterion
+  // |q - sum h_i v_i| < |q| / sqrt 2), decided identically in every block
+  cgs_reduce_cols(K.partial, stride, K.nblocks, 0, cnt, K.vscale, sm);
+  if ((threadIdx.x >> 5) == 0) {
+    const double t = strided_sum(K.partial + 2 * K.m + 1, stride, threadIdx.x & 31, K.nblocks);
+    if (threadIdx.x == 0) s_qq[0] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int i = 0; i < cnt; ++i) hh += sm[i] * sm[i];
+    s_flag = (s_qq[0] - hh) < 0.5 * s_qq[0] ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_flag) {
+    cgs_update_body<S, true>(K, j, 0, K.m + 1, sm, sm + (K.m + 1), false);      // pass B
+    __threadfence();
+    grid.sync();
+    cgs_update_body<S, false>(K, j, K.m + 1, 2 * (K.m + 1), sm, nullptr);      // pass C
+  } else {
+    cgs_update_body<S, false>(K, j, 0, 2 * (K.m + 1), sm, nullptr, false);     // the only update
+    if (blockIdx.x == 0)   // its coefficients went to the second slot: the first is zero
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) K.hc[i] = 0.0;
+  }
   __threadfence();
   grid.sync();
   if (blockIdx.x != 0) return;

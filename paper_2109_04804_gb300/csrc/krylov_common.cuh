@@ -63,6 +63,93 @@ __device__ __forceinline__ A warp_sum(A x) {
   return x;
 }
 
+// Warp-wide sum of p[b * stride] for b = 0 .. n-1 (lane handles b = lane,
+// lane + 32, ..; four independent accumulators keep four loads in flight);
+// every lane returns the total.  The order is fixed, so every block that
+// reduces the same data gets the same value.
+__device__ __forceinline__ double strided_sum(const double* p, int stride, int lane, int n) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int b = lane;
+  for (; b + 96 < n; b += 128) {
+    a0 += __ldcg(p + size_t(b) * stride);
+    a1 += __ldcg(p + size_t(b + 32) * stride);
+    a2 += __ldcg(p + size_t(b + 64) * stride);
+    a3 += __ldcg(p + size_t(b + 96) * stride);
+  }
+  for (; b < n; b += 32) a0 += __ldcg(p + size_t(b) * stride);
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// Dot products of this thread's kRows values x (rows base + r kVecThreads,
+// valid where in[r]) with columns [0, cnt) of V (stride ld), warp-reduced;
+// lane 0 stores (ACC: adds) the warp's sum of column i at s_red[i kVecWarps +
+// warp].  Four columns per step, so that 4 kRows independent loads are in
+// flight (the sums of every column keep their order).
+template <bool ACC, typename S, typename A>
+__device__ __forceinline__ void col_dots(const S* V, size_t ld, size_t base, const A* x, const bool* in, int cnt,
+                                         double* s_red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = 0;
+  for (; i + 3 < cnt; i += 4) {
+    A v[4][kRows];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        v[c][r] = in[r] ? A(V[size_t(i + c) * ld + base + size_t(r) * kVecThreads]) : A(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      A a = A(0);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) a += x[r] * v[c][r];
+      a = warp_sum(a);
+      if (lane == 0) {
+        if (ACC) s_red[(i + c) * kVecWarps + warp] += double(a);
+        else s_red[(i + c) * kVecWarps + warp] = double(a);
+      }
+    }
+  }
+  for (; i < cnt; ++i) {
+    A a = A(0);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      if (in[r]) a += x[r] * A(V[size_t(i) * ld + base + size_t(r) * kVecThreads]);
+    a = warp_sum(a);
+    if (lane == 0) {
+      if (ACC) s_red[i * kVecWarps + warp] += double(a);
+      else s_red[i * kVecWarps + warp] = double(a);
+    }
+  }
+}
+
+// x[r] -= sum_i c_i V_i(row) over columns [0, cnt), c_i = coef[i] (times
+// scale[i] when scale is given), in ascending i; four columns' loads per step.
+template <typename S, typename A>
+__device__ __forceinline__ void col_axpy(const S* V, size_t ld, size_t base, A* x, const bool* in, int cnt,
+                                         const double* coef, const double* scale) {
+  int i = 0;
+  for (; i + 3 < cnt; i += 4) {
+    A v[4][kRows];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        v[c][r] = in[r] ? A(V[size_t(i + c) * ld + base + size_t(r) * kVecThreads]) : A(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const A cc = A(scale ? coef[i + c] * scale[i + c] : coef[i + c]);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) x[r] -= cc * v[c][r];
+    }
+  }
+  for (; i < cnt; ++i) {
+    const A cc = A(scale ? coef[i] * scale[i] : coef[i]);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      if (in[r]) x[r] -= cc * A(V[size_t(i) * ld + base + size_t(r) * kVecThreads]);
+  }
+}
+
 // Last-block election: returns true in every thread of the last block to
 // arrive.  Partials written before must be visible (threadfence first).
 __device__ __forceinline__ bool last_block(unsigned* ticket, int nblocks) {

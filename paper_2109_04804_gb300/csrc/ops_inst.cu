@@ -65,6 +65,13 @@ struct Inst {
   }
   static void jv_linear(const DGParams<double>& p, const JvInput& z, const JvCoef& c,
                         cudaStream_t s) {
+    if constexpr (LINEAR) {
+      if (!p.visc) {   // both halves in one AdvectionPair pass
+        JobJvLinearPair<NN, double, double> j{z, c};
+        launch<LAW_ADV2, DIM, P, LGL>(j, p, s);
+        return;
+      }
+    }
     JobJvLinear<NV, NN> j{z, c};
     launch<LAW, DIM, P, LGL>(j, p, s);
   }
@@ -73,8 +80,13 @@ struct Inst {
   static void jv_f(const DGParams<float>& p, const JvInputT<float>& z, const JvCoef& c, const float* Wf,
                    const float* Sf, cudaStream_t s) {
     if constexpr (LINEAR) {
-      JobJvLinear<NV, NN, float, float> j{z, c};
-      launch<LAW, DIM, P, LGL, JobJvLinear<NV, NN, float, float>, float>(j, p, s);
+      if (!p.visc) {
+        JobJvLinearPair<NN, float, float> j{z, c};
+        launch<LAW_ADV2, DIM, P, LGL, JobJvLinearPair<NN, float, float>, float>(j, p, s);
+      } else {
+        JobJvLinear<NV, NN, float, float> j{z, c};
+        launch<LAW, DIM, P, LGL, JobJvLinear<NV, NN, float, float>, float>(j, p, s);
+      }
     } else {
       JobJvMixed<NV, NN> j{Wf, Sf, z, c};
       launch<LAW, DIM, P, LGL, JobJvMixed<NV, NN>, Dual<float>>(j, p, s);

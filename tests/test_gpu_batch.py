@@ -116,3 +116,23 @@ def test_batch_instance_matches_oracle(hb):
     ref = ohbpc.dg_stepper(disc, dt, 6, 1, opts)(initial(disc.node_coords(), seed=40 + k))
     assert rel(b.get_state(k), ref) <= 1e-11
     b.close()
+
+
+def test_batch_grouping_does_not_change_the_answer(hb):
+    """The same instances in one group per N, in groups of at most two, and one
+    per group (mixed precision: per-instance GMRES inside every group) reach the
+    same states: every instance stops on its own Newton tests."""
+    kw = dict(q=4, kmax=1, dt=0.01, tol_newton_rel=1e-13, tol_newton_abs=1e-13, tol_gmres_rel=1e-5,
+              gmres_restart=60, pc=hb.PC_BJEXT, precision=hb.PREC_MIXED)
+    out = []
+    for mpg in (0, 2, 1):
+        b = make_batch(hb, max_per_group=mpg, **kw)
+        assert b.groups() == {0: 4, 2: 4, 1: 6}[mpg]
+        for i in range(len(INST)):
+            b.set_state(i, initial(b.node_coords(i), seed=60 + i))
+        b.step(2)
+        out.append([b.get_state(i) for i in range(len(INST))])
+        b.close()
+    for k in (1, 2):
+        for i in range(len(INST)):
+            assert rel(out[k][i], out[0][i]) <= 1e-11, (k, i)

@@ -535,7 +535,9 @@ def run_vortex(args):
         c.close()
         return {"ok": ok, "ms_per_step": ms / steps, "value": ndof * steps / (ms / 1000.0) if ok is True else 0.0,
                 "gmres_its_per_step": st["gmres_its"] / steps, "newton_its_per_step": st["newton_its"] / steps,
-                "launches": int(st["launches"])}, w
+                "launches": int(st["launches"]),
+                "exact_blocks_per_build": (st["pc_exact_blocks"] / max(1, st["newton_its"])
+                                           if pc == hbpc.PC_LEARNED else None)}, w
 
     r_bj, w_bj = timed(hbpc.PC_BJEXT, args.steps)
     r_ln, w_ln = timed(hbpc.PC_LEARNED, args.steps, params)

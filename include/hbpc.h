@@ -120,6 +120,9 @@ typedef struct {
   double t;               /* simulated time */
   long long arnoldi_cols; /* sum over Arnoldi iterations of the columns
                              orthogonalised against (j + 1 at column j) */
+  long long pc_exact_blocks; /* learned preconditioner: element blocks that
+                                failed their probe check and got the exact
+                                inverse instead (summed over builds) */
 } hbpc_stats;
 
 /* Phases of the per-launch device timing (hbpc_profile_*). */
@@ -210,6 +213,10 @@ hbpc_status hbpc_reset_stats(hbpc_ctx* ctx);
 hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc);
 
 /* Learned block preconditioner (the workload's addition; the paper has none).
+ * At every build each learned block is checked with one random sign probe x:
+ * if |M~ S x - x| > 0.5 |x| the element gets the exact inverse S^-1 (formed
+ * and inverted like BJ_ext) instead; hbpc_stats.pc_exact_blocks counts them. */
+/* Learned block preconditioner, details.
  * Network: f = standardised [W_e, c1, c2] (d_in = n_b + 2, zero padded to a
  * multiple of 16) -> tanh(256) -> tanh(256) -> O (n_b^2, padded to a multiple
  * of 8); M~_e = I + reshape(O) row-major.  BF16 tensor-core GEMMs with FP32

@@ -11,9 +11,9 @@ namespace hbpc {
 // mode, where the blocks only precondition).  Dynamic shared memory: nb * nb T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T* __restrict__ Sall, int nb,
-                                                   int nE, const double* c12) {
+                                                   int nE, const double* c12, const int* only = nullptr) {
   const int e = blockIdx.x;
-  if (e >= nE) return;
+  if (e >= nE || (only && !only[e])) return;   // only: the elements flagged for an exact block
   extern __shared__ __align__(16) unsigned char sJ_raw[];
   T* sJ = reinterpret_cast<T*>(sJ_raw);
   const T* J = Jall + size_t(e) * nb * nb;
@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T
 // sets *singular (the preconditioner is then skipped by the host).
 // Dynamic shared memory: (nb * nb + nb) T + nb ints.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pc_invert(T* __restrict__ Mall, int nb, int nE, int* singular) {
+__global__ void __launch_bounds__(256) k_pc_invert(T* __restrict__ Mall, int nb, int nE, int* singular,
+                                                   const int* only = nullptr) {
   const int e = blockIdx.x;
-  if (e >= nE) return;
+  if (e >= nE || (only && !only[e])) return;
   extern __shared__ __align__(16) unsigned char inv_raw[];
   T* A = reinterpret_cast<T*>(inv_raw);   // column-major nb x nb
   T* colk = A + nb * nb;                  // copy of the pivot column
@@ -110,6 +111,68 @@ __global__ void __launch_bounds__(256) k_pc_invert(T* __restrict__ Mall, int nb,
     __syncthreads();
   }
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) M[t] = A[t];
+}
+
+// Verification of learned blocks: for every element, one Rademacher probe x
+// (SplitMix64 of seed and row), u = S x = x - c1 J x + c2 J (J x), and
+// r = M~ u - x.  flag[e] = |r|^2 > tau^2 |x|^2: the block does not map S x
+// near x and gets the exact inverse instead; count += flagged elements.
+// EPB elements per block, one thread per row (the apply's layout).
+// Dynamic shared memory: epb * 3 * nb values of S.
+__device__ __forceinline__ unsigned long long pc_mix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_pc_verify(const S* __restrict__ M, const S* __restrict__ J, int nb, int nE,
+                                                   const double* c12, unsigned long long seed, double tau,
+                                                   int* __restrict__ flag, int* __restrict__ count) {
+  const int epb = blockDim.x / nb;
+  const int le = threadIdx.x / nb, r = threadIdx.x - le * nb;
+  const int e = blockIdx.x * epb + le;
+  const bool live = le < epb && e < nE;
+  extern __shared__ double vf_raw[];
+  S* sm = reinterpret_cast<S*>(vf_raw);
+  S* sx = sm + le * 3 * nb;
+  S* sy = sx + nb;
+  S* su = sy + nb;
+  if (live) sx[r] = (pc_mix64(seed * 0x100000001B3ull + size_t(e) * nb + r) >> 63) ? S(1) : S(-1);
+  __syncthreads();
+  const S* Je = J + size_t(live ? e : 0) * nb * nb;
+  if (live) {
+    S y = S(0);
+    for (int c = 0; c < nb; ++c) y += Je[size_t(c) * nb + r] * sx[c];
+    sy[r] = y;
+  }
+  __syncthreads();
+  if (live) {
+    S z = S(0);
+    for (int c = 0; c < nb; ++c) z += Je[size_t(c) * nb + r] * sy[c];
+    su[r] = sx[r] - S(c12[0]) * sy[r] + S(c12[1]) * z;
+  }
+  __syncthreads();
+  double rr = 0.0;
+  if (live) {
+    const S* Me = M + size_t(e) * nb * nb;
+    S t = S(0);
+    for (int c = 0; c < nb; ++c) t += Me[size_t(c) * nb + r] * su[c];
+    const double d = double(t) - double(sx[r]);
+    rr = d * d;
+  }
+  // per-element sum over its nb rows (the rows of one element are consecutive threads)
+  __shared__ double s_rows[256];
+  s_rows[threadIdx.x] = rr;
+  __syncthreads();
+  if (live && r == 0) {
+    double tt = 0.0;
+    for (int k = 0; k < nb; ++k) tt += s_rows[le * nb + k];
+    const int bad = tt > tau * tau * double(nb) ? 1 : 0;
+    flag[e] = bad;
+    if (bad) atomicAdd(count, 1);
+  }
 }
 
 template <typename S>

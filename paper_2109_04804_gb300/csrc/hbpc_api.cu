@@ -231,6 +231,9 @@ struct hbpc_ctx {
     __nv_bfloat16* W2T = nullptr; __nv_bfloat16* W3T = nullptr;
     float* mu = nullptr; float* sd = nullptr;
     float* ckey = nullptr; float* cmean = nullptr;   // stage classes and their mean inverses
+    int* vflag = nullptr;                             // per element: learned block failed its check
+    int* vcount = nullptr;                            // blocks replaced by the exact inverse (running sum)
+    unsigned long long builds = 0;
     int* cls = nullptr;                               // class of every training sample
     bool stats = false;
     int adam_t = 0;
@@ -251,6 +254,7 @@ struct hbpc_ctx {
   hbpc_stats stats{};
   std::string err;
   int nblocks = 0;
+  int vcount_base = 0;      // learned-block fallbacks before the last reset_stats
   int vcols = 0;            // columns of the FP64 basis V
   bool coop = false;        // CGS2 as one cooperative launch (all blocks resident)
   int coop_max_blocks = 0;  // resident blocks of the cooperative kernel
@@ -262,6 +266,9 @@ struct hbpc_ctx {
 namespace {
 
 constexpr int kMaxPcBlock = 160;   // largest BJ_ext block (shared-memory inverse)
+// A learned block M~ is kept when |M~ S x - x| <= tau |x| for a random sign
+// probe x; otherwise the element gets the exact inverse.
+constexpr double kPcVerifyTau = 0.5;
 
 hbpc_status fail(hbpc_ctx* ctx, hbpc_status code, const std::string& msg) {
   if (ctx) ctx->err = msg; else g_create_error = msg;
@@ -524,6 +531,8 @@ hbpc_status lp_alloc(hbpc_ctx* x) {
       (e = dalloc_any(x, &L.Fi, size_t(x->nE) * L.dinp)) || (e = dalloc_any(x, &L.H1i, size_t(x->nE) * H)) ||
       (e = dalloc_any(x, &L.H2i, size_t(x->nE) * H)))
     return e;
+  if ((e = dalloc_any(x, &L.vflag, size_t(x->nE))) || (e = dalloc_any(x, &L.vcount, 1))) return e;
+  HBPC_CK(x, cudaMemsetAsync(L.vcount, 0, sizeof(int), x->stream));
   L.mu = L.P + L.np_train;
   L.sd = L.mu + L.dinp;
   L.ckey = L.sd + L.dinp;
@@ -570,7 +579,7 @@ void lp_free(hbpc_ctx* x) {
                   (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
                   (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
                   (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
-                  (void*)L.lpart, (void*)L.idx, (void*)L.cls})
+                  (void*)L.lpart, (void*)L.idx, (void*)L.cls, (void*)L.vflag, (void*)L.vcount})
     cudaFree(q);
   L = hbpc_ctx::Learned{};
 }
@@ -699,6 +708,33 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   if (x->sol.pc == HBPC_PC_LEARNED) {   // M~ from the network instead of the LU
     if (collecting) x->lp.targets = false;   // no exact inverse for these rows
     if ((s0 = lp_infer(x, W, c1, c2)) != HBPC_OK) return s0;
+    // check every learned block with a random probe; the blocks that fail get
+    // the exact inverse (form S, Gauss-Jordan) instead
+    auto& L = x->lp;
+    const int epb = x->pc_threads / x->nb;
+    const unsigned long long seed = 0x5EED0000ull + (L.builds++);
+    if (mixed) {
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_verify<float><<<x->pc_grid, x->pc_threads, size_t(epb) * 3 * nb * sizeof(float), x->stream>>>(
+                   x->Mf, x->Jf, x->nb, int(x->nE), x->c12, seed, kPcVerifyTau, L.vflag, L.vcount));
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_form_S<float><<<int(x->nE), 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb,
+                                                                                           int(x->nE), x->c12, L.vflag));
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_invert<float><<<int(x->nE), 256, (nb * nb + nb) * sizeof(float) + nb * sizeof(int), x->stream>>>(
+                   x->Mf, x->nb, int(x->nE), x->singular, L.vflag));
+    } else {
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_verify<double><<<x->pc_grid, x->pc_threads, size_t(epb) * 3 * nb * sizeof(double), x->stream>>>(
+                   x->Mpc, x->Jpc, x->nb, int(x->nE), x->c12, seed, kPcVerifyTau, L.vflag, L.vcount));
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_form_S<double><<<int(x->nE), 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb,
+                                                                                             int(x->nE), x->c12, L.vflag));
+      HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+               k_pc_invert<double><<<int(x->nE), 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
+                   x->Mpc, x->nb, int(x->nE), x->singular, L.vflag));
+    }
+    HBPC_LAUNCH_CK(x, "learned block check");
     x->pc_built = true;
     x->pc_c1 = c1;
     x->pc_c2 = c2;
@@ -2077,9 +2113,17 @@ hbpc_status hbpc_newton_solve(hbpc_ctx* ctx, const double* b, double alpha1, dou
   return sync(ctx, "newton_solve");
 }
 
-hbpc_status hbpc_get_stats(const hbpc_ctx* ctx, hbpc_stats* out) {
-  if (!ctx || !out) return HBPC_ERR_INVALID_ARG;
+hbpc_status hbpc_get_stats(const hbpc_ctx* cctx, hbpc_stats* out) {
+  if (!cctx || !out) return HBPC_ERR_INVALID_ARG;
+  hbpc_ctx* ctx = const_cast<hbpc_ctx*>(cctx);
   *out = ctx->stats;
+  if (ctx->lp.vcount) {   // learned blocks replaced by exact inverses so far
+    int v = 0;
+    HBPC_CK(ctx, cudaMemcpyAsync(&v, ctx->lp.vcount, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    hbpc_status s = sync(ctx, "get_stats");
+    if (s != HBPC_OK) return s;
+    out->pc_exact_blocks = v - ctx->vcount_base;
+  }
   return HBPC_OK;
 }
 
@@ -2088,6 +2132,13 @@ hbpc_status hbpc_reset_stats(hbpc_ctx* ctx) {
   const double t = ctx->stats.t;
   ctx->stats = hbpc_stats{};
   ctx->stats.t = t;
+  if (ctx->lp.vcount) {
+    int v = 0;
+    HBPC_CK(ctx, cudaMemcpyAsync(&v, ctx->lp.vcount, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    hbpc_status s = sync(ctx, "reset_stats");
+    if (s != HBPC_OK) return s;
+    ctx->vcount_base = v;
+  }
   return HBPC_OK;
 }
 

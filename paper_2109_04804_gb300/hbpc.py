@@ -64,7 +64,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("newton_solves", ctypes.c_longlong),
                 ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
                 ("r1_evals", ctypes.c_longlong), ("r2_evals", ctypes.c_longlong),
-                ("launches", ctypes.c_longlong), ("t", ctypes.c_double), ("arnoldi_cols", ctypes.c_longlong)]
+                ("launches", ctypes.c_longlong), ("t", ctypes.c_double), ("arnoldi_cols", ctypes.c_longlong),
+                ("pc_exact_blocks", ctypes.c_longlong)]
 
 
 _P = ctypes.c_void_p

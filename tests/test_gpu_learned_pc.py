@@ -224,3 +224,31 @@ def test_learned_pc_training_cuts_gmres_iterations_same_answer(hb):
         assert err <= 1e-11, (pc, err)
         ctx.close()
     assert its[hb.PC_LEARNED] < its[hb.PC_NONE], its
+
+
+def test_learned_blocks_failing_their_check_fall_back_to_exact(hb):
+    """An untrained network (M~ close to I) fails the probe check on (nearly)
+    every element at dt = 0.08, so those blocks get the exact inverse: the solve
+    then takes about BJ_ext's iteration count, the counter reports the
+    fallbacks, and the root is the same."""
+    dt = 0.08
+    n = (6, 5)
+    ctx = euler_stage(hb, hb.PC_LEARNED, hb.PREC_FP64, dt, n)
+    ctx.pc_model_init(seed=3, out_scale=1e-3)
+    ref = euler_stage(hb, hb.PC_BJEXT, hb.PREC_FP64, dt, n)
+    w0 = inputs.density_wave(ctx.node_coords())
+    b = torch.from_numpy(w0.ravel().copy()).cuda()
+    its = []
+    outs = []
+    for c in (ctx, ref):
+        Wd = torch.empty_like(b)
+        c.reset_stats()
+        c.newton_solve(b, 1.0, 1.0, b, Wd)
+        its.append(c.stats())
+        outs.append(Wd.cpu().numpy())
+    st = its[0]
+    assert st["pc_exact_blocks"] >= 0.9 * 30 * st["newton_its"]    # (nearly) every element, every build
+    assert st["gmres_its"] <= 1.5 * its[1]["gmres_its"] + 2
+    assert np.linalg.norm(outs[0] - outs[1]) <= 1e-11 * np.linalg.norm(outs[1])
+    ctx.close()
+    ref.close()

@@ -4,8 +4,13 @@ Workload (default): 2-D linear advection u_t + div((1, 1) u) = 0 on the periodic
 unit square, 64 x 64 elements, N = 5 (Gauss-Lobatto), u0 = sin(2 pi x) sin(2 pi y),
 HBPC(8, 4) (the highest order of the paper), CFL 8 -> dt = 1/96, matrix-free
 Newton-GMRES with the paper's BJ_ext preconditioner, eps_Newton = 1e-12 with
-the absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5, FP64.  One bench step = one HBPC time step (15 implicit
-stage solves).  Metric: DOF-timesteps/s = n_dof x steps / device seconds.
+the absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5, mixed precision (FP64
+Newton residual, update and state; FP32 Krylov loop).  One bench step = one
+HBPC time step (15 implicit stage solves).  Metric: DOF-timesteps/s = n_dof x
+steps / device seconds.  The same line carries, under "learned_vs_plain", the
+metric's comparison on the Euler vortex workload (learned block preconditioner
+trained on the GPU from the run's own Newton-GMRES data vs plain GMRES and
+BJ_ext; --no-vortex skips it).
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
   python bench.py --workload burgers_batch   (256 viscous Burgers instances, below)
@@ -291,6 +296,19 @@ def run_ours(args):
             "gpu_launches": int(stats["launches"]), "roofline": roofline, "e2e": e2e, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(dt)
+    if rank == 0 and world == 1 and not args.no_vortex:
+        # the metric's comparison, on the Euler vortex workload (learned block
+        # preconditioner trained on the run's own Newton-GMRES data vs plain
+        # GMRES and BJ_ext); see --workload euler_vortex for the full line
+        va = argparse.Namespace(steps=1, warmup=2)
+        v = run_vortex(va, emit=False)
+        ln, pl, bj = v["learned"], v["plain_gmres"], v["bjext"]
+        line["learned_vs_plain"] = {
+            "workload": v["config"]["workload"], "unit": UNIT,
+            "learned": ln, "plain_gmres": pl, "bjext": bj,
+            "speedup_learned_over_plain": (ln["value"] / pl["value"]) if pl["value"] > 0 else None,
+            "speedup_learned_over_bjext": (ln["value"] / bj["value"]) if bj["value"] > 0 else None,
+            "training": v["config"]["training"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -462,7 +480,7 @@ def vortex_dt():
     return VORTEX["cfl"] / sum(lam[m] * (VORTEX["N"] + 1) / h[m] for m in range(2))
 
 
-def run_vortex(args):
+def run_vortex(args, emit=True):
     """2-D Euler isentropic vortex (strength 5, Mach 0.5) on [-10, 10]^2, 128 x 128
     elements, N = 4, Rusanov, HBPC(6, 2), CFL 10, Newton tol 1e-10, mixed
     precision.  The learned block preconditioner is trained on the GPU on
@@ -568,7 +586,9 @@ def run_vortex(args):
                                               "loss_first_last": probe_losses},
                                     "train_s": round(t_train, 2)}},
             "gpu_launches": head["launches"], "learned": r_ln, "bjext": r_bj, "plain_gmres": r_pl}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_reference(args):
@@ -604,6 +624,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-vortex", action="store_true",
+                    help="skip the learned-vs-plain-GMRES comparison on the Euler vortex in the default line")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
     ap.add_argument("--workload", default="advection2d", choices=["advection2d", "burgers_batch", "euler_vortex"],

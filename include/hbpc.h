@@ -304,14 +304,14 @@ hbpc_status hbpc_fp64_fma_peak(double* gflops);
 
 /* Launch-shape autotuner (no counterpart in the paper): times, on the
  * context's own buffers, the candidate shapes of the Krylov reductions (blocks
- * = 1..4 x SMs; the CGS2 column at j = m/2) and of the block-preconditioner
+ * = 1..4 x SMs; CGS2 columns at j = 16 and m/2) and of the block-preconditioner
  * apply (1, 2, 4, 8 or 16 elements per block, at most 256 threads), median of
  * 7 launches each, and
  * keeps the fastest.  Call it before stepping or between steps; the result
  * changes only the summation order of the reductions.  out may be NULL. */
 typedef struct {
   int krylov_blocks;        /* chosen blocks of the Krylov reductions */
-  double krylov_us;         /* its time per CGS2 column (microseconds) */
+  double krylov_us;         /* its time for the two probe columns (microseconds) */
   double krylov_us_default; /* the same at the creation-time shape */
   int pc_elems_per_block;   /* chosen elements per block of the apply */
   double pc_us;             /* its time per apply (0 without a block preconditioner) */

@@ -44,7 +44,7 @@ struct BKrylovT {
 // part[tile * stride + i] (one tile per block iteration; fixed-order sums).
 template <typename S>
 __device__ __forceinline__ void bk_tile_dots(const BKrylovT<S>& K, const S* q, long long r0, int cnt, int j,
-                                             double* part_row, double* s_red) {
+                                             double* part_row, typename AccOf<S>::type* s_red) {
   using A = typename AccOf<S>::type;
   A qv[kRows];
   bool in[kRows];
@@ -58,7 +58,7 @@ __device__ __forceinline__ void bk_tile_dots(const BKrylovT<S>& K, const S* q, l
   __syncthreads();
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     double t = 0.0;
-    for (int w = 0; w < kVecWarps; ++w) t += s_red[i * kVecWarps + w];
+    for (int w = 0; w < kVecWarps; ++w) t += double(s_red[i * kVecWarps + w]);
     part_row[i] = t;
   }
   __syncthreads();
@@ -85,7 +85,7 @@ __device__ __forceinline__ void bk_reduce(const BKrylovT<S>& K, int cnt, int str
 // cooperative launch (grid-wide barriers between the phases; the launch is
 // refused if the grid cannot be resident).  The early exit and the column
 // index are read before any block writes the state, so they are grid-uniform.
-// Dynamic shared memory: (m + 1) kVecWarps doubles.
+// Dynamic shared memory: (m + 1)(kVecWarps + 1) values of the accumulation type.
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
   using A = typename AccOf<S>::type;
@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
   const int j = st->j, cnt = j + 1, m = K.m;
   const int stride = m + 3, hstride = 2 * (m + 2);
   S* q = K.V + size_t(j + 1) * K.ld;
-  extern __shared__ double s_red[];
+  extern __shared__ double sm_raw[];
+  A* s_red = reinterpret_cast<A*>(sm_raw);            // [m + 1][kVecWarps]
+  A* s_c = s_red + size_t(m + 1) * kVecWarps;          // [m + 1] coefficients of the tile's instance
+  __shared__ double s_w[kVecWarps];
   // pass 1: dots
   for (int t = blockIdx.x; t < K.ntiles; t += gridDim.x) {
     if (K.conv[K.tinst[t]]) continue;
@@ -113,6 +116,8 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
       const double* h = K.hc + size_t(inst) * hstride + (pass ? (m + 2) : 0);
       const long long r0 = K.trow[t];
       const int rows = K.tcnt[t];
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) s_c[i] = A(__ldcg(h + i));
+      __syncthreads();
       A x[kRows];
       bool in[kRows];
 #pragma unroll
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
         in[r] = row < rows;
         x[r] = in[r] ? A(q[r0 + row]) : A(0);
       }
-      col_axpy(K.V, K.ld, size_t(r0) + threadIdx.x, x, in, j + 1, h, static_cast<const double*>(nullptr));
+      col_axpy_c(K.V, K.ld, size_t(r0) + threadIdx.x, x, in, j + 1, s_c);
       A sq = A(0);
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
@@ -133,11 +138,11 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
         bk_tile_dots(K, q, r0, rows, j, K.part + size_t(t) * stride, s_red);
       } else {
         sq = warp_sum(sq);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = double(sq);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = double(sq);
         __syncthreads();
         if (threadIdx.x == 0) {
           double tt = 0.0;
-          for (int w = 0; w < kVecWarps; ++w) tt += s_red[w];
+          for (int w = 0; w < kVecWarps; ++w) tt += s_w[w];
           K.part[size_t(t) * stride] = tt;
         }
         __syncthreads();

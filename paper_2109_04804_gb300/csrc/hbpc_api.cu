@@ -786,7 +786,7 @@ template <typename S>
 void cgs_launch(hbpc_ctx* x, const KrylovT<S>& K) {
   if (x->coop) {   // one cooperative launch (k_cgs_coop) instead of four
     const size_t m1 = size_t(K.m + 1);
-    const size_t shm = std::max(m1 * (kVecWarps + 1), 3 * (m1 + 1)) * sizeof(double);
+    const size_t shm = std::max(m1 * (kVecWarps + 1) * sizeof(typename AccOf<S>::type), 3 * (m1 + 1) * sizeof(double));
     void* args[] = {const_cast<KrylovT<S>*>(&K)};
     HBPC_RUN(x, HBPC_PHASE_DOT, 1,
              cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cgs_coop<S>), dim3(x->nblocks),
@@ -995,7 +995,7 @@ hbpc_status gmres_bf(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const size_t n2 = size_t(2 * x->ndof);
   BKrylovT<float>& K = x->BK;
   const int grid = x->bk_grid;
-  const size_t shm = size_t(K.m + 1) * kVecWarps * sizeof(double);
+  const size_t shm = size_t(K.m + 1) * (kVecWarps + 1) * sizeof(double);
   hbpc_status s;
   HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
   if ((s = to_float(x, x->G, x->Vf, n2)) != HBPC_OK) return s;
@@ -1624,7 +1624,7 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
 // kernels on the context's own buffers and keeps the fastest.
 //   Krylov reductions: blocks in {1, 2, 3, 4} x SMs (at most one row tile per
 //     block, and resident all at once for the cooperative CGS2 kernel); timed
-//     on a CGS2 column at j = m/2 (the state is restored afterwards).
+//     on CGS2 columns at j = 16 and j = m/2 (the state is restored afterwards).
 //   Block preconditioner apply: elements per block in {1, 2, 4, 8, 16} (one
 //     thread per block row, at most the 256 threads the kernel is built for).
 // Every timing is the median of 7 launches after 2 warm-ups (CUDA events on
@@ -1657,10 +1657,13 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
   GmresState saved{};
   HBPC_CK(x, cudaMemcpy(&saved, x->st, sizeof(GmresState), cudaMemcpyDeviceToHost));
+  // the CGS2 column is timed at two column indices, a short one (most
+  // iterations of a well-preconditioned solve) and the middle of a cycle
   GmresState probe = saved;
-  probe.j = std::max(1, x->sol.gmres_restart / 2);
   probe.done = 0; probe.its = 0; probe.max_its = 1 << 30; probe.m = x->sol.gmres_restart;
   probe.target = 0.0; probe.reorth = 0;
+  const int jprobe[2] = {std::min(16, std::max(1, x->sol.gmres_restart - 1)),
+                         std::max(1, x->sol.gmres_restart / 2)};
   GmresState* hprobe = x->st_host;           // pinned
   *hprobe = probe;
   const size_t n2 = size_t(2 * x->ndof);
@@ -1674,10 +1677,14 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
     if (x->coop) nbk = std::min(nbk, x->coop_max_blocks);
     if (c > 1 && nbk <= std::min((c - 1) * x->sms, std::max(1, tiles))) continue;
     x->nblocks = nbk; x->K.nblocks = nbk; x->Kf.nblocks = nbk;
-    const double us = median_us(x, [&]() {
-      cudaMemcpyAsync(x->st, hprobe, sizeof(GmresState), cudaMemcpyHostToDevice, x->stream);
-      if (mixed) cgs_launch<float>(x, x->Kf); else cgs_launch<double>(x, x->K);
-    });
+    double us = 0.0;
+    for (int jp : jprobe) {
+      hprobe->j = jp;
+      us += median_us(x, [&]() {
+        cudaMemcpyAsync(x->st, hprobe, sizeof(GmresState), cudaMemcpyHostToDevice, x->stream);
+        if (mixed) cgs_launch<float>(x, x->Kf); else cgs_launch<double>(x, x->K);
+      });
+    }
     if (cudaGetLastError() != cudaSuccess) continue;   // a shape that cannot launch is no candidate
     if (nbk == old_blocks) first_k = us;
     if (us < best_k) { best_k = us; best_b = nbk; }
@@ -1757,7 +1764,7 @@ hbpc_status bk_setup(hbpc_ctx* x) {
   itile.push_back(int(tcnt.size()));
   const int nt = int(tcnt.size());
   int per_sm = 0;
-  const size_t shm = size_t(m + 1) * kVecWarps * sizeof(double);
+  const size_t shm = size_t(m + 1) * (kVecWarps + 1) * sizeof(double);
   if (shm > 48 * 1024)
     cudaFuncSetAttribute(k_bcgs_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcgs_coop<float>, kVecThreads, shm);

@@ -272,14 +272,100 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
   finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
 }
 
-// The CGS2 passes and the finalisation in one cooperative launch, the kernel
-// boundaries replaced by grid-wide barriers; the second Gram-Schmidt pass runs
-// only when the DGKS test asks for it (the four-kernel form always runs it).
-// Launched with cudaLaunchCooperativeKernel, which refuses a grid whose blocks
-// cannot all be resident, so every barrier is reached by every block.  The
-// early exit reads st->done before any block writes the state (the state is
-// written only by block 0 after the last barrier), so it is grid-uniform.
-// Dynamic shared memory: max((m+1)(kVecWarps+1), 3(m+2)) doubles.
+// One pass of the cooperative CGS2 kernel over the block's tiles of the new
+// vector q = V_{j+1}: q -= sum_i c_i V_i (UPDATE, coefficients c already in the
+// accumulation type), then either the dot products with V_0..V_{cnt-1} (DOTS,
+// to partial[b][col_out + i]) or the squared norms of the W and sigma halves
+// (to partial[b][col_out], [col_out + 1]); QQ adds |q|^2 to partial[b][qq_col].
+// The hot loop has no FP64 instruction for an FP32 basis (GB300 runs FP64 at
+// 1/64 of the FP32 rate); only the cross-warp sums are FP64.
+template <typename S, bool UPDATE, bool DOTS, bool QQ>
+__device__ __forceinline__ void coop_pass(const KrylovT<S>& K, S* q, int cnt, const typename AccOf<S>::type* s_c,
+                                          typename AccOf<S>::type* s_red, int col_out, int qq_col) {
+  using A = typename AccOf<S>::type;
+  const int stride = cgs_stride(K.m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double s_w[3][kVecWarps];
+  if (DOTS)
+    for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = A(0);
+  __syncthreads();
+  A aw = A(0), as = A(0), qq = A(0);
+  const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const size_t base = tile * kTile + threadIdx.x;
+    A x[kRows];
+    bool in[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      in[r] = row < K.n2;
+      x[r] = in[r] ? A(q[row]) : A(0);
+    }
+    if (UPDATE) {
+      col_axpy_c(K.V, K.ld, base, x, in, cnt, s_c);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        if (in[r]) {
+          q[row] = S(x[r]);
+          if (row < K.half) aw += x[r] * x[r]; else as += x[r] * x[r];
+        }
+      }
+    }
+    if (QQ)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) qq += x[r] * x[r];
+    if (DOTS) col_dots<true>(K.V, K.ld, base, x, in, cnt, s_red);
+  }
+  aw = warp_sum(aw); as = warp_sum(as); qq = warp_sum(qq);
+  if (lane == 0) { s_w[0][warp] = double(aw); s_w[1][warp] = double(as); s_w[2][warp] = double(qq); }
+  __syncthreads();
+  double* prow = K.partial + size_t(blockIdx.x) * stride;
+  if (DOTS) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < kVecWarps; ++w) t += double(s_red[i * kVecWarps + w]);
+      prow[col_out + i] = t;
+    }
+  } else if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) { ta += s_w[0][w]; tb += s_w[1][w]; }
+    prow[col_out] = ta;
+    prow[col_out + 1] = tb;
+  }
+  if (QQ && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) t += s_w[2][w];
+    prow[qq_col] = t;
+  }
+}
+
+// Sum of the blocks' partials of columns [col0, col0 + cnt) into out[c] (times
+// scale[c] when given), one warp per column spread over the blocks (the
+// reduction is done once, not redundantly by every block).
+template <typename S>
+__device__ __forceinline__ void coop_reduce(const KrylovT<S>& K, int col0, int cnt, const double* scale,
+                                            double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stride = cgs_stride(K.m);
+  for (int c = blockIdx.x * kVecWarps + warp; c < cnt; c += gridDim.x * kVecWarps) {
+    const double t = strided_sum(K.partial + col0 + c, stride, lane, K.nblocks);
+    if (lane == 0) out[c] = scale ? t * scale[c] : t;
+  }
+}
+
+// One Arnoldi column in one cooperative launch (kernel boundaries replaced by
+// grid-wide barriers): classical Gram-Schmidt, a second pass only when the DGKS
+// test asks for it (|q - sum h_i v_i| < |q| / sqrt 2; the four-kernel form
+// always runs it), the Hessenberg column, Givens rotation and stopping test.
+// Every reduction across blocks is done once by one warp per column (written to
+// hc) and read back by all after a barrier.  Launched with
+// cudaLaunchCooperativeKernel, which refuses a grid that cannot be resident.
+// The early exit and the column index are read before any block writes the
+// state (block 0 writes it after the last barrier), so they are grid-uniform,
+// and so is the DGKS decision (every block reads the same reduced values).
+// Dynamic shared memory: max((m + 1)(kVecWarps + 1) accumulation values,
+// 3 (m + 2) doubles).
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
   using A = typename AccOf<S>::type;
@@ -287,83 +373,54 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
   cg::grid_group grid = cg::this_grid();
   GmresState* st = K.st;
   if (st->done) return;
-  const int j = st->j, cnt = j + 1;
-  const int stride = cgs_stride(K.m);
+  const int j = st->j, cnt = j + 1, m = K.m;
   extern __shared__ double sm[];
-  __shared__ double s_qq[kVecWarps];
+  A* s_red = reinterpret_cast<A*>(sm);              // [m + 1][kVecWarps]
+  A* s_c = s_red + size_t(m + 1) * kVecWarps;         // [m + 1] update coefficients
   __shared__ int s_flag;
-  {   // pass A: partial dots <q, V_i>_b and |q|^2
-    const S* q = K.V + size_t(j + 1) * K.ld;
-    double* s_red = sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double qq_b = 0.0;
-    for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = 0.0;
-    __syncthreads();
-    const size_t ntiles = (K.n2 + kTile - 1) / kTile;
-    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const size_t base = tile * kTile + threadIdx.x;
-      A qv[kRows];
-      bool in[kRows];
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const size_t row = base + size_t(r) * kVecThreads;
-        in[r] = row < K.n2;
-        qv[r] = in[r] ? A(q[row]) : A(0);
-      }
-      col_dots<true>(K.V, K.ld, base, qv, in, cnt, s_red);
-      A qq = A(0);
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) qq += qv[r] * qv[r];
-      qq_b += double(warp_sum(qq));
-    }
-    if (lane == 0) s_qq[warp] = qq_b;
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      double t = 0.0;
-      for (int w = 0; w < kVecWarps; ++w) t += s_red[i * kVecWarps + w];
-      K.partial[size_t(blockIdx.x) * stride + i] = t;
-    }
-    if (threadIdx.x == 0) {   // |q|^2 of this block's rows; column 2m+1 is free until pass C
-      double t = 0.0;
-      for (int w = 0; w < kVecWarps; ++w) t += s_qq[w];
-      K.partial[size_t(blockIdx.x) * stride + 2 * K.m + 1] = t;
-    }
-  }
-  __threadfence();
+  S* q = K.V + size_t(j + 1) * K.ld;
+  // pass 1: <q, V_i> and |q|^2
+  coop_pass<S, false, true, true>(K, q, cnt, s_c, s_red, 0, 2 * m + 1);
   grid.sync();
-  // first-pass coefficients h_i = <q, v_i> and |q|^2, reduced redundantly (and
-  // identically) by every block; a second Gram-Schmidt pass only when the
-  // projection removed more than half of |q|^2 (the DGKS criterion
-  // |q - sum h_i v_i| < |q| / sqrt 2), decided identically in every block
-  cgs_reduce_cols(K.partial, stride, K.nblocks, 0, cnt, K.vscale, sm);
-  if ((threadIdx.x >> 5) == 0) {
-    const double t = strided_sum(K.partial + 2 * K.m + 1, stride, threadIdx.x & 31, K.nblocks);
-    if (threadIdx.x == 0) s_qq[0] = t;
+  // h_i = vscale_i <q, V_i> into hc[0..cnt), |q|^2 into hc[m + 1]
+  coop_reduce(K, 0, cnt, K.vscale, K.hc);
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 32) {
+    const double t = strided_sum(K.partial + 2 * m + 1, cgs_stride(m), threadIdx.x, K.nblocks);
+    if (threadIdx.x == 0) K.hc[m + 1] = t;
   }
-  __syncthreads();
+  grid.sync();
   if (threadIdx.x == 0) {
     double hh = 0.0;
-    for (int i = 0; i < cnt; ++i) hh += sm[i] * sm[i];
-    s_flag = (s_qq[0] - hh) < 0.5 * s_qq[0] ? 1 : 0;
+    for (int i = 0; i < cnt; ++i) hh += __ldcg(K.hc + i) * __ldcg(K.hc + i);
+    const double qq = __ldcg(K.hc + m + 1);
+    s_flag = (qq - hh) < 0.5 * qq ? 1 : 0;
   }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(__ldcg(K.hc + i) * K.vscale[i]);
   __syncthreads();
-  if (s_flag) {
-    cgs_update_body<S, true>(K, j, 0, K.m + 1, sm, sm + (K.m + 1), false);      // pass B
-    __threadfence();
+  if (!s_flag) {
+    coop_pass<S, true, false, false>(K, q, cnt, s_c, s_red, 2 * (m + 1), 0);   // the only update
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) K.hc[(m + 2) + i] = 0.0;
     grid.sync();
-    cgs_update_body<S, false>(K, j, K.m + 1, 2 * (K.m + 1), sm, nullptr);      // pass C
   } else {
-    cgs_update_body<S, false>(K, j, 0, 2 * (K.m + 1), sm, nullptr, false);     // the only update
-    if (blockIdx.x == 0)   // its coefficients went to the second slot: the first is zero
-      for (int i = threadIdx.x; i <= j; i += blockDim.x) K.hc[i] = 0.0;
+    coop_pass<S, true, true, false>(K, q, cnt, s_c, s_red, m + 1, 0);          // update + second dots
+    grid.sync();
+    coop_reduce(K, m + 1, cnt, K.vscale, K.hc + (m + 2));
+    grid.sync();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(__ldcg(K.hc + (m + 2) + i) * K.vscale[i]);
+    __syncthreads();
+    coop_pass<S, true, false, false>(K, q, cnt, s_c, s_red, 2 * (m + 1), 0);   // second update + norms
+    grid.sync();
   }
-  __threadfence();
-  grid.sync();
   if (blockIdx.x != 0) return;
   __shared__ double nrm[2];
-  cgs_reduce_cols(K.partial, stride, K.nblocks, 2 * (K.m + 1), 2, nullptr, nrm);
-  double* Hj = K.H + size_t(j) * (K.m + 1);
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = K.hc[i] + K.hc[(K.m + 2) + i];
+  if (threadIdx.x < 64) {
+    const int w = threadIdx.x >> 5;
+    const double t = strided_sum(K.partial + 2 * (m + 1) + w, cgs_stride(m), threadIdx.x & 31, K.nblocks);
+    if ((threadIdx.x & 31) == 0) nrm[w] = t;
+  }
+  double* Hj = K.H + size_t(j) * (m + 1);
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = __ldcg(K.hc + i) + __ldcg(K.hc + (m + 2) + i);
   __syncthreads();
   finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
 }

@@ -85,9 +85,9 @@ __device__ __forceinline__ double strided_sum(const double* p, int stride, int l
 // lane 0 stores (ACC: adds) the warp's sum of column i at s_red[i kVecWarps +
 // warp].  Four columns per step, so that 4 kRows independent loads are in
 // flight (the sums of every column keep their order).
-template <bool ACC, typename S, typename A>
+template <bool ACC, typename S, typename A, typename R>
 __device__ __forceinline__ void col_dots(const S* V, size_t ld, size_t base, const A* x, const bool* in, int cnt,
-                                         double* s_red) {
+                                         R* s_red) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int i = 0;
   for (; i + 3 < cnt; i += 4) {
@@ -104,8 +104,8 @@ __device__ __forceinline__ void col_dots(const S* V, size_t ld, size_t base, con
       for (int r = 0; r < kRows; ++r) a += x[r] * v[c][r];
       a = warp_sum(a);
       if (lane == 0) {
-        if (ACC) s_red[(i + c) * kVecWarps + warp] += double(a);
-        else s_red[(i + c) * kVecWarps + warp] = double(a);
+        if (ACC) s_red[(i + c) * kVecWarps + warp] += R(a);
+        else s_red[(i + c) * kVecWarps + warp] = R(a);
       }
     }
   }
@@ -116,10 +116,34 @@ __device__ __forceinline__ void col_dots(const S* V, size_t ld, size_t base, con
       if (in[r]) a += x[r] * A(V[size_t(i) * ld + base + size_t(r) * kVecThreads]);
     a = warp_sum(a);
     if (lane == 0) {
-      if (ACC) s_red[i * kVecWarps + warp] += double(a);
-      else s_red[i * kVecWarps + warp] = double(a);
+      if (ACC) s_red[i * kVecWarps + warp] += R(a);
+      else s_red[i * kVecWarps + warp] = R(a);
     }
   }
+}
+
+// x[r] -= sum_i c[i] V_i(row) over columns [0, cnt) with coefficients already
+// in the accumulation type (no FP64 work in the loop), ascending i.
+template <typename S, typename A>
+__device__ __forceinline__ void col_axpy_c(const S* V, size_t ld, size_t base, A* x, const bool* in, int cnt,
+                                           const A* c) {
+  int i = 0;
+  for (; i + 3 < cnt; i += 4) {
+    A v[4][kRows];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        v[k][r] = in[r] ? A(V[size_t(i + k) * ld + base + size_t(r) * kVecThreads]) : A(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) x[r] -= c[i + k] * v[k][r];
+  }
+  for (; i < cnt; ++i)
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      if (in[r]) x[r] -= c[i] * A(V[size_t(i) * ld + base + size_t(r) * kVecThreads]);
 }
 
 // x[r] -= sum_i c_i V_i(row) over columns [0, cnt), c_i = coef[i] (times

@@ -85,7 +85,8 @@ __device__ __forceinline__ void bk_reduce(const BKrylovT<S>& K, int cnt, int str
 // cooperative launch (grid-wide barriers between the phases; the launch is
 // refused if the grid cannot be resident).  The early exit and the column
 // index are read before any block writes the state, so they are grid-uniform.
-// Dynamic shared memory: (m + 1)(kVecWarps + 1) values of the accumulation type.
+// Dynamic shared memory: (m + 1)(kVecWarps + 1) doubles (covers the
+// accumulation arrays and the 3 m + 2 doubles of the per-instance finalisation).
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
   using A = typename AccOf<S>::type;
@@ -154,34 +155,44 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
       grid.sync();
     }
   }
-  // per instance: norm, Hessenberg column h + c, rotations, residual (one warp
-  // per instance, lane 0 runs the sequential rotation chain)
+  // per instance (one block each): norm, Hessenberg column h + c, rotations,
+  // residual; the column and the rotations are staged in shared memory in one
+  // parallel round trip, thread 0 runs the sequential rotation chain there
   {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kVecWarps + warp, nw = gridDim.x * kVecWarps;
-    for (int inst = gw; inst < K.ninst; inst += nw) {
-      if (K.conv[inst]) continue;
+    double* hcol = reinterpret_cast<double*>(sm_raw);     // [m + 2]
+    double* scs = hcol + (m + 2);                         // [m]
+    double* ssn = scs + m;                                // [m]
+    __shared__ double s_nq;
+    for (int inst = blockIdx.x; inst < K.ninst; inst += gridDim.x) {
+      if (K.conv[inst]) continue;                         // block-uniform
       const int t0 = K.itile[inst];
-      const double s = strided_sum(K.part + size_t(t0) * stride, stride, lane, K.itile[inst + 1] - t0);
-      if (lane == 0) {
-        const double* hh = K.hc + size_t(inst) * hstride;
-        double* Hj = K.H + size_t(inst) * (m + 1) * m + size_t(j) * (m + 1);
-        double* cs = K.cs + size_t(inst) * m;
-        double* sn = K.sn + size_t(inst) * m;
+      if (threadIdx.x < 32) {
+        const double sq = strided_sum(K.part + size_t(t0) * stride, stride, threadIdx.x, K.itile[inst + 1] - t0);
+        if (threadIdx.x == 0) s_nq = sq;
+      }
+      const double* hh = K.hc + size_t(inst) * hstride;
+      double* Hj = K.H + size_t(inst) * (m + 1) * m + size_t(j) * (m + 1);
+      double* cs = K.cs + size_t(inst) * m;
+      double* sn = K.sn + size_t(inst) * m;
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        hcol[i] = __ldcg(hh + i) + __ldcg(hh + (m + 2) + i);
+        if (i < j) { scs[i] = cs[i]; ssn[i] = sn[i]; }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
         double* gg = K.g + size_t(inst) * (m + 1);
-        for (int i = 0; i <= j; ++i) Hj[i] = hh[i] + hh[(m + 2) + i];
-        const double hnext = sqrt(s);
-        Hj[j + 1] = hnext;
+        const double hnext = sqrt(s_nq);
+        hcol[j + 1] = hnext;
         K.inv[inst] = hnext > 0.0 ? 1.0 / hnext : 0.0;
         for (int i = 0; i < j; ++i) {
-          const double a = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
-          Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
-          Hj[i] = a;
+          const double a = scs[i] * hcol[i] + ssn[i] * hcol[i + 1];
+          hcol[i + 1] = -ssn[i] * hcol[i] + scs[i] * hcol[i + 1];
+          hcol[i] = a;
         }
-        const double den = hypot(Hj[j], Hj[j + 1]);
-        const double c = den > 0.0 ? Hj[j] / den : 1.0, sv = den > 0.0 ? Hj[j + 1] / den : 0.0;
+        const double den = hypot(hcol[j], hcol[j + 1]);
+        const double c = den > 0.0 ? hcol[j] / den : 1.0, sv = den > 0.0 ? hcol[j + 1] / den : 0.0;
         cs[j] = c; sn[j] = sv;
-        Hj[j] = den; Hj[j + 1] = 0.0;
+        hcol[j] = den; hcol[j + 1] = 0.0;
         const double gj = gg[j];
         gg[j + 1] = -sv * gj;
         gg[j] = c * gj;
@@ -189,6 +200,9 @@ __global__ void __launch_bounds__(kVecThreads) k_bcgs_coop(BKrylovT<S> K) {
         K.jn[inst] = j + 1;
         if (K.resid[inst] <= K.target[inst] || !(hnext > 0.0)) K.conv[inst] = 1;
       }
+      __syncthreads();
+      for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hj[i] = hcol[i];
+      __syncthreads();
     }
   }
   grid.sync();

@@ -786,7 +786,8 @@ template <typename S>
 void cgs_launch(hbpc_ctx* x, const KrylovT<S>& K) {
   if (x->coop) {   // one cooperative launch (k_cgs_coop) instead of four
     const size_t m1 = size_t(K.m + 1);
-    const size_t shm = std::max(m1 * (kVecWarps + 1) * sizeof(typename AccOf<S>::type), 3 * (m1 + 1) * sizeof(double));
+    const size_t shm = std::max(m1 * sizeof(double) + m1 * (kVecWarps + 1) * sizeof(typename AccOf<S>::type),
+                                3 * (m1 + 1) * sizeof(double));
     void* args[] = {const_cast<KrylovT<S>*>(&K)};
     HBPC_RUN(x, HBPC_PHASE_DOT, 1,
              cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cgs_coop<S>), dim3(x->nblocks),
@@ -1528,7 +1529,7 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
     int coop_attr = 0, per_sm_d = 0, per_sm_f = 0;
     cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev);
     const size_t m1 = size_t(solver->gmres_restart + 1);
-    const size_t shm = std::max(m1 * (kVecWarps + 1), 3 * (m1 + 1)) * sizeof(double);
+    const size_t shm = std::max(m1 * (kVecWarps + 2), 3 * (m1 + 1)) * sizeof(double);
     if (shm > 48 * 1024) {
       cudaFuncSetAttribute(k_cgs_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
       cudaFuncSetAttribute(k_cgs_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));

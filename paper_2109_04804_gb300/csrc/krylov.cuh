@@ -364,8 +364,8 @@ __device__ __forceinline__ void coop_reduce(const KrylovT<S>& K, int col0, int c
 // The early exit and the column index are read before any block writes the
 // state (block 0 writes it after the last barrier), so they are grid-uniform,
 // and so is the DGKS decision (every block reads the same reduced values).
-// Dynamic shared memory: max((m + 1)(kVecWarps + 1) accumulation values,
-// 3 (m + 2) doubles).
+// Dynamic shared memory: max((m + 1) doubles + (m + 1)(kVecWarps + 1)
+// accumulation values, 3 (m + 2) doubles).
 template <typename S>
 __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
   using A = typename AccOf<S>::type;
@@ -375,9 +375,11 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
   if (st->done) return;
   const int j = st->j, cnt = j + 1, m = K.m;
   extern __shared__ double sm[];
-  A* s_red = reinterpret_cast<A*>(sm);              // [m + 1][kVecWarps]
+  double* s_h = sm;                                   // [m + 1] reduced coefficients
+  A* s_red = reinterpret_cast<A*>(s_h + (m + 1));     // [m + 1][kVecWarps]
   A* s_c = s_red + size_t(m + 1) * kVecWarps;         // [m + 1] update coefficients
   __shared__ int s_flag;
+  __shared__ double s_qq;
   S* q = K.V + size_t(j + 1) * K.ld;
   // pass 1: <q, V_i> and |q|^2
   coop_pass<S, false, true, true>(K, q, cnt, s_c, s_red, 0, 2 * m + 1);
@@ -389,13 +391,16 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
     if (threadIdx.x == 0) K.hc[m + 1] = t;
   }
   grid.sync();
+  // the reduced values into shared memory in one parallel round trip
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_h[i] = __ldcg(K.hc + i);
+  if (threadIdx.x == 0) s_qq = __ldcg(K.hc + m + 1);
+  __syncthreads();
   if (threadIdx.x == 0) {
     double hh = 0.0;
-    for (int i = 0; i < cnt; ++i) hh += __ldcg(K.hc + i) * __ldcg(K.hc + i);
-    const double qq = __ldcg(K.hc + m + 1);
-    s_flag = (qq - hh) < 0.5 * qq ? 1 : 0;
+    for (int i = 0; i < cnt; ++i) hh += s_h[i] * s_h[i];
+    s_flag = (s_qq - hh) < 0.5 * s_qq ? 1 : 0;
   }
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(__ldcg(K.hc + i) * K.vscale[i]);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(s_h[i] * K.vscale[i]);
   __syncthreads();
   if (!s_flag) {
     coop_pass<S, true, false, false>(K, q, cnt, s_c, s_red, 2 * (m + 1), 0);   // the only update

@@ -151,6 +151,13 @@ def pc_work_per_dof(mixed=False):
     return ((8.0 * nb + 16.0) if mixed else (16.0 * nb + 32.0)), 8.0 * nb + 4.0
 
 
+# DRAM bytes (read + write) per launch measured by ncu on this workload's
+# kernels (summaries in profiles/: k_cgs_coop_c2_advection_64x64_N5.md, the mean
+# of three captured columns; k_pc_apply_c2_advection_64x64_N5.md).  A kernel
+# changed after its capture must have its entry set to None.
+NCU_TRAFFIC = {"cgs2": 3.68e6, "pc_apply": 43.68e6, "jv": None}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -252,7 +259,8 @@ def run_ours(args):
         gb = bpd * ndof / avg / 1e9
         if mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are HBM-bound
             entries[ph] = {"kernel": name, "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
-                           "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": None,
+                           "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": NCU_TRAFFIC.get(ph),
+                           "algorithmic_bytes_per_launch": round(bpd * ndof),
                            "alu_tflops": round(gf / 1000.0, 3)}
         else:
             entries[ph] = {"kernel": name, "bound": "alu", "achieved": round(gf / 1000.0, 4),

@@ -304,7 +304,8 @@ hbpc_status hbpc_fp64_fma_peak(double* gflops);
 
 /* Launch-shape autotuner (no counterpart in the paper): times, on the
  * context's own buffers, the candidate shapes of the Krylov reductions (blocks
- * = 1..4 x SMs; CGS2 columns at j = 16 and m/2) and of the block-preconditioner
+ * = 1..4 x SMs or the row-tile count / 1..3; CGS2 columns at j = 16 and m/2)
+ * and of the block-preconditioner
  * apply (1, 2, 4, 8 or 16 elements per block, at most 256 threads), median of
  * 7 launches each, and
  * keeps the fastest.  Call it before stepping or between steps; the result

@@ -1623,9 +1623,10 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
 
 // Launch-shape autotuner: times the candidates of the two runtime-shaped hot
 // kernels on the context's own buffers and keeps the fastest.
-//   Krylov reductions: blocks in {1, 2, 3, 4} x SMs (at most one row tile per
-//     block, and resident all at once for the cooperative CGS2 kernel); timed
-//     on CGS2 columns at j = 16 and j = m/2 (the state is restored afterwards).
+//   Krylov reductions: blocks in {1, 2, 3, 4} x SMs and tiles / {1, 2, 3} (at
+//     most one row tile per block, and resident all at once for the
+//     cooperative CGS2 kernel); timed on CGS2 columns at j = 16 and j = m/2
+//     (the state is restored afterwards).
 //   Block preconditioner apply: elements per block in {1, 2, 4, 8, 16} (one
 //     thread per block row, at most the 256 threads the kernel is built for).
 // Every timing is the median of 7 launches after 2 warm-ups (CUDA events on
@@ -1673,10 +1674,19 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
   double best_k = 1e300;
   int best_b = old_blocks;
   double first_k = 0.0;
-  for (int c = 1; c <= 4; ++c) {
-    int nbk = std::min(c * x->sms, std::max(1, tiles));
-    if (x->coop) nbk = std::min(nbk, x->coop_max_blocks);
-    if (c > 1 && nbk <= std::min((c - 1) * x->sms, std::max(1, tiles))) continue;
+  // candidates: 1..4 x SMs, and the tile count divided by 1, 2, 3 (every block
+  // then gets the same number of tiles, which the grid barriers reward)
+  std::vector<int> kc;
+  for (int c = 1; c <= 4; ++c) kc.push_back(c * x->sms);
+  for (int d = 1; d <= 3; ++d) kc.push_back((std::max(1, tiles) + d - 1) / d);
+  for (int& v : kc) {
+    v = std::min(v, std::max(1, tiles));
+    if (x->coop) v = std::min(v, x->coop_max_blocks);
+    v = std::max(v, 1);
+  }
+  std::sort(kc.begin(), kc.end());
+  kc.erase(std::unique(kc.begin(), kc.end()), kc.end());
+  for (int nbk : kc) {
     x->nblocks = nbk; x->K.nblocks = nbk; x->Kf.nblocks = nbk;
     double us = 0.0;
     for (int jp : jprobe) {

@@ -31,7 +31,7 @@ def test_autotune_keeps_the_answer(hb, prec):
         if tune:
             t = c.autotune()
             sms = torch.cuda.get_device_properties(0).multi_processor_count
-            assert 1 <= t["krylov_blocks"] <= 4 * sms
+            assert 1 <= t["krylov_blocks"] <= max(4 * sms, 4096)
             assert 1 <= t["pc_elems_per_block"] <= 16
             assert t["krylov_us"] > 0 and t["pc_us"] > 0
             assert t["krylov_us"] <= t["krylov_us_default"] * 1.0001 or t["krylov_us_default"] == 0

@@ -153,9 +153,10 @@ def pc_work_per_dof(mixed=False):
 
 # DRAM bytes (read + write) per launch measured by ncu on this workload's
 # kernels (summaries in profiles/: k_cgs_coop_c2_advection_64x64_N5.md, the mean
-# of three captured columns; k_pc_apply_c2_advection_64x64_N5.md).  A kernel
+# of three captured columns; k_pc_apply_c2_advection_64x64_N5.md;
+# dg_operator_jv_pair_c2_advection_64x64_N5.md).  A kernel
 # changed after its capture must have its entry set to None.
-NCU_TRAFFIC = {"cgs2": 3.68e6, "pc_apply": 43.68e6, "jv": None}
+NCU_TRAFFIC = {"cgs2": 3.68e6, "pc_apply": 43.68e6, "jv": 1.20e6}
 
 
 def run_ours(args):
@@ -354,7 +355,7 @@ def cpu_baseline(dt, budget_s=20.0):
 
 BATCH = dict(n_inst=256, n_range=(16, 96), N_range=(3, 7), nu_range=(1e-3, 1e-2), seed=2024,
              q=6, kmax=2, cfl_finest=2.0, tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3,
-             gmres_restart=100, gmres_max_iter=3000, newton_max_iter=50, max_per_group=1)
+             gmres_restart=100, gmres_max_iter=3000, newton_max_iter=50, max_per_group=0)
 
 
 def batch_instances(n_inst):

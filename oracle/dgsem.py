@@ -24,7 +24,9 @@ same dissipation coefficient (evaluated at w, not differentiated).
 Scalar laws may carry a viscous term nu Laplace(w), discretised with the BR2
 lifting of Sec. 5.1.1 (``viscous``).  Its flux F^v = nu d does not depend on w,
 so it adds nu L_h(w) to R^(1) and, by Eq. 31-33 with dF^v/dw = 0 and
-eta = d_t, nu L_h(sigma) to R^(2).
+eta = d_t, nu L_h(sigma) to R^(2).  The Navier-Stokes law adds the viscous
+flux of Eq. 25 with the same lifting applied to w_grad = (v, T)
+(``viscous_ns``).
 """
 import numpy as np
 
@@ -157,6 +159,8 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False):
     res = disc.from_grid(out)
     if ph.nu != 0.0:
         res = res + viscous(disc, w if mode == "R1" else sigma, frozen_neighbor and mode == "R2")
+    if ph.law == laws.NAVIER_STOKES and ph.mu != 0.0:
+        res = res + viscous_ns(disc, w, sigma if mode == "R2" else None, frozen_neighbor and mode == "R2")
     return res
 
 
@@ -235,6 +239,114 @@ def viscous(disc, u, frozen_neighbor=False):
         out = out + H * (Disc._apply(b.Dhat, ph.nu * d, na)
                          + disc._lift(ph.nu * fp_grad, b.lhat_p, na)
                          - disc._lift(ph.nu * fm_grad, b.lhat_m, na))
+    return disc.from_grid(out)
+
+
+def br2_faces(disc, U, m, frozen_neighbor=False):
+    """BR2 face quantities of a grid array of channels U (channels on axis 0)
+    along direction m, for systems (Sec. 5.1.1): the broken gradient of every
+    channel (all d components, tangential ones included, as the viscous flux
+    of a system needs them) traced on the element's + and - faces, the
+    neighbours' values across those faces, the common value u* of Eq. 30 and
+    the face-local lifting that adds eta c_pm (2/h_m)(u* - u_own) to the normal
+    component (the same lifting as ``br2_traces``).
+    frozen_neighbor: the neighbours' channel values are taken as zero.
+    Returns dict with, for the + face ('p') and the - face ('m') of every
+    element, the left and right traces gL, gR (channels) and gradients dL, dR
+    (lists over the direction k of channel arrays) and u*."""
+    b = disc.basis
+    ph = disc.ph
+    ea, na = disc.elem_axis(m), disc.node_axis(m)
+    eta = ph.eta_br2
+    H = 2.0 / disc.mesh.h[m]
+    c_p = float(np.sum(b.l_p * b.lhat_p))
+    c_m = float(np.sum(b.l_m * b.lhat_m))
+    # broken gradient at the nodes, then traced on the two faces of direction m
+    DU = [(2.0 / disc.mesh.h[k]) * Disc._apply(b.D, U, disc.node_axis(k)) for k in range(disc.d)]
+    up = Disc._trace(b.l_p, U, na)
+    um = Disc._trace(b.l_m, U, na)
+    gp = [Disc._trace(b.l_p, x, na) for x in DU]
+    gm = [Disc._trace(b.l_m, x, na) for x in DU]
+    if frozen_neighbor:
+        nb_m, nb_gm = 0.0 * um, [0.0 * x for x in gm]    # right neighbour's - face
+        nb_p, nb_gp = 0.0 * up, [0.0 * x for x in gp]    # left neighbour's + face
+    else:
+        nb_m, nb_gm = np.roll(um, -1, axis=ea), [np.roll(x, -1, axis=ea) for x in gm]
+        nb_p, nb_gp = np.roll(up, 1, axis=ea), [np.roll(x, 1, axis=ea) for x in gp]
+    # + face: left = own, right = neighbour
+    us_p = 0.5 * (up + nb_m)
+    dL_p = list(gp)
+    dL_p[m] = gp[m] + H * eta * c_p * (us_p - up)
+    dR_p = list(nb_gm)
+    dR_p[m] = nb_gm[m] + H * eta * c_m * (nb_m - us_p)
+    # - face: left = neighbour, right = own
+    us_m = 0.5 * (nb_p + um)
+    dL_m = list(nb_gp)
+    dL_m[m] = nb_gp[m] + H * eta * c_p * (us_m - nb_p)
+    dR_m = list(gm)
+    dR_m[m] = gm[m] + H * eta * c_m * (um - us_m)
+    return {"p": dict(gL=up, gR=nb_m, dL=dL_p, dR=dR_p, us=us_p),
+            "m": dict(gL=nb_p, gR=um, dL=dL_m, dR=dR_m, us=us_m)}
+
+
+def br2_lifted_gradient(disc, U, faces):
+    """The lifted gradient d (Eq. 29, weak form on the collocated nodes) of every
+    channel of U, all directions: d^k = (2/h_k)[Dhat U + lhat(+1) u*_+ - lhat(-1) u*_-]
+    along the node axis of k, with u* of ``br2_faces`` (faces[k])."""
+    b = disc.basis
+    out = []
+    for k in range(disc.d):
+        nk = disc.node_axis(k)
+        Hk = 2.0 / disc.mesh.h[k]
+        out.append(Hk * (Disc._apply(b.Dhat, U, nk) + disc._lift(faces[k]["p"]["us"], b.lhat_p, nk)
+                         - disc._lift(faces[k]["m"]["us"], b.lhat_m, nk)))
+    return out
+
+
+def viscous_ns(disc, w, sigma=None, frozen_neighbor=False):
+    """The viscous part of the Navier-Stokes operators (Sec. 5.1).
+
+    R^(1) (sigma None), Eq. 28-30: the gradient variables g = w_grad(w) of
+    Eq. 26 at the nodes, their lifted gradient d (Eq. 29), and
+        out_i = sum_m (2/h_m)[ Dhat F^v_m(g, d) + lhat_i(+1) F^v*_+ - lhat_i(-1) F^v*_- ]
+    with the central viscous face flux of Eq. 30,
+        F^v*_pm = 1/2 (F^v_m(g^L, d^L) + F^v_m(g^R, d^R)),
+    where g^L,R are the traces of the nodal g and d^L,R the face-local BR2
+    gradients (``br2_faces``).
+    R^(2) (sigma given), Eq. 32-33: the same structure with the linearised flux
+    (dF^v/dw) sigma + (dF^v/dd) eta, where eta is the lifting (Eq. 33) of
+    gs = (dw_grad/dw) sigma, built exactly like d from g.  frozen_neighbor
+    zeroes the neighbours' gs (their sigma), not their g."""
+    ph, b = disc.ph, disc.basis
+    W = disc.to_grid(w)
+    g = laws.ns_grad_vars(W, ph)
+    fg = [br2_faces(disc, g, m) for m in range(disc.d)]
+    dg = br2_lifted_gradient(disc, g, fg)
+    if sigma is not None:
+        S = disc.to_grid(sigma)
+        gs = laws.ns_grad_vars_jvp(W, S, ph)
+        fs = [br2_faces(disc, gs, m, frozen_neighbor) for m in range(disc.d)]
+        ds = br2_lifted_gradient(disc, gs, fs)
+    out = np.zeros(W.shape, dtype=np.result_type(W, sigma) if sigma is not None else W.dtype)
+    for m in range(disc.d):
+        na = disc.node_axis(m)
+        H = 2.0 / disc.mesh.h[m]
+        fp, fm = fg[m]["p"], fg[m]["m"]
+        if sigma is None:
+            Fv = laws.ns_viscous_flux(g, dg, m, ph)
+            fstar_p = 0.5 * (laws.ns_viscous_flux(fp["gL"], fp["dL"], m, ph)
+                             + laws.ns_viscous_flux(fp["gR"], fp["dR"], m, ph))
+            fstar_m = 0.5 * (laws.ns_viscous_flux(fm["gL"], fm["dL"], m, ph)
+                             + laws.ns_viscous_flux(fm["gR"], fm["dR"], m, ph))
+        else:
+            sp, sm = fs[m]["p"], fs[m]["m"]
+            Fv = laws.ns_viscous_flux_jvp(g, dg, gs, ds, m, ph)
+            fstar_p = 0.5 * (laws.ns_viscous_flux_jvp(fp["gL"], fp["dL"], sp["gL"], sp["dL"], m, ph)
+                             + laws.ns_viscous_flux_jvp(fp["gR"], fp["dR"], sp["gR"], sp["dR"], m, ph))
+            fstar_m = 0.5 * (laws.ns_viscous_flux_jvp(fm["gL"], fm["dL"], sm["gL"], sm["dL"], m, ph)
+                             + laws.ns_viscous_flux_jvp(fm["gR"], fm["dR"], sm["gR"], sm["dR"], m, ph))
+        out = out + H * (Disc._apply(b.Dhat, Fv, na) + disc._lift(fstar_p, b.lhat_p, na)
+                         - disc._lift(fstar_m, b.lhat_m, na))
     return disc.from_grid(out)
 
 

@@ -11,6 +11,12 @@ plain arithmetic so that it also runs on complex arrays (complex-step tests).
               operator of ``dgsem.viscous``)
   euler       Eq. 21: F^m = (rho v_m, rho v_m v + p/eps^2 e_m, v_m (E + p)),
               p = (gamma - 1)(E - eps^2/2 rho |v|^2)
+  navier_stokes  the Euler flux plus the viscous flux of Sec. 5 (Eq. 25):
+              F^v_m = (0, tau_{k m}, sum_k tau_{m k} v_k + lambda dT/dx_m),
+              tau = mu (grad v + grad v^T - 2/3 div v I), T = p / (rho R),
+              R = 1 / (gamma eps^2), c_p = R gamma / (gamma - 1),
+              lambda = c_p mu / Pr; its input is the gradient variable
+              w_grad = (v, T) and its gradient d (Eq. 26)
 
 Numerical-flux dissipation (Eq. 13 and its parameters in Sec. 4.1):
   global Lax-Friedrichs: lambda is a constant per variable; advection
@@ -23,11 +29,12 @@ import numpy as np
 ADVECTION = "advection"
 BURGERS = "burgers"
 EULER = "euler"
+NAVIER_STOKES = "navier_stokes"
 
 
 class Physics:
     def __init__(self, law, dim, a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0,
-                 flux="lf", lf_scale=1.0, nu=0.0, eta_br2=None):
+                 flux="lf", lf_scale=1.0, nu=0.0, eta_br2=None, mu=0.0, prandtl=0.72):
         self.law = law
         self.dim = dim
         self.a = np.array(a[:dim], dtype=np.float64)
@@ -35,15 +42,24 @@ class Physics:
         self.eps = eps
         self.flux = flux            # "lf" (global Lax-Friedrichs) or "rusanov"
         self.lf_scale = lf_scale    # multiplies the paper's lambda in "lf"
-        self.nv = {ADVECTION: 1, BURGERS: 1, EULER: dim + 2}[law]
+        self.nv = {ADVECTION: 1, BURGERS: 1, EULER: dim + 2, NAVIER_STOKES: dim + 2}[law]
         self.linear = law == ADVECTION
         # viscous term nu Laplace(w) (scalar laws only) with the BR2 lifting of
         # Sec. 6.1; eta_br2 scales the face-local liftings (the paper leaves its
         # value open; default: the number of faces of an element, 2 dim)
-        if nu != 0.0 and law == EULER:
-            raise ValueError("the viscous term is implemented for scalar laws only")
+        if nu != 0.0 and law in (EULER, NAVIER_STOKES):
+            raise ValueError("nu is the viscosity of the scalar laws; Navier-Stokes takes mu")
+        if mu != 0.0 and law != NAVIER_STOKES:
+            raise ValueError("mu is the dynamic viscosity of the Navier-Stokes law")
         self.nu = float(nu)
         self.eta_br2 = float(2 * dim if eta_br2 is None else eta_br2)
+        # Navier-Stokes (Sec. 5): constant dynamic viscosity mu, Prandtl number,
+        # gas constant R = 1/(gamma eps^2), c_p = R gamma/(gamma - 1), lambda = c_p mu/Pr
+        self.mu = float(mu)
+        self.prandtl = float(prandtl)
+        self.R_gas = 1.0 / (gamma * eps ** 2)
+        self.cp = self.R_gas * gamma / (gamma - 1.0)
+        self.kappa_heat = self.cp * self.mu / self.prandtl
 
 
 def _re(x):
@@ -146,3 +162,68 @@ def dissipation(wL, wR, m, ph):
     if ph.flux == "rusanov":
         return 0.5 * cs_max(max_speed(wL, m, ph), max_speed(wR, m, ph))[None]
     raise ValueError(ph.flux)
+
+
+# -- Navier-Stokes viscous part (Sec. 5) -----------------------------------
+
+def ns_grad_vars(w, ph):
+    """w_grad = (v_1, .., v_d, T) of Eq. 26, T = p / (rho R)."""
+    rho, v, E, p = euler_primitives(w, ph)
+    return np.stack(v + [p / (rho * ph.R_gas)])
+
+
+def ns_grad_vars_jvp(w, s, ph):
+    """(d w_grad / dw) s: the velocity and temperature parts of the direction s
+    (the matrix of Eq. 31 applied to sigma)."""
+    d = ph.dim
+    g, e2 = ph.gamma, ph.eps ** 2
+    rho, v, E, p = euler_primitives(w, ph)
+    srho, sE = s[0], s[d + 1]
+    smom = [s[1 + k] for k in range(d)]
+    dv = [(smom[k] - v[k] * srho) / rho for k in range(d)]
+    v2 = sum(vk * vk for vk in v)
+    vdots = sum(v[k] * smom[k] for k in range(d))
+    dp = (g - 1.0) * (sE - e2 * vdots + 0.5 * e2 * v2 * srho)
+    dT = (dp / rho - p * srho / (rho * rho)) / ph.R_gas
+    return np.stack(dv + [dT])
+
+
+def _tau(dg, i, j, ph):
+    """tau_ij = mu (dv_j/dx_i + dv_i/dx_j - 2/3 delta_ij div v); dg[k][c] is the
+    derivative of gradient variable c along x_k."""
+    t = dg[i][j] + dg[j][i]
+    if i == j:
+        t = t - (2.0 / 3.0) * sum(dg[k][k] for k in range(ph.dim))
+    return ph.mu * t
+
+
+def ns_viscous_flux(g, dg, m, ph):
+    """F^v along x_m (Eq. 25) from the gradient variables g = (v, T) and their
+    gradient dg (dg[k][c] = d g_c / d x_k):
+    (0, tau_{k m} for k < d, sum_k tau_{m k} v_k + lambda dT/dx_m)."""
+    d = ph.dim
+    zero = 0.0 * g[0]
+    rows = [zero]
+    for k in range(d):
+        rows.append(_tau(dg, k, m, ph))
+    energy = ph.kappa_heat * dg[m][d]
+    for k in range(d):
+        energy = energy + _tau(dg, m, k, ph) * g[k]
+    rows.append(energy)
+    return np.stack(rows)
+
+
+def ns_viscous_flux_jvp(g, dg, gs, dgs, m, ph):
+    """The linearisation of ns_viscous_flux in the direction (gs, dgs) of
+    (g, d): tau is linear in d and independent of w, so (Eq. 32)
+    (0, tau(dgs)_{k m}, sum_k [tau(dgs)_{m k} v_k + tau(dg)_{m k} gs_k] + lambda dgs[m][T])."""
+    d = ph.dim
+    zero = 0.0 * g[0]
+    rows = [zero]
+    for k in range(d):
+        rows.append(_tau(dgs, k, m, ph))
+    energy = ph.kappa_heat * dgs[m][d]
+    for k in range(d):
+        energy = energy + _tau(dgs, m, k, ph) * g[k] + _tau(dg, m, k, ph) * gs[k]
+    rows.append(energy)
+    return np.stack(rows)

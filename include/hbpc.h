@@ -41,7 +41,17 @@ typedef enum {
 /* Conservation laws.  ADVECTION: w_t + div(a w) = 0 (Sec. 4.1.1).
  * BURGERS: w_t + div((w^2/2)(1,..,1)) = 0 (inviscid part of the Burgers workload).
  * EULER: compressible Euler with reference Mach number eps (Eq. 21). */
-typedef enum { HBPC_LAW_ADVECTION = 0, HBPC_LAW_BURGERS = 1, HBPC_LAW_EULER = 2 } hbpc_law;
+typedef enum {
+  HBPC_LAW_ADVECTION = 0,
+  HBPC_LAW_BURGERS = 1,
+  HBPC_LAW_EULER = 2,
+  /* Euler flux plus the Navier-Stokes viscous flux of Sec. 5 (Eq. 25: stress
+     tensor with constant dynamic viscosity mu = nu, heat flux lambda grad T,
+     lambda = c_p mu / Pr, R = 1/(gamma eps^2)), discretised with the BR2
+     lifting of the gradient variables (v, T) (Sec. 5.1.1) and its
+     linearisation for R^(2) (Sec. 5.1.2).  Compiled for dim 2 and 3. */
+  HBPC_LAW_NAVIER_STOKES = 3
+} hbpc_law;
 
 /* Numerical flux of Eq. 13: f* = 1/2 (F(wL) + F(wR)) . n + kappa (wL - wR).
  * GLOBAL_LF: kappa is a global constant per variable, lf_scale times the paper's
@@ -84,15 +94,18 @@ typedef struct {
   double eps;       /* reference Mach number eps (Euler, Eq. 21); also enters
                        eps_FD of Eq. 23 for every law (use 1 for advection) */
   double lf_scale;  /* multiplies the global-LF lambda; 1 = Eq. 13 as printed */
-  double nu;        /* viscosity of a term nu Laplace(w) added to a scalar law
-                       (advection or Burgers), discretised by the BR2 lifting of
-                       Sec. 5.1.1 (Eqs. 26-30 with F^v = nu grad w, central
-                       face fluxes, face-local liftings).  0 = inviscid; < 0 is
-                       HBPC_ERR_INVALID_ARG; > 0 with Euler is
-                       HBPC_ERR_UNSUPPORTED. */
+  double nu;        /* viscosity: nu of a term nu Laplace(w) added to a scalar
+                       law (advection or Burgers), discretised by the BR2
+                       lifting of Sec. 5.1.1 (Eqs. 26-30 with F^v = nu grad w,
+                       central face fluxes, face-local liftings), or the dynamic
+                       viscosity mu of HBPC_LAW_NAVIER_STOKES.  0 = inviscid;
+                       < 0 is HBPC_ERR_INVALID_ARG; > 0 with Euler is
+                       HBPC_ERR_UNSUPPORTED (use the Navier-Stokes law). */
   double eta_br2;   /* BR2 stabilisation factor of the face-local liftings (the
                        paper leaves its value open); <= 0 selects 2 * dim, the
                        number of faces of an element */
+  double prandtl;   /* Prandtl number of the Navier-Stokes heat flux; <= 0
+                       selects 0.72, the paper's value.  Ignored by other laws. */
 } hbpc_physics;
 
 typedef struct {

@@ -43,8 +43,8 @@ template <class T> struct BaseOf<Dual<T>> { using type = T; };
 template <class V> __device__ __forceinline__ typename BaseOf<V>::type real_part(const V& x) { return x; }
 template <class T> __device__ __forceinline__ T real_part(const Dual<T>& x) { return x.v; }
 
-enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2,
-           LAW_ADV2 = 3 };   // internal: two advected components (both halves of a Krylov vector)
+enum Law { LAW_ADV = 0, LAW_BURGERS = 1, LAW_EULER = 2, LAW_NS = 3,
+           LAW_ADV2 = 4 };   // internal: two advected components (both halves of a Krylov vector)
 
 // Operator parameters, passed by value (kernel parameter space).  All matrices
 // already carry the Cartesian metric -(2/h_m) of the reference-element
@@ -96,6 +96,9 @@ struct DGParams {
   T bp[3], bm[3];           // (2/h_m) eta c_+, (2/h_m) eta c_-
   const T* vtab;            // device: Dg[DIM][P][P] = (2/h) D, gp[DIM][P], gm[DIM][P] = (2/h) l_j'(+-1)
   const double* vloc;       // device: element-diagonal viscous block per direction [DIM][P][P], unit nu
+  // Navier-Stokes viscous flux (Sec. 5, Eq. 25): dynamic viscosity, heat
+  // conductivity lambda = c_p mu / Pr and 1/R = gamma eps^2 (T = p / (rho R))
+  T mu, kheat, invR;
   // batch of instances (null for a single problem): per-instance geometry and,
   // per block of the operator kernel, the instance it belongs to
   const InstGeo<T>* inst;
@@ -296,10 +299,83 @@ struct Euler {
   }
 };
 
+// Navier-Stokes viscous flux (Sec. 5, Eq. 25) as a function of the gradient
+// variables g = (v_1..v_d, T) of Eq. 26 and their gradient d[k][c] (derivative
+// of channel c along x_k):
+//   F^v_m = (0, tau_{k m}, sum_k tau_{m k} v_k + lambda dT/dx_m),
+//   tau = mu (grad v + grad v^T - 2/3 div v I).
+// tau depends on d only, so the linearisation (Eq. 32) in the direction
+// (gs, ds) is (0, tau(ds)_{k m}, sum_k [tau(ds)_{m k} v_k + tau(d)_{m k} gs_k] + lambda ds[m][T]).
+template <int DIM, typename T>
+struct NSVisc {
+  static constexpr int NG = DIM + 1;
+  static constexpr int NV = DIM + 2;
+  // g = (m / rho, p / (rho R))
+  template <class V>
+  __device__ __forceinline__ static void grad_vars(const V* w, V* g, const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v2 = V(T(0));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { g[k] = w[1 + k] * ir; v2 += g[k] * g[k]; }
+    const V pr = p.gm1 * (w[DIM + 1] - (T(0.5) * p.eps2) * (w[0] * v2));
+    g[DIM] = (pr * ir) * p.invR;
+  }
+  // (dg/dw) s (the matrix of Eq. 31 applied to sigma)
+  template <class V>
+  __device__ __forceinline__ static void grad_vars_jvp(const V* w, const V* s, V* gs, const DGParams<T>& p) {
+    const V ir = V(T(1)) / w[0];
+    V v[DIM], v2 = V(T(0)), vs = V(T(0));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; vs += v[k] * s[1 + k]; }
+    const V pr = p.gm1 * (w[DIM + 1] - (T(0.5) * p.eps2) * (w[0] * v2));
+    const V dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + (T(0.5) * p.eps2) * (v2 * s[0]));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) gs[k] = (s[1 + k] - v[k] * s[0]) * ir;
+    gs[DIM] = ((dp - (pr * ir) * s[0]) * ir) * p.invR;
+  }
+  template <class V>
+  __device__ __forceinline__ static V tau(const V (*d)[NG], int i, int j, T mu) {
+    V t = d[i][j] + d[j][i];
+    if (i == j) {
+      V dv = V(T(0));
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) dv += d[k][k];
+      t -= T(2.0 / 3.0) * dv;
+    }
+    return mu * t;
+  }
+  // F^v along x_m; F[0] (mass) is zero and is not written
+  template <class V>
+  __device__ __forceinline__ static void flux(const V* g, const V (*d)[NG], int m, V* F, const DGParams<T>& p) {
+    V e = p.kheat * d[m][DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const V t = tau(d, k, m, p.mu);
+      F[1 + k] = t;
+      e += t * g[k];
+    }
+    F[DIM + 1] = e;
+  }
+  template <class V>
+  __device__ __forceinline__ static void flux_lin(const V* g, const V (*d)[NG], const V* gs, const V (*ds)[NG], int m,
+                                                  V* F, const DGParams<T>& p) {
+    V e = p.kheat * ds[m][DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const V ts = tau(ds, k, m, p.mu);
+      F[1 + k] = ts;
+      e += ts * g[k] + tau(d, m, k, p.mu) * gs[k];
+    }
+    F[DIM + 1] = e;
+  }
+};
+
 template <int LAW, int DIM, typename T> struct LawOf;
 template <int DIM, typename T> struct LawOf<LAW_ADV, DIM, T> { using type = Advection<DIM, T>; };
 template <int DIM, typename T> struct LawOf<LAW_BURGERS, DIM, T> { using type = Burgers<DIM, T>; };
 template <int DIM, typename T> struct LawOf<LAW_EULER, DIM, T> { using type = Euler<DIM, T>; };
+// Navier-Stokes: the Euler flux; the viscous part is added by the operator kernel
+template <int DIM, typename T> struct LawOf<LAW_NS, DIM, T> { using type = Euler<DIM, T>; };
 template <int DIM, typename T> struct LawOf<LAW_ADV2, DIM, T> { using type = AdvectionPair<DIM, T>; };
 
 }  // namespace hbpc

@@ -16,27 +16,56 @@
 // gradients (the neighbour's line is read in full for its derivative at the
 // face); a pass 2b then forms the lifted gradient d at every node and folds
 // -nu d into the nodal flux, and the viscous face flux into the face flux, so
-// pass 3 is unchanged.
+// pass 3 is unchanged.  The Navier-Stokes law (Sec. 5) does the same for the
+// d + 1 gradient variables (v, T): pass 1 converts the nodes to them, pass 2
+// stores the face traces of both sides (stage A), and after the barrier the
+// face-local gradients (with tangential components from the stored traces) give
+// the central viscous face flux (stage B) while every node forms its lifted
+// gradient and F^v (Eq. 25), or their linearisations for R2 (Eq. 31-33).
 // A Job supplies how node values are loaded (so that perturbed states W + eps dW
 // are formed on the fly) and what is done with the results (the epilogue), so
 // Jacobian-vector products and residuals are single passes over memory.
 #pragma once
+#include <type_traits>
+
 #include "dg_common.cuh"
 
 namespace hbpc {
 
 enum EvalKind { EV_R1 = 0, EV_R2 = 1 };
 
+// A job with kFrozenNb = true evaluates R2 with the neighbours' direction taken
+// as zero (the element-diagonal block of the preconditioner, Sec. 3.2.3); every
+// load of a neighbour's direction goes through load_nb_dir.
+template <class Job, class = void> struct FrozenNb { static constexpr bool value = false; };
+template <class Job> struct FrozenNb<Job, std::void_t<decltype(Job::kFrozenNb)>> {
+  static constexpr bool value = Job::kFrozenNb;
+};
+template <int NV, class Job, typename V>
+__device__ __forceinline__ void load_nb_dir(const Job& job, int k, int en, int node, V* x) {
+  if constexpr (FrozenNb<Job>::value) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = V(0);
+  } else {
+    job.load_dir(k, en, node, x);
+  }
+}
+
 
 template <int LAW, int DIM, int P>
 struct KernelShape {
-  static constexpr int NV = (LAW == LAW_EULER) ? DIM + 2 : (LAW == LAW_ADV2 ? 2 : 1);
-  static constexpr bool VISC = NV == 1;          // BR2 viscous term available
+  static constexpr int NV = (LAW == LAW_EULER || LAW == LAW_NS) ? DIM + 2 : (LAW == LAW_ADV2 ? 2 : 1);
+  static constexpr bool NSV = LAW == LAW_NS;     // Navier-Stokes viscous flux (system BR2)
+  static constexpr bool VISC = NV == 1 || NSV;   // BR2 viscous term available
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF, EPB = Geo<DIM, P>::EPB;
+  // gradient channels of the system path: g = (v, T) and, for R2, gs = (dg/dw) s
+  static constexpr int NCH = NSV ? 2 * (DIM + 1) : 0;
   // shared values per element: state + direction + DIM fluxes + 2*DIM faces
-  // (+ 2*DIM faces of u* - u for the viscous term)
-  static constexpr int PER_ELEM =
-      2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF + (VISC ? 2 * DIM * NF : 0);
+  // (+ 2*DIM faces of u* - u for the scalar viscous term; + the nodal channels
+  // and, per face, the own trace, the neighbour's trace and the neighbour's
+  // normal derivative of every channel for the system)
+  static constexpr int PER_ELEM = 2 * NV * NN + DIM * NV * NN + 2 * DIM * NV * NF + (NV == 1 ? 2 * DIM * NF : 0) +
+                                  (NSV ? NCH * NN + 3 * 2 * DIM * NCH * NF : 0);
   // Dvol, sp, sm (+ Dg, gp, gm)
   static constexpr int MATS = DIM * P * P + 2 * DIM * P + (VISC ? DIM * P * P + 2 * DIM * P : 0);
   // operator matrices (base type B, padded to 16 bytes) then element data (V)
@@ -79,7 +108,7 @@ struct FaceFlux {
         if (r2) so[v] = sdir[v * NN + own_node];
       }
       job.load_state(k, en, nb_node, wn);
-      if (r2) job.load_dir(k, en, nb_node, sn);
+      if (r2) load_nb_dir<NV>(job, k, en, nb_node, sn);
     } else {
 #pragma unroll
       for (int i = 0; i < P; ++i) {
@@ -88,7 +117,7 @@ struct FaceFlux {
         const T ln = SIDE ? prm.lm[i] : prm.lp[i];   // neighbour's trace at this face
         V tw[NV], ts[NV];
         job.load_state(k, en, node, tw);
-        if (r2) job.load_dir(k, en, node, ts);
+        if (r2) load_nb_dir<NV>(job, k, en, node, ts);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           wo[v] += lo * sst[v * NN + node];
@@ -162,7 +191,7 @@ struct FaceVisc {
     for (int i = 0; i < P; ++i) {
       const int node = base + i * st;
       V y[1];
-      if (r2) job.load_dir(k, en, node, y); else job.load_state(k, en, node, y);
+      if (r2) load_nb_dir<1>(job, k, en, node, y); else job.load_state(k, en, node, y);
       const V x = u[node];
       uo += (SIDE ? prm.lp[i] : prm.lm[i]) * x;
       go += (SIDE ? sgp[M * P + i] : sgm[M * P + i]) * x;
@@ -185,6 +214,150 @@ struct FaceVisc {
   }
 };
 
+// Navier-Stokes BR2 (Sec. 5.1.1-5.1.2), stage A at one face point: the own
+// trace of every gradient channel (from the element's nodal channels in shared
+// memory) and the neighbour's trace and normal derivative (its line of nodes
+// through this face point is read from global memory and converted to g, and
+// for R2 to gs = (dg/dw) s).  Stored per face for stage B, which needs the
+// traces of neighbouring face points for the tangential derivatives.
+// Channel layout: [0, NG) g, [NG, 2 NG) gs (R2 only).
+template <int DIM, int P, typename V, class Job>
+struct FaceViscSysA {
+  using T = typename BaseOf<V>::type;
+  using NS = NSVisc<DIM, T>;
+  static constexpr int NV = DIM + 2, NG = DIM + 1, NCH = 2 * NG;
+  static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
+  template <int M, int SIDE>
+  __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, const InstGeo<T>& g, int k,
+                                             bool r2, const int* ec, int pt, const V* sgc, const T* sgp, const T* sgm,
+                                             V* sfo, V* sfn, V* sfd) {
+    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    const int base = (pt % st) + (pt / st) * st * P;
+    int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
+    int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
+    c += SIDE ? 1 : -1;
+    if (c < 0) c += g.n[M];
+    if (c >= g.n[M]) c -= g.n[M];
+    const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
+    const int f = 2 * M + SIDE;
+    const int nch = r2 ? NCH : NG;
+    V un[NCH], gn[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) { un[q] = V(T(0)); gn[q] = V(T(0)); }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const int node = base + i * st;
+      V x[NV], ch[NCH];
+      job.load_state(k, en, node, x);
+      NS::grad_vars(x, ch, prm);
+      if (r2) {
+        V y[NV];
+        load_nb_dir<NV>(job, k, en, node, y);
+        NS::grad_vars_jvp(x, y, ch + NG, prm);
+      }
+      const T ln = SIDE ? prm.lm[i] : prm.lp[i];                       // neighbour's trace at this face
+      const T dn = SIDE ? sgm[M * P + i] : sgp[M * P + i];             // and its normal derivative
+#pragma unroll
+      for (int q = 0; q < NCH; ++q)
+        if (q < nch) { un[q] += ln * ch[q]; gn[q] += dn * ch[q]; }
+    }
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      if (q < nch) {
+        V uo = V(T(0));
+#pragma unroll
+        for (int i = 0; i < P; ++i) uo += (SIDE ? prm.lp[i] : prm.lm[i]) * sgc[q * NN + base + i * st];
+        sfo[(f * NCH + q) * NF + pt] = uo;
+        sfn[(f * NCH + q) * NF + pt] = un[q];
+        sfd[(f * NCH + q) * NF + pt] = gn[q];
+      }
+    }
+  }
+};
+
+// Stage B at one face point: the face-local BR2 gradients of both sides, all
+// directions -- the normal component from the normal derivative plus eta times
+// the face's own lifting, the tangential ones from the traces of the face
+// points along that direction -- and the central viscous flux of Eq. 30 (R1)
+// or its linearisation (R2, Eq. 32), added to sface with the sign convention
+// of the inviscid flux (outward normal).
+template <int DIM, int P, typename V>
+struct FaceViscSysB {
+  using T = typename BaseOf<V>::type;
+  using NS = NSVisc<DIM, T>;
+  static constexpr int NV = DIM + 2, NG = DIM + 1, NCH = 2 * NG;
+  static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
+  template <int M, int SIDE>
+  __device__ __forceinline__ static void run(const DGParams<T>& prm, const InstGeo<T>& g, bool r2, int pt,
+                                             const V* sgc, const T* sDg, const T* sgp, const T* sgm, const V* sfo,
+                                             const V* sfn, const V* sfd, V* sface) {
+    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    const int base = (pt % st) + (pt / st) * st * P;
+    const int f = 2 * M + SIDE;
+    const int nch = r2 ? NCH : NG;
+    // gradients of the own (o) and neighbour (n) side: [channel set][direction][channel]
+    V dO[2][DIM][NG], dN[2][DIM][NG], gO[NCH], gN[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      const int set = q / NG, cq = q - set * NG;
+      if (q >= nch) {
+        gO[q] = V(T(0)); gN[q] = V(T(0));
+#pragma unroll
+        for (int kk = 0; kk < DIM; ++kk) { dO[set][kk][cq] = V(T(0)); dN[set][kk][cq] = V(T(0)); }
+        continue;
+      }
+      const V uo = sfo[(f * NCH + q) * NF + pt], un = sfn[(f * NCH + q) * NF + pt];
+      gO[q] = uo; gN[q] = un;
+      // own normal derivative along the line of this face point
+      V go = V(T(0));
+#pragma unroll
+      for (int i = 0; i < P; ++i) go += (SIDE ? sgp[M * P + i] : sgm[M * P + i]) * sgc[q * NN + base + i * st];
+      const V gn = sfd[(f * NCH + q) * NF + pt];
+      const V us = T(0.5) * (uo + un);
+      // normal component: + face (own = L): d^L = go + bp (u* - uo), d^R = gn + bm (un - u*);
+      //                   - face (own = R): d^L = gn + bp (u* - un), d^R = go + bm (uo - u*)
+      if (SIDE) {
+        dO[set][M][cq] = g.hs[M] * (go + prm.bp[M] * (us - uo));
+        dN[set][M][cq] = g.hs[M] * (gn + prm.bm[M] * (un - us));
+      } else {
+        dO[set][M][cq] = g.hs[M] * (go + prm.bm[M] * (uo - us));
+        dN[set][M][cq] = g.hs[M] * (gn + prm.bp[M] * (us - un));
+      }
+      // tangential components: derivative of the face traces along x_kk
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) {
+        if (kk == M) continue;
+        // face point stride of direction kk: the lower tangential direction is fastest
+        // (pt = j + P k on x faces, i + P k on y faces, i + P j on z faces)
+        const int lo_t = (M == 0) ? 1 : 0;
+        const int tstride = (kk == lo_t) ? 1 : P;
+        const int it = (pt / tstride) % P;
+        const int p0 = pt - it * tstride;
+        const T* Drow = sDg + (kk * P + it) * P;
+        V a = V(T(0)), b = V(T(0));
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          a += Drow[j] * sfo[(f * NCH + q) * NF + p0 + j * tstride];
+          b += Drow[j] * sfn[(f * NCH + q) * NF + p0 + j * tstride];
+        }
+        dO[set][kk][cq] = g.hs[kk] * a;
+        dN[set][kk][cq] = g.hs[kk] * b;
+      }
+    }
+    V FO[NV], FN[NV];
+    if (r2) {
+      NS::flux_lin(gO, dO[0], gO + NG, dO[1], M, FO, prm);
+      NS::flux_lin(gN, dN[0], gN + NG, dN[1], M, FN, prm);
+    } else {
+      NS::flux(gO, dO[0], M, FO, prm);
+      NS::flux(gN, dN[0], M, FN, prm);
+    }
+    const T sg = SIDE ? T(-0.5) : T(0.5);
+#pragma unroll
+    for (int v = 1; v < NV; ++v) sface[(f * NV + v) * NF + pt] += sg * (FO[v] + FN[v]);
+  }
+};
+
 template <int LAW, int DIM, int P, bool LGL, typename V, class Job>
 __global__ void __launch_bounds__(Geo<DIM, P>::THREADS)
 dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) {
@@ -194,6 +367,9 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
   constexpr int NV = L::NV, NN = G::NN, NF = G::NF, EPB = G::EPB;
   constexpr int PER_ELEM = KernelShape<LAW, DIM, P>::PER_ELEM;
   constexpr bool VISC = KernelShape<LAW, DIM, P>::VISC;
+  constexpr bool NSV = KernelShape<LAW, DIM, P>::NSV;
+  constexpr int NCH = KernelShape<LAW, DIM, P>::NCH;
+  constexpr int NG = DIM + 1;
 
   if (!job.active()) return;
 
@@ -228,7 +404,13 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
   V* const sdir = sst + NV * NN;           // [NV][NN] direction (R2)
   V* const sG = sdir + NV * NN;            // [DIM][NV][NN] nodal fluxes
   V* const sface = sG + DIM * NV * NN;     // [2*DIM][NV][NF] face fluxes
-  V* const sjump = sface + 2 * DIM * NV * NF;   // [2*DIM][NF] u* - u_own (viscous)
+  V* const sjump = sface + 2 * DIM * NV * NF;   // [2*DIM][NF] u* - u_own (scalar viscous)
+  // system viscous: nodal channels [NCH][NN]; per face [2*DIM][NCH][NF] the own
+  // trace, the neighbour's trace and the neighbour's normal derivative
+  V* const sgc = sjump + (NV == 1 ? 2 * DIM * NF : 0);
+  V* const sfo = sgc + NCH * NN;
+  V* const sfn = sfo + 2 * DIM * NCH * NF;
+  V* const sfd = sfn + 2 * DIM * NCH * NF;
 
   int ec[3] = {0, 0, 0};
   if (live) {
@@ -264,6 +446,16 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
 #pragma unroll
           for (int v = 0; v < NV; ++v) sG[(m * NV + v) * NN + n] = F[m][v];
       }
+      if constexpr (NSV) {
+        if (visc) {   // gradient variables g = (v, T) (Eq. 26) and, for R2, gs = (dg/dw) s
+          V ch[NCH];
+          NSVisc<DIM, T>::grad_vars(w, ch, prm);
+          if (r2) NSVisc<DIM, T>::grad_vars_jvp(w, s, ch + NG, prm);
+#pragma unroll
+          for (int q = 0; q < NCH; ++q)
+            if (q < NG || r2) sgc[q * NN + n] = ch[q];
+        }
+      }
     }
     __syncthreads();
     // -- 2. face fluxes ------------------------------------------------------
@@ -280,7 +472,20 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
           case 5: if constexpr (DIM > 2) FF::template run<2, 1>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
           default: break;
         }
-        if constexpr (VISC) {
+        if constexpr (NSV) {
+          if (visc) {
+            using FA = FaceViscSysA<DIM, P, V, Job>;
+            switch (f) {
+              case 0: FA::template run<0, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              case 1: FA::template run<0, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              case 2: if constexpr (DIM > 1) FA::template run<1, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              case 3: if constexpr (DIM > 1) FA::template run<1, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              case 4: if constexpr (DIM > 2) FA::template run<2, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              case 5: if constexpr (DIM > 2) FA::template run<2, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
+              default: break;
+            }
+          }
+        } else if constexpr (VISC) {
           if (visc) {
             using FV = FaceVisc<DIM, P, V, Job>;
             const V* u = r2 ? sdir : sst;
@@ -298,9 +503,74 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
       }
     }
     __syncthreads();
+    // -- 2b (system). Navier-Stokes: the viscous face fluxes (stage B) and, per
+    // node, the lifted gradient of every channel (Eq. 29 / Eq. 33, strong form)
+    // and the viscous flux F^v (R1) or its linearisation (R2), folded into sG --
+    if constexpr (NSV) {
+      if (visc) {
+        if (live) {
+          for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
+            const int f = fp / NF, pt = fp - f * NF;
+            using FB = FaceViscSysB<DIM, P, V>;
+            switch (f) {
+              case 0: FB::template run<0, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              case 1: FB::template run<0, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              case 2: if constexpr (DIM > 1) FB::template run<1, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              case 3: if constexpr (DIM > 1) FB::template run<1, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              case 4: if constexpr (DIM > 2) FB::template run<2, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              case 5: if constexpr (DIM > 2) FB::template run<2, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
+              default: break;
+            }
+          }
+          const int nch = r2 ? NCH : NG;
+          V d[2][DIM][NG], gch[NCH];
+#pragma unroll
+          for (int q = 0; q < NCH; ++q) {
+            const int set = q / NG, cq = q - set * NG;
+            if (q >= nch) {
+              gch[q] = V(T(0));
+#pragma unroll
+              for (int kk = 0; kk < DIM; ++kk) d[set][kk][cq] = V(T(0));
+              continue;
+            }
+            gch[q] = sgc[q * NN + n];
+#pragma unroll
+            for (int kk = 0; kk < DIM; ++kk) {
+              const int st = (kk == 0) ? 1 : (kk == 1 ? P : P * P);
+              const int i = idx[kk];
+              const int b0 = n - i * st;
+              const T* Grow = sDg + (kk * P + i) * P;
+              V a = V(T(0));
+#pragma unroll
+              for (int l = 0; l < P; ++l) a += Grow[l] * sgc[q * NN + b0 + l * st];
+              const int pt = (n % st) + (n / (st * P)) * st;
+              // u* - u_own at the + and - faces of direction kk
+              const V jp = T(0.5) * (sfn[((2 * kk + 1) * NCH + q) * NF + pt] - sfo[((2 * kk + 1) * NCH + q) * NF + pt]);
+              const V jm = T(0.5) * (sfn[((2 * kk) * NCH + q) * NF + pt] - sfo[((2 * kk) * NCH + q) * NF + pt]);
+              if constexpr (LGL) {
+                if (i == P - 1) a -= sSp[kk * P + P - 1] * jp;
+                if (i == 0) a += sSm[kk * P] * jm;
+              } else {
+                a += sSm[kk * P + i] * jm - sSp[kk * P + i] * jp;
+              }
+              d[set][kk][cq] = geo.hs[kk] * a;
+            }
+          }
+#pragma unroll
+          for (int m = 0; m < DIM; ++m) {
+            V F[NV];
+            if (r2) NSVisc<DIM, T>::flux_lin(gch, d[0], gch + NG, d[1], m, F, prm);
+            else NSVisc<DIM, T>::flux(gch, d[0], m, F, prm);
+#pragma unroll
+            for (int v = 1; v < NV; ++v) sG[(m * NV + v) * NN + n] -= F[v];
+          }
+        }
+        __syncthreads();
+      }
+    }
     // -- 2b. viscous: lifted gradient (Eq. 29, strong form) folded into sG -----
     //   d^m_i = (2/h)(D u)_i + (2/h) lhat_i(+1)(u*_+ - u_+) - (2/h) lhat_i(-1)(u*_- - u_-)
-    if constexpr (VISC) {
+    if constexpr (VISC && !NSV) {
       if (visc) {
         if (live) {
           const V* u = r2 ? sdir : sst;
@@ -646,6 +916,37 @@ struct JobJvMixed {
       ow[i] = sc * zw[i] - c1 * d0 + c2 * d1;
       os[i] = sc * zs[i] - d0;
     }
+  }
+};
+
+// Element-diagonal block J_i of the BJ_ext preconditioner (Sec. 3.2.3) by
+// columns: column c = blockIdx.y of every element's block is R2(W, e_c) on that
+// element with the neighbours' direction zero (kFrozenNb), i.e. dR1/dW
+// restricted to the element with the neighbours' values frozen -- for a law
+// whose viscous Jacobian has no compact closed form (Navier-Stokes).  Blocks
+// are column-major, entry (r, c) at c * n_b + r, as the analytic assembly.
+template <int NV, int NN, typename T>
+struct JobPcCols {
+  static constexpr int K = 1;
+  static constexpr bool kFrozenNb = true;
+  static constexpr int NB = NV * NN;
+  const double* w; T* J;
+  __device__ static constexpr int kind(int) { return EV_R2; }
+  __device__ bool active() const { return true; }
+  __device__ void load_state(int, int e, int n, T* x) const {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = T(w[(size_t(e) * NV + v) * NN + n]);
+  }
+  // only the element's own nodes (neighbours go through load_nb_dir -> 0)
+  __device__ void load_dir(int, int, int n, T* x) const {
+    const int col = blockIdx.y;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = (v * NN + n == col) ? T(1) : T(0);
+  }
+  __device__ void epilogue(int e, int n, const T (*r)[NV]) const {
+    T* Jc = J + (size_t(e) * NB + blockIdx.y) * NB;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Jc[v * NN + n] = r[0][v];
   }
 };
 

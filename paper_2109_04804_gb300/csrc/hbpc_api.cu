@@ -1338,6 +1338,9 @@ hbpc_status pc_alloc_f(hbpc_ctx* x) {
   return HBPC_OK;
 }
 
+bool law_is_euler(int law) { return law == HBPC_LAW_EULER || law == HBPC_LAW_NAVIER_STOKES; }
+int law_nv(int law, int dim) { return law_is_euler(law) ? dim + 2 : 1; }
+
 hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics* ph,
                      const hbpc_solver* so) {
   auto bad = [](const std::string& m) { return fail(nullptr, HBPC_ERR_INVALID_ARG, m); };
@@ -1349,14 +1352,15 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   }
   if (N < 1 || N + 1 > kMaxP) return bad("N must satisfy 1 <= N <= 7");
   if (nodes != HBPC_NODES_LOBATTO && nodes != HBPC_NODES_GAUSS) return bad("unknown node family");
-  if (ph->law < 0 || ph->law > 2) return bad("unknown law");
+  if (ph->law < 0 || ph->law > 3) return bad("unknown law");
   if (ph->flux != HBPC_FLUX_GLOBAL_LF && ph->flux != HBPC_FLUX_RUSANOV) return bad("unknown flux");
   if (!(ph->eps > 0.0)) return bad("eps must be > 0");
-  if (ph->law == HBPC_LAW_EULER && !(ph->gamma > 1.0)) return bad("gamma must be > 1");
+  if (law_is_euler(ph->law) && !(ph->gamma > 1.0)) return bad("gamma must be > 1");
+  if (std::isnan(ph->prandtl) || std::isinf(ph->prandtl)) return bad("prandtl must be finite");
   if (!(ph->nu >= 0.0) || !std::isfinite(ph->nu)) return bad("nu must be finite and >= 0");
   if (std::isnan(ph->eta_br2) || std::isinf(ph->eta_br2)) return bad("eta_br2 must be finite");
   if (ph->nu > 0.0 && ph->law == HBPC_LAW_EULER)
-    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "the viscous term is implemented for scalar laws only");
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "a viscous Euler flow is HBPC_LAW_NAVIER_STOKES");
   if (so->q != 4 && so->q != 6 && so->q != 8) return bad("q must be 4, 6 or 8");
   if (so->kmax < 0) return bad("kmax must be >= 0");
   if (!(so->dt > 0.0)) return bad("dt must be > 0");
@@ -1367,7 +1371,7 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   if (so->pc != HBPC_PC_NONE && so->pc != HBPC_PC_BJEXT && so->pc != HBPC_PC_LEARNED)
     return bad("unknown preconditioner");
   if (so->pc != HBPC_PC_NONE) {
-    int nb = (ph->law == HBPC_LAW_EULER) ? mesh->dim + 2 : 1;
+    int nb = law_nv(ph->law, mesh->dim);
     for (int m = 0; m < mesh->dim; ++m) nb *= (N + 1);
     if (nb > kMaxPcBlock)
       return fail(nullptr, HBPC_ERR_UNSUPPORTED, "BJ_ext block n_var (N+1)^dim exceeds the supported size");
@@ -1397,7 +1401,7 @@ void fill_params(hbpc_ctx* x) {
     for (int v = 0; v < 5; ++v) {
       double lam = 1.0;
       if (x->phys.law == HBPC_LAW_ADVECTION) lam = std::fabs(x->phys.a[m]);
-      else if (x->phys.law == HBPC_LAW_EULER) lam = (v == 0 || v == x->nv - 1) ? 1.0 / x->phys.eps : 1.0;
+      else if (law_is_euler(x->phys.law)) lam = (v == 0 || v == x->nv - 1) ? 1.0 / x->phys.eps : 1.0;
       p.lam[m][v] = x->phys.lf_scale * lam;
     }
     p.a[m] = x->phys.a[m];
@@ -1412,6 +1416,16 @@ void fill_params(hbpc_ctx* x) {
   // BR2 viscous term (tables on the device are attached by visc_setup)
   p.visc = x->phys.nu > 0.0 ? 1 : 0;
   p.nu = x->phys.nu;
+  // Navier-Stokes (Sec. 5): mu = nu, R = 1/(gamma eps^2), c_p = R gamma/(gamma - 1),
+  // lambda = c_p mu / Pr
+  if (x->phys.law == HBPC_LAW_NAVIER_STOKES) {
+    const double R = 1.0 / (x->phys.gamma * p.eps2);
+    const double cp = R * x->phys.gamma / (x->phys.gamma - 1.0);
+    const double pr = x->phys.prandtl > 0.0 ? x->phys.prandtl : 0.72;
+    p.mu = x->phys.nu;
+    p.kheat = cp * x->phys.nu / pr;
+    p.invR = 1.0 / R;
+  }
   // FP32 copy for the mixed-precision Jacobian-vector product
   DGParams<float>& f = x->prmf;
   std::memset(&f, 0, sizeof(f));
@@ -1432,6 +1446,7 @@ void fill_params(hbpc_ctx* x) {
   f.rusanov = p.rusanov;
   f.visc = p.visc;
   f.nu = float(p.nu);
+  f.mu = float(p.mu); f.kheat = float(p.kheat); f.invR = float(p.invR);
 }
 
 // Tables of the BR2 viscous term on the device (Sec. 5.1.1): per direction the
@@ -1836,7 +1851,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   for (int id : ids) numax = std::max(numax, phys[id].nu);
   x->phys.nu = numax;   // the viscous passes run if any instance is viscous
   x->N = N; x->P = N + 1; x->nodes = nodes; x->dim = m0.dim;
-  x->nv = x->phys.law == HBPC_LAW_EULER ? x->dim + 2 : 1;
+  x->nv = law_nv(x->phys.law, x->dim);
   long long nn = 1;
   for (int m = 0; m < x->dim; ++m) nn *= x->P;
   const int epb = nn >= 256 ? 1 : int(256 / nn);   // Geo<DIM, P>::EPB
@@ -1954,7 +1969,7 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
   if (!x) return fail(nullptr, HBPC_ERR_OOM, "host allocation failed");
   x->mesh = *mesh; x->phys = *phys; x->sol = *solver;
   x->N = N; x->P = N + 1; x->nodes = nodes; x->dim = mesh->dim;
-  x->nv = phys->law == HBPC_LAW_EULER ? mesh->dim + 2 : 1;
+  x->nv = law_nv(phys->law, mesh->dim);
   x->nE = 1;
   for (int m = 0; m < x->dim; ++m) x->nE *= mesh->n[m];
   long long nn = 1;
@@ -2395,7 +2410,7 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   hbpc_ctx x;
   x.mesh = *mesh; x.phys = *phys; x.sol = so;
   x.N = N; x.P = N + 1; x.nodes = nodes; x.dim = mesh->dim;
-  x.nv = phys->law == HBPC_LAW_EULER ? mesh->dim + 2 : 1;
+  x.nv = law_nv(phys->law, mesh->dim);
   x.nE = 1;
   for (int m = 0; m < x.dim; ++m) x.nE *= mesh->n[m];
   long long nn = 1;
@@ -2460,6 +2475,8 @@ hbpc_status hbpc_batch_create(hbpc_batch** out, int n_inst, const hbpc_mesh* mes
   for (int i = 0; i < n_inst; ++i) {
     hbpc_status s = validate(&meshes[i], N[i], nodes, &phys[i], solver);
     if (s != HBPC_OK) return s;
+    if (phys[i].law == HBPC_LAW_NAVIER_STOKES)
+      return fail(nullptr, HBPC_ERR_UNSUPPORTED, "batches of the Navier-Stokes law are not supported");
     const hbpc_physics& a = phys[0];
     const hbpc_physics& b = phys[i];
     if (b.law != a.law || b.flux != a.flux || b.gamma != a.gamma || b.eps != a.eps || b.lf_scale != a.lf_scale ||

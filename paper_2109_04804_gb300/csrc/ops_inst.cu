@@ -19,8 +19,9 @@
 namespace hbpc {
 namespace {
 
+// cols > 1: a second grid dimension (the block columns of JobPcCols)
 template <int LAW, int DIM, int P, bool LGL, class Job, typename V = double>
-void launch(const Job& job, const DGParams<typename BaseOf<V>::type>& prm, cudaStream_t s) {
+void launch(const Job& job, const DGParams<typename BaseOf<V>::type>& prm, cudaStream_t s, int cols = 1) {
   using KS = KernelShape<LAW, DIM, P>;
   using Gm = Geo<DIM, P>;
   constexpr size_t smem = KS::template smem_bytes<V, typename BaseOf<V>::type>();
@@ -31,7 +32,7 @@ void launch(const Job& job, const DGParams<typename BaseOf<V>::type>& prm, cudaS
     (void)attr;
   }
   const int blocks = (prm.nE + Gm::EPB - 1) / Gm::EPB;
-  kern<<<blocks, Gm::THREADS, smem, s>>>(job, prm);
+  kern<<<dim3(blocks, cols), Gm::THREADS, smem, s>>>(job, prm);
 }
 
 template <int LAW, int DIM, int P, bool LGL>
@@ -92,12 +93,25 @@ struct Inst {
       launch<LAW, DIM, P, LGL, JobJvMixed<NV, NN>, Dual<float>>(j, p, s);
     }
   }
+  // Navier-Stokes: the blocks by columns of the frozen-neighbour R2 (its
+  // viscous Jacobian has no compact closed form); other laws: the analytic
+  // assembly from the flux Jacobians
   static void pc_assemble(const DGParams<double>& p, const double* W, double* J, cudaStream_t s) {
-    k_pc_assemble<LAW, DIM, P, LGL, double><<<p.nE, 128, 0, s>>>(W, J, p);
+    if constexpr (LAW == LAW_NS) {
+      JobPcCols<NV, NN, double> j{W, J};
+      launch<LAW, DIM, P, LGL, JobPcCols<NV, NN, double>, double>(j, p, s, NV * NN);
+    } else {
+      k_pc_assemble<LAW, DIM, P, LGL, double><<<p.nE, 128, 0, s>>>(W, J, p);
+    }
   }
   // FP32 assembly for the mixed-precision mode (the blocks only precondition)
   static void pc_assemble_f(const DGParams<float>& p, const double* W, float* J, cudaStream_t s) {
-    k_pc_assemble<LAW, DIM, P, LGL, float><<<p.nE, 128, 0, s>>>(W, J, p);
+    if constexpr (LAW == LAW_NS) {
+      JobPcCols<NV, NN, float> j{W, J};
+      launch<LAW, DIM, P, LGL, JobPcCols<NV, NN, float>, float>(j, p, s, NV * NN);
+    } else {
+      k_pc_assemble<LAW, DIM, P, LGL, float><<<p.nE, 128, 0, s>>>(W, J, p);
+    }
   }
   static void fill(OpsTable& t) {
     t.nv = NV;

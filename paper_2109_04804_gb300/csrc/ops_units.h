@@ -14,4 +14,9 @@
   X(eul2a, 2, 2, 0x18, 0x18)         \
   X(eul2b, 2, 2, 0x60, 0x0)          \
   X(eul3a, 2, 3, 0x18, 0x0)          \
-  X(eul3b, 2, 3, 0x60, 0x0)
+  X(eul3b, 2, 3, 0x60, 0x0)          \
+  X(ns2a, 3, 2, 0x18, 0x18)          \
+  X(ns2b, 3, 2, 0x60, 0x0)           \
+  X(ns3a, 3, 3, 0x18, 0x0)           \
+  X(ns3b, 3, 3, 0x40, 0x0)           \
+  X(ns3c, 3, 3, 0x20, 0x0)

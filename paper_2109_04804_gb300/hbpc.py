@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # -- enums (hbpc.h) -----------------------------------------------------------
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NO_CONVERGENCE, ERR_NONFINITE, ERR_TIMEOUT, \
     ERR_UNSUPPORTED = range(8)
-LAW_ADVECTION, LAW_BURGERS, LAW_EULER = 0, 1, 2
+LAW_ADVECTION, LAW_BURGERS, LAW_EULER, LAW_NAVIER_STOKES = 0, 1, 2, 3
 FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
 PC_NONE, PC_BJEXT, PC_LEARNED = 0, 1, 2
@@ -43,7 +43,7 @@ class Mesh(ctypes.Structure):
 class Physics(ctypes.Structure):
     _fields_ = [("law", ctypes.c_int), ("flux", ctypes.c_int), ("a", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("lf_scale", ctypes.c_double),
-                ("nu", ctypes.c_double), ("eta_br2", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("eta_br2", ctypes.c_double), ("prandtl", ctypes.c_double)]
 
 
 class Solver(ctypes.Structure):
@@ -187,15 +187,16 @@ class Context:
 
     def __init__(self, dim, n, lo, hi, N, law=LAW_ADVECTION, flux=FLUX_GLOBAL_LF,
                  a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, nu=0.0, eta_br2=0.0,
-                 nodes=NODES_LOBATTO,
+                 nodes=NODES_LOBATTO, mu=None, prandtl=0.72,
                  q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0,
                  tol_gmres_rel=1e-5, gmres_restart=100, gmres_max_iter=7000,
                  newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64, stream=None):
         pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
         self.mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                          (ctypes.c_double * 3)(*pad(hi, 1.0)))
+        # the Navier-Stokes law takes its dynamic viscosity mu in the nu field
         self.phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
-                            nu, eta_br2)
+                            nu if mu is None else mu, eta_br2, prandtl)
         self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel,
                              gmres_restart, gmres_max_iter, newton_max_iter, pc, precision)
         self.N, self.dim, self.nodes = N, dim, nodes
@@ -373,12 +374,12 @@ class Batch:
             self.M[i] = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                              (ctypes.c_double * 3)(*pad(hi, 1.0)))
             self.Ph[i] = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
-                                 float(nus[i]), eta_br2)
+                                 float(nus[i]), eta_br2, 0.72)
         self.Nv = (ctypes.c_int * k)(*Ns)
         self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel, gmres_restart,
                              gmres_max_iter, newton_max_iter, pc, precision)
         self.dim, self.n_inst, self.Ns = dim, k, list(Ns)
-        self.nv = (dim + 2) if law == LAW_EULER else 1
+        self.nv = (dim + 2) if law in (LAW_EULER, LAW_NAVIER_STOKES) else 1
         self.meshes = [tuple(m) for m in meshes]
         self._b = _CTX()
         st = _lib.hbpc_batch_create(ctypes.byref(self._b), k, ctypes.addressof(self.M), ctypes.addressof(self.Nv),

@@ -53,7 +53,8 @@ def test_basis_matches_oracle(hbpc, N, family, code):
     (dict(kmax=-1), 1), (dict(gmres_restart=0), 1), (dict(gmres_max_iter=0), 1),
     (dict(eps=0.0), 1), (dict(law=7), 1), (dict(nodes=3), 1), (dict(dim=4), 1),
     (dict(nu=-0.1), 1), (dict(nu=float("nan")), 1), (dict(nu=0.01, eta_br2=float("inf")), 1),
-    (dict(nu=0.01, law=2), 7),
+    (dict(nu=0.01, law=2), 7), (dict(law=3, nu=0.01, prandtl=float("nan")), 1),
+    (dict(law=3, nu=0.01, gamma=1.0), 1), (dict(law=4), 1),
 ])
 def test_invalid_arguments_rejected(hbpc, kw, code):
     args = dict(dim=2, n=(2, 2), lo=(0, 0), hi=(1, 1), N=3)
@@ -81,4 +82,7 @@ def test_batch_invalid_arguments_rejected(hbpc):
     assert ei.value.status == 1
     with pytest.raises(hbpc.HBPCError) as ei:          # the learned preconditioner
         hbpc.Batch(2, meshes, [3, 4], nus=[0.01, 0.02], pc=hbpc.PC_LEARNED)
+    assert ei.value.status == 7
+    with pytest.raises(hbpc.HBPCError) as ei:          # Navier-Stokes batches
+        hbpc.Batch(2, meshes, [3, 4], nus=[0.01, 0.02], law=hbpc.LAW_NAVIER_STOKES)
     assert ei.value.status == 7

@@ -600,6 +600,112 @@ def run_vortex(args, emit=True):
     return line
 
 
+TGV = dict(n=32, N=5, q=4, kmax=0, cfl=20.0, eps=0.1, re=1600.0, prandtl=0.72, tol_newton_rel=1e-10,
+           tol_newton_abs=1e-10, tol_gmres_rel=1e-3, gmres_restart=100, gmres_max_iter=5000, newton_max_iter=30,
+           check_n=8)
+
+
+def tgv_dt(n):
+    """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v|_max + c of the
+    initial state (|v| <= 1, c = 1/eps with p ~ 1/gamma)."""
+    h = 2.0 * np.pi / n
+    lam = 1.0 + 1.0 / TGV["eps"]
+    return TGV["cfl"] / (3 * lam * (TGV["N"] + 1) / h)
+
+
+def run_tgv(args, emit=True):
+    """3-D Navier-Stokes Taylor-Green vortex (Mach 0.1 through the reference
+    Mach number eps, Re 1600, Pr 0.72) on [0, 2 pi]^3, 32^3 elements, N = 5,
+    Rusanov, HBPC(4, 0), CFL 20, in the mixed mode with plain GMRES: BJ_ext
+    blocks of n_b = 5 * 6^3 = 1080 do not fit (2 x 32768 x 1080^2 values), and
+    a compact learned preconditioner for them is not built.  Newton stops at
+    ||G|| <= 1e-10 ||G0|| or ||dW|| <= 1e-10 (the FP64 residual of 70.8 M values
+    has a rounding floor near 5e-9).  The FP64-vs-mixed difference of the answer
+    is measured on an 8^3 mesh at the same CFL (one step each)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    L = 2.0 * np.pi
+
+    def ctx(n, prec):
+        return hbpc.Context(3, (n, n, n), (0, 0, 0), (L, L, L), TGV["N"], law=hbpc.LAW_NAVIER_STOKES,
+                            flux=hbpc.FLUX_RUSANOV, mu=1.0 / TGV["re"], eps=TGV["eps"], prandtl=TGV["prandtl"],
+                            q=TGV["q"], kmax=TGV["kmax"], dt=tgv_dt(n), tol_newton_rel=TGV["tol_newton_rel"],
+                            tol_newton_abs=TGV["tol_newton_abs"], tol_gmres_rel=TGV["tol_gmres_rel"],
+                            gmres_restart=TGV["gmres_restart"], gmres_max_iter=TGV["gmres_max_iter"],
+                            newton_max_iter=TGV["newton_max_iter"], pc=hbpc.PC_NONE, precision=prec)
+
+    def stepped(c, w0, steps):
+        c.set_state(w0)
+        ms = 0.0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            c.step(1)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms
+
+    n = TGV["n"]
+    c = ctx(n, hbpc.PREC_MIXED)
+    w0 = inputs.taylor_green(c.node_coords(), eps=TGV["eps"])
+    ndof = c.ndof
+    # R1 evaluations per second (FP64 operator, full mesh, inputs resident)
+    wd = torch.from_numpy(w0).cuda()
+    o = torch.empty_like(wd)
+    for _ in range(3):
+        c.eval_R1(wd, o)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        c.eval_R1(wd, o)
+    e1.record()
+    torch.cuda.synchronize()
+    r1_ms = e0.elapsed_time(e1) / 10
+    del wd, o
+    warm = max(1, min(args.warmup, 1))
+    steps = max(1, min(args.steps, 2))
+    stepped(c, w0, warm)
+    st0 = c.stats()
+    ms = stepped(c, c.get_state(), steps)
+    st = c.stats()
+    c.close()
+    # FP64 vs mixed on the reduced mesh, same CFL, one step each
+    chk = {}
+    for prec, name in ((hbpc.PREC_FP64, "fp64"), (hbpc.PREC_MIXED, "mixed")):
+        cc = ctx(TGV["check_n"], prec)
+        w = inputs.taylor_green(cc.node_coords(), eps=TGV["eps"])
+        t = stepped(cc, w, 1)
+        chk[name] = (cc.get_state(), t, cc.stats())
+        cc.close()
+    wf, wm = chk["fp64"][0], chk["mixed"][0]
+    line = {"metric": METRIC, "value": ndof * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov and Jacobian-vector products",
+            "data": "synthetic",
+            "config": {"workload": "3d_navier_stokes_taylor_green_32x32x32_N5_HBPC(4,0)_CFL20_Rusanov_Re1600_Ma0.1",
+                       "dt": tgv_dt(n), "eps_newton": TGV["tol_newton_rel"], "eps_newton_abs": TGV["tol_newton_abs"],
+                       "eps_gmres": TGV["tol_gmres_rel"], "gmres_restart": TGV["gmres_restart"],
+                       "precision": "mixed", "preconditioner": "none (plain GMRES)",
+                       "l2_flush": "inputs larger than L2 (a Krylov vector is 283 MB)"},
+            "gpu_launches": int(st["launches"] - st0["launches"]),
+            "gmres_its_per_step": (st["gmres_its"] - st0["gmres_its"]) / steps,
+            "newton_its_per_step": (st["newton_its"] - st0["newton_its"]) / steps,
+            "r1_fp64_ms": r1_ms, "r1_evals_per_s_fp64": 1000.0 / r1_ms,
+            "fp64_vs_mixed_8cubed": {"rel_l2": float(np.linalg.norm(wm - wf) / np.linalg.norm(wf)),
+                                     "fp64_ms": chk["fp64"][1], "mixed_ms": chk["mixed"][1],
+                                     "fp64_gmres_its": int(chk["fp64"][2]["gmres_its"]),
+                                     "mixed_gmres_its": int(chk["mixed"][2]["gmres_its"])}}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -637,9 +743,11 @@ def main():
                     help="skip the learned-vs-plain-GMRES comparison on the Euler vortex in the default line")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
-    ap.add_argument("--workload", default="advection2d", choices=["advection2d", "burgers_batch", "euler_vortex"],
+    ap.add_argument("--workload", default="advection2d",
+                    choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
-                         "viscous Burgers instances")
+                         "viscous Burgers instances; euler_vortex: learned vs BJ_ext vs plain GMRES; "
+                         "taylor_green: the 3-D Navier-Stokes line")
     ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
     ap.add_argument("--max-per-group", type=int, default=BATCH["max_per_group"],
                     help="instances sharing one context and one GMRES (<= 0: all of one N)")
@@ -651,6 +759,8 @@ def main():
         run_batch(args)
     elif args.workload == "euler_vortex":
         run_vortex(args)
+    elif args.workload == "taylor_green":
+        run_tgv(args)
     else:
         run_ours(args)
 

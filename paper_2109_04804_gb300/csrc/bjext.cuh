@@ -147,6 +147,8 @@ struct PcApplyT {
   int accumulate;
   double* zn;
   int nb, nE;
+  int shared;                   // 1: every element uses block 0 (a state- and
+                                // element-independent J_i, see pc_build)
 };
 using PcApply = PcApplyT<double>;
 

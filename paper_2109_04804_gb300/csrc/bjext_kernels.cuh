@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   __syncthreads();
   S u = S(0), v = S(0);
   if (live) {
-    const S* Me = a.M + size_t(e) * nb * nb;
+    const S* Me = a.M + (a.shared ? size_t(0) : size_t(e) * nb * nb);
     int c = 0;
     for (; c + 3 < nb; c += 4) {   // four columns' loads in flight, sums in column order
       const S m0 = Me[size_t(c) * nb + r], m1 = Me[size_t(c + 1) * nb + r];
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   __syncthreads();
   double aw = 0.0, as = 0.0;
   if (live) {
-    const S* Je = a.J + size_t(e) * nb * nb;
+    const S* Je = a.J + (a.shared ? size_t(0) : size_t(e) * nb * nb);
     S ju = S(0), jv = S(0);
     int c = 0;
     for (; c + 3 < nb; c += 4) {
@@ -267,6 +267,89 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
     a.zn[0] = sqrt(rr[0] + rr[1]);
     a.zn[1] = sqrt(rr[0]);
     a.zn[2] = sqrt(rr[1]);
+  }
+}
+
+// P^-1 with one block for all elements (PcApplyT::shared): the same algebra as
+// k_pc_apply, organised as the small dense products they are.  M and J live in
+// shared memory; a thread owns row r of EG elements, so every loaded entry of M
+// and J is used for 2 EG multiply-adds, and the elements' inputs are staged with
+// the EG elements of a group interleaved (one vector load per column).  The
+// block covers (blockDim.x / n_b) groups.  No norms (callers with a.zn use
+// k_pc_apply).  Dynamic shared memory: (2 n_b^2 + 4 EG n_b groups) S.
+template <typename S, int EG>
+__global__ void __launch_bounds__(256) k_pc_apply_shared(PcApplyT<S> a) {
+  if (a.skip && *a.skip) return;
+  const int nb = a.nb;
+  const int groups = blockDim.x / nb;
+  const int g = threadIdx.x / nb, r = threadIdx.x - g * nb;
+  const bool live_t = g < groups;
+  extern __shared__ double sh_raw[];
+  S* sM = reinterpret_cast<S*>(sh_raw);
+  S* sJ = sM + nb * nb;
+  S* X = sJ + nb * nb;                        // [groups][nb][EG] xw, then xs, u, v
+  const int gsz = nb * EG;
+  S* Xw = X;
+  S* Xs = Xw + groups * gsz;
+  S* U = Xs + groups * gsz;
+  S* Vv = U + groups * gsz;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) { sM[t] = a.M[t]; sJ[t] = a.J[t]; }
+  const long long e0 = (long long)blockIdx.x * groups * EG;   // first element of the block
+  const size_t off = (a.jidx ? size_t(*a.jidx) * a.ld : 0);
+  const S sc = S(a.scale ? (a.jidx ? a.scale[*a.jidx] : *a.scale) : 1.0);
+  // stage the block's inputs (contiguous in memory), interleaving the EG
+  // elements of each group
+  const int nvals = groups * EG * nb;
+  for (int t = threadIdx.x; t < nvals; t += blockDim.x) {
+    const long long e = e0 + t / nb;
+    const int c = t % nb;
+    const int le = t / nb, gg = le / EG, k = le - gg * EG;
+    S w = S(0), z = S(0);
+    if (e < a.nE) {
+      w = sc * a.xW[off + size_t(e) * nb + c];
+      z = sc * a.xS[off + size_t(e) * nb + c];
+    }
+    Xw[gg * gsz + c * EG + k] = w;
+    Xs[gg * gsz + c * EG + k] = z;
+  }
+  __syncthreads();
+  S u[EG], v[EG];
+#pragma unroll
+  for (int k = 0; k < EG; ++k) { u[k] = S(0); v[k] = S(0); }
+  if (live_t) {
+    const S* xw = Xw + g * gsz;
+    const S* xs = Xs + g * gsz;
+    for (int c = 0; c < nb; ++c) {
+      const S m = sM[c * nb + r];
+#pragma unroll
+      for (int k = 0; k < EG; ++k) { u[k] += m * xw[c * EG + k]; v[k] += m * xs[c * EG + k]; }
+    }
+#pragma unroll
+    for (int k = 0; k < EG; ++k) { U[g * gsz + r * EG + k] = u[k]; Vv[g * gsz + r * EG + k] = v[k]; }
+  }
+  __syncthreads();
+  if (!live_t) return;
+  S ju[EG], jv[EG];
+#pragma unroll
+  for (int k = 0; k < EG; ++k) { ju[k] = S(0); jv[k] = S(0); }
+  const S* su = U + g * gsz;
+  const S* sv = Vv + g * gsz;
+  for (int c = 0; c < nb; ++c) {
+    const S j = sJ[c * nb + r];
+#pragma unroll
+    for (int k = 0; k < EG; ++k) { ju[k] += j * su[c * EG + k]; jv[k] += j * sv[c * EG + k]; }
+  }
+  const S c1 = S(a.c12[0]), c2 = S(a.c12[1]);
+#pragma unroll
+  for (int k = 0; k < EG; ++k) {
+    const long long e = e0 + g * EG + k;
+    if (e >= a.nE) break;
+    S top = u[k] - c2 * jv[k];
+    S bot = ju[k] + v[k] - c1 * jv[k];
+    const size_t o = size_t(e) * nb + r;
+    if (a.accumulate) { top += a.oW[o]; bot += a.oS[o]; }
+    a.oW[o] = top;
+    a.oS[o] = bot;
   }
 }
 

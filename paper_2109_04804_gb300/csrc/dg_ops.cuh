@@ -60,6 +60,9 @@ struct KernelShape {
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF, EPB = Geo<DIM, P>::EPB;
   // gradient channels of the system path: g = (v, T) and, for R2, gs = (dg/dw) s
   static constexpr int NCH = NSV ? 2 * (DIM + 1) : 0;
+  // resident blocks per SM the register allocation must allow (shared memory
+  // admits two blocks of the 3-D Navier-Stokes kernel)
+  static constexpr int MIN_BLOCKS = (NSV && DIM == 3) ? 2 : 1;
   // shared values per element: state + direction + DIM fluxes + 2*DIM faces
   // (+ 2*DIM faces of u* - u for the scalar viscous term; + the nodal channels
   // and, per face, the own trace, the neighbour's trace and the neighbour's
@@ -220,27 +223,31 @@ struct FaceVisc {
 // through this face point is read from global memory and converted to g, and
 // for R2 to gs = (dg/dw) s).  Stored per face for stage B, which needs the
 // traces of neighbouring face points for the tangential derivatives.
-// Channel layout: [0, NG) g, [NG, 2 NG) gs (R2 only).
+// Channel layout: [0, NG) g, [NG, 2 NG) gs (R2 only).  The face direction M and
+// side are runtime values (one copy of the code for all 2 DIM faces keeps the
+// kernel inside the instruction cache); register arrays are indexed only by
+// unrolled loop counters.
 template <int DIM, int P, typename V, class Job>
 struct FaceViscSysA {
   using T = typename BaseOf<V>::type;
   using NS = NSVisc<DIM, T>;
   static constexpr int NV = DIM + 2, NG = DIM + 1, NCH = 2 * NG;
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
-  template <int M, int SIDE>
   __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, const InstGeo<T>& g, int k,
-                                             bool r2, const int* ec, int pt, const V* sgc, const T* sgp, const T* sgm,
-                                             V* sfo, V* sfn, V* sfd) {
-    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+                                             bool r2, const int* ec, int f, int pt, const V* sgc, const T* sgp,
+                                             const T* sgm, V* sfo, V* sfn, V* sfd) {
+    const int M = f >> 1, side = f & 1;
+    const int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;
-    int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
-    int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
-    c += SIDE ? 1 : -1;
-    if (c < 0) c += g.n[M];
-    if (c >= g.n[M]) c -= g.n[M];
+    // neighbour element across this face (periodic within the instance)
+    const int dlt = side ? 1 : -1;
+    int nc0 = ec[0] + (M == 0 ? dlt : 0), nc1 = ec[1] + (M == 1 ? dlt : 0), nc2 = ec[2] + (M == 2 ? dlt : 0);
+    nc0 = nc0 < 0 ? nc0 + g.n[0] : (nc0 >= g.n[0] ? nc0 - g.n[0] : nc0);
+    nc1 = nc1 < 0 ? nc1 + g.n[1] : (nc1 >= g.n[1] ? nc1 - g.n[1] : nc1);
+    nc2 = nc2 < 0 ? nc2 + g.n[2] : (nc2 >= g.n[2] ? nc2 - g.n[2] : nc2);
     const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
-    const int f = 2 * M + SIDE;
     const int nch = r2 ? NCH : NG;
+    const T* dnb = (side ? sgm : sgp) + M * P;             // neighbour's normal-derivative weights
     V un[NCH], gn[NCH];
 #pragma unroll
     for (int q = 0; q < NCH; ++q) { un[q] = V(T(0)); gn[q] = V(T(0)); }
@@ -255,8 +262,9 @@ struct FaceViscSysA {
         load_nb_dir<NV>(job, k, en, node, y);
         NS::grad_vars_jvp(x, y, ch + NG, prm);
       }
-      const T ln = SIDE ? prm.lm[i] : prm.lp[i];                       // neighbour's trace at this face
-      const T dn = SIDE ? sgm[M * P + i] : sgp[M * P + i];             // and its normal derivative
+      // the neighbour's trace weights at this face (parameters read by value:
+      // no pointer into the parameter space)
+      const T ln = side ? prm.lm[i] : prm.lp[i], dn = dnb[i];
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
         if (q < nch) { un[q] += ln * ch[q]; gn[q] += dn * ch[q]; }
@@ -266,7 +274,7 @@ struct FaceViscSysA {
       if (q < nch) {
         V uo = V(T(0));
 #pragma unroll
-        for (int i = 0; i < P; ++i) uo += (SIDE ? prm.lp[i] : prm.lm[i]) * sgc[q * NN + base + i * st];
+        for (int i = 0; i < P; ++i) uo += (side ? prm.lp[i] : prm.lm[i]) * sgc[q * NN + base + i * st];
         sfo[(f * NCH + q) * NF + pt] = uo;
         sfn[(f * NCH + q) * NF + pt] = un[q];
         sfd[(f * NCH + q) * NF + pt] = gn[q];
@@ -280,21 +288,24 @@ struct FaceViscSysA {
 // the face's own lifting, the tangential ones from the traces of the face
 // points along that direction -- and the central viscous flux of Eq. 30 (R1)
 // or its linearisation (R2, Eq. 32), added to sface with the sign convention
-// of the inviscid flux (outward normal).
+// of the inviscid flux (outward normal).  Runtime face as in stage A.
 template <int DIM, int P, typename V>
 struct FaceViscSysB {
   using T = typename BaseOf<V>::type;
   using NS = NSVisc<DIM, T>;
   static constexpr int NV = DIM + 2, NG = DIM + 1, NCH = 2 * NG;
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
-  template <int M, int SIDE>
-  __device__ __forceinline__ static void run(const DGParams<T>& prm, const InstGeo<T>& g, bool r2, int pt,
+  __device__ __forceinline__ static void run(const DGParams<T>& prm, const InstGeo<T>& g, bool r2, int f, int pt,
                                              const V* sgc, const T* sDg, const T* sgp, const T* sgm, const V* sfo,
                                              const V* sfn, const V* sfd, V* sface) {
-    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    const int M = f >> 1, side = f & 1;
+    const int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;
-    const int f = 2 * M + SIDE;
     const int nch = r2 ? NCH : NG;
+    const T* gown = (side ? sgp : sgm) + M * P;            // own normal-derivative weights
+    // lower tangential direction is fastest in the face numbering
+    // (pt = j + P k on x faces, i + P k on y faces, i + P j on z faces)
+    const int lo_t = (M == 0) ? 1 : 0;
     // gradients of the own (o) and neighbour (n) side: [channel set][direction][channel]
     V dO[2][DIM][NG], dN[2][DIM][NG], gO[NCH], gN[NCH];
 #pragma unroll
@@ -306,60 +317,63 @@ struct FaceViscSysB {
         for (int kk = 0; kk < DIM; ++kk) { dO[set][kk][cq] = V(T(0)); dN[set][kk][cq] = V(T(0)); }
         continue;
       }
-      const V uo = sfo[(f * NCH + q) * NF + pt], un = sfn[(f * NCH + q) * NF + pt];
+      const V* fo = sfo + (f * NCH + q) * NF;
+      const V* fn = sfn + (f * NCH + q) * NF;
+      const V uo = fo[pt], un = fn[pt];
       gO[q] = uo; gN[q] = un;
-      // own normal derivative along the line of this face point
-      V go = V(T(0));
-#pragma unroll
-      for (int i = 0; i < P; ++i) go += (SIDE ? sgp[M * P + i] : sgm[M * P + i]) * sgc[q * NN + base + i * st];
-      const V gn = sfd[(f * NCH + q) * NF + pt];
-      const V us = T(0.5) * (uo + un);
-      // normal component: + face (own = L): d^L = go + bp (u* - uo), d^R = gn + bm (un - u*);
-      //                   - face (own = R): d^L = gn + bp (u* - un), d^R = go + bm (uo - u*)
-      if (SIDE) {
-        dO[set][M][cq] = g.hs[M] * (go + prm.bp[M] * (us - uo));
-        dN[set][M][cq] = g.hs[M] * (gn + prm.bm[M] * (un - us));
-      } else {
-        dO[set][M][cq] = g.hs[M] * (go + prm.bm[M] * (uo - us));
-        dN[set][M][cq] = g.hs[M] * (gn + prm.bp[M] * (us - un));
-      }
-      // tangential components: derivative of the face traces along x_kk
 #pragma unroll
       for (int kk = 0; kk < DIM; ++kk) {
-        if (kk == M) continue;
-        // face point stride of direction kk: the lower tangential direction is fastest
-        // (pt = j + P k on x faces, i + P k on y faces, i + P j on z faces)
-        const int lo_t = (M == 0) ? 1 : 0;
-        const int tstride = (kk == lo_t) ? 1 : P;
-        const int it = (pt / tstride) % P;
-        const int p0 = pt - it * tstride;
-        const T* Drow = sDg + (kk * P + it) * P;
-        V a = V(T(0)), b = V(T(0));
+        if (kk == M) {
+          // normal component: + face (own = L): d^L = go + bp (u* - uo), d^R = gn + bm (un - u*);
+          //                   - face (own = R): d^L = gn + bp (u* - un), d^R = go + bm (uo - u*)
+          V go = V(T(0));
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-          a += Drow[j] * sfo[(f * NCH + q) * NF + p0 + j * tstride];
-          b += Drow[j] * sfn[(f * NCH + q) * NF + p0 + j * tstride];
+          for (int i = 0; i < P; ++i) go += gown[i] * sgc[q * NN + base + i * st];
+          const V gn = sfd[(f * NCH + q) * NF + pt];
+          const V us = T(0.5) * (uo + un);
+          const V lo_ = side ? prm.bp[kk] * (us - uo) : prm.bm[kk] * (uo - us);
+          const V ln_ = side ? prm.bm[kk] * (un - us) : prm.bp[kk] * (us - un);
+          dO[set][kk][cq] = g.hs[kk] * (go + lo_);
+          dN[set][kk][cq] = g.hs[kk] * (gn + ln_);
+        } else {
+          // tangential component: derivative of the face traces along x_kk
+          const int tstride = (kk == lo_t) ? 1 : P;
+          const int it = (pt / tstride) % P;
+          const int p0 = pt - it * tstride;
+          const T* Drow = sDg + (kk * P + it) * P;
+          V a = V(T(0)), b = V(T(0));
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            a += Drow[j] * fo[p0 + j * tstride];
+            b += Drow[j] * fn[p0 + j * tstride];
+          }
+          dO[set][kk][cq] = g.hs[kk] * a;
+          dN[set][kk][cq] = g.hs[kk] * b;
         }
-        dO[set][kk][cq] = g.hs[kk] * a;
-        dN[set][kk][cq] = g.hs[kk] * b;
       }
     }
+    // flux along x_M: the direction is expanded over the unrolled m so that the
+    // register arrays keep compile-time indices
     V FO[NV], FN[NV];
-    if (r2) {
-      NS::flux_lin(gO, dO[0], gO + NG, dO[1], M, FO, prm);
-      NS::flux_lin(gN, dN[0], gN + NG, dN[1], M, FN, prm);
-    } else {
-      NS::flux(gO, dO[0], M, FO, prm);
-      NS::flux(gN, dN[0], M, FN, prm);
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      if (m != M) continue;
+      if (r2) {
+        NS::flux_lin(gO, dO[0], gO + NG, dO[1], m, FO, prm);
+        NS::flux_lin(gN, dN[0], gN + NG, dN[1], m, FN, prm);
+      } else {
+        NS::flux(gO, dO[0], m, FO, prm);
+        NS::flux(gN, dN[0], m, FN, prm);
+      }
     }
-    const T sg = SIDE ? T(-0.5) : T(0.5);
+    const T sg = side ? T(-0.5) : T(0.5);
 #pragma unroll
     for (int v = 1; v < NV; ++v) sface[(f * NV + v) * NF + pt] += sg * (FO[v] + FN[v]);
   }
 };
 
 template <int LAW, int DIM, int P, bool LGL, typename V, class Job>
-__global__ void __launch_bounds__(Geo<DIM, P>::THREADS)
+__global__ void __launch_bounds__(Geo<DIM, P>::THREADS, KernelShape<LAW, DIM, P>::MIN_BLOCKS)
 dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) {
   using T = typename BaseOf<V>::type;
   using L = typename LawOf<LAW, DIM, T>::type;
@@ -473,18 +487,7 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
           default: break;
         }
         if constexpr (NSV) {
-          if (visc) {
-            using FA = FaceViscSysA<DIM, P, V, Job>;
-            switch (f) {
-              case 0: FA::template run<0, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              case 1: FA::template run<0, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              case 2: if constexpr (DIM > 1) FA::template run<1, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              case 3: if constexpr (DIM > 1) FA::template run<1, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              case 4: if constexpr (DIM > 2) FA::template run<2, 0>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              case 5: if constexpr (DIM > 2) FA::template run<2, 1>(job, prm, geo, k, r2, ec, pt, sgc, sgp, sgm, sfo, sfn, sfd); break;
-              default: break;
-            }
-          }
+          if (visc) FaceViscSysA<DIM, P, V, Job>::run(job, prm, geo, k, r2, ec, f, pt, sgc, sgp, sgm, sfo, sfn, sfd);
         } else if constexpr (VISC) {
           if (visc) {
             using FV = FaceVisc<DIM, P, V, Job>;
@@ -511,16 +514,7 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
         if (live) {
           for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
             const int f = fp / NF, pt = fp - f * NF;
-            using FB = FaceViscSysB<DIM, P, V>;
-            switch (f) {
-              case 0: FB::template run<0, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              case 1: FB::template run<0, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              case 2: if constexpr (DIM > 1) FB::template run<1, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              case 3: if constexpr (DIM > 1) FB::template run<1, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              case 4: if constexpr (DIM > 2) FB::template run<2, 0>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              case 5: if constexpr (DIM > 2) FB::template run<2, 1>(prm, geo, r2, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface); break;
-              default: break;
-            }
+            FaceViscSysB<DIM, P, V>::run(prm, geo, r2, f, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface);
           }
           const int nch = r2 ? NCH : NG;
           V d[2][DIM][NG], gch[NCH];

@@ -211,6 +211,10 @@ struct hbpc_ctx {
   int pc_grid = 0, pc_threads = 0;
   size_t pc_smem = 0;
   bool pc_built = false;
+  // BJ_ext with one block for all elements: linear advection (with or without
+  // a viscous term) on one uniform mesh has the same J_i in every element and
+  // for every state, so one J, one S^-1 serve the whole mesh
+  bool pc_shared = false;
   double pc_c1 = 0.0, pc_c2 = 0.0;
   // mixed precision (FP32 Krylov loop, FP64 Newton)
   DGParams<float> prmf{};
@@ -440,6 +444,25 @@ JvInput krylov_input(hbpc_ctx* x) {
   return z;
 }
 
+// The shared-block apply (k_pc_apply_shared, 4 elements per thread) when its
+// shared memory fits the default 48 KB and no norms are wanted; false: the
+// caller launches the general apply (which also handles a shared block).
+constexpr int kPcSharedEG = 4;
+template <typename S>
+bool pc_shared_launch(hbpc_ctx* x, const PcApplyT<S>& a) {
+  if (a.zn) return false;
+  const int nb = a.nb;
+  const int groups = 256 / nb;
+  if (groups < 1) return false;
+  const size_t smem = (2 * size_t(nb) * nb + 4 * size_t(kPcSharedEG) * nb * groups) * sizeof(S);
+  if (smem > 48 * 1024) return false;
+  const int per_block = groups * kPcSharedEG;
+  const int grid = int((x->nE + per_block - 1) / per_block);
+  HBPC_RUN(x, HBPC_PHASE_PC, 1,
+           (k_pc_apply_shared<S, kPcSharedEG><<<grid, groups * nb, smem, x->stream>>>(a)));
+  return cudaPeekAtLastError() == cudaSuccess;
+}
+
 // P^-1 applied to scale * in -> out (out += when accumulate), norms to x->zn
 hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const double* scale,
                      double* out, int accumulate, const int* skip) {
@@ -451,6 +474,8 @@ hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const doubl
   a.c12 = x->c12; a.skip = skip; a.accumulate = accumulate;
   a.zn = x->ops.jv_linear ? nullptr : x->zn;   // ||z|| halves feed eps_FD of Eq. 23 only
   a.nb = x->nb; a.nE = int(x->nE);
+  a.shared = x->pc_shared ? 1 : 0;
+  if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<double><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply");
   return HBPC_OK;
@@ -467,6 +492,8 @@ hbpc_status pc_apply_f(hbpc_ctx* x, const float* in, const int* jidx, const doub
   a.c12 = x->c12; a.skip = skip; a.accumulate = accumulate;
   a.zn = nullptr;   // the analytic FP32 Jv needs no norms
   a.nb = x->nb; a.nE = int(x->nE);
+  a.shared = x->pc_shared ? 1 : 0;
+  if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<float><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply<float>");
   return HBPC_OK;
@@ -699,10 +726,21 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
     return HBPC_OK;
   const size_t nb = size_t(x->nb);
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
+  // one shared block when J_i is the same for every element and state (the
+  // training-data collection and the learned network want per-element blocks)
+  x->pc_shared = linear && x->ninst == 0 && x->sol.pc == HBPC_PC_BJEXT && !collecting;
+  const int nEb = x->pc_shared ? 1 : int(x->nE);   // blocks to build
   // J_i in the precision of the apply: FP32 in the mixed mode (the blocks only
   // precondition the FP32 Krylov loop), FP64 otherwise
-  if (mixed) HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble_f(x->prmf, W, x->Jf, x->stream));
-  else HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(x->prm, W, x->Jpc, x->stream));
+  if (mixed) {
+    DGParams<float> pf = x->prmf;
+    pf.nE = nEb;
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble_f(pf, W, x->Jf, x->stream));
+  } else {
+    DGParams<double> pd = x->prm;
+    pd.nE = nEb;
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(pd, W, x->Jpc, x->stream));
+  }
   hbpc_status s0;
   if (collecting && (s0 = lp_collect(x, W, c1, c2)) != HBPC_OK) return s0;
   if (x->sol.pc == HBPC_PC_LEARNED) {   // M~ from the network instead of the LU
@@ -743,18 +781,17 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   if (mixed) {
     // S and its inverse in FP32 as well
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_form_S<float><<<int(x->nE), 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb,
-                                                                                         int(x->nE), x->c12));
+             k_pc_form_S<float><<<nEb, 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb, nEb, x->c12));
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_invert<float><<<int(x->nE), 256, (nb * nb + nb) * sizeof(float) + nb * sizeof(int), x->stream>>>(
-                 x->Mf, x->nb, int(x->nE), x->singular));
+             k_pc_invert<float><<<nEb, 256, (nb * nb + nb) * sizeof(float) + nb * sizeof(int), x->stream>>>(
+                 x->Mf, x->nb, nEb, x->singular));
   } else {
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_form_S<double><<<int(x->nE), 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb,
-                                                                                           int(x->nE), x->c12));
+             k_pc_form_S<double><<<nEb, 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb, nEb,
+                                                                                   x->c12));
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_invert<double><<<int(x->nE), 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
-                 x->Mpc, x->nb, int(x->nE), x->singular));
+             k_pc_invert<double><<<nEb, 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
+                 x->Mpc, x->nb, nEb, x->singular));
   }
   if (collecting && x->lp.Tbuf) {   // the block inverses as training targets
     auto& L = x->lp;
@@ -1281,6 +1318,10 @@ hbpc_status dmalloc(hbpc_ctx* x, Tp** p, size_t count) {
     *p = nullptr;
     return fail(x, HBPC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
+  // zeroed: the padding entries between the instances of a batch are never
+  // written by the operator kernels and must stay finite (they enter norms)
+  e = cudaMemset(*p, 0, count * sizeof(Tp));
+  if (e != cudaSuccess) return fail(x, HBPC_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
   return HBPC_OK;
 }
 
@@ -1756,6 +1797,16 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
   }
   *hprobe = saved;
   HBPC_CK(x, cudaMemcpyAsync(x->st, hprobe, sizeof(GmresState), cudaMemcpyHostToDevice, x->stream));
+  // the trial launches ran on whatever the buffers held (blocks not yet built,
+  // an empty basis) and may have left non-finite values, also in the padding
+  // entries of a batch that no later kernel overwrites: clear what they wrote
+  const size_t n2b = size_t(2 * x->ndof);
+  if (x->V) HBPC_CK(x, cudaMemsetAsync(x->V, 0, size_t(x->vcols) * n2b * sizeof(double), x->stream));
+  if (x->G) HBPC_CK(x, cudaMemsetAsync(x->G, 0, n2b * sizeof(double), x->stream));
+  if (x->Z) HBPC_CK(x, cudaMemsetAsync(x->Z, 0, n2b * sizeof(double), x->stream));
+  if (x->Vf) HBPC_CK(x, cudaMemsetAsync(x->Vf, 0, size_t(x->sol.gmres_restart + 1) * n2b * sizeof(float), x->stream));
+  if (x->Zf) HBPC_CK(x, cudaMemsetAsync(x->Zf, 0, n2b * sizeof(float), x->stream));
+  if (x->Zf2) HBPC_CK(x, cudaMemsetAsync(x->Zf2, 0, n2b * sizeof(float), x->stream));
   if ((s = sync(x, "autotune")) != HBPC_OK) return s;
   if (out) {
     out->krylov_blocks = best_b;

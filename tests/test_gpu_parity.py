@@ -170,7 +170,8 @@ def test_bjext_apply_parity(hb, law, dim, N, family, flux):
 
 
 @pytest.mark.parametrize("law,dim,N,flux", [(laws.ADVECTION, 2, 5, "lf"), (laws.EULER, 2, 4, "rusanov"),
-                                            (laws.BURGERS, 2, 3, "lf")])
+                                            (laws.BURGERS, 2, 3, "lf"), (laws.ADVECTION, 1, 3, "lf"),
+                                            (laws.ADVECTION, 3, 2, "lf")])
 def test_bjext_apply_parity_mixed(hb, law, dim, N, flux):
     """In the mixed mode the blocks S_e, their Gauss-Jordan inverses and the
     apply are FP32: the result against the oracle's FP64 construction is within

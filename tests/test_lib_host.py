@@ -64,6 +64,17 @@ def test_invalid_arguments_rejected(hbpc, kw, code):
     assert ei.value.status == code
 
 
+@pytest.mark.parametrize("dim,N,nodes", [(1, 3, 0), (2, 1, 0), (2, 6, 0), (3, 6, 0), (2, 4, 1)])
+def test_navier_stokes_outside_the_compiled_set_is_unsupported(hbpc, dim, N, nodes):
+    """The Navier-Stokes kernels exist for dim 2 (N = 2-5 Lobatto, N = 2-3
+    Gauss) and dim 3 (N = 2-5 Lobatto); anything else is HBPC_ERR_UNSUPPORTED
+    before the device is touched."""
+    n = (3,) * dim
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(dim, n, (0,) * dim, (1,) * dim, N, law=hbpc.LAW_NAVIER_STOKES, mu=0.01, nodes=nodes)
+    assert ei.value.status == 7
+
+
 def test_invalid_mesh_rejected(hbpc):
     with pytest.raises(hbpc.HBPCError):
         hbpc.Context(2, (0, 2), (0, 0), (1, 1), 3)

@@ -58,7 +58,9 @@ def config_dict(dt, extra=None):
          "dt": dt, "eps_newton": WL["tol_newton_rel"], "newton_abs_dW": WL["tol_newton_abs"],
          "eps_gmres": WL["tol_gmres_rel"],
          "gmres_restart": WL["gmres_restart"], "preconditioner": "BJ_ext (Sec. 3.2.3)",
-         "l2_between_steps": "flushed (256 MB write) between timed steps"}
+         "l2_between_steps": "flushed (256 MB write) between timed steps",
+         "launches": ("Arnoldi steps in batches of 4 replayed as one CUDA graph each"
+                      if os.environ.get("HBPC_GRAPH", "1") != "0" else "one launch per kernel (HBPC_GRAPH=0)")}
     if extra:
         c.update(extra)
     return c

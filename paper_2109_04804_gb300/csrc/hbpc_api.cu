@@ -264,6 +264,15 @@ struct hbpc_ctx {
   int coop_max_blocks = 0;  // resident blocks of the cooperative kernel
   int sms = 0;
   int verbose = 0;          // HBPC_VERBOSE=1: Newton/GMRES trace on stderr
+  // CUDA graphs of one batch of Arnoldi steps ([0] FP64, [1] mixed); graph_mode
+  // 0 (HBPC_GRAPH=0) launches the kernels one by one
+  struct ArnGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;        // the runtime refused the capture: direct launches
+    long long launches = 0;     // kernel launches the graph replays
+    long long key[8] = {};      // launch shapes it was captured with
+  } arn_graph[2];
+  int graph_mode = 1;
   Prof prof;
 };
 
@@ -875,6 +884,68 @@ hbpc_status arnoldi_step(hbpc_ctx* x) {
   return HBPC_OK;
 }
 
+hbpc_status arnoldi_step_f(hbpc_ctx* x);
+
+// One batch of Arnoldi steps.  Every launch of a step takes its column index,
+// scale and stopping flag from device memory, so a batch is the same launch
+// sequence every time: it is captured into a CUDA graph once per context (again
+// when a launch shape changes) and replayed with one cudaGraphLaunch.  Direct
+// launches instead with HBPC_GRAPH=0, during a phase-profiled step (its events
+// would be captured), when the caller is capturing the stream, and after the
+// runtime refused a capture (e.g. of the cooperative launch).
+hbpc_status arnoldi_batch(hbpc_ctx* x, int batch, bool f32) {
+  hbpc_status (*step)(hbpc_ctx*) = f32 ? arnoldi_step_f : arnoldi_step;
+  auto& g = x->arn_graph[f32 ? 1 : 0];
+  bool use = x->graph_mode != 0 && !x->prof.on && !g.failed;
+  if (use) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(x->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) use = false;
+  }
+  if (use) {
+    const long long key[8] = {x->nblocks, x->pc_threads, x->pc_grid, (long long)x->pc_smem, x->pc_shared ? 1 : 0,
+                              x->coop ? 1 : 0, x->sol.pc, batch};
+    if (g.exec && std::memcmp(key, g.key, sizeof(key)) != 0) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    if (!g.exec) {
+      const long long l0 = x->stats.launches;
+      const std::string err0 = x->err;
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(x->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        hbpc_status s = HBPC_OK;
+        for (int b = 0; b < batch && s == HBPC_OK; ++b) s = step(x);
+        const cudaError_t e = cudaStreamEndCapture(x->stream, &graph);
+        ok = s == HBPC_OK && e == cudaSuccess && graph != nullptr;
+      }
+      if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      g.launches = x->stats.launches - l0;
+      x->stats.launches = l0;   // the capture ran nothing
+      if (!ok) {
+        g.exec = nullptr;
+        g.failed = true;
+        (void)cudaGetLastError();   // the refused capture's error is not the caller's
+        x->err = err0;
+        if (x->verbose) std::fprintf(stderr, "[hbpc] Arnoldi batch not captured: direct launches\n");
+      } else {
+        std::memcpy(g.key, key, sizeof(key));
+      }
+    }
+    if (g.exec) {
+      HBPC_CK(x, cudaGraphLaunch(g.exec, x->stream));
+      x->stats.launches += g.launches;
+      return HBPC_OK;
+    }
+  }
+  for (int b = 0; b < batch; ++b) {
+    const hbpc_status s = step(x);
+    if (s != HBPC_OK) return s;
+  }
+  return HBPC_OK;
+}
+
 // Solve J dX = -G (G in x->G with squared norms in st->nrm) by restarted GMRES
 // from dX = 0; returns the iteration count through *its.
 hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
@@ -886,11 +957,9 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const int batch = 4;
   int j_prev = 0;
   for (;;) {
-    for (int b = 0; b < batch; ++b) {
-      hbpc_status s = arnoldi_step(x);
-      if (s != HBPC_OK) return s;
-    }
-    hbpc_status s = read_state(x);
+    hbpc_status s = arnoldi_batch(x, batch, false);
+    if (s != HBPC_OK) return s;
+    s = read_state(x);
     if (s != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
     x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
@@ -986,8 +1055,7 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const int batch = 4;
   int j_prev = 0;
   for (;;) {
-    for (int b = 0; b < batch; ++b)
-      if ((s = arnoldi_step_f(x)) != HBPC_OK) return s;
+    if ((s = arnoldi_batch(x, batch, true)) != HBPC_OK) return s;
     if ((s = read_state(x)) != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
     x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
@@ -1326,6 +1394,8 @@ hbpc_status dmalloc(hbpc_ctx* x, Tp** p, size_t count) {
 }
 
 void free_all(hbpc_ctx* x) {
+  for (auto& g : x->arn_graph)
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
   for (auto& p : x->prof.pend) { x->prof.pool.push_back(p.a); x->prof.pool.push_back(p.b); }
   for (cudaEvent_t e : x->prof.pool) cudaEventDestroy(e);
   x->prof.pool.clear();
@@ -1927,6 +1997,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   }
   x->stream = st;
   if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
+  if (const char* v = std::getenv("HBPC_GRAPH")) x->graph_mode = std::atoi(v);
   if (!basis_1d(N, nodes, x->basis) ||
       !get_ops(x->phys.law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
     cudaStreamDestroy(st);
@@ -2028,6 +2099,7 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
   x->ndof = x->nE * x->nv * nn;
   x->stream = static_cast<cudaStream_t>(cuda_stream);
   if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
+  if (const char* v = std::getenv("HBPC_GRAPH")) x->graph_mode = std::atoi(v);
   if (!basis_1d(N, nodes, x->basis)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis"); }
   if (!get_ops(phys->law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
     delete x;

@@ -251,7 +251,7 @@ def run_ours(args):
     prof_cgs = (prof["arnoldi_dot"][0] + prof["arnoldi_update"][0], its_p)
     kernels = {"jv": ("dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)"
                       % ("float" if mixed else "double"), jv_work_per_dof(mixed), prof["jv"]),
-               "pc_apply": (("k_pc_apply_shared<float, 4> (BJ_ext, Sec. 3.2.3; one block pair for all elements)"
+               "pc_apply": (("k_pc_apply_shared<float, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements)"
                              if mixed else "k_pc_apply<double> (BJ_ext, Sec. 3.2.3; one block pair for all elements)"),
                             pc_work_per_dof(mixed), prof["pc_apply"]),
                "cgs2": ("k_cgs_coop<%s> (Arnoldi CGS2 column, one cooperative launch; mean j + 1 = %.1f)"

@@ -453,10 +453,10 @@ JvInput krylov_input(hbpc_ctx* x) {
   return z;
 }
 
-// The shared-block apply (k_pc_apply_shared, 4 elements per thread) when its
+// The shared-block apply (k_pc_apply_shared, 2 elements per thread) when its
 // shared memory fits the default 48 KB and no norms are wanted; false: the
 // caller launches the general apply (which also handles a shared block).
-constexpr int kPcSharedEG = 4;
+constexpr int kPcSharedEG = 2;
 template <typename S>
 bool pc_shared_launch(hbpc_ctx* x, const PcApplyT<S>& a) {
   if (a.zn) return false;

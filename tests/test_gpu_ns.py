@@ -216,3 +216,38 @@ def test_taylor_green_3d_step_vs_oracle(hb):
     ref = ohbpc.dg_stepper(disc, dt, 4, 1, opts)(inputs.taylor_green(disc.node_coords(), eps=0.1))
     assert rel(w, ref) <= 1e-10
     ctx.close()
+
+
+def test_taylor_green_full_size_sampled_parity(hb):
+    """The bench's Taylor-Green configuration at full size (32^3 elements,
+    N = 5, 35.4 M values): R1 and R2 on sampled elements against the oracle.
+    An element's operators depend only on it and its face neighbours (BR2 is
+    compact), so the oracle evaluates a periodic 3 x 3 x 3 patch of elements
+    centred on the sample and its centre element is compared."""
+    n, N = 32, 5
+    L = 2 * np.pi
+    ctx = hb.Context(3, (n, n, n), (0, 0, 0), (L, L, L), N, law=hb.LAW_NAVIER_STOKES, flux=FLUX["rusanov"],
+                     mu=1.0 / 1600, eps=0.1, q=4, kmax=0, dt=0.02, gmres_restart=2)
+    w = inputs.taylor_green(ctx.node_coords(), eps=0.1)
+    rng = np.random.default_rng(70)
+    w = w * (1.0 + 1e-3 * rng.standard_normal(w.shape))
+    s = rng.standard_normal(w.shape)
+    wd, sd = dev(w), dev(s)
+    out = torch.empty_like(wd)
+    ctx.eval_R1(wd, out)
+    r1 = host(out)
+    ctx.eval_R2(wd, sd, out)
+    r2 = host(out)
+    ctx.close()
+    del wd, sd, out
+    h = L / n
+    ph = laws.Physics(laws.NAVIER_STOKES, 3, flux="rusanov", mu=1.0 / 1600, eps=0.1)
+    patch = dgsem.Disc(dgsem.Mesh(3, (3, 3, 3), (0, 0, 0), (3 * h,) * 3), N, ph, LOBATTO)
+    for e in rng.integers(0, n ** 3, size=8):
+        ex, ey, ez = e % n, (e // n) % n, e // (n * n)
+        idx = [((ex + a) % n) + n * (((ey + b) % n) + n * ((ez + c) % n))
+               for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)]
+        ref1 = dgsem.R1(patch, w[idx])[13]
+        ref2 = dgsem.R2(patch, w[idx], s[idx])[13]
+        assert np.abs(r1[e] - ref1).max() <= 1e-12 * np.abs(ref1).max(), e
+        assert np.abs(r2[e] - ref2).max() <= 1e-12 * np.abs(ref2).max(), e

@@ -153,8 +153,16 @@ enum {
 typedef struct hbpc_ctx hbpc_ctx;
 
 /* Create a context: computes the basis (Sec. 3.1.1) on the host, allocates all
- * device memory the method needs and binds to the current CUDA device and the
- * given stream (cudaStream_t, NULL = default).  N >= 1 and (N+1) <= 8. */
+ * device memory the method needs (zero-filled) and binds to the current CUDA
+ * device and the given stream (cudaStream_t, NULL = default).  N >= 1 and
+ * (N+1) <= 8; a (law, dim, N, node family) whose kernels are not compiled in is
+ * HBPC_ERR_UNSUPPORTED before any device call.
+ * Environment, read at creation: HBPC_VERBOSE=1 prints the Newton and GMRES
+ * iterations on stderr; HBPC_GRAPH=0 launches the kernels of the GMRES
+ * iterations one by one instead of replaying each batch of four iterations as
+ * a CUDA graph captured on the context's stream (the default; a stream the
+ * caller is capturing, a phase-profiled call or a capture the runtime refuses
+ * also take direct launches). */
 hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
                         const hbpc_physics* phys, const hbpc_solver* solver,
                         void* cuda_stream);

@@ -237,3 +237,22 @@ def test_invalid_viscosity_arguments():
     assert ph.R_gas == pytest.approx(1.0 / (1.4 * 0.25))
     assert ph.cp == pytest.approx(ph.R_gas * 1.4 / 0.4)
     assert ph.kappa_heat == pytest.approx(ph.cp * 2e-3 / 0.72)
+
+
+@pytest.mark.parametrize("dim,flux", [(2, "lf"), (2, "rusanov"), (3, "lf")])
+def test_navier_stokes_jfnk_matches_dense_newton(dim, flux):
+    """The matrix-free Newton-GMRES stage solve of the viscous law (Eq. 17 with
+    the Eq. 23 quotients) reaches the root of a dense Newton whose Jacobian is
+    built column by column by complex step and solved by LU."""
+    from oracle import exact
+    n = (2, 2) if dim == 2 else (2, 1, 2)   # 3-D: one element in y, its own periodic neighbour
+    disc = ns_disc(dim, n, 2 if dim == 2 else 1, mu=0.05, flux=flux)
+    W0 = random_state(disc, 61)
+    b = W0 + 0.01 * np.random.default_rng(62).standard_normal(disc.shape)
+    dt, a1, a2 = 0.05, 0.5, 1.0 / 6.0
+    Wd, Sd = exact.dense_newton(lambda w: dgsem.R1(disc, w), lambda w, s: dgsem.R2(disc, w, s), b, a1, a2, dt, W0)
+    for jv in ("fd", "analytic"):
+        opts = newton.NewtonOptions(tol_rel=1e-13, tol_abs=1e-14, gmres_tol=1e-8, restart=400, jv=jv)
+        W, S, st = newton.newton_solve(disc, b, a1, a2, dt, W0, opts)
+        assert st.converged
+        assert np.linalg.norm(W - Wd) / np.linalg.norm(Wd) < 1e-12, jv

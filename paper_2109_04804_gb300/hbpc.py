@@ -183,7 +183,17 @@ def eval_Jv_noalloc(dim, n, lo, hi, N, dt, alpha1, alpha2, X, dX, out, law=LAW_A
 
 
 class Context:
-    """One HBPC-DGSEM problem on the current CUDA device."""
+    """One HBPC-DGSEM problem on the current CUDA device.
+
+    Arguments follow the C structs of ``include/hbpc.h``: the mesh (dim, n, lo,
+    hi), the degree N and node family, the law and flux (a: advection speed;
+    gamma, eps: Euler and Navier-Stokes; nu: the viscosity of a scalar law's
+    BR2 term; mu, prandtl: the Navier-Stokes viscosity and Prandtl number, mu
+    filling the same field as nu; eta_br2: the BR2 face factor, <= 0 for 2 dim)
+    and the solver (HBPC(q, kmax), dt, Newton and GMRES tolerances, restart,
+    iteration caps, preconditioner, precision).  Arrays passed to the eval_*
+    and newton_solve methods are CUDA tensors in the canonical layout
+    w[e][v][node]; set_state/get_state take and return numpy arrays."""
 
     def __init__(self, dim, n, lo, hi, N, law=LAW_ADVECTION, flux=FLUX_GLOBAL_LF,
                  a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0, nu=0.0, eta_br2=0.0,

@@ -251,3 +251,20 @@ def test_taylor_green_full_size_sampled_parity(hb):
         ref2 = dgsem.R2(patch, w[idx], s[idx])[13]
         assert np.abs(r1[e] - ref1).max() <= 1e-12 * np.abs(ref1).max(), e
         assert np.abs(r2[e] - ref2).max() <= 1e-12 * np.abs(ref2).max(), e
+
+
+@pytest.mark.parametrize("dim,n", [(2, (1, 4)), (3, (2, 1, 3))])
+def test_single_element_direction_is_its_own_neighbour(hb, dim, n):
+    """A direction with one element: the element is its own periodic neighbour
+    across both faces (the degenerate mesh of the lifting and the fluxes)."""
+    ctx, disc = pair(hb, dim, 3 if dim == 2 else 2, n, 0.03, LOBATTO, "rusanov", lo=(0, 0, 0), hi=(1.0, 0.5, 2.0))
+    w = random_state(disc, 900 + dim)
+    s = np.random.default_rng(901).standard_normal(disc.shape)
+    out = torch.empty_like(dev(w))
+    ctx.eval_R1(dev(w), out)
+    ref = dgsem.R1(disc, w)
+    assert np.abs(host(out) - ref).max() <= 1e-12 * np.abs(ref).max()
+    ctx.eval_R2(dev(w), dev(s), out)
+    ref = dgsem.R2(disc, w, s)
+    assert np.abs(host(out) - ref).max() <= 1e-12 * np.abs(ref).max()
+    ctx.close()

@@ -17,7 +17,8 @@
  *    the library copies what it keeps.  All device work is enqueued on the
  *    stream given at creation (NULL = legacy default stream) and the calls
  *    return after that stream has finished the call's work.
- *  - Meshes are uniform, Cartesian and periodic in every direction.
+ *  - Meshes are uniform, Cartesian and periodic in every direction
+ *    (hbpc_mesh.periodic must be 1; other boundaries are HBPC_ERR_UNSUPPORTED).
  *  - Invalid arguments are rejected before anything is allocated or launched.
  */
 #ifndef HBPC_H
@@ -34,7 +35,8 @@ typedef enum {
   HBPC_ERR_CUDA = 3,           /* a CUDA call failed (message has the CUDA error) */
   HBPC_ERR_NO_CONVERGENCE = 4, /* Newton or GMRES iteration cap reached */
   HBPC_ERR_NONFINITE = 5,      /* a residual or update norm is NaN or Inf */
-  HBPC_ERR_TIMEOUT = 6,        /* reserved: a bounded device wait gave up */
+  HBPC_ERR_TIMEOUT = 6,        /* a bounded wait for the device gave up
+                                  (hbpc_set_wait_limit) */
   HBPC_ERR_UNSUPPORTED = 7     /* valid request that this build does not cover */
 } hbpc_status;
 
@@ -84,6 +86,9 @@ typedef struct {
   int n[3];         /* elements per direction (n[m] >= 1 for m < dim) */
   double lo[3];     /* domain [lo, hi] per direction */
   double hi[3];
+  int periodic;     /* 1: periodic in every direction, the only boundary this
+                       build implements; 0 (walls or inflow/outflow boundaries)
+                       is HBPC_ERR_UNSUPPORTED */
 } hbpc_mesh;
 
 typedef struct {
@@ -120,6 +125,9 @@ typedef struct {
   int newton_max_iter;   /* Newton iterations per stage solve (cap), >= 1 */
   int pc;                /* hbpc_pc */
   int precision;         /* hbpc_precision */
+  double t_end;          /* final time T_end of the problem (Algorithm 1), used
+                            by hbpc_run; 0 = not given; < 0 or not finite is
+                            HBPC_ERR_INVALID_ARG */
 } hbpc_solver;
 
 typedef struct {
@@ -191,8 +199,32 @@ hbpc_status hbpc_set_time(hbpc_ctx* ctx, double t);
 
 /* Advance the state by n_steps HBPC(q, k_max) steps (Algorithm 1, Sec. 2.1).
  * On non-convergence the state stays at the last completed step and
- * HBPC_ERR_NO_CONVERGENCE is returned. */
+ * HBPC_ERR_NO_CONVERGENCE is returned; a non-finite Newton residual or update
+ * (for instance from a state holding NaN) gives HBPC_ERR_NONFINITE, with the
+ * state likewise left at the last completed step. */
 hbpc_status hbpc_step(hbpc_ctx* ctx, int n_steps);
+
+/* Advance the state from the context's time t (hbpc_set_time, 0 at creation)
+ * to t_end (Algorithm 1 run to T_end): whole steps of the solver's dt while
+ * they fit, then, if t_end - t is not a whole number of steps (a remainder of
+ * more than 1e-10 dt), one last step of the remaining length, so that the
+ * state lands on t_end exactly; the time is t_end afterwards.  t_end < t (by
+ * more than 1e-10 dt) or not finite is HBPC_ERR_INVALID_ARG.  Errors as
+ * hbpc_step; the time then counts the steps completed. */
+hbpc_status hbpc_advance_to(hbpc_ctx* ctx, double t_end);
+
+/* hbpc_advance_to(ctx, solver.t_end); HBPC_ERR_INVALID_ARG if the solver was
+ * created without a final time (t_end = 0). */
+hbpc_status hbpc_run(hbpc_ctx* ctx);
+
+/* Bounded waits.  Every call of the context waits for its stream before it
+ * returns (and inside the Newton loop, for the residual norms).  With a limit
+ * of `seconds` > 0 such a wait gives up after that long and the call returns
+ * HBPC_ERR_TIMEOUT; 0 (the default) waits without a limit.  After
+ * HBPC_ERR_TIMEOUT the work already enqueued keeps running on the device and
+ * the context's state is unspecified: destroy the context (hbpc_destroy waits
+ * for its stream to finish). */
+hbpc_status hbpc_set_wait_limit(hbpc_ctx* ctx, double seconds);
 
 /* r = R1(w), Eq. 12 with the flux of Eq. 13.  w, r: device, n_dof FP64. */
 hbpc_status hbpc_eval_R1(hbpc_ctx* ctx, const double* w, double* r);
@@ -311,9 +343,16 @@ hbpc_status hbpc_profile_get(hbpc_ctx* ctx, double* ms, long long* launches, int
  *  - all calls share the array, which keeps the last call's contents; each call
  *    clears the part that must start at zero, but calls that overlap on the GPU
  *    (concurrent streams or threads) race on it and must be serialised;
+ *  - the device address is looked up once per device and kept; after
+ *    cudaDeviceReset on that device it is stale, so do not call this entry
+ *    point again in that process;
  *  - work is enqueued on cuda_stream (NULL = default) and the call returns when
- *    that stream has finished it; errors are reported by hbpc_last_error(NULL).
- * X, dX, out: device, 2 n_dof FP64 (X = (W, S)). */
+ *    that stream has finished it, also when it fails after its first launch;
+ *    errors are reported by hbpc_last_error(NULL).
+ * X, dX, out: device, 2 n_dof FP64 (X = (W, S)).  `out` must not overlap X or
+ * dX (the kernels read X and dX after they have begun writing out; an
+ * overlapping out is HBPC_ERR_INVALID_ARG, nothing launched); X and dX may
+ * overlap each other. */
 hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics* phys,
                                  double dt, double alpha1, double alpha2, const double* X,
                                  const double* dX, double* out, void* cuda_stream);

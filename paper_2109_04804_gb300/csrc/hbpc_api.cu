@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -273,6 +275,7 @@ struct hbpc_ctx {
     long long key[8] = {};      // launch shapes it was captured with
   } arn_graph[2];
   int graph_mode = 1;
+  double wait_limit_s = 0.0;  // bounded host waits (hbpc_set_wait_limit); 0 = none
   Prof prof;
 };
 
@@ -392,8 +395,24 @@ hbpc_status lincomb(hbpc_ctx* x, double* out, std::initializer_list<std::pair<do
   return HBPC_OK;
 }
 
+// Wait for the context's stream.  With a wait limit the stream is polled and
+// the wait gives up with HBPC_ERR_TIMEOUT after that many seconds (the work
+// keeps running on the device).
 hbpc_status sync(hbpc_ctx* x, const char* where) {
-  cudaError_t e = cudaStreamSynchronize(x->stream);
+  cudaError_t e = cudaSuccess;
+  if (x->wait_limit_s > 0.0) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long long spin = 0;; ++spin) {
+      e = cudaStreamQuery(x->stream);
+      if (e != cudaErrorNotReady) break;
+      const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (waited > x->wait_limit_s)
+        return fail(x, HBPC_ERR_TIMEOUT, std::string(where) + ": the wait limit ran out");
+      if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  } else {
+    e = cudaStreamSynchronize(x->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(x, e, where);
   if (x->prof.on) prof_flush(x);
   return HBPC_OK;
@@ -1457,6 +1476,11 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   auto bad = [](const std::string& m) { return fail(nullptr, HBPC_ERR_INVALID_ARG, m); };
   if (!mesh || !ph || !so) return bad("null argument");
   if (mesh->dim < 1 || mesh->dim > 3) return bad("dim must be 1, 2 or 3");
+  if (mesh->periodic != 1) {
+    if (mesh->periodic == 0)
+      return fail(nullptr, HBPC_ERR_UNSUPPORTED, "only periodic meshes are implemented (periodic = 1)");
+    return bad("periodic must be 0 or 1");
+  }
   for (int m = 0; m < mesh->dim; ++m) {
     if (mesh->n[m] < 1) return bad("n[m] must be >= 1");
     if (!(mesh->hi[m] > mesh->lo[m])) return bad("hi must exceed lo");
@@ -1488,6 +1512,7 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
       return fail(nullptr, HBPC_ERR_UNSUPPORTED, "BJ_ext block n_var (N+1)^dim exceeds the supported size");
   }
   if (so->precision != HBPC_PREC_FP64 && so->precision != HBPC_PREC_MIXED) return bad("unknown precision");
+  if (!(so->t_end >= 0.0) || !std::isfinite(so->t_end)) return bad("t_end must be finite and >= 0");
   return HBPC_OK;
 }
 
@@ -2178,6 +2203,47 @@ hbpc_status hbpc_step(hbpc_ctx* ctx, int n_steps) {
   return HBPC_OK;
 }
 
+hbpc_status hbpc_advance_to(hbpc_ctx* ctx, double t_end) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  if (!std::isfinite(t_end)) return fail(ctx, HBPC_ERR_INVALID_ARG, "t_end must be finite");
+  const double dt = ctx->sol.dt, t0 = ctx->stats.t;
+  const double tol = 1e-10 * dt;
+  const double span = t_end - t0;
+  if (span < -tol) return fail(ctx, HBPC_ERR_INVALID_ARG, "t_end lies before the current time");
+  // whole steps, then the remainder (if more than rounding of t) as one last step
+  long long whole = span > 0.0 ? (long long)std::floor(span / dt) : 0;
+  double rem = span - double(whole) * dt;
+  if (rem > dt - tol) { whole += 1; rem = 0.0; }
+  if (rem < tol) rem = 0.0;
+  for (long long i = 0; i < whole; ++i) {
+    hbpc_status s = hbpc_one_step(ctx);
+    if (s != HBPC_OK) return s;
+    ctx->stats.steps += 1;
+    ctx->stats.t = t0 + double(i + 1) * dt;
+  }
+  if (rem > 0.0) {
+    ctx->sol.dt = rem;
+    hbpc_status s = hbpc_one_step(ctx);
+    ctx->sol.dt = dt;
+    if (s != HBPC_OK) return s;
+    ctx->stats.steps += 1;
+  }
+  ctx->stats.t = t_end;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_run(hbpc_ctx* ctx) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  if (!(ctx->sol.t_end > 0.0)) return fail(ctx, HBPC_ERR_INVALID_ARG, "the solver has no final time t_end");
+  return hbpc_advance_to(ctx, ctx->sol.t_end);
+}
+
+hbpc_status hbpc_set_wait_limit(hbpc_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds >= 0.0) || !std::isfinite(seconds)) return HBPC_ERR_INVALID_ARG;
+  ctx->wait_limit_s = seconds;
+  return HBPC_OK;
+}
+
 hbpc_status hbpc_eval_R1(hbpc_ctx* ctx, const double* w, double* r) {
   if (!ctx || !w || !r) return HBPC_ERR_INVALID_ARG;
   ctx->ops.r1(ctx->prm, w, r, ctx->stream);
@@ -2542,6 +2608,16 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   if (x.ndof > kNoAllocMaxDof)
     return fail(nullptr, HBPC_ERR_INVALID_ARG,
                 "n_dof exceeds the allocation-free limit of 262144 values; use hbpc_eval_Jv");
+  {
+    // out is written while X and dX are still being read: no overlap allowed
+    const uintptr_t len = uintptr_t(2 * x.ndof) * sizeof(double);
+    auto overlaps = [&](const void* a, const void* b) {
+      const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+      return pa < pb + len && pb < pa + len;
+    };
+    if (overlaps(out, X) || overlaps(out, dX))
+      return fail(nullptr, HBPC_ERR_INVALID_ARG, "out overlaps X or dX; pass a separate output array");
+  }
   if (!basis_1d(N, nodes, x.basis)) return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis");
   if (!get_ops(phys->law, x.dim, x.P, nodes == HBPC_NODES_LOBATTO, x.ops))
     return fail(nullptr, HBPC_ERR_UNSUPPORTED, "this (law, dim, N, node family) is not compiled in");
@@ -2564,8 +2640,12 @@ hbpc_status hbpc_eval_Jv_noalloc(const hbpc_mesh* mesh, int N, int nodes, const 
   double* c12 = scr + kNoAllocC12;
   double* nrm = scr + kNoAllocNrm;
   const double c1 = alpha1 * dt, c2 = alpha2 * dt * dt / 2.0;
+  // after the first enqueue an error still waits for the stream, so that no
+  // work of a failed call is left running on the shared array
   auto ck = [&](cudaError_t e, const char* what) -> hbpc_status {
-    return e == cudaSuccess ? HBPC_OK : cuda_fail(nullptr, e, what);
+    if (e == cudaSuccess) return HBPC_OK;
+    cudaStreamSynchronize(stream);
+    return cuda_fail(nullptr, e, what);
   };
   // the shared array keeps the previous call's contents: the ticket must start at 0
   if ((st = ck(cudaMemsetAsync(K.ticket, 0, sizeof(unsigned), stream), "clear ticket")) != HBPC_OK) return st;

@@ -37,7 +37,13 @@ STATUS_NAMES = {0: "HBPC_OK", 1: "HBPC_ERR_INVALID_ARG", 2: "HBPC_ERR_OOM", 3: "
 
 class Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int)]
+
+
+def _mesh(dim, n, lo, hi, periodic=1):
+    pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
+    return Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
+                (ctypes.c_double * 3)(*pad(hi, 1.0)), periodic)
 
 
 class Physics(ctypes.Structure):
@@ -51,7 +57,7 @@ class Solver(ctypes.Structure):
                 ("tol_newton_rel", ctypes.c_double), ("tol_newton_abs", ctypes.c_double),
                 ("tol_gmres_rel", ctypes.c_double), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iter", ctypes.c_int), ("newton_max_iter", ctypes.c_int),
-                ("pc", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("pc", ctypes.c_int), ("precision", ctypes.c_int), ("t_end", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -85,6 +91,9 @@ _SIGS = {
     "hbpc_get_state": (_I, [_CTX, _P, _I]),
     "hbpc_set_time": (_I, [_CTX, _D]),
     "hbpc_step": (_I, [_CTX, _I]),
+    "hbpc_advance_to": (_I, [_CTX, _D]),
+    "hbpc_run": (_I, [_CTX]),
+    "hbpc_set_wait_limit": (_I, [_CTX, _D]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -170,13 +179,12 @@ def fp64_fma_peak():
 
 def eval_Jv_noalloc(dim, n, lo, hi, N, dt, alpha1, alpha2, X, dX, out, law=LAW_ADVECTION,
                     flux=FLUX_GLOBAL_LF, a=(1.0, 1.0, 1.0), gamma=1.4, eps=1.0, lf_scale=1.0,
-                    nodes=NODES_LOBATTO, stream=None):
+                    nodes=NODES_LOBATTO, stream=None, nu=0.0):
     """Jacobian-vector product of one stage system without a context and without
     any device allocation (hbpc_eval_Jv_noalloc; n_dof <= 262144)."""
     pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
-    mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
-                (ctypes.c_double * 3)(*pad(hi, 1.0)))
-    phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale)
+    mesh = _mesh(dim, n, lo, hi)
+    phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale, nu)
     _check(_lib.hbpc_eval_Jv_noalloc(ctypes.byref(mesh), N, nodes, ctypes.byref(phys), dt, alpha1,
                                      alpha2, _ptr(X), _ptr(dX), _ptr(out), stream))
     return out
@@ -200,15 +208,15 @@ class Context:
                  nodes=NODES_LOBATTO, mu=None, prandtl=0.72,
                  q=4, kmax=0, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=0.0,
                  tol_gmres_rel=1e-5, gmres_restart=100, gmres_max_iter=7000,
-                 newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64, stream=None):
+                 newton_max_iter=50, pc=PC_NONE, precision=PREC_FP64, stream=None, t_end=0.0,
+                 periodic=1):
         pad = lambda v, fill: (list(v) + [fill] * 3)[:3]
-        self.mesh = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
-                         (ctypes.c_double * 3)(*pad(hi, 1.0)))
+        self.mesh = _mesh(dim, n, lo, hi, periodic)
         # the Navier-Stokes law takes its dynamic viscosity mu in the nu field
         self.phys = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
                             nu if mu is None else mu, eta_br2, prandtl)
         self.solver = Solver(q, kmax, dt, tol_newton_rel, tol_newton_abs, tol_gmres_rel,
-                             gmres_restart, gmres_max_iter, newton_max_iter, pc, precision)
+                             gmres_restart, gmres_max_iter, newton_max_iter, pc, precision, t_end)
         self.N, self.dim, self.nodes = N, dim, nodes
         self._ctx = _CTX()
         _check(_lib.hbpc_create(ctypes.byref(self._ctx), ctypes.byref(self.mesh), N, nodes,
@@ -267,6 +275,15 @@ class Context:
 
     def step(self, n=1):
         self._c(_lib.hbpc_step(self._ctx, n))
+
+    def advance_to(self, t_end):
+        self._c(_lib.hbpc_advance_to(self._ctx, t_end))
+
+    def run(self):
+        self._c(_lib.hbpc_run(self._ctx))
+
+    def set_wait_limit(self, seconds):
+        self._c(_lib.hbpc_set_wait_limit(self._ctx, seconds))
 
     def eval_R1(self, w, out):
         self._c(_lib.hbpc_eval_R1(self._ctx, _ptr(w), _ptr(out)))
@@ -381,8 +398,7 @@ class Batch:
         self.M = (Mesh * k)()
         self.Ph = (Physics * k)()
         for i, (n, lo, hi) in enumerate(meshes):
-            self.M[i] = Mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
-                             (ctypes.c_double * 3)(*pad(hi, 1.0)))
+            self.M[i] = _mesh(dim, n, lo, hi)
             self.Ph[i] = Physics(law, flux, (ctypes.c_double * 3)(*pad(a, 0.0)), gamma, eps, lf_scale,
                                  float(nus[i]), eta_br2, 0.72)
         self.Nv = (ctypes.c_int * k)(*Ns)

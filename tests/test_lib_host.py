@@ -97,3 +97,70 @@ def test_batch_invalid_arguments_rejected(hbpc):
     with pytest.raises(hbpc.HBPCError) as ei:          # Navier-Stokes batches
         hbpc.Batch(2, meshes, [3, 4], nus=[0.01, 0.02], law=hbpc.LAW_NAVIER_STOKES)
     assert ei.value.status == 7
+
+
+def test_non_periodic_mesh_is_unsupported(hbpc):
+    """Only periodic meshes are implemented: periodic = 0 is
+    HBPC_ERR_UNSUPPORTED and any other value HBPC_ERR_INVALID_ARG, both before
+    the device is touched."""
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(2, (2, 2), (0, 0), (1, 1), 3, periodic=0)
+    assert ei.value.status == 7
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(2, (2, 2), (0, 0), (1, 1), 3, periodic=2)
+    assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("t_end", [-1.0, float("nan"), float("inf")])
+def test_invalid_final_time_rejected(hbpc, t_end):
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(2, (2, 2), (0, 0), (1, 1), 3, t_end=t_end)
+    assert ei.value.status == 1
+
+
+def test_noalloc_rejects_overlapping_output(hbpc):
+    """The allocation-free Jv reads X and dX while it writes out: an out that
+    overlaps either is rejected before anything is launched (addresses only;
+    no device memory is touched)."""
+    import ctypes
+
+    class FakeTensor:    # a device pointer the check compares but never dereferences
+        def __init__(self, addr):
+            self.addr = addr
+
+        def is_contiguous(self):
+            return True
+
+        dtype = "torch.float64"
+
+        def data_ptr(self):
+            return self.addr
+
+    n2 = 2 * 4 * 4 * 16         # 2 n_dof of a 4 x 4 mesh at N = 3
+    base = 1 << 40
+    X, dX = FakeTensor(base), FakeTensor(base + 8 * n2)
+    for out in (FakeTensor(base), FakeTensor(base + 8 * n2 + 8), FakeTensor(base + 8 * (n2 - 1))):
+        with pytest.raises(hbpc.HBPCError) as ei:
+            hbpc.eval_Jv_noalloc(2, (4, 4), (0, 0), (1, 1), 3, 0.01, 0.5, 0.1, X, dX, out)
+        assert ei.value.status == 1
+        assert "overlap" in str(ei.value)
+    assert ctypes.sizeof(hbpc.Mesh) == 4 + 12 + 48 + 4 + 4    # periodic field, padded to 8
+
+
+def test_noalloc_rejects_viscous_law_on_the_host(hbpc):
+    class FakeTensor:
+        dtype = "torch.float64"
+
+        def __init__(self, addr):
+            self.addr = addr
+
+        def is_contiguous(self):
+            return True
+
+        def data_ptr(self):
+            return self.addr
+
+    X, dX, out = FakeTensor(1 << 40), FakeTensor(1 << 41), FakeTensor(1 << 42)
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.eval_Jv_noalloc(2, (4, 4), (0, 0), (1, 1), 3, 0.01, 0.5, 0.1, X, dX, out, nu=0.01)
+    assert ei.value.status == 7

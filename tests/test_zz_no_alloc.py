@@ -72,3 +72,46 @@ def test_noalloc_rejects_oversized_problem(hb):
         hb.eval_Jv_noalloc(2, (128, 128), (0, 0), (1, 1), 5, 0.01, 1.0, 1.0, X, X, X)
     assert ei.value.status == hb.ERR_INVALID_ARG
     assert "262144" in str(ei.value)
+
+
+def test_noalloc_jv_on_a_side_stream(hb):
+    """Work enqueued on a caller's (non-default) stream: the same product as
+    the context-based entry point, twice in a row."""
+    dim, n, N, lo, hi = 2, (5, 6), 4, (0.0, 0.0), (1.0, 1.0)
+    dt, a1, a2 = 0.02, 1.0, 1.0
+    ctx = hb.Context(dim, n, lo, hi, N, law=hb.LAW_EULER, flux=hb.FLUX_RUSANOV, eps=0.8, dt=dt)
+    from paper_2109_04804_gb300 import inputs
+    rng = np.random.default_rng(77)
+    W = inputs.density_wave(ctx.node_coords()) * (1.0 + 0.02 * rng.standard_normal(ctx.shape))
+    side = torch.cuda.Stream()
+    for call in range(2):
+        S = 0.1 * rng.standard_normal(ctx.shape)
+        X = torch.from_numpy(np.concatenate([W.ravel(), S.ravel()])).cuda()
+        dX = torch.from_numpy(rng.standard_normal(2 * ctx.ndof)).cuda()
+        ref = torch.empty_like(X)
+        ctx.eval_Jv(a1, a2, X, dX, ref)
+        out = torch.full_like(X, float("nan"))
+        torch.cuda.synchronize()
+        hb.eval_Jv_noalloc(dim, n, lo, hi, N, dt, a1, a2, X, dX, out, law=hb.LAW_EULER,
+                           flux=hb.FLUX_RUSANOV, eps=0.8, stream=side.cuda_stream)
+        assert rel(out, ref) <= 1e-6, (call, rel(out, ref))
+    ctx.close()
+
+
+def test_noalloc_rejects_aliased_output_and_viscous_law(hb):
+    """out == dX or out == X is rejected (the kernels read both while writing
+    out) and leaves the inputs untouched; a viscous law is unsupported."""
+    n, N = (4, 4), 3
+    ndof = 16 * 16
+    X = torch.randn(2 * ndof, dtype=torch.float64, device="cuda")
+    dX = torch.randn(2 * ndof, dtype=torch.float64, device="cuda")
+    X0, dX0 = X.clone(), dX.clone()
+    for out in (dX, X, X[1:]):
+        with pytest.raises(hb.HBPCError) as ei:
+            hb.eval_Jv_noalloc(2, n, (0, 0), (1, 1), N, 0.01, 0.5, 0.1, X, dX, out)
+        assert ei.value.status == hb.ERR_INVALID_ARG
+    assert torch.equal(X, X0) and torch.equal(dX, dX0)
+    out = torch.empty_like(X)
+    with pytest.raises(hb.HBPCError) as ei:
+        hb.eval_Jv_noalloc(2, n, (0, 0), (1, 1), N, 0.01, 0.5, 0.1, X, dX, out, nu=0.01)
+    assert ei.value.status == hb.ERR_UNSUPPORTED

@@ -2,30 +2,41 @@
 
 Workload (default): 2-D linear advection u_t + div((1, 1) u) = 0 on the periodic
 unit square, 64 x 64 elements, N = 5 (Gauss-Lobatto), u0 = sin(2 pi x) sin(2 pi y),
-HBPC(8, 4) (the highest order of the paper), CFL 8 -> dt = 1/96, matrix-free
-Newton-GMRES with the paper's BJ_ext preconditioner, eps_Newton = 1e-12 with
-the absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5, mixed precision (FP64
-Newton residual, update and state; FP32 Krylov loop).  One bench step = one
-HBPC time step (15 implicit stage solves).  Metric: DOF-timesteps/s = n_dof x
-steps / device seconds.  The same line carries, under "learned_vs_plain", the
-metric's comparison on the Euler vortex workload (learned block preconditioner
-trained on the GPU from the run's own Newton-GMRES data vs plain GMRES and
-BJ_ext; --no-vortex skips it).
+HBPC(8, 4) (the highest order of the paper), CFL 8 -> dt = 1/96, FP64, matrix-free
+Newton-GMRES with the paper's BJ_ext preconditioner, eps_Newton = 1e-12 with the
+absolute test ||dW|| <= 1e-12, eps_GMRES = 1e-5.  One bench step = one HBPC time
+step (15 implicit stage solves).  Metric: DOF-timesteps/s = n_dof x steps /
+device seconds, with every result's distance to the FP64 oracle.
 
-  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
-  python bench.py --workload burgers_batch   (256 viscous Burgers instances, below)
-  python bench.py --workload euler_vortex    (learned vs BJ_ext vs plain GMRES, below)
+The same line carries (N = 1):
+  mixed_precision   the same workload with the FP32 Krylov loop (FP64 Newton
+                    residual, update and state), its error against the oracle
+  r1_roofline       the operator pass on the Euler vortex (128^2, N = 4) and
+                    Taylor-Green (32^3, N = 5) meshes: FP64 R1 against the FP64
+                    ALU and HBM roofs, the FP32 Jacobian-vector pass against HBM
+  learned_vs_plain  the metric's comparison on the Euler vortex: learned block
+                    preconditioner (trained on the GPU from the run's own
+                    Newton-GMRES data) vs plain GMRES vs BJ_ext, every arm's
+                    answer against the FP64 GPU result and the FP64 oracle
+  cpu_baseline      the FP64 oracle on the host cores: whole HBPC(8,4) steps on
+                    a 16 x 16 mesh at the same CFL, 1 BLAS thread and all
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--precision fp64|mixed]
+  python bench.py --workload burgers_batch   (256 viscous Burgers instances)
+  python bench.py --workload euler_vortex    (learned vs BJ_ext vs plain GMRES)
+  python bench.py --workload taylor_green    (3-D Navier-Stokes, 32^3, N = 5)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path has no data-path collective), value = sum over ranks / max time.
-The reference arm (--impl reference) times the FP64 CPU oracle on the host on
-a bounded sample of the same workload.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host:
+whole HBPC(8,4) steps of the same configuration on a 16 x 16 mesh.
 """
 import argparse
 import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -35,35 +46,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF-timesteps/s per HBPC step at fixed L2 error; learned vs plain GMRES"
-PRECISION = ["mixed"]   # set from --precision
 UNIT = "DOF-timesteps/s"
 
 WL = dict(dim=2, n=(64, 64), lo=(0.0, 0.0), hi=(1.0, 1.0), N=5, a=(1.0, 1.0), q=8, kmax=4,
           cfl=8.0, t_end=1.0, tol_newton_rel=1e-12, tol_newton_abs=1e-12, tol_gmres_rel=1e-5,
           gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50)
+SAMPLE_N = (16, 16)     # the oracle's sample: same CFL, whole HBPC steps
 
 
-def workload_dt():
-    # dt_raw = CFL / sum_m(|a_m| p / h_m), rounded to T_end / ceil(T_end / dt_raw)
+def workload_dt(n=None):
+    """dt_raw = CFL / sum_m(|a_m| p / h_m), rounded to T_end / ceil(T_end / dt_raw)."""
+    n = n or WL["n"]
     p = WL["N"] + 1
-    s = sum(abs(WL["a"][m]) * p / ((WL["hi"][m] - WL["lo"][m]) / WL["n"][m]) for m in range(WL["dim"]))
+    s = sum(abs(WL["a"][m]) * p / ((WL["hi"][m] - WL["lo"][m]) / n[m]) for m in range(WL["dim"]))
     raw = WL["cfl"] / s
     return WL["t_end"] / np.ceil(WL["t_end"] / raw - 1e-12)
 
 
-def config_dict(dt, extra=None):
-    c = {"workload": "2d_linear_advection_64x64_N5_HBPC(8,4)_CFL8_BJext_GMRES",
-         "precision": PRECISION[0],
-         "mesh": "64x64 periodic [0,1]^2", "N": 5, "nodes": "Gauss-Lobatto", "hbpc": "q=8,kmax=4",
-         "dt": dt, "eps_newton": WL["tol_newton_rel"], "newton_abs_dW": WL["tol_newton_abs"],
-         "eps_gmres": WL["tol_gmres_rel"],
-         "gmres_restart": WL["gmres_restart"], "preconditioner": "BJ_ext (Sec. 3.2.3)",
-         "l2_between_steps": "flushed (256 MB write) between timed steps",
-         "launches": ("Arnoldi steps in batches of 4 replayed as one CUDA graph each"
-                      if os.environ.get("HBPC_GRAPH", "1") != "0" else "one launch per kernel (HBPC_GRAPH=0)")}
-    if extra:
-        c.update(extra)
-    return c
+def config_dict(dt, precision):
+    return {"workload": "2d_linear_advection_64x64_N5_HBPC(8,4)_CFL8_BJext_GMRES_%s" % precision,
+            "precision": precision,
+            "mesh": "64x64 periodic [0,1]^2", "N": 5, "nodes": "Gauss-Lobatto", "hbpc": "q=8,kmax=4",
+            "dt": dt, "eps_newton": WL["tol_newton_rel"], "newton_abs_dW": WL["tol_newton_abs"],
+            "eps_gmres": WL["tol_gmres_rel"], "gmres_restart": WL["gmres_restart"],
+            "preconditioner": "BJ_ext (Sec. 3.2.3)",
+            "l2_between_steps": "flushed (256 MB write) between timed steps"}
 
 
 class Clocks:
@@ -134,8 +141,19 @@ def exact_solution(coords, t):
     return inputs.sine_product(sh)
 
 
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
 # -- algorithmic work per launch (bytes, flops per W-DOF) ----------------------
-def jv_work_per_dof(mixed=False):
+def jv_work_per_dof(mixed):
     """Linear Jv (Eq. 24): reads dW, dS and writes the two outputs: 32 B per
     W-DOF in FP64 (16 B in FP32).  Flops: two R1 passes, each 2*d*p (volume)
     + 2*d/p face points x 7 (flux 5, lifting 2), plus 3 FMAs to combine."""
@@ -144,7 +162,7 @@ def jv_work_per_dof(mixed=False):
     return (16.0 if mixed else 32.0), 2 * r1 + 6
 
 
-def pc_work_per_dof(mixed=False):
+def pc_work_per_dof(mixed):
     """BJ_ext apply on this workload: linear advection on one uniform mesh has
     the same J_i (hence M_i) in every element, so the library builds one block
     pair and the apply reads only the two input halves and writes the two
@@ -155,12 +173,547 @@ def pc_work_per_dof(mixed=False):
     return (16.0 if mixed else 32.0), 8.0 * nb + 4.0
 
 
-# DRAM bytes (read + write) per launch measured by ncu on this workload's
-# kernels (summaries in profiles/: k_cgs_coop_c2_advection_64x64_N5.md, the mean
-# of three captured columns; dg_operator_jv_pair_c2_advection_64x64_N5.md).
-# A kernel changed after its capture must have its entry set to None (the
-# shared-block apply has not been captured).
-NCU_TRAFFIC = {"cgs2": 3.68e6, "pc_apply": None, "jv": 1.20e6}
+def cgs_work_per_dof(mixed, cavg):
+    """CGS2 column (one launch per Arnoldi iteration) at the mean column count
+    cavg = j + 1: the three passes read the new vector and the j + 1 basis
+    vectors and write the new vector twice, (3 cavg + 5) vectors of 2 values
+    per W-DOF; 6 cavg + 8 flops per value."""
+    vb = 4.0 if mixed else 8.0
+    return (3.0 * cavg + 5.0) * 2.0 * vb, (6.0 * cavg + 8.0) * 2.0
+
+
+# DRAM bytes (read + write) per launch measured by ncu for the kernels of this
+# workload (summaries in profiles/, one per kernel and precision).  An entry is
+# None until its kernel, as committed, has been captured.
+NCU_TRAFFIC = {
+    "mixed": {"cgs2": None, "pc_apply": None, "jv": None},
+    "fp64": {"cgs2": None, "pc_apply": None, "jv": None},
+}
+
+KERNEL_NAMES = {
+    "jv": "dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)",
+    "pc_apply": "k_pc_apply_shared<%s, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements)",
+    "cgs2": "k_cgs_coop<%s> (Arnoldi CGS2 column, one cooperative launch; mean j + 1 = %.1f)",
+}
+
+
+def c2_context(hbpc, n, precision, stream):
+    dt = workload_dt(n)
+    return hbpc.Context(WL["dim"], n, WL["lo"], WL["hi"], WL["N"], law=hbpc.LAW_ADVECTION,
+                        a=WL["a"], q=WL["q"], kmax=WL["kmax"], dt=dt,
+                        tol_newton_rel=WL["tol_newton_rel"], tol_newton_abs=WL["tol_newton_abs"],
+                        tol_gmres_rel=WL["tol_gmres_rel"], gmres_restart=WL["gmres_restart"],
+                        gmres_max_iter=WL["gmres_max_iter"], newton_max_iter=WL["newton_max_iter"],
+                        pc=hbpc.PC_BJEXT, stream=stream.cuda_stream if stream is not None else None,
+                        precision=hbpc.PREC_MIXED if precision == "mixed" else hbpc.PREC_FP64, t_end=WL["t_end"])
+
+
+def timed_steps(torch, ctx, stream, steps, flush):
+    """`steps` HBPC steps, each timed with CUDA events on the context's stream
+    after an L2 flush outside the timed window; returns the summed ms."""
+    total = 0.0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total
+
+
+def c2_roofline(hbpc, ctx, precision, stats0, fp64_peak_gf, hbm):
+    """One more step with per-launch CUDA events (a separate, profiled step):
+    per phase device time; the roofline entry of every measured kernel and of
+    the dominant one."""
+    ctx.profile(True)
+    ctx.step(1)
+    prof = ctx.profile_get()
+    pstats = ctx.stats()
+    ctx.profile(False)
+    mixed = precision == "mixed"
+    ndof = ctx.ndof
+    its_p = pstats["gmres_its"] - stats0["gmres_its"]
+    cols_p = pstats["arnoldi_cols"] - stats0["arnoldi_cols"]
+    cavg = cols_p / max(1, its_p)
+    tname = "float" if mixed else "double"
+    kernels = {"jv": (KERNEL_NAMES["jv"] % tname, jv_work_per_dof(mixed), prof["jv"]),
+               "pc_apply": (KERNEL_NAMES["pc_apply"] % tname, pc_work_per_dof(mixed), prof["pc_apply"]),
+               "cgs2": (KERNEL_NAMES["cgs2"] % (tname, cavg), cgs_work_per_dof(mixed, cavg),
+                        (prof["arnoldi_dot"][0] + prof["arnoldi_update"][0], its_p))}
+    step_ms = sum(v[0] for v in prof.values())
+    entries = {}
+    for ph, (name, (bpd, fpd), (ms, n)) in kernels.items():
+        if n == 0:
+            continue
+        avg = ms / 1000.0 / n
+        gf = fpd * ndof / avg / 1e9
+        gb = bpd * ndof / avg / 1e9
+        e = {"kernel": name, "algorithmic_bytes_per_launch": round(bpd * ndof),
+             "algorithmic_flops_per_launch": round(fpd * ndof),
+             "traffic": NCU_TRAFFIC[precision].get(ph), "avg_launch_us": round(avg * 1e6, 2),
+             "launches_profiled": n, "share_of_step": round(ms / step_ms, 3)}
+        if mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are bound by memory
+            e.update({"bound": "hbm", "achieved": round(gb, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(gb / hbm, 4), "alu_tflops": round(gf / 1000.0, 3)})
+        else:       # GB300's FP64 pipe (1/64 of FP32) binds these
+            e.update({"bound": "alu", "achieved": round(gf / 1000.0, 4), "peak": round(fp64_peak_gf / 1000.0, 4),
+                      "unit": "TFLOP/s", "frac": round(gf / fp64_peak_gf, 4), "hbm_achieved_gbs": round(gb, 1),
+                      "hbm_frac_of_measured": round(gb / hbm, 4)})
+        entries[ph] = e
+    dom = max(entries, key=lambda k: kernels[k][2][0])
+    roof = dict(entries[dom])
+    roof["peak_source"] = ("measured HBM copy bandwidth (MEASURED_PEAKS.json)" if mixed else
+                           "FP64 FMA throughput measured in this run (hbpc_fp64_fma_peak), "
+                           "nominal 1.25 TFLOP/s")
+    roof["phase_ms_one_step"] = {k: round(v[0], 3) for k, v in prof.items()}
+    roof["phase_launches_one_step"] = {k: v[1] for k, v in prof.items()}
+    roof["other_kernels"] = {k: v for k, v in entries.items() if k != dom}
+    return roof
+
+
+def run_c2_arm(torch, hbpc, inputs, precision, args, stream, flush, fp64_peak_gf, hbm, world, headline):
+    """W warm-up steps, the launch-shape autotuner, K timed steps (CUDA events
+    on the context's stream, L2 flushed between steps), one profiled step for
+    the roofline; on the headline arm also the clocks during the timed region
+    and the end-to-end run through host buffers."""
+    dt = workload_dt()
+    ctx = c2_context(hbpc, WL["n"], precision, stream)
+    coords = ctx.node_coords()
+    w0 = inputs.sine_product(coords)
+    ctx.set_state(w0)
+    ndof = ctx.ndof
+    for _ in range(args.warmup):
+        ctx.step(1)
+    tuning = ctx.autotune()        # launch shapes of the Krylov reductions and the PC apply
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    clocks = Clocks(dist_env()[2]) if headline else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    total_ms = timed_steps(torch, ctx, stream, args.steps, flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    stats = ctx.stats()
+    t_sec = total_ms / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_sec], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sec = float(tt.item())
+        torch.distributed.barrier()
+    roof = c2_roofline(hbpc, ctx, precision, stats, fp64_peak_gf, hbm)
+    n_steps = args.warmup + args.steps + 1
+    w_fin = ctx.get_state()
+    err = float(np.sqrt(np.mean((w_fin - exact_solution(coords, n_steps * dt)) ** 2)))
+    res = {"value": ndof * args.steps * world / t_sec, "ms_per_step": 1000.0 * t_sec / args.steps,
+           "steps_total": n_steps, "gmres_its_per_step": stats["gmres_its"] / args.steps,
+           "newton_its_per_step": stats["newton_its"] / args.steps,
+           "r1_evals_per_s": (stats["r1_evals"] + stats["r2_evals"]) / t_sec,
+           "gpu_launches": int(stats["launches"]), "l2_error_vs_exact": err, "roofline": roof,
+           "autotuned": tuning, "clocks": clk, "ndof": ndof, "w_final": w_fin}
+    if headline:
+        # e2e: the public API with pinned host buffers, copies inside the timed
+        # region, the L2 flush outside it (as in the device-timed loop)
+        host_in = torch.from_numpy(w0.copy()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_state_host_ptr(host_in.data_ptr())
+            ctx.step(1)
+            ctx.get_state_host_ptr(host_out.data_ptr())
+            e2e_s += time.perf_counter() - t0
+        res["e2e"] = {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
+    ctx.close()
+    return res
+
+
+def c2_sample_steps(torch, hbpc, inputs):
+    """One HBPC(8,4) step of the oracle's sample (16 x 16 elements, same CFL)
+    from u0 in both precisions, for the comparison with the oracle's step."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        c = c2_context(hbpc, SAMPLE_N, prec, None)
+        c.set_state(inputs.sine_product(c.node_coords()))
+        c.step(1)
+        out[prec] = c.get_state()
+        c.close()
+    return out
+
+
+def r1_roofline(torch, hbpc, inputs, flush, fp64_peak_gf, hbm, launches=8):
+    """The operator pass at the two large meshes: FP64 R1 (hbpc_eval_R1;
+    16 B per W-DOF, FP64-ALU bound on GB300) and the FP32 Jacobian-vector pass
+    of the mixed Krylov loop (hbpc_eval_Jv of a mixed context: reads the FP32
+    state and direction, writes the product: 24 B per W-DOF).  Every launch
+    after an L2 flush, CUDA events (R1) or the library's per-launch events (Jv).
+    Flops counted for the ALU fraction: the tensor-product contractions alone,
+    2 d p per W-DOF for the flux divergence and, for Navier-Stokes, 2 p d (d+1)
+    per node for the gradients of (v, T): a lower bound of the work, so the
+    fraction is a lower bound too."""
+    L = 2.0 * np.pi
+    cases = [("euler_vortex_128x128_N4", dict(dim=2, n=(128, 128), lo=(-10, -10), hi=(10, 10), N=4,
+                                              law=hbpc.LAW_EULER, flux=hbpc.FLUX_RUSANOV), "vortex"),
+             ("taylor_green_32x32x32_N5", dict(dim=3, n=(32, 32, 32), lo=(0, 0, 0), hi=(L, L, L), N=5,
+                                               law=hbpc.LAW_NAVIER_STOKES, flux=hbpc.FLUX_RUSANOV,
+                                               mu=1.0 / 1600.0, eps=0.1, prandtl=0.72), "tgv")]
+    out = {}
+    for name, kw, ic in cases:
+        d, p = kw["dim"], kw["N"] + 1
+        nv = d + 2
+        flops = 2.0 * d * p + (2.0 * p * d * (d + 1) / nv if kw["law"] == hbpc.LAW_NAVIER_STOKES else 0.0)
+        entry = {}
+        for prec in ("fp64", "mixed"):
+            ctx = hbpc.Context(kw["dim"], kw["n"], kw["lo"], kw["hi"], kw["N"], law=kw["law"], flux=kw["flux"],
+                               mu=kw.get("mu"), eps=kw.get("eps", 1.0), prandtl=kw.get("prandtl", 0.72),
+                               dt=0.01, gmres_restart=2, pc=hbpc.PC_NONE,
+                               precision=hbpc.PREC_FP64 if prec == "fp64" else hbpc.PREC_MIXED)
+            co = ctx.node_coords()
+            w = inputs.isentropic_vortex(co) if ic == "vortex" else inputs.taylor_green(co, eps=0.1)
+            wd = torch.from_numpy(w).cuda()
+            o = torch.empty_like(wd)
+            ndof = ctx.ndof
+            if prec == "fp64":
+                for _ in range(2):
+                    ctx.eval_R1(wd, o)
+                ms = []
+                for _ in range(launches):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    ctx.eval_R1(wd, o)
+                    e1.record()
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                avg = float(np.mean(ms)) / 1000.0
+                gf = flops * ndof / avg / 1e9
+                gb = 16.0 * ndof / avg / 1e9
+                entry["fp64_r1"] = {"kernel": "dg_operator_kernel<JobR1<double>>", "bound": "alu",
+                                    "avg_launch_us": round(avg * 1e6, 1), "launches": launches, "ndof": ndof,
+                                    "r1_evals_per_s": round(1.0 / avg, 1),
+                                    "alu_tflops_contractions_only": round(gf / 1000.0, 4),
+                                    "alu_frac_lower_bound": round(gf / fp64_peak_gf, 4),
+                                    "fp64_peak_tflops": round(fp64_peak_gf / 1000.0, 4),
+                                    "hbm_achieved_gbs": round(gb, 1), "hbm_frac": round(gb / hbm, 4),
+                                    "algorithmic_bytes_per_launch": 16 * ndof,
+                                    "flops_counted_per_dof": round(flops, 2)}
+            else:
+                ctx.eval_R1(wd, o)
+                X = torch.cat([wd, o])
+                gen = torch.Generator(device="cuda")
+                gen.manual_seed(5)
+                dX = torch.randn(2 * ndof, dtype=torch.float64, device="cuda", generator=gen)
+                out2 = torch.empty_like(X)
+                ctx.eval_Jv(0.5, 1.0 / 6.0, X, dX, out2)
+                ctx.profile(True)
+                for _ in range(launches):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    ctx.eval_Jv(0.5, 1.0 / 6.0, X, dX, out2)
+                ms, n = ctx.profile_get()["jv"]
+                ctx.profile(False)
+                avg = ms / 1000.0 / max(1, n)
+                gb = 24.0 * ndof / avg / 1e9
+                entry["fp32_jv_mixed"] = {"kernel": "dg_operator_kernel<JobJvMixed<float>> (dual numbers)",
+                                          "bound": "hbm", "avg_launch_us": round(avg * 1e6, 1), "launches": n,
+                                          "ndof": ndof, "achieved": round(gb, 1), "peak": hbm, "unit": "GB/s",
+                                          "frac": round(gb / hbm, 4),
+                                          "algorithmic_bytes_per_launch": 24 * ndof}
+                del X, dX, out2
+            del wd, o
+            ctx.close()
+            torch.cuda.empty_cache()
+        out[name] = entry
+    return out
+
+
+# -- the oracle on the host cores (cpu_baseline leg and reference arm) ---------
+def host_cpu():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def oracle_task(name, outdir, steps):
+    """Run in a child process (bench.py --oracle-task): the FP64 oracle as it
+    stands.  c2_sample: whole HBPC(8,4) steps of the 2-D advection workload on
+    the 16 x 16 sample at CFL 8, timed; c2_exact: the exact per-Fourier-mode
+    HBPC(8,4) result at full size after `steps` steps (what the Newton-GMRES
+    iteration converges to); vortex_sample: one HBPC(6,2) step of the Euler
+    vortex on a 16 x 16 mesh at CFL 10.  Prints one JSON line; states go to
+    outdir/<name>.npy."""
+    from oracle import dgsem, exact, hbpc as ohbpc, laws, newton
+    from paper_2109_04804_gb300 import inputs
+    res = {"task": name}
+    if name in ("c2_sample", "c2_exact"):
+        ph = laws.Physics(laws.ADVECTION, 2, a=WL["a"])
+        n = SAMPLE_N if name == "c2_sample" else WL["n"]
+        disc = dgsem.Disc(dgsem.Mesh(2, n, WL["lo"], WL["hi"]), WL["N"], ph)
+        w = inputs.sine_product(disc.node_coords())
+        dt = workload_dt(n)
+        if name == "c2_exact":
+            w = exact.fourier_hbpc(disc, w, dt, WL["q"], WL["kmax"], steps)
+        else:
+            opts = newton.NewtonOptions(tol_rel=WL["tol_newton_rel"], tol_abs=WL["tol_newton_abs"],
+                                        gmres_tol=WL["tol_gmres_rel"], restart=WL["gmres_restart"],
+                                        gmres_maxiter=WL["gmres_max_iter"], newton_max=WL["newton_max_iter"],
+                                        jv="linear", pc="bjext")
+            st = newton.Stats()
+            adv = ohbpc.dg_stepper(disc, dt, WL["q"], WL["kmax"], opts, stats=st)
+            times = []
+            for _ in range(steps):
+                t0 = time.perf_counter()
+                w = adv(w)
+                times.append(time.perf_counter() - t0)
+            res.update({"seconds": times, "ndof": disc.ndof, "gmres_its": st.gmres_its,
+                        "newton_its": st.newton_its})
+        res["ndof"] = disc.ndof
+    elif name == "vortex_sample":
+        ph = laws.Physics(laws.EULER, 2, flux="rusanov")
+        n = (16, 16)
+        disc = dgsem.Disc(dgsem.Mesh(2, n, VORTEX["lo"], VORTEX["hi"]), VORTEX["N"], ph)
+        opts = newton.NewtonOptions(tol_rel=VORTEX["tol_newton_rel"], tol_abs=VORTEX["tol_newton_abs"],
+                                    gmres_tol=VORTEX["tol_gmres_rel"], restart=VORTEX["gmres_restart"],
+                                    gmres_maxiter=VORTEX["gmres_max_iter"], newton_max=VORTEX["newton_max_iter"],
+                                    jv="fd", pc="bjext")
+        t0 = time.perf_counter()
+        w = ohbpc.dg_stepper(disc, vortex_dt(n), VORTEX["q"], VORTEX["kmax"], opts)(
+            inputs.isentropic_vortex(disc.node_coords()))
+        res.update({"seconds": [time.perf_counter() - t0], "ndof": disc.ndof})
+    else:
+        raise ValueError(name)
+    np.save(os.path.join(outdir, name + ".npy"), w)
+    print(json.dumps(res), flush=True)
+
+
+class OracleRun:
+    """A child process running one oracle task (subprocess: fork and exec, so
+    it is independent of the parent's CUDA context)."""
+
+    def __init__(self, name, outdir, steps=1, one_thread=True):
+        env = dict(os.environ)
+        if one_thread:
+            env.update(ONE_THREAD)
+        self.name, self.outdir = name, outdir
+        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-task", name,
+                                      "--oracle-out", outdir, "--oracle-steps", str(steps)],
+                                     stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+
+    def result(self, timeout=1800):
+        try:
+            out, err = self.proc.communicate(timeout=timeout)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            return None, None
+        if self.proc.returncode != 0:
+            sys.stderr.write("oracle task %s failed:\n%s\n" % (self.name, err[-2000:]))
+            return None, None
+        info = json.loads(out.strip().splitlines()[-1])
+        return info, np.load(os.path.join(self.outdir, self.name + ".npy"))
+
+
+def cpu_baseline_timing(outdir):
+    """The oracle's C2 sample (whole HBPC(8,4) steps on 16 x 16 elements, CFL 8)
+    with BLAS pinned to one thread and with all host threads allowed, one after
+    the other.  Returns (cpu_baseline dict, the one-thread run's state after
+    one step)."""
+    r1, w1 = OracleRun("c2_sample", outdir, steps=1, one_thread=True).result()
+    alldir = os.path.join(outdir, "all")
+    os.makedirs(alldir, exist_ok=True)
+    ra, _ = OracleRun("c2_sample", alldir, steps=1, one_thread=False).result()
+    if r1 is None:
+        return None, None
+    hc = host_cpu()
+    ndof = r1["ndof"]
+    base = {"value": ndof / r1["seconds"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("one whole HBPC(8,4) step (15 Newton-GMRES stage solves, %d GMRES iterations) of the "
+                       "same workload on a 16x16-element mesh at the same CFL 8 (dt = 1/24, %d DOF), "
+                       "numpy with BLAS pinned to 1 thread, %.1f s" % (r1["gmres_its"], ndof, r1["seconds"][0])),
+            "host": hc}
+    if ra is not None:
+        base["all_threads"] = {"value": ndof / ra["seconds"][0], "unit": UNIT, "threads": hc["nproc"],
+                               "seconds": ra["seconds"][0],
+                               "note": "numpy's BLAS may use every host thread; the oracle's element "
+                                       "loops are vectorised numpy, not threaded"}
+    return base, w1
+
+
+VORTEX = dict(n=(128, 128), lo=(-10.0, -10.0), hi=(10.0, 10.0), N=4, q=6, kmax=2, cfl=10.0,
+              tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3, gmres_restart=100,
+              gmres_max_iter=3000, newton_max_iter=30, collect_per_newton=1024, collect_capacity=32768,
+              train_inverse_its=20000, train_lr=1e-3, train_batch=256,
+              train_probe=((8000, 1e-5), (8000, 1e-5), (8000, 5e-6), (8000, 2e-6)), train_probes=8,
+              sample_n=(16, 16))
+
+
+def vortex_dt(n=None):
+    """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v| + c of the
+    free stream plus the vortex's peak velocity (about 0.5 c_inf)."""
+    n = n or VORTEX["n"]
+    g = 1.4
+    lam = (0.5 * np.sqrt(g) + np.sqrt(g), np.sqrt(g))
+    h = [(VORTEX["hi"][m] - VORTEX["lo"][m]) / n[m] for m in range(2)]
+    return VORTEX["cfl"] / sum(lam[m] * (VORTEX["N"] + 1) / h[m] for m in range(2))
+
+
+def run_vortex(args, emit=True, oracle_state=None):
+    """2-D Euler isentropic vortex (strength 5, Mach 0.5) on [-10, 10]^2, 128 x 128
+    elements, N = 4, Rusanov, HBPC(6, 2), CFL 10, Newton tol 1e-10.  The learned
+    block preconditioner is trained on the GPU on (features, exact block
+    inverse) samples of the method's own BJ_ext Newton iterations during the
+    warm-up steps; then the same time step is taken with the learned
+    preconditioner, with BJ_ext and with plain GMRES (no preconditioner), all in
+    the mixed mode, and with BJ_ext in FP64.  Every answer is compared with the
+    FP64 GPU result at full size and, on a 16 x 16 mesh of the same domain and
+    CFL (same network), with the FP64 oracle's step (oracle_state: a callable
+    returning it, or None)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+
+    def ctx(pc, n=VORTEX["n"], prec=hbpc.PREC_MIXED):
+        return hbpc.Context(2, n, VORTEX["lo"], VORTEX["hi"], VORTEX["N"], law=hbpc.LAW_EULER,
+                            flux=hbpc.FLUX_RUSANOV, q=VORTEX["q"], kmax=VORTEX["kmax"], dt=vortex_dt(n),
+                            tol_newton_rel=VORTEX["tol_newton_rel"], tol_newton_abs=VORTEX["tol_newton_abs"],
+                            tol_gmres_rel=VORTEX["tol_gmres_rel"], gmres_restart=VORTEX["gmres_restart"],
+                            gmres_max_iter=VORTEX["gmres_max_iter"], newton_max_iter=VORTEX["newton_max_iter"],
+                            pc=pc, precision=prec)
+    gen = ctx(hbpc.PC_BJEXT)
+    gen.pc_collect(VORTEX["collect_per_newton"], VORTEX["collect_capacity"])
+    gen.set_state(inputs.isentropic_vortex(gen.node_coords()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gen.step(max(1, args.warmup))
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    w_start = gen.get_state()
+    gen.pc_collect(0, 0)
+    gen.pc_model_init(seed=1, out_scale=1e-2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    l0, l1 = gen.pc_train(iters=VORTEX["train_inverse_its"], batch=VORTEX["train_batch"], probes=4,
+                          lr=VORTEX["train_lr"], seed=11, loss="inverse")
+    # then the probe loss |M~ S x - x|^2, what the preconditioner has to achieve
+    probe_losses = []
+    for k, (its, lr) in enumerate(VORTEX["train_probe"]):
+        pa, pb = gen.pc_train(iters=its, batch=VORTEX["train_batch"], probes=VORTEX["train_probes"], lr=lr,
+                              seed=50 + k, loss="probe")
+        probe_losses.append((pa, pb))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    params = gen.pc_model_get()
+    ndof = gen.ndof
+    gen.close()
+
+    def timed(pc, steps, params=None, prec=hbpc.PREC_MIXED, n=VORTEX["n"], w0=None):
+        c = ctx(pc, n, prec)
+        if params is not None:
+            c.pc_model_set(params)
+        c.set_state(w_start if w0 is None else w0)
+        ok, ms, states = True, 0.0, []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            try:
+                c.step(1)
+            except hbpc.HBPCError as e:
+                ok = str(e)[:80]
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            if ok is not True:
+                break
+            states.append(c.get_state())
+        st = c.stats()
+        nd = c.ndof
+        c.close()
+        return {"ok": ok, "ms_per_step": ms / steps, "value": nd * steps / (ms / 1000.0) if ok is True else 0.0,
+                "gmres_its_per_step": st["gmres_its"] / steps, "newton_its_per_step": st["newton_its"] / steps,
+                "launches": int(st["launches"]),
+                "exact_blocks_per_build": (st["pc_exact_blocks"] / max(1, st["newton_its"])
+                                           if pc == hbpc.PC_LEARNED else None)}, states
+
+    r_bj, s_bj = timed(hbpc.PC_BJEXT, args.steps)
+    r_ln, s_ln = timed(hbpc.PC_LEARNED, args.steps, params)
+    r_pl, s_pl = timed(hbpc.PC_NONE, 1)
+    r_64, s_64 = timed(hbpc.PC_BJEXT, args.steps, prec=hbpc.PREC_FP64)
+    # every answer against the FP64 GPU result after the same number of steps
+    for r, s in ((r_bj, s_bj), (r_ln, s_ln), (r_pl, s_pl)):
+        if r["ok"] is True and r_64["ok"] is True:
+            r["rel_l2_vs_fp64_gpu"] = rel_l2(s[-1], s_64[len(s) - 1])
+    # the same arms on the 16 x 16 mesh, one step from the vortex, against the oracle
+    small = {}
+    w16 = None
+    for name, pc, prec, prm in (("learned", hbpc.PC_LEARNED, hbpc.PREC_MIXED, params),
+                                ("bjext", hbpc.PC_BJEXT, hbpc.PREC_MIXED, None),
+                                ("plain_gmres", hbpc.PC_NONE, hbpc.PREC_MIXED, None),
+                                ("fp64_bjext", hbpc.PC_BJEXT, hbpc.PREC_FP64, None)):
+        c = ctx(pc, VORTEX["sample_n"], prec)
+        w16 = inputs.isentropic_vortex(c.node_coords())
+        c.close()
+        r, s = timed(pc, 1, prm, prec, VORTEX["sample_n"], w16)
+        small[name] = (r, s)
+    ref16 = oracle_state() if oracle_state is not None else None
+    for name, (r, s) in small.items():
+        r["mesh"] = "16x16"
+        if ref16 is not None and r["ok"] is True:
+            r["rel_l2_vs_oracle"] = rel_l2(s[-1], ref16)
+    for key, r in (("learned", r_ln), ("bjext", r_bj), ("plain_gmres", r_pl)):
+        if "rel_l2_vs_oracle" in small[key][0]:
+            r["rel_l2_vs_oracle_16x16"] = small[key][0]["rel_l2_vs_oracle"]
+    head = r_ln if r_ln["ok"] is True else r_bj
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov, bf16 network",
+            "data": "synthetic",
+            "config": {"workload": "2d_euler_isentropic_vortex_128x128_N4_HBPC(6,2)_CFL10_Rusanov",
+                       "value_is": "learned preconditioner" if r_ln["ok"] is True else
+                                   "BJ_ext (the learned preconditioner did not converge)",
+                       "dt": vortex_dt(), "eps_newton": VORTEX["tol_newton_rel"],
+                       "eps_gmres": VORTEX["tol_gmres_rel"],
+                       "gmres_restart": VORTEX["gmres_restart"], "gmres_max_iter": VORTEX["gmres_max_iter"],
+                       "newton_max_iter": VORTEX["newton_max_iter"], "precision": "mixed",
+                       "training": {"data_steps": max(1, args.warmup), "data_s": round(t_data, 2),
+                                    "samples_per_newton": VORTEX["collect_per_newton"],
+                                    "inverse_regression": {"iters": VORTEX["train_inverse_its"],
+                                                           "loss_first": l0, "loss_last": l1},
+                                    "probe": {"rounds": [list(r) for r in VORTEX["train_probe"]],
+                                              "probes": VORTEX["train_probes"],
+                                              "loss_first_last": probe_losses},
+                                    "train_s": round(t_train, 2)}},
+            "gpu_launches": head["launches"], "learned": r_ln, "bjext": r_bj, "plain_gmres": r_pl,
+            "fp64_bjext": r_64,
+            "accuracy_16x16": {k: {kk: v[0].get(kk) for kk in ("ok", "rel_l2_vs_oracle", "gmres_its_per_step",
+                                                                 "exact_blocks_per_build")}
+                               for k, v in small.items()},
+            "oracle_16x16": "one HBPC(6,2) step of the FP64 oracle (Eq. 23 Jv, BJ_ext) on a 16x16 mesh of "
+                            "the same domain at CFL 10" if ref16 is not None else None}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_ours(args):
@@ -173,189 +726,128 @@ def run_ours(args):
     import __graft_entry__ as g
     g.build()
     from paper_2109_04804_gb300 import hbpc, inputs
+    head = args.precision
+    other = "mixed" if head == "fp64" else "fp64"
+    extras = rank == 0 and world == 1
     dt = workload_dt()
     stream = torch.cuda.Stream()
-    ctx = hbpc.Context(WL["dim"], WL["n"], WL["lo"], WL["hi"], WL["N"], law=hbpc.LAW_ADVECTION,
-                       a=WL["a"], q=WL["q"], kmax=WL["kmax"], dt=dt,
-                       tol_newton_rel=WL["tol_newton_rel"], tol_newton_abs=WL["tol_newton_abs"],
-                       tol_gmres_rel=WL["tol_gmres_rel"], gmres_restart=WL["gmres_restart"],
-                       gmres_max_iter=WL["gmres_max_iter"], newton_max_iter=WL["newton_max_iter"],
-                       pc=hbpc.PC_BJEXT, stream=stream.cuda_stream,
-                       precision=hbpc.PREC_MIXED if PRECISION[0] == "mixed" else hbpc.PREC_FP64)
-    coords = ctx.node_coords()
-    w0 = inputs.sine_product(coords)
-    ctx.set_state(w0)
-    ndof = ctx.ndof
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        ctx.step(1)
-    tuning = ctx.autotune()        # launch shapes of the Krylov reductions and the PC apply
-    torch.cuda.synchronize()
-    ctx.reset_stats()
-    clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    total_ms = 0.0
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)             # L2 flush outside the timed window
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.step(1)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    stats = ctx.stats()
-    t_sec = total_ms / 1000.0
-    if world > 1:
-        tt = torch.tensor([t_sec], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_sec = float(tt.item())
-        torch.distributed.barrier()
-    value = ndof * args.steps * world / t_sec
-    r1_per_s = (stats["r1_evals"] + stats["r2_evals"]) / t_sec
-    # accuracy: L2 error vs the exact solution at the final time
-    w = ctx.get_state()
-    t_fin = (args.warmup + args.steps) * dt
-    err = float(np.sqrt(np.mean((w - exact_solution(coords, t_fin)) ** 2)))
-
-    # per-phase device time from a separate profiled step (events around launches)
-    ctx.profile(True)
-    ctx.step(1)
-    prof = ctx.profile_get()
-    pstats = ctx.stats()
-    ctx.profile(False)
-    # roofline of the dominant kernel phase (FP64 on GB300 is ALU-bound: the
-    # denominator is the measured FP64 FMA throughput; HBM fraction alongside)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    hbm = peaks().get("hbm_gbs", 6800.0)
     fp64_peak = hbpc.fp64_fma_peak()          # measured live on this GPU
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    mixed = PRECISION[0] == "mixed"
-    # CGS2 column (one launch per Arnoldi iteration): the three passes read the
-    # new vector and the j + 1 basis vectors and write the new vector twice:
-    # (3 (j + 1) + 5) vectors of 2 n_dof values; 6 (j + 1) + 8 flops per value
-    its_p = pstats["gmres_its"] - stats["gmres_its"]
-    cols_p = pstats["arnoldi_cols"] - stats["arnoldi_cols"]
-    cavg = cols_p / max(1, its_p)
-    vb = 4.0 if mixed else 8.0
-    cgs_b = (3.0 * cavg + 5.0) * 2.0 * vb       # bytes per W-DOF per launch
-    cgs_f = (6.0 * cavg + 8.0) * 2.0            # flops per W-DOF per launch
-    prof_cgs = (prof["arnoldi_dot"][0] + prof["arnoldi_update"][0], its_p)
-    kernels = {"jv": ("dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)"
-                      % ("float" if mixed else "double"), jv_work_per_dof(mixed), prof["jv"]),
-               "pc_apply": (("k_pc_apply_shared<float, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements)"
-                             if mixed else "k_pc_apply<double> (BJ_ext, Sec. 3.2.3; one block pair for all elements)"),
-                            pc_work_per_dof(mixed), prof["pc_apply"]),
-               "cgs2": ("k_cgs_coop<%s> (Arnoldi CGS2 column, one cooperative launch; mean j + 1 = %.1f)"
-                        % ("float" if mixed else "double", cavg), (cgs_b, cgs_f), prof_cgs)}
-    entries = {}
-    for ph, (name, (bpd, fpd), (ms, n)) in kernels.items():
-        if n == 0:
-            continue
-        avg = ms / 1000.0 / n
-        gf = fpd * ndof / avg / 1e9
-        gb = bpd * ndof / avg / 1e9
-        if mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are HBM-bound
-            entries[ph] = {"kernel": name, "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
-                           "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": NCU_TRAFFIC.get(ph),
-                           "algorithmic_bytes_per_launch": round(bpd * ndof),
-                           "alu_tflops": round(gf / 1000.0, 3)}
-        else:
-            entries[ph] = {"kernel": name, "bound": "alu", "achieved": round(gf / 1000.0, 4),
-                           "peak": fp64_peak / 1000.0, "unit": "TFLOP/s", "frac": round(gf / fp64_peak, 4),
-                           "traffic": None, "hbm_achieved_gbs": round(gb, 1),
-                           "hbm_frac_of_measured": round(gb / hbm, 4)}
-        entries[ph].update({"avg_launch_us": round(avg * 1e6, 2), "launches_profiled": n,
-                            "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3)})
-    dom = max(entries, key=lambda k: kernels[k][2][0])
-    roofline = dict(entries[dom])
-    roofline["peak_source"] = ("measured HBM copy bandwidth (MEASURED_PEAKS.json)" if mixed else
-                               "FP64 FMA throughput measured in this run (hbpc_fp64_fma_peak)")
-    roofline["phase_ms_one_step"] = {k: round(v[0], 3) for k, v in prof.items()}
-    roofline["phase_launches_one_step"] = {k: v[1] for k, v in prof.items()}
-    roofline["other_kernels"] = {k: v for k, v in entries.items() if k != dom}
+    want_oracle = extras and not args.no_cpu_baseline
+    tmp = tempfile.mkdtemp(prefix="hbpc_oracle_") if want_oracle else None
 
-    # e2e: the public API with host buffers, copies inside the timed region
-    host_in = torch.from_numpy(w0.copy()).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.set_state_host_ptr(host_in.data_ptr())
-        ctx.step(1)
-        ctx.get_state_host_ptr(host_out.data_ptr())
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
-    ctx.close()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+    res = run_c2_arm(torch, hbpc, inputs, head, args, stream, flush, fp64_peak, hbm, world, headline=True)
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if PRECISION[0] == "fp64" else "f64 state/Newton, f32 Krylov",
-            "data": "synthetic",
-            "config": config_dict(dt, {"parallelism": "replicas" if world > 1 else "single",
-                                       "autotuned": tuning}),
-            "r1_evals_per_s": r1_per_s, "l2_error_vs_exact": err,
-            "gmres_its_per_step": stats["gmres_its"] / args.steps,
-            "newton_its_per_step": stats["newton_its"] / args.steps,
-            "gpu_launches": int(stats["launches"]), "roofline": roofline, "e2e": e2e, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(dt)
-    if rank == 0 and world == 1 and not args.no_vortex:
-        # the metric's comparison, on the Euler vortex workload (learned block
-        # preconditioner trained on the run's own Newton-GMRES data vs plain
-        # GMRES and BJ_ext); see --workload euler_vortex for the full line
+            "dtype": "f64" if head == "fp64" else "f64 state/Newton, f32 Krylov", "data": "synthetic",
+            "config": dict(config_dict(dt, head), parallelism="replicas" if world > 1 else "single"),
+            "autotuned": res["autotuned"], "r1_evals_per_s": res["r1_evals_per_s"],
+            "l2_error_vs_exact": res["l2_error_vs_exact"], "gmres_its_per_step": res["gmres_its_per_step"],
+            "newton_its_per_step": res["newton_its_per_step"], "gpu_launches": res["gpu_launches"],
+            "roofline": res["roofline"], "e2e": res["e2e"], "clocks": res["clocks"]}
+    if not extras:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    # oracle references that are not timed run beside the GPU work, on one host core each
+    bg = {}
+    if want_oracle:
+        bg["c2_exact"] = OracleRun("c2_exact", tmp, steps=res["steps_total"])
+        if not args.no_vortex:
+            bg["vortex_sample"] = OracleRun("vortex_sample", tmp)
+    sec = run_c2_arm(torch, hbpc, inputs, other, args, stream, flush, fp64_peak, hbm, world, headline=False)
+    sample = c2_sample_steps(torch, hbpc, inputs)
+    line["r1_roofline"] = None if args.no_r1_roofline else r1_roofline(torch, hbpc, inputs, flush, fp64_peak, hbm)
+    if not args.no_vortex:
+        def vortex_ref():
+            if "vortex_sample" not in bg:
+                return None
+            info, w = bg["vortex_sample"].result()
+            return w
         va = argparse.Namespace(steps=1, warmup=2)
-        v = run_vortex(va, emit=False)
+        v = run_vortex(va, emit=False, oracle_state=vortex_ref)
         ln, pl, bj = v["learned"], v["plain_gmres"], v["bjext"]
         line["learned_vs_plain"] = {
-            "workload": v["config"]["workload"], "unit": UNIT,
-            "learned": ln, "plain_gmres": pl, "bjext": bj,
+            "workload": v["config"]["workload"], "unit": UNIT, "learned": ln, "plain_gmres": pl, "bjext": bj,
+            "fp64_bjext": v["fp64_bjext"], "accuracy_16x16": v["accuracy_16x16"],
+            "oracle_16x16": v["oracle_16x16"],
             "speedup_learned_over_plain": (ln["value"] / pl["value"]) if pl["value"] > 0 else None,
             "speedup_learned_over_bjext": (ln["value"] / bj["value"]) if bj["value"] > 0 else None,
             "training": v["config"]["training"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    # the oracle: the timed CPU baseline, then the accuracy of both precisions
+    acc = {"fp64" if head == "fp64" else "mixed": {"l2_error_vs_exact_solution": res["l2_error_vs_exact"]},
+           other: {"l2_error_vs_exact_solution": sec["l2_error_vs_exact"]}}
+    if want_oracle:
+        info, w_ex = bg["c2_exact"].result()
+        if w_ex is not None:
+            acc[head]["rel_l2_vs_oracle_64x64"] = rel_l2(res["w_final"], w_ex)
+            acc[other]["rel_l2_vs_oracle_64x64"] = rel_l2(sec["w_final"], w_ex)
+            acc["oracle_64x64"] = ("exact per-Fourier-mode HBPC(8,4) result after %d steps (dense solves of "
+                                   "every stage per mode: the root the Newton iterations converge to)"
+                                   % res["steps_total"])
+        cb, w16 = cpu_baseline_timing(tmp)
+        if cb is not None:
+            line["cpu_baseline"] = cb
+            for prec in ("fp64", "mixed"):
+                acc[prec]["rel_l2_vs_oracle_16x16_one_step"] = rel_l2(sample[prec], w16)
+            acc["oracle_16x16"] = "one HBPC(8,4) step of the FP64 oracle (Newton-GMRES, BJ_ext) on 16x16, CFL 8"
+    line["accuracy"] = acc
+    sec.pop("w_final")
+    line["mixed_precision" if head == "fp64" else "fp64_precision"] = {
+        k: sec[k] for k in ("value", "ms_per_step", "gmres_its_per_step", "newton_its_per_step", "r1_evals_per_s",
+                            "gpu_launches", "roofline", "autotuned")}
+    line[("mixed_precision" if head == "fp64" else "fp64_precision")]["unit"] = UNIT
+    line[("mixed_precision" if head == "fp64" else "fp64_precision")]["dtype"] = (
+        "f64 state/Newton, f32 Krylov" if other == "mixed" else "f64")
+    print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(dt, budget_s=20.0):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the workload: the first predictor stage solve of one HBPC(8,4) step (one of
-    its 15 stage solves), scaled to a full step."""
-    from oracle import dgsem, laws, newton
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on the host cores: W + K whole
+    HBPC(8,4) steps of the 2-D advection workload on the 16 x 16 sample at the
+    same CFL 8 (each step continues from the last), K of them timed."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import dgsem, hbpc as ohbpc, laws, newton
     from paper_2109_04804_gb300 import inputs
     ph = laws.Physics(laws.ADVECTION, 2, a=WL["a"])
-    disc = dgsem.Disc(dgsem.Mesh(2, WL["n"], WL["lo"], WL["hi"]), WL["N"], ph)
-    w0 = inputs.sine_product(disc.node_coords())
+    disc = dgsem.Disc(dgsem.Mesh(2, SAMPLE_N, WL["lo"], WL["hi"]), WL["N"], ph)
+    dts = workload_dt(SAMPLE_N)
     opts = newton.NewtonOptions(tol_rel=WL["tol_newton_rel"], tol_abs=WL["tol_newton_abs"],
                                 gmres_tol=WL["tol_gmres_rel"], restart=WL["gmres_restart"],
+                                gmres_maxiter=WL["gmres_max_iter"], newton_max=WL["newton_max_iter"],
                                 jv="linear", pc="bjext")
-    dc = 1.0 / 3.0
-    a1, a2 = dc / 2.0, dc * dc / 6.0
-    r1 = dgsem.R1(disc, w0)
-    b = w0 + a1 * dt * r1 + (a2 * dt * dt / 2.0) * dgsem.R2(disc, w0, r1)
+    st = newton.Stats()
+    adv = ohbpc.dg_stepper(disc, dts, WL["q"], WL["kmax"], opts, stats=st)
+    w = inputs.sine_product(disc.node_coords())
+    for _ in range(args.warmup):
+        w = adv(w)
+    its0 = st.gmres_its
     t0 = time.perf_counter()
-    _, _, st = newton.newton_solve(disc, b, a1, a2, dt, w0, opts)
-    t1 = time.perf_counter() - t0
-    solves_per_step = (4 - 1) * (1 + 4)
-    step_s = t1 * solves_per_step
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
-    return {"value": disc.ndof / step_s, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "first predictor stage solve of one HBPC(8,4) step on the full 64x64 N=5 "
-                      "mesh (%d GMRES its, %.1f s), scaled x%d stage solves per step"
-                      % (st.gmres_its, t1, solves_per_step)}
+    for _ in range(args.steps):
+        w = adv(w)
+    t = time.perf_counter() - t0
+    value = disc.ndof * args.steps / t
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    hc = host_cpu()
+    sample = ("%d whole HBPC(8,4) steps (after %d warm-up steps) of the same workload on a 16x16-element mesh "
+              "at the same CFL 8 (dt = 1/24, %d DOF), %d GMRES iterations per step, FP64 numpy oracle"
+              % (args.steps, args.warmup, disc.ndof, (st.gmres_its - its0) // max(1, args.steps)))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(config_dict(workload_dt(), "fp64"), parallelism="replicas" if world > 1 else "single"),
+            "impl": "reference", "sample": sample,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "host": hc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 BATCH = dict(n_inst=256, n_range=(16, 96), N_range=(3, 7), nu_range=(1e-3, 1e-2), seed=2024,
@@ -478,133 +970,6 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
-VORTEX = dict(n=(128, 128), lo=(-10.0, -10.0), hi=(10.0, 10.0), N=4, q=6, kmax=2, cfl=10.0,
-              tol_newton_rel=1e-10, tol_newton_abs=1e-12, tol_gmres_rel=1e-3, gmres_restart=100,
-              gmres_max_iter=3000, newton_max_iter=30, collect_per_newton=1024, collect_capacity=32768,
-              train_inverse_its=20000, train_lr=1e-3, train_batch=256,
-              train_probe=((8000, 1e-5), (8000, 1e-5), (8000, 5e-6), (8000, 2e-6)), train_probes=8)
-
-
-def vortex_dt():
-    """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v| + c of the
-    free stream plus the vortex's peak velocity (about 0.5 c_inf)."""
-    g = 1.4
-    lam = (0.5 * np.sqrt(g) + np.sqrt(g), np.sqrt(g))
-    h = [(VORTEX["hi"][m] - VORTEX["lo"][m]) / VORTEX["n"][m] for m in range(2)]
-    return VORTEX["cfl"] / sum(lam[m] * (VORTEX["N"] + 1) / h[m] for m in range(2))
-
-
-def run_vortex(args, emit=True):
-    """2-D Euler isentropic vortex (strength 5, Mach 0.5) on [-10, 10]^2, 128 x 128
-    elements, N = 4, Rusanov, HBPC(6, 2), CFL 10, Newton tol 1e-10, mixed
-    precision.  The learned block preconditioner is trained on the GPU on
-    (features, exact block inverse) samples of the method's own BJ_ext Newton
-    iterations during the warm-up steps; then the same time step is taken with
-    the learned preconditioner, with BJ_ext, and with plain GMRES (no
-    preconditioner), each against the FP64-state BJ_ext result."""
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__ as g
-    g.build()
-    from paper_2109_04804_gb300 import hbpc, inputs
-    dt = vortex_dt()
-
-    def ctx(pc):
-        return hbpc.Context(2, VORTEX["n"], VORTEX["lo"], VORTEX["hi"], VORTEX["N"], law=hbpc.LAW_EULER,
-                            flux=hbpc.FLUX_RUSANOV, q=VORTEX["q"], kmax=VORTEX["kmax"], dt=dt,
-                            tol_newton_rel=VORTEX["tol_newton_rel"], tol_newton_abs=VORTEX["tol_newton_abs"],
-                            tol_gmres_rel=VORTEX["tol_gmres_rel"], gmres_restart=VORTEX["gmres_restart"],
-                            gmres_max_iter=VORTEX["gmres_max_iter"], newton_max_iter=VORTEX["newton_max_iter"],
-                            pc=pc, precision=hbpc.PREC_MIXED)
-    gen = ctx(hbpc.PC_BJEXT)
-    gen.pc_collect(VORTEX["collect_per_newton"], VORTEX["collect_capacity"])
-    gen.set_state(inputs.isentropic_vortex(gen.node_coords()))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    gen.step(max(1, args.warmup))
-    torch.cuda.synchronize()
-    t_data = time.perf_counter() - t0
-    w_start = gen.get_state()
-    gen.pc_collect(0, 0)
-    gen.pc_model_init(seed=1, out_scale=1e-2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    l0, l1 = gen.pc_train(iters=VORTEX["train_inverse_its"], batch=VORTEX["train_batch"], probes=4,
-                          lr=VORTEX["train_lr"], seed=11, loss="inverse")
-    # then the probe loss |M~ S x - x|^2, what the preconditioner has to achieve
-    probe_losses = []
-    for k, (its, lr) in enumerate(VORTEX["train_probe"]):
-        pa, pb = gen.pc_train(iters=its, batch=VORTEX["train_batch"], probes=VORTEX["train_probes"], lr=lr,
-                              seed=50 + k, loss="probe")
-        probe_losses.append((pa, pb))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    params = gen.pc_model_get()
-    ndof = gen.ndof
-    gen.close()
-
-    def timed(pc, steps, params=None):
-        c = ctx(pc)
-        if params is not None:
-            c.pc_model_set(params)
-        c.set_state(w_start)
-        ok, ms = True, 0.0
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
-            try:
-                c.step(1)
-            except hbpc.HBPCError as e:
-                ok = str(e)[:80]
-            e1.record()
-            torch.cuda.synchronize()
-            ms += e0.elapsed_time(e1)
-            if ok is not True:
-                break
-        st = c.stats()
-        w = c.get_state()
-        c.close()
-        return {"ok": ok, "ms_per_step": ms / steps, "value": ndof * steps / (ms / 1000.0) if ok is True else 0.0,
-                "gmres_its_per_step": st["gmres_its"] / steps, "newton_its_per_step": st["newton_its"] / steps,
-                "launches": int(st["launches"]),
-                "exact_blocks_per_build": (st["pc_exact_blocks"] / max(1, st["newton_its"])
-                                           if pc == hbpc.PC_LEARNED else None)}, w
-
-    r_bj, w_bj = timed(hbpc.PC_BJEXT, args.steps)
-    r_ln, w_ln = timed(hbpc.PC_LEARNED, args.steps, params)
-    r_pl, w_pl = timed(hbpc.PC_NONE, 1)
-    # every result against the BJ_ext run (the same Newton tolerance fixes the answer)
-    for r, w in ((r_ln, w_ln), (r_pl, w_pl)):
-        if r["ok"] is True:
-            ref = w_bj if r is r_ln else None
-            if ref is not None:
-                r["rel_l2_vs_bjext"] = float(np.linalg.norm(w - ref) / np.linalg.norm(ref))
-    head = r_ln if r_ln["ok"] is True else r_bj
-    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 state/Newton, f32 Krylov, bf16 network",
-            "data": "synthetic",
-            "config": {"workload": "2d_euler_isentropic_vortex_128x128_N4_HBPC(6,2)_CFL10_Rusanov",
-                       "value_is": "learned preconditioner" if r_ln["ok"] is True else
-                                   "BJ_ext (the learned preconditioner did not converge)",
-                       "dt": dt, "eps_newton": VORTEX["tol_newton_rel"], "eps_gmres": VORTEX["tol_gmres_rel"],
-                       "gmres_restart": VORTEX["gmres_restart"], "gmres_max_iter": VORTEX["gmres_max_iter"],
-                       "newton_max_iter": VORTEX["newton_max_iter"], "precision": "mixed",
-                       "training": {"data_steps": max(1, args.warmup), "data_s": round(t_data, 2),
-                                    "samples_per_newton": VORTEX["collect_per_newton"],
-                                    "inverse_regression": {"iters": VORTEX["train_inverse_its"],
-                                                           "loss_first": l0, "loss_last": l1},
-                                    "probe": {"rounds": [list(r) for r in VORTEX["train_probe"]],
-                                              "probes": VORTEX["train_probes"],
-                                              "loss_first_last": probe_losses},
-                                    "train_s": round(t_train, 2)}},
-            "gpu_launches": head["launches"], "learned": r_ln, "bjext": r_bj, "plain_gmres": r_pl}
-    if emit:
-        print(json.dumps(line), flush=True)
-    return line
-
-
 TGV = dict(n=32, N=5, q=4, kmax=0, cfl=20.0, eps=0.1, re=1600.0, prandtl=0.72, tol_newton_rel=1e-10,
            tol_newton_abs=1e-10, tol_gmres_rel=1e-3, gmres_restart=100, gmres_max_iter=5000, newton_max_iter=30,
            check_n=8)
@@ -714,30 +1079,6 @@ def run_tgv(args, emit=True):
     return line
 
 
-def run_reference(args):
-    world, rank, _ = dist_env()
-    if rank != 0:
-        return
-    dt = workload_dt()
-    vals = []
-    sample = None
-    t_all = time.perf_counter()
-    for _ in range(max(1, args.warmup) + max(1, args.steps)):
-        cb = cpu_baseline(dt)
-        vals.append(cb["value"])
-        sample = cb
-        if time.perf_counter() - t_all > 240:
-            break
-    timed = vals[-max(1, args.steps):]
-    value = float(np.mean(timed))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * 147456 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(dt), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
-                             "sample": sample["sample"]},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -746,11 +1087,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle (timed CPU baseline and the accuracy against the oracle)")
     ap.add_argument("--no-vortex", action="store_true",
                     help="skip the learned-vs-plain-GMRES comparison on the Euler vortex in the default line")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="mixed: FP32 Krylov loop, FP64 Newton residual/update; fp64: all FP64")
+    ap.add_argument("--no-r1-roofline", action="store_true",
+                    help="skip the operator-pass roofline on the Euler vortex and Taylor-Green meshes")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the headline value (the other one is reported beside it): fp64, the "
+                         "workload's own; mixed: FP32 Krylov loop, FP64 Newton residual/update")
     ap.add_argument("--workload", default="advection2d",
                     choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
@@ -763,9 +1108,13 @@ def main():
                     help="taylor_green: skip the FP64-vs-mixed comparison on the 8^3 mesh")
     ap.add_argument("--max-per-group", type=int, default=BATCH["max_per_group"],
                     help="instances sharing one context and one GMRES (<= 0: all of one N)")
+    ap.add_argument("--oracle-task", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    PRECISION[0] = args.precision
-    if args.impl == "reference":
+    if args.oracle_task:
+        oracle_task(args.oracle_task, args.oracle_out, args.oracle_steps)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "burgers_batch":
         run_batch(args)

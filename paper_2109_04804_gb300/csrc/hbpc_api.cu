@@ -1847,7 +1847,12 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
         if (mixed) cgs_launch<float>(x, x->Kf); else cgs_launch<double>(x, x->K);
       });
     }
-    if (cudaGetLastError() != cudaSuccess) continue;   // a shape that cannot launch is no candidate
+    // every candidate is a launchable shape (capped by the residency check),
+    // so an error here is a fault of the trial launch: stop, do not go on
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+      x->nblocks = old_blocks; x->K.nblocks = old_blocks; x->Kf.nblocks = old_blocks;
+      return cuda_fail(x, e, "autotune: trial CGS2 column");
+    }
     if (nbk == old_blocks) first_k = us;
     if (us < best_k) { best_k = us; best_b = nbk; }
   }
@@ -1883,7 +1888,10 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
         if (mixed) pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr);
         else pc_apply(x, x->Z, nullptr, nullptr, x->G, 0, nullptr);
       });
-      if (cudaGetLastError() != cudaSuccess) continue;
+      if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+        x->pc_threads = old_threads; x->pc_grid = old_grid; x->pc_smem = old_smem;
+        return cuda_fail(x, e, "autotune: trial preconditioner apply");
+      }
       if (threads == old_threads) first_p = us;
       if (us < best_p) { best_p = us; bt = threads; bg = grid; bs = smem; best_e = epb; }
     }
@@ -2285,8 +2293,23 @@ hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const doub
   ctx->ops.residual(ctx->prm, ctx->X, ctx->X + n, ctx->X, c1, c2, ctx->G, ctx->G + n, ctx->r1, ctx->r2,
                     ctx->stream);
   HBPC_LAUNCH_CK(ctx, "Jv residual");
+  hbpc_status s;
+  if (ctx->sol.precision == HBPC_PREC_MIXED) {
+    // the product the FP32 Krylov loop uses: the analytic linearisation at the
+    // FP32 copy of X (dual numbers), on the FP32 direction
+    if ((s = to_float(ctx, ctx->X, ctx->Wf, n2)) != HBPC_OK) return s;
+    if ((s = to_float(ctx, dX, ctx->Zf, n2)) != HBPC_OK) return s;
+    JvInputT<float> zf{};
+    zf.V = ctx->Zf; zf.ld = n2; zf.half = size_t(n);
+    zf.out = ctx->Zf2; zf.out_ld = n2; zf.out_offset = 0;
+    if ((s = apply_jv_f(ctx, zf)) != HBPC_OK) return s;
+    HBPC_CK(ctx, cudaMemsetAsync(out, 0, n2 * sizeof(double), ctx->stream));
+    HBPC_RUN(ctx, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, ctx->stream>>>(ctx->Zf2, out, n2));
+    HBPC_LAUNCH_CK(ctx, "eval_Jv (mixed)");
+    return sync(ctx, "eval_Jv");
+  }
   HBPC_CK(ctx, cudaMemcpyAsync(ctx->dX, dX, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  hbpc_status s = norms(ctx, ctx->dX, n2, ctx->dxn);
+  s = norms(ctx, ctx->dX, n2, ctx->dxn);
   if (s != HBPC_OK) return s;
   JvInput z{};
   z.V = ctx->dX; z.ld = n2; z.half = size_t(n);

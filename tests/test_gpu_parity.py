@@ -143,6 +143,33 @@ def test_residual_and_jv_parity(hb, law, dim, flux):
     ctx.close()
 
 
+@pytest.mark.parametrize("law,dim,flux", [(laws.ADVECTION, 2, "lf"), (laws.BURGERS, 2, "lf"),
+                                          (laws.EULER, 2, "lf"), (laws.EULER, 3, "lf")])
+def test_mixed_precision_jv_parity(hb, law, dim, flux):
+    """In the mixed mode hbpc_eval_Jv returns the FP32 product of the Krylov
+    loop: the analytic linearisation of Eq. 18 (dR1/dW v = R2(W, v), Sec. 3.2.1,
+    and the exact derivative of R2 for the Hessian block) in FP32 arithmetic.
+    With a constant dissipation coefficient it equals the oracle's analytic
+    form, whose Hessian block is the Eq. 23 quotient (error ~1e-8); the FP32
+    operator's rounding (~1e-7 per term) sets the 2e-5 bound."""
+    N = 3
+    ctx, disc = pair(hb, law, dim, N, mesh_for(dim), LOBATTO, flux, dt=0.03, precision=hb.PREC_MIXED)
+    rng = np.random.default_rng(8)
+    W = euler_field(disc, 4) if law == laws.EULER else 0.5 + 0.3 * rng.standard_normal(disc.shape)
+    S = dgsem.R1(disc, W) + 0.01 * rng.standard_normal(disc.shape)
+    a1, a2 = 0.5, 1.0 / 6.0
+    sysm = newton.StageSystem(disc, W, a1, a2, 0.03)
+    X = np.concatenate([W.ravel(), S.ravel()])
+    _, r1, r2 = sysm.residual(X)
+    for k in range(2):
+        dX = rng.standard_normal(2 * disc.ndof)
+        out = torch.empty(2 * disc.ndof, dtype=torch.float64, device="cuda")
+        ctx.eval_Jv(a1, a2, dev(X), dev(dX), out)
+        ref = sysm.jv(X, r1, r2, dX, "linear" if disc.ph.linear else "analytic")
+        assert rel(host(out), ref) <= 2e-5, (k, rel(host(out), ref))
+    ctx.close()
+
+
 @pytest.mark.parametrize("law,dim,N,family,flux", [
     (laws.ADVECTION, 2, 5, LOBATTO, "lf"), (laws.ADVECTION, 1, 3, GAUSS, "lf"),
     (laws.BURGERS, 2, 3, LOBATTO, "rusanov"), (laws.EULER, 2, 4, LOBATTO, "rusanov"),

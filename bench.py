@@ -319,7 +319,9 @@ def run_c2_arm(torch, hbpc, inputs, precision, args, stream, flush, fp64_peak_gf
     if headline:
         # e2e: the public API with pinned host buffers, copies inside the timed
         # region, the L2 flush outside it (as in the device-timed loop)
-        host_in = torch.from_numpy(w0.copy()).pin_memory()
+        # the trajectory continues from the state reached: every step copies
+        # the last step's host result in and its own result out
+        host_in = torch.from_numpy(w_fin.copy()).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         e2e_s = 0.0
         for _ in range(args.steps):
@@ -331,6 +333,7 @@ def run_c2_arm(torch, hbpc, inputs, precision, args, stream, flush, fp64_peak_gf
             ctx.step(1)
             ctx.get_state_host_ptr(host_out.data_ptr())
             e2e_s += time.perf_counter() - t0
+            host_in, host_out = host_out, host_in
         res["e2e"] = {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8}
     ctx.close()
@@ -734,7 +737,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     hbm = peaks().get("hbm_gbs", 6800.0)
     fp64_peak = hbpc.fp64_fma_peak()          # measured live on this GPU
-    want_oracle = extras and not args.no_cpu_baseline
+    want_oracle = extras and not args.no_cpu_baseline and not args.headline_only
     tmp = tempfile.mkdtemp(prefix="hbpc_oracle_") if want_oracle else None
 
     res = run_c2_arm(torch, hbpc, inputs, head, args, stream, flush, fp64_peak, hbm, world, headline=True)
@@ -760,6 +763,9 @@ def run_ours(args):
         bg["c2_exact"] = OracleRun("c2_exact", tmp, steps=res["steps_total"])
         if not args.no_vortex:
             bg["vortex_sample"] = OracleRun("vortex_sample", tmp)
+    if args.headline_only:
+        print(json.dumps(line), flush=True)
+        return
     sec = run_c2_arm(torch, hbpc, inputs, other, args, stream, flush, fp64_peak, hbm, world, headline=False)
     sample = c2_sample_steps(torch, hbpc, inputs)
     line["r1_roofline"] = None if args.no_r1_roofline else r1_roofline(torch, hbpc, inputs, flush, fp64_peak, hbm)
@@ -805,6 +811,18 @@ def run_ours(args):
     line[("mixed_precision" if head == "fp64" else "fp64_precision")]["dtype"] = (
         "f64 state/Newton, f32 Krylov" if other == "mixed" else "f64")
     print(json.dumps(line), flush=True)
+
+
+def run_r1_only(args):
+    """The default line's r1_roofline object alone (for profiling)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = r1_roofline(torch, hbpc, inputs, flush, hbpc.fp64_fma_peak(), peaks().get("hbm_gbs", 6800.0))
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -1091,16 +1109,19 @@ def main():
                     help="skip the oracle (timed CPU baseline and the accuracy against the oracle)")
     ap.add_argument("--no-vortex", action="store_true",
                     help="skip the learned-vs-plain-GMRES comparison on the Euler vortex in the default line")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="the headline arm alone (for profiling): no second precision, oracle or vortex")
     ap.add_argument("--no-r1-roofline", action="store_true",
                     help="skip the operator-pass roofline on the Euler vortex and Taylor-Green meshes")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline value (the other one is reported beside it): fp64, the "
                          "workload's own; mixed: FP32 Krylov loop, FP64 Newton residual/update")
     ap.add_argument("--workload", default="advection2d",
-                    choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green"],
+                    choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green", "r1_roofline"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances; euler_vortex: learned vs BJ_ext vs plain GMRES; "
-                         "taylor_green: the 3-D Navier-Stokes line")
+                         "taylor_green: the 3-D Navier-Stokes line; r1_roofline: the operator-pass roofline "
+                         "object of the default line alone")
     ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
     ap.add_argument("--tgv-n", type=int, default=0,
                     help="taylor_green: elements per direction (default 32; smaller for profiling)")
@@ -1122,6 +1143,8 @@ def main():
         run_vortex(args)
     elif args.workload == "taylor_green":
         run_tgv(args)
+    elif args.workload == "r1_roofline":
+        run_r1_only(args)
     else:
         run_ours(args)
 

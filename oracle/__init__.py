@@ -4,8 +4,10 @@ the discontinuous Galerkin method").
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the package
 ``paper_2109_04804_gb300`` and its CUDA library) may import, call or link this
-package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` use it.  The oracle shares no code with the CUDA path: it is written
+package; only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s oracle
+runs use it (the timed CPU baseline, the reference arm, and the reference
+answers the bench's accuracy fields compare against, all in child processes or
+the reference arm's own process).  The oracle shares no code with the CUDA path: it is written
 from the paper, in numpy, in the order and notation of the paper, with library
 primitives (tensordot, solve, expm) used only as single steps.
 

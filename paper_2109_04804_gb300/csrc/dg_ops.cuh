@@ -473,9 +473,30 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
     }
     __syncthreads();
     // -- 2. face fluxes ------------------------------------------------------
-    if (live) {
-      for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
-        const int f = fp / NF, pt = fp - f * NF;
+    // The block's face points are spread over all its threads in face-major
+    // order (face direction and side, then element, then point): the threads of
+    // a warp mostly run the same face's code, with all lanes active, which on
+    // GB300's narrow FP64 pipe matters (a partially masked FP64 warp
+    // instruction occupies the pipe as long as a full one).
+    for (int wi = threadIdx.x; wi < EPB * 2 * DIM * NF; wi += blockDim.x) {
+      const int f = wi / (EPB * NF);
+      const int rem = wi - f * (EPB * NF);
+      const int fle = rem / NF, pt = rem - fle * NF;
+      const int fe = blockIdx.x * EPB + fle, fel = fe - geo.e0;
+      if (fe >= prm.nE || fel >= geo.nE) continue;
+      int ec[3];
+      ec[0] = fel % geo.n[0];
+      ec[1] = (fel / geo.n[0]) % geo.n[1];
+      ec[2] = fel / (geo.n[0] * geo.n[1]);
+      V* const sst = smem + fle * PER_ELEM;
+      V* const sdir = sst + NV * NN;
+      V* const sface = sdir + NV * NN + DIM * NV * NN;
+      V* const sjump = sface + 2 * DIM * NV * NF;
+      V* const sgc = sjump + (NV == 1 ? 2 * DIM * NF : 0);
+      V* const sfo = sgc + NCH * NN;
+      V* const sfn = sfo + 2 * DIM * NCH * NF;
+      V* const sfd = sfn + 2 * DIM * NCH * NF;
+      {
         using FF = FaceFlux<LAW, DIM, P, LGL, V, Job>;
         switch (f) {
           case 0: FF::template run<0, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
@@ -511,11 +532,22 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
     // and the viscous flux F^v (R1) or its linearisation (R2), folded into sG --
     if constexpr (NSV) {
       if (visc) {
+        // stage B over the block's face points in face-major order (as pass 2)
+        for (int wi = threadIdx.x; wi < EPB * 2 * DIM * NF; wi += blockDim.x) {
+          const int f = wi / (EPB * NF);
+          const int rem = wi - f * (EPB * NF);
+          const int fle = rem / NF, pt = rem - fle * NF;
+          const int fe = blockIdx.x * EPB + fle, fel = fe - geo.e0;
+          if (fe >= prm.nE || fel >= geo.nE) continue;
+          V* const fst = smem + fle * PER_ELEM;
+          V* const fface = fst + 2 * NV * NN + DIM * NV * NN;
+          V* const fgc = fface + 2 * DIM * NV * NF + (NV == 1 ? 2 * DIM * NF : 0);
+          V* const ffo = fgc + NCH * NN;
+          V* const ffn = ffo + 2 * DIM * NCH * NF;
+          V* const ffd = ffn + 2 * DIM * NCH * NF;
+          FaceViscSysB<DIM, P, V>::run(prm, geo, r2, f, pt, fgc, sDg, sgp, sgm, ffo, ffn, ffd, fface);
+        }
         if (live) {
-          for (int fp = n; fp < 2 * DIM * NF; fp += NN) {
-            const int f = fp / NF, pt = fp - f * NF;
-            FaceViscSysB<DIM, P, V>::run(prm, geo, r2, f, pt, sgc, sDg, sgp, sgm, sfo, sfn, sfd, sface);
-          }
           const int nch = r2 ? NCH : NG;
           V d[2][DIM][NG], gch[NCH];
 #pragma unroll

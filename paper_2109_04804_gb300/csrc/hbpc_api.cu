@@ -849,13 +849,15 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
 // dot, update + norms, finalisation (krylov.cuh).
 template <typename S>
 void cgs_launch(hbpc_ctx* x, const KrylovT<S>& K) {
-  if (x->coop) {   // one cooperative launch (k_cgs_coop) instead of four
-    const size_t m1 = size_t(K.m + 1);
-    const size_t shm = std::max(m1 * sizeof(double) + m1 * (kVecWarps + 1) * sizeof(typename AccOf<S>::type),
-                                3 * (m1 + 1) * sizeof(double));
-    void* args[] = {const_cast<KrylovT<S>*>(&K)};
+  if (x->coop) {   // one cooperative launch (k_cgs_lowsync) instead of four
+    const size_t shm = cgs_lowsync_smem<S>(K.m);
+    // the halves' norms of the new column feed only the difference-quotient
+    // Jv applied to the basis itself (FP64, nonlinear flux, no preconditioner)
+    int half_norms = (!x->ops.jv_linear && x->sol.pc == HBPC_PC_NONE &&
+                      x->sol.precision != HBPC_PREC_MIXED) ? 1 : 0;
+    void* args[] = {const_cast<KrylovT<S>*>(&K), &half_norms};
     HBPC_RUN(x, HBPC_PHASE_DOT, 1,
-             cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cgs_coop<S>), dim3(x->nblocks),
+             cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cgs_lowsync<S>), dim3(x->nblocks),
                                          dim3(kVecThreads), args, shm, x->stream));
     return;
   }
@@ -1679,14 +1681,13 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
   {   // the fused CGS2 kernel needs every block resident at once
     int coop_attr = 0, per_sm_d = 0, per_sm_f = 0;
     cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, dev);
-    const size_t m1 = size_t(solver->gmres_restart + 1);
-    const size_t shm = std::max(m1 * (kVecWarps + 2), 3 * (m1 + 1)) * sizeof(double);
-    if (shm > 48 * 1024) {
-      cudaFuncSetAttribute(k_cgs_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
-      cudaFuncSetAttribute(k_cgs_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
-    }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, k_cgs_coop<double>, kVecThreads, shm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_cgs_coop<float>, kVecThreads, shm);
+    const size_t shm_d = cgs_lowsync_smem<double>(m), shm_f = cgs_lowsync_smem<float>(m);
+    if (shm_d > 48 * 1024)
+      cudaFuncSetAttribute(k_cgs_lowsync<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_d));
+    if (shm_f > 48 * 1024)
+      cudaFuncSetAttribute(k_cgs_lowsync<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm_f));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_d, k_cgs_lowsync<double>, kVecThreads, shm_d);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_cgs_lowsync<float>, kVecThreads, shm_f);
     cudaGetLastError();
     x->coop_max_blocks = std::min(per_sm_d, per_sm_f) * sms;
     x->coop = coop_attr && x->coop_max_blocks >= x->nblocks;
@@ -1729,7 +1730,7 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
       free_all(x); delete x; return e;
     }
   }
-  if ((e = dmalloc(x, &x->small, nsmall)) || (e = dmalloc(x, &x->partial, size_t(prows) * (2 * m + 4))) ||
+  if ((e = dmalloc(x, &x->small, nsmall)) || (e = dmalloc(x, &x->partial, size_t(prows) * size_t(cgs_stride(m)))) ||
       (e = dmalloc(x, &x->ticket, 1)) || (e = dmalloc(x, &x->st, 1))) {
     g_create_error = x->err;
     free_all(x); delete x; return e;

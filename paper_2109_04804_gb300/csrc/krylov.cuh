@@ -134,7 +134,7 @@ __device__ __forceinline__ void finalize_column(const KrylovT<S>& K, double nq2,
 // Partial layout: row b of K.partial holds P0 / P2 in columns [0, m+1) and
 // [m+1, 2m+2), P3 in the two columns after.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int cgs_stride(int m) { return 2 * (m + 1) + 2; }
+__device__ __host__ __forceinline__ int cgs_stride(int m) { return 2 * (m + 1) + 4; }
 
 // Block-redundant reduction of partial columns [col0, col0 + cnt) into shared
 // s_out (times vscale when given).  Warp w handles columns w, w + 8, ..
@@ -272,25 +272,129 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
   finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
 }
 
-// One pass of the cooperative CGS2 kernel over the block's tiles of the new
-// vector q = V_{j+1}: q -= sum_i c_i V_i (UPDATE, coefficients c already in the
-// accumulation type), then either the dot products with V_0..V_{cnt-1} (DOTS,
-// to partial[b][col_out + i]) or the squared norms of the W and sigma halves
-// (to partial[b][col_out], [col_out + 1]); QQ adds |q|^2 to partial[b][qq_col].
-// The hot loop has no FP64 instruction for an FP32 basis (GB300 runs FP64 at
-// 1/64 of the FP32 rate); only the cross-warp sums are FP64.
-template <typename S, bool UPDATE, bool DOTS, bool QQ>
-__device__ __forceinline__ void coop_pass(const KrylovT<S>& K, S* q, int cnt, const typename AccOf<S>::type* s_c,
-                                          typename AccOf<S>::type* s_red, int col_out, int qq_col) {
+// ---------------------------------------------------------------------------
+// One Arnoldi column with one grid-wide barrier in the common case.
+//
+// Classical Gram-Schmidt needs <q, V_i> for i <= j and, for the Hessenberg
+// entry H(j+1, j), the norm of q - sum h_i v_i.  With an orthonormal basis that
+// norm follows from |q|^2 and the coefficients (Pythagoras):
+//     |q - V h|^2 = |q|^2 - |h|^2,
+// accurate to rounding whenever no cancellation has happened, i.e. exactly when
+// the DGKS test |q|^2 - |h|^2 >= |q|^2 / 2 says that no second pass is needed.
+// So the column is
+//   pass 1: block partials of <q, V_i> and |q|^2                 grid barrier
+//   every block: h (the same sums in the same order in every block), DGKS test
+//   common case:  block 0 closes the column (H(:, j) = h, H(j+1, j) from
+//                 Pythagoras, Givens rotation, residual, stopping test) while
+//                 every block applies q -= sum h_i v_i to its rows
+//   re-orthogonalisation (DGKS): q -= V h with second-pass partials of
+//                 <q', V_i> and |q'|^2                           grid barrier
+//                 block 0 closes the column with H(:, j) = h + c and
+//                 H(j+1, j)^2 = |q'|^2 - |c|^2; every block applies q' -= V c.
+// The norms of the two halves of the new vector (needed only by the
+// difference-quotient Jv without a preconditioner, half_norms != 0) are summed
+// by the last block to finish (ticket, no waiting).
+// Partial layout per block row (stride cgs_stride(m) = 2 m + 6): pass-1 dots
+// [0, m + 1), |q|^2 at m + 1, pass-2 dots [m + 2, 2 m + 3), |q'|^2 at 2 m + 3,
+// half norms at 2 m + 4 and 2 m + 5.
+// Dot products are summed per thread over the block's rows for chunks of C
+// columns, then across the warp with a transposed butterfly (C - 1 + 5 -
+// log2 C exchanges per lane instead of 5 C), then across warps and blocks in
+// FP64 in a fixed order.
+// ---------------------------------------------------------------------------
+
+// Transposed warp sum of C per-lane partials a[0..C): afterwards a[0] of lane
+// l holds the warp total of column l / (32 / C) (the same value in the 32 / C
+// lanes of that column).  C is a power of two, 1 <= C <= 32.
+template <int K, int O, typename A>
+struct TransposeSum {
+  __device__ __forceinline__ static void run(A* a, int lane) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      const A send = up ? a[i] : a[i + K / 2];
+      const A keep = up ? a[i + K / 2] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+    TransposeSum<K / 2, O / 2, A>::run(a, lane);
+  }
+};
+template <int O, typename A>
+struct TransposeSum<1, O, A> {
+  __device__ __forceinline__ static void run(A* a, int) {
+#pragma unroll
+    for (int o = O; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+  }
+};
+
+constexpr int kCgsChunk = 16;   // columns per transposed reduction
+
+// Block partials of <q, V_i> for i in [0, cnt) into s_w[warp * ldw + i]
+// (per-warp totals), and of |q|^2 into s_qq[warp] when QQ.
+template <typename S, bool QQ>
+__device__ __forceinline__ void lowsync_dots(const KrylovT<S>& K, const S* q, int cnt, double* s_w, int ldw,
+                                             double* s_qq) {
   using A = typename AccOf<S>::type;
-  const int stride = cgs_stride(K.m);
+  constexpr int C = kCgsChunk, L = 32 / C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ double s_w[3][kVecWarps];
-  if (DOTS)
-    for (int t = threadIdx.x; t < cnt * kVecWarps; t += blockDim.x) s_red[t] = A(0);
-  __syncthreads();
-  A aw = A(0), as = A(0), qq = A(0);
   const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  A qq = A(0);
+  for (int c0 = 0; c0 < cnt; c0 += C) {
+    const int nc = cnt - c0 < C ? cnt - c0 : C;
+    A acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = A(0);
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const size_t base = tile * kTile + threadIdx.x;
+      A x[kRows];
+      bool in[kRows];
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const size_t row = base + size_t(r) * kVecThreads;
+        in[r] = row < K.n2;
+        x[r] = in[r] ? A(q[row]) : A(0);
+      }
+      if (QQ && c0 == 0)
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) qq += x[r] * x[r];
+      const S* V0 = K.V + size_t(c0) * K.ld + base;
+      if (nc == C) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int r = 0; r < kRows; ++r)
+            if (in[r]) acc[c] += x[r] * A(V0[size_t(c) * K.ld + size_t(r) * kVecThreads]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          if (c < nc)
+#pragma unroll
+            for (int r = 0; r < kRows; ++r)
+              if (in[r]) acc[c] += x[r] * A(V0[size_t(c) * K.ld + size_t(r) * kVecThreads]);
+      }
+    }
+    TransposeSum<C, 16, A>::run(acc, lane);
+    if ((lane % L) == 0) {
+      const int c = c0 + lane / L;
+      if (c < cnt) s_w[warp * ldw + c] = double(acc[0]);
+    }
+  }
+  if (QQ) {
+    qq = warp_sum(qq);
+    if (lane == 0) s_qq[warp] = double(qq);
+  }
+}
+
+// q -= sum_{i < cnt} s_c[i] V_i over the block's rows (coefficients already in
+// the accumulation type and scaled for the unscaled columns); with HALF the
+// squared norms of the two halves of the result into s_n[0][warp], s_n[1][warp].
+template <typename S, bool HALF>
+__device__ __forceinline__ void lowsync_update(const KrylovT<S>& K, S* q, int cnt,
+                                               const typename AccOf<S>::type* s_c, double (*s_n)[kVecWarps]) {
+  using A = typename AccOf<S>::type;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t ntiles = (K.n2 + kTile - 1) / kTile;
+  A aw = A(0), as = A(0);
   for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const size_t base = tile * kTile + threadIdx.x;
     A x[kRows];
@@ -301,133 +405,202 @@ __device__ __forceinline__ void coop_pass(const KrylovT<S>& K, S* q, int cnt, co
       in[r] = row < K.n2;
       x[r] = in[r] ? A(q[row]) : A(0);
     }
-    if (UPDATE) {
-      col_axpy_c(K.V, K.ld, base, x, in, cnt, s_c);
+    col_axpy_c(K.V, K.ld, base, x, in, cnt, s_c);
 #pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const size_t row = base + size_t(r) * kVecThreads;
-        if (in[r]) {
-          q[row] = S(x[r]);
-          if (row < K.half) aw += x[r] * x[r]; else as += x[r] * x[r];
-        }
+    for (int r = 0; r < kRows; ++r) {
+      const size_t row = base + size_t(r) * kVecThreads;
+      if (in[r]) {
+        q[row] = S(x[r]);
+        if (HALF) { if (row < K.half) aw += x[r] * x[r]; else as += x[r] * x[r]; }
       }
     }
-    if (QQ)
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) qq += x[r] * x[r];
-    if (DOTS) col_dots<true>(K.V, K.ld, base, x, in, cnt, s_red);
   }
-  aw = warp_sum(aw); as = warp_sum(as); qq = warp_sum(qq);
-  if (lane == 0) { s_w[0][warp] = double(aw); s_w[1][warp] = double(as); s_w[2][warp] = double(qq); }
+  if (HALF) {
+    aw = warp_sum(aw);
+    as = warp_sum(as);
+    if (lane == 0) { s_n[0][warp] = double(aw); s_n[1][warp] = double(as); }
+  }
+}
+
+// Block 0 closes column j: H(0..j, j) = hcol[0..j] (in shared memory),
+// H(j+1, j) = hnext, vscale[j+1] = 1 / hnext, previous rotations, the new
+// rotation, residual and stopping decision.  hcol has m + 2 entries; scs,
+// ssn m + 1 each (shared).
+template <typename S>
+__device__ __forceinline__ void lowsync_close(const KrylovT<S>& K, int j, double* hcol, double hnext, double* scs,
+                                              double* ssn) {
+  GmresState* st = K.st;
+  const int ldh = K.m + 1;
+  double* Hj = K.H + size_t(j) * ldh;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) { scs[i] = K.cs[i]; ssn[i] = K.sn[i]; }
   __syncthreads();
-  double* prow = K.partial + size_t(blockIdx.x) * stride;
-  if (DOTS) {
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      double t = 0.0;
-      for (int w = 0; w < kVecWarps; ++w) t += double(s_red[i * kVecWarps + w]);
-      prow[col_out + i] = t;
+  if (threadIdx.x == 0) {
+    hcol[j + 1] = hnext;
+    K.vscale[j + 1] = hnext > 0.0 ? 1.0 / hnext : 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double t = scs[i] * hcol[i] + ssn[i] * hcol[i + 1];
+      hcol[i + 1] = -ssn[i] * hcol[i] + scs[i] * hcol[i + 1];
+      hcol[i] = t;
     }
-  } else if (threadIdx.x == 0) {
-    double ta = 0.0, tb = 0.0;
-    for (int w = 0; w < kVecWarps; ++w) { ta += s_w[0][w]; tb += s_w[1][w]; }
-    prow[col_out] = ta;
-    prow[col_out + 1] = tb;
+    const double den = hypot(hcol[j], hcol[j + 1]);
+    const double c = den > 0.0 ? hcol[j] / den : 1.0, s = den > 0.0 ? hcol[j + 1] / den : 0.0;
+    K.cs[j] = c; K.sn[j] = s;
+    hcol[j] = den; hcol[j + 1] = 0.0;
+    const double gj = K.g[j];
+    K.g[j + 1] = -s * gj;
+    K.g[j] = c * gj;
+    st->resid = fabs(K.g[j + 1]);
+    st->its += 1;
+    st->j = j + 1;
+    st->reorth = 0;
+    const bool ok = st->resid <= st->target;
+    const bool brk = !(hnext > 0.0);
+    st->breakdown = brk ? 1 : 0;
+    st->converged = (ok || brk) ? 1 : 0;
+    st->done = (ok || brk || st->j >= K.m || st->its >= st->max_its) ? 1 : 0;
   }
-  if (QQ && threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kVecWarps; ++w) t += s_w[2][w];
-    prow[qq_col] = t;
-  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hj[i] = hcol[i];
 }
 
-// Sum of the blocks' partials of columns [col0, col0 + cnt) into out[c] (times
-// scale[c] when given), one warp per column spread over the blocks (the
-// reduction is done once, not redundantly by every block).
+// Half norms of the new vector: block partials, the last block sums them into
+// nrmW[j + 1], nrmS[j + 1].
 template <typename S>
-__device__ __forceinline__ void coop_reduce(const KrylovT<S>& K, int col0, int cnt, const double* scale,
-                                            double* out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void lowsync_half_norms(const KrylovT<S>& K, int j, double (*s_n)[kVecWarps]) {
   const int stride = cgs_stride(K.m);
-  for (int c = blockIdx.x * kVecWarps + warp; c < cnt; c += gridDim.x * kVecWarps) {
-    const double t = strided_sum(K.partial + col0 + c, stride, lane, K.nblocks);
-    if (lane == 0) out[c] = scale ? t * scale[c] : t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) { ta += s_n[0][w]; tb += s_n[1][w]; }
+    K.partial[size_t(blockIdx.x) * stride + 2 * K.m + 4] = ta;
+    K.partial[size_t(blockIdx.x) * stride + 2 * K.m + 5] = tb;
+  }
+  if (!last_block(K.ticket, K.nblocks)) return;
+  if (threadIdx.x < 64) {
+    const int w = threadIdx.x >> 5;
+    const double t = strided_sum(K.partial + 2 * K.m + 4 + w, stride, threadIdx.x & 31, K.nblocks);
+    if ((threadIdx.x & 31) == 0) (w == 0 ? K.nrmW : K.nrmS)[j + 1] = sqrt(t);
   }
 }
 
-// One Arnoldi column in one cooperative launch (kernel boundaries replaced by
-// grid-wide barriers): classical Gram-Schmidt, a second pass only when the DGKS
-// test asks for it (|q - sum h_i v_i| < |q| / sqrt 2; the four-kernel form
-// always runs it), the Hessenberg column, Givens rotation and stopping test.
-// Every reduction across blocks is done once by one warp per column (written to
-// hc) and read back by all after a barrier.  Launched with
-// cudaLaunchCooperativeKernel, which refuses a grid that cannot be resident.
-// The early exit and the column index are read before any block writes the
-// state (block 0 writes it after the last barrier), so they are grid-uniform,
-// and so is the DGKS decision (every block reads the same reduced values).
-// Dynamic shared memory: max((m + 1) doubles + (m + 1)(kVecWarps + 1)
-// accumulation values, 3 (m + 2) doubles).
+// Dynamic shared memory of k_cgs_lowsync: per-warp dot totals [kVecWarps][m+1],
+// coefficients h [m + 2] and c [m + 1] (FP64), update coefficients [m + 1] (A),
+// rotation scratch 2 (m + 1).
 template <typename S>
-__global__ void __launch_bounds__(kVecThreads) k_cgs_coop(KrylovT<S> K) {
+constexpr size_t cgs_lowsync_smem(int m) {
+  return (size_t(kVecWarps) * (m + 1) + (m + 2) + (m + 1) + 2 * (m + 1)) * sizeof(double) +
+         size_t(m + 1) * sizeof(typename AccOf<S>::type);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, int half_norms) {
   using A = typename AccOf<S>::type;
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   GmresState* st = K.st;
-  if (st->done) return;
+  if (st->done) return;                     // read by every block before block 0 writes it
   const int j = st->j, cnt = j + 1, m = K.m;
+  const int stride = cgs_stride(m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   extern __shared__ double sm[];
-  double* s_h = sm;                                   // [m + 1] reduced coefficients
-  A* s_red = reinterpret_cast<A*>(s_h + (m + 1));     // [m + 1][kVecWarps]
-  A* s_c = s_red + size_t(m + 1) * kVecWarps;         // [m + 1] update coefficients
-  __shared__ int s_flag;
-  __shared__ double s_qq;
+  double* s_w = sm;                                   // [kVecWarps][m + 1]
+  double* s_h = s_w + size_t(kVecWarps) * (m + 1);    // [m + 2]
+  double* s_c2 = s_h + (m + 2);                       // [m + 1]
+  double* scs = s_c2 + (m + 1);                       // [m + 1]
+  double* ssn = scs + (m + 1);                        // [m + 1]
+  A* s_c = reinterpret_cast<A*>(ssn + (m + 1));       // [m + 1]
+  __shared__ double s_qq[kVecWarps];
+  __shared__ double s_n[2][kVecWarps];
+  __shared__ double s_tot[2];                         // |q|^2 (or |q'|^2), |h|^2 (or |c|^2)
+  __shared__ int s_reorth;
   S* q = K.V + size_t(j + 1) * K.ld;
-  // pass 1: <q, V_i> and |q|^2
-  coop_pass<S, false, true, true>(K, q, cnt, s_c, s_red, 0, 2 * m + 1);
-  grid.sync();
-  // h_i = vscale_i <q, V_i> into hc[0..cnt), |q|^2 into hc[m + 1]
-  coop_reduce(K, 0, cnt, K.vscale, K.hc);
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 32) {
-    const double t = strided_sum(K.partial + 2 * m + 1, cgs_stride(m), threadIdx.x, K.nblocks);
-    if (threadIdx.x == 0) K.hc[m + 1] = t;
+  double* prow = K.partial + size_t(blockIdx.x) * stride;
+
+  // pass 1: <q, V_i>, |q|^2
+  lowsync_dots<S, true>(K, q, cnt, s_w, m + 1, s_qq);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) t += s_w[w * (m + 1) + i];
+    prow[i] = t;
+  }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) t += s_qq[w];
+    prow[m + 1] = t;
   }
   grid.sync();
-  // the reduced values into shared memory in one parallel round trip
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_h[i] = __ldcg(K.hc + i);
-  if (threadIdx.x == 0) s_qq = __ldcg(K.hc + m + 1);
+  // h_i = vscale_i <q, V_i> and |q|^2, summed identically in every block
+  for (int c = warp; c <= cnt; c += kVecWarps) {
+    const int col = c < cnt ? c : m + 1;
+    const double t = strided_sum(K.partial + col, stride, lane, K.nblocks);
+    if (lane == 0) {
+      if (c < cnt) s_h[c] = t * K.vscale[c];
+      else s_tot[0] = t;
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double hh = 0.0;
     for (int i = 0; i < cnt; ++i) hh += s_h[i] * s_h[i];
-    s_flag = (s_qq - hh) < 0.5 * s_qq ? 1 : 0;
+    s_tot[1] = hh;
+    s_reorth = (s_tot[0] - hh) < 0.5 * s_tot[0] ? 1 : 0;
   }
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(s_h[i] * K.vscale[i]);
   __syncthreads();
-  if (!s_flag) {
-    coop_pass<S, true, false, false>(K, q, cnt, s_c, s_red, 2 * (m + 1), 0);   // the only update
-    if (blockIdx.x == 0)
-      for (int i = threadIdx.x; i < cnt; i += blockDim.x) K.hc[(m + 2) + i] = 0.0;
-    grid.sync();
-  } else {
-    coop_pass<S, true, true, false>(K, q, cnt, s_c, s_red, m + 1, 0);          // update + second dots
-    grid.sync();
-    coop_reduce(K, m + 1, cnt, K.vscale, K.hc + (m + 2));
-    grid.sync();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(__ldcg(K.hc + (m + 2) + i) * K.vscale[i]);
-    __syncthreads();
-    coop_pass<S, true, false, false>(K, q, cnt, s_c, s_red, 2 * (m + 1), 0);   // second update + norms
-    grid.sync();
+  if (!s_reorth) {
+    if (blockIdx.x == 0) lowsync_close(K, j, s_h, sqrt(s_tot[0] - s_tot[1]), scs, ssn);
+    if (half_norms) {
+      lowsync_update<S, true>(K, q, cnt, s_c, s_n);
+      lowsync_half_norms(K, j, s_n);
+    } else {
+      lowsync_update<S, false>(K, q, cnt, s_c, s_n);
+    }
+    return;
   }
-  if (blockIdx.x != 0) return;
-  __shared__ double nrm[2];
-  if (threadIdx.x < 64) {
-    const int w = threadIdx.x >> 5;
-    const double t = strided_sum(K.partial + 2 * (m + 1) + w, cgs_stride(m), threadIdx.x & 31, K.nblocks);
-    if ((threadIdx.x & 31) == 0) nrm[w] = t;
-  }
-  double* Hj = K.H + size_t(j) * (m + 1);
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) Hj[i] = __ldcg(K.hc + i) + __ldcg(K.hc + (m + 2) + i);
+  // second pass (DGKS): q' = q - V h, then <q', V_i>, |q'|^2
+  lowsync_update<S, false>(K, q, cnt, s_c, s_n);
+  lowsync_dots<S, true>(K, q, cnt, s_w, m + 1, s_qq);
   __syncthreads();
-  finalize_column(K, nrm[0] + nrm[1], nrm[0], nrm[1], sm);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) t += s_w[w * (m + 1) + i];
+    prow[m + 2 + i] = t;
+  }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kVecWarps; ++w) t += s_qq[w];
+    prow[2 * m + 3] = t;
+  }
+  grid.sync();
+  for (int c = warp; c <= cnt; c += kVecWarps) {
+    const int col = c < cnt ? m + 2 + c : 2 * m + 3;
+    const double t = strided_sum(K.partial + col, stride, lane, K.nblocks);
+    if (lane == 0) {
+      if (c < cnt) s_c2[c] = t * K.vscale[c];
+      else s_tot[0] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cc = 0.0;
+    for (int i = 0; i < cnt; ++i) cc += s_c2[i] * s_c2[i];
+    s_tot[1] = cc;
+  }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(s_c2[i] * K.vscale[i]);
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_h[i] += s_c2[i];
+    __syncthreads();
+    const double r2 = s_tot[0] - s_tot[1];
+    lowsync_close(K, j, s_h, r2 > 0.0 ? sqrt(r2) : 0.0, scs, ssn);
+  }
+  if (half_norms) {
+    lowsync_update<S, true>(K, q, cnt, s_c, s_n);
+    lowsync_half_norms(K, j, s_n);
+  } else {
+    lowsync_update<S, false>(K, q, cnt, s_c, s_n);
+  }
 }
 
 // y = R^-1 g over the j columns of the finished cycle; y_i *= vscale_i.  One

@@ -149,6 +149,10 @@ struct PcApplyT {
   int nb, nE;
   int shared;                   // 1: every element uses block 0 (a state- and
                                 // element-independent J_i, see pc_build)
+  // shared block only: J_0 as a Kronecker sum of 1-D p x p factors
+  // (kron[m][i][l], row-major, direction m), valid when *kron_ok != 0
+  const S* kron; const int* kron_ok;
+  int P, dim;
 };
 using PcApply = PcApplyT<double>;
 

@@ -270,6 +270,63 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   }
 }
 
+// The element Jacobian of linear advection (with or without its viscous term)
+// on a Cartesian element acts along each direction separately: J = sum_m
+// I (x) .. (x) A_m (x) .. (x) I, one p x p factor A_m per direction m (the 1-D
+// operator of Eq. 12 along x_m, its own-trace face terms included).  This
+// kernel (one block) reads the factors off the assembled dense J_0 (column-
+// major, node index i_0 + p i_1 + p^2 i_2): off-diagonal entries of A_m from
+// the line through node 0 along x_m, diagonals split as A_0(i, i) = J(i, i)
+// and A_m(i, i) = J(i p^m, i p^m) - J(0, 0) for m > 0.  It then rebuilds every
+// entry of J_0 from the factors and sets *ok only if all agree with the
+// assembled block to rounding (tol times max |J_0|), so the apply falls back
+// to the dense J_0 for anything that is not a Kronecker sum.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pc_kron_factors(const T* __restrict__ J, int nb, int P, int dim, T tol,
+                                                         T* __restrict__ A, int* ok) {
+  __shared__ T sA[3 * 8 * 8];
+  __shared__ T s_red[2][256 / 32];
+  const int pp = P * P;
+  for (int t = threadIdx.x; t < dim * pp; t += blockDim.x) {
+    const int m = t / pp, i = (t / P) % P, l = t % P;
+    int st = 1;
+    for (int k = 0; k < m; ++k) st *= P;
+    T a = J[size_t(l * st) * nb + size_t(i * st)];
+    if (i == l && m > 0) a -= J[0];
+    sA[t] = a;
+    A[t] = a;
+  }
+  __syncthreads();
+  T dmax = T(0), jmax = T(0);
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int c = t / nb, r = t - c * nb;
+    int rr = r, cc = c;
+    int rd[3] = {0, 0, 0}, cd[3] = {0, 0, 0};
+    for (int m = 0; m < dim; ++m) { rd[m] = rr % P; rr /= P; cd[m] = cc % P; cc /= P; }
+    T rec = T(0);
+    for (int m = 0; m < dim; ++m) {
+      bool same = true;
+      for (int k = 0; k < dim; ++k)
+        if (k != m && rd[k] != cd[k]) same = false;
+      if (same) rec += sA[m * pp + rd[m] * P + cd[m]];
+    }
+    const T jv = J[t];
+    dmax = fmax(dmax, fabs(rec - jv));
+    jmax = fmax(jmax, fabs(jv));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    jmax = fmax(jmax, __shfl_xor_sync(0xffffffffu, jmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) { s_red[0][threadIdx.x >> 5] = dmax; s_red[1][threadIdx.x >> 5] = jmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T d = T(0), jm = T(0);
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { d = fmax(d, s_red[0][w]); jm = fmax(jm, s_red[1][w]); }
+    *ok = (d <= tol * jm) ? 1 : 0;
+  }
+}
+
 // P^-1 with one block for all elements (PcApplyT::shared): the same algebra as
 // k_pc_apply, organised as the small dense products they are.  M and J live in
 // shared memory; a thread owns row r of EG elements, so every loaded entry of M
@@ -293,7 +350,15 @@ __global__ void __launch_bounds__(256) k_pc_apply_shared(PcApplyT<S> a) {
   S* Xs = Xw + groups * gsz;
   S* U = Xs + groups * gsz;
   S* Vv = U + groups * gsz;
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) { sM[t] = a.M[t]; sJ[t] = a.J[t]; }
+  // J as Kronecker factors when they reproduce it (k_pc_kron_factors), kept
+  // in the sJ slot
+  const bool kron = a.kron && *a.kron_ok;
+  S* const sK = sJ;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) sM[t] = a.M[t];
+  if (kron)
+    for (int t = threadIdx.x; t < a.dim * a.P * a.P; t += blockDim.x) sK[t] = a.kron[t];
+  else
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) sJ[t] = a.J[t];
   const long long e0 = (long long)blockIdx.x * groups * EG;   // first element of the block
   const size_t off = (a.jidx ? size_t(*a.jidx) * a.ld : 0);
   const S sc = S(a.scale ? (a.jidx ? a.scale[*a.jidx] : *a.scale) : 1.0);
@@ -334,10 +399,30 @@ __global__ void __launch_bounds__(256) k_pc_apply_shared(PcApplyT<S> a) {
   for (int k = 0; k < EG; ++k) { ju[k] = S(0); jv[k] = S(0); }
   const S* su = U + g * gsz;
   const S* sv = Vv + g * gsz;
-  for (int c = 0; c < nb; ++c) {
-    const S j = sJ[c * nb + r];
+  if (kron) {
+    // J as a Kronecker sum: along each direction m the p values of row r's
+    // line through x_m (d p multiply-adds per row instead of n_b)
+    const int P = a.P;
+    int st = 1, rr = r;
+    for (int m = 0; m < a.dim; ++m) {
+      const int im = rr % P;
+      rr /= P;
+      const int b0 = r - im * st;
+      const S* Arow = sK + (m * P + im) * P;
+      for (int l = 0; l < P; ++l) {
+        const S am = Arow[l];
+        const int c = b0 + l * st;
 #pragma unroll
-    for (int k = 0; k < EG; ++k) { ju[k] += j * su[c * EG + k]; jv[k] += j * sv[c * EG + k]; }
+        for (int k = 0; k < EG; ++k) { ju[k] += am * su[c * EG + k]; jv[k] += am * sv[c * EG + k]; }
+      }
+      st *= P;
+    }
+  } else {
+    for (int c = 0; c < nb; ++c) {
+      const S j = sJ[c * nb + r];
+#pragma unroll
+      for (int k = 0; k < EG; ++k) { ju[k] += j * su[c * EG + k]; jv[k] += j * sv[c * EG + k]; }
+    }
   }
   const S c1 = S(a.c12[0]), c2 = S(a.c12[1]);
 #pragma unroll

@@ -218,6 +218,10 @@ struct hbpc_ctx {
   // for every state, so one J, one S^-1 serve the whole mesh
   bool pc_shared = false;
   double pc_c1 = 0.0, pc_c2 = 0.0;
+  // the shared block's J as 1-D Kronecker factors (k_pc_kron_factors)
+  double* kron_d = nullptr;
+  float* kron_f = nullptr;
+  int* kron_ok = nullptr;
   // mixed precision (FP32 Krylov loop, FP64 Newton)
   DGParams<float> prmf{};
   KrylovT<float> Kf{};
@@ -503,6 +507,7 @@ hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const doubl
   a.zn = x->ops.jv_linear ? nullptr : x->zn;   // ||z|| halves feed eps_FD of Eq. 23 only
   a.nb = x->nb; a.nE = int(x->nE);
   a.shared = x->pc_shared ? 1 : 0;
+  a.kron = x->pc_shared ? x->kron_d : nullptr; a.kron_ok = x->kron_ok; a.P = x->P; a.dim = x->dim;
   if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<double><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply");
@@ -521,6 +526,7 @@ hbpc_status pc_apply_f(hbpc_ctx* x, const float* in, const int* jidx, const doub
   a.zn = nullptr;   // the analytic FP32 Jv needs no norms
   a.nb = x->nb; a.nE = int(x->nE);
   a.shared = x->pc_shared ? 1 : 0;
+  a.kron = x->pc_shared ? x->kron_f : nullptr; a.kron_ok = x->kron_ok; a.P = x->P; a.dim = x->dim;
   if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<float><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply<float>");
@@ -820,6 +826,23 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
              k_pc_invert<double><<<nEb, 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
                  x->Mpc, x->nb, nEb, x->singular));
+  }
+  if (x->pc_shared && x->kron_ok) {
+    // the shared J_0 as Kronecker factors for the apply (checked entry by entry)
+    int nn = 1;
+    for (int m = 0; m < x->dim; ++m) nn *= x->P;
+    if (nn == x->nb && x->P <= kMaxP) {
+      if (mixed)
+        HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+                 k_pc_kron_factors<float><<<1, 256, 0, x->stream>>>(x->Jf, x->nb, x->P, x->dim, 1e-5f, x->kron_f,
+                                                                    x->kron_ok));
+      else
+        HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+                 k_pc_kron_factors<double><<<1, 256, 0, x->stream>>>(x->Jpc, x->nb, x->P, x->dim, 1e-12, x->kron_d,
+                                                                     x->kron_ok));
+    } else {
+      HBPC_CK(x, cudaMemsetAsync(x->kron_ok, 0, sizeof(int), x->stream));
+    }
   }
   if (collecting && x->lp.Tbuf) {   // the block inverses as training targets
     auto& L = x->lp;
@@ -1424,6 +1447,7 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->Wn); cudaFree(x->X); cudaFree(x->G); cudaFree(x->r1); cudaFree(x->r2);
   cudaFree(x->dX); cudaFree(x->bvec); cudaFree(x->stage); cudaFree(x->V); cudaFree(x->small);
   cudaFree(x->partial); cudaFree(x->ticket); cudaFree(x->st);
+  cudaFree(x->kron_d); cudaFree(x->kron_f); cudaFree(x->kron_ok);
   cudaFree(x->Jpc); cudaFree(x->Mpc); cudaFree(x->Z); cudaFree(x->singular);
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
   cudaFree(x->vtab_d); cudaFree(x->vtab_f); cudaFree(x->vloc_d);
@@ -1447,7 +1471,8 @@ hbpc_status pc_alloc(hbpc_ctx* x) {
   const size_t blk = size_t(x->nE) * x->nb * x->nb, n2 = size_t(2 * x->ndof);
   hbpc_status e;
   if ((e = dmalloc(x, &x->Jpc, blk)) || (e = dmalloc(x, &x->Mpc, blk)) || (e = dmalloc(x, &x->Z, n2)) ||
-      (e = dmalloc(x, &x->singular, 1)))
+      (e = dmalloc(x, &x->singular, 1)) || (e = dmalloc(x, &x->kron_d, 3 * kMaxP * kMaxP)) ||
+      (e = dmalloc(x, &x->kron_f, 3 * kMaxP * kMaxP)) || (e = dmalloc(x, &x->kron_ok, 1)))
     return e;
   HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
   const size_t nbz = size_t(x->nb);
@@ -1675,7 +1700,9 @@ hbpc_status ctx_finish(hbpc_ctx* x) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  x->nblocks = std::max(1, std::min<int>(2 * sms, int((n2 + 1023) / 1024)));
+  // one block per tile up to two per SM, plus one when the tiles run out first:
+  // the Arnoldi column's closing block then has no rows of its own
+  x->nblocks = std::max(1, std::min<int>(2 * sms, int((n2 + 1023) / 1024) + 1));
   x->nb = int(x->ndof / x->nE);
   pc_launch_config(x);
   {   // the fused CGS2 kernel needs every block resident at once
@@ -1831,8 +1858,9 @@ hbpc_status autotune(hbpc_ctx* x, hbpc_tuning* out) {
   std::vector<int> kc;
   for (int c = 1; c <= 4; ++c) kc.push_back(c * x->sms);
   for (int d = 1; d <= 3; ++d) kc.push_back((std::max(1, tiles) + d - 1) / d);
+  kc.push_back(tiles + 1);   // every block one tile, plus the closing block
   for (int& v : kc) {
-    v = std::min(v, std::max(1, tiles));
+    v = std::min(v, std::max(1, tiles) + 1);
     if (x->coop) v = std::min(v, x->coop_max_blocks);
     v = std::max(v, 1);
   }

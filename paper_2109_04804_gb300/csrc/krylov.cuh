@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
 }
 
 // ---------------------------------------------------------------------------
-// One Arnoldi column with one grid-wide barrier in the common case.
+// One Arnoldi column with two grid-wide barriers in the common case.
 //
 // Classical Gram-Schmidt needs <q, V_i> for i <= j and, for the Hessenberg
 // entry H(j+1, j), the norm of q - sum h_i v_i.  With an orthonormal basis that
@@ -283,13 +283,14 @@ __global__ void __launch_bounds__(kVecThreads) k_cgs_finalize(KrylovT<S> K) {
 // the DGKS test |q|^2 - |h|^2 >= |q|^2 / 2 says that no second pass is needed.
 // So the column is
 //   pass 1: block partials of <q, V_i> and |q|^2                 grid barrier
-//   every block: h (the same sums in the same order in every block), DGKS test
-//   common case:  block 0 closes the column (H(:, j) = h, H(j+1, j) from
+//   the sums over the blocks, one warp per sum over the grid      grid barrier
+//   every block reads h and |q|^2 back and takes the DGKS test (grid-uniform)
+//   common case:  the last block closes the column (H(:, j) = h, H(j+1, j) from
 //                 Pythagoras, Givens rotation, residual, stopping test) while
 //                 every block applies q -= sum h_i v_i to its rows
 //   re-orthogonalisation (DGKS): q -= V h with second-pass partials of
-//                 <q', V_i> and |q'|^2                           grid barrier
-//                 block 0 closes the column with H(:, j) = h + c and
+//                 <q', V_i> and |q'|^2, summed the same way   two grid barriers
+//                 the last block closes the column with H(:, j) = h + c and
 //                 H(j+1, j)^2 = |q'|^2 - |c|^2; every block applies q' -= V c.
 // The norms of the two halves of the new vector (needed only by the
 // difference-quotient Jv without a preconditioner, half_norms != 0) are summed
@@ -422,7 +423,7 @@ __device__ __forceinline__ void lowsync_update(const KrylovT<S>& K, S* q, int cn
   }
 }
 
-// Block 0 closes column j: H(0..j, j) = hcol[0..j] (in shared memory),
+// One block closes column j: H(0..j, j) = hcol[0..j] (in shared memory),
 // H(j+1, j) = hnext, vscale[j+1] = 1 / hnext, previous rotations, the new
 // rotation, residual and stopping decision.  hcol has m + 2 entries; scs,
 // ssn m + 1 each (shared).
@@ -483,6 +484,20 @@ __device__ __forceinline__ void lowsync_half_norms(const KrylovT<S>& K, int j, d
   }
 }
 
+// Sums over the blocks of partial columns [col0, col0 + cnt) and of column
+// colq, one warp per sum, the warps of the whole grid sharing the work; the
+// results go to hc at the same column indices (hc[col0 + i], hc[colq]).
+template <typename S>
+__device__ __forceinline__ void lowsync_reduce(const KrylovT<S>& K, int col0, int cnt, int colq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stride = cgs_stride(K.m);
+  for (int c = blockIdx.x * kVecWarps + warp; c <= cnt; c += gridDim.x * kVecWarps) {
+    const int col = c < cnt ? col0 + c : colq;
+    const double t = strided_sum(K.partial + col, stride, lane, K.nblocks);
+    if (lane == 0) K.hc[col] = t;
+  }
+}
+
 // Dynamic shared memory of k_cgs_lowsync: per-warp dot totals [kVecWarps][m+1],
 // coefficients h [m + 2] and c [m + 1] (FP64), update coefficients [m + 1] (A),
 // rotation scratch 2 (m + 1).
@@ -498,10 +513,9 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   GmresState* st = K.st;
-  if (st->done) return;                     // read by every block before block 0 writes it
+  if (st->done) return;                     // read by every block before the closer writes it
   const int j = st->j, cnt = j + 1, m = K.m;
   const int stride = cgs_stride(m);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   extern __shared__ double sm[];
   double* s_w = sm;                                   // [kVecWarps][m + 1]
   double* s_h = s_w + size_t(kVecWarps) * (m + 1);    // [m + 2]
@@ -516,8 +530,17 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
   S* q = K.V + size_t(j + 1) * K.ld;
   double* prow = K.partial + size_t(blockIdx.x) * stride;
 
+  auto dots = [&]() { lowsync_dots<S, true>(K, q, cnt, s_w, m + 1, s_qq); };
+  auto update = [&](bool half) {
+    if (half) {
+      lowsync_update<S, true>(K, q, cnt, s_c, s_n);
+      lowsync_half_norms(K, j, s_n);
+    } else {
+      lowsync_update<S, false>(K, q, cnt, s_c, s_n);
+    }
+  };
   // pass 1: <q, V_i>, |q|^2
-  lowsync_dots<S, true>(K, q, cnt, s_w, m + 1, s_qq);
+  dots();
   __syncthreads();
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     double t = 0.0;
@@ -530,15 +553,12 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
     prow[m + 1] = t;
   }
   grid.sync();
-  // h_i = vscale_i <q, V_i> and |q|^2, summed identically in every block
-  for (int c = warp; c <= cnt; c += kVecWarps) {
-    const int col = c < cnt ? c : m + 1;
-    const double t = strided_sum(K.partial + col, stride, lane, K.nblocks);
-    if (lane == 0) {
-      if (c < cnt) s_h[c] = t * K.vscale[c];
-      else s_tot[0] = t;
-    }
-  }
+  // the cnt + 1 sums over the blocks, one warp each, spread over the grid,
+  // into hc[0, cnt) and hc[m + 1]; then every block reads them back
+  lowsync_reduce(K, 0, cnt, m + 1);
+  grid.sync();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_h[i] = __ldcg(K.hc + i) * K.vscale[i];
+  if (threadIdx.x == 0) s_tot[0] = __ldcg(K.hc + m + 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     double hh = 0.0;
@@ -548,19 +568,17 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
   }
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(s_h[i] * K.vscale[i]);
   __syncthreads();
+  // the last block closes the column (it has no rows, or as many as the
+  // others, depending on the grid the autotuner picked)
+  const bool closer = blockIdx.x == gridDim.x - 1;
   if (!s_reorth) {
-    if (blockIdx.x == 0) lowsync_close(K, j, s_h, sqrt(s_tot[0] - s_tot[1]), scs, ssn);
-    if (half_norms) {
-      lowsync_update<S, true>(K, q, cnt, s_c, s_n);
-      lowsync_half_norms(K, j, s_n);
-    } else {
-      lowsync_update<S, false>(K, q, cnt, s_c, s_n);
-    }
+    if (closer) lowsync_close(K, j, s_h, sqrt(s_tot[0] - s_tot[1]), scs, ssn);
+    update(half_norms != 0);
     return;
   }
   // second pass (DGKS): q' = q - V h, then <q', V_i>, |q'|^2
-  lowsync_update<S, false>(K, q, cnt, s_c, s_n);
-  lowsync_dots<S, true>(K, q, cnt, s_w, m + 1, s_qq);
+  update(false);
+  dots();
   __syncthreads();
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     double t = 0.0;
@@ -573,14 +591,10 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
     prow[2 * m + 3] = t;
   }
   grid.sync();
-  for (int c = warp; c <= cnt; c += kVecWarps) {
-    const int col = c < cnt ? m + 2 + c : 2 * m + 3;
-    const double t = strided_sum(K.partial + col, stride, lane, K.nblocks);
-    if (lane == 0) {
-      if (c < cnt) s_c2[c] = t * K.vscale[c];
-      else s_tot[0] = t;
-    }
-  }
+  lowsync_reduce(K, m + 2, cnt, 2 * m + 3);
+  grid.sync();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c2[i] = __ldcg(K.hc + m + 2 + i) * K.vscale[i];
+  if (threadIdx.x == 0) s_tot[0] = __ldcg(K.hc + 2 * m + 3);
   __syncthreads();
   if (threadIdx.x == 0) {
     double cc = 0.0;
@@ -589,18 +603,13 @@ __global__ void __launch_bounds__(kVecThreads, 2) k_cgs_lowsync(KrylovT<S> K, in
   }
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_c[i] = A(s_c2[i] * K.vscale[i]);
   __syncthreads();
-  if (blockIdx.x == 0) {
+  if (closer) {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_h[i] += s_c2[i];
     __syncthreads();
     const double r2 = s_tot[0] - s_tot[1];
     lowsync_close(K, j, s_h, r2 > 0.0 ? sqrt(r2) : 0.0, scs, ssn);
   }
-  if (half_norms) {
-    lowsync_update<S, true>(K, q, cnt, s_c, s_n);
-    lowsync_half_norms(K, j, s_n);
-  } else {
-    lowsync_update<S, false>(K, q, cnt, s_c, s_n);
-  }
+  update(half_norms != 0);
 }
 
 // y = R^-1 g over the j columns of the finished cycle; y_i *= vscale_i.  One

@@ -193,11 +193,14 @@ __device__ __forceinline__ bool last_block(unsigned* ticket, int nblocks) {
 }
 
 // Deterministic cross-block sum of partial[b * stride + c] for c in [0, cnt):
-// warp w sums columns c = w, w + kVecWarps, ..; lanes stride over blocks.
+// warp w of the block's warps sums columns c = w, w + warps, ..; lanes stride
+// over blocks.  The block may have any whole number of warps (the block
+// preconditioner's apply runs with as few as one).
 __device__ __forceinline__ void reduce_partials(const double* partial, int stride, int nblocks,
                                                 int cnt, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < cnt; c += kVecWarps) {
+  const int warps = int(blockDim.x >> 5);
+  for (int c = warp; c < cnt; c += warps) {
     double s = 0.0;
     for (int b = lane; b < nblocks; b += 32) s += __ldcg(partial + size_t(b) * stride + c);
     s = warp_sum(s);

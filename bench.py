@@ -166,11 +166,12 @@ def pc_work_per_dof(mixed):
     """BJ_ext apply on this workload: linear advection on one uniform mesh has
     the same J_i (hence M_i) in every element, so the library builds one block
     pair and the apply reads only the two input halves and writes the two
-    output halves: 32 B per W-DOF in FP64, 16 B in FP32 (the 2 n_b^2 block
-    values once per launch are negligible); four n_b x n_b matrix-vector
-    products: 8 n_b flops per W-DOF (+ 4)."""
+    output halves: 32 B per W-DOF in FP64, 16 B in FP32 (the block values once
+    per launch are negligible).  Flops: M_i w and M_i sigma, dense n_b x n_b
+    (4 n_b per W-DOF), and J_i u, J_i v with J_i the Kronecker sum of its d
+    one-dimensional p x p factors (4 d p per W-DOF), plus 4."""
     nb = (WL["N"] + 1) ** WL["dim"]
-    return (16.0 if mixed else 32.0), 8.0 * nb + 4.0
+    return (16.0 if mixed else 32.0), 4.0 * nb + 4.0 * WL["dim"] * (WL["N"] + 1) + 4.0
 
 
 def cgs_work_per_dof(mixed, cavg):
@@ -192,7 +193,7 @@ NCU_TRAFFIC = {
 
 KERNEL_NAMES = {
     "jv": "dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)",
-    "pc_apply": "k_pc_apply_shared<%s, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements)",
+    "pc_apply": "k_pc_apply_shared<%s, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements, J as Kronecker factors)",
     "cgs2": "k_cgs_coop<%s> (Arnoldi CGS2 column, one cooperative launch; mean j + 1 = %.1f)",
 }
 
@@ -281,6 +282,12 @@ def run_c2_arm(torch, hbpc, inputs, precision, args, stream, flush, fp64_peak_gf
     and the end-to-end run through host buffers."""
     dt = workload_dt()
     ctx = c2_context(hbpc, WL["n"], precision, stream)
+    # corrector batching pays in the mixed mode (per-stage GMRES, latency-bound
+    # kernels); the FP64 mode shares one GMRES between the stages and its
+    # kernels are FP64-ALU bound, so it stays sequential unless asked
+    cbatch = (precision == "mixed") if args.corrector_batch < 0 else bool(args.corrector_batch)
+    if cbatch:
+        ctx.set_corrector_batch(True)
     coords = ctx.node_coords()
     w0 = inputs.sine_product(coords)
     ctx.set_state(w0)
@@ -315,7 +322,8 @@ def run_c2_arm(torch, hbpc, inputs, precision, args, stream, flush, fp64_peak_gf
            "newton_its_per_step": stats["newton_its"] / args.steps,
            "r1_evals_per_s": (stats["r1_evals"] + stats["r2_evals"]) / t_sec,
            "gpu_launches": int(stats["launches"]), "l2_error_vs_exact": err, "roofline": roof,
-           "autotuned": tuning, "clocks": clk, "ndof": ndof, "w_final": w_fin}
+           "autotuned": tuning, "clocks": clk, "ndof": ndof, "w_final": w_fin,
+           "corrector_batch": cbatch}
     if headline:
         # e2e: the public API with pinned host buffers, copies inside the timed
         # region, the L2 flush outside it (as in the device-timed loop)
@@ -749,7 +757,8 @@ def run_ours(args):
             "autotuned": res["autotuned"], "r1_evals_per_s": res["r1_evals_per_s"],
             "l2_error_vs_exact": res["l2_error_vs_exact"], "gmres_its_per_step": res["gmres_its_per_step"],
             "newton_its_per_step": res["newton_its_per_step"], "gpu_launches": res["gpu_launches"],
-            "roofline": res["roofline"], "e2e": res["e2e"], "clocks": res["clocks"]}
+            "roofline": res["roofline"], "e2e": res["e2e"], "clocks": res["clocks"],
+            "corrector_batch": res["corrector_batch"]}
     if not extras:
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -806,7 +815,7 @@ def run_ours(args):
     sec.pop("w_final")
     line["mixed_precision" if head == "fp64" else "fp64_precision"] = {
         k: sec[k] for k in ("value", "ms_per_step", "gmres_its_per_step", "newton_its_per_step", "r1_evals_per_s",
-                            "gpu_launches", "roofline", "autotuned")}
+                            "gpu_launches", "roofline", "autotuned", "corrector_batch")}
     line[("mixed_precision" if head == "fp64" else "fp64_precision")]["unit"] = UNIT
     line[("mixed_precision" if head == "fp64" else "fp64_precision")]["dtype"] = (
         "f64 state/Newton, f32 Krylov" if other == "mixed" else "f64")
@@ -1109,6 +1118,9 @@ def main():
                     help="skip the oracle (timed CPU baseline and the accuracy against the oracle)")
     ap.add_argument("--no-vortex", action="store_true",
                     help="skip the learned-vs-plain-GMRES comparison on the Euler vortex in the default line")
+    ap.add_argument("--corrector-batch", type=int, default=-1, choices=[-1, 0, 1],
+                    help="1: the s - 1 corrector stages of every sweep solved as one batched Newton-GMRES; "
+                         "0: one after the other; -1 (default): batched in the mixed mode only")
     ap.add_argument("--headline-only", action="store_true",
                     help="the headline arm alone (for profiling): no second precision, oracle or vortex")
     ap.add_argument("--no-r1-roofline", action="store_true",

@@ -217,6 +217,19 @@ hbpc_status hbpc_advance_to(hbpc_ctx* ctx, double t_end);
  * created without a final time (t_end = 0). */
 hbpc_status hbpc_run(hbpc_ctx* ctx);
 
+/* Corrector batching (the paper's outlook, Sec. 6; Algorithm 1 unchanged):
+ * the right-hand sides of the s - 1 corrector stages of one sweep depend only
+ * on the previous level, so with on = 1 every sweep solves them together as
+ * one batched Newton-GMRES (stage l is instance l - 1 of an internal group
+ * with the context's mesh, law, solver and precision; each stage keeps its own
+ * Newton stopping test and, in the MIXED mode, its own GMRES; in FP64 mode the
+ * stages share one GMRES with rows scaled by 1 / ||G_l||).  Every launch then
+ * covers s - 1 stages.  The answer is the same to the Newton tolerance.
+ * Allocates about (s - 1) times the context's solver memory on on = 1; 0
+ * releases it.  HBPC_ERR_UNSUPPORTED for the Navier-Stokes law and the learned
+ * preconditioner.  Runs on the context's stream. */
+hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on);
+
 /* Bounded waits.  Every call of the context waits for its stream before it
  * returns (and inside the Newton loop, for the residual norms).  With a limit
  * of `seconds` > 0 such a wait gives up after that long and the call returns

@@ -280,6 +280,12 @@ struct hbpc_ctx {
   } arn_graph[2];
   int graph_mode = 1;
   double wait_limit_s = 0.0;  // bounded host waits (hbpc_set_wait_limit); 0 = none
+  // every instance of a batch group has the same mesh (then J_i is shared
+  // between instances as between elements)
+  bool same_mesh = false;
+  // corrector batching: the s - 1 corrector stages of a sweep as the
+  // instances of one group context (hbpc_set_corrector_batch), on this stream
+  hbpc_ctx* cb = nullptr;
   Prof prof;
 };
 
@@ -762,7 +768,7 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
   // one shared block when J_i is the same for every element and state (the
   // training-data collection and the learned network want per-element blocks)
-  x->pc_shared = linear && x->ninst == 0 && x->sol.pc == HBPC_PC_BJEXT && !collecting;
+  x->pc_shared = linear && (x->ninst == 0 || x->same_mesh) && x->sol.pc == HBPC_PC_BJEXT && !collecting;
   const int nEb = x->pc_shared ? 1 : int(x->nE);   // blocks to build
   // J_i in the precision of the apply: FP32 in the mixed mode (the blocks only
   // precondition the FP32 Krylov loop), FP64 otherwise
@@ -1398,7 +1404,8 @@ hbpc_status hbpc_one_step(hbpc_ctx* x) {
     auto Wc = [&](int l) { return l == 0 ? W(0, 0) : W(cur, l); };
     auto R1c = [&](int l) { return l == 0 ? R1(0, 0) : R1(cur, l); };
     auto R2c = [&](int l) { return l == 0 ? R2(0, 0) : R2(cur, l); };
-    for (int l = 1; l < s; ++l) {
+    // right-hand side of corrector stage l (Eq. 6 with the quadrature I_l)
+    auto rhs = [&](int l, double* out) -> hbpc_status {
       LinComb lc{};
       auto add = [&](double c, const double* p) {
         if (c != 0.0) { lc.x[lc.nterm] = p; lc.c[lc.nterm] = c; ++lc.nterm; }
@@ -1410,8 +1417,40 @@ hbpc_status hbpc_one_step(hbpc_ctx* x) {
         add(dt * x->B1[l][j], R1c(j));
         add(dt * dt * x->B2[l][j], R2c(j));
       }
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_lincomb<<<grid_for(size_t(n)), 256, 0, x->stream>>>(lc, x->bvec, size_t(n)));
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_lincomb<<<grid_for(size_t(n)), 256, 0, x->stream>>>(lc, out, size_t(n)));
       HBPC_LAUNCH_CK(x, "corrector rhs");
+      return HBPC_OK;
+    };
+    if (x->cb && s > 1) {
+      // the s - 1 stages of this sweep depend only on level cur: one batched
+      // Newton solve with stage l as instance l - 1 (Sec. 6 outlook)
+      hbpc_ctx* g = x->cb;
+      const size_t vpe = size_t(g->ndof / g->nE);
+      for (int l = 1; l < s; ++l) {
+        const size_t off = size_t(g->ie0[l - 1]) * vpe;
+        if ((st = rhs(l, g->bvec + off)) != HBPC_OK) return st;
+        HBPC_CK(x, cudaMemcpyAsync(g->stage + off, Wc(l), n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+      }
+      const hbpc_stats before = g->stats;
+      st = newton(g, g->bvec, 1.0, 1.0, g->stage);
+      x->stats.newton_solves += g->stats.newton_solves - before.newton_solves;
+      x->stats.newton_its += g->stats.newton_its - before.newton_its;
+      x->stats.gmres_its += g->stats.gmres_its - before.gmres_its;
+      x->stats.r1_evals += g->stats.r1_evals - before.r1_evals;
+      x->stats.r2_evals += g->stats.r2_evals - before.r2_evals;
+      x->stats.launches += g->stats.launches - before.launches;
+      x->stats.arnoldi_cols += g->stats.arnoldi_cols - before.arnoldi_cols;
+      if (st != HBPC_OK) return fail(x, st, "corrector batch: " + g->err);
+      for (int l = 1; l < s; ++l) {
+        const size_t off = size_t(g->ie0[l - 1]) * vpe;
+        HBPC_CK(x, cudaMemcpyAsync(W(nxt, l), g->X + off, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+        if ((st = eval_r1r2(x, W(nxt, l), R1(nxt, l), R2(nxt, l))) != HBPC_OK) return st;
+      }
+      cur = nxt;
+      continue;
+    }
+    for (int l = 1; l < s; ++l) {
+      if ((st = rhs(l, x->bvec)) != HBPC_OK) return st;
       if ((st = newton(x, x->bvec, 1.0, 1.0, Wc(l))) != HBPC_OK) return st;
       HBPC_CK(x, cudaMemcpyAsync(W(nxt, l), x->X, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
       if ((st = eval_r1r2(x, W(nxt, l), R1(nxt, l), R2(nxt, l))) != HBPC_OK) return st;
@@ -2052,6 +2091,13 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   x->nE = e;
   x->ndof = x->nE * x->nv * nn;
   if (x->nE > (1LL << 30)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "batch too large"); }
+  x->same_mesh = true;
+  for (int id : ids) {
+    const hbpc_mesh& mi = meshes[id];
+    for (int m = 0; m < x->dim; ++m)
+      if (mi.n[m] != m0.n[m] || mi.lo[m] != m0.lo[m] || mi.hi[m] != m0.hi[m]) x->same_mesh = false;
+    if (phys[id].nu != phys[ids[0]].nu) x->same_mesh = false;
+  }
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
     delete x;
@@ -2179,6 +2225,11 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
 void hbpc_destroy(hbpc_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->cb) {   // runs on this context's stream, which it does not own
+    free_all(ctx->cb);
+    delete ctx->cb;
+    ctx->cb = nullptr;
+  }
   free_all(ctx);
   delete ctx;
 }
@@ -2278,6 +2329,38 @@ hbpc_status hbpc_run(hbpc_ctx* ctx) {
 hbpc_status hbpc_set_wait_limit(hbpc_ctx* ctx, double seconds) {
   if (!ctx || !(seconds >= 0.0) || !std::isfinite(seconds)) return HBPC_ERR_INVALID_ARG;
   ctx->wait_limit_s = seconds;
+  if (ctx->cb) ctx->cb->wait_limit_s = seconds;
+  return HBPC_OK;
+}
+
+hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
+  if (ctx->ninst > 0) return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching is for single problems");
+  hbpc_status s = sync(ctx, "set_corrector_batch");
+  if (s != HBPC_OK) return s;
+  if (!on) {
+    if (ctx->cb) { free_all(ctx->cb); delete ctx->cb; ctx->cb = nullptr; }
+    return HBPC_OK;
+  }
+  if (ctx->cb) return HBPC_OK;
+  if (ctx->phys.law == HBPC_LAW_NAVIER_STOKES)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching of the Navier-Stokes law is not built");
+  if (ctx->sol.pc == HBPC_PC_LEARNED)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching with the learned preconditioner is not built");
+  const int ns = std::max(1, ctx->s - 1);
+  std::vector<int> ids(ns);
+  std::vector<hbpc_mesh> meshes(ns, ctx->mesh);
+  std::vector<hbpc_physics> phys(ns, ctx->phys);
+  for (int i = 0; i < ns; ++i) ids[i] = i;
+  hbpc_ctx* g = nullptr;
+  s = create_group(ids, meshes.data(), ctx->N, ctx->nodes, phys.data(), &ctx->sol, &g);
+  if (s != HBPC_OK) return fail(ctx, s, std::string("corrector batch: ") + g_create_error);
+  // the group works on this context's stream (its own one is released)
+  cudaStreamSynchronize(g->stream);
+  cudaStreamDestroy(g->stream);
+  g->stream = ctx->stream;
+  g->wait_limit_s = ctx->wait_limit_s;
+  ctx->cb = g;
   return HBPC_OK;
 }
 
@@ -2427,6 +2510,12 @@ hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc) {
     if ((s = pc_alloc(ctx)) != HBPC_OK) return s;
     if (ctx->sol.precision == HBPC_PREC_MIXED && (s = pc_alloc_f(ctx)) != HBPC_OK) return s;
     if (pc == HBPC_PC_LEARNED && (s = lp_alloc(ctx)) != HBPC_OK) return s;
+  }
+  if (ctx->cb) {
+    if (pc == HBPC_PC_LEARNED)
+      return fail(ctx, HBPC_ERR_UNSUPPORTED, "the learned preconditioner needs corrector batching off");
+    hbpc_status s = hbpc_set_pc(ctx->cb, pc);
+    if (s != HBPC_OK) return fail(ctx, s, "corrector batch: " + ctx->cb->err);
   }
   ctx->sol.pc = pc;
   ctx->pc_built = false;
@@ -2620,6 +2709,7 @@ hbpc_status hbpc_profile_enable(hbpc_ctx* ctx, int enable) {
   if (s != HBPC_OK) return s;
   ctx->prof.on = enable != 0;
   for (int i = 0; i < HBPC_NPHASES; ++i) { ctx->prof.ms[i] = 0.0; ctx->prof.cnt[i] = 0; }
+  if (ctx->cb) return hbpc_profile_enable(ctx->cb, enable);
   return HBPC_OK;
 }
 
@@ -2630,6 +2720,13 @@ hbpc_status hbpc_profile_get(hbpc_ctx* ctx, double* ms, long long* launches, int
   for (int i = 0; i < n_phases && i < HBPC_NPHASES; ++i) {
     if (ms) ms[i] = ctx->prof.ms[i];
     if (launches) launches[i] = ctx->prof.cnt[i];
+  }
+  if (ctx->cb) {   // the batched correctors' launches
+    if ((s = sync(ctx->cb, "profile_get")) != HBPC_OK) return s;
+    for (int i = 0; i < n_phases && i < HBPC_NPHASES; ++i) {
+      if (ms) ms[i] += ctx->cb->prof.ms[i];
+      if (launches) launches[i] += ctx->cb->prof.cnt[i];
+    }
   }
   return HBPC_OK;
 }
@@ -2888,6 +2985,10 @@ hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out) {
 
 hbpc_status hbpc_autotune(hbpc_ctx* ctx, hbpc_tuning* out) {
   if (!ctx) return HBPC_ERR_INVALID_ARG;
+  if (ctx->cb) {   // the corrector batch has its own vector lengths
+    hbpc_status s = autotune(ctx->cb, nullptr);
+    if (s != HBPC_OK) return fail(ctx, s, "corrector batch: " + ctx->cb->err);
+  }
   return autotune(ctx, out);
 }
 

@@ -94,6 +94,7 @@ _SIGS = {
     "hbpc_advance_to": (_I, [_CTX, _D]),
     "hbpc_run": (_I, [_CTX]),
     "hbpc_set_wait_limit": (_I, [_CTX, _D]),
+    "hbpc_set_corrector_batch": (_I, [_CTX, _I]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -284,6 +285,10 @@ class Context:
 
     def set_wait_limit(self, seconds):
         self._c(_lib.hbpc_set_wait_limit(self._ctx, seconds))
+
+    def set_corrector_batch(self, on=True):
+        """Solve the s - 1 corrector stages of every sweep as one batched Newton."""
+        self._c(_lib.hbpc_set_corrector_batch(self._ctx, 1 if on else 0))
 
     def eval_R1(self, w, out):
         self._c(_lib.hbpc_eval_R1(self._ctx, _ptr(w), _ptr(out)))

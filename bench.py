@@ -184,17 +184,19 @@ def cgs_work_per_dof(mixed, cavg):
 
 
 # DRAM bytes (read + write) per launch measured by ncu for the kernels of this
-# workload (summaries in profiles/, one per kernel and precision).  An entry is
-# None until its kernel, as committed, has been captured.
+# workload with caches as the run leaves them (--cache-control none; mean of
+# ten launches inside the timed step; summaries in profiles/, one per kernel
+# and precision).  An entry is None until its kernel, as committed, has been
+# captured.
 NCU_TRAFFIC = {
     "mixed": {"cgs2": None, "pc_apply": None, "jv": None},
-    "fp64": {"cgs2": None, "pc_apply": None, "jv": None},
+    "fp64": {"cgs2": 1.411e5, "pc_apply": 8.233e4, "jv": 1.441e5},
 }
 
 KERNEL_NAMES = {
     "jv": "dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)",
     "pc_apply": "k_pc_apply_shared<%s, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements, J as Kronecker factors)",
-    "cgs2": "k_cgs_coop<%s> (Arnoldi CGS2 column, one cooperative launch; mean j + 1 = %.1f)",
+    "cgs2": "k_cgs_lowsync<%s> (Arnoldi CGS2 column, one cooperative launch, two grid barriers; mean j + 1 = %.1f)",
 }
 
 

@@ -796,6 +796,16 @@ def run_ours(args):
             "speedup_learned_over_plain": (ln["value"] / pl["value"]) if pl["value"] > 0 else None,
             "speedup_learned_over_bjext": (ln["value"] / bj["value"]) if bj["value"] > 0 else None,
             "training": v["config"]["training"]}
+    if not args.no_batch:
+        # the batched workload (256 viscous Burgers instances), one warm-up and
+        # one timed step; --workload burgers_batch for the full line
+        ba = argparse.Namespace(steps=1, warmup=1, instances=BATCH["n_inst"], max_per_group=BATCH["max_per_group"])
+        bl = run_batch(ba, emit=False)
+        line["batch"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "gmres_its_per_step",
+                                            "newton_its_per_step", "gpu_launches", "e2e", "steps", "warmup")}
+        line["batch"]["workload"] = bl["config"]["workload"]
+        line["batch"]["total_dof"] = bl["config"]["total_dof"]
+        line["batch"]["groups"] = bl["config"]["groups"]
     # the oracle: the timed CPU baseline, then the accuracy of both precisions
     acc = {"fp64" if head == "fp64" else "mixed": {"l2_error_vs_exact_solution": res["l2_error_vs_exact"]},
            other: {"l2_error_vs_exact_solution": sec["l2_error_vs_exact"]}}
@@ -899,7 +909,7 @@ def batch_instances(n_inst):
     return out
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched workload: independent 2-D viscous Burgers instances
     u_t + div(u^2/2 (1, 1)) = nu Laplace(u) (BR2, Sec. 5.1.1; global LF flux), one batch
     (hbpc_batch_*) advanced by HBPC(6, 2) with a common dt (CFL 2 on the finest
@@ -992,11 +1002,12 @@ def run_batch(args):
             "e2e": {"value": ndof * args.steps * world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8},
             "clocks": clk}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return line
 
 
 TGV = dict(n=32, N=5, q=4, kmax=0, cfl=20.0, eps=0.1, re=1600.0, prandtl=0.72, tol_newton_rel=1e-10,
@@ -1125,6 +1136,8 @@ def main():
                          "0: one after the other; -1 (default): batched in the mixed mode only")
     ap.add_argument("--headline-only", action="store_true",
                     help="the headline arm alone (for profiling): no second precision, oracle or vortex")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched viscous Burgers workload in the default line")
     ap.add_argument("--no-r1-roofline", action="store_true",
                     help="skip the operator-pass roofline on the Euler vortex and Taylor-Green meshes")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],

@@ -16,6 +16,12 @@ Jv (Sec. 4.2):
   "analytic" Eq. 18 with dR1/dW v = R2(W, v) (identity of Sec. 3.2.1) and the
            Hessian block by the FD quotient of Eq. 23.
 
+Schur form (Sec. 3.2.4, Eq. 19): Newton with the linear system reduced to the
+W unknowns, J_Schur dW = -G1 + (a2 dt^2/2) dR2/dsigma . G2,
+dsigma = -G2 + dR1/dW dW, J_Schur = I - a1 dt dR1/dW + (a2 dt^2/2) dR2/dW
++ (a2 dt^2/2) (dR1/dW)^2; its products reuse the extended product above on
+(v, dR1/dW v), whose first half is J_Schur v.
+
 GMRES: restarted, right preconditioned, modified Gram-Schmidt Arnoldi with
 Givens rotations and zero initial guess (textbook form, Saad 2003, Alg. 6.9 /
 9.5), relative tolerance against the norm of the right-hand side.
@@ -232,6 +238,68 @@ def newton_solve(disc, b, alpha1, alpha2, dt, W0, opts, stats=None):
         G, r1, r2 = sysm.residual(X)
         converged = (np.linalg.norm(G) <= opts.tol_rel * g0
                      or np.linalg.norm(dX[:sysm.n]) <= opts.tol_abs)
+    st.converged = st.converged and converged
+    W, S = sysm.split(X)
+    return W.copy(), S.copy(), st
+
+
+def schur_step(sysm, X, r1, r2, G, opts):
+    """One Newton increment dX = (dW, dsigma) of Sec. 3.2.4 at X (residual G,
+    r1 = R1(W), r2 = R2(W, sigma)):
+        J_Schur dW = -G1 + (a2 dt^2/2) (dR2/dsigma) G2,
+        dsigma     = -G2 + (dR1/dW) dW,
+    J_Schur of Eq. 19.  R2 is linear in sigma, so (dR2/dsigma) G2 = R2(W, G2).
+    dR1/dW v is the second half of the extended product on (v, 0) with the sign
+    turned, and J_Schur v the first half of the extended product on
+    (v, dR1/dW v), in the same form (opts.jv) as newton_solve.  With
+    opts.pc == "bjext" GMRES is right preconditioned by the element blocks
+    (I - a1 dt J_i + (a2 dt^2/2) J_i^2)^-1 (the D block of BJ_ext, the
+    element-local J_Schur without the Hessian).  Returns (dX, GMRES iterations)."""
+    disc, n = sysm.disc, sysm.n
+    zero = np.zeros(n)
+    W, _ = sysm.split(X)
+    G1, G2 = G[:n], G[n:]
+
+    def dr1(v):
+        return -sysm.jv(X, r1, r2, np.concatenate([v, zero]), opts.jv)[n:]
+
+    def jschur(v):
+        return sysm.jv(X, r1, r2, np.concatenate([v, dr1(v)]), opts.jv)[:n]
+
+    rhs = -G1 + sysm.c2 * sysm.R2(W, G2.reshape(disc.shape)).ravel()
+    pc = None
+    if opts.pc == "bjext":
+        blocks = BJExt(sysm, W)
+
+        def pc(v, M=blocks.M):
+            return (M @ v.reshape(blocks.nE, blocks.nb, 1)).ravel()
+
+    dW, its, _ = gmres(jschur, rhs, opts.gmres_tol, opts.restart, opts.gmres_maxiter, pc)
+    dS = -G2 + dr1(dW)
+    return np.concatenate([dW, dS]), its
+
+
+def schur_newton_solve(disc, b, alpha1, alpha2, dt, W0, opts, stats=None):
+    """Solve G(X) = 0 from X^0 = (W0, R1(W0)) with the Schur-complement linear
+    system of Sec. 3.2.4 in every Newton step (schur_step); the same stopping
+    tests as newton_solve.  Returns (W, sigma, stats)."""
+    sysm = StageSystem(disc, b, alpha1, alpha2, dt, stats)
+    st = sysm.stats
+    n = sysm.n
+    X = np.concatenate([W0.ravel(), sysm.R1(W0).ravel()])
+    G, r1, r2 = sysm.residual(X)
+    g0 = np.linalg.norm(G)
+    converged = g0 == 0.0
+    r = 0
+    while not converged and r < opts.newton_max:
+        dX, its = schur_step(sysm, X, r1, r2, G, opts)
+        st.gmres_its += its
+        X = X + dX
+        r += 1
+        st.newton_its += 1
+        G, r1, r2 = sysm.residual(X)
+        converged = (np.linalg.norm(G) <= opts.tol_rel * g0
+                     or np.linalg.norm(dX[:n]) <= opts.tol_abs)
     st.converged = st.converged and converged
     W, S = sysm.split(X)
     return W.copy(), S.copy(), st

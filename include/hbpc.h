@@ -230,6 +230,20 @@ hbpc_status hbpc_run(hbpc_ctx* ctx);
  * preconditioner.  Runs on the context's stream. */
 hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on);
 
+/* Schur form of the Newton systems (Sec. 3.2.4, Eq. 19): with on = 1 every
+ * Newton step solves J_Schur dW = -G1 + (alpha2 dt^2/2) (dR2/dsigma) G2 with
+ * J_Schur = I - alpha1 dt dR1/dW + (alpha2 dt^2/2) dR2/dW
+ * + (alpha2 dt^2/2) (dR1/dW)^2 by matrix-free GMRES (each product two
+ * passes of the extended product of Eq. 23/24: on (z, 0) for dR1/dW z, then
+ * on (z, dR1/dW z)), right preconditioned by the BJ_ext D blocks
+ * (I - c1 J_i + c2 J_i^2)^-1 when the context has a block preconditioner, and
+ * then sets dsigma = -G2 + (dR1/dW) dW.  The Newton stopping tests and the
+ * root are those of the extended form.  FP64 mode and single problems only
+ * (HBPC_ERR_UNSUPPORTED otherwise, also with corrector batching on).
+ * Allocates three 2 n_dof vectors on the first on = 1; 0 returns to the
+ * extended form. */
+hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on);
+
 /* Bounded waits.  Every call of the context waits for its stream before it
  * returns (and inside the Newton loop, for the residual norms).  With a limit
  * of `seconds` > 0 such a wait gives up after that long and the call returns

@@ -64,6 +64,59 @@ __global__ void k_neg_sum(const double* a, const double* b, double* out, size_t 
     out[i] = -a[i] - b[i];
 }
 
+// Schur form (Sec. 3.2.4) helpers on 2 n vectors whose second half is the
+// sigma part.  A step is skipped when *skip != 0 (the GMRES cycle is done).
+// out = scale[j] * V[j] (j = *jidx), the column of the Krylov basis
+__global__ void k_gather_col(const double* V, const int* jidx, const double* scale, double* out, size_t n2,
+                             const int* skip) {
+  if (skip && *skip) return;
+  const int j = *jidx;
+  const double sc = scale[j];
+  const double* v = V + size_t(j) * n2;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n2; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = sc * v[i];
+}
+// zero the sigma half of column (*jidx + off) of V (jidx null: of V itself)
+__global__ void k_zero_half(double* V, const int* jidx, int off, size_t n, const int* skip) {
+  if (skip && *skip) return;
+  double* v = V + (jidx ? size_t(*jidx + off) * 2 * n : 0) + n;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    v[i] = 0.0;
+}
+// y_S = -o_S (o = the extended product on (z, 0), whose sigma half is -J z):
+// y = (z, J z) in place of y = (z, 0)
+__global__ void k_schur_pair(double* y, const double* o, size_t n, const int* skip) {
+  if (skip && *skip) return;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    y[n + i] = -o[n + i];
+}
+// out = (-G1 - c2 o_S, 0) with o_S = -J G2: the Schur right-hand side
+// -G1 + c2 (dR2/dsigma) G2 (R2 is linear in sigma, and dR2/dsigma = dR1/dW)
+__global__ void k_schur_rhs(const double* G, const double* o, const double* c12, double* out, size_t n) {
+  const double c2 = c12[1];
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    out[i] = -G[i] - c2 * o[n + i];
+    out[n + i] = 0.0;
+  }
+}
+// dX_S = -G2 - o_S (o_S = -J dW): the sigma increment -G2 + (dR1/dW) dW
+__global__ void k_schur_sigma(const double* G, const double* o, double* dX, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    dX[n + i] = -G[n + i] - o[n + i];
+}
+// y_W += x_W (first halves only)
+__global__ void k_add_half(const double* x, double* y, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    y[i] += x[i];
+}
+// out = (r_W - p_W, 0): the restart residual of the Schur system
+__global__ void k_schur_restart(const double* r, const double* p, double* out, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    out[i] = r[i] - p[i];
+    out[n + i] = 0.0;
+  }
+}
+
 __global__ void k_set2(double* p, double a, double b) {
   if (threadIdx.x == 0) { p[0] = a; p[1] = b; }
 }
@@ -277,7 +330,7 @@ struct hbpc_ctx {
     bool failed = false;        // the runtime refused the capture: direct launches
     long long launches = 0;     // kernel launches the graph replays
     long long key[8] = {};      // launch shapes it was captured with
-  } arn_graph[2];
+  } arn_graph[3];   // [2]: the Schur form
   int graph_mode = 1;
   double wait_limit_s = 0.0;  // bounded host waits (hbpc_set_wait_limit); 0 = none
   // every instance of a batch group has the same mesh (then J_i is shared
@@ -286,6 +339,13 @@ struct hbpc_ctx {
   // corrector batching: the s - 1 corrector stages of a sweep as the
   // instances of one group context (hbpc_set_corrector_batch), on this stream
   hbpc_ctx* cb = nullptr;
+  // Schur form of the Newton systems (hbpc_set_schur): scratch 2 n vectors,
+  // the right-hand side and the norms of the product inputs
+  bool schur = false;
+  double* sa = nullptr;
+  double* sb = nullptr;
+  double* srhs = nullptr;
+  double* snrm = nullptr;   // 3 norms (total, W, sigma) of the current product input
   Prof prof;
 };
 
@@ -935,6 +995,7 @@ hbpc_status arnoldi_step(hbpc_ctx* x) {
 }
 
 hbpc_status arnoldi_step_f(hbpc_ctx* x);
+hbpc_status arnoldi_step_schur(hbpc_ctx* x);
 
 // One batch of Arnoldi steps.  Every launch of a step takes its column index,
 // scale and stopping flag from device memory, so a batch is the same launch
@@ -943,9 +1004,10 @@ hbpc_status arnoldi_step_f(hbpc_ctx* x);
 // launches instead with HBPC_GRAPH=0, during a phase-profiled step (its events
 // would be captured), when the caller is capturing the stream, and after the
 // runtime refused a capture (e.g. of the cooperative launch).
-hbpc_status arnoldi_batch(hbpc_ctx* x, int batch, bool f32) {
-  hbpc_status (*step)(hbpc_ctx*) = f32 ? arnoldi_step_f : arnoldi_step;
-  auto& g = x->arn_graph[f32 ? 1 : 0];
+// kind 0: FP64 extended system, 1: mixed (FP32 Krylov loop), 2: FP64 Schur form
+hbpc_status arnoldi_batch(hbpc_ctx* x, int batch, int kind) {
+  hbpc_status (*step)(hbpc_ctx*) = kind == 1 ? arnoldi_step_f : kind == 2 ? arnoldi_step_schur : arnoldi_step;
+  auto& g = x->arn_graph[kind];
   bool use = x->graph_mode != 0 && !x->prof.on && !g.failed;
   if (use) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1007,7 +1069,7 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const int batch = 4;
   int j_prev = 0;
   for (;;) {
-    hbpc_status s = arnoldi_batch(x, batch, false);
+    hbpc_status s = arnoldi_batch(x, batch, 0);
     if (s != HBPC_OK) return s;
     s = read_state(x);
     if (s != HBPC_OK) return s;
@@ -1059,6 +1121,134 @@ hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
 // update and stage logic in FP64.  Hessenberg, Givens rotations and the
 // cross-thread / cross-block sums of the Arnoldi reductions stay FP64.
 // ---------------------------------------------------------------------------
+// ---- Schur form of the Newton system (Sec. 3.2.4, Eq. 19) -----------------
+// The Krylov vectors are 2 n vectors whose sigma half is zero, so the basis,
+// the Arnoldi column, the small solve and the combination are those of the
+// extended system; only the product and the right-hand side differ.
+
+// The extended product (Eq. 23/24) at X on the 2 n vector `in` into `out`
+// (norms of in's halves first when the difference quotients need them).
+hbpc_status jv_plain(hbpc_ctx* x, const double* in, double* out, const int* skip) {
+  const size_t n2 = size_t(2 * x->ndof);
+  if (!x->ops.jv_linear) {
+    hbpc_status s = norms(x, in, n2, x->snrm);
+    if (s != HBPC_OK) return s;
+  }
+  JvInput z{};
+  z.V = in; z.ld = n2; z.half = size_t(x->ndof);
+  z.nrmW = x->snrm + 1; z.nrmS = x->snrm + 2;
+  z.skip = skip;
+  z.out = out; z.out_ld = n2; z.out_offset = 0;
+  return apply_jv(x, z);
+}
+
+// J_Schur z = the first half of the extended product on (z, dR1/dW z): sa
+// holds (z, 0) on entry, (z, J z) on exit; the product goes to `out`
+// (column *out_jidx + out_offset of out when out_jidx is given).
+hbpc_status schur_product(hbpc_ctx* x, double* out, const int* out_jidx, int out_offset, const int* skip) {
+  const size_t n = size_t(x->ndof), n2 = 2 * n;
+  hbpc_status s = jv_plain(x, x->sa, x->sb, skip);              // sb = (.., -J z)
+  if (s != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_schur_pair<<<grid_for(n), 256, 0, x->stream>>>(x->sa, x->sb, n, skip));
+  if (!x->ops.jv_linear && (s = norms(x, x->sa, n2, x->snrm)) != HBPC_OK) return s;
+  JvInput z{};
+  z.V = x->sa; z.ld = n2; z.half = n;
+  z.nrmW = x->snrm + 1; z.nrmS = x->snrm + 2;
+  z.skip = skip;
+  z.out = out; z.out_ld = n2; z.out_offset = out_offset; z.out_jidx = out_jidx;
+  if ((s = apply_jv(x, z)) != HBPC_OK) return s;
+  HBPC_LAUNCH_CK(x, "Schur product");
+  return HBPC_OK;
+}
+
+// One Arnoldi iteration of the Schur system: z = P^-1 v_j (the D block of
+// BJ_ext: its apply on (v_j, 0) has M v_j in the first half), the product
+// J_Schur z into column j + 1 (its sigma half cleared), the CGS column.
+hbpc_status arnoldi_step_schur(hbpc_ctx* x) {
+  const size_t n = size_t(x->ndof), n2 = 2 * n;
+  const int* jd = &x->st->j;
+  const int* skip = &x->st->done;
+  hbpc_status s;
+  if (x->sol.pc != HBPC_PC_NONE) {
+    if ((s = pc_apply(x, x->V, jd, x->K.vscale, x->sa, 0, skip)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_PC, 1, k_zero_half<<<grid_for(n), 256, 0, x->stream>>>(x->sa, nullptr, 0, n, skip));
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1,
+             k_gather_col<<<grid_for(n2), 256, 0, x->stream>>>(x->V, jd, x->K.vscale, x->sa, n2, skip));
+  }
+  if ((s = schur_product(x, x->V, jd, 1, skip)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_zero_half<<<grid_for(n), 256, 0, x->stream>>>(x->V, jd, 1, n, skip));
+  cgs_launch<double>(x, x->K);
+  HBPC_LAUNCH_CK(x, "arnoldi (Schur)");
+  return HBPC_OK;
+}
+
+// GMRES on J_Schur dW = -G1 + c2 (dR2/dsigma) G2 (right preconditioned by the
+// BJ_ext D blocks when there is a preconditioner); dW into the first half of
+// x->dX.  G = (G1, G2) is the current residual.
+hbpc_status gmres_schur(hbpc_ctx* x, int* its_out, bool* conv_out) {
+  const size_t n = size_t(x->ndof), n2 = 2 * n;
+  HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
+  // right-hand side: the extended product on (G2, 0) has -J G2 in its second half
+  HBPC_CK(x, cudaMemcpyAsync(x->sa, x->G + n, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+  HBPC_CK(x, cudaMemsetAsync(x->sa + n, 0, n * sizeof(double), x->stream));
+  hbpc_status s = jv_plain(x, x->sa, x->sb, nullptr);
+  if (s != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_schur_rhs<<<grid_for(n), 256, 0, x->stream>>>(x->G, x->sb, x->c12, x->srhs, n));
+  HBPC_CK(x, cudaMemcpyAsync(x->V, x->srhs, n2 * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+  if ((s = norms(x, x->V, n2)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
+  HBPC_LAUNCH_CK(x, "k_cycle_init (Schur)");
+  const int batch = 4;
+  int j_prev = 0;
+  for (;;) {
+    if ((s = arnoldi_batch(x, batch, 2)) != HBPC_OK) return s;
+    if ((s = read_state(x)) != HBPC_OK) return s;
+    const GmresState& h = *x->st_host;
+    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
+    j_prev = h.j;
+    if (!(h.resid == h.resid) || std::isinf(h.resid))
+      return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite (Schur)");
+    if (!h.done) continue;
+    // end of a cycle: dW += P^-1 V y
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<double><<<1, 32, 0, x->stream>>>(x->K));
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->sa, 0));
+    if (x->sol.pc != HBPC_PC_NONE) {
+      if ((s = pc_apply(x, x->sa, nullptr, nullptr, x->sb, 0, nullptr)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_half<<<grid_for(n), 256, 0, x->stream>>>(x->sb, x->dX, n));
+    } else {
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_half<<<grid_for(n), 256, 0, x->stream>>>(x->sa, x->dX, n));
+    }
+    HBPC_LAUNCH_CK(x, "GMRES update (Schur)");
+    if (h.converged || h.its >= h.max_its) {
+      *its_out = h.its;
+      *conv_out = h.converged != 0;
+      return HBPC_OK;
+    }
+    // restart: V_0 = rhs - J_Schur dW
+    HBPC_CK(x, cudaMemcpyAsync(x->sa, x->dX, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+    HBPC_CK(x, cudaMemsetAsync(x->sa + n, 0, n * sizeof(double), x->stream));
+    if ((s = schur_product(x, x->sb, nullptr, 0, nullptr)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_schur_restart<<<grid_for(n), 256, 0, x->stream>>>(x->srhs, x->sb, x->V, n));
+    if ((s = norms(x, x->V, n2)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
+    HBPC_LAUNCH_CK(x, "k_cycle_init (Schur restart)");
+    j_prev = 0;
+  }
+}
+
+// sigma increment of the Schur form: dX_S = -G2 + (dR1/dW) dW
+hbpc_status schur_sigma(hbpc_ctx* x) {
+  const size_t n = size_t(x->ndof);
+  HBPC_CK(x, cudaMemcpyAsync(x->sa, x->dX, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+  HBPC_CK(x, cudaMemsetAsync(x->sa + n, 0, n * sizeof(double), x->stream));
+  hbpc_status s = jv_plain(x, x->sa, x->sb, nullptr);
+  if (s != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_schur_sigma<<<grid_for(n), 256, 0, x->stream>>>(x->G, x->sb, x->dX, n));
+  HBPC_LAUNCH_CK(x, "Schur sigma");
+  return HBPC_OK;
+}
+
 JvInputT<float> krylov_input_f(hbpc_ctx* x) {
   JvInputT<float> z{};
   z.V = x->Vf; z.ld = size_t(2 * x->ndof); z.half = size_t(x->ndof);
@@ -1105,7 +1295,7 @@ hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
   const int batch = 4;
   int j_prev = 0;
   for (;;) {
-    if ((s = arnoldi_batch(x, batch, true)) != HBPC_OK) return s;
+    if ((s = arnoldi_batch(x, batch, 1)) != HBPC_OK) return s;
     if ((s = read_state(x)) != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
     x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
@@ -1251,7 +1441,10 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
     int its = 0;
     bool conv = false;
     if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
-    if (x->sol.precision == HBPC_PREC_MIXED) {
+    if (x->schur) {
+      if ((s = gmres_schur(x, &its, &conv)) != HBPC_OK) return s;
+      if ((s = schur_sigma(x)) != HBPC_OK) return s;
+    } else if (x->sol.precision == HBPC_PREC_MIXED) {
       if ((s = to_float(x, x->X, x->Wf, size_t(2 * n))) != HBPC_OK) return s;
       if ((s = gmres_f(x, &its, &conv)) != HBPC_OK) return s;
     } else {
@@ -1259,7 +1452,7 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
     }
     x->stats.gmres_its += its;
     x->stats.newton_its += 1;
-    const int per = x->ops.jv_linear ? 2 : 3;
+    const int per = (x->ops.jv_linear ? 2 : 3) * (x->schur ? 2 : 1);
     x->stats.r1_evals += (long long)its * (x->ops.jv_linear ? 2 : 1);
     x->stats.r2_evals += (long long)its * (per - (x->ops.jv_linear ? 2 : 1));
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add<<<grid_for(size_t(2 * n)), 256, 0, x->stream>>>(x->dX, x->X, size_t(2 * n)));
@@ -1487,6 +1680,7 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->dX); cudaFree(x->bvec); cudaFree(x->stage); cudaFree(x->V); cudaFree(x->small);
   cudaFree(x->partial); cudaFree(x->ticket); cudaFree(x->st);
   cudaFree(x->kron_d); cudaFree(x->kron_f); cudaFree(x->kron_ok);
+  cudaFree(x->sa); cudaFree(x->sb); cudaFree(x->srhs); cudaFree(x->snrm);
   cudaFree(x->Jpc); cudaFree(x->Mpc); cudaFree(x->Z); cudaFree(x->singular);
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
   cudaFree(x->vtab_d); cudaFree(x->vtab_f); cudaFree(x->vloc_d);
@@ -2333,9 +2527,28 @@ hbpc_status hbpc_set_wait_limit(hbpc_ctx* ctx, double seconds) {
   return HBPC_OK;
 }
 
+hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
+  if (!on) { ctx->schur = false; return HBPC_OK; }
+  if (ctx->ninst > 0) return fail(ctx, HBPC_ERR_UNSUPPORTED, "the Schur form is for single problems");
+  if (ctx->cb) return fail(ctx, HBPC_ERR_UNSUPPORTED, "the Schur form needs corrector batching off");
+  if (ctx->sol.precision != HBPC_PREC_FP64)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "the Schur form is built for the FP64 mode");
+  if (!ctx->sa) {
+    const size_t n2 = size_t(2 * ctx->ndof);
+    hbpc_status s;
+    if ((s = dmalloc(ctx, &ctx->sa, n2)) || (s = dmalloc(ctx, &ctx->sb, n2)) || (s = dmalloc(ctx, &ctx->srhs, n2)) ||
+        (s = dmalloc(ctx, &ctx->snrm, 4)))
+      return s;
+  }
+  ctx->schur = true;
+  return HBPC_OK;
+}
+
 hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
   if (ctx->ninst > 0) return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching is for single problems");
+  if (on && ctx->schur) return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching needs the Schur form off");
   hbpc_status s = sync(ctx, "set_corrector_batch");
   if (s != HBPC_OK) return s;
   if (!on) {

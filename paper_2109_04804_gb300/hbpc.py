@@ -95,6 +95,7 @@ _SIGS = {
     "hbpc_run": (_I, [_CTX]),
     "hbpc_set_wait_limit": (_I, [_CTX, _D]),
     "hbpc_set_corrector_batch": (_I, [_CTX, _I]),
+    "hbpc_set_schur": (_I, [_CTX, _I]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -285,6 +286,10 @@ class Context:
 
     def set_wait_limit(self, seconds):
         self._c(_lib.hbpc_set_wait_limit(self._ctx, seconds))
+
+    def set_schur(self, on=True):
+        """Newton steps through the Schur-complement system of Sec. 3.2.4 (FP64)."""
+        self._c(_lib.hbpc_set_schur(self._ctx, 1 if on else 0))
 
     def set_corrector_batch(self, on=True):
         """Solve the s - 1 corrector stages of every sweep as one batched Newton."""

@@ -332,6 +332,16 @@ typedef enum { HBPC_PC_LOSS_PROBE = 0, HBPC_PC_LOSS_INVERSE = 1 } hbpc_pc_loss;
  * grads (host, n_params) may be NULL. */
 hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int loss_kind, int B, int P, const float* F, const float* J,
                               const float* c12, const float* X, double* loss, float* grads);
+/* The network's block approximations for given inputs (host): F (B x
+ * d_in_padded, already standardised), c12 (B x 2) -> M (B x n_b x n_b,
+ * row-major) = I + C_k + reshape(O), the same BF16 GEMM chain with FP32
+ * accumulation as the preconditioner build.  B a multiple of 8. */
+hbpc_status hbpc_pc_model_forward(hbpc_ctx* ctx, int B, const float* F, const float* c12, float* M);
+/* One Adam step (Kingma & Ba 2015; b1 = 0.9, b2 = 0.999, eps = 1e-8, the
+ * training's settings and its step counter) of the network parameters with
+ * the given gradient (host, the first n_params - (2 d_in_padded + classes)
+ * entries: the weights and biases). */
+hbpc_status hbpc_pc_adam_step(hbpc_ctx* ctx, const float* grads, double lr);
 /* Sample `samples_per_newton` elements' (features, J_e, c1, c2) at every Newton
  * iteration that builds a block preconditioner into a replay buffer of
  * `capacity` samples (0 stops sampling); with the BJ_ext preconditioner the

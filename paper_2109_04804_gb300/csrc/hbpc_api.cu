@@ -2823,6 +2823,48 @@ hbpc_status hbpc_pc_loss_grad(hbpc_ctx* ctx, int loss_kind, int B, int P, const 
   return sync(ctx, "pc_loss_grad");
 }
 
+hbpc_status hbpc_pc_model_forward(hbpc_ctx* ctx, int B, const float* F, const float* c12, float* M) {
+  if (!ctx || !F || !c12 || !M || B < 8 || B % 8) return HBPC_ERR_INVALID_ARG;
+  if (!ctx->lp.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
+  hbpc_status s;
+  if ((s = lp_alloc_train(ctx, B, 1)) != HBPC_OK) return s;
+  auto& L = ctx->lp;
+  const size_t nf = size_t(B) * L.dinp;
+  // the features go through the block buffer (B x n_b^2 FP32, wider than the
+  // B x d_in_padded features), FP32 -> BF16 on the device
+  if (nf > size_t(B) * L.dout) return fail(ctx, HBPC_ERR_UNSUPPORTED, "feature rows wider than the blocks");
+  HBPC_CK(ctx, cudaMemcpyAsync(L.Jb, F, nf * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(nf), 256, 0, ctx->stream>>>(L.Jb, L.Fb, nf));
+  HBPC_CK(ctx, cudaMemcpyAsync(L.cb, c12, size_t(B) * 2 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  const int H = L.H;
+  if ((s = gemm(ctx, L.Fb, L.dinp, L.W1h, L.dinp, B, H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1b, H})) != HBPC_OK) return s;
+  if ((s = gemm(ctx, L.H1b, H, L.W2h, H, B, H, H, EpiBiasTanh{L.P + L.ob2, L.H2b, H})) != HBPC_OK) return s;
+  if ((s = gemm(ctx, L.H2b, H, L.W3h, H, B, L.doutp, H, EpiBiasF32{L.P + L.ob3, L.Ob, L.doutp})) != HBPC_OK) return s;
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_mlp_classify<<<(B + 255) / 256, 256, 0, ctx->stream>>>(L.cb, B, L.ckey, L.cls));
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_mlp_mtilde<<<B, 256, 0, ctx->stream>>>(L.Ob, B, L.nb, L.doutp, L.cmean, L.cls, L.Jb));
+  HBPC_LAUNCH_CK(ctx, "pc_model_forward");
+  HBPC_CK(ctx, cudaMemcpyAsync(M, L.Jb, size_t(B) * L.dout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx, "pc_model_forward");
+}
+
+hbpc_status hbpc_pc_adam_step(hbpc_ctx* ctx, const float* grads, double lr) {
+  if (!ctx || !grads || !(lr > 0.0)) return HBPC_ERR_INVALID_ARG;
+  if (!ctx->lp.alloc) return fail(ctx, HBPC_ERR_INVALID_ARG, "model not initialised");
+  auto& L = ctx->lp;
+  HBPC_CK(ctx, cudaMemcpyAsync(L.G, grads, L.np_train * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  L.adam_t += 1;
+  const float bc1 = 1.0f - std::pow(b1, float(L.adam_t)), bc2 = 1.0f - std::pow(b2, float(L.adam_t));
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1,
+           k_adam<<<grid_for(L.np_train), 256, 0, ctx->stream>>>(L.P, L.G, L.Mo, L.Ve, L.np_train, float(lr), b1, b2, eps,
+                                                               bc1, bc2));
+  HBPC_LAUNCH_CK(ctx, "k_adam");
+  hbpc_status s = lp_refresh(ctx);
+  if (s != HBPC_OK) return s;
+  ctx->pc_built = false;
+  return sync(ctx, "pc_adam_step");
+}
+
 hbpc_status hbpc_pc_collect(hbpc_ctx* ctx, int samples_per_newton, int capacity) {
   if (!ctx || samples_per_newton < 0 || capacity < 0) return HBPC_ERR_INVALID_ARG;
   hbpc_status s;

@@ -298,6 +298,20 @@ __global__ void k_mlp_collect_target(const T* __restrict__ Mpc, int nE, int nb, 
     Tbuf[row * nb * nb + t] = float(Mpc[size_t(e) * nb * nb + t]);
 }
 
+// M~_b = I + C_k + reshape(O_b) (row-major n_b x n_b) for sample b of stage
+// class k = cls[b]; one block per sample.
+__global__ void k_mlp_mtilde(const float* __restrict__ O, int B, int nb, int doutp, const float* __restrict__ cmean,
+                             const int* __restrict__ cls, float* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const float* Ob = O + size_t(b) * doutp;
+  const float* Cb = cmean + size_t(cls[b]) * doutp;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    out[size_t(b) * nb * nb + t] = (i == j ? 1.f : 0.f) + Cb[t] + Ob[t];
+  }
+}
+
 // Adam (Kingma & Ba 2015) on FP32 parameters.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float bc1,

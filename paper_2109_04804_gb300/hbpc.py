@@ -109,6 +109,8 @@ _SIGS = {
     "hbpc_pc_model_set": (_I, [_CTX, _P]),
     "hbpc_pc_loss_grad": (_I, [_CTX, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "hbpc_pc_collect": (_I, [_CTX, _I, _I]),
+    "hbpc_pc_model_forward": (_I, [_CTX, _I, _P, _P, _P]),
+    "hbpc_pc_adam_step": (_I, [_CTX, _P, _D]),
     "hbpc_pc_train": (_I, [_CTX, _I, _I, _I, _I, _D, ctypes.c_ulonglong, _P, _P]),
     "hbpc_fp64_fma_peak": (_I, [ctypes.POINTER(ctypes.c_double)]),
     "hbpc_eval_Jv_noalloc": (_I, [ctypes.POINTER(Mesh), _I, _I, ctypes.POINTER(Physics), _D, _D, _D,
@@ -354,6 +356,20 @@ class Context:
         self._c(_lib.hbpc_pc_loss_grad(self._ctx, kind, B, P, F.ctypes.data, J.ctypes.data, c12.ctypes.data,
                                        xp, ctypes.addressof(out), grads.ctypes.data))
         return out.value, grads
+
+    def pc_model_forward(self, F, c12):
+        """The network's blocks M~ (B x n_b x n_b) for standardised features F and (c1, c2)."""
+        F = np.ascontiguousarray(F, dtype=np.float32)
+        c12 = np.ascontiguousarray(c12, dtype=np.float32)
+        B = F.shape[0]
+        nb = self.nv * (self.N + 1) ** self.dim
+        out = np.zeros((B, nb, nb), dtype=np.float32)
+        self._c(_lib.hbpc_pc_model_forward(self._ctx, B, F.ctypes.data, c12.ctypes.data, out.ctypes.data))
+        return out
+
+    def pc_adam_step(self, grads, lr):
+        grads = np.ascontiguousarray(grads, dtype=np.float32)
+        self._c(_lib.hbpc_pc_adam_step(self._ctx, grads.ctypes.data, lr))
 
     def pc_collect(self, samples_per_newton, capacity):
         self._c(_lib.hbpc_pc_collect(self._ctx, samples_per_newton, capacity))

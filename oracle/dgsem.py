@@ -110,12 +110,25 @@ class Disc:
         return np.expand_dims(f, axis) * lhat.reshape(shp)
 
 
-def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False):
+def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False, frozen_neighbor_state=False):
     """R^(1)(w) if mode == "R1"; R^(2)(w, sigma) if mode == "R2".
 
     frozen_neighbor (R2 only): the neighbours' sigma traces are taken as zero,
     which gives the element-local linearisation used by the block
-    preconditioners of Sec. 3.2.3 (neighbour dependencies neglected)."""
+    preconditioners of Sec. 3.2.3 (neighbour dependencies neglected).
+
+    frozen_neighbor_state (R2 only, inviscid and scalar viscous laws): for a
+    complex state w, the neighbours' state traces enter with their real parts
+    and the dissipation coefficient kappa is that of the real traces, so that
+    Im R2(W + i h e_k, sigma) / h is the derivative of R2 with respect to the
+    element's own node k at fixed sigma and fixed neighbour states: the
+    element block of dR2/dW, where the physical flux Jacobians of the
+    assembly are replaced by the physical flux Hessians (Sec. 3.2.2); the
+    dissipation coefficient is not differentiated."""
+    if frozen_neighbor and frozen_neighbor_state:
+        raise ValueError("frozen_neighbor and frozen_neighbor_state exclude each other")
+    if frozen_neighbor_state and (mode != "R2" or disc.ph.law == laws.NAVIER_STOKES):
+        raise ValueError("frozen_neighbor_state: R2 of an inviscid or scalar viscous law only")
     ph, b = disc.ph, disc.basis
     W = disc.to_grid(w)
     S = disc.to_grid(sigma) if sigma is not None else None
@@ -142,7 +155,19 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False):
             sp = Disc._trace(b.l_p, S, na)
             sm = Disc._trace(b.l_m, S, na)
             sR = np.roll(sm, -1, axis=ea)
-            if not frozen_neighbor:
+            if frozen_neighbor_state:
+                # + face (e, e+1): neighbour trace wR; - face (e-1, e): the
+                # neighbour's + trace, both real, kappa of the real traces
+                wRr = np.real(wR)
+                wLr = np.roll(np.real(wp), 1, axis=ea)
+                sL = np.roll(sp, 1, axis=ea)
+                kp = laws.dissipation(np.real(wp), wRr, m, ph)
+                km = laws.dissipation(wLr, np.real(wm), m, ph)
+                fplus = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wRr, sR, m, ph))
+                         + kp * (sp - sR))
+                fminus = -(0.5 * (laws.flux_jvp(wLr, sL, m, ph) + laws.flux_jvp(wm, sm, m, ph))
+                           + km * (sL - sm))
+            elif not frozen_neighbor:
                 fface = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wR, sR, m, ph))
                          + kappa * (sp - sR))
                 fplus = fface

@@ -119,7 +119,7 @@ def flux_jvp(w, s, m, ph):
     v2 = sum(vk * vk for vk in v)
     vdots = sum(v[k] * smom[k] for k in range(d))
     dp = (g - 1.0) * (sE - e2 * vdots + 0.5 * e2 * v2 * srho)
-    J = np.empty_like(s)
+    J = np.empty(s.shape, dtype=np.result_type(w, s))   # complex w: complex step in w
     J[0] = smom[m]
     for k in range(d):
         J[1 + k] = v[m] * smom[k] + v[k] * smom[m] - v[m] * v[k] * srho

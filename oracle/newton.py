@@ -1,5 +1,5 @@
 """Implicit stage solve of the HBPC scheme: extended residual, matrix-free
-Jacobian-vector product, GMRES, Newton and the BJ_ext preconditioner.
+Jacobian-vector product, GMRES, Newton and the BJ_ext and BJ^H_ext preconditioners.
 Test infrastructure only (see ``oracle/__init__``).
 
 Extended unknown X = (W, sigma) (Sec. 3.2.1).  Residual (reading: the printed
@@ -166,6 +166,40 @@ def gmres(matvec, rhs, tol, restart, maxiter, precond=None):
         r = rhs - matvec(x)
 
 
+def element_jacobians(disc, W):
+    """J_i = dR1/dW restricted to element i (neighbours frozen), column k of
+    every element at once as R2(W, e_k) with the neighbours' sigma traces zero
+    (dR2/dsigma = dR1/dW, Sec. 3.2.1).  Returns (n_E, n_b, n_b)."""
+    nE = disc.mesh.nE
+    nb = disc.ndof // nE
+    J = np.zeros((nE, nb, nb))
+    for k in range(nb):
+        v = np.zeros((nE, nb))
+        v[:, k] = 1.0
+        col = dgsem.operator(disc, W, v.reshape(disc.shape), mode="R2", frozen_neighbor=True)
+        J[:, :, k] = col.reshape(nE, nb)
+    return J
+
+
+def element_hessian_blocks(disc, W, S, h=1e-30):
+    """H_i = dR2/dW restricted to element i at fixed sigma = S (neighbour
+    states and sigma fixed), the Hessian contribution of Sec. 3.2.2, column k
+    of every element at once by complex step in the elements' own node k:
+        H_i[:, k] = Im R2(W + i h e_k, S) / h
+    with the neighbours' traces real (operator's frozen_neighbor_state).
+    Exact to rounding for h = 1e-30 (no subtraction).  Returns (n_E, n_b, n_b)."""
+    nE = disc.mesh.nE
+    nb = disc.ndof // nE
+    H = np.zeros((nE, nb, nb))
+    W0 = np.asarray(W, dtype=np.complex128).reshape(nE, nb)
+    for k in range(nb):
+        Wc = W0.copy()
+        Wc[:, k] += 1j * h
+        col = dgsem.operator(disc, Wc.reshape(disc.shape), S, mode="R2", frozen_neighbor_state=True)
+        H[:, :, k] = np.imag(col).reshape(nE, nb) / h
+    return H
+
+
 class BJExt:
     """BJ_ext preconditioner (Sec. 3.2.3): per element J_i = dR1/dW restricted
     to the element (neighbour dependencies neglected), M_i = (A_i - B_i C_i)^-1
@@ -177,13 +211,7 @@ class BJExt:
         disc = system.disc
         nE = disc.mesh.nE
         nb = disc.ndof // nE
-        J = np.zeros((nE, nb, nb))
-        for k in range(nb):
-            v = np.zeros((nE, nb))
-            v[:, k] = 1.0
-            col = dgsem.operator(disc, W, v.reshape(disc.shape), mode="R2",
-                                 frozen_neighbor=True)
-            J[:, :, k] = col.reshape(nE, nb)
+        J = element_jacobians(disc, W)
         I = np.eye(nb)[None]
         S = I - system.c1 * J + system.c2 * (J @ J)
         self.J = J
@@ -208,6 +236,52 @@ class BJExt:
         return np.concatenate([top.ravel(), bot.ravel()])
 
 
+class BJExtH:
+    """BJ^H_ext preconditioner (Sec. 3.2.3): the blocks of P keep the Hessian
+    contribution in A,
+        A_i = I - a1 dt J_i + (a2 dt^2/2) H_i,  B_i = (a2 dt^2/2) J_i,  C_i = -J_i,
+    with J_i of BJ_ext and H_i = element_hessian_blocks at the current (W,
+    sigma).  A_i no longer commutes with B_i, so the inverse blocks are
+        D = M, E = -M B, F = -C M, G = I + C M B,  M = (A - B C)^-1
+    with A - B C = I - a1 dt J + (a2 dt^2/2) H + (a2 dt^2/2) J^2 (one LU per
+    element), and P^-1 (w, s) = (D w + E s, F w + G s)."""
+
+    def __init__(self, system, W, S):
+        disc = system.disc
+        nE = disc.mesh.nE
+        nb = disc.ndof // nE
+        self.J = element_jacobians(disc, W)
+        self.H = element_hessian_blocks(disc, W, S)
+        I = np.eye(nb)[None]
+        self.c1, self.c2 = system.c1, system.c2
+        A = I - self.c1 * self.J + self.c2 * self.H
+        B = self.c2 * self.J
+        C = -self.J
+        self.M = np.linalg.inv(A - B @ C)
+        self.nE, self.nb, self.n = nE, nb, disc.ndof
+        self._blocks = (self.M, -self.M @ B, -C @ self.M, I + C @ self.M @ B)
+
+    def __call__(self, X):
+        D, E, F, G = self._blocks
+        w = X[:self.n].reshape(self.nE, self.nb, 1)
+        s = X[self.n:].reshape(self.nE, self.nb, 1)
+        top = D @ w + E @ s
+        bot = F @ w + G @ s
+        return np.concatenate([top.ravel(), bot.ravel()])
+
+
+def make_preconditioner(sysm, X, kind):
+    """None, BJ_ext ("bjext") or BJ^H_ext ("bjext_h") at X = (W, sigma)."""
+    W, S = sysm.split(X)
+    if kind == "bjext":
+        return BJExt(sysm, W)
+    if kind == "bjext_h":
+        return BJExtH(sysm, W, S)
+    if kind == "none":
+        return None
+    raise ValueError(kind)
+
+
 class NewtonOptions:
     def __init__(self, tol_rel=1e-12, tol_abs=0.0, gmres_tol=1e-5, restart=100,
                  gmres_maxiter=7000, newton_max=50, jv="fd", pc="none"):
@@ -227,8 +301,7 @@ def newton_solve(disc, b, alpha1, alpha2, dt, W0, opts, stats=None):
     converged = g0 == 0.0
     r = 0
     while not converged and r < opts.newton_max:
-        W, _ = sysm.split(X)
-        pc = BJExt(sysm, W) if opts.pc == "bjext" else None
+        pc = make_preconditioner(sysm, X, opts.pc)
         dX, its, _ = gmres(lambda v: sysm.jv(X, r1, r2, v, opts.jv), -G,
                            opts.gmres_tol, opts.restart, opts.gmres_maxiter, pc)
         st.gmres_its += its
@@ -254,7 +327,8 @@ def schur_step(sysm, X, r1, r2, G, opts):
     (v, dR1/dW v), in the same form (opts.jv) as newton_solve.  With
     opts.pc == "bjext" GMRES is right preconditioned by the element blocks
     (I - a1 dt J_i + (a2 dt^2/2) J_i^2)^-1 (the D block of BJ_ext, the
-    element-local J_Schur without the Hessian).  Returns (dX, GMRES iterations)."""
+    element-local J_Schur without the Hessian); with "bjext_h" by the D block
+    of BJ^H_ext, (I - a1 dt J_i + (a2 dt^2/2) (H_i + J_i^2))^-1.  Returns (dX, GMRES iterations)."""
     disc, n = sysm.disc, sysm.n
     zero = np.zeros(n)
     W, _ = sysm.split(X)
@@ -268,8 +342,8 @@ def schur_step(sysm, X, r1, r2, G, opts):
 
     rhs = -G1 + sysm.c2 * sysm.R2(W, G2.reshape(disc.shape)).ravel()
     pc = None
-    if opts.pc == "bjext":
-        blocks = BJExt(sysm, W)
+    if opts.pc in ("bjext", "bjext_h"):
+        blocks = make_preconditioner(sysm, X, opts.pc)
 
         def pc(v, M=blocks.M):
             return (M @ v.reshape(blocks.nE, blocks.nb, 1)).ravel()

@@ -70,9 +70,17 @@ typedef enum { HBPC_NODES_LOBATTO = 0, HBPC_NODES_GAUSS = 1 } hbpc_nodes;
  * n_var (N+1)^dim <= 160 and 2 n_E (n_var (N+1)^dim)^2 doubles of device memory.
  * LEARNED: the BJ_ext structure with the block inverse (I - c1 J + c2 J^2)^-1
  * replaced by a learned per-element network (hbpc_pc_* below; no counterpart in
- * the paper).  The preconditioner never changes the answer, only the GMRES
- * iteration count: Newton stops on the same FP64 residual. */
-typedef enum { HBPC_PC_NONE = 0, HBPC_PC_BJEXT = 1, HBPC_PC_LEARNED = 2 } hbpc_pc;
+ * the paper).  BJEXT_H: the BJ^H_ext preconditioner of Sec. 3.2.3, BJ_ext with
+ * the element Hessian block H_i = dR2/dW|_i (at the current sigma, neighbours
+ * frozen, the Rusanov kappa not differentiated) kept in A_i, so that
+ * M_i = (I - c1 J_i + c2 H_i + c2 J_i^2)^-1 and P^-1 (w, s) = (u, J u + s) with
+ * u = M (w - c2 J s); the same size limit and memory as BJEXT.  For a linear
+ * flux H = 0 and BJEXT_H is BJEXT; Navier-Stokes is HBPC_ERR_UNSUPPORTED (the
+ * paper also drops the Hessian there).  With hbpc_set_schur the D block of
+ * either preconditions the Schur system.  The preconditioner never changes the
+ * answer, only the GMRES iteration count: Newton stops on the same FP64
+ * residual. */
+typedef enum { HBPC_PC_NONE = 0, HBPC_PC_BJEXT = 1, HBPC_PC_LEARNED = 2, HBPC_PC_BJEXT_H = 3 } hbpc_pc;
 
 /* Arithmetic of the Krylov loop.  FP64: everything in FP64, Jv by the
  * difference quotients of Eq. 23 (Eq. 24 for a linear flux).  MIXED: the
@@ -271,9 +279,10 @@ hbpc_status hbpc_eval_G(hbpc_ctx* ctx, const double* b, double alpha1, double al
 hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
                          const double* dX, double* out);
 
-/* Block preconditioner (BJ_ext of Sec. 3.2.3, or the learned blocks) built at
- * the state W of X = (W, S) for the stage coefficients alpha1, alpha2, applied
- * to `in`: out = P^-1 in.  Needs a context with pc != HBPC_PC_NONE.  In the
+/* Block preconditioner (BJ_ext or BJ^H_ext of Sec. 3.2.3, or the learned
+ * blocks) built at the state W of X = (W, S) (BJ^H_ext: its Hessian blocks at
+ * (W, S)) for the stage coefficients alpha1, alpha2, applied to `in`:
+ * out = P^-1 in.  Needs a context with pc != HBPC_PC_NONE.  In the
  * MIXED precision mode the blocks S_e, their inverses and the apply are FP32
  * (what the Krylov loop uses); in FP64 mode everything is FP64.
  * X, in, out: device, 2 n_dof FP64. */

@@ -7,6 +7,11 @@
 //   A = I - c1 J, B = c2 J, C = -J; because J commutes with M this is applied as
 //     u = M w, v = M s,  top = u - c2 J v,  bottom = J u + v - c1 J v.
 //
+// BJ^H_ext keeps the Hessian block H_i = dR2/dW|_i in A = I - c1 J + c2 H:
+//   M_i = (I - c1 J_i + c2 H_i + c2 J_i^2)^-1,
+//   D = M, E = -M B, F = -C M, G = I + C M B, applied as
+//     t = w - c2 J s,  u = M t,  top = u,  bottom = J u + s.
+//
 // Storage: per element an n_b x n_b block, column-major (entry (r, c) at
 // c * n_b + r), n_b = n_var (N+1)^dim, so that the threads of one element, one
 // per row, read consecutive addresses.
@@ -22,16 +27,28 @@ namespace hbpc {
 // derivative with respect to the element's own trace (the neighbour is frozen).
 // A BR2 viscous term adds nu times its element-diagonal block along the line
 // (a constant table, the same for every element).
-template <int LAW, int DIM, int P, bool LGL, typename T = double>
+//
+// HESS = true assembles instead the Hessian block H_i = dR2/dW restricted to
+// element i at fixed sigma (BJ^H_ext, Sec. 3.2.3): the same routine with the
+// physical flux Jacobian A(w) e_u replaced by the flux Hessian H(w)[sigma, e_u]
+// (Sec. 3.2.2), evaluated in dual numbers as the derivative of A(w + eps e_u)
+// sigma; sigma is the element's own (volume node, or own face trace).  The
+// dissipation coefficient is not differentiated and the viscous part of R2 is
+// linear in sigma, so neither contributes.  Sg: sigma, same layout as W.
+template <int LAW, int DIM, int P, bool LGL, typename T = double, bool HESS = false>
 __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ W, T* __restrict__ Jout,
-                                                     const DGParams<T> prm) {
+                                                     const DGParams<T> prm, const double* __restrict__ Sg = nullptr) {
   using L = typename LawOf<LAW, DIM, T>::type;
+  using D = Dual<T>;
   constexpr int NV = L::NV, NN = ipow(P, DIM), NB = NV * NN;
   const int e = blockIdx.x;
   if (e >= prm.nE) return;
   T* J = Jout + size_t(e) * NB * NB;
   __shared__ T sw[NB];
+  __shared__ T ss[HESS ? NB : 1];
   for (int t = threadIdx.x; t < NB; t += blockDim.x) sw[t] = T(W[size_t(e) * NB + t]);
+  if constexpr (HESS)
+    for (int t = threadIdx.x; t < NB; t += blockDim.x) ss[t] = T(Sg[size_t(e) * NB + t]);
   for (size_t t = threadIdx.x; t < size_t(NB) * NB; t += blockDim.x) J[t] = T(0);
   __syncthreads();
   // the instance of this element (batches): its mesh and scales; padding
@@ -55,7 +72,20 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
       const int st = (m == 0) ? 1 : (m == 1 ? P : P * P);
       const int b0 = q - qi[m] * st;
       T a[NV];
-      if constexpr (L::LINEAR) {
+      if constexpr (HESS) {
+        // H^m(w_q)[sigma_q, e_u]: eps part of A^m(w_q + eps e_u) sigma_q
+        if constexpr (L::LINEAR) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) a[v] = T(0);
+        } else {
+          D wd[NV], sd[NV], hd[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) { wd[v] = D(wq[v], eu[v]); sd[v] = D(ss[v * NN + q]); }
+          L::jvp(wd, sd, m, hd, prm);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) a[v] = hd[v].d;
+        }
+      } else if constexpr (L::LINEAR) {
         // a_m is folded into Dvol unless a viscous term is present
         const T am = prm.visc ? prm.a[m] : T(1);
 #pragma unroll
@@ -70,20 +100,25 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
         for (int v = 0; v < NV; ++v) Jc[v * NN + b0 + l * st] += hs * prm.Dvol[m][l][qi[m]] * a[v];
       // BR2 viscous term (scalar laws): its element-diagonal block along the line
       // (a second-derivative operator: two factors 2/h)
-      if constexpr (NV == 1) {
+      if constexpr (NV == 1 && !HESS) {
         if (prm.visc)
           for (int l = 0; l < P; ++l) Jc[b0 + l * st] += geo.nu * hs * hs * T(prm.vloc[(m * P + l) * P + qi[m]]);
       }
       // faces: own traces at the - and + face of the line through q
       T Ap[NV];
-      L::jvp(wq, eu, m, Ap, prm);   // dF^m/dw at w_q applied to e_u (used for Lobatto)
+      if constexpr (HESS) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ap[v] = a[v];   // the node's Hessian term (Lobatto)
+      } else {
+        L::jvp(wq, eu, m, Ap, prm);   // dF^m/dw at w_q applied to e_u (used for Lobatto)
+      }
       for (int side = 0; side < 2; ++side) {
         const T lq = side ? prm.lp[qi[m]] : prm.lm[qi[m]];   // d(own trace)/d(w_q)
         if (lq == T(0)) continue;
         // own trace t_o and neighbour trace t_n at this face point
-        T to[NV], tn[NV];
+        T to[NV], tn[NV], so[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { to[v] = T(0); tn[v] = T(0); }
+        for (int v = 0; v < NV; ++v) { to[v] = T(0); tn[v] = T(0); so[v] = T(0); }
         int nc[3] = {ec[0], ec[1], ec[2]};
         nc[m] += side ? 1 : -1;
         if (nc[m] < 0) nc[m] += geo.n[m];
@@ -95,17 +130,34 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             to[v] += lo * sw[v * NN + b0 + i * st];
-            tn[v] += ln * T(W[(size_t(en) * NV + v) * NN + b0 + i * st]);
+            if constexpr (HESS) so[v] += lo * ss[v * NN + b0 + i * st];
+            else tn[v] += ln * T(W[(size_t(en) * NV + v) * NN + b0 + i * st]);
           }
         }
         T A[NV], kap[NV];
         if (LGL) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) A[v] = Ap[v];
+        } else if constexpr (HESS) {
+          if constexpr (L::LINEAR) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) A[v] = T(0);
+          } else {
+            D td[NV], sd[NV], hd[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { td[v] = D(to[v], eu[v]); sd[v] = D(so[v]); }
+            L::jvp(td, sd, m, hd, prm);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) A[v] = hd[v].d;
+          }
         } else {
           L::jvp(to, eu, m, A, prm);
         }
-        if (prm.rusanov) {
+        if (HESS) {
+          // sigma's jump does not depend on W and kappa is not differentiated
+#pragma unroll
+          for (int v = 0; v < NV; ++v) kap[v] = T(0);
+        } else if (prm.rusanov) {
           const T c = T(0.5) * fmax(L::speed(to, m, prm), L::speed(tn, m, prm));
 #pragma unroll
           for (int v = 0; v < NV; ++v) kap[v] = c;
@@ -153,6 +205,9 @@ struct PcApplyT {
   // (kron[m][i][l], row-major, direction m), valid when *kron_ok != 0
   const S* kron; const int* kron_ok;
   int P, dim;
+  // BJ^H_ext (M = (I - c1 J + c2 H + c2 J^2)^-1): A no longer commutes with B,
+  // and P^-1 (w, s) is applied as t = w - c2 J s, u = M t, (u, J u + s)
+  int hess;
 };
 using PcApply = PcApplyT<double>;
 

@@ -9,9 +9,13 @@ namespace hbpc {
 // S = I - c1 J + c2 J^2 for one element per block (J staged in shared memory),
 // written to `S` (same layout), in T (FP64, or FP32 for the mixed-precision
 // mode, where the blocks only precondition).  Dynamic shared memory: nb * nb T.
+//
+// Hall (BJ^H_ext): the Hessian blocks, S = I - c1 J + c2 (H + J^2); may be
+// the same buffer as Sall (each entry is read once, before it is written).
 template <typename T>
-__global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T* __restrict__ Sall, int nb,
-                                                   int nE, const double* c12, const int* only = nullptr) {
+__global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T* Sall, int nb,
+                                                   int nE, const double* c12, const int* only = nullptr,
+                                                   const T* Hall = nullptr) {
   const int e = blockIdx.x;
   if (e >= nE || (only && !only[e])) return;   // only: the elements flagged for an exact block
   extern __shared__ __align__(16) unsigned char sJ_raw[];
@@ -21,9 +25,10 @@ __global__ void __launch_bounds__(256) k_pc_form_S(const T* __restrict__ Jall, T
   __syncthreads();
   const T c1 = T(c12[0]), c2 = T(c12[1]);
   T* S = Sall + size_t(e) * nb * nb;
+  const T* H = Hall ? Hall + size_t(e) * nb * nb : nullptr;
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
     const int c = t / nb, r = t - c * nb;          // entry (r, c)
-    T jj = T(0);
+    T jj = H ? H[t] : T(0);
     for (int k = 0; k < nb; ++k) jj += sJ[k * nb + r] * sJ[c * nb + k];   // (J J)(r, c)
     S[t] = (r == c ? T(1) : T(0)) - c1 * sJ[t] + c2 * jj;
   }
@@ -175,6 +180,52 @@ __global__ void __launch_bounds__(256) k_pc_verify(const S* __restrict__ M, cons
   }
 }
 
+// Row r of the column-major n_b x n_b block A times x (shared memory): four
+// columns' loads in flight, the sum in column order.
+template <typename S>
+__device__ __forceinline__ S pc_row_dot(const S* __restrict__ A, int nb, int r, const S* x) {
+  S y = S(0);
+  int c = 0;
+  for (; c + 3 < nb; c += 4) {
+    const S a0 = A[size_t(c) * nb + r], a1 = A[size_t(c + 1) * nb + r];
+    const S a2 = A[size_t(c + 2) * nb + r], a3 = A[size_t(c + 3) * nb + r];
+    y += a0 * x[c];
+    y += a1 * x[c + 1];
+    y += a2 * x[c + 2];
+    y += a3 * x[c + 3];
+  }
+  for (; c < nb; ++c) y += A[size_t(c) * nb + r] * x[c];
+  return y;
+}
+
+// The norms of the apply's result (total, W half, S half) through the last
+// block, when the caller asked for them (a.zn); aw, as: this thread's squares.
+template <typename S>
+__device__ __forceinline__ void pc_apply_norms(const PcApplyT<S>& a, const Krylov& K, double aw, double as) {
+  if (!a.zn) return;   // norms only needed by the difference-quotient Jv
+  __shared__ double s2[2][kVecWarps];
+  aw = warp_sum(aw);
+  as = warp_sum(as);
+  if ((threadIdx.x & 31) == 0) { s2[0][threadIdx.x >> 5] = aw; s2[1][threadIdx.x >> 5] = as; }
+  __syncthreads();
+  const int stride = K.m + 3;
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { ta += s2[0][w]; tb += s2[1][w]; }
+    K.partial[size_t(blockIdx.x) * stride + 0] = ta;
+    K.partial[size_t(blockIdx.x) * stride + 1] = tb;
+  }
+  if (!last_block(K.ticket, gridDim.x)) return;
+  __shared__ double rr[2];
+  reduce_partials(K.partial, stride, gridDim.x, 2, rr);
+  __syncthreads();
+  if (threadIdx.x == 0 && a.zn) {
+    a.zn[0] = sqrt(rr[0] + rr[1]);
+    a.zn[1] = sqrt(rr[0]);
+    a.zn[2] = sqrt(rr[1]);
+  }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
   if (a.skip && *a.skip) return;
@@ -196,6 +247,27 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
     xs[r] = sc * a.xS[off + r];
   }
   __syncthreads();
+  if (a.hess) {   // BJ^H_ext (uniform over the block): t = w - c2 J s, u = M t
+    const S* Me = a.M + size_t(live ? e : 0) * nb * nb;
+    const S* Je = a.J + size_t(live ? e : 0) * nb * nb;
+    if (live) sv[r] = xw[r] - S(a.c12[1]) * pc_row_dot(Je, nb, r, xs);
+    __syncthreads();
+    if (live) su[r] = pc_row_dot(Me, nb, r, sv);
+    __syncthreads();
+    double aw = 0.0, as = 0.0;
+    if (live) {
+      S top = su[r];
+      S bot = pc_row_dot(Je, nb, r, su) + xs[r];
+      const size_t o = size_t(e) * nb + r;
+      if (a.accumulate) { top += a.oW[o]; bot += a.oS[o]; }
+      a.oW[o] = top;
+      a.oS[o] = bot;
+      aw = double(top * top);
+      as = double(bot * bot);
+    }
+    pc_apply_norms(a, K, aw, as);
+    return;
+  }
   S u = S(0), v = S(0);
   if (live) {
     const S* Me = a.M + (a.shared ? size_t(0) : size_t(e) * nb * nb);
@@ -245,29 +317,7 @@ __global__ void __launch_bounds__(256) k_pc_apply(PcApplyT<S> a, Krylov K) {
     aw = double(top * top);
     as = double(bot * bot);
   }
-  if (!a.zn) return;   // norms only needed by the difference-quotient Jv
-  // norms of the result through the last block
-  __shared__ double s2[2][kVecWarps];
-  aw = warp_sum(aw);
-  as = warp_sum(as);
-  if ((threadIdx.x & 31) == 0) { s2[0][threadIdx.x >> 5] = aw; s2[1][threadIdx.x >> 5] = as; }
-  __syncthreads();
-  const int stride = K.m + 3;
-  if (threadIdx.x == 0) {
-    double ta = 0.0, tb = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) { ta += s2[0][w]; tb += s2[1][w]; }
-    K.partial[size_t(blockIdx.x) * stride + 0] = ta;
-    K.partial[size_t(blockIdx.x) * stride + 1] = tb;
-  }
-  if (!last_block(K.ticket, gridDim.x)) return;
-  __shared__ double rr[2];
-  reduce_partials(K.partial, stride, gridDim.x, 2, rr);
-  __syncthreads();
-  if (threadIdx.x == 0 && a.zn) {
-    a.zn[0] = sqrt(rr[0] + rr[1]);
-    a.zn[1] = sqrt(rr[0]);
-    a.zn[2] = sqrt(rr[1]);
-  }
+  pc_apply_norms(a, K, aw, as);
 }
 
 // The element Jacobian of linear advection (with or without its viscous term)

@@ -270,6 +270,9 @@ struct hbpc_ctx {
   // a viscous term) on one uniform mesh has the same J_i in every element and
   // for every state, so one J, one S^-1 serve the whole mesh
   bool pc_shared = false;
+  // BJ^H_ext with a nonlinear flux: the Hessian blocks are in M (pc_build)
+  // and the apply takes the BJ^H_ext algebra
+  bool pc_hess = false;
   double pc_c1 = 0.0, pc_c2 = 0.0;
   // the shared block's J as 1-D Kronecker factors (k_pc_kron_factors)
   double* kron_d = nullptr;
@@ -574,6 +577,7 @@ hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const doubl
   a.nb = x->nb; a.nE = int(x->nE);
   a.shared = x->pc_shared ? 1 : 0;
   a.kron = x->pc_shared ? x->kron_d : nullptr; a.kron_ok = x->kron_ok; a.P = x->P; a.dim = x->dim;
+  a.hess = x->pc_hess ? 1 : 0;
   if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<double><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply");
@@ -593,6 +597,7 @@ hbpc_status pc_apply_f(hbpc_ctx* x, const float* in, const int* jidx, const doub
   a.nb = x->nb; a.nE = int(x->nE);
   a.shared = x->pc_shared ? 1 : 0;
   a.kron = x->pc_shared ? x->kron_f : nullptr; a.kron_ok = x->kron_ok; a.P = x->P; a.dim = x->dim;
+  a.hess = x->pc_hess ? 1 : 0;
   if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<float><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply<float>");
@@ -828,18 +833,26 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
   // one shared block when J_i is the same for every element and state (the
   // training-data collection and the learned network want per-element blocks)
-  x->pc_shared = linear && (x->ninst == 0 || x->same_mesh) && x->sol.pc == HBPC_PC_BJEXT && !collecting;
+  x->pc_shared = linear && (x->ninst == 0 || x->same_mesh) &&
+                 (x->sol.pc == HBPC_PC_BJEXT || x->sol.pc == HBPC_PC_BJEXT_H) && !collecting;
+  // BJ^H_ext: the Hessian blocks at (W, sigma), sigma the second half of the
+  // extended state W points to; a linear flux has none (H = 0, Sec. 3.2.1)
+  // and BJ^H_ext is then BJ_ext
+  x->pc_hess = x->sol.pc == HBPC_PC_BJEXT_H && x->ops.pc_hessian != nullptr;
   const int nEb = x->pc_shared ? 1 : int(x->nE);   // blocks to build
   // J_i in the precision of the apply: FP32 in the mixed mode (the blocks only
-  // precondition the FP32 Krylov loop), FP64 otherwise
+  // precondition the FP32 Krylov loop), FP64 otherwise; the Hessian blocks go
+  // straight into M, where S = I - c1 J + c2 (H + J^2) replaces them
   if (mixed) {
     DGParams<float> pf = x->prmf;
     pf.nE = nEb;
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble_f(pf, W, x->Jf, x->stream));
+    if (x->pc_hess) HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_hessian_f(pf, W, W + x->ndof, x->Mf, x->stream));
   } else {
     DGParams<double> pd = x->prm;
     pd.nE = nEb;
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_assemble(pd, W, x->Jpc, x->stream));
+    if (x->pc_hess) HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, x->ops.pc_hessian(pd, W, W + x->ndof, x->Mpc, x->stream));
   }
   hbpc_status s0;
   if (collecting && (s0 = lp_collect(x, W, c1, c2)) != HBPC_OK) return s0;
@@ -881,14 +894,15 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   if (mixed) {
     // S and its inverse in FP32 as well
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_form_S<float><<<nEb, 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb, nEb, x->c12));
+             k_pc_form_S<float><<<nEb, 256, nb * nb * sizeof(float), x->stream>>>(x->Jf, x->Mf, x->nb, nEb, x->c12,
+                                                                                 nullptr, x->pc_hess ? x->Mf : nullptr));
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
              k_pc_invert<float><<<nEb, 256, (nb * nb + nb) * sizeof(float) + nb * sizeof(int), x->stream>>>(
                  x->Mf, x->nb, nEb, x->singular));
   } else {
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
-             k_pc_form_S<double><<<nEb, 256, nb * nb * sizeof(double), x->stream>>>(x->Jpc, x->Mpc, x->nb, nEb,
-                                                                                   x->c12));
+             k_pc_form_S<double><<<nEb, 256, nb * nb * sizeof(double), x->stream>>>(
+                 x->Jpc, x->Mpc, x->nb, nEb, x->c12, nullptr, x->pc_hess ? x->Mpc : nullptr));
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
              k_pc_invert<double><<<nEb, 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
                  x->Mpc, x->nb, nEb, x->singular));
@@ -1763,8 +1777,10 @@ hbpc_status validate(const hbpc_mesh* mesh, int N, int nodes, const hbpc_physics
   if (so->gmres_max_iter < 1 || so->newton_max_iter < 1) return bad("iteration caps must be >= 1");
   if (!(so->tol_gmres_rel > 0.0) || !(so->tol_newton_rel >= 0.0) || !(so->tol_newton_abs >= 0.0))
     return bad("tolerances must be positive");
-  if (so->pc != HBPC_PC_NONE && so->pc != HBPC_PC_BJEXT && so->pc != HBPC_PC_LEARNED)
+  if (so->pc != HBPC_PC_NONE && so->pc != HBPC_PC_BJEXT && so->pc != HBPC_PC_LEARNED && so->pc != HBPC_PC_BJEXT_H)
     return bad("unknown preconditioner");
+  if (so->pc == HBPC_PC_BJEXT_H && ph->law == HBPC_LAW_NAVIER_STOKES)
+    return fail(nullptr, HBPC_ERR_UNSUPPORTED, "BJ^H_ext has no Navier-Stokes Hessian blocks");
   if (so->pc != HBPC_PC_NONE) {
     int nb = law_nv(ph->law, mesh->dim);
     for (int m = 0; m < mesh->dim; ++m) nb *= (N + 1);
@@ -2714,8 +2730,10 @@ hbpc_status hbpc_reset_stats(hbpc_ctx* ctx) {
 
 hbpc_status hbpc_set_pc(hbpc_ctx* ctx, int pc) {
   if (!ctx) return HBPC_ERR_INVALID_ARG;
-  if (pc != HBPC_PC_NONE && pc != HBPC_PC_BJEXT && pc != HBPC_PC_LEARNED)
+  if (pc != HBPC_PC_NONE && pc != HBPC_PC_BJEXT && pc != HBPC_PC_LEARNED && pc != HBPC_PC_BJEXT_H)
     return fail(ctx, HBPC_ERR_INVALID_ARG, "unknown preconditioner");
+  if (pc == HBPC_PC_BJEXT_H && ctx->phys.law == HBPC_LAW_NAVIER_STOKES)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "BJ^H_ext has no Navier-Stokes Hessian blocks");
   if (pc != HBPC_PC_NONE) {
     if (ctx->nb > kMaxPcBlock)
       return fail(ctx, HBPC_ERR_UNSUPPORTED, "block n_var (N+1)^dim exceeds the supported size");

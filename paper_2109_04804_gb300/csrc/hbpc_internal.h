@@ -47,6 +47,12 @@ struct OpsTable {
   // BJ_ext element Jacobians J_i (Sec. 3.2.3), column-major n_b x n_b per element
   void (*pc_assemble)(const DGParams<double>&, const double* W, double* J, cudaStream_t) = nullptr;
   void (*pc_assemble_f)(const DGParams<float>&, const double* W, float* J, cudaStream_t) = nullptr;
+  // BJ^H_ext Hessian blocks H_i = dR2/dW|_i at (W, sigma = S), same layout;
+  // null for a linear flux (H = 0) and for Navier-Stokes
+  void (*pc_hessian)(const DGParams<double>&, const double* W, const double* S, double* H,
+                     cudaStream_t) = nullptr;
+  void (*pc_hessian_f)(const DGParams<float>&, const double* W, const double* S, float* H,
+                       cudaStream_t) = nullptr;
 };
 
 // Returns false if the combination was not compiled.

@@ -113,10 +113,19 @@ struct Inst {
       k_pc_assemble<LAW, DIM, P, LGL, float><<<p.nE, 128, 0, s>>>(W, J, p);
     }
   }
+  // BJ^H_ext Hessian blocks (inviscid flux Hessian; no Navier-Stokes form)
+  template <typename T>
+  static void pc_hessian(const DGParams<T>& p, const double* W, const double* S, T* H, cudaStream_t s) {
+    k_pc_assemble<LAW, DIM, P, LGL, T, true><<<p.nE, 128, 0, s>>>(W, H, p, S);
+  }
   static void fill(OpsTable& t) {
     t.nv = NV;
     t.pc_assemble = &pc_assemble;
     t.pc_assemble_f = &pc_assemble_f;
+    if constexpr (!LINEAR && LAW != LAW_NS) {
+      t.pc_hessian = &pc_hessian<double>;
+      t.pc_hessian_f = &pc_hessian<float>;
+    }
     t.jv_f = &jv_f;
     t.r1 = &r1;
     t.r2 = &r2;

@@ -25,7 +25,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NO_CONVERGENCE, ERR_NONFINITE, ERR_T
 LAW_ADVECTION, LAW_BURGERS, LAW_EULER, LAW_NAVIER_STOKES = 0, 1, 2, 3
 FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
-PC_NONE, PC_BJEXT, PC_LEARNED = 0, 1, 2
+PC_NONE, PC_BJEXT, PC_LEARNED, PC_BJEXT_H = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 PC_LOSS = {"probe": 0, "inverse": 1}
 PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")

@@ -164,3 +164,15 @@ def test_noalloc_rejects_viscous_law_on_the_host(hbpc):
     with pytest.raises(hbpc.HBPCError) as ei:
         hbpc.eval_Jv_noalloc(2, (4, 4), (0, 0), (1, 1), 3, 0.01, 0.5, 0.1, X, dX, out, nu=0.01)
     assert ei.value.status == 7
+
+
+def test_bjext_h_preconditioner_checks(hbpc):
+    """BJ^H_ext has no Navier-Stokes Hessian blocks (HBPC_ERR_UNSUPPORTED) and an
+    unknown preconditioner code is HBPC_ERR_INVALID_ARG, both before the device
+    is touched."""
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(2, (3, 3), (0, 0), (1, 1), 3, law=hbpc.LAW_NAVIER_STOKES, mu=0.01, pc=hbpc.PC_BJEXT_H)
+    assert ei.value.status == 7
+    with pytest.raises(hbpc.HBPCError) as ei:
+        hbpc.Context(2, (3, 3), (0, 0), (1, 1), 3, pc=4)
+    assert ei.value.status == 1

@@ -25,6 +25,7 @@ The same line carries (N = 1):
   python bench.py --workload burgers_batch   (256 viscous Burgers instances)
   python bench.py --workload euler_vortex    (learned vs BJ_ext vs plain GMRES)
   python bench.py --workload taylor_green    (3-D Navier-Stokes, 32^3, N = 5)
+  python bench.py --workload euler_pc        (no PC vs BJ_ext vs BJ^H_ext, Euler, eps sweep)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the path has no data-path collective), value = sum over ranks / max time.
@@ -1015,6 +1016,75 @@ TGV = dict(n=32, N=5, q=4, kmax=0, cfl=20.0, eps=0.1, re=1600.0, prandtl=0.72, t
            check_n=8)
 
 
+EPC = dict(n=(16, 16), lo=(-1.0, -1.0), hi=(1.0, 1.0), N=5, q=4, kmax=0, tol_newton_rel=1e-8,
+           tol_gmres_rel=1e-3, gmres_restart=700, gmres_max_iter=7000, newton_max_iter=50,
+           eps=(1.0, 0.1, 0.01), dts=(0.0125, 0.05, 0.2, 0.8))
+
+
+def run_euler_pc(args, emit=True):
+    """The preconditioner comparison of the paper's Euler study: the density
+    wave rho = 1 + 0.3 sin(pi (x + y)), v = (0.3, 0.3), p = 1 on [-1, 1]^2, 16 x 16
+    elements, N = 5, global LF with lambda = diag(1/eps, 1, 1, 1/eps), reference
+    Mach numbers eps = 1, 0.1, 0.01, eps_GMRES = 1e-3, eps_Newton = 1e-8, restart
+    700, at most 7000 GMRES iterations per Newton step; one predictor step of
+    HBPC(4, 0) (the J^predictor system, alpha = 1/2, 1/6) per time step size,
+    in FP64, with no preconditioner, BJ_ext and BJ^H_ext (rebuilt every Newton
+    iteration).  Reports GMRES iterations and device milliseconds per time step,
+    and each answer's distance to the no-preconditioner one."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    arms = (("no_pc", hbpc.PC_NONE), ("bjext", hbpc.PC_BJEXT), ("bjext_h", hbpc.PC_BJEXT_H))
+
+    def one(eps, dt, pc):
+        c = hbpc.Context(2, EPC["n"], EPC["lo"], EPC["hi"], EPC["N"], law=hbpc.LAW_EULER,
+                         flux=hbpc.FLUX_GLOBAL_LF, eps=eps, q=EPC["q"], kmax=EPC["kmax"], dt=dt,
+                         tol_newton_rel=EPC["tol_newton_rel"], tol_newton_abs=0.0,
+                         tol_gmres_rel=EPC["tol_gmres_rel"], gmres_restart=EPC["gmres_restart"],
+                         gmres_max_iter=EPC["gmres_max_iter"], newton_max_iter=EPC["newton_max_iter"],
+                         pc=pc, precision=hbpc.PREC_FP64)
+        c.set_state(inputs.density_wave(c.node_coords(), eps=eps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ok = True
+        try:
+            c.step(1)
+        except hbpc.HBPCError as e:
+            ok = str(e)[:80]
+        e1.record()
+        torch.cuda.synchronize()
+        st = c.stats()
+        w = c.get_state() if ok is True else None
+        c.close()
+        return {"ok": ok, "ms": round(e0.elapsed_time(e1), 3), "gmres_its": int(st["gmres_its"]),
+                "newton_its": int(st["newton_its"])}, w
+
+    for pc in (hbpc.PC_BJEXT, hbpc.PC_BJEXT_H):   # kernels loaded, first-call allocations done
+        one(1.0, EPC["dts"][0], pc)
+    rows = []
+    for eps in EPC["eps"]:
+        for dt in EPC["dts"]:
+            row = {"eps": eps, "dt": dt}
+            ref = None
+            for name, pc in arms:
+                r, w = one(eps, dt, pc)
+                if name == "no_pc":
+                    ref = w
+                elif w is not None and ref is not None:
+                    r["rel_l2_vs_no_pc"] = rel_l2(w, ref)
+                row[name] = r
+            rows.append(row)
+    line = {"workload": "2d_euler_density_wave_16x16_N5_predictor_HBPC(4,0)_globalLF_pc_comparison",
+            "unit": "GMRES iterations and device ms per time step", "n_dof": 16 * 16 * 36 * 4,
+            "config": {k: v for k, v in EPC.items()}, "rows": rows}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def tgv_dt(n):
     """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v|_max + c of the
     initial state (|v| <= 1, c = 1/eps with p ~ 1/gamma)."""
@@ -1144,11 +1214,13 @@ def main():
                     help="precision of the headline value (the other one is reported beside it): fp64, the "
                          "workload's own; mixed: FP32 Krylov loop, FP64 Newton residual/update")
     ap.add_argument("--workload", default="advection2d",
-                    choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green", "r1_roofline"],
+                    choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green", "r1_roofline",
+                             "euler_pc"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances; euler_vortex: learned vs BJ_ext vs plain GMRES; "
                          "taylor_green: the 3-D Navier-Stokes line; r1_roofline: the operator-pass roofline "
-                         "object of the default line alone")
+                         "object of the default line alone; euler_pc: no preconditioner vs BJ_ext vs BJ^H_ext "
+                         "on the Euler density wave (16x16, N=5, eps = 1, 0.1, 0.01)")
     ap.add_argument("--instances", type=int, default=BATCH["n_inst"])
     ap.add_argument("--tgv-n", type=int, default=0,
                     help="taylor_green: elements per direction (default 32; smaller for profiling)")
@@ -1172,6 +1244,8 @@ def main():
         run_tgv(args)
     elif args.workload == "r1_roofline":
         run_r1_only(args)
+    elif args.workload == "euler_pc":
+        run_euler_pc(args)
     else:
         run_ours(args)
 

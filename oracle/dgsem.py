@@ -35,13 +35,21 @@ from .basis import Basis, LOBATTO
 
 
 class Mesh:
-    def __init__(self, dim, n, lo, hi):
+    """Uniform Cartesian mesh.  bc: None (periodic in every direction) or one
+    entry per direction, None (periodic) or a pair (lower, upper) of boundary
+    specifications ("dirichlet", state) (a constant exterior state of n_var
+    values) or ("wall",) (slip wall of the Euler equations)."""
+
+    def __init__(self, dim, n, lo, hi, bc=None):
         self.dim = dim
         self.n = tuple(int(x) for x in n[:dim])
         self.lo = np.array(lo[:dim], dtype=np.float64)
         self.hi = np.array(hi[:dim], dtype=np.float64)
         self.h = (self.hi - self.lo) / np.array(self.n)
         self.nE = int(np.prod(self.n))
+        self.bc = [None] * dim if bc is None else list(bc)
+        assert len(self.bc) == dim
+        self.periodic = all(b is None for b in self.bc)
 
 
 class Disc:
@@ -110,6 +118,34 @@ class Disc:
         return np.expand_dims(f, axis) * lhat.reshape(shp)
 
 
+def _end(ndim, axis, last):
+    """Index of the first (last = False) or last element along `axis`, axis kept."""
+    idx = [slice(None)] * ndim
+    idx[axis] = slice(-1, None) if last else slice(0, 1)
+    return tuple(idx)
+
+
+def _neighbour_traces(disc, own_p, own_m, m, ea, exterior, nb=None):
+    """The traces the element's faces see across them along direction m:
+    L at its - face (the + trace of element e-1) and R at its + face (the -
+    trace of element e+1).  nb (optional) maps the rolled neighbour values
+    (real parts, zeros).  On a bounded direction the first element's L and
+    the last element's R are the exterior values exterior(own trace, spec)."""
+    R = np.roll(own_m, -1, axis=ea)
+    L = np.roll(own_p, 1, axis=ea)
+    if nb is not None:
+        R, L = nb(R), nb(L)
+    bc = disc.mesh.bc[m]
+    if bc is not None:
+        lo, hi = bc
+        dt = np.result_type(R, own_p)
+        R, L = R.astype(dt, copy=True), L.astype(dt, copy=True)
+        e_hi, e_lo = _end(R.ndim, ea, True), _end(L.ndim, ea, False)
+        R[e_hi] = exterior(own_p[e_hi], hi)
+        L[e_lo] = exterior(own_m[e_lo], lo)
+    return L, R
+
+
 def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False, frozen_neighbor_state=False):
     """R^(1)(w) if mode == "R1"; R^(2)(w, sigma) if mode == "R2".
 
@@ -130,6 +166,8 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False, frozen_neigh
     if frozen_neighbor_state and (mode != "R2" or disc.ph.law == laws.NAVIER_STOKES):
         raise ValueError("frozen_neighbor_state: R2 of an inviscid or scalar viscous law only")
     ph, b = disc.ph, disc.basis
+    if not disc.mesh.periodic and (ph.nu != 0.0 or ph.law == laws.NAVIER_STOKES):
+        raise ValueError("boundary conditions: inviscid laws only")
     W = disc.to_grid(w)
     S = disc.to_grid(sigma) if sigma is not None else None
     out = np.zeros(W.shape, dtype=np.result_type(W, S) if S is not None else W.dtype)
@@ -144,41 +182,33 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False, frozen_neigh
         # traces: own + face (right trace) and own - face (left trace)
         wp = Disc._trace(b.l_p, W, na)
         wm = Disc._trace(b.l_m, W, na)
-        # neighbour e+1 seen from element e: its minus trace
-        wR = np.roll(wm, -1, axis=ea)
-        kappa = laws.dissipation(wp, wR, m, ph)
+        ext_w = lambda own, spec: laws.exterior_state(own, spec, m, ph)
+        # neighbours' traces: wL at the - face (e-1's + trace), wR at the +
+        # face (e+1's - trace); real parts when the neighbours are frozen
+        wL, wR = _neighbour_traces(disc, wp, wm, m, ea, ext_w,
+                                   np.real if frozen_neighbor_state else None)
+        if frozen_neighbor_state:
+            kp = laws.dissipation(np.real(wp), np.real(wR), m, ph)
+            km = laws.dissipation(np.real(wL), np.real(wm), m, ph)
+        else:
+            kp = laws.dissipation(wp, wR, m, ph)
+            km = laws.dissipation(wL, wm, m, ph)
         if mode == "R1":
-            fface = 0.5 * (laws.flux(wp, m, ph) + laws.flux(wR, m, ph)) + kappa * (wp - wR)
-            fplus = fface
-            fminus = -np.roll(fface, 1, axis=ea)
+            # + face: f*(own, e+1); - face: -f*(e-1, own) (outward normal -e_m)
+            fplus = 0.5 * (laws.flux(wp, m, ph) + laws.flux(wR, m, ph)) + kp * (wp - wR)
+            fminus = -(0.5 * (laws.flux(wL, m, ph) + laws.flux(wm, m, ph)) + km * (wL - wm))
         else:
             sp = Disc._trace(b.l_p, S, na)
             sm = Disc._trace(b.l_m, S, na)
-            sR = np.roll(sm, -1, axis=ea)
-            if frozen_neighbor_state:
-                # + face (e, e+1): neighbour trace wR; - face (e-1, e): the
-                # neighbour's + trace, both real, kappa of the real traces
-                wRr = np.real(wR)
-                wLr = np.roll(np.real(wp), 1, axis=ea)
-                sL = np.roll(sp, 1, axis=ea)
-                kp = laws.dissipation(np.real(wp), wRr, m, ph)
-                km = laws.dissipation(wLr, np.real(wm), m, ph)
-                fplus = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wRr, sR, m, ph))
-                         + kp * (sp - sR))
-                fminus = -(0.5 * (laws.flux_jvp(wLr, sL, m, ph) + laws.flux_jvp(wm, sm, m, ph))
-                           + km * (sL - sm))
-            elif not frozen_neighbor:
-                fface = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wR, sR, m, ph))
-                         + kappa * (sp - sR))
-                fplus = fface
-                fminus = -np.roll(fface, 1, axis=ea)
-            else:
-                # element's + face: neighbour sigma trace set to zero
-                fplus = 0.5 * laws.flux_jvp(wp, sp, m, ph) + kappa * sp
-                # element's - face: the face (e-1, e) seen from e, with the
-                # neighbour (e-1) sigma trace zero; outward normal is -e_m
-                kappa_prev = np.roll(kappa, 1, axis=ea)
-                fminus = -(0.5 * laws.flux_jvp(wm, sm, m, ph) - kappa_prev * sm)
+            ext_s = lambda own, spec: laws.exterior_direction(own, spec, m, ph)
+            # frozen_neighbor: the neighbours' sigma traces are zero (an
+            # exterior value stays: it is the element's own)
+            sL, sR = _neighbour_traces(disc, sp, sm, m, ea, ext_s,
+                                       np.zeros_like if frozen_neighbor else None)
+            fplus = (0.5 * (laws.flux_jvp(wp, sp, m, ph) + laws.flux_jvp(wR, sR, m, ph))
+                     + kp * (sp - sR))
+            fminus = -(0.5 * (laws.flux_jvp(wL, sL, m, ph) + laws.flux_jvp(wm, sm, m, ph))
+                       + km * (sL - sm))
         surf = disc._lift(fplus, b.lhat_p, na) + disc._lift(fminus, b.lhat_m, na)
         out = out - (2.0 / disc.mesh.h[m]) * (vol + surf)
     res = disc.from_grid(out)

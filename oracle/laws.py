@@ -164,6 +164,35 @@ def dissipation(wL, wR, m, ph):
     raise ValueError(ph.flux)
 
 
+# -- boundary exteriors (non-periodic directions) ----------------------------
+
+def exterior_state(w_own, spec, m, ph):
+    """The state the numerical flux sees outside a boundary face of direction
+    m, from the element's own trace w_own (variables on axis 0):
+      ("dirichlet", state): the given constant state;
+      ("wall",): the Euler slip wall, the own state with its momentum along m
+                 reversed (zero normal velocity at the face)."""
+    if spec[0] == "dirichlet":
+        st = np.asarray(spec[1], dtype=np.float64).reshape((ph.nv,) + (1,) * (w_own.ndim - 1))
+        return np.broadcast_to(st, w_own.shape).astype(np.result_type(w_own, st))
+    if spec[0] == "wall":
+        if ph.law != EULER:
+            raise ValueError("a slip wall needs the Euler equations")
+        out = np.array(w_own, copy=True)
+        out[1 + m] = -out[1 + m]
+        return out
+    raise ValueError(spec)
+
+
+def exterior_direction(s_own, spec, m, ph):
+    """The direction sigma outside a boundary face: the time derivative of the
+    exterior state, so zero for constant Dirichlet data and the mirrored own
+    sigma at a slip wall (the exterior state is linear in the own state)."""
+    if spec[0] == "dirichlet":
+        return np.zeros_like(s_own)
+    return exterior_state(s_own, spec, m, ph)
+
+
 # -- Navier-Stokes viscous part (Sec. 5) -----------------------------------
 
 def ns_grad_vars(w, ph):

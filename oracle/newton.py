@@ -12,7 +12,8 @@ Newton (Eq. 17): J dX = -G, X <- X + dX, stopped when ||G(X^r)|| <= tol_rel
 Jv (Sec. 4.2):
   "fd"     Eq. 23 with eps_FD = sqrt(eps_machine) / (eps ||d.||_2) per block,
            eps_machine = 2^-52 (the Fortran epsilon of a double);
-  "linear" the right-hand form of Eq. 24 (exact for a linear flux);
+  "linear" the right-hand form of Eq. 24 (exact for a linear flux), R1 of a
+           direction taken as its linear part R2(W, .) (boundary data dropped);
   "analytic" Eq. 18 with dR1/dW v = R2(W, v) (identity of Sec. 3.2.1) and the
            Hessian block by the FD quotient of Eq. 23.
 
@@ -76,8 +77,12 @@ class StageSystem:
         dW, dS = self.split(dX)
         eps_ref = self.disc.ph.eps
         if mode == "linear":
-            q1 = self.R1(dW)
-            top = dW - self.c1 * q1 + self.c2 * self.R1(dS)
+            # Eq. 24 for a linear flux: R1 of the direction, taken as its
+            # linear part dR1/dW v = R2(W, v) (Sec. 3.2.1), which equals R1(v)
+            # on a periodic mesh and drops the data of a Dirichlet boundary,
+            # where R1 is affine
+            q1 = self.R2(W, dW)
+            top = dW - self.c1 * q1 + self.c2 * self.R2(W, dS)
             bot = -q1 + dS
             return np.concatenate([top.ravel(), bot.ravel()])
         nw, ns = np.linalg.norm(dW), np.linalg.norm(dS)

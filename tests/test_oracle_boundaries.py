@@ -169,3 +169,21 @@ def test_periodic_connection_unchanged():
     d1 = dgsem.Disc(dgsem.Mesh(2, (3, 2), (0, 0), (1, 1), bc=[None, None]), 3, ph)
     w = random_gas(d0, 67)
     assert np.array_equal(dgsem.R1(d0, w), dgsem.R1(d1, w))
+
+
+def test_linear_jv_is_the_derivative_of_G_with_dirichlet_data():
+    """With nonzero Dirichlet data R1 of a linear flux is affine: the linear
+    Jacobian-vector product (Eq. 24) must be the derivative of G, which the
+    complex step of the residual gives exactly."""
+    ph = laws.Physics(laws.ADVECTION, 2, a=(0.8, -0.45))
+    bc = [(("dirichlet", [0.7]), ("dirichlet", [-0.3])), (("dirichlet", [0.2]), ("dirichlet", [0.1]))]
+    disc = dgsem.Disc(dgsem.Mesh(2, (3, 4), (0, 0), (1, 1), bc=bc), 3, ph, GAUSS)
+    rng = np.random.default_rng(68)
+    sysm = newton.StageSystem(disc, rng.standard_normal(disc.shape), 0.5, 1.0 / 6.0, 0.1)
+    X = rng.standard_normal(2 * disc.ndof)
+    dX = rng.standard_normal(2 * disc.ndof)
+    G, r1, r2 = sysm.residual(X)
+    h = 1e-30
+    ref = np.imag(sysm.residual(X + 1j * h * dX)[0]) / h
+    out = sysm.jv(X, r1, r2, dX, "linear")
+    assert np.linalg.norm(out - ref) <= 1e-13 * np.linalg.norm(ref)

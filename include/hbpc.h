@@ -17,8 +17,10 @@
  *    the library copies what it keeps.  All device work is enqueued on the
  *    stream given at creation (NULL = legacy default stream) and the calls
  *    return after that stream has finished the call's work.
- *  - Meshes are uniform, Cartesian and periodic in every direction
- *    (hbpc_mesh.periodic must be 1; other boundaries are HBPC_ERR_UNSUPPORTED).
+ *  - Meshes are uniform and Cartesian.  A context is created periodic in
+ *    every direction (hbpc_mesh.periodic must be 1); hbpc_set_boundary then
+ *    replaces the periodic connection of a direction by two boundaries
+ *    (constant Dirichlet states or Euler slip walls, inviscid laws).
  *  - Invalid arguments are rejected before anything is allocated or launched.
  */
 #ifndef HBPC_H
@@ -94,9 +96,10 @@ typedef struct {
   int n[3];         /* elements per direction (n[m] >= 1 for m < dim) */
   double lo[3];     /* domain [lo, hi] per direction */
   double hi[3];
-  int periodic;     /* 1: periodic in every direction, the only boundary this
-                       build implements; 0 (walls or inflow/outflow boundaries)
-                       is HBPC_ERR_UNSUPPORTED */
+  int periodic;     /* 1: periodic in every direction (the connectivity at
+                       creation; hbpc_set_boundary bounds a direction later);
+                       0 is HBPC_ERR_UNSUPPORTED, any other value
+                       HBPC_ERR_INVALID_ARG */
 } hbpc_mesh;
 
 typedef struct {
@@ -251,6 +254,27 @@ hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on);
  * Allocates three 2 n_dof vectors on the first on = 1; 0 returns to the
  * extended form. */
 hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on);
+
+/* Boundaries of direction `dir` (0 <= dir < dim): the lower (x_dir = lo) and
+ * upper (x_dir = hi) ends get kinds kind_lo, kind_hi, both HBPC_BC_PERIODIC
+ * (the periodic connection, the default) or both bounded:
+ *   HBPC_BC_DIRICHLET  a constant exterior state: `state_*` points to n_var host
+ *                      doubles (conservative variables; Euler: density and
+ *                      pressure > 0), copied;
+ *   HBPC_BC_WALL       the slip wall of the Euler equations: the exterior state
+ *                      is the own trace with the momentum along dir reversed.
+ * A boundary face takes the numerical flux of Eq. 13 (or f~* of Sec. 3.1.2 for
+ * R2) with that exterior state; the exterior direction of R2 is its time
+ * derivative (zero for Dirichlet data, the mirrored own sigma at a wall), so
+ * R2 stays the derivative of R1 and every Jacobian-vector product, the BJ_ext
+ * and BJ^H_ext blocks and the mixed mode include the boundaries.  Inviscid
+ * laws only (nu = 0, not Navier-Stokes: HBPC_ERR_UNSUPPORTED); a wall needs
+ * the Euler equations; mixed periodic/bounded ends, an unknown kind or a bad
+ * state are HBPC_ERR_INVALID_ARG; nothing changes on an error.  Applies to the
+ * following calls (the preconditioner is rebuilt). */
+typedef enum { HBPC_BC_PERIODIC = 0, HBPC_BC_DIRICHLET = 1, HBPC_BC_WALL = 2 } hbpc_bc;
+hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double* state_lo, int kind_hi,
+                              const double* state_hi);
 
 /* Bounded waits.  Every call of the context waits for its stream before it
  * returns (and inside the Newton loop, for the residual norms).  With a limit

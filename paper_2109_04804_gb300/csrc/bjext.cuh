@@ -121,6 +121,9 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
         for (int v = 0; v < NV; ++v) { to[v] = T(0); tn[v] = T(0); so[v] = T(0); }
         int nc[3] = {ec[0], ec[1], ec[2]};
         nc[m] += side ? 1 : -1;
+        // a boundary face: the exterior state depends only on the own trace
+        const bool bnd = (nc[m] < 0 || nc[m] >= geo.n[m]) && prm.bck[m][side] != BC_PERIODIC;
+        const bool wall = bnd && prm.bck[m][side] == BC_WALL;
         if (nc[m] < 0) nc[m] += geo.n[m];
         if (nc[m] >= geo.n[m]) nc[m] -= geo.n[m];
         const int en = geo.e0 + nc[0] + geo.n[0] * (nc[1] + geo.n[1] * nc[2]);
@@ -131,7 +134,32 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
           for (int v = 0; v < NV; ++v) {
             to[v] += lo * sw[v * NN + b0 + i * st];
             if constexpr (HESS) so[v] += lo * ss[v * NN + b0 + i * st];
-            else tn[v] += ln * T(W[(size_t(en) * NV + v) * NN + b0 + i * st]);
+            else if (!bnd) tn[v] += ln * T(W[(size_t(en) * NV + v) * NN + b0 + i * st]);
+          }
+        }
+        if (bnd) exterior_state<NV>(prm, m, side, to, tn);
+        // wall: the exterior trace M t_o (momentum along m reversed) moves with
+        // the own trace, d(M t_o)/d(w_q) e_u = lq M e_u, and contributes
+        // 1/2 A(M t_o) M e_u (Hessian form: 1/2 H(M t_o)[M s_o, M e_u]) and
+        // -kappa M e_u to the derivative of the face flux
+        T Aw[NV], meu[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { Aw[v] = T(0); meu[v] = (v == 1 + m) ? -eu[v] : eu[v]; }
+        if constexpr (!L::LINEAR) {
+          if (wall) {
+            if constexpr (HESS) {
+              D td[NV], sd[NV], hd[NV];
+#pragma unroll
+              for (int v = 0; v < NV; ++v) {
+                td[v] = D(tn[v], meu[v]);
+                sd[v] = D((v == 1 + m) ? -so[v] : so[v]);
+              }
+              L::jvp(td, sd, m, hd, prm);
+#pragma unroll
+              for (int v = 0; v < NV; ++v) Aw[v] = hd[v].d;
+            } else {
+              L::jvp(tn, meu, m, Aw, prm);
+            }
           }
         }
         T A[NV], kap[NV];
@@ -172,7 +200,8 @@ __global__ void __launch_bounds__(128) k_pc_assemble(const double* __restrict__ 
           if (lift == T(0)) continue;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
-            const T d = (side ? T(0.5) : T(-0.5)) * A[v] + kap[v] * eu[v];
+            T d = (side ? T(0.5) : T(-0.5)) * A[v] + kap[v] * eu[v];
+            if (wall) d += (side ? T(0.5) : T(-0.5)) * Aw[v] - kap[v] * meu[v];
             Jc[v * NN + b0 + l * st] += lift * lq * d;
           }
         }

@@ -103,7 +103,40 @@ struct DGParams {
   // per block of the operator kernel, the instance it belongs to
   const InstGeo<T>* inst;
   const int* blk_inst;
+  // boundaries of a non-periodic direction m (single problems, inviscid laws):
+  // bck[m][side] (side 0 = lower, 1 = upper end) is BC_PERIODIC, BC_DIRICHLET
+  // (exterior state bcw[m][side], constant in time) or BC_WALL (Euler slip
+  // wall: the own trace with its momentum along m reversed)
+  int bck[3][2];
+  T bcw[3][2][5];
 };
+
+enum BoundaryKind { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_WALL = 2 };
+
+// The state and the direction the numerical flux sees outside a boundary face
+// of direction m (Sec. 3.1.1 with an exterior trace): Dirichlet data are
+// constant, so their direction is zero; the wall state is linear in the own
+// trace, so its direction is the mirrored own direction.
+template <int NV, typename V, typename T>
+__device__ __forceinline__ void exterior_state(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
+  if (p.bck[m][side] == BC_WALL) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = V(p.bcw[m][side][v]);
+  }
+}
+template <int NV, typename V, typename T>
+__device__ __forceinline__ void exterior_dir(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
+  if (p.bck[m][side] == BC_WALL) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = V(T(0));
+  }
+}
 
 // Geometry of the instance that operator block `blk` works on.
 template <typename T>

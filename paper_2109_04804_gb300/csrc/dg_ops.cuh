@@ -41,6 +41,14 @@ template <class Job, class = void> struct FrozenNb { static constexpr bool value
 template <class Job> struct FrozenNb<Job, std::void_t<decltype(Job::kFrozenNb)>> {
   static constexpr bool value = Job::kFrozenNb;
 };
+// A job with kDirectionState = true loads directions where the operator
+// expects states (the linear Jv of Eq. 24 applies R1 to Krylov vectors): a
+// boundary's exterior is then the exterior direction, not the exterior state.
+template <class Job, class = void> struct DirectionState { static constexpr bool value = false; };
+template <class Job> struct DirectionState<Job, std::void_t<decltype(Job::kDirectionState)>> {
+  static constexpr bool value = Job::kDirectionState;
+};
+
 template <int NV, class Job, typename V>
 __device__ __forceinline__ void load_nb_dir(const Job& job, int k, int en, int node, V* x) {
   if constexpr (FrozenNb<Job>::value) {
@@ -92,10 +100,12 @@ struct FaceFlux {
                                              const V* sdir, V* sface) {
     constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;   // face point -> node with idx_M = 0
-    // neighbour element across this face (periodic within the instance)
+    // neighbour element across this face (periodic within the instance), or
+    // a boundary face of a non-periodic direction
     int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
     int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
     c += SIDE ? 1 : -1;
+    const bool bnd = (c < 0 || c >= g.n[M]) && prm.bck[M][SIDE] != BC_PERIODIC;
     if (c < 0) c += g.n[M];
     if (c >= g.n[M]) c -= g.n[M];
     const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
@@ -110,8 +120,10 @@ struct FaceFlux {
         wo[v] = sst[v * NN + own_node];
         if (r2) so[v] = sdir[v * NN + own_node];
       }
-      job.load_state(k, en, nb_node, wn);
-      if (r2) load_nb_dir<NV>(job, k, en, nb_node, sn);
+      if (!bnd) {
+        job.load_state(k, en, nb_node, wn);
+        if (r2) load_nb_dir<NV>(job, k, en, nb_node, sn);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < P; ++i) {
@@ -119,8 +131,12 @@ struct FaceFlux {
         const T lo = SIDE ? prm.lp[i] : prm.lm[i];   // own trace at this face
         const T ln = SIDE ? prm.lm[i] : prm.lp[i];   // neighbour's trace at this face
         V tw[NV], ts[NV];
-        job.load_state(k, en, node, tw);
-        if (r2) load_nb_dir<NV>(job, k, en, node, ts);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { tw[v] = V(T(0)); ts[v] = V(T(0)); }
+        if (!bnd) {
+          job.load_state(k, en, node, tw);
+          if (r2) load_nb_dir<NV>(job, k, en, node, ts);
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           wo[v] += lo * sst[v * NN + node];
@@ -128,6 +144,12 @@ struct FaceFlux {
           if (r2) { so[v] += lo * sdir[v * NN + node]; sn[v] += ln * ts[v]; }
         }
       }
+    }
+    if (bnd) {
+      // exterior of the boundary face from the element's own traces
+      if constexpr (DirectionState<Job>::value) exterior_dir<NV>(prm, M, SIDE, wo, wn);
+      else exterior_state<NV>(prm, M, SIDE, wo, wn);
+      if (r2) exterior_dir<NV>(prm, M, SIDE, so, sn);
     }
     // (L, R) = (own, neighbour) on the + face, (neighbour, own) on the - face
     V wL[NV], wR[NV], sL[NV], sR[NV];
@@ -849,6 +871,7 @@ struct JobJvFD_B {
 template <int NV, int NN, typename T = double, typename S = double>
 struct JobJvLinear {
   static constexpr int K = 2;
+  static constexpr bool kDirectionState = true;   // R1 of Krylov vectors: the derivative
   JvInputT<S> z; JvCoef c;
   __device__ static constexpr int kind(int) { return EV_R1; }
   __device__ bool active() const { return !z.skipped(); }
@@ -879,6 +902,7 @@ struct JobJvLinear {
 template <int NN, typename T = double, typename S = double>
 struct JobJvLinearPair {
   static constexpr int K = 1;
+  static constexpr bool kDirectionState = true;
   JvInputT<S> z; JvCoef c;
   __device__ static constexpr int kind(int) { return EV_R1; }
   __device__ bool active() const { return !z.skipped(); }

@@ -270,6 +270,9 @@ struct hbpc_ctx {
   // a viscous term) on one uniform mesh has the same J_i in every element and
   // for every state, so one J, one S^-1 serve the whole mesh
   bool pc_shared = false;
+  // some direction has boundaries (hbpc_set_boundary): the element blocks of a
+  // linear problem then differ at the boundary elements
+  bool bounded = false;
   // BJ^H_ext with a nonlinear flux: the Hessian blocks are in M (pc_build)
   // and the apply takes the BJ^H_ext algebra
   bool pc_hess = false;
@@ -833,7 +836,7 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
   // one shared block when J_i is the same for every element and state (the
   // training-data collection and the learned network want per-element blocks)
-  x->pc_shared = linear && (x->ninst == 0 || x->same_mesh) &&
+  x->pc_shared = linear && !x->bounded && (x->ninst == 0 || x->same_mesh) &&
                  (x->sol.pc == HBPC_PC_BJEXT || x->sol.pc == HBPC_PC_BJEXT_H) && !collecting;
   // BJ^H_ext: the Hessian blocks at (W, sigma), sigma the second half of the
   // extended state W points to; a linear flux has none (H = 0, Sec. 3.2.1)
@@ -2561,6 +2564,75 @@ hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on) {
   return HBPC_OK;
 }
 
+// Copies the boundary description of `from` into the operator parameters of
+// `to` (FP64 and FP32): the corrector-batch group of a context shares its
+// boundaries.
+void copy_boundaries(const hbpc_ctx* from, hbpc_ctx* to) {
+  for (int m = 0; m < 3; ++m)
+    for (int sd = 0; sd < 2; ++sd) {
+      to->prm.bck[m][sd] = from->prm.bck[m][sd];
+      to->prmf.bck[m][sd] = from->prm.bck[m][sd];
+      for (int v = 0; v < 5; ++v) {
+        to->prm.bcw[m][sd][v] = from->prm.bcw[m][sd][v];
+        to->prmf.bcw[m][sd][v] = float(from->prm.bcw[m][sd][v]);
+      }
+    }
+  to->bounded = from->bounded;
+  to->pc_built = false;
+}
+
+hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double* state_lo, int kind_hi,
+                              const double* state_hi) {
+  if (!ctx) return HBPC_ERR_INVALID_ARG;
+  auto bad = [&](const std::string& m) { return fail(ctx, HBPC_ERR_INVALID_ARG, m); };
+  if (ctx->ninst > 0) return fail(ctx, HBPC_ERR_UNSUPPORTED, "boundaries are for single problems");
+  if (dir < 0 || dir >= ctx->dim) return bad("dir must be in [0, dim)");
+  const int kinds[2] = {kind_lo, kind_hi};
+  const double* states[2] = {state_lo, state_hi};
+  for (int sd = 0; sd < 2; ++sd)
+    if (kinds[sd] != HBPC_BC_PERIODIC && kinds[sd] != HBPC_BC_DIRICHLET && kinds[sd] != HBPC_BC_WALL)
+      return bad("unknown boundary kind");
+  if ((kind_lo == HBPC_BC_PERIODIC) != (kind_hi == HBPC_BC_PERIODIC))
+    return bad("a direction is periodic at both ends or at neither");
+  const bool bounded = kind_lo != HBPC_BC_PERIODIC;
+  if (bounded && (ctx->phys.nu > 0.0 || ctx->phys.law == HBPC_LAW_NAVIER_STOKES))
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "boundaries are built for the inviscid laws");
+  double val[2][5] = {};
+  for (int sd = 0; sd < 2; ++sd) {
+    if (kinds[sd] == HBPC_BC_WALL && ctx->phys.law != HBPC_LAW_EULER)
+      return bad("a slip wall needs the Euler equations");
+    if (kinds[sd] != HBPC_BC_DIRICHLET) continue;
+    if (!states[sd]) return bad("a Dirichlet boundary needs its state");
+    for (int v = 0; v < ctx->nv; ++v) {
+      if (!std::isfinite(states[sd][v])) return bad("the Dirichlet state must be finite");
+      val[sd][v] = states[sd][v];
+    }
+    if (ctx->phys.law == HBPC_LAW_EULER) {
+      const double rho = val[sd][0];
+      double m2 = 0.0;
+      for (int k = 0; k < ctx->dim; ++k) m2 += val[sd][1 + k] * val[sd][1 + k];
+      const double eps2 = ctx->phys.eps * ctx->phys.eps;
+      const double p = rho > 0.0 ? (ctx->phys.gamma - 1.0) * (val[sd][ctx->dim + 1] - 0.5 * eps2 * m2 / rho) : -1.0;
+      if (!(rho > 0.0) || !(p > 0.0)) return bad("the Dirichlet state needs density and pressure > 0");
+    }
+  }
+  hbpc_status s = sync(ctx, "set_boundary");   // no kernel of the context reads the parameters meanwhile
+  if (s != HBPC_OK) return s;
+  for (int sd = 0; sd < 2; ++sd) {
+    ctx->prm.bck[dir][sd] = kinds[sd];
+    ctx->prmf.bck[dir][sd] = kinds[sd];
+    for (int v = 0; v < 5; ++v) {
+      ctx->prm.bcw[dir][sd][v] = val[sd][v];
+      ctx->prmf.bcw[dir][sd][v] = float(val[sd][v]);
+    }
+  }
+  ctx->bounded = false;
+  for (int m = 0; m < ctx->dim; ++m) ctx->bounded = ctx->bounded || ctx->prm.bck[m][0] != HBPC_BC_PERIODIC;
+  ctx->pc_built = false;
+  if (ctx->cb) copy_boundaries(ctx, ctx->cb);
+  return HBPC_OK;
+}
+
 hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
   if (ctx->ninst > 0) return fail(ctx, HBPC_ERR_UNSUPPORTED, "corrector batching is for single problems");
@@ -2589,6 +2661,7 @@ hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on) {
   cudaStreamDestroy(g->stream);
   g->stream = ctx->stream;
   g->wait_limit_s = ctx->wait_limit_s;
+  copy_boundaries(ctx, g);
   ctx->cb = g;
   return HBPC_OK;
 }

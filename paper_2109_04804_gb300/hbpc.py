@@ -27,6 +27,7 @@ FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
 PC_NONE, PC_BJEXT, PC_LEARNED, PC_BJEXT_H = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
+BC_PERIODIC, BC_DIRICHLET, BC_WALL = 0, 1, 2
 PC_LOSS = {"probe": 0, "inverse": 1}
 PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")
 
@@ -96,6 +97,7 @@ _SIGS = {
     "hbpc_set_wait_limit": (_I, [_CTX, _D]),
     "hbpc_set_corrector_batch": (_I, [_CTX, _I]),
     "hbpc_set_schur": (_I, [_CTX, _I]),
+    "hbpc_set_boundary": (_I, [_CTX, _I, _I, _P, _I, _P]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -292,6 +294,24 @@ class Context:
     def set_schur(self, on=True):
         """Newton steps through the Schur-complement system of Sec. 3.2.4 (FP64)."""
         self._c(_lib.hbpc_set_schur(self._ctx, 1 if on else 0))
+
+    def set_boundary(self, dim_index, lo, hi):
+        """Boundaries of direction dim_index: lo and hi are each None (periodic;
+        both or neither), "wall" (Euler slip wall) or a sequence of n_var
+        conservative values (constant Dirichlet state)."""
+        def kind(b):
+            if b is None:
+                return BC_PERIODIC, None
+            if isinstance(b, str):
+                if b != "wall":
+                    raise ValueError(b)
+                return BC_WALL, None
+            arr = np.ascontiguousarray(np.asarray(b, dtype=np.float64).ravel())
+            return BC_DIRICHLET, arr
+        klo, alo = kind(lo)
+        khi, ahi = kind(hi)
+        p = lambda a: a.ctypes.data if a is not None else None
+        self._c(_lib.hbpc_set_boundary(self._ctx, dim_index, klo, p(alo), khi, p(ahi)))
 
     def set_corrector_batch(self, on=True):
         """Solve the s - 1 corrector stages of every sweep as one batched Newton."""

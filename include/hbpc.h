@@ -276,6 +276,30 @@ typedef enum { HBPC_BC_PERIODIC = 0, HBPC_BC_DIRICHLET = 1, HBPC_BC_WALL = 2 } h
 hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double* state_lo, int kind_hi,
                               const double* state_hi);
 
+/* Device-driven steps (Algorithm 1 with the Newton iteration of Eq. 17 and
+ * restarted GMRES; no counterpart in the paper's host-driven solver).  With
+ * on = 1 every hbpc_step / hbpc_advance_to step is ONE CUDA graph launch: the
+ * stages are straight-line work, every Newton iteration and every GMRES cycle
+ * a conditional WHILE node, a cycle's end and its restart IF nodes, and small
+ * control kernels take the decisions the host takes otherwise (the stopping
+ * tests of Sec. 3.2.1, the GMRES state, the iteration caps), so the host
+ * waits once per step instead of once per few Arnoldi columns.  The kernels,
+ * their order and hence the results are those of the host-driven step.  The
+ * graph is captured on the first step and again whenever the solver settings,
+ * the operator parameters (boundaries included) or launch shapes changed
+ * (hbpc_advance_to's shorter last step captures once more).  A failed solve
+ * ends the step with the same status as the host-driven step (HBPC_ERR_NONFINITE,
+ * HBPC_ERR_NO_CONVERGENCE) and leaves the state at the previous step; the
+ * counters (hbpc_get_stats) are read from the device after the step.  Covers
+ * FP64 and mixed precision, no preconditioner, BJ_ext and BJ^H_ext, single
+ * problems and batch groups; with the Schur form, corrector batching, the
+ * learned preconditioner, training-data collection, phase profiling or a
+ * stream the caller is capturing, steps run host-driven.  Allocates a small
+ * control block and a capture stream on the first on = 1; on = 1 with the
+ * Schur form, corrector batching or the learned preconditioner set is
+ * HBPC_ERR_UNSUPPORTED. */
+hbpc_status hbpc_set_step_graph(hbpc_ctx* ctx, int on);
+
 /* Bounded waits.  Every call of the context waits for its stream before it
  * returns (and inside the Newton loop, for the residual norms).  With a limit
  * of `seconds` > 0 such a wait gives up after that long and the call returns
@@ -482,6 +506,8 @@ hbpc_status hbpc_batch_node_coords(hbpc_batch* b, int inst, double* x);
 hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r);
 /* n_steps HBPC steps of every instance. */
 hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps);
+/* hbpc_set_step_graph for every group: each group's step is one graph launch. */
+hbpc_status hbpc_batch_set_step_graph(hbpc_batch* b, int on);
 /* Counters summed over groups (steps, t: the maximum). */
 hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out);
 hbpc_status hbpc_batch_profile_enable(hbpc_batch* b, int enable);

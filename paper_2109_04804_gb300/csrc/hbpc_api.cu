@@ -26,6 +26,7 @@
 #include "krylov.cuh"
 #include "batch_krylov.cuh"
 #include "bjext_kernels.cuh"
+#include "step_graph.cuh"
 #include "mlp.cuh"
 
 namespace hbpc {
@@ -338,6 +339,21 @@ struct hbpc_ctx {
     long long key[8] = {};      // launch shapes it was captured with
   } arn_graph[3];   // [2]: the Schur form
   int graph_mode = 1;
+  // the device-driven step (hbpc_set_step_graph): one CUDA graph per HBPC step,
+  // its Newton and GMRES loops as conditional WHILE/IF nodes
+  struct StepGraph {
+    bool on = false;
+    bool capturing = false;              // the step is being captured (no host waits)
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;      // configuration the graph was built for
+    cudaStream_t cap = nullptr;          // stream the graph is captured on
+    StepCtl* ctl = nullptr;              // device control block
+    StepCtl* ctl_host = nullptr;         // pinned copy, read after the graph
+    double* g0 = nullptr;                // per instance (groups): ||G_i^0||, ||dW_i||, active
+    double* dw = nullptr;
+    int* active = nullptr;
+    long long top_launches = 0, top_r1 = 0, top_r2 = 0;   // per step, outside the loops
+  } sg;
   double wait_limit_s = 0.0;  // bounded host waits (hbpc_set_wait_limit); 0 = none
   // every instance of a batch group has the same mesh (then J_i is shared
   // between instances as between elements)
@@ -829,8 +845,9 @@ hbpc_status lp_collect(hbpc_ctx* x, const double* W, double c1, double c2) {
 hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
   const bool linear = x->phys.law == HBPC_LAW_ADVECTION;
   const bool collecting = x->lp.per_newton > 0;
-  if (linear && !collecting && x->sol.pc != HBPC_PC_LEARNED && x->pc_built && x->pc_c1 == c1 &&
-      x->pc_c2 == c2)
+  // (a captured step rebuilds every time: its replays do not see this test)
+  if (!x->sg.capturing && linear && !collecting && x->sol.pc != HBPC_PC_LEARNED && x->pc_built &&
+      x->pc_c1 == c1 && x->pc_c2 == c2)
     return HBPC_OK;
   const size_t nb = size_t(x->nb);
   const bool mixed = x->sol.precision == HBPC_PREC_MIXED;
@@ -940,6 +957,10 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
                    x->Mpc, int(x->nE), L.nb, L.last_count, stride, L.last_off, L.last_row, L.cap, L.Tbuf));
   }
   HBPC_LAUNCH_CK(x, "pc build");
+  if (x->sg.capturing) {   // the singular flag is read after the step graph
+    x->pc_built = false;
+    return HBPC_OK;
+  }
   int sing = 0;
   HBPC_CK(x, cudaMemcpyAsync(&sing, x->singular, sizeof(int), cudaMemcpyDeviceToHost, x->stream));
   hbpc_status s = sync(x, "pc build");
@@ -1075,62 +1096,96 @@ hbpc_status arnoldi_batch(hbpc_ctx* x, int batch, int kind) {
   return HBPC_OK;
 }
 
-// Solve J dX = -G (G in x->G with squared norms in st->nrm) by restarted GMRES
-// from dX = 0; returns the iteration count through *its.
-hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) {
+// A restarted GMRES solve of J dX = -G (G in x->G with squared norms in
+// st->nrm) from dX = 0, split into the pieces that the host-driven loop
+// (gmres_run) and the device-driven step graph both launch:
+//   init     dX = 0, V_0 = -G, the first cycle's state;
+//   columns  a batch of Arnoldi columns (their kernels skip once the cycle's
+//            done flag is set);
+//   finish   end of a cycle: the small solve and dX += P^-1 V y;
+//   restart  V_0 = -G - J dX and the next cycle's state.
+// Kinds: the FP64 Krylov loop, the mixed (FP32) one, and the per-instance
+// FP32 GMRES of a batch group (batch_krylov.cuh).
+enum GmresKind { GM_FP64 = 0, GM_MIXED = 1, GM_BATCH = 2 };
+constexpr int kGmresBatch = 4;   // Arnoldi columns between two looks at the state
+
+hbpc_status gmres_init_fp64(hbpc_ctx* x) {
   const size_t n2 = size_t(2 * x->ndof);
   HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
   HBPC_CK(x, cudaMemcpyAsync(x->V, x->G, n2 * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
   HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
   HBPC_LAUNCH_CK(x, "k_cycle_init");
-  const int batch = 4;
+  return HBPC_OK;
+}
+
+hbpc_status gmres_finish_fp64(hbpc_ctx* x) {
+  hbpc_status s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<double><<<1, 32, 0, x->stream>>>(x->K));
+  if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->Z, 0));
+    s = pc_apply(x, x->Z, nullptr, nullptr, x->dX, 1, nullptr);
+    if (s != HBPC_OK) return s;
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->dX, 1));
+  }
+  HBPC_LAUNCH_CK(x, "gmres update");
+  return HBPC_OK;
+}
+
+hbpc_status gmres_restart_fp64(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  hbpc_status s = norms(x, x->dX, n2, x->dxn);
+  if (s != HBPC_OK) return s;
+  JvInput z{};
+  z.V = x->dX; z.ld = n2; z.half = size_t(x->ndof);
+  z.jidx = nullptr; z.vscale = nullptr;
+  z.nrmW = x->dxn + 1; z.nrmS = x->dxn + 2;
+  z.skip = nullptr;
+  z.out = x->V + n2; z.out_ld = n2; z.out_offset = 0; z.out_jidx = nullptr;
+  s = apply_jv(x, z);
+  if (s != HBPC_OK) return s;
+  if ((s = inst_scale<double>(x, x->V + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->V + n2, x->V, n2));
+  s = norms(x, x->V, n2);
+  if (s != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
+  HBPC_LAUNCH_CK(x, "k_cycle_init");
+  return HBPC_OK;
+}
+
+hbpc_status gmres_init(hbpc_ctx* x, int kind);
+hbpc_status gmres_columns(hbpc_ctx* x, int kind);
+hbpc_status gmres_finish(hbpc_ctx* x, int kind);
+hbpc_status gmres_restart(hbpc_ctx* x, int kind);
+
+// The host-driven loop: a look at the GMRES state after every batch of
+// columns; *its / *conv as the solve ended (a solve that reaches its
+// iteration cap returns with *conv false, Newton goes on).
+hbpc_status gmres_run(hbpc_ctx* x, int kind, int* its_out, bool* conv_out) {
+  hbpc_status s;
+  if ((s = gmres_init(x, kind)) != HBPC_OK) return s;
   int j_prev = 0;
   for (;;) {
-    hbpc_status s = arnoldi_batch(x, batch, 0);
-    if (s != HBPC_OK) return s;
-    s = read_state(x);
-    if (s != HBPC_OK) return s;
+    if ((s = gmres_columns(x, kind)) != HBPC_OK) return s;
+    if ((s = read_state(x)) != HBPC_OK) return s;
     const GmresState& h = *x->st_host;
     x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
     j_prev = h.j;
-    if (!(h.resid == h.resid) || std::isinf(h.resid))
+    if (kind != GM_BATCH && (!(h.resid == h.resid) || std::isinf(h.resid)))
       return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
     if (!h.done) continue;
-    // end of a cycle: dX += V y
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<double><<<1, 32, 0, x->stream>>>(x->K));
-    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->Z, 0));
-      s = pc_apply(x, x->Z, nullptr, nullptr, x->dX, 1, nullptr);
-      if (s != HBPC_OK) return s;
-    } else {
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<double, double><<<x->nblocks, kVecThreads, sizeof(double) * size_t(x->K.m + 1), x->stream>>>(x->K, x->dX, 1));
-    }
-    HBPC_LAUNCH_CK(x, "gmres update");
+    if ((s = gmres_finish(x, kind)) != HBPC_OK) return s;
     if (h.converged || h.its >= h.max_its) {
       *its_out = h.its;
       *conv_out = h.converged != 0;
       return HBPC_OK;
     }
-    // restart: V_0 = -G - J dX
-    s = norms(x, x->dX, n2, x->dxn);
-    if (s != HBPC_OK) return s;
-    JvInput z{};
-    z.V = x->dX; z.ld = n2; z.half = size_t(x->ndof);
-    z.jidx = nullptr; z.vscale = nullptr;
-    z.nrmW = x->dxn + 1; z.nrmS = x->dxn + 2;
-    z.skip = nullptr;
-    z.out = x->V + n2; z.out_ld = n2; z.out_offset = 0; z.out_jidx = nullptr;
-    s = apply_jv(x, z);
-    if (s != HBPC_OK) return s;
-    if ((s = inst_scale<double>(x, x->V + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->V + n2, x->V, n2));
-    s = norms(x, x->V, n2);
-    if (s != HBPC_OK) return s;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<double><<<1, 32, 0, x->stream>>>(x->K, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
-    HBPC_LAUNCH_CK(x, "k_cycle_init");
+    if ((s = gmres_restart(x, kind)) != HBPC_OK) return s;
     j_prev = 0;
   }
 }
+
+hbpc_status gmres(hbpc_ctx* x, int* its_out, bool* conv_out) { return gmres_run(x, GM_FP64, its_out, conv_out); }
 
 // ---------------------------------------------------------------------------
 // Mixed precision: the Krylov loop in FP32 (basis, Jacobian-vector product
@@ -1302,125 +1357,143 @@ hbpc_status arnoldi_step_f(hbpc_ctx* x) {
   return HBPC_OK;
 }
 
-hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) {
+hbpc_status gmres_init_mixed(hbpc_ctx* x) {
   const size_t n2 = size_t(2 * x->ndof);
   hbpc_status s;
   HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
   if ((s = to_float(x, x->G, x->Vf, n2)) != HBPC_OK) return s;
   HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, -1.0, x->sol.tol_gmres_rel, 1, x->sol.gmres_max_iter));
   HBPC_LAUNCH_CK(x, "k_cycle_init<float>");
-  const int batch = 4;
-  int j_prev = 0;
-  for (;;) {
-    if ((s = arnoldi_batch(x, batch, 1)) != HBPC_OK) return s;
-    if ((s = read_state(x)) != HBPC_OK) return s;
-    const GmresState& h = *x->st_host;
-    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
-    j_prev = h.j;
-    if (!(h.resid == h.resid) || std::isinf(h.resid))
-      return fail(x, HBPC_ERR_NONFINITE, "GMRES residual is not finite");
-    if (!h.done) continue;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<float><<<1, 32, 0, x->stream>>>(x->Kf));
-    const size_t smy = sizeof(double) * size_t(x->Kf.m + 1);
-    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, float><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->Zf, 0));
-      if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
-    } else {
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, double><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->dX, 1));
-    }
-    HBPC_LAUNCH_CK(x, "gmres<float> update");
-    if (h.converged || h.its >= h.max_its) {
-      *its_out = h.its;
-      *conv_out = h.converged != 0;
-      return HBPC_OK;
-    }
-    // restart: V_0 = -G - J dX (FP32 Jacobian-vector product of the FP32 copy of dX)
-    if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
-    JvInputT<float> z{};
-    z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
-    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
-    z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
-    if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
-    if ((s = inst_scale<float>(x, x->Vf + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, float><<<x->nblocks, kVecThreads, 0, x->stream>>>(x->Vf, n2, size_t(x->ndof), x->K, nullptr));
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
-    HBPC_LAUNCH_CK(x, "gmres<float> restart");
-    j_prev = 0;
-  }
+  return HBPC_OK;
 }
+
+hbpc_status gmres_finish_mixed(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  hbpc_status s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_solve_y<float><<<1, 32, 0, x->stream>>>(x->Kf));
+  const size_t smy = sizeof(double) * size_t(x->Kf.m + 1);
+  if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, float><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->Zf, 0));
+    if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_combine<float, double><<<x->nblocks, kVecThreads, smy, x->stream>>>(x->Kf, x->dX, 1));
+  }
+  HBPC_LAUNCH_CK(x, "gmres<float> update");
+  return HBPC_OK;
+}
+
+// restart: V_0 = -G - J dX (FP32 Jacobian-vector product of the FP32 copy of dX)
+hbpc_status gmres_restart_mixed(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  hbpc_status s;
+  if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
+  JvInputT<float> z{};
+  z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
+  z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
+  z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
+  if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+  if ((s = inst_scale<float>(x, x->Vf + n2, nullptr, 0, nullptr)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_norms<double, float><<<x->nblocks, kVecThreads, 0, x->stream>>>(x->Vf, n2, size_t(x->ndof), x->K, nullptr));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_cycle_init<float><<<1, 32, 0, x->stream>>>(x->Kf, 1.0, x->sol.tol_gmres_rel, 0, x->sol.gmres_max_iter));
+  HBPC_LAUNCH_CK(x, "gmres<float> restart");
+  return HBPC_OK;
+}
+
+hbpc_status gmres_f(hbpc_ctx* x, int* its_out, bool* conv_out) { return gmres_run(x, GM_MIXED, its_out, conv_out); }
 
 // Per-instance GMRES of a batch group in the mixed mode: J dX = -G for every
 // active instance with its own Krylov space (batch_krylov.cuh); converged
 // instances (zero right-hand side after the Newton freeze) take no step.
-hbpc_status gmres_bf(hbpc_ctx* x, int* its_out, bool* conv_out) {
-  const size_t n2 = size_t(2 * x->ndof);
+hbpc_status gmres_bstart(hbpc_ctx* x, double sign, int first) {
   BKrylovT<float>& K = x->BK;
   const int grid = x->bk_grid;
-  const size_t shm = size_t(K.m + 1) * (kVecWarps + 1) * sizeof(double);
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_btile_sqnorm<float><<<grid, kVecThreads, 0, x->stream>>>(K));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcycle_init<float><<<1, 256, 0, x->stream>>>(K, sign, x->sol.tol_gmres_rel, first, x->sol.gmres_max_iter));
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bscale0<float><<<grid, kVecThreads, 0, x->stream>>>(K));
+  HBPC_LAUNCH_CK(x, "batched cycle start");
+  return HBPC_OK;
+}
+
+hbpc_status gmres_init_batch(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
   hbpc_status s;
   HBPC_CK(x, cudaMemsetAsync(x->dX, 0, n2 * sizeof(double), x->stream));
   if ((s = to_float(x, x->G, x->Vf, n2)) != HBPC_OK) return s;
-  auto start = [&](double sign, int first) -> hbpc_status {
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_btile_sqnorm<float><<<grid, kVecThreads, 0, x->stream>>>(K));
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcycle_init<float><<<1, 256, 0, x->stream>>>(K, sign, x->sol.tol_gmres_rel, first, x->sol.gmres_max_iter));
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bscale0<float><<<grid, kVecThreads, 0, x->stream>>>(K));
-    HBPC_LAUNCH_CK(x, "batched cycle start");
-    return HBPC_OK;
-  };
-  if ((s = start(-1.0, 1)) != HBPC_OK) return s;
-  const int batch = 4;
-  int j_prev = 0;
-  for (;;) {
-    for (int b = 0; b < batch; ++b) {
-      if (x->sol.pc != HBPC_PC_NONE &&
-          (s = pc_apply_f(x, x->Vf, &x->st->j, nullptr, x->Zf, 0, &x->st->done)) != HBPC_OK)
-        return s;
-      JvInputT<float> z{};
-      z.V = x->sol.pc != HBPC_PC_NONE ? x->Zf : x->Vf;
-      z.ld = n2; z.half = size_t(x->ndof);
-      z.jidx = x->sol.pc != HBPC_PC_NONE ? nullptr : &x->st->j;
-      z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;   // not read by the FP32 products
-      z.skip = &x->st->done;
-      z.out = x->Vf; z.out_ld = n2; z.out_offset = 1; z.out_jidx = &x->st->j;
-      if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
-      void* args[] = {&K};
-      HBPC_RUN(x, HBPC_PHASE_DOT, 1,
-               cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_bcgs_coop<float>), dim3(grid),
-                                           dim3(kVecThreads), args, shm, x->stream));
-      HBPC_LAUNCH_CK(x, "k_bcgs_coop");
-    }
-    if ((s = read_state(x)) != HBPC_OK) return s;
-    const GmresState& h = *x->st_host;
-    x->stats.arnoldi_cols += arnoldi_cols(j_prev, h.j);
-    j_prev = h.j;
-    if (!h.done) continue;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bsolve_y<float><<<(K.ninst + 7) / 8, 256, 0, x->stream>>>(K));
-    if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, float><<<grid, kVecThreads, 0, x->stream>>>(K, x->Zf, 0));
-      if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
-    } else {
-      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, double><<<grid, kVecThreads, 0, x->stream>>>(K, x->dX, 1));
-    }
-    HBPC_LAUNCH_CK(x, "batched gmres update");
-    if (h.converged || h.its >= h.max_its) {
-      *its_out = h.its;
-      *conv_out = h.converged != 0;
-      return HBPC_OK;
-    }
-    // restart: V_0 = -G - J dX, every instance from its own residual
-    if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
+  return gmres_bstart(x, -1.0, 1);
+}
+
+hbpc_status gmres_columns_batch(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  BKrylovT<float>& K = x->BK;
+  const size_t shm = size_t(K.m + 1) * (kVecWarps + 1) * sizeof(double);
+  hbpc_status s;
+  for (int b = 0; b < kGmresBatch; ++b) {
+    if (x->sol.pc != HBPC_PC_NONE &&
+        (s = pc_apply_f(x, x->Vf, &x->st->j, nullptr, x->Zf, 0, &x->st->done)) != HBPC_OK)
+      return s;
     JvInputT<float> z{};
-    z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
-    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
-    z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
+    z.V = x->sol.pc != HBPC_PC_NONE ? x->Zf : x->Vf;
+    z.ld = n2; z.half = size_t(x->ndof);
+    z.jidx = x->sol.pc != HBPC_PC_NONE ? nullptr : &x->st->j;
+    z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;   // not read by the FP32 products
+    z.skip = &x->st->done;
+    z.out = x->Vf; z.out_ld = n2; z.out_offset = 1; z.out_jidx = &x->st->j;
     if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
-    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
-    if ((s = start(1.0, 0)) != HBPC_OK) return s;
-    j_prev = 0;
+    void* args[] = {&K};
+    HBPC_RUN(x, HBPC_PHASE_DOT, 1,
+             cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_bcgs_coop<float>), dim3(x->bk_grid),
+                                         dim3(kVecThreads), args, shm, x->stream));
+    HBPC_LAUNCH_CK(x, "k_bcgs_coop");
   }
+  return HBPC_OK;
+}
+
+hbpc_status gmres_finish_batch(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  BKrylovT<float>& K = x->BK;
+  const int grid = x->bk_grid;
+  hbpc_status s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bsolve_y<float><<<(K.ninst + 7) / 8, 256, 0, x->stream>>>(K));
+  if (x->sol.pc != HBPC_PC_NONE) {   // dX += P^-1 (V y)
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, float><<<grid, kVecThreads, 0, x->stream>>>(K, x->Zf, 0));
+    if ((s = pc_apply_f(x, x->Zf, nullptr, nullptr, x->Zf2, 0, nullptr)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add_float<<<grid_for(n2), 256, 0, x->stream>>>(x->Zf2, x->dX, n2));
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_bcombine<float, double><<<grid, kVecThreads, 0, x->stream>>>(K, x->dX, 1));
+  }
+  HBPC_LAUNCH_CK(x, "batched gmres update");
+  return HBPC_OK;
+}
+
+// restart: V_0 = -G - J dX, every instance from its own residual
+hbpc_status gmres_restart_batch(hbpc_ctx* x) {
+  const size_t n2 = size_t(2 * x->ndof);
+  hbpc_status s;
+  if ((s = to_float(x, x->dX, x->Zf, n2)) != HBPC_OK) return s;
+  JvInputT<float> z{};
+  z.V = x->Zf; z.ld = n2; z.half = size_t(x->ndof);
+  z.nrmW = x->zn + 1; z.nrmS = x->zn + 2;
+  z.out = x->Vf + n2; z.out_ld = n2; z.out_offset = 0;
+  if ((s = apply_jv_f(x, z)) != HBPC_OK) return s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_neg_sum_f<<<grid_for(n2), 256, 0, x->stream>>>(x->G, x->Vf + n2, x->Vf, n2));
+  return gmres_bstart(x, 1.0, 0);
+}
+
+hbpc_status gmres_bf(hbpc_ctx* x, int* its_out, bool* conv_out) { return gmres_run(x, GM_BATCH, its_out, conv_out); }
+
+hbpc_status gmres_init(hbpc_ctx* x, int kind) {
+  return kind == GM_FP64 ? gmres_init_fp64(x) : kind == GM_MIXED ? gmres_init_mixed(x) : gmres_init_batch(x);
+}
+hbpc_status gmres_columns(hbpc_ctx* x, int kind) {
+  return kind == GM_BATCH ? gmres_columns_batch(x) : arnoldi_batch(x, kGmresBatch, kind);
+}
+hbpc_status gmres_finish(hbpc_ctx* x, int kind) {
+  return kind == GM_FP64 ? gmres_finish_fp64(x) : kind == GM_MIXED ? gmres_finish_mixed(x) : gmres_finish_batch(x);
+}
+hbpc_status gmres_restart(hbpc_ctx* x, int kind) {
+  return kind == GM_FP64 ? gmres_restart_fp64(x) : kind == GM_MIXED ? gmres_restart_mixed(x) : gmres_restart_batch(x);
 }
 
 hbpc_status residual(hbpc_ctx* x, const double* b, double c1, double c2) {
@@ -1585,8 +1658,12 @@ hbpc_status eval_r1r2(hbpc_ctx* x, const double* w, double* r1, double* r2) {
   return HBPC_OK;
 }
 
-// One HBPC(q, k_max) step of Algorithm 1 on x->Wn.
-hbpc_status hbpc_one_step(hbpc_ctx* x) {
+// One HBPC(q, k_max) step of Algorithm 1 on x->Wn, every implicit stage
+// solved by `solve` (the host-driven Newton, or its graph form while the step
+// is captured: then the new state is copied to x->Wn only if no solve failed,
+// and nothing waits for the device).
+using NewtonFn = hbpc_status (*)(hbpc_ctx*, const double*, double, double, const double*);
+hbpc_status step_body(hbpc_ctx* x, NewtonFn solve, bool graph) {
   const long long n = x->ndof;
   const int s = x->s;
   const double dt = x->sol.dt;
@@ -1603,7 +1680,7 @@ hbpc_status hbpc_one_step(hbpc_ctx* x) {
     const double a1 = dc / 2.0, a2 = dc * dc / 6.0;
     if ((st = lincomb(x, x->bvec, {{1.0, W(0, l - 1)}, {a1 * dt, R1(0, l - 1)},
                                    {a2 * dt * dt / 2.0, R2(0, l - 1)}})) != HBPC_OK) return st;
-    if ((st = newton(x, x->bvec, a1, a2, W(0, l - 1))) != HBPC_OK) return st;
+    if ((st = solve(x, x->bvec, a1, a2, W(0, l - 1))) != HBPC_OK) return st;
     HBPC_CK(x, cudaMemcpyAsync(W(0, l), x->X, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
     if ((st = eval_r1r2(x, W(0, l), R1(0, l), R2(0, l))) != HBPC_OK) return st;
   }
@@ -1631,7 +1708,7 @@ hbpc_status hbpc_one_step(hbpc_ctx* x) {
       HBPC_LAUNCH_CK(x, "corrector rhs");
       return HBPC_OK;
     };
-    if (x->cb && s > 1) {
+    if (x->cb && s > 1 && !graph) {
       // the s - 1 stages of this sweep depend only on level cur: one batched
       // Newton solve with stage l as instance l - 1 (Sec. 6 outlook)
       hbpc_ctx* g = x->cb;
@@ -1661,15 +1738,300 @@ hbpc_status hbpc_one_step(hbpc_ctx* x) {
     }
     for (int l = 1; l < s; ++l) {
       if ((st = rhs(l, x->bvec)) != HBPC_OK) return st;
-      if ((st = newton(x, x->bvec, 1.0, 1.0, Wc(l))) != HBPC_OK) return st;
+      if ((st = solve(x, x->bvec, 1.0, 1.0, Wc(l))) != HBPC_OK) return st;
       HBPC_CK(x, cudaMemcpyAsync(W(nxt, l), x->X, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
       if ((st = eval_r1r2(x, W(nxt, l), R1(nxt, l), R2(nxt, l))) != HBPC_OK) return st;
     }
     cur = nxt;
   }
   const double* last = (s - 1 == 0) ? W(0, 0) : W(cur, s - 1);
+  if (graph) {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_copy_if_ok<<<grid_for(size_t(n)), 256, 0, x->stream>>>(last, x->Wn, size_t(n), x->sg.ctl));
+    HBPC_LAUNCH_CK(x, "step result");
+    return HBPC_OK;
+  }
   HBPC_CK(x, cudaMemcpyAsync(x->Wn, last, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
   return sync(x, "hbpc step");
+}
+
+// ---- the step as one CUDA graph ----------------------------------------------
+// The graph is captured segment by segment (cudaStreamBeginCaptureToGraph on a
+// private stream): straight-line work between two loops is one captured
+// segment, a loop or branch is a conditional node whose body graph is captured
+// the same way.  Each level keeps its frontier (the nodes the next one depends
+// on) and counts the kernels launched in it outside its nested bodies, which
+// the control kernel of that level adds to the step's count every time it runs.
+struct GBuild {
+  hbpc_ctx* x;
+  struct Level {
+    cudaGraph_t g;
+    std::vector<cudaGraphNode_t> front;
+    long long l0, nested;
+  };
+  std::vector<Level> lv;
+  cudaError_t e = cudaSuccess;
+  bool open_seg = false;
+
+  void begin() {
+    if (e != cudaSuccess) return;
+    Level& L = lv.back();
+    e = cudaStreamBeginCaptureToGraph(x->stream, L.g, L.front.empty() ? nullptr : L.front.data(), nullptr,
+                                      L.front.size(), cudaStreamCaptureModeThreadLocal);
+    open_seg = e == cudaSuccess;
+  }
+  void end() {
+    if (!open_seg) return;
+    open_seg = false;
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e1 = cudaStreamGetCaptureInfo(x->stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    std::vector<cudaGraphNode_t> f;
+    if (e1 == cudaSuccess) f.assign(deps, deps + nd);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(x->stream, &out);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) lv.back().front = f;
+  }
+  cudaGraphConditionalHandle handle() {
+    end();
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, lv.back().g, 0, 0);
+    begin();
+    return h;
+  }
+  void open(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+    end();
+    if (e != cudaSuccess) return;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    Level& L = lv.back();
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, L.g, L.front.empty() ? nullptr : L.front.data(), nullptr, L.front.size(), &p);
+    if (e != cudaSuccess) return;
+    L.front.assign(1, node);
+    lv.push_back(Level{p.conditional.phGraph_out[0], {}, x->stats.launches, 0});
+    begin();
+  }
+  void close() {
+    end();
+    const long long total = x->stats.launches - lv.back().l0;
+    lv.pop_back();
+    lv.back().nested += total;
+    begin();
+  }
+  // kernels of the current level outside its nested bodies, plus one (the
+  // control kernel about to be launched)
+  int own() const { return int(x->stats.launches - lv.back().l0 - lv.back().nested) + 1; }
+};
+
+thread_local GBuild* g_build = nullptr;   // the builder of the step this thread captures
+
+// The GMRES solve of gmres_run as nodes: a WHILE loop over batches of columns
+// with the cycle end and the restart as nested IF branches.
+hbpc_status gmres_graph(hbpc_ctx* x, GBuild& B, int kind) {
+  hbpc_status s;
+  if ((s = gmres_init(x, kind)) != HBPC_OK) return s;
+  const cudaGraphConditionalHandle h_loop = B.handle();
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_gmres_begin<<<1, 32, 0, x->stream>>>(x->sg.ctl, h_loop, 0));
+  B.open(h_loop, cudaGraphCondTypeWhile);
+  {
+    const cudaGraphConditionalHandle h_end = B.handle();
+    if ((s = gmres_columns(x, kind)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_gmres_tick<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl, h_loop, h_end, kind != GM_BATCH ? 1 : 0, B.own()));
+    B.open(h_end, cudaGraphCondTypeIf);
+    {
+      const cudaGraphConditionalHandle h_restart = B.handle();
+      if ((s = gmres_finish(x, kind)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_gmres_end<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl, h_loop, h_restart, B.own()));
+      B.open(h_restart, cudaGraphCondTypeIf);
+      if ((s = gmres_restart(x, kind)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_count<<<1, 32, 0, x->stream>>>(x->sg.ctl, B.own()));
+      B.close();
+    }
+    B.close();
+  }
+  B.close();
+  HBPC_LAUNCH_CK(x, "gmres graph");
+  return B.e == cudaSuccess ? HBPC_OK : cuda_fail(x, B.e, "gmres graph");
+}
+
+// Newton of `newton` / `newton_batch` as nodes: a WHILE loop whose control
+// kernel applies the stopping tests; the evaluation counts of its body are
+// taken out of the per-step (outside-the-loops) counts.
+hbpc_status newton_graph(hbpc_ctx* x, const double* b, double a1, double a2, const double* W0) {
+  GBuild& B = *g_build;
+  const long long n = x->ndof;
+  const size_t n2 = size_t(2 * n);
+  const int ni = x->ninst;
+  const double dt = x->sol.dt;
+  const double c1 = a1 * dt, c2 = a2 * dt * dt / 2.0;
+  hbpc_status s;
+  HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_set2<<<1, 32, 0, x->stream>>>(x->c12, c1, c2));
+  if (W0 != x->X) HBPC_CK(x, cudaMemcpyAsync(x->X, W0, n * sizeof(double), cudaMemcpyDeviceToDevice, x->stream));
+  HBPC_RUN(x, HBPC_PHASE_OPERATOR, 1, x->ops.r1(x->prm, x->X, x->X + n, x->stream));
+  HBPC_LAUNCH_CK(x, "r1");
+  x->stats.r1_evals += 1;
+  if ((s = residual(x, b, c1, c2)) != HBPC_OK) return s;
+  auto inst_sq = [&](const double* v) {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1,
+             k_inst_sqnorms<<<ni, kInstThreads, 0, x->stream>>>(v, size_t(n), x->d_irange, x->d_inrm));
+  };
+  const int per_inst = x->bk ? 1 : 0;
+  const cudaGraphConditionalHandle h_newton = B.handle();
+  if (ni > 0) {
+    inst_sq(x->G);
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_newton_begin_batch<<<1, 256, 0, x->stream>>>(ni, x->d_inrm, x->sg.g0, x->sg.active, x->d_iscale, per_inst, x->sg.ctl, h_newton, 0));
+  } else {
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_newton_begin<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl, h_newton, 0));
+  }
+  HBPC_LAUNCH_CK(x, "newton graph start");
+  const long long r1_0 = x->stats.r1_evals, r2_0 = x->stats.r2_evals;
+  B.open(h_newton, cudaGraphCondTypeWhile);
+  {
+    if (ni > 0) {
+      if ((s = inst_scale<double>(x, x->G, nullptr, 0, nullptr)) != HBPC_OK) return s;
+      if ((s = norms(x, x->G, n2)) != HBPC_OK) return s;   // of the scaled right-hand side
+    }
+    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    int kind = GM_FP64;
+    if (x->sol.precision == HBPC_PREC_MIXED) {
+      if ((s = to_float(x, x->X, x->Wf, n2)) != HBPC_OK) return s;
+      kind = (ni > 0 && x->bk) ? GM_BATCH : GM_MIXED;
+    }
+    if ((s = gmres_graph(x, B, kind)) != HBPC_OK) return s;
+    HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_add<<<grid_for(n2), 256, 0, x->stream>>>(x->dX, x->X, n2));
+    if (ni > 0) {
+      inst_sq(x->dX);
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_save_dw_batch<<<1, 256, 0, x->stream>>>(ni, x->d_inrm, x->sg.dw));
+    } else {
+      if ((s = norms(x, x->dX, n2)) != HBPC_OK) return s;
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_save_dw<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl));
+    }
+    if ((s = residual(x, b, c1, c2)) != HBPC_OK) return s;
+    if (ni > 0) {
+      inst_sq(x->G);
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_newton_check_batch<<<1, 256, 0, x->stream>>>(ni, x->d_inrm, x->sg.dw, x->sg.g0, x->sg.active, x->d_iscale, per_inst, x->sg.ctl, h_newton, x->sol.tol_newton_rel, x->sol.tol_newton_abs, x->sol.newton_max_iter, B.own()));
+    } else {
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_newton_check<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl, h_newton, x->sol.tol_newton_rel, x->sol.tol_newton_abs, x->sol.newton_max_iter, B.own()));
+    }
+    HBPC_LAUNCH_CK(x, "newton graph check");
+  }
+  B.close();
+  x->stats.r1_evals = r1_0;   // the body's evaluations are counted per iteration after the step
+  x->stats.r2_evals = r2_0;
+  return B.e == cudaSuccess ? HBPC_OK : cuda_fail(x, B.e, "newton graph");
+}
+
+// The configuration a step graph depends on: solver settings, operator
+// parameters (passed by value into its kernels), launch shapes and buffers.
+std::vector<unsigned char> step_graph_key(const hbpc_ctx* x) {
+  std::vector<unsigned char> k;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    k.insert(k.end(), c, c + n);
+  };
+  put(&x->sol, sizeof(x->sol));
+  put(&x->prm, sizeof(x->prm));
+  put(&x->prmf, sizeof(x->prmf));
+  const long long v[] = {x->nblocks, x->pc_threads, x->pc_grid, (long long)x->pc_smem, x->bk_grid, x->coop ? 1 : 0,
+                         x->pc_shared ? 1 : 0, (long long)(uintptr_t)x->Jpc, (long long)(uintptr_t)x->Mpc,
+                         (long long)(uintptr_t)x->Jf, (long long)(uintptr_t)x->Mf, x->s};
+  put(v, sizeof(v));
+  return k;
+}
+
+// One step through the step graph: captured on first use and whenever the
+// configuration changed, then one cudaGraphLaunch, one wait and one read of
+// the control block.
+hbpc_status step_graph_run(hbpc_ctx* x) {
+  auto key = step_graph_key(x);
+  if (!x->sg.exec || key != x->sg.key) {
+    if (x->sg.exec) { cudaGraphExecDestroy(x->sg.exec); x->sg.exec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    HBPC_CK(x, cudaGraphCreate(&graph, 0));
+    const cudaStream_t real = x->stream;
+    const hbpc_stats stats0 = x->stats;
+    const std::string err0 = x->err;
+    GBuild B{x};
+    B.lv.push_back(GBuild::Level{graph, {}, x->stats.launches, 0});
+    x->stream = x->sg.cap;
+    x->sg.capturing = true;
+    g_build = &B;
+    B.begin();
+    hbpc_status s = HBPC_OK;
+    if (B.e == cudaSuccess) {
+      HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_reset<<<1, 32, 0, x->stream>>>(x->sg.ctl));
+      s = step_body(x, newton_graph, true);
+    }
+    B.end();
+    const long long top = int(x->stats.launches - B.lv[0].l0 - B.lv[0].nested);
+    x->sg.top_launches = top - 1;   // k_sg_reset counts itself on the device
+    x->sg.top_r1 = x->stats.r1_evals - stats0.r1_evals;
+    x->sg.top_r2 = x->stats.r2_evals - stats0.r2_evals;
+    g_build = nullptr;
+    x->sg.capturing = false;
+    x->stream = real;
+    x->stats = stats0;   // the capture ran nothing
+    if (s == HBPC_OK && B.e != cudaSuccess) s = cuda_fail(x, B.e, "step graph capture");
+    if (s == HBPC_OK) {
+      const cudaError_t e = cudaGraphInstantiate(&x->sg.exec, graph, 0);
+      if (e != cudaSuccess) { x->sg.exec = nullptr; s = cuda_fail(x, e, "step graph instantiate"); }
+    }
+    cudaGraphDestroy(graph);
+    if (s != HBPC_OK) {
+      (void)cudaGetLastError();
+      return s;
+    }
+    x->err = err0;
+    x->sg.key = key;
+  }
+  HBPC_CK(x, cudaGraphLaunch(x->sg.exec, x->stream));
+  HBPC_CK(x, cudaMemcpyAsync(x->sg.ctl_host, x->sg.ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, x->stream));
+  int sing = 0;
+  if (x->singular) HBPC_CK(x, cudaMemcpyAsync(&sing, x->singular, sizeof(int), cudaMemcpyDeviceToHost, x->stream));
+  hbpc_status s = sync(x, "step graph");
+  if (s != HBPC_OK) return s;
+  const StepCtl& c = *x->sg.ctl_host;
+  const bool lin = x->ops.jv_linear != nullptr;
+  const long long per = lin ? 2 : 3;
+  x->stats.launches += x->sg.top_launches + c.launches;
+  x->stats.newton_solves += c.newton_solves;
+  x->stats.newton_its += c.newton_its;
+  x->stats.gmres_its += c.gmres_its;
+  x->stats.arnoldi_cols += c.arnoldi_cols;
+  x->stats.r1_evals += x->sg.top_r1 + c.newton_its + c.gmres_its * (lin ? 2 : 1);
+  x->stats.r2_evals += x->sg.top_r2 + c.newton_its + c.gmres_its * (per - (lin ? 2 : 1));
+  if (sing) {
+    HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
+    return fail(x, HBPC_ERR_NONFINITE, "BJ_ext block is singular");
+  }
+  if (c.err) {
+    const char* what = c.where == 1 ? "initial Newton residual is not finite"
+                       : c.where == 2 ? "Newton residual is not finite"
+                       : c.where == 3 ? "GMRES residual is not finite"
+                                      : "Newton did not converge within newton_max_iter";
+    return fail(x, hbpc_status(c.err), std::string("step graph: ") + what);
+  }
+  return HBPC_OK;
+}
+
+// Settings the step graph does not cover: the step then runs host-driven.
+bool step_graph_covers(const hbpc_ctx* x) {
+  return !x->schur && !x->cb && x->sol.pc != HBPC_PC_LEARNED && !x->prof.on && x->lp.per_newton == 0;
+}
+
+hbpc_status hbpc_one_step(hbpc_ctx* x) {
+  if (x->sg.on && step_graph_covers(x)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (x->stream == nullptr || (cudaStreamIsCapturing(x->stream, &cs) == cudaSuccess &&
+                                 cs == cudaStreamCaptureStatusNone))
+      return step_graph_run(x);
+  }
+  return step_body(x, newton, false);
 }
 
 template <typename Tp>
@@ -1689,6 +2051,10 @@ hbpc_status dmalloc(hbpc_ctx* x, Tp** p, size_t count) {
 void free_all(hbpc_ctx* x) {
   for (auto& g : x->arn_graph)
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+  if (x->sg.exec) { cudaGraphExecDestroy(x->sg.exec); x->sg.exec = nullptr; }
+  if (x->sg.cap) { cudaStreamDestroy(x->sg.cap); x->sg.cap = nullptr; }
+  cudaFree(x->sg.ctl); cudaFree(x->sg.g0); cudaFree(x->sg.dw); cudaFree(x->sg.active);
+  if (x->sg.ctl_host) cudaFreeHost(x->sg.ctl_host);
   for (auto& p : x->prof.pend) { x->prof.pool.push_back(p.a); x->prof.pool.push_back(p.b); }
   for (cudaEvent_t e : x->prof.pool) cudaEventDestroy(e);
   x->prof.pool.clear();
@@ -2546,6 +2912,31 @@ hbpc_status hbpc_set_wait_limit(hbpc_ctx* ctx, double seconds) {
   return HBPC_OK;
 }
 
+hbpc_status hbpc_set_step_graph(hbpc_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
+  if (!on) {
+    ctx->sg.on = false;
+    return HBPC_OK;
+  }
+  if (ctx->schur) return fail(ctx, HBPC_ERR_UNSUPPORTED, "the step graph needs the Schur form off");
+  if (ctx->cb) return fail(ctx, HBPC_ERR_UNSUPPORTED, "the step graph needs corrector batching off");
+  if (ctx->sol.pc == HBPC_PC_LEARNED)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "the step graph does not cover the learned preconditioner");
+  if (!ctx->sg.ctl) {
+    hbpc_status s;
+    if ((s = dmalloc(ctx, &ctx->sg.ctl, 1)) != HBPC_OK) return s;
+    if (ctx->ninst > 0 && ((s = dmalloc(ctx, &ctx->sg.g0, ctx->ninst)) || (s = dmalloc(ctx, &ctx->sg.dw, ctx->ninst)) ||
+                           (s = dmalloc(ctx, &ctx->sg.active, ctx->ninst))))
+      return s;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&ctx->sg.ctl_host), sizeof(StepCtl));
+    if (e != cudaSuccess) { ctx->sg.ctl_host = nullptr; return fail(ctx, HBPC_ERR_OOM, "cudaMallocHost"); }
+    e = cudaStreamCreateWithFlags(&ctx->sg.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ctx->sg.cap = nullptr; return cuda_fail(ctx, e, "step graph stream"); }
+  }
+  ctx->sg.on = true;
+  return HBPC_OK;
+}
+
 hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
   if (!on) { ctx->schur = false; return HBPC_OK; }
@@ -3291,6 +3682,15 @@ hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r) {
   HBPC_LAUNCH_CK(x, "batch eval_R1");
   HBPC_CK(x, cudaMemcpyAsync(r, x->r1 + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
   return sync(x, "batch eval_R1");
+}
+
+hbpc_status hbpc_batch_set_step_graph(hbpc_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
+  for (hbpc_ctx* x : b->g) {
+    const hbpc_status s = hbpc_set_step_graph(x, on);
+    if (s != HBPC_OK) { b->err = x->err; return s; }
+  }
+  return HBPC_OK;
 }
 
 hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps) {

@@ -98,6 +98,7 @@ _SIGS = {
     "hbpc_set_corrector_batch": (_I, [_CTX, _I]),
     "hbpc_set_schur": (_I, [_CTX, _I]),
     "hbpc_set_boundary": (_I, [_CTX, _I, _I, _P, _I, _P]),
+    "hbpc_set_step_graph": (_I, [_CTX, _I]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -131,6 +132,7 @@ _SIGS = {
     "hbpc_batch_node_coords": (_I, [_CTX, _I, _P]),
     "hbpc_batch_eval_R1": (_I, [_CTX, _I, _P]),
     "hbpc_batch_step": (_I, [_CTX, _I]),
+    "hbpc_batch_set_step_graph": (_I, [_CTX, _I]),
     "hbpc_batch_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
     "hbpc_batch_profile_enable": (_I, [_CTX, _I]),
     "hbpc_batch_last_error": (ctypes.c_char_p, [_CTX]),
@@ -312,6 +314,10 @@ class Context:
         khi, ahi = kind(hi)
         p = lambda a: a.ctypes.data if a is not None else None
         self._c(_lib.hbpc_set_boundary(self._ctx, dim_index, klo, p(alo), khi, p(ahi)))
+
+    def set_step_graph(self, on=True):
+        """Every step as one CUDA graph launch (device-driven Newton and GMRES)."""
+        self._c(_lib.hbpc_set_step_graph(self._ctx, 1 if on else 0))
 
     def set_corrector_batch(self, on=True):
         """Solve the s - 1 corrector stages of every sweep as one batched Newton."""
@@ -508,6 +514,10 @@ class Batch:
 
     def step(self, n=1):
         self._c(_lib.hbpc_batch_step(self._b, n))
+
+    def set_step_graph(self, on=True):
+        """Every group's step as one CUDA graph launch."""
+        self._c(_lib.hbpc_batch_set_step_graph(self._b, 1 if on else 0))
 
     def stats(self):
         s = Stats()

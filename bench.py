@@ -895,6 +895,9 @@ BATCH = dict(n_inst=256, n_range=(16, 96), N_range=(3, 7), nu_range=(1e-3, 1e-2)
              gmres_restart=100, gmres_max_iter=3000, newton_max_iter=50, max_per_group=0)
 
 
+STEP_GRAPH = True   # the batch's steps as one CUDA graph per group (--no-step-graph: host-driven)
+
+
 def batch_instances(n_inst):
     """The seeded instance list of the batched viscous Burgers workload: square
     periodic meshes n x n on [0, 1]^2 with n uniform in 16..96, N uniform in
@@ -946,6 +949,11 @@ def run_batch(args, emit=True):
     for _ in range(args.warmup):
         b.step(1)
     tuning = b.autotune()          # launch shapes per group, on the warmed-up state
+    if STEP_GRAPH:
+        # every group's step as one graph launch, captured here (outside the
+        # timed steps) with the tuned launch shapes
+        b.set_step_graph(True)
+        b.step(1)
     torch.cuda.synchronize()
     st0 = b.stats()
     clocks = Clocks(local)
@@ -995,6 +1003,8 @@ def run_batch(args, emit=True):
                        "gmres_restart": BATCH["gmres_restart"], "precision": "mixed",
                        "timing": "host clock between device synchronisations (groups run on their own streams)",
                        "autotuned": tuning,
+                       "step_graph": STEP_GRAPH,
+                       "graph_launches_per_step": groups if STEP_GRAPH else 0,
                        "l2_between_steps": "flushed (256 MB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "r1_evals_per_s": (d["r1_evals"] + d["r2_evals"]) / t_sec,
@@ -1215,6 +1225,9 @@ def main():
                          "0: one after the other; -1 (default): batched in the mixed mode only")
     ap.add_argument("--headline-only", action="store_true",
                     help="the headline arm alone (for profiling): no second precision, oracle or vortex")
+    ap.add_argument("--no-step-graph", action="store_true",
+                    help="host-driven steps (a look at the GMRES state every few columns) instead of one CUDA "
+                         "graph launch per step with device-driven Newton and GMRES loops")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched viscous Burgers workload in the default line")
     ap.add_argument("--no-r1-roofline", action="store_true",
@@ -1241,6 +1254,8 @@ def main():
     ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    global STEP_GRAPH
+    STEP_GRAPH = not args.no_step_graph
     if args.oracle_task:
         oracle_task(args.oracle_task, args.oracle_out, args.oracle_steps)
     elif args.impl == "reference":

@@ -303,6 +303,7 @@ struct hbpc_ctx {
     float* ckey = nullptr; float* cmean = nullptr;   // stage classes and their mean inverses
     int* vflag = nullptr;                             // per element: learned block failed its check
     int* vcount = nullptr;                            // blocks replaced by the exact inverse (running sum)
+    int* gerr = nullptr;                              // a tensor-core GEMM's bounded wait ran out
     unsigned long long builds = 0;
     int* cls = nullptr;                               // class of every training sample
     bool stats = false;
@@ -647,9 +648,13 @@ hbpc_status gemm(hbpc_ctx* x, const __nv_bfloat16* A, int lda, const __nv_bfloat
                  int K, Epi epi) {
   if (K % 8 || lda % 8 || ldb % 8 || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
     return fail(x, HBPC_ERR_INVALID_ARG, "GEMM operands must be 16-byte aligned with K, ld multiples of 8");
-  const dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM);
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_gemm_bf16_nt<Epi><<<grid, kGemmThreads, 0, x->stream>>>(A, lda, B, ldb, M, N, K, epi));
-  HBPC_LAUNCH_CK(x, "k_gemm_bf16_nt");
+  if (M <= 0 || N <= 0 || K <= 0) return HBPC_OK;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_gemm_bf16_tc<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (attr != cudaSuccess) return cuda_fail(x, attr, "tensor-core GEMM shared memory");
+  const dim3 grid((N + kTcBN - 1) / kTcBN, (M + kTcBM - 1) / kTcBM);
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_gemm_bf16_tc<Epi><<<grid, kTcThreads, kTcSmem, x->stream>>>(A, lda, B, ldb, M, N, K, epi, x->lp.gerr));
+  HBPC_LAUNCH_CK(x, "k_gemm_bf16_tc");
   return HBPC_OK;
 }
 
@@ -682,8 +687,11 @@ hbpc_status lp_alloc(hbpc_ctx* x) {
       (e = dalloc_any(x, &L.Fi, size_t(x->nE) * L.dinp)) || (e = dalloc_any(x, &L.H1i, size_t(x->nE) * H)) ||
       (e = dalloc_any(x, &L.H2i, size_t(x->nE) * H)))
     return e;
-  if ((e = dalloc_any(x, &L.vflag, size_t(x->nE))) || (e = dalloc_any(x, &L.vcount, 1))) return e;
+  if ((e = dalloc_any(x, &L.vflag, size_t(x->nE))) || (e = dalloc_any(x, &L.vcount, 1)) ||
+      (e = dalloc_any(x, &L.gerr, 1)))
+    return e;
   HBPC_CK(x, cudaMemsetAsync(L.vcount, 0, sizeof(int), x->stream));
+  HBPC_CK(x, cudaMemsetAsync(L.gerr, 0, sizeof(int), x->stream));
   L.mu = L.P + L.np_train;
   L.sd = L.mu + L.dinp;
   L.ckey = L.sd + L.dinp;
@@ -723,6 +731,21 @@ hbpc_status lp_alloc_train(hbpc_ctx* x, int B, int P) {
   return HBPC_OK;
 }
 
+// The flag of the tensor-core GEMMs' bounded waits (read after the stream's
+// work; a set flag is an error and is cleared).
+hbpc_status lp_gemm_check(hbpc_ctx* x) {
+  if (!x->lp.gerr) return HBPC_OK;
+  int e = 0;
+  HBPC_CK(x, cudaMemcpyAsync(&e, x->lp.gerr, sizeof(int), cudaMemcpyDeviceToHost, x->stream));
+  hbpc_status s = sync(x, "tensor-core GEMM");
+  if (s != HBPC_OK) return s;
+  if (e) {
+    HBPC_CK(x, cudaMemsetAsync(x->lp.gerr, 0, sizeof(int), x->stream));
+    return fail(x, HBPC_ERR_CUDA, "a tensor-core GEMM gave up waiting for its MMAs");
+  }
+  return HBPC_OK;
+}
+
 void lp_free(hbpc_ctx* x) {
   auto& L = x->lp;
   for (void* q : {(void*)L.P, (void*)L.G, (void*)L.Mo, (void*)L.Ve, (void*)L.W1h, (void*)L.W2h, (void*)L.W3h,
@@ -730,7 +753,7 @@ void lp_free(hbpc_ctx* x) {
                   (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
                   (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
                   (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
-                  (void*)L.lpart, (void*)L.idx, (void*)L.cls, (void*)L.vflag, (void*)L.vcount})
+                  (void*)L.lpart, (void*)L.idx, (void*)L.cls, (void*)L.vflag, (void*)L.vcount, (void*)L.gerr})
     cudaFree(q);
   L = hbpc_ctx::Learned{};
 }
@@ -762,7 +785,7 @@ hbpc_status lp_infer(hbpc_ctx* x, const double* W, double c1, double c2) {
   // the stage class of (c1, c2) from the keys (host copy of the parameters' keys)
   float keys[2 * kMlpClasses];
   HBPC_CK(x, cudaMemcpyAsync(keys, L.ckey, sizeof(keys), cudaMemcpyDeviceToHost, x->stream));
-  if ((s = sync(x, "class keys")) != HBPC_OK) return s;
+  if ((s = lp_gemm_check(x)) != HBPC_OK) return s;   // waits for the keys too
   const float* cm = L.cmean + size_t(mlp_class(keys, float(c1), float(c2))) * L.doutp;
   if (x->sol.precision == HBPC_PREC_MIXED)
     return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.P + L.ob3, cm, x->Mf, L.nb});
@@ -3326,7 +3349,7 @@ hbpc_status hbpc_pc_model_forward(hbpc_ctx* ctx, int B, const float* F, const fl
   HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_mlp_mtilde<<<B, 256, 0, ctx->stream>>>(L.Ob, B, L.nb, L.doutp, L.cmean, L.cls, L.Jb));
   HBPC_LAUNCH_CK(ctx, "pc_model_forward");
   HBPC_CK(ctx, cudaMemcpyAsync(M, L.Jb, size_t(B) * L.dout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-  return sync(ctx, "pc_model_forward");
+  return lp_gemm_check(ctx);   // waits for the stream
 }
 
 hbpc_status hbpc_pc_adam_step(hbpc_ctx* ctx, const float* grads, double lr) {
@@ -3437,7 +3460,7 @@ hbpc_status hbpc_pc_train(hbpc_ctx* ctx, int loss_kind, int iters, int batch, in
     if ((s = lp_refresh(ctx)) != HBPC_OK) return s;
   }
   ctx->pc_built = false;
-  return sync(ctx, "pc_train");
+  return lp_gemm_check(ctx);   // waits for the stream
 }
 
 hbpc_status hbpc_profile_enable(hbpc_ctx* ctx, int enable) {

@@ -8,13 +8,13 @@
 // learned preconditioner; the same Newton tolerance fixes the answer whatever
 // preconditioner is used.
 //
-// GEMMs: BF16 operands, FP32 accumulation (gemm_bf16.cuh); master weights,
+// GEMMs: BF16 operands, FP32 accumulation on tcgen05 (gemm_tc.cuh); master weights,
 // Adam moments and the probe arithmetic in FP32.  Included by one translation
 // unit.
 #pragma once
 #include <cuda_bf16.h>
 
-#include "gemm_bf16.cuh"
+#include "gemm_tc.cuh"
 
 namespace hbpc {
 

@@ -50,12 +50,14 @@ def model(hb, seed):
     return ctx, info, p, rng, nb, din, dout
 
 
-def test_forward_blocks_elementwise(hb):
+@pytest.mark.parametrize("B", [24, 300])
+def test_forward_blocks_elementwise(hb, B):
+    """B = 300 spans three 128-row tiles of the tensor-core GEMMs with a ragged
+    last one (and n_b^2 = 1296 output columns, a ragged last 128-column tile)."""
     ctx, info, p, rng, nb, din, dout = model(hb, 41)
     keys = [(0.05, 0.002), (0.2, 0.015)]
     cms = [np.float32(0.1 * rng.standard_normal(dout)).astype(np.float64) for _ in keys]
     ctx.pc_model_set(layout(info, p, info["d_in_padded"], list(zip(keys, cms))))
-    B = 24
     F = np.zeros((B, info["d_in_padded"]))
     F[:, :din] = rng.standard_normal((B, din))
     F = bf16(F)

@@ -652,8 +652,11 @@ hbpc_status gemm(hbpc_ctx* x, const __nv_bfloat16* A, int lda, const __nv_bfloat
   static const cudaError_t attr =
       cudaFuncSetAttribute(k_gemm_bf16_tc<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (attr != cudaSuccess) return cuda_fail(x, attr, "tensor-core GEMM shared memory");
+  CUtensorMap ta, tb;
+  if (!tc_tensor_map(&ta, A, K, M, lda) || !tc_tensor_map(&tb, B, K, N, ldb))
+    return fail(x, HBPC_ERR_CUDA, "tensor map of a GEMM operand rejected");
   const dim3 grid((N + kTcBN - 1) / kTcBN, (M + kTcBM - 1) / kTcBM);
-  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_gemm_bf16_tc<Epi><<<grid, kTcThreads, kTcSmem, x->stream>>>(A, lda, B, ldb, M, N, K, epi, x->lp.gerr));
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_gemm_bf16_tc<Epi><<<grid, kTcThreads, kTcSmem, x->stream>>>(ta, tb, M, N, K, epi, x->lp.gerr));
   HBPC_LAUNCH_CK(x, "k_gemm_bf16_tc");
   return HBPC_OK;
 }

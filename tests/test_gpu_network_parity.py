@@ -50,10 +50,11 @@ def model(hb, seed):
     return ctx, info, p, rng, nb, din, dout
 
 
-@pytest.mark.parametrize("B", [24, 300])
+@pytest.mark.parametrize("B", [24, 296])
 def test_forward_blocks_elementwise(hb, B):
-    """B = 300 spans three 128-row tiles of the tensor-core GEMMs with a ragged
-    last one (and n_b^2 = 1296 output columns, a ragged last 128-column tile)."""
+    """B = 296 (a multiple of 8, as the entry point requires) spans three
+    128-row tiles of the tensor-core GEMMs with a ragged last one (and
+    n_b^2 = 1296 output columns, a ragged last 128-column tile)."""
     ctx, info, p, rng, nb, din, dout = model(hb, 41)
     keys = [(0.05, 0.002), (0.2, 0.015)]
     cms = [np.float32(0.1 * rng.standard_normal(dout)).astype(np.float64) for _ in keys]

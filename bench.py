@@ -1104,6 +1104,51 @@ def run_euler_pc(args, emit=True):
     return line
 
 
+def run_pc_network(args, emit=True):
+    """The learned preconditioner's build on the Euler vortex mesh (128^2, N = 4,
+    16,384 elements, n_b = 100): network inference (three BF16 tcgen05 GEMMs,
+    16,384 x 112 -> 256 -> 256 -> 10,000, the last one writing the FP32 blocks),
+    the probe check of every block and one apply, per hbpc_eval_pc call (mixed
+    precision, random network).  Reports ms per call and the GEMMs' FLOPs per
+    call; the GEMM kernels' own durations come from the profile."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    c = hbpc.Context(2, VORTEX["n"], VORTEX["lo"], VORTEX["hi"], VORTEX["N"], law=hbpc.LAW_EULER,
+                     flux=hbpc.FLUX_RUSANOV, q=VORTEX["q"], kmax=VORTEX["kmax"], dt=vortex_dt(), pc=hbpc.PC_LEARNED,
+                     precision=hbpc.PREC_MIXED)
+    c.pc_model_init(seed=1, out_scale=1e-2)
+    info = c.pc_model_info()
+    w = inputs.isentropic_vortex(c.node_coords())
+    n = c.ndof
+    X = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    X[:n] = torch.from_numpy(np.ascontiguousarray(w.ravel())).cuda()
+    v = torch.randn(2 * n, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    for _ in range(max(1, args.warmup)):
+        c.eval_pc(1.0, 1.0, X, v, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        c.eval_pc(1.0, 1.0, X, v, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    nE = c.ndof // (4 * 25)
+    H, din, dout = info["hidden"], info["d_in_padded"], 100 * 100
+    flops = 2.0 * nE * H * (din + H + dout)
+    c.close()
+    line = {"workload": "learned_pc_build_euler_vortex_128x128_N4", "ms_per_call": ms,
+            "gemm_gflop_per_call": flops / 1e9, "elements": nE,
+            "gemm_shapes": [[nE, H, din], [nE, H, H], [nE, dout, H]]}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def tgv_dt(n):
     """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v|_max + c of the
     initial state (|v| <= 1, c = 1/eps with p ~ 1/gamma)."""
@@ -1237,7 +1282,7 @@ def main():
                          "workload's own; mixed: FP32 Krylov loop, FP64 Newton residual/update")
     ap.add_argument("--workload", default="advection2d",
                     choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green", "r1_roofline",
-                             "euler_pc"],
+                             "euler_pc", "pc_network"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances; euler_vortex: learned vs BJ_ext vs plain GMRES; "
                          "taylor_green: the 3-D Navier-Stokes line; r1_roofline: the operator-pass roofline "
@@ -1270,6 +1315,8 @@ def main():
         run_r1_only(args)
     elif args.workload == "euler_pc":
         run_euler_pc(args)
+    elif args.workload == "pc_network":
+        run_pc_network(args)
     else:
         run_ours(args)
 

@@ -1027,7 +1027,8 @@ TGV = dict(n=32, N=5, q=4, kmax=0, cfl=20.0, eps=0.1, re=1600.0, prandtl=0.72, t
 
 
 EPC = dict(n=(16, 16), lo=(-1.0, -1.0), hi=(1.0, 1.0), N=5, q=4, kmax=0, tol_newton_rel=1e-8,
-           tol_newton_abs=1e-10, tol_gmres_rel=1e-3, gmres_restart=700, gmres_max_iter=7000, newton_max_iter=10,
+           tol_newton_abs=1e-10, tol_gmres_rel=1e-3, gmres_restart=700, gmres_max_iter=7000, newton_max_iter=50,
+           newton_max_iter_no_pc=10,
            eps=(1.0, 0.1, 0.01), dts=(0.0125, 0.05, 0.2, 0.8))
 
 
@@ -1037,13 +1038,14 @@ def run_euler_pc(args, emit=True):
     elements, N = 5, global LF with lambda = diag(1/eps, 1, 1, 1/eps), reference
     Mach numbers eps = 1, 0.1, 0.01, eps_GMRES = 1e-3, eps_Newton = 1e-8, restart
     700, at most 7000 GMRES iterations per Newton step (and the absolute
-    Newton test ||dW|| <= 1e-10, at most 10 Newton steps); one predictor step of
+    Newton test ||dW|| <= 1e-10, at most 50 Newton steps, 10 without a
+    preconditioner); one predictor step of
     HBPC(4, 0) (the J^predictor system, alpha = 1/2, 1/6) per time step size,
     in FP64, with no preconditioner, BJ_ext and BJ^H_ext (rebuilt every Newton
     iteration).  Reports GMRES iterations and device milliseconds per time step,
-    and each answer's distance to the no-preconditioner one.  An arm that did
-    not converge at some time step is not run at the larger ones of the same
-    eps (its cost only grows there)."""
+    and each answer's distance to the no-preconditioner one.  Without a
+    preconditioner, once a time step did not converge the larger ones of the
+    same eps are not run (each costs up to 70,000 GMRES iterations)."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__ as g
@@ -1056,7 +1058,8 @@ def run_euler_pc(args, emit=True):
                          flux=hbpc.FLUX_GLOBAL_LF, eps=eps, q=EPC["q"], kmax=EPC["kmax"], dt=dt,
                          tol_newton_rel=EPC["tol_newton_rel"], tol_newton_abs=EPC["tol_newton_abs"],
                          tol_gmres_rel=EPC["tol_gmres_rel"], gmres_restart=EPC["gmres_restart"],
-                         gmres_max_iter=EPC["gmres_max_iter"], newton_max_iter=EPC["newton_max_iter"],
+                         gmres_max_iter=EPC["gmres_max_iter"],
+                         newton_max_iter=EPC["newton_max_iter"] if pc != hbpc.PC_NONE else EPC["newton_max_iter_no_pc"],
                          pc=pc, precision=hbpc.PREC_FP64)
         c.set_state(inputs.density_wave(c.node_coords(), eps=eps))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1088,7 +1091,7 @@ def run_euler_pc(args, emit=True):
                     row[name] = {"ok": "not run: no convergence at a smaller dt"}
                     continue
                 r, w = one(eps, dt, pc)
-                if r["ok"] is not True:
+                if r["ok"] is not True and name == "no_pc":
                     failed.add(name)
                 if name == "no_pc":
                     ref = w

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 namespace hbpc {
 
@@ -82,6 +83,14 @@ __device__ __forceinline__ void tc_tma_box(uint32_t dst, const CUtensorMap* map,
       "l"(reinterpret_cast<uint64_t>(map)), "r"(k), "r"(row), "r"(mbar)
       : "memory");
 }
+
+// An epilogue with kStore16 takes the 16 consecutive columns a thread reads
+// from tensor memory at once (store16(m, n0, acc_bits, N)), so that it can
+// write them with vector stores.
+template <class Epi, class = void> struct TcStore16 { static constexpr bool value = false; };
+template <class Epi> struct TcStore16<Epi, std::void_t<decltype(Epi::kStore16)>> {
+  static constexpr bool value = Epi::kStore16;
+};
 
 template <class Epi>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap ta,
@@ -180,10 +189,14 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_bf16_tc(const __grid_consta
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
       if (m < M) {
+        if constexpr (TcStore16<Epi>::value) {
+          epi.store16(m, n0 + col, r, N);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = n0 + col + j;
-          if (n < N) epi(m, n, __uint_as_float(r[j]));
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + col + j;
+            if (n < N) epi(m, n, __uint_as_float(r[j]));
+          }
         }
       }
     }

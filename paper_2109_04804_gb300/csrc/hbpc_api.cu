@@ -299,6 +299,8 @@ struct hbpc_ctx {
     float* P = nullptr; float* G = nullptr; float* Mo = nullptr; float* Ve = nullptr;
     __nv_bfloat16* W1h = nullptr; __nv_bfloat16* W2h = nullptr; __nv_bfloat16* W3h = nullptr;
     __nv_bfloat16* W2T = nullptr; __nv_bfloat16* W3T = nullptr;
+    __nv_bfloat16* W3p = nullptr;   // W3's rows in block storage order (inference)
+    float* bp = nullptr;            // per class: bias + class mean + identity in storage order
     float* mu = nullptr; float* sd = nullptr;
     float* ckey = nullptr; float* cmean = nullptr;   // stage classes and their mean inverses
     int* vflag = nullptr;                             // per element: learned block failed its check
@@ -687,6 +689,7 @@ hbpc_status lp_alloc(hbpc_ctx* x) {
       (e = dalloc_any(x, &L.Ve, L.np)) || (e = dalloc_any(x, &L.W1h, H * L.dinp)) ||
       (e = dalloc_any(x, &L.W2h, H * H)) || (e = dalloc_any(x, &L.W3h, size_t(L.doutp) * H)) ||
       (e = dalloc_any(x, &L.W2T, H * H)) || (e = dalloc_any(x, &L.W3T, size_t(L.doutp) * H)) ||
+      (e = dalloc_any(x, &L.W3p, size_t(L.doutp) * H)) || (e = dalloc_any(x, &L.bp, size_t(kMlpClasses) * L.doutp)) ||
       (e = dalloc_any(x, &L.Fi, size_t(x->nE) * L.dinp)) || (e = dalloc_any(x, &L.H1i, size_t(x->nE) * H)) ||
       (e = dalloc_any(x, &L.H2i, size_t(x->nE) * H)))
     return e;
@@ -756,7 +759,8 @@ void lp_free(hbpc_ctx* x) {
                   (void*)L.cbuf, (void*)L.Fi, (void*)L.H1i, (void*)L.H2i, (void*)L.Fb, (void*)L.H1b, (void*)L.H2b,
                   (void*)L.dOb, (void*)L.dZ2, (void*)L.dZ1, (void*)L.dOT, (void*)L.H2T, (void*)L.dZ2T,
                   (void*)L.H1T, (void*)L.dZ1T, (void*)L.FT, (void*)L.Jb, (void*)L.cb, (void*)L.Ob, (void*)L.Xb,
-                  (void*)L.lpart, (void*)L.idx, (void*)L.cls, (void*)L.vflag, (void*)L.vcount, (void*)L.gerr})
+                  (void*)L.lpart, (void*)L.idx, (void*)L.cls, (void*)L.vflag, (void*)L.vcount, (void*)L.gerr,
+                  (void*)L.W3p, (void*)L.bp})
     cudaFree(q);
   L = hbpc_ctx::Learned{};
 }
@@ -768,6 +772,7 @@ hbpc_status lp_refresh(hbpc_ctx* x) {
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(H * L.dinp), 256, 0, x->stream>>>(L.P + L.oW1, L.W1h, H * L.dinp));
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(H * H), 256, 0, x->stream>>>(L.P + L.oW2, L.W2h, H * H));
   HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_f32_to_bf16<<<grid_for(size_t(L.doutp) * H), 256, 0, x->stream>>>(L.P + L.oW3, L.W3h, size_t(L.doutp) * H));
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_w3_permute<<<grid_for(size_t(L.doutp) * H), 256, 0, x->stream>>>(L.W3h, L.W3p, L.nb, L.doutp, L.H));
   HBPC_LAUNCH_CK(x, "lp_refresh");
   hbpc_status s;
   if ((s = lp_transpose(x, L.W2h, L.W2T, L.H, L.H)) != HBPC_OK) return s;
@@ -790,9 +795,10 @@ hbpc_status lp_infer(hbpc_ctx* x, const double* W, double c1, double c2) {
   HBPC_CK(x, cudaMemcpyAsync(keys, L.ckey, sizeof(keys), cudaMemcpyDeviceToHost, x->stream));
   if ((s = lp_gemm_check(x)) != HBPC_OK) return s;   // waits for the keys too
   const float* cm = L.cmean + size_t(mlp_class(keys, float(c1), float(c2))) * L.doutp;
+  HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1, k_pc_bias_storage<<<grid_for(L.doutp), 256, 0, x->stream>>>(L.P + L.ob3, cm, 1, L.nb, L.doutp, L.bp));
   if (x->sol.precision == HBPC_PREC_MIXED)
-    return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.P + L.ob3, cm, x->Mf, L.nb});
-  return gemm(x, L.H2i, L.H, L.W3h, L.H, nE, L.dout, L.H, EpiPcBlock<double>{L.P + L.ob3, cm, x->Mpc, L.nb});
+    return gemm(x, L.H2i, L.H, L.W3p, L.H, nE, L.dout, L.H, EpiPcBlock<float>{L.bp, nullptr, L.doutp, x->Mf, L.nb});
+  return gemm(x, L.H2i, L.H, L.W3p, L.H, nE, L.dout, L.H, EpiPcBlock<double>{L.bp, nullptr, L.doutp, x->Mpc, L.nb});
 }
 
 // One forward/backward pass on the batch already in Fb, Jb, cb, Xb: loss and
@@ -3347,9 +3353,13 @@ hbpc_status hbpc_pc_model_forward(hbpc_ctx* ctx, int B, const float* F, const fl
   const int H = L.H;
   if ((s = gemm(ctx, L.Fb, L.dinp, L.W1h, L.dinp, B, H, L.dinp, EpiBiasTanh{L.P + L.ob1, L.H1b, H})) != HBPC_OK) return s;
   if ((s = gemm(ctx, L.H1b, H, L.W2h, H, B, H, H, EpiBiasTanh{L.P + L.ob2, L.H2b, H})) != HBPC_OK) return s;
-  if ((s = gemm(ctx, L.H2b, H, L.W3h, H, B, L.doutp, H, EpiBiasF32{L.P + L.ob3, L.Ob, L.doutp})) != HBPC_OK) return s;
+  // the inference path of the preconditioner build: blocks in storage
+  // (column-major) order with every row's class, then row-major for the caller
   HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_mlp_classify<<<(B + 255) / 256, 256, 0, ctx->stream>>>(L.cb, B, L.ckey, L.cls));
-  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_mlp_mtilde<<<B, 256, 0, ctx->stream>>>(L.Ob, B, L.nb, L.doutp, L.cmean, L.cls, L.Jb));
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_pc_bias_storage<<<grid_for(size_t(kMlpClasses) * L.doutp), 256, 0, ctx->stream>>>(L.P + L.ob3, L.cmean, kMlpClasses, L.nb, L.doutp, L.bp));
+  if ((s = gemm(ctx, L.H2b, H, L.W3p, H, B, L.dout, H, EpiPcBlock<float>{L.bp, L.cls, L.doutp, L.Ob, L.nb})) != HBPC_OK)
+    return s;
+  HBPC_RUN(ctx, HBPC_PHASE_PC_BUILD, 1, k_blocks_to_rowmajor<<<B, 256, 0, ctx->stream>>>(L.Ob, B, L.nb, L.Jb));
   HBPC_LAUNCH_CK(ctx, "pc_model_forward");
   HBPC_CK(ctx, cudaMemcpyAsync(M, L.Jb, size_t(B) * L.dout * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   return lp_gemm_check(ctx);   // waits for the stream

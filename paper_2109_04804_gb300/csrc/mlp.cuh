@@ -59,16 +59,84 @@ struct EpiDtanh {               // out = bf16(acc * (1 - h^2)), h the layer's ac
   }
 };
 // M~ of element m = I + C_k + reshape(acc + b), C_k the mean block inverse
-// (minus I) of the stage class k: entry (r, c) = O[r nb + c], stored
-// column-major per element for the BJ_ext apply.
+// (minus I) of the element's stage class k: network output n = r nb + c is
+// entry (r, c).  The GEMM runs with the rows of W3 permuted (W3p, from
+// k_w3_permute) so that its output column p = c nb + r is already the
+// column-major storage position of entry (r, c) in the element's block, and
+// bias, class mean and identity come pre-permuted (k_pc_bias_storage): the 16
+// accumulator values a thread holds become 16 consecutive floats (doubles) of
+// one block, read and written with 16-byte accesses.
 template <typename S>
 struct EpiPcBlock {
-  const float* b; const float* cm; S* M; int nb;
-  __device__ void operator()(int m, int n, float acc) const {
-    const int r = n / nb, c = n - r * nb;
-    M[size_t(m) * nb * nb + size_t(c) * nb + r] = S(acc + b[n] + cm[n] + (r == c ? 1.f : 0.f));
+  static constexpr bool kStore16 = true;
+  const float* bp;   // per class: bias + class mean + identity in storage order (k_pc_bias_storage)
+  const int* cls;    // class of every row, or null: one class (bp is its row)
+  int doutp; S* M; int nb;
+  __device__ __forceinline__ const float* row_bias(int m) const { return cls ? bp + size_t(cls[m]) * doutp : bp; }
+  __device__ void operator()(int m, int p, float acc) const {
+    M[size_t(m) * nb * nb + p] = S(acc + row_bias(m)[p]);
+  }
+  // columns p0 .. p0 + 15 of row m (those < N), accumulators as raw FP32 bits
+  __device__ void store16(int m, int p0, const uint32_t* acc, int N) const {
+    const float* bb = row_bias(m) + p0;
+    S* dst = M + size_t(m) * nb * nb + p0;
+    if (p0 + 16 <= N && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (reinterpret_cast<uintptr_t>(bb) & 15) == 0) {
+      S v[16];
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(bb + q);
+        v[q] = S(__uint_as_float(acc[q]) + b4.x);
+        v[q + 1] = S(__uint_as_float(acc[q + 1]) + b4.y);
+        v[q + 2] = S(__uint_as_float(acc[q + 2]) + b4.z);
+        v[q + 3] = S(__uint_as_float(acc[q + 3]) + b4.w);
+      }
+      constexpr int per = 16 / sizeof(S);
+#pragma unroll
+      for (int q = 0; q < 16; q += per) *reinterpret_cast<uint4*>(dst + q) = *reinterpret_cast<const uint4*>(v + q);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (p0 + j < N) dst[j] = S(__uint_as_float(acc[j]) + bb[j]);
+    }
   }
 };
+
+// out[k][p] = b[n] + cm[k][n] + (r == c) for the classes k < ncls, p = c nb + r
+// the storage position of entry (r, c), n = r nb + c its network output
+// (rows of doutp floats; padding zero).
+__global__ void k_pc_bias_storage(const float* __restrict__ b, const float* __restrict__ cm, int ncls, int nb,
+                                  int doutp, float* __restrict__ out) {
+  const size_t total = size_t(ncls) * doutp;
+  for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+    const int k = int(t / doutp), p = int(t - size_t(k) * doutp);
+    if (p >= nb * nb) { out[t] = 0.f; continue; }
+    const int c = p / nb, r = p - c * nb, n = r * nb + c;
+    out[t] = b[n] + cm[size_t(k) * doutp + n] + (r == c ? 1.f : 0.f);
+  }
+}
+
+// W3p row p = W3 row n(p), n(p) = (p mod nb) nb + p div nb for p < nb^2 (the
+// storage order of the blocks, see EpiPcBlock); padding rows zero.
+__global__ void k_w3_permute(const __nv_bfloat16* __restrict__ W3, __nv_bfloat16* __restrict__ W3p, int nb,
+                             int doutp, int H) {
+  const size_t total = size_t(doutp) * H;
+  for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+    const int p = int(t / H), k = int(t - size_t(p) * H);
+    if (p >= nb * nb) { W3p[t] = __float2bfloat16(0.f); continue; }
+    const int n = (p % nb) * nb + p / nb;
+    W3p[t] = W3[size_t(n) * H + k];
+  }
+}
+
+// Column-major blocks (the storage order) to row-major ones, B blocks of nb^2.
+__global__ void k_blocks_to_rowmajor(const float* __restrict__ in, int B, int nb, float* __restrict__ out) {
+  const int e = blockIdx.x;
+  if (e >= B) return;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t - i * nb;
+    out[size_t(e) * nb * nb + t] = in[size_t(e) * nb * nb + size_t(j) * nb + i];
+  }
+}
 
 // ---- small kernels ----------------------------------------------------------
 // Features of every element: standardised state and stage coefficients.
@@ -296,20 +364,6 @@ __global__ void k_mlp_collect_target(const T* __restrict__ Mpc, int nE, int nb, 
   const size_t row = size_t((row0 + s) % cap);
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
     Tbuf[row * nb * nb + t] = float(Mpc[size_t(e) * nb * nb + t]);
-}
-
-// M~_b = I + C_k + reshape(O_b) (row-major n_b x n_b) for sample b of stage
-// class k = cls[b]; one block per sample.
-__global__ void k_mlp_mtilde(const float* __restrict__ O, int B, int nb, int doutp, const float* __restrict__ cmean,
-                             const int* __restrict__ cls, float* __restrict__ out) {
-  const int b = blockIdx.x;
-  if (b >= B) return;
-  const float* Ob = O + size_t(b) * doutp;
-  const float* Cb = cmean + size_t(cls[b]) * doutp;
-  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-    const int i = t / nb, j = t - i * nb;
-    out[size_t(b) * nb * nb + t] = (i == j ? 1.f : 0.f) + Cb[t] + Ob[t];
-  }
 }
 
 // Adam (Kingma & Ba 2015) on FP32 parameters.

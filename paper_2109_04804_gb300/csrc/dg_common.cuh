@@ -117,19 +117,36 @@ enum BoundaryKind { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_WALL = 2 };
 // of direction m (Sec. 3.1.1 with an exterior trace): Dirichlet data are
 // constant, so their direction is zero; the wall state is linear in the own
 // trace, so its direction is the mirrored own direction.
+// p.bck[m][side] and p.bcw[m][side][v] read with constant indices (selects),
+// so that a runtime face keeps the parameters out of local memory
+template <typename T>
+__device__ __forceinline__ int bc_kind(const DGParams<T>& p, int m, int side) {
+  int k = side ? p.bck[0][1] : p.bck[0][0];
+  if (m == 1) k = side ? p.bck[1][1] : p.bck[1][0];
+  if (m == 2) k = side ? p.bck[2][1] : p.bck[2][0];
+  return k;
+}
+template <typename T>
+__device__ __forceinline__ T bc_value(const DGParams<T>& p, int m, int side, int v) {
+  T x = side ? p.bcw[0][1][v] : p.bcw[0][0][v];
+  if (m == 1) x = side ? p.bcw[1][1][v] : p.bcw[1][0][v];
+  if (m == 2) x = side ? p.bcw[2][1][v] : p.bcw[2][0][v];
+  return x;
+}
+
 template <int NV, typename V, typename T>
 __device__ __forceinline__ void exterior_state(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
-  if (p.bck[m][side] == BC_WALL) {
+  if (bc_kind(p, m, side) == BC_WALL) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
   } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) ext[v] = V(p.bcw[m][side][v]);
+    for (int v = 0; v < NV; ++v) ext[v] = V(bc_value(p, m, side, v));
   }
 }
 template <int NV, typename V, typename T>
 __device__ __forceinline__ void exterior_dir(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
-  if (p.bck[m][side] == BC_WALL) {
+  if (bc_kind(p, m, side) == BC_WALL) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
   } else {
@@ -244,6 +261,17 @@ struct Burgers {
   }
 };
 
+// a[m] of a short register array for a runtime m (selects over unrolled
+// indices, so the array stays in registers; a constant m folds)
+template <int K, class V>
+__device__ __forceinline__ V pick(const V* a, int m) {
+  V r = a[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k)
+    if (k == m) r = a[k];
+  return r;
+}
+
 // Euler with reference Mach number eps (Eq. 21):
 //   F^m = (rho v_m, rho v_m v + p/eps^2 e_m, v_m (E + p)),
 //   p = (gamma - 1)(E - eps^2/2 rho |v|^2),  c = sqrt(gamma p / rho) / eps.
@@ -276,10 +304,11 @@ struct Euler {
     for (int k = 0; k < DIM; ++k) { v[k] = w[1 + k] * ir; v2 += v[k] * v[k]; }
     const V E = w[DIM + 1];
     const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
-    F[0] = w[1 + m];
+    const V wm = pick<DIM>(w + 1, m), vm = pick<DIM>(v, m);
+    F[0] = wm;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) F[1 + k] = (k == m) ? w[1 + m] * v[k] + pr * p.inv_eps2 : w[1 + m] * v[k];
-    F[DIM + 1] = v[m] * (E + pr);
+    for (int k = 0; k < DIM; ++k) F[1 + k] = (k == m) ? wm * v[k] + pr * p.inv_eps2 : wm * v[k];
+    F[DIM + 1] = vm * (E + pr);
   }
   // (dF^m/dw) s with dp = (gamma-1)(s_E - eps^2 v.s_mom + eps^2/2 |v|^2 s_rho)
   template <class V>
@@ -313,14 +342,15 @@ struct Euler {
     const V E = w[DIM + 1];
     const V pr = p.gm1 * (E - (T(0.5) * p.eps2) * (w[0] * v2));
     const V dp = p.gm1 * (s[DIM + 1] - p.eps2 * vs + (T(0.5) * p.eps2) * (v2 * s[0]));
-    J[0] = s[1 + m];
+    const V sm = pick<DIM>(s + 1, m), vm = pick<DIM>(v, m);
+    J[0] = sm;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      const V t = v[m] * s[1 + k] + v[k] * s[1 + m] - v[m] * (v[k] * s[0]);
+      const V t = vm * s[1 + k] + v[k] * sm - vm * (v[k] * s[0]);
       J[1 + k] = (k == m) ? t + dp * p.inv_eps2 : t;
     }
-    const V dvm = (s[1 + m] - v[m] * s[0]) * ir;
-    J[DIM + 1] = dvm * (E + pr) + v[m] * (s[DIM + 1] + dp);
+    const V dvm = (sm - vm * s[0]) * ir;
+    J[DIM + 1] = dvm * (E + pr) + vm * (s[DIM + 1] + dp);
   }
   __device__ __forceinline__ static T speed(const T* w, int m, const DGParams<T>& p) {
     const T ir = T(1) / w[0];
@@ -328,7 +358,7 @@ struct Euler {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { const T vk = w[1 + k] * ir; v2 += vk * vk; }
     const T pr = p.gm1 * (w[DIM + 1] - T(0.5) * p.eps2 * w[0] * v2);
-    return fabs(w[1 + m] * ir) + sqrt(p.gamma * pr * ir) * p.inv_eps;
+    return fabs(pick<DIM>(w + 1, m) * ir) + sqrt(p.gamma * pr * ir) * p.inv_eps;
   }
 };
 

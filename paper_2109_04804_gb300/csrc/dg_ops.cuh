@@ -94,20 +94,30 @@ struct FaceFlux {
   using T = typename BaseOf<V>::type;
   using L = typename LawOf<LAW, DIM, T>::type;
   static constexpr int NV = L::NV, NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
+  // Face M (direction) / SIDE of the element: compile-time constants where
+  // the caller dispatches on the face (one inlined copy per face), runtime
+  // values where one copy serves every face (the large Navier-Stokes kernels,
+  // whose instruction footprint otherwise stalls issue).
   template <int M, int SIDE>
   __device__ __forceinline__ static void run(const Job& job, const DGParams<T>& prm, const InstGeo<T>& g,
                                              int k, bool r2, const int* ec, int pt, const V* sst,
                                              const V* sdir, V* sface) {
-    constexpr int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
+    run_face(M, SIDE, job, prm, g, k, r2, ec, pt, sst, sdir, sface);
+  }
+  __device__ __forceinline__ static void run_face(const int M, const int SIDE, const Job& job,
+                                                  const DGParams<T>& prm, const InstGeo<T>& g, int k, bool r2,
+                                                  const int* ec, int pt, const V* sst, const V* sdir, V* sface) {
+    const int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;   // face point -> node with idx_M = 0
     // neighbour element across this face (periodic within the instance), or
     // a boundary face of a non-periodic direction
-    int nc0 = ec[0], nc1 = ec[1], nc2 = ec[2];
-    int& c = (M == 0) ? nc0 : (M == 1 ? nc1 : nc2);
+    const int gnM = M == 0 ? g.n[0] : (M == 1 ? g.n[1] : g.n[2]);
+    int c = M == 0 ? ec[0] : (M == 1 ? ec[1] : ec[2]);
     c += SIDE ? 1 : -1;
-    const bool bnd = (c < 0 || c >= g.n[M]) && prm.bck[M][SIDE] != BC_PERIODIC;
-    if (c < 0) c += g.n[M];
-    if (c >= g.n[M]) c -= g.n[M];
+    const bool bnd = (c < 0 || c >= gnM) && bc_kind(prm, M, SIDE) != BC_PERIODIC;
+    if (c < 0) c += gnM;
+    if (c >= gnM) c -= gnM;
+    const int nc0 = M == 0 ? c : ec[0], nc1 = M == 1 ? c : ec[1], nc2 = M == 2 ? c : ec[2];
     const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
     V wo[NV], wn[NV], so[NV], sn[NV];
 #pragma unroll
@@ -172,7 +182,7 @@ struct FaceFlux {
       for (int v = 0; v < NV; ++v) kap[v] = cmax;
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) kap[v] = prm.lam[M][v];
+      for (int v = 0; v < NV; ++v) kap[v] = M == 0 ? prm.lam[0][v] : (M == 1 ? prm.lam[1][v] : prm.lam[2][v]);
     }
     if (r2) { L::jvp(wL, sL, M, FL, prm); L::jvp(wR, sR, M, FR, prm); }
     else { L::flux(wL, M, FL, prm); L::flux(wR, M, FR, prm); }
@@ -520,7 +530,9 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
       V* const sfd = sfn + 2 * DIM * NCH * NF;
       {
         using FF = FaceFlux<LAW, DIM, P, LGL, V, Job>;
-        switch (f) {
+        if constexpr (NSV) {
+          FF::run_face(f >> 1, f & 1, job, prm, geo, k, r2, ec, pt, sst, sdir, sface);
+        } else switch (f) {
           case 0: FF::template run<0, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
           case 1: FF::template run<0, 1>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;
           case 2: if constexpr (DIM > 1) FF::template run<1, 0>(job, prm, geo, k, r2, ec, pt, sst, sdir, sface); break;

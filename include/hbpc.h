@@ -276,6 +276,15 @@ typedef enum { HBPC_BC_PERIODIC = 0, HBPC_BC_DIRICHLET = 1, HBPC_BC_WALL = 2 } h
 hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double* state_lo, int kind_hi,
                               const double* state_hi);
 
+/* When the block preconditioner is built: every_newton_iteration = 1 (the
+ * default) rebuilds it before every Newton iteration, as in the paper's study
+ * (Sec. 4.1.2); 0 builds it once per Newton solve, at the solve's first
+ * iterate X^0, and reuses it for the later iterations (the reuse the paper
+ * suggests at the end of Sec. 4.1.2: fewer builds, possibly more GMRES
+ * iterations; Newton still stops on the same residual).  Other values:
+ * HBPC_ERR_INVALID_ARG.  The batch form sets every group. */
+hbpc_status hbpc_set_pc_rebuild(hbpc_ctx* ctx, int every_newton_iteration);
+
 /* Device-driven steps (Algorithm 1 with the Newton iteration of Eq. 17 and
  * restarted GMRES; no counterpart in the paper's host-driven solver).  With
  * on = 1 every hbpc_step / hbpc_advance_to step is ONE CUDA graph launch: the
@@ -508,6 +517,8 @@ hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r);
 hbpc_status hbpc_batch_step(hbpc_batch* b, int n_steps);
 /* hbpc_set_step_graph for every group: each group's step is one graph launch. */
 hbpc_status hbpc_batch_set_step_graph(hbpc_batch* b, int on);
+/* hbpc_set_pc_rebuild for every group. */
+hbpc_status hbpc_batch_set_pc_rebuild(hbpc_batch* b, int every_newton_iteration);
 /* Counters summed over groups (steps, t: the maximum). */
 hbpc_status hbpc_batch_get_stats(const hbpc_batch* b, hbpc_stats* out);
 hbpc_status hbpc_batch_profile_enable(hbpc_batch* b, int enable);

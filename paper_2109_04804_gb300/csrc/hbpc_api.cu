@@ -267,6 +267,10 @@ struct hbpc_ctx {
   int pc_grid = 0, pc_threads = 0;
   size_t pc_smem = 0;
   bool pc_built = false;
+  // 1: the block preconditioner is rebuilt before every Newton iteration (the
+  // setting of the paper's study, Sec. 4.1.2); 0: once per Newton solve, at
+  // its first iterate (the reuse the paper suggests, end of Sec. 4.1.2)
+  int pc_every = 1;
   // BJ_ext with one block for all elements: linear advection (with or without
   // a viscous term) on one uniform mesh has the same J_i in every element and
   // for every state, so one J, one S^-1 serve the whole mesh
@@ -1562,7 +1566,7 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
   for (int r = 0; r < x->sol.newton_max_iter; ++r) {
     int its = 0;
     bool conv = false;
-    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    if (x->sol.pc != HBPC_PC_NONE && (x->pc_every || r == 0) && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
     if (x->schur) {
       if ((s = gmres_schur(x, &its, &conv)) != HBPC_OK) return s;
       if ((s = schur_sigma(x)) != HBPC_OK) return s;
@@ -1646,7 +1650,7 @@ hbpc_status newton_batch(hbpc_ctx* x, const double* b, double a1, double a2, con
     if ((s = norms(x, x->G, size_t(2 * n))) != HBPC_OK) return s;   // of the scaled right-hand side
     int its = 0;
     bool conv = false;
-    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    if (x->sol.pc != HBPC_PC_NONE && (x->pc_every || r == 0) && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
     if (x->sol.precision == HBPC_PREC_MIXED) {
       if ((s = to_float(x, x->X, x->Wf, size_t(2 * n))) != HBPC_OK) return s;
       if ((s = (x->bk ? gmres_bf(x, &its, &conv) : gmres_f(x, &its, &conv))) != HBPC_OK) return s;
@@ -1921,6 +1925,8 @@ hbpc_status newton_graph(hbpc_ctx* x, const double* b, double a1, double a2, con
     HBPC_RUN(x, HBPC_PHASE_VECTOR, 1, k_sg_newton_begin<<<1, 32, 0, x->stream>>>(x->st, x->sg.ctl, h_newton, 0));
   }
   HBPC_LAUNCH_CK(x, "newton graph start");
+  // blocks built once per solve, at X^0 (skipped work if the loop does not run)
+  if (!x->pc_every && x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
   const long long r1_0 = x->stats.r1_evals, r2_0 = x->stats.r2_evals;
   B.open(h_newton, cudaGraphCondTypeWhile);
   {
@@ -1928,7 +1934,7 @@ hbpc_status newton_graph(hbpc_ctx* x, const double* b, double a1, double a2, con
       if ((s = inst_scale<double>(x, x->G, nullptr, 0, nullptr)) != HBPC_OK) return s;
       if ((s = norms(x, x->G, n2)) != HBPC_OK) return s;   // of the scaled right-hand side
     }
-    if (x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
+    if (x->pc_every && x->sol.pc != HBPC_PC_NONE && (s = pc_build(x, x->X, c1, c2)) != HBPC_OK) return s;
     int kind = GM_FP64;
     if (x->sol.precision == HBPC_PREC_MIXED) {
       if ((s = to_float(x, x->X, x->Wf, n2)) != HBPC_OK) return s;
@@ -1971,7 +1977,7 @@ std::vector<unsigned char> step_graph_key(const hbpc_ctx* x) {
   put(&x->prmf, sizeof(x->prmf));
   const long long v[] = {x->nblocks, x->pc_threads, x->pc_grid, (long long)x->pc_smem, x->bk_grid, x->coop ? 1 : 0,
                          x->pc_shared ? 1 : 0, (long long)(uintptr_t)x->Jpc, (long long)(uintptr_t)x->Mpc,
-                         (long long)(uintptr_t)x->Jf, (long long)(uintptr_t)x->Mf, x->s};
+                         (long long)(uintptr_t)x->Jf, (long long)(uintptr_t)x->Mf, x->s, x->pc_every};
   put(v, sizeof(v));
   return k;
 }
@@ -2969,6 +2975,13 @@ hbpc_status hbpc_set_step_graph(hbpc_ctx* ctx, int on) {
   return HBPC_OK;
 }
 
+hbpc_status hbpc_set_pc_rebuild(hbpc_ctx* ctx, int every_newton_iteration) {
+  if (!ctx || (every_newton_iteration != 0 && every_newton_iteration != 1)) return HBPC_ERR_INVALID_ARG;
+  ctx->pc_every = every_newton_iteration;
+  if (ctx->cb) ctx->cb->pc_every = every_newton_iteration;
+  return HBPC_OK;
+}
+
 hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return HBPC_ERR_INVALID_ARG;
   if (!on) { ctx->schur = false; return HBPC_OK; }
@@ -3085,6 +3098,7 @@ hbpc_status hbpc_set_corrector_batch(hbpc_ctx* ctx, int on) {
   g->stream = ctx->stream;
   g->wait_limit_s = ctx->wait_limit_s;
   copy_boundaries(ctx, g);
+  g->pc_every = ctx->pc_every;
   ctx->cb = g;
   return HBPC_OK;
 }
@@ -3718,6 +3732,12 @@ hbpc_status hbpc_batch_eval_R1(hbpc_batch* b, int inst, double* r) {
   HBPC_LAUNCH_CK(x, "batch eval_R1");
   HBPC_CK(x, cudaMemcpyAsync(r, x->r1 + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, x->stream));
   return sync(x, "batch eval_R1");
+}
+
+hbpc_status hbpc_batch_set_pc_rebuild(hbpc_batch* b, int every_newton_iteration) {
+  if (!b || (every_newton_iteration != 0 && every_newton_iteration != 1)) return HBPC_ERR_INVALID_ARG;
+  for (hbpc_ctx* x : b->g) x->pc_every = every_newton_iteration;
+  return HBPC_OK;
 }
 
 hbpc_status hbpc_batch_set_step_graph(hbpc_batch* b, int on) {

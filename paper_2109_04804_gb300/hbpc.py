@@ -99,6 +99,7 @@ _SIGS = {
     "hbpc_set_schur": (_I, [_CTX, _I]),
     "hbpc_set_boundary": (_I, [_CTX, _I, _I, _P, _I, _P]),
     "hbpc_set_step_graph": (_I, [_CTX, _I]),
+    "hbpc_set_pc_rebuild": (_I, [_CTX, _I]),
     "hbpc_eval_R1": (_I, [_CTX, _P, _P]),
     "hbpc_eval_R2": (_I, [_CTX, _P, _P, _P]),
     "hbpc_eval_G": (_I, [_CTX, _P, _D, _D, _P, _P]),
@@ -133,6 +134,7 @@ _SIGS = {
     "hbpc_batch_eval_R1": (_I, [_CTX, _I, _P]),
     "hbpc_batch_step": (_I, [_CTX, _I]),
     "hbpc_batch_set_step_graph": (_I, [_CTX, _I]),
+    "hbpc_batch_set_pc_rebuild": (_I, [_CTX, _I]),
     "hbpc_batch_get_stats": (_I, [_CTX, ctypes.POINTER(Stats)]),
     "hbpc_batch_profile_enable": (_I, [_CTX, _I]),
     "hbpc_batch_last_error": (ctypes.c_char_p, [_CTX]),
@@ -318,6 +320,11 @@ class Context:
     def set_step_graph(self, on=True):
         """Every step as one CUDA graph launch (device-driven Newton and GMRES)."""
         self._c(_lib.hbpc_set_step_graph(self._ctx, 1 if on else 0))
+
+    def set_pc_rebuild(self, every_newton_iteration=True):
+        """Rebuild the block preconditioner before every Newton iteration (True)
+        or once per Newton solve (False)."""
+        self._c(_lib.hbpc_set_pc_rebuild(self._ctx, 1 if every_newton_iteration else 0))
 
     def set_corrector_batch(self, on=True):
         """Solve the s - 1 corrector stages of every sweep as one batched Newton."""
@@ -518,6 +525,9 @@ class Batch:
     def set_step_graph(self, on=True):
         """Every group's step as one CUDA graph launch."""
         self._c(_lib.hbpc_batch_set_step_graph(self._b, 1 if on else 0))
+
+    def set_pc_rebuild(self, every_newton_iteration=True):
+        self._c(_lib.hbpc_batch_set_pc_rebuild(self._b, 1 if every_newton_iteration else 0))
 
     def stats(self):
         s = Stats()

@@ -169,3 +169,30 @@ def test_step_graph_argument_checks(hb):
         c.set_step_graph(True)
     assert ei.value.status == hb.ERR_UNSUPPORTED
     c.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_preconditioner_built_once_per_solve(hb, graph):
+    """hbpc_set_pc_rebuild(0): the blocks are built at every Newton solve's first
+    iterate only; the answer is that of the rebuild-every-iteration run to the
+    Newton tolerance, and the graph form equals the host-driven one."""
+    make, init = CASES["euler_fp64_bjext"](hb)
+
+    def go(every, g):
+        c = make()
+        c.set_pc_rebuild(every)
+        if g:
+            c.set_step_graph(True)
+        c.set_state(init(c))
+        c.step(2)
+        w = c.get_state()
+        s = c.stats()
+        c.close()
+        return w, s
+    w_every, _ = go(True, False)
+    w_once, s_once = go(False, graph)
+    assert np.linalg.norm(w_once - w_every) <= 1e-10 * np.linalg.norm(w_every)
+    if graph:
+        w_host, s_host = go(False, False)
+        assert np.array_equal(w_once, w_host)
+        assert s_once["gmres_its"] == s_host["gmres_its"]

@@ -166,8 +166,8 @@ def operator(disc, w, sigma=None, mode="R1", frozen_neighbor=False, frozen_neigh
     if frozen_neighbor_state and (mode != "R2" or disc.ph.law == laws.NAVIER_STOKES):
         raise ValueError("frozen_neighbor_state: R2 of an inviscid or scalar viscous law only")
     ph, b = disc.ph, disc.basis
-    if not disc.mesh.periodic and (ph.nu != 0.0 or ph.law == laws.NAVIER_STOKES):
-        raise ValueError("boundary conditions: inviscid laws only")
+    if not disc.mesh.periodic and ph.nu != 0.0:
+        raise ValueError("boundary conditions: not for the scalar viscous term")
     W = disc.to_grid(w)
     S = disc.to_grid(sigma) if sigma is not None else None
     out = np.zeros(W.shape, dtype=np.result_type(W, S) if S is not None else W.dtype)
@@ -297,7 +297,37 @@ def viscous(disc, u, frozen_neighbor=False):
     return disc.from_grid(out)
 
 
-def br2_faces(disc, U, m, frozen_neighbor=False):
+def ns_channel_ghost(disc, spec, own_val, own_grads, m, linear):
+    """The values and the broken gradient of the gradient channels (v, T) of
+    Eq. 26 outside a boundary face of direction m, from the element's own
+    traces there (own_grads[k]: the own d/dx_k traced on the face).  The
+    exterior gradient is the own one, except that an adiabatic wall reverses
+    the normal derivative of T:
+      ("noslip",): adiabatic no-slip wall: the velocity reversed (u* = 0), T
+          kept; the velocity gradient kept, so that the central viscous flux
+          takes the wall shear stress of the own side and does no work at the
+          wall, and dT/dn reversed, so that no heat crosses it;
+      ("dirichlet", state): the channels of the given state (zero for the
+          linearised channels, linear=True), the own gradient."""
+    d = disc.d
+    shp = (d + 1,) + (1,) * (own_val.ndim - 1)
+    if spec[0] == "noslip":
+        s_val = np.array([-1.0] * d + [1.0]).reshape(shp)
+        s_nrm = np.array([1.0] * d + [-1.0]).reshape(shp)
+        val = s_val * own_val
+        grads = [s_nrm * gk if k == m else gk for k, gk in enumerate(own_grads)]
+        return val, grads
+    if spec[0] == "dirichlet":
+        if linear:
+            val = np.zeros_like(own_val)
+        else:
+            st = np.asarray(spec[1], dtype=np.float64).reshape((disc.nv,) + (1,) * (own_val.ndim - 1))
+            val = np.broadcast_to(laws.ns_grad_vars(st, disc.ph), own_val.shape).astype(own_val.dtype)
+        return val, list(own_grads)
+    raise ValueError(spec)
+
+
+def br2_faces(disc, U, m, frozen_neighbor=False, linear=False):
     """BR2 face quantities of a grid array of channels U (channels on axis 0)
     along direction m, for systems (Sec. 5.1.1): the broken gradient of every
     channel (all d components, tangential ones included, as the viscous flux
@@ -306,6 +336,8 @@ def br2_faces(disc, U, m, frozen_neighbor=False):
     the face-local lifting that adds eta c_pm (2/h_m)(u* - u_own) to the normal
     component (the same lifting as ``br2_traces``).
     frozen_neighbor: the neighbours' channel values are taken as zero.
+    On a bounded direction the first and last elements see the exterior
+    channels of ``ns_channel_ghost`` (linear: U holds linearised channels).
     Returns dict with, for the + face ('p') and the - face ('m') of every
     element, the left and right traces gL, gR (channels) and gradients dL, dR
     (lists over the direction k of channel arrays) and u*."""
@@ -328,6 +360,21 @@ def br2_faces(disc, U, m, frozen_neighbor=False):
     else:
         nb_m, nb_gm = np.roll(um, -1, axis=ea), [np.roll(x, -1, axis=ea) for x in gm]
         nb_p, nb_gp = np.roll(up, 1, axis=ea), [np.roll(x, 1, axis=ea) for x in gp]
+    bc = disc.mesh.bc[m]
+    if bc is not None:
+        dt = np.result_type(up, nb_m)
+        nb_m, nb_p = nb_m.astype(dt, copy=True), nb_p.astype(dt, copy=True)
+        nb_gm = [x.astype(dt, copy=True) for x in nb_gm]
+        nb_gp = [x.astype(dt, copy=True) for x in nb_gp]
+        e_hi, e_lo = _end(up.ndim, ea, True), _end(up.ndim, ea, False)
+        v, gs = ns_channel_ghost(disc, bc[1], up[e_hi], [x[e_hi] for x in gp], m, linear)
+        nb_m[e_hi] = v
+        for k in range(disc.d):
+            nb_gm[k][e_hi] = gs[k]
+        v, gs = ns_channel_ghost(disc, bc[0], um[e_lo], [x[e_lo] for x in gm], m, linear)
+        nb_p[e_lo] = v
+        for k in range(disc.d):
+            nb_gp[k][e_lo] = gs[k]
     # + face: left = own, right = neighbour
     us_p = 0.5 * (up + nb_m)
     dL_p = list(gp)
@@ -380,7 +427,7 @@ def viscous_ns(disc, w, sigma=None, frozen_neighbor=False):
     if sigma is not None:
         S = disc.to_grid(sigma)
         gs = laws.ns_grad_vars_jvp(W, S, ph)
-        fs = [br2_faces(disc, gs, m, frozen_neighbor) for m in range(disc.d)]
+        fs = [br2_faces(disc, gs, m, frozen_neighbor, linear=True) for m in range(disc.d)]
         ds = br2_lifted_gradient(disc, gs, fs)
     out = np.zeros(W.shape, dtype=np.result_type(W, sigma) if sigma is not None else W.dtype)
     for m in range(disc.d):

@@ -171,7 +171,9 @@ def exterior_state(w_own, spec, m, ph):
     m, from the element's own trace w_own (variables on axis 0):
       ("dirichlet", state): the given constant state;
       ("wall",): the Euler slip wall, the own state with its momentum along m
-                 reversed (zero normal velocity at the face)."""
+                 reversed (zero normal velocity at the face);
+      ("noslip",): the Navier-Stokes no-slip adiabatic wall, the own state
+                 with its whole momentum reversed (zero velocity at the face)."""
     if spec[0] == "dirichlet":
         st = np.asarray(spec[1], dtype=np.float64).reshape((ph.nv,) + (1,) * (w_own.ndim - 1))
         return np.broadcast_to(st, w_own.shape).astype(np.result_type(w_own, st))
@@ -181,13 +183,20 @@ def exterior_state(w_own, spec, m, ph):
         out = np.array(w_own, copy=True)
         out[1 + m] = -out[1 + m]
         return out
+    if spec[0] == "noslip":
+        if ph.law != NAVIER_STOKES:
+            raise ValueError("a no-slip wall needs the Navier-Stokes equations")
+        out = np.array(w_own, copy=True)
+        for k in range(ph.dim):
+            out[1 + k] = -out[1 + k]
+        return out
     raise ValueError(spec)
 
 
 def exterior_direction(s_own, spec, m, ph):
     """The direction sigma outside a boundary face: the time derivative of the
     exterior state, so zero for constant Dirichlet data and the mirrored own
-    sigma at a slip wall (the exterior state is linear in the own state)."""
+    sigma at a wall (the exterior state is linear in the own state)."""
     if spec[0] == "dirichlet":
         return np.zeros_like(s_own)
     return exterior_state(s_own, spec, m, ph)

@@ -187,3 +187,68 @@ def test_linear_jv_is_the_derivative_of_G_with_dirichlet_data():
     ref = np.imag(sysm.residual(X + 1j * h * dX)[0]) / h
     out = sysm.jv(X, r1, r2, dX, "linear")
     assert np.linalg.norm(out - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+# ---- Navier-Stokes: adiabatic no-slip walls and Dirichlet states ---------------
+
+def ns_disc(bc, fam=LOBATTO, flux="lf", n=(3, 3), N=2):
+    ph = laws.Physics(laws.NAVIER_STOKES, 2, flux=flux, mu=0.05, eps=1.0)
+    return dgsem.Disc(dgsem.Mesh(2, n, (0, 0), (1, 1), bc=bc), N, ph, fam)
+
+
+NOSLIP = ("noslip",)
+
+
+def lid_state():
+    from paper_2109_04804_gb300 import inputs
+    return inputs.euler_from_primitive(np.array([1.0]), [np.array([0.4]), np.array([0.0])], np.array([1.0]))[0]
+
+
+@pytest.mark.parametrize("fam", [LOBATTO, GAUSS])
+def test_ns_r2_is_the_derivative_of_r1_at_walls(fam):
+    """Global LF: R2 (with the linearised ghost channels) equals the complex-step
+    derivative of R1 with walls and a lid."""
+    disc = ns_disc([(NOSLIP, NOSLIP), (NOSLIP, ("dirichlet", lid_state()))], fam)
+    w = random_gas(disc, 91)
+    s = np.random.default_rng(92).standard_normal(disc.shape)
+    h = 1e-30
+    ref = np.imag(dgsem.R1(disc, w + 1j * h * s)) / h
+    r2 = dgsem.R2(disc, w, s)
+    assert np.abs(r2 - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("fam", [LOBATTO, GAUSS])
+@pytest.mark.parametrize("flux", ["lf", "rusanov"])
+def test_ns_noslip_box_conserves_mass_and_energy(fam, flux):
+    """Walls pass no mass (reversed momentum, equal density) and no energy (no
+    work at zero wall velocity, no heat through an adiabatic wall): the
+    totals of R1's density and energy rows vanish."""
+    disc = ns_disc([(NOSLIP, NOSLIP), (NOSLIP, NOSLIP)], fam, flux, n=(4, 3), N=3)
+    w = random_gas(disc, 93)
+    rate = dgsem.cell_integral(disc, dgsem.R1(disc, w))
+    scale = np.abs(dgsem.R1(disc, w)).max()
+    assert abs(rate[0]) <= 1e-13 * scale and abs(rate[3]) <= 1e-13 * scale
+    assert abs(rate[1]) > 1e-8 * scale          # the walls do push on the gas
+
+
+@pytest.mark.parametrize("fam", [LOBATTO, GAUSS])
+def test_ns_gas_at_rest_and_dirichlet_free_stream(fam):
+    from paper_2109_04804_gb300 import inputs
+    disc = ns_disc([(NOSLIP, NOSLIP), (NOSLIP, NOSLIP)], fam, "rusanov", N=3)
+    X = disc.node_coords()
+    w = inputs.euler_from_primitive(np.full_like(X[0], 1.2), [0 * X[0], 0 * X[0]], np.full_like(X[0], 0.9))
+    assert np.abs(dgsem.R1(disc, w)).max() <= 1e-12
+    st = lid_state()
+    d2 = ns_disc([(("dirichlet", st), ("dirichlet", st)), (("dirichlet", st), ("dirichlet", st))], fam, "rusanov")
+    w2 = np.broadcast_to(st.reshape(1, 4, 1, 1), d2.shape).copy()
+    assert np.abs(dgsem.R1(d2, w2)).max() <= 1e-12
+
+
+def test_ns_element_blocks_at_walls():
+    """The frozen-neighbour element blocks J_i (global LF) are the diagonal
+    blocks of the full complex-step dR1/dW, wall and lid elements included."""
+    disc = ns_disc([(NOSLIP, NOSLIP), (NOSLIP, ("dirichlet", lid_state()))], LOBATTO, "lf", n=(3, 2))
+    w = random_gas(disc, 94)
+    J = newton.element_jacobians(disc, w)
+    Jd = diag_blocks(dense_derivative(disc, lambda x: dgsem.operator(disc, x, mode="R1"), w), disc.mesh.nE)
+    assert np.abs(J - Jd).max() <= 1e-11 * np.abs(Jd).max()

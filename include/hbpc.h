@@ -20,7 +20,8 @@
  *  - Meshes are uniform and Cartesian.  A context is created periodic in
  *    every direction (hbpc_mesh.periodic must be 1); hbpc_set_boundary then
  *    replaces the periodic connection of a direction by two boundaries
- *    (constant Dirichlet states or Euler slip walls, inviscid laws).
+ *    (constant Dirichlet states, Euler slip walls, Navier-Stokes no-slip
+ *    walls).
  *  - Invalid arguments are rejected before anything is allocated or launched.
  */
 #ifndef HBPC_H
@@ -262,17 +263,27 @@ hbpc_status hbpc_set_schur(hbpc_ctx* ctx, int on);
  *                      doubles (conservative variables; Euler: density and
  *                      pressure > 0), copied;
  *   HBPC_BC_WALL       the slip wall of the Euler equations: the exterior state
- *                      is the own trace with the momentum along dir reversed.
+ *                      is the own trace with the momentum along dir reversed;
+ *   HBPC_BC_NOSLIP     the adiabatic no-slip wall of the Navier-Stokes
+ *                      equations: the exterior state is the own trace with its
+ *                      whole momentum reversed; the BR2 lifting (Sec. 5.1.1)
+ *                      sees exterior channels (v, T) = (-v, T) and the own
+ *                      gradient with dT/dn reversed, so the wall velocity is
+ *                      zero, the wall takes the own shear stress, does no work
+ *                      and passes no heat.  A Dirichlet state gives the
+ *                      Navier-Stokes lifting the state's (v, T) and the own
+ *                      gradient.
  * A boundary face takes the numerical flux of Eq. 13 (or f~* of Sec. 3.1.2 for
  * R2) with that exterior state; the exterior direction of R2 is its time
  * derivative (zero for Dirichlet data, the mirrored own sigma at a wall), so
  * R2 stays the derivative of R1 and every Jacobian-vector product, the BJ_ext
- * and BJ^H_ext blocks and the mixed mode include the boundaries.  Inviscid
- * laws only (nu = 0, not Navier-Stokes: HBPC_ERR_UNSUPPORTED); a wall needs
- * the Euler equations; mixed periodic/bounded ends, an unknown kind or a bad
- * state are HBPC_ERR_INVALID_ARG; nothing changes on an error.  Applies to the
+ * and BJ^H_ext blocks and the mixed mode include the boundaries.  Not for the
+ * scalar viscous term (nu > 0 with advection or Burgers: HBPC_ERR_UNSUPPORTED);
+ * a slip wall needs the Euler equations, a no-slip wall Navier-Stokes; mixed
+ * periodic/bounded ends, an unknown kind or a bad state are
+ * HBPC_ERR_INVALID_ARG; nothing changes on an error.  Applies to the
  * following calls (the preconditioner is rebuilt). */
-typedef enum { HBPC_BC_PERIODIC = 0, HBPC_BC_DIRICHLET = 1, HBPC_BC_WALL = 2 } hbpc_bc;
+typedef enum { HBPC_BC_PERIODIC = 0, HBPC_BC_DIRICHLET = 1, HBPC_BC_WALL = 2, HBPC_BC_NOSLIP = 3 } hbpc_bc;
 hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double* state_lo, int kind_hi,
                               const double* state_hi);
 

@@ -103,15 +103,16 @@ struct DGParams {
   // per block of the operator kernel, the instance it belongs to
   const InstGeo<T>* inst;
   const int* blk_inst;
-  // boundaries of a non-periodic direction m (single problems, inviscid laws):
-  // bck[m][side] (side 0 = lower, 1 = upper end) is BC_PERIODIC, BC_DIRICHLET
-  // (exterior state bcw[m][side], constant in time) or BC_WALL (Euler slip
-  // wall: the own trace with its momentum along m reversed)
+  // boundaries of a non-periodic direction m (single problems): bck[m][side]
+  // (side 0 = lower, 1 = upper end) is BC_PERIODIC, BC_DIRICHLET (exterior
+  // state bcw[m][side], constant in time), BC_WALL (Euler slip wall: the own
+  // trace with its momentum along m reversed) or BC_NOSLIP (Navier-Stokes
+  // adiabatic no-slip wall: the own trace with its whole momentum reversed)
   int bck[3][2];
   T bcw[3][2][5];
 };
 
-enum BoundaryKind { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_WALL = 2 };
+enum BoundaryKind { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_WALL = 2, BC_NOSLIP = 3 };
 
 // The state and the direction the numerical flux sees outside a boundary face
 // of direction m (Sec. 3.1.1 with an exterior trace): Dirichlet data are
@@ -136,9 +137,13 @@ __device__ __forceinline__ T bc_value(const DGParams<T>& p, int m, int side, int
 
 template <int NV, typename V, typename T>
 __device__ __forceinline__ void exterior_state(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
-  if (bc_kind(p, m, side) == BC_WALL) {
+  const int kind = bc_kind(p, m, side);
+  if (kind == BC_WALL) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
+  } else if (kind == BC_NOSLIP) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = (v >= 1 && v < NV - 1) ? -own[v] : own[v];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = V(bc_value(p, m, side, v));
@@ -146,9 +151,13 @@ __device__ __forceinline__ void exterior_state(const DGParams<T>& p, int m, int 
 }
 template <int NV, typename V, typename T>
 __device__ __forceinline__ void exterior_dir(const DGParams<T>& p, int m, int side, const V* own, V* ext) {
-  if (bc_kind(p, m, side) == BC_WALL) {
+  const int kind = bc_kind(p, m, side);
+  if (kind == BC_WALL) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = (v == 1 + m) ? -own[v] : own[v];
+  } else if (kind == BC_NOSLIP) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = (v >= 1 && v < NV - 1) ? -own[v] : own[v];
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) ext[v] = V(T(0));

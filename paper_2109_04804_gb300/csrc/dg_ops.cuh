@@ -271,6 +271,50 @@ struct FaceViscSysA {
     const int M = f >> 1, side = f & 1;
     const int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;
+    const int nch = r2 ? NCH : NG;
+    // a boundary face: the exterior channels from the own ones (adiabatic
+    // no-slip wall: the velocity reversed, T kept, the own normal derivative
+    // with dT/dn reversed; Dirichlet: the state's channels, zero for the
+    // linearised ones, the own normal derivative); the exterior's tangential
+    // derivatives are the own ones (stage B)
+    {
+      const int ecM = M == 0 ? ec[0] : (M == 1 ? ec[1] : ec[2]);
+      const int gnM = M == 0 ? g.n[0] : (M == 1 ? g.n[1] : g.n[2]);
+      const int kind = bc_kind(prm, M, side);
+      if (kind != BC_PERIODIC && (side ? ecM == gnM - 1 : ecM == 0)) {
+        V gbc[NG];
+        if (kind == BC_DIRICHLET) {
+          V sb[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) sb[v] = V(bc_value(prm, M, side, v));
+          NS::grad_vars(sb, gbc, prm);
+        }
+        const T* gown = (side ? sgp : sgm) + M * P;   // shared-memory table
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+          if (q >= nch) continue;
+          const int cq = q % NG;
+          V uo = V(T(0)), go = V(T(0));
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            uo += (side ? prm.lp[i] : prm.lm[i]) * sgc[q * NN + base + i * st];
+            go += gown[i] * sgc[q * NN + base + i * st];
+          }
+          V ux, gx;
+          if (kind == BC_DIRICHLET) {
+            ux = q < NG ? gbc[cq] : V(T(0));
+            gx = go;
+          } else {
+            ux = cq < DIM ? -uo : uo;
+            gx = cq == DIM ? -go : go;
+          }
+          sfo[(f * NCH + q) * NF + pt] = uo;
+          sfn[(f * NCH + q) * NF + pt] = ux;
+          sfd[(f * NCH + q) * NF + pt] = gx;
+        }
+        return;
+      }
+    }
     // neighbour element across this face (periodic within the instance)
     const int dlt = side ? 1 : -1;
     int nc0 = ec[0] + (M == 0 ? dlt : 0), nc1 = ec[1] + (M == 1 ? dlt : 0), nc2 = ec[2] + (M == 2 ? dlt : 0);
@@ -278,7 +322,6 @@ struct FaceViscSysA {
     nc1 = nc1 < 0 ? nc1 + g.n[1] : (nc1 >= g.n[1] ? nc1 - g.n[1] : nc1);
     nc2 = nc2 < 0 ? nc2 + g.n[2] : (nc2 >= g.n[2] ? nc2 - g.n[2] : nc2);
     const int en = g.e0 + nc0 + g.n[0] * (nc1 + g.n[1] * nc2);
-    const int nch = r2 ? NCH : NG;
     const T* dnb = (side ? sgm : sgp) + M * P;             // neighbour's normal-derivative weights
     V un[NCH], gn[NCH];
 #pragma unroll
@@ -327,9 +370,11 @@ struct FaceViscSysB {
   using NS = NSVisc<DIM, T>;
   static constexpr int NV = DIM + 2, NG = DIM + 1, NCH = 2 * NG;
   static constexpr int NN = Geo<DIM, P>::NN, NF = Geo<DIM, P>::NF;
+  // bnd: a boundary face, whose exterior side takes the own tangential
+  // derivatives (stage A's exterior gradient)
   __device__ __forceinline__ static void run(const DGParams<T>& prm, const InstGeo<T>& g, bool r2, int f, int pt,
                                              const V* sgc, const T* sDg, const T* sgp, const T* sgm, const V* sfo,
-                                             const V* sfn, const V* sfd, V* sface) {
+                                             const V* sfn, const V* sfd, V* sface, bool bnd) {
     const int M = f >> 1, side = f & 1;
     const int st = (M == 0) ? 1 : (M == 1 ? P : P * P);
     const int base = (pt % st) + (pt / st) * st * P;
@@ -380,7 +425,7 @@ struct FaceViscSysB {
             b += Drow[j] * fn[p0 + j * tstride];
           }
           dO[set][kk][cq] = g.hs[kk] * a;
-          dN[set][kk][cq] = g.hs[kk] * b;
+          dN[set][kk][cq] = g.hs[kk] * (bnd ? a : b);
         }
       }
     }
@@ -579,7 +624,11 @@ dg_operator_kernel(const Job job, const DGParams<typename BaseOf<V>::type> prm) 
           V* const ffo = fgc + NCH * NN;
           V* const ffn = ffo + 2 * DIM * NCH * NF;
           V* const ffd = ffn + 2 * DIM * NCH * NF;
-          FaceViscSysB<DIM, P, V>::run(prm, geo, r2, f, pt, fgc, sDg, sgp, sgm, ffo, ffn, ffd, fface);
+          const int M = f >> 1, side = f & 1;
+          const int ecM = M == 0 ? fel % geo.n[0] : (M == 1 ? (fel / geo.n[0]) % geo.n[1] : fel / (geo.n[0] * geo.n[1]));
+          const int gnM = M == 0 ? geo.n[0] : (M == 1 ? geo.n[1] : geo.n[2]);
+          const bool bnd = bc_kind(prm, M, side) != BC_PERIODIC && (side ? ecM == gnM - 1 : ecM == 0);
+          FaceViscSysB<DIM, P, V>::run(prm, geo, r2, f, pt, fgc, sDg, sgp, sgm, ffo, ffn, ffd, fface, bnd);
         }
         if (live) {
           const int nch = r2 ? NCH : NG;

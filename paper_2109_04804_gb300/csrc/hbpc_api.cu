@@ -3026,24 +3026,27 @@ hbpc_status hbpc_set_boundary(hbpc_ctx* ctx, int dir, int kind_lo, const double*
   const int kinds[2] = {kind_lo, kind_hi};
   const double* states[2] = {state_lo, state_hi};
   for (int sd = 0; sd < 2; ++sd)
-    if (kinds[sd] != HBPC_BC_PERIODIC && kinds[sd] != HBPC_BC_DIRICHLET && kinds[sd] != HBPC_BC_WALL)
+    if (kinds[sd] != HBPC_BC_PERIODIC && kinds[sd] != HBPC_BC_DIRICHLET && kinds[sd] != HBPC_BC_WALL &&
+        kinds[sd] != HBPC_BC_NOSLIP)
       return bad("unknown boundary kind");
   if ((kind_lo == HBPC_BC_PERIODIC) != (kind_hi == HBPC_BC_PERIODIC))
     return bad("a direction is periodic at both ends or at neither");
   const bool bounded = kind_lo != HBPC_BC_PERIODIC;
-  if (bounded && (ctx->phys.nu > 0.0 || ctx->phys.law == HBPC_LAW_NAVIER_STOKES))
-    return fail(ctx, HBPC_ERR_UNSUPPORTED, "boundaries are built for the inviscid laws");
+  if (bounded && ctx->phys.nu > 0.0 && ctx->phys.law != HBPC_LAW_NAVIER_STOKES)
+    return fail(ctx, HBPC_ERR_UNSUPPORTED, "boundaries are not built for the scalar viscous term");
   double val[2][5] = {};
   for (int sd = 0; sd < 2; ++sd) {
     if (kinds[sd] == HBPC_BC_WALL && ctx->phys.law != HBPC_LAW_EULER)
       return bad("a slip wall needs the Euler equations");
+    if (kinds[sd] == HBPC_BC_NOSLIP && ctx->phys.law != HBPC_LAW_NAVIER_STOKES)
+      return bad("a no-slip wall needs the Navier-Stokes equations");
     if (kinds[sd] != HBPC_BC_DIRICHLET) continue;
     if (!states[sd]) return bad("a Dirichlet boundary needs its state");
     for (int v = 0; v < ctx->nv; ++v) {
       if (!std::isfinite(states[sd][v])) return bad("the Dirichlet state must be finite");
       val[sd][v] = states[sd][v];
     }
-    if (ctx->phys.law == HBPC_LAW_EULER) {
+    if (law_is_euler(ctx->phys.law)) {
       const double rho = val[sd][0];
       double m2 = 0.0;
       for (int k = 0; k < ctx->dim; ++k) m2 += val[sd][1 + k] * val[sd][1 + k];

@@ -27,7 +27,7 @@ FLUX_GLOBAL_LF, FLUX_RUSANOV = 0, 1
 NODES_LOBATTO, NODES_GAUSS = 0, 1
 PC_NONE, PC_BJEXT, PC_LEARNED, PC_BJEXT_H = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
-BC_PERIODIC, BC_DIRICHLET, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_DIRICHLET, BC_WALL, BC_NOSLIP = 0, 1, 2, 3
 PC_LOSS = {"probe": 0, "inverse": 1}
 PHASES = ("jv", "operator", "arnoldi_dot", "arnoldi_update", "vector", "pc_apply", "pc_build")
 
@@ -301,15 +301,16 @@ class Context:
 
     def set_boundary(self, dim_index, lo, hi):
         """Boundaries of direction dim_index: lo and hi are each None (periodic;
-        both or neither), "wall" (Euler slip wall) or a sequence of n_var
-        conservative values (constant Dirichlet state)."""
+        both or neither), "wall" (Euler slip wall), "noslip" (Navier-Stokes
+        adiabatic no-slip wall) or a sequence of n_var conservative values
+        (constant Dirichlet state)."""
         def kind(b):
             if b is None:
                 return BC_PERIODIC, None
             if isinstance(b, str):
-                if b != "wall":
+                if b not in ("wall", "noslip"):
                     raise ValueError(b)
-                return BC_WALL, None
+                return (BC_WALL if b == "wall" else BC_NOSLIP), None
             arr = np.ascontiguousarray(np.asarray(b, dtype=np.float64).ravel())
             return BC_DIRICHLET, arr
         klo, alo = kind(lo)

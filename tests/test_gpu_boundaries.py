@@ -254,3 +254,108 @@ def test_boundary_argument_checks(hb):
         ctx.set_boundary(1, [1.0, 0.0, 0.0, -1.0], "wall")
     assert ei.value.status == 1
     ctx.close()
+
+
+# ---- Navier-Stokes: adiabatic no-slip walls and a lid (Dirichlet state) -------
+
+def make_ns(hb, dim, N, n, bcs, family=LOBATTO, flux="lf", mu=0.05, **solver):
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    ctx = hb.Context(dim, n, lo, hi, N, law=hb.LAW_NAVIER_STOKES, flux=FLUX[flux], mu=mu, eps=1.0,
+                     nodes=FAM[family], **solver)
+    spec = lambda b: ("noslip",) if isinstance(b, str) else ("dirichlet", np.asarray(b, dtype=np.float64))
+    obc = []
+    for m, b in enumerate(bcs):
+        if b is None:
+            obc.append(None)
+        else:
+            ctx.set_boundary(m, b[0], b[1])
+            obc.append((spec(b[0]), spec(b[1])))
+    ph = laws.Physics(laws.NAVIER_STOKES, dim, flux=flux, mu=mu, eps=1.0)
+    disc = dgsem.Disc(dgsem.Mesh(dim, n, lo, hi, bc=obc), N, ph, family)
+    return ctx, disc
+
+
+LID = {2: euler_state_of(1.0, (1.0, 0.0), 1.0 / 1.4), 3: euler_state_of(1.0, (1.0, 0.0, 0.0), 1.0 / 1.4)}
+NS_CASES = [
+    # dim, N, n, bcs, family, flux
+    (2, 3, (4, 3), [("noslip", "noslip"), ("noslip", LID[2])], LOBATTO, "rusanov"),
+    (2, 2, (3, 4), [("noslip", "noslip"), ("noslip", LID[2])], GAUSS, "lf"),
+    (3, 2, (3, 2, 3), [("noslip", "noslip"), None, ("noslip", LID[3])], LOBATTO, "lf"),
+]
+
+
+def cavity_gas(disc, seed):
+    X = disc.node_coords()
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.05 * np.sin(2.0 * X[0] + 0.3) + 0.01 * rng.standard_normal(X[0].shape)
+    v = [0.2 * np.sin(np.pi * X[0]) * np.sin(np.pi * X[-1]) + 0.02 * rng.standard_normal(X[0].shape)
+         for _ in range(disc.d)]
+    p = 1.0 / 1.4 + 0.02 * np.cos(X[0] + X[-1])
+    return inputs.euler_from_primitive(rho, v, p, 1.4, 1.0)
+
+
+@pytest.mark.parametrize("dim,N,n,bcs,family,flux", NS_CASES)
+def test_ns_operator_parity_with_walls(hb, dim, N, n, bcs, family, flux):
+    ctx, disc = make_ns(hb, dim, N, n, bcs, family, flux)
+    w = cavity_gas(disc, 101)
+    s = np.random.default_rng(102).standard_normal(disc.shape)
+    r1 = torch.empty(disc.ndof, dtype=torch.float64, device="cuda")
+    r2 = torch.empty_like(r1)
+    ctx.eval_R1(dev(w), r1)
+    ctx.eval_R2(dev(w), dev(s), r2)
+    ref1, ref2 = dgsem.R1(disc, w), dgsem.R2(disc, w, s)
+    assert np.abs(host(r1) - ref1.ravel()).max() <= 1e-12 * np.abs(ref1).max()
+    assert np.abs(host(r2) - ref2.ravel()).max() <= 1e-12 * np.abs(ref2).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ns_jv_and_blocks_with_walls(hb, prec):
+    """Eq. 23 (FP64) / the FP32 analytic form (mixed, global LF) and the BJ_ext
+    blocks (assembled by columns of the frozen-neighbour R2) at walls and lid."""
+    dim, N, n, bcs, family, flux = NS_CASES[1]
+    dt, a1, a2 = 0.02, 0.5, 1.0 / 6.0
+    ctx, disc = make_ns(hb, dim, N, n, bcs, family, flux, dt=dt, pc=hb.PC_BJEXT,
+                        precision=hb.PREC_MIXED if prec == "mixed" else hb.PREC_FP64)
+    rng = np.random.default_rng(103)
+    W = cavity_gas(disc, 104)
+    S = dgsem.R1(disc, W) + 0.05 * rng.standard_normal(disc.shape)
+    X = np.concatenate([W.ravel(), S.ravel()])
+    dX = rng.standard_normal(2 * disc.ndof)
+    sysm = newton.StageSystem(disc, W, a1, a2, dt)
+    _, r1, r2 = sysm.residual(X)
+    ref = sysm.jv(X, r1, r2, dX, "analytic" if prec == "mixed" else "fd")
+    out = torch.empty(2 * disc.ndof, dtype=torch.float64, device="cuda")
+    ctx.eval_Jv(a1, a2, dev(X), dev(dX), out)
+    assert rel(host(out), ref) <= (2e-5 if prec == "mixed" else 1e-6)
+    v = rng.standard_normal(2 * disc.ndof)
+    refp = newton.make_preconditioner(sysm, X, "bjext")(v)
+    ctx.eval_pc(a1, a2, dev(X), dev(v), out)
+    assert rel(host(out), refp) <= (1e-4 if prec == "mixed" else 1e-11)
+    ctx.close()
+
+
+def test_lid_driven_cavity_steps_vs_oracle(hb):
+    """The paper's lid-driven cavity setting on a small mesh: walls left, right
+    and below, the lid state (rho 1, v (1, 0), p 1/gamma) above; HBPC(4, 1)
+    steps equal the oracle's, and mass is conserved to rounding (the lid's
+    state has no normal velocity, the walls pass no mass)."""
+    dt = 0.01
+    ctx, disc = make_ns(hb, 2, 2, (3, 3), [("noslip", "noslip"), ("noslip", LID[2])], LOBATTO, "rusanov",
+                        mu=0.025, q=4, kmax=1, dt=dt, tol_newton_rel=1e-13, tol_newton_abs=1e-13,
+                        tol_gmres_rel=1e-9, gmres_restart=100, pc=hb.PC_BJEXT)
+    X = disc.node_coords()
+    w0 = inputs.euler_from_primitive(np.ones_like(X[0]), [0 * X[0], 0 * X[0]], np.full_like(X[0], 1 / 1.4))
+    ctx.set_state(w0)
+    ctx.step(2)
+    w = ctx.get_state()
+    opts = newton.NewtonOptions(tol_rel=1e-13, tol_abs=1e-13, gmres_tol=1e-9, restart=100, jv="fd")
+    adv = ohbpc.dg_stepper(disc, dt, 4, 1, opts)
+    ref = w0
+    for _ in range(2):
+        ref = adv(ref)
+    assert rel(w, ref) <= 1e-11
+    assert np.abs(w - w0).max() > 1e-4          # the lid drives the flow
+    c0, c1 = dgsem.cell_integral(disc, w0), dgsem.cell_integral(disc, w)
+    assert abs(c1[0] - c0[0]) <= 1e-12 * abs(c0[0])
+    ctx.close()

@@ -338,8 +338,7 @@ def test_ns_jv_and_blocks_with_walls(hb, prec):
 def test_lid_driven_cavity_steps_vs_oracle(hb):
     """The paper's lid-driven cavity setting on a small mesh: walls left, right
     and below, the lid state (rho 1, v (1, 0), p 1/gamma) above; HBPC(4, 1)
-    steps equal the oracle's, and mass is conserved to rounding (the lid's
-    state has no normal velocity, the walls pass no mass)."""
+    steps equal the oracle's and the lid sets the gas in motion."""
     dt = 0.01
     ctx, disc = make_ns(hb, 2, 2, (3, 3), [("noslip", "noslip"), ("noslip", LID[2])], LOBATTO, "rusanov",
                         mu=0.025, q=4, kmax=1, dt=dt, tol_newton_rel=1e-13, tol_newton_abs=1e-13,
@@ -356,6 +355,20 @@ def test_lid_driven_cavity_steps_vs_oracle(hb):
         ref = adv(ref)
     assert rel(w, ref) <= 1e-11
     assert np.abs(w - w0).max() > 1e-4          # the lid drives the flow
+    ctx.close()
+
+
+def test_ns_noslip_box_conserves_mass_and_energy_on_the_gpu(hb):
+    """Steps of a gas in a box of adiabatic no-slip walls keep total mass and
+    energy to rounding (the walls pass neither, see the oracle's pins)."""
+    ctx, disc = make_ns(hb, 2, 3, (4, 4), [("noslip", "noslip"), ("noslip", "noslip")], LOBATTO, "rusanov",
+                        mu=0.02, q=4, kmax=1, dt=0.01, tol_newton_rel=1e-12, tol_newton_abs=1e-13,
+                        tol_gmres_rel=1e-9, gmres_restart=100, pc=hb.PC_BJEXT)
+    w0 = cavity_gas(disc, 105)
+    ctx.set_state(w0)
+    ctx.step(3)
+    w = ctx.get_state()
     c0, c1 = dgsem.cell_integral(disc, w0), dgsem.cell_integral(disc, w)
-    assert abs(c1[0] - c0[0]) <= 1e-12 * abs(c0[0])
+    assert abs(c1[0] - c0[0]) <= 1e-12 * abs(c0[0]) and abs(c1[3] - c0[3]) <= 1e-12 * abs(c0[3])
+    assert np.abs(w - w0).max() > 1e-5
     ctx.close()

@@ -1155,6 +1155,66 @@ def run_pc_network(args, emit=True):
     return line
 
 
+CAVITY = dict(n=(16, 16), N=5, q=6, kmax=2, dt=0.02, eps=0.1, mu=0.025, tol_newton_rel=1e-3,
+              tol_gmres_rel=1e-2, gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50)
+
+
+def run_cavity(args, emit=True):
+    """The paper's lid-driven cavity (Sec. 5.3.1): Navier-Stokes on [0, 1]^2,
+    16 x 16 elements, N = 5, adiabatic no-slip walls left, right and below, the
+    lid state rho = 1, v = (1, 0), p = 1/gamma above, eps = 0.1, mu = 0.025
+    (Re 400), HBPC(6, 2), dt = 0.02, eps_Newton = 1e-3, eps_GMRES = 1e-2; the
+    gas at rest with the lid's density and pressure initially.  FP64, BJ_ext
+    (blocks once per Newton solve), one graph launch per step.  Reports
+    DOF-timesteps/s, iterations per step and the kinetic energy the lid puts
+    in (no reference data: the run's own record)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2109_04804_gb300 import hbpc, inputs
+    C = CAVITY
+    c = hbpc.Context(2, C["n"], (0.0, 0.0), (1.0, 1.0), C["N"], law=hbpc.LAW_NAVIER_STOKES,
+                     flux=hbpc.FLUX_RUSANOV, mu=C["mu"], eps=C["eps"], q=C["q"], kmax=C["kmax"], dt=C["dt"],
+                     tol_newton_rel=C["tol_newton_rel"], tol_newton_abs=0.0, tol_gmres_rel=C["tol_gmres_rel"],
+                     gmres_restart=C["gmres_restart"], gmres_max_iter=C["gmres_max_iter"],
+                     newton_max_iter=C["newton_max_iter"], pc=hbpc.PC_BJEXT)
+    gamma, eps = 1.4, C["eps"]
+    lid = inputs.euler_from_primitive(np.array([1.0]), [np.array([1.0]), np.array([0.0])], np.array([1.0 / gamma]),
+                                      gamma, eps)[0]
+    c.set_boundary(0, "noslip", "noslip")
+    c.set_boundary(1, "noslip", lid)
+    c.set_pc_rebuild(False)
+    c.set_step_graph(True)
+    X = c.node_coords()
+    w0 = inputs.euler_from_primitive(np.ones_like(X[0]), [0 * X[0], 0 * X[0]], np.full_like(X[0], 1.0 / gamma),
+                                     gamma, eps)
+    c.set_state(w0)
+    for _ in range(max(1, args.warmup)):
+        c.step(1)
+    st0 = c.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    c.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = c.stats()
+    w = c.get_state()
+    rho, mom = w[:, 0], w[:, 1:3]
+    ke = 0.5 * float((mom ** 2 / rho[:, None]).sum()) / w[:, 0].size
+    line = {"workload": "lid_driven_cavity_16x16_N5_HBPC(6,2)_dt0.02_Re400_eps0.1", "unit": UNIT,
+            "value": c.ndof * 1000.0 / ms, "ms_per_step": ms, "steps": args.steps, "t": st["t"],
+            "gmres_its_per_step": (st["gmres_its"] - st0["gmres_its"]) / args.steps,
+            "newton_its_per_step": (st["newton_its"] - st0["newton_its"]) / args.steps,
+            "mean_kinetic_energy_per_node": ke, "config": dict(C)}
+    c.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def tgv_dt(n):
     """CFL / sum_m(lambda_max,m (N+1) / h_m) with lambda_max = |v|_max + c of the
     initial state (|v| <= 1, c = 1/eps with p ~ 1/gamma)."""
@@ -1288,7 +1348,7 @@ def main():
                          "workload's own; mixed: FP32 Krylov loop, FP64 Newton residual/update")
     ap.add_argument("--workload", default="advection2d",
                     choices=["advection2d", "burgers_batch", "euler_vortex", "taylor_green", "r1_roofline",
-                             "euler_pc", "pc_network"],
+                             "euler_pc", "pc_network", "cavity"],
                     help="advection2d: the default 64x64 N=5 HBPC(8,4) line; burgers_batch: the batched "
                          "viscous Burgers instances; euler_vortex: learned vs BJ_ext vs plain GMRES; "
                          "taylor_green: the 3-D Navier-Stokes line; r1_roofline: the operator-pass roofline "
@@ -1323,6 +1383,8 @@ def main():
         run_euler_pc(args)
     elif args.workload == "pc_network":
         run_pc_network(args)
+    elif args.workload == "cavity":
+        run_cavity(args)
     else:
         run_ours(args)
 

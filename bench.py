@@ -1156,60 +1156,99 @@ def run_pc_network(args, emit=True):
 
 
 CAVITY = dict(n=(16, 16), N=5, q=6, kmax=2, dt=0.02, eps=0.1, mu=0.025, tol_newton_rel=1e-3,
-              tol_gmres_rel=1e-2, gmres_restart=100, gmres_max_iter=7000, newton_max_iter=50)
+              tol_newton_abs=1e-10, tol_gmres_rel=1e-2, gmres_restart=200, gmres_max_iter=7000, newton_max_iter=50,
+              startup=((0.002, 10), (0.005, 4), (0.01, 4)))
 
 
 def run_cavity(args, emit=True):
     """The paper's lid-driven cavity (Sec. 5.3.1): Navier-Stokes on [0, 1]^2,
     16 x 16 elements, N = 5, adiabatic no-slip walls left, right and below, the
     lid state rho = 1, v = (1, 0), p = 1/gamma above, eps = 0.1, mu = 0.025
-    (Re 400), HBPC(6, 2), dt = 0.02, eps_Newton = 1e-3, eps_GMRES = 1e-2; the
-    gas at rest with the lid's density and pressure initially.  FP64, BJ_ext
-    (blocks once per Newton solve), one graph launch per step.  Reports
-    DOF-timesteps/s, iterations per step and the kinetic energy the lid puts
-    in (no reference data: the run's own record)."""
+    (Re 400), HBPC(6, 2), dt = 0.02, eps_Newton = 1e-3 (or an update
+    ||dW|| <= 1e-10), eps_GMRES = 1e-2; the gas at rest with the lid's density and
+    pressure initially.  From the gas at rest the first dt = 0.02 step fails
+    (the first Newton update of the corrector drives the pressure negative, on
+    the oracle as on the GPU), so an untimed start-up of shorter steps
+    (dt 0.002 x 10, 0.005 x 4, 0.01 x 4; t = 0.08) precedes the timed
+    dt = 0.02 steps.  FP64, BJ_ext, one graph launch per step; two arms: the
+    blocks built at every Newton iteration, and once per Newton solve.
+    Reports DOF-timesteps/s, iterations per step, and the kinetic energy, the
+    smallest density and the largest speed after the steps (no reference data:
+    the run's own record)."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__ as g
     g.build()
     from paper_2109_04804_gb300 import hbpc, inputs
     C = CAVITY
-    c = hbpc.Context(2, C["n"], (0.0, 0.0), (1.0, 1.0), C["N"], law=hbpc.LAW_NAVIER_STOKES,
-                     flux=hbpc.FLUX_RUSANOV, mu=C["mu"], eps=C["eps"], q=C["q"], kmax=C["kmax"], dt=C["dt"],
-                     tol_newton_rel=C["tol_newton_rel"], tol_newton_abs=0.0, tol_gmres_rel=C["tol_gmres_rel"],
-                     gmres_restart=C["gmres_restart"], gmres_max_iter=C["gmres_max_iter"],
-                     newton_max_iter=C["newton_max_iter"], pc=hbpc.PC_BJEXT)
     gamma, eps = 1.4, C["eps"]
     lid = inputs.euler_from_primitive(np.array([1.0]), [np.array([1.0]), np.array([0.0])], np.array([1.0 / gamma]),
                                       gamma, eps)[0]
-    c.set_boundary(0, "noslip", "noslip")
-    c.set_boundary(1, "noslip", lid)
-    c.set_pc_rebuild(False)
-    c.set_step_graph(True)
+
+    def ctx(dt):
+        c = hbpc.Context(2, C["n"], (0.0, 0.0), (1.0, 1.0), C["N"], law=hbpc.LAW_NAVIER_STOKES,
+                         flux=hbpc.FLUX_RUSANOV, mu=C["mu"], eps=eps, q=C["q"], kmax=C["kmax"], dt=dt,
+                         tol_newton_rel=C["tol_newton_rel"], tol_newton_abs=C["tol_newton_abs"],
+                         tol_gmres_rel=C["tol_gmres_rel"], gmres_restart=C["gmres_restart"],
+                         gmres_max_iter=C["gmres_max_iter"], newton_max_iter=C["newton_max_iter"], pc=hbpc.PC_BJEXT)
+        c.set_boundary(0, "noslip", "noslip")
+        c.set_boundary(1, "noslip", lid)
+        return c
+
+    c = ctx(C["dt"])
     X = c.node_coords()
-    w0 = inputs.euler_from_primitive(np.ones_like(X[0]), [0 * X[0], 0 * X[0]], np.full_like(X[0], 1.0 / gamma),
-                                     gamma, eps)
-    c.set_state(w0)
-    for _ in range(max(1, args.warmup)):
-        c.step(1)
-    st0 = c.stats()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    c.step(args.steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    st = c.stats()
-    w = c.get_state()
-    rho, mom = w[:, 0], w[:, 1:3]
-    ke = 0.5 * float((mom ** 2 / rho[:, None]).sum()) / w[:, 0].size
-    line = {"workload": "lid_driven_cavity_16x16_N5_HBPC(6,2)_dt0.02_Re400_eps0.1", "unit": UNIT,
-            "value": c.ndof * 1000.0 / ms, "ms_per_step": ms, "steps": args.steps, "t": st["t"],
-            "gmres_its_per_step": (st["gmres_its"] - st0["gmres_its"]) / args.steps,
-            "newton_its_per_step": (st["newton_its"] - st0["newton_its"]) / args.steps,
-            "mean_kinetic_energy_per_node": ke, "config": dict(C)}
+    ndof = c.ndof
     c.close()
+    w = inputs.euler_from_primitive(np.ones_like(X[0]), [0 * X[0], 0 * X[0]], np.full_like(X[0], 1.0 / gamma),
+                                    gamma, eps)
+    t0 = 0.0
+    for dt, n in C["startup"]:
+        c = ctx(dt)
+        c.set_state(w)
+        c.step(n)
+        w = c.get_state()
+        t0 += c.stats()["t"]
+        c.close()
+
+    def arm(every):
+        c = ctx(C["dt"])
+        c.set_pc_rebuild(every)
+        c.set_step_graph(not args.no_step_graph)
+        c.set_state(w)
+        ok = True
+        try:
+            c.step(max(1, args.warmup))
+        except hbpc.HBPCError as e:
+            ok = "warm-up step: " + str(e)[:100]
+        st0 = c.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        if ok is True:
+            try:
+                c.step(args.steps)
+            except hbpc.HBPCError as e:
+                ok = str(e)[:100]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = c.stats()
+        wt = c.get_state()
+        c.close()
+        rho, mom = wt[:, 0], wt[:, 1:3]
+        out = {"ok": ok, "value": ndof * 1000.0 / ms if ok is True else 0.0, "ms_per_step": ms,
+               "t": t0 + st["t"], "gmres_its_per_step": (st["gmres_its"] - st0["gmres_its"]) / args.steps,
+               "newton_its_per_step": (st["newton_its"] - st0["newton_its"]) / args.steps,
+               "mean_kinetic_energy_per_node": 0.5 * float((mom ** 2 / rho[:, None]).sum()) / rho.size,
+               "min_density": float(rho.min()), "max_speed": float(np.sqrt(((mom / rho[:, None]) ** 2).sum(1)).max())}
+        return out
+
+    arms = {"pc_every_newton_iteration": arm(True), "pc_once_per_newton_solve": arm(False)}
+    best = max(arms, key=lambda k: arms[k]["value"])
+    line = {"workload": "lid_driven_cavity_16x16_N5_HBPC(6,2)_dt0.02_Re400_eps0.1", "unit": UNIT,
+            "value": arms[best]["value"], "best_arm": best, "steps": args.steps, "ndof": ndof,
+            "step_graph": not args.no_step_graph, "arms": arms,
+            "config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in C.items()}}
     if emit:
         print(json.dumps(line), flush=True)
     return line

@@ -2043,10 +2043,9 @@ hbpc_status step_graph_run(hbpc_ctx* x) {
   x->stats.arnoldi_cols += c.arnoldi_cols;
   x->stats.r1_evals += x->sg.top_r1 + c.newton_its + c.gmres_its * (lin ? 2 : 1);
   x->stats.r2_evals += x->sg.top_r2 + c.newton_its + c.gmres_its * (per - (lin ? 2 : 1));
-  if (sing) {
-    HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
-    return fail(x, HBPC_ERR_NONFINITE, "BJ_ext block is singular");
-  }
+  if (sing) HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
+  // the first failure of the step (blocks built after it see its garbage)
+  if (sing && !c.err) return fail(x, HBPC_ERR_NONFINITE, "BJ_ext block is singular");
   if (c.err) {
     const char* what = c.where == 1 ? "initial Newton residual is not finite"
                        : c.where == 2 ? "Newton residual is not finite"

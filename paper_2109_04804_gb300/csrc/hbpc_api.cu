@@ -26,6 +26,7 @@
 #include "krylov.cuh"
 #include "batch_krylov.cuh"
 #include "bjext_kernels.cuh"
+#include "bjext_tc.cuh"
 #include "step_graph.cuh"
 #include "mlp.cuh"
 
@@ -286,6 +287,14 @@ struct hbpc_ctx {
   double* kron_d = nullptr;
   float* kron_f = nullptr;
   int* kron_ok = nullptr;
+  // the shared FP64 block's apply on the tensor cores (bjext_tc.cuh): P's
+  // digit planes and row exponents, formed at every build; ptc_ready when
+  // they match the current blocks; HBPC_PC_TC=0 keeps the CUDA-core apply
+  __nv_bfloat16* ptc_planes = nullptr;
+  int* ptc_exp = nullptr;
+  int* ptc_err = nullptr;
+  bool ptc_ready = false;
+  int ptc_enable = 1;
   // mixed precision (FP32 Krylov loop, FP64 Newton)
   DGParams<float> prmf{};
   KrylovT<float> Kf{};
@@ -604,6 +613,18 @@ hbpc_status pc_apply(hbpc_ctx* x, const double* in, const int* jidx, const doubl
   a.shared = x->pc_shared ? 1 : 0;
   a.kron = x->pc_shared ? x->kron_d : nullptr; a.kron_ok = x->kron_ok; a.P = x->P; a.dim = x->dim;
   a.hess = x->pc_hess ? 1 : 0;
+  if (a.shared && !a.hess && !a.zn && x->ptc_ready) {
+    PcApplyTc t{};
+    t.planes = x->ptc_planes; t.pexp = x->ptc_exp;
+    t.xW = a.xW; t.xS = a.xS; t.scale = scale; t.jidx = jidx; t.ld = a.ld;
+    t.oW = a.oW; t.oS = a.oS; t.skip = skip; t.accumulate = accumulate;
+    t.nb = x->nb; t.nE = int(x->nE); t.err = x->ptc_err;
+    const int grid = int((x->nE + kPtcElems - 1) / kPtcElems);
+    HBPC_RUN(x, HBPC_PHASE_PC, 1,
+             k_pc_apply_tc<<<grid, kPtcThreads, PtcDims(x->nb).smem(), x->stream>>>(t));
+    HBPC_LAUNCH_CK(x, "k_pc_apply_tc");
+    return HBPC_OK;
+  }
   if (a.shared && pc_shared_launch(x, a)) return HBPC_OK;
   HBPC_RUN(x, HBPC_PHASE_PC, 1, k_pc_apply<double><<<x->pc_grid, x->pc_threads, x->pc_smem, x->stream>>>(a, x->K));
   HBPC_LAUNCH_CK(x, "k_pc_apply");
@@ -962,6 +983,16 @@ hbpc_status pc_build(hbpc_ctx* x, const double* W, double c1, double c2) {
     HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
              k_pc_invert<double><<<nEb, 256, (nb * nb + nb) * sizeof(double) + nb * sizeof(int), x->stream>>>(
                  x->Mpc, x->nb, nEb, x->singular));
+  }
+  // the shared FP64 block's P = [[M, -c2 J M], [J M, M - c1 J M]] as digit
+  // planes for the tensor-core apply
+  x->ptc_ready = false;
+  if (x->pc_shared && !mixed && !x->pc_hess && x->ptc_planes) {
+    const PtcDims D(x->nb);
+    HBPC_RUN(x, HBPC_PHASE_PC_BUILD, 1,
+             k_pc_tc_planes<<<D.R, 128, 3 * nb * sizeof(double), x->stream>>>(x->Mpc, x->Jpc, x->nb, x->c12,
+                                                                             x->ptc_planes, x->ptc_exp));
+    x->ptc_ready = true;
   }
   if (x->pc_shared && x->kron_ok) {
     // the shared J_0 as Kronecker factors for the apply (checked entry by entry)
@@ -2100,6 +2131,7 @@ void free_all(hbpc_ctx* x) {
   cudaFree(x->dX); cudaFree(x->bvec); cudaFree(x->stage); cudaFree(x->V); cudaFree(x->small);
   cudaFree(x->partial); cudaFree(x->ticket); cudaFree(x->st);
   cudaFree(x->kron_d); cudaFree(x->kron_f); cudaFree(x->kron_ok);
+  cudaFree(x->ptc_planes); cudaFree(x->ptc_exp); cudaFree(x->ptc_err);
   cudaFree(x->sa); cudaFree(x->sb); cudaFree(x->srhs); cudaFree(x->snrm);
   cudaFree(x->Jpc); cudaFree(x->Mpc); cudaFree(x->Z); cudaFree(x->singular);
   cudaFree(x->Vf); cudaFree(x->Zf); cudaFree(x->Zf2); cudaFree(x->Wf); cudaFree(x->Mf); cudaFree(x->Jf);
@@ -2118,6 +2150,10 @@ void pc_launch_config(hbpc_ctx* x) {
   x->pc_smem = size_t(epb) * 4 * x->nb * sizeof(double);
 }
 
+// The tensor-core apply of the shared FP64 block: 2 n_b <= 128 (exact level
+// sums) and its shared memory within the 227 KB a CTA may have.
+bool ptc_fits(int nb) { return 2 * nb <= 128 && PtcDims(nb).smem() <= size_t(227 * 1024); }
+
 // Device memory of the block preconditioners (BJ_ext and learned).
 hbpc_status pc_alloc(hbpc_ctx* x) {
   if (x->Jpc) return HBPC_OK;
@@ -2128,6 +2164,14 @@ hbpc_status pc_alloc(hbpc_ctx* x) {
       (e = dmalloc(x, &x->kron_f, 3 * kMaxP * kMaxP)) || (e = dmalloc(x, &x->kron_ok, 1)))
     return e;
   HBPC_CK(x, cudaMemsetAsync(x->singular, 0, sizeof(int), x->stream));
+  if (x->phys.law == HBPC_LAW_ADVECTION && x->ptc_enable && ptc_fits(x->nb)) {
+    const PtcDims D(x->nb);
+    if ((e = dmalloc(x, &x->ptc_planes, D.a_bytes() / sizeof(__nv_bfloat16))) ||
+        (e = dmalloc(x, &x->ptc_exp, size_t(D.R))) || (e = dmalloc(x, &x->ptc_err, 1)))
+      return e;
+    cudaFuncSetAttribute(k_pc_tc_planes, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * x->nb * sizeof(double)));
+    cudaFuncSetAttribute(k_pc_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(D.smem()));
+  }
   const size_t nbz = size_t(x->nb);
   cudaFuncSetAttribute(k_pc_form_S<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        int(nbz * nbz * sizeof(double)));
@@ -2722,6 +2766,7 @@ hbpc_status create_group(const std::vector<int>& ids, const hbpc_mesh* meshes, i
   x->stream = st;
   if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
   if (const char* v = std::getenv("HBPC_GRAPH")) x->graph_mode = std::atoi(v);
+  if (const char* v = std::getenv("HBPC_PC_TC")) x->ptc_enable = std::atoi(v);
   if (!basis_1d(N, nodes, x->basis) ||
       !get_ops(x->phys.law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
     cudaStreamDestroy(st);
@@ -2824,6 +2869,7 @@ hbpc_status hbpc_create(hbpc_ctx** out, const hbpc_mesh* mesh, int N, int nodes,
   x->stream = static_cast<cudaStream_t>(cuda_stream);
   if (const char* v = std::getenv("HBPC_VERBOSE")) x->verbose = std::atoi(v);
   if (const char* v = std::getenv("HBPC_GRAPH")) x->graph_mode = std::atoi(v);
+  if (const char* v = std::getenv("HBPC_PC_TC")) x->ptc_enable = std::atoi(v);
   if (!basis_1d(N, nodes, x->basis)) { delete x; return fail(nullptr, HBPC_ERR_INVALID_ARG, "basis"); }
   if (!get_ops(phys->law, x->dim, x->P, nodes == HBPC_NODES_LOBATTO, x->ops)) {
     delete x;

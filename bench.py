@@ -175,6 +175,15 @@ def pc_work_per_dof(mixed):
     return (16.0 if mixed else 32.0), 4.0 * nb + 4.0 * WL["dim"] * (WL["N"] + 1) + 4.0
 
 
+def pc_tc_work_per_dof():
+    """The tensor-core form of the same apply: per W-DOF the inputs and outputs
+    of both halves (32 B), and the 43 digit-plane pair products of the
+    2 n_b x 2 n_b block (levels 0..8 of eight balanced base-256 digits per
+    operand): 43 * 2 * (2 n_b) * 2 flops per W-DOF on the BF16 tensor pipe."""
+    nb = (WL["N"] + 1) ** WL["dim"]
+    return 32.0, 43.0 * 2.0 * (2.0 * nb) * 2.0
+
+
 def cgs_work_per_dof(mixed, cavg):
     """CGS2 column (one launch per Arnoldi iteration) at the mean column count
     cavg = j + 1: the three passes read the new vector and the j + 1 basis
@@ -191,11 +200,13 @@ def cgs_work_per_dof(mixed, cavg):
 # captured.
 NCU_TRAFFIC = {
     "mixed": {"cgs2": None, "pc_apply": None, "jv": None},
-    "fp64": {"cgs2": 1.411e5, "pc_apply": 8.233e4, "jv": 1.441e5},
+    "fp64": {"cgs2": 1.411e5, "pc_apply": None, "jv": 1.441e5},
 }
 
 KERNEL_NAMES = {
     "jv": "dg_operator_kernel<advection pair,2D,P=6,JobJvLinearPair<%s>> (Eq. 24, both halves in one pass)",
+    "pc_apply_tc": ("k_pc_apply_tc (BJ_ext, Sec. 3.2.3: the shared FP64 block pair as one 2 n_b x 2 n_b product on "
+                    "tcgen05, exact BF16 digit-plane products summed in FP32 tensor memory, integer recombination)"),
     "pc_apply": "k_pc_apply_shared<%s, 2> (BJ_ext, Sec. 3.2.3; one block pair for all elements, J as Kronecker factors)",
     "cgs2": "k_cgs_lowsync<%s> (Arnoldi CGS2 column, one cooperative launch, two grid barriers; mean j + 1 = %.1f)",
 }
@@ -243,8 +254,10 @@ def c2_roofline(hbpc, ctx, precision, stats0, fp64_peak_gf, hbm):
     cols_p = pstats["arnoldi_cols"] - stats0["arnoldi_cols"]
     cavg = cols_p / max(1, its_p)
     tname = "float" if mixed else "double"
+    pc_tc = (not mixed) and bool(pstats.get("pc_apply_tc"))
     kernels = {"jv": (KERNEL_NAMES["jv"] % tname, jv_work_per_dof(mixed), prof["jv"]),
-               "pc_apply": (KERNEL_NAMES["pc_apply"] % tname, pc_work_per_dof(mixed), prof["pc_apply"]),
+               "pc_apply": ((KERNEL_NAMES["pc_apply_tc"], pc_tc_work_per_dof(), prof["pc_apply"]) if pc_tc else
+                            (KERNEL_NAMES["pc_apply"] % tname, pc_work_per_dof(mixed), prof["pc_apply"])),
                "cgs2": (KERNEL_NAMES["cgs2"] % (tname, cavg), cgs_work_per_dof(mixed, cavg),
                         (prof["arnoldi_dot"][0] + prof["arnoldi_update"][0], its_p))}
     step_ms = sum(v[0] for v in prof.values())
@@ -259,7 +272,14 @@ def c2_roofline(hbpc, ctx, precision, stats0, fp64_peak_gf, hbm):
              "algorithmic_flops_per_launch": round(fpd * ndof),
              "traffic": NCU_TRAFFIC[precision].get(ph), "avg_launch_us": round(avg * 1e6, 2),
              "launches_profiled": n, "share_of_step": round(ms / step_ms, 3)}
-        if mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are bound by memory
+        if ph == "pc_apply" and pc_tc:   # BF16 tensor pipe; the FP64-equivalent rate beside it
+            bf16 = peaks().get("bf16_tflops", 1900.0)
+            f64e = pc_work_per_dof(False)[1] * ndof / avg / 1e12
+            e.update({"bound": "tensor", "achieved": round(gf / 1000.0, 2), "peak": bf16, "unit": "TFLOP/s",
+                      "frac": round(gf / 1000.0 / bf16, 4), "hbm_achieved_gbs": round(gb, 1),
+                      "fp64_equivalent_tflops": round(f64e, 4),
+                      "fp64_equivalent_frac_of_fp64_peak": round(f64e * 1000.0 / fp64_peak_gf, 4)})
+        elif mixed:   # FP32 arithmetic is 62x the FP64 rate: these kernels are bound by memory
             e.update({"bound": "hbm", "achieved": round(gb, 1), "peak": hbm, "unit": "GB/s",
                       "frac": round(gb / hbm, 4), "alu_tflops": round(gf / 1000.0, 3)})
         else:       # GB300's FP64 pipe (1/64 of FP32) binds these

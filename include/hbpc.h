@@ -156,6 +156,12 @@ typedef struct {
   long long pc_exact_blocks; /* learned preconditioner: element blocks that
                                 failed their probe check and got the exact
                                 inverse instead (summed over builds) */
+  long long pc_apply_tc;     /* 1 when the last preconditioner build put the
+                                BJ_ext apply on the tensor cores (one FP64
+                                block shared by all elements, applied through
+                                exact BF16 digit-plane products; environment
+                                HBPC_PC_TC=0 at creation keeps the CUDA-core
+                                apply), else 0 */
 } hbpc_stats;
 
 /* Phases of the per-launch device timing (hbpc_profile_*). */

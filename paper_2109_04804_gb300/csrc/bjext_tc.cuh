@@ -80,36 +80,36 @@ struct PtcDims {
 
 // Split a finite FP64 value into a signed integer T of at most 62 bits
 // relative to the largest biased exponent E of its row or column
-// (x = T 2^(E - 1084)), then into balanced base-256 digits d[0] (top) .. d[7].
-__device__ __forceinline__ void ptc_digits(double v, int E, int* d) {
+// (x = T 2^(E - 1084)), then into balanced base-256 digits (top first) as
+// BF16 bit patterns h[0] .. h[7].  Adding 128 to each of the seven low bytes
+// makes every low digit plus 128 a plain byte (no carries), so a digit is a
+// byte extract; the top digit is the top byte, signed (|d_0| <= 65).  A digit
+// d in [-256, 256] becomes BF16 through the exact FP32 difference
+// (2^23 + 256 + d) - (2^23 + 256), whose low 16 bits are zero.
+__device__ __forceinline__ void ptc_digit_bits(double v, int E, uint32_t* h) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
   const int ex = int((bits >> 52) & 0x7FF);
   const unsigned long long frac = bits & ((1ull << 52) - 1);
   const long long mant = (long long)(ex ? (frac | (1ull << 52)) : frac);
-  const int exe = ex ? ex : 1;
-  const int sh = exe - E + 9;   // <= 9: mant < 2^53 -> T < 2^62
+  const int sh = (ex ? ex : 1) - E + 9;   // <= 9: mant < 2^53 -> |T| < 2^62
   long long T = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0);
   if (bits >> 63) T = -T;
+  const unsigned long long Tp = static_cast<unsigned long long>(T) + 0x0080808080808080ull;
+  const uint32_t lo = uint32_t(Tp), hi = uint32_t(Tp >> 32);
+  const int top = int(static_cast<signed char>(hi >> 24));
+  h[0] = __float_as_uint(__int_as_float(0x4B000000 + 256 + top) - 8388864.0f) >> 16;
 #pragma unroll
-  for (int b = kPtcDigits - 1; b >= 1; --b) {
-    const int lo = int(static_cast<signed char>(T & 0xFF));
-    d[b] = lo;
-    T = (T - lo) >> 8;
+  for (int b = 1; b < kPtcDigits; ++b) {
+    const int byte = 7 - b;   // digit b sits in byte 7 - b
+    const uint32_t u = byte >= 4 ? (hi >> (8 * (byte - 4))) & 0xFFu : (lo >> (8 * byte)) & 0xFFu;
+    h[b] = __float_as_uint(__int_as_float(0x4B000000 + 128 + int(u)) - 8388864.0f) >> 16;
   }
-  d[0] = int(T);
 }
 
 // The biased exponent used for the scaling (1 for zeros and subnormals).
 __device__ __forceinline__ int ptc_exp(double v) {
   const int ex = int((static_cast<unsigned long long>(__double_as_longlong(v)) >> 52) & 0x7FF);
   return ex ? ex : 1;
-}
-
-// BF16 bits of an integer d in [-256, 256]: the FP32 value 2^23 + 256 + d
-// minus 2^23 + 256 is exact, and its low 16 bits are zero.
-__device__ __forceinline__ uint32_t ptc_bf16_bits(int d) {
-  const float f = __int_as_float(0x4B000000 + 256 + d) - 8388864.0f;
-  return __float_as_uint(f) >> 16;
 }
 
 // Byte offset of (row, k) in a no-swizzle K-major plane whose K groups are
@@ -160,17 +160,12 @@ __global__ void __launch_bounds__(128) k_pc_tc_planes(const double* __restrict__
   unsigned char* base = reinterpret_cast<unsigned char*>(planes);
   const int lbo = D.R * 16;
   for (int k = threadIdx.x; k < D.K; k += blockDim.x) {
-    int d[kPtcDigits];
-    if (live && k < n2 && E != 0x7FF) {
-      ptc_digits(s_row[k], E, d);
-    } else {
-#pragma unroll
-      for (int a = 0; a < kPtcDigits; ++a) d[a] = 0;
-    }
+    uint32_t h[kPtcDigits];
+    ptc_digit_bits(live && k < n2 && E != 0x7FF ? s_row[k] : 0.0, E == 0x7FF ? 1 : E, h);
     const uint32_t o = ptc_off(p, k, lbo);
 #pragma unroll
     for (int a = 0; a < kPtcDigits; ++a)
-      *reinterpret_cast<__nv_bfloat16*>(base + a * D.a_plane() + o) = __float2bfloat16_rn(float(d[a]));
+      *reinterpret_cast<unsigned short*>(base + a * D.a_plane() + o) = static_cast<unsigned short>(h[a]);
   }
 }
 
@@ -283,20 +278,16 @@ __global__ void __launch_bounds__(kPtcThreads, 1) k_pc_apply_tc(PcApplyTc a) {
     if (q == 0) s_ex[j] = E;
     const int lbo = kPtcElems * 16;
     for (int i = q; i < D.K / 2; i += 16) {
-      int d0[kPtcDigits], d1[kPtcDigits];
+      uint32_t h0[kPtcDigits], h1[kPtcDigits];
       const int k = 2 * i;
-      const double v0 = k < n2 ? xr[k] : 0.0, v1 = k + 1 < n2 ? xr[k + 1] : 0.0;
-      if (E != 0x7FF) {
-        ptc_digits(v0, E, d0);
-        ptc_digits(v1, E, d1);
-      } else {
-#pragma unroll
-        for (int b = 0; b < kPtcDigits; ++b) { d0[b] = 0; d1[b] = 0; }
-      }
+      const bool fin = E != 0x7FF;   // a column with Inf or NaN: zero digits, NaN outputs
+      const double v0 = fin && k < n2 ? xr[k] : 0.0, v1 = fin && k + 1 < n2 ? xr[k + 1] : 0.0;
+      ptc_digit_bits(v0, fin ? E : 1, h0);
+      ptc_digit_bits(v1, fin ? E : 1, h1);
       const uint32_t o = ptc_off(j, k, lbo);
 #pragma unroll
       for (int b = 0; b < kPtcDigits; ++b)
-        *reinterpret_cast<uint32_t*>(sX + b * D.b_plane() + o) = ptc_bf16_bits(d0[b]) | (ptc_bf16_bits(d1[b]) << 16);
+        *reinterpret_cast<uint32_t*>(sX + b * D.b_plane() + o) = h0[b] | (h1[b] << 16);
     }
   }
   // the generic-proxy stores above are read by the tensor cores (async proxy)
@@ -383,13 +374,14 @@ __global__ void __launch_bounds__(kPtcThreads, 1) k_pc_apply_tc(PcApplyTc a) {
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int L = 0; L < kPtcLevels; ++L)
+      for (int j = 0; j < 8; ++j) {
+        int D[kPtcLevels];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const long long dl = (long long)__float2int_rn(__uint_as_float(v[L][j]));
-          if (L < 4) qh[j] = (qh[j] << 8) + dl;
-          else ql[j] = (ql[j] << 8) + dl;
-        }
+        for (int L = 0; L < kPtcLevels; ++L) D[L] = __float2int_rn(__uint_as_float(v[L][j]));
+        qh[j] = (long long)D[0] * 16777216ll + (long long)D[1] * 65536ll + (long long)D[2] * 256ll + D[3];
+        ql[j] = ((long long)D[4] << 32) + (long long)D[5] * 16777216ll + (long long)D[6] * 65536ll +
+                (long long)D[7] * 256ll + D[8];
+      }
     }
     if (p < n2) {
       const int EP = a.pexp[p];

@@ -3261,6 +3261,7 @@ hbpc_status hbpc_get_stats(const hbpc_ctx* cctx, hbpc_stats* out) {
   if (!cctx || !out) return HBPC_ERR_INVALID_ARG;
   hbpc_ctx* ctx = const_cast<hbpc_ctx*>(cctx);
   *out = ctx->stats;
+  out->pc_apply_tc = ctx->ptc_ready ? 1 : 0;
   if (ctx->lp.vcount) {   // learned blocks replaced by exact inverses so far
     int v = 0;
     HBPC_CK(ctx, cudaMemcpyAsync(&v, ctx->lp.vcount, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -72,7 +72,7 @@ class Stats(ctypes.Structure):
                 ("newton_its", ctypes.c_longlong), ("gmres_its", ctypes.c_longlong),
                 ("r1_evals", ctypes.c_longlong), ("r2_evals", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong), ("t", ctypes.c_double), ("arnoldi_cols", ctypes.c_longlong),
-                ("pc_exact_blocks", ctypes.c_longlong)]
+                ("pc_exact_blocks", ctypes.c_longlong), ("pc_apply_tc", ctypes.c_longlong)]
 
 
 _P = ctypes.c_void_p

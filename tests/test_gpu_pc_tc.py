@@ -137,7 +137,9 @@ def test_tc_apply_steps_vs_oracle_and_cuda_core(hb):
         ctx = make(hb, dim, N, n, tc, **opts)
         ctx.set_state(w0)
         ctx.step(2)
-        res.append((ctx.get_state(), ctx.stats()["gmres_its"]))
+        st = ctx.stats()
+        assert st["pc_apply_tc"] == (1 if tc else 0)
+        res.append((ctx.get_state(), st["gmres_its"]))
         ctx.close()
     o = newton.NewtonOptions(tol_rel=1e-12, tol_abs=1e-13, gmres_tol=1e-10, restart=40, jv="linear", pc="bjext")
     adv = ohbpc.dg_stepper(disc, dt, q, kmax, o)

@@ -200,7 +200,7 @@ def cgs_work_per_dof(mixed, cavg):
 # captured.
 NCU_TRAFFIC = {
     "mixed": {"cgs2": None, "pc_apply": None, "jv": None},
-    "fp64": {"cgs2": 1.411e5, "pc_apply": None, "jv": 1.441e5},
+    "fp64": {"cgs2": 1.411e5, "pc_apply": 8.581e4, "jv": 1.441e5},
 }
 
 KERNEL_NAMES = {

@@ -39,7 +39,9 @@ typedef enum {
   HBPC_ERR_NO_CONVERGENCE = 4, /* Newton or GMRES iteration cap reached */
   HBPC_ERR_NONFINITE = 5,      /* a residual or update norm is NaN or Inf */
   HBPC_ERR_TIMEOUT = 6,        /* a bounded wait for the device gave up
-                                  (hbpc_set_wait_limit) */
+                                  (hbpc_set_wait_limit), or a bounded
+                                  wait inside the tensor-core block apply
+                                  ran out (its outputs are then NaN) */
   HBPC_ERR_UNSUPPORTED = 7     /* valid request that this build does not cover */
 } hbpc_status;
 
@@ -358,7 +360,9 @@ hbpc_status hbpc_eval_Jv(hbpc_ctx* ctx, double alpha1, double alpha2, const doub
  * (W, S)) for the stage coefficients alpha1, alpha2, applied to `in`:
  * out = P^-1 in.  Needs a context with pc != HBPC_PC_NONE.  In the
  * MIXED precision mode the blocks S_e, their inverses and the apply are FP32
- * (what the Krylov loop uses); in FP64 mode everything is FP64.
+ * (what the Krylov loop uses); in FP64 mode everything is FP64 (a block
+ * shared by all elements is applied through exact BF16 digit-plane products
+ * on the tensor cores, rounded once to FP64; hbpc_stats.pc_apply_tc).
  * X, in, out: device, 2 n_dof FP64. */
 hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const double* X,
                          const double* in, double* out);

@@ -777,6 +777,26 @@ hbpc_status lp_gemm_check(hbpc_ctx* x) {
   return HBPC_OK;
 }
 
+// The flag of the tensor-core block apply's bounded waits (a wait that ran
+// out wrote NaN outputs): read after the stream's work; a set flag is
+// HBPC_ERR_TIMEOUT (with `what`) and is cleared.
+hbpc_status ptc_check(hbpc_ctx* x, const std::string& what) {
+  if (!x->ptc_err) return HBPC_OK;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, x->ptc_err, sizeof(int), cudaMemcpyDeviceToHost, x->stream) != cudaSuccess ||
+      cudaStreamSynchronize(x->stream) != cudaSuccess || !e)
+    return HBPC_OK;
+  cudaMemsetAsync(x->ptc_err, 0, sizeof(int), x->stream);
+  return fail(x, HBPC_ERR_TIMEOUT, what + " (a bounded wait of the tensor-core block apply ran out)");
+}
+
+// A non-finite result: HBPC_ERR_TIMEOUT when the tensor-core block apply gave
+// up waiting (its NaN outputs are the cause), else HBPC_ERR_NONFINITE.
+hbpc_status nonfinite(hbpc_ctx* x, const std::string& what) {
+  const hbpc_status t = ptc_check(x, what);
+  return t != HBPC_OK ? t : fail(x, HBPC_ERR_NONFINITE, what);
+}
+
 void lp_free(hbpc_ctx* x) {
   auto& L = x->lp;
   for (void* q : {(void*)L.P, (void*)L.G, (void*)L.Mo, (void*)L.Ve, (void*)L.W1h, (void*)L.W2h, (void*)L.W3h,
@@ -1590,7 +1610,7 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
   if (s != HBPC_OK) return s;
   if ((s = read_state(x)) != HBPC_OK) return s;
   const double g0 = std::sqrt(x->st_host->nrm[0]);
-  if (!std::isfinite(g0)) return fail(x, HBPC_ERR_NONFINITE, "initial Newton residual is not finite");
+  if (!std::isfinite(g0)) return nonfinite(x, "initial Newton residual is not finite");
   x->stats.newton_solves += 1;
   if (x->verbose) std::fprintf(stderr, "[hbpc] newton a1=%g a2=%g ||G0||=%.6e\n", a1, a2, g0);
   if (g0 == 0.0) return HBPC_OK;
@@ -1624,7 +1644,7 @@ hbpc_status newton(hbpc_ctx* x, const double* b, double a1, double a2, const dou
       std::fprintf(stderr, "[hbpc]   it %d gmres %d conv %d ||G||=%.6e rel %.3e ||dW||=%.3e\n", r, its,
                    int(conv), gn, gn / g0, dW);
     if (!std::isfinite(gn) || !std::isfinite(dW))
-      return fail(x, HBPC_ERR_NONFINITE, "Newton residual is not finite");
+      return nonfinite(x, "Newton residual is not finite");
     if (gn <= x->sol.tol_newton_rel * g0 || dW <= x->sol.tol_newton_abs) return HBPC_OK;
   }
   return fail(x, HBPC_ERR_NO_CONVERGENCE, "Newton did not converge within newton_max_iter");
@@ -2082,6 +2102,7 @@ hbpc_status step_graph_run(hbpc_ctx* x) {
                        : c.where == 2 ? "Newton residual is not finite"
                        : c.where == 3 ? "GMRES residual is not finite"
                                       : "Newton did not converge within newton_max_iter";
+    if (c.err == HBPC_ERR_NONFINITE) return nonfinite(x, std::string("step graph: ") + what);
     return fail(x, hbpc_status(c.err), std::string("step graph: ") + what);
   }
   return HBPC_OK;
@@ -3241,7 +3262,8 @@ hbpc_status hbpc_eval_pc(hbpc_ctx* ctx, double alpha1, double alpha2, const doub
   }
   HBPC_CK(ctx, cudaMemcpyAsync(ctx->Z, in, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   if ((s = pc_apply(ctx, ctx->Z, nullptr, nullptr, out, 0, nullptr)) != HBPC_OK) return s;
-  return sync(ctx, "eval_pc");
+  if ((s = sync(ctx, "eval_pc")) != HBPC_OK) return s;
+  return ptc_check(ctx, "eval_pc");
 }
 
 hbpc_status hbpc_newton_solve(hbpc_ctx* ctx, const double* b, double alpha1, double alpha2,

@@ -176,3 +176,34 @@ def test_bjext_h_preconditioner_checks(hbpc):
     with pytest.raises(hbpc.HBPCError) as ei:
         hbpc.Context(2, (3, 3), (0, 0), (1, 1), 3, pc=4)
     assert ei.value.status == 1
+
+
+def test_binding_structs_match_the_header(hbpc, tmp_path):
+    """The ctypes structures of the binding have the C compiler's layout of the
+    header's structs: size and the offset of every field, in order (a field
+    added on one side only would shift every later one)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"hbpc_mesh": hbpc.Mesh, "hbpc_physics": hbpc.Physics, "hbpc_solver": hbpc.Solver,
+             "hbpc_stats": hbpc.Stats, "hbpc_tuning": hbpc.Tuning}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "hbpc.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True).stdout.splitlines())
+    for cname, cls in pairs.items():
+        assert int(out["%s size" % cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out["%s.%s" % (cname, fname)]) == getattr(cls, fname).offset, (cname, fname)

@@ -852,6 +852,16 @@ def run_ours(args):
     line[("mixed_precision" if head == "fp64" else "fp64_precision")]["unit"] = UNIT
     line[("mixed_precision" if head == "fp64" else "fp64_precision")]["dtype"] = (
         "f64 state/Newton, f32 Krylov" if other == "mixed" else "f64")
+    if not args.no_cavity:
+        # the lid-driven cavity (Sec. 5.3.1): three timed steps of each arm after
+        # its start-up; --workload cavity for the line alone.  A failure there is
+        # recorded, not raised: the lines above stand on their own.
+        try:
+            ca = argparse.Namespace(steps=3, warmup=1, no_step_graph=args.no_step_graph)
+            cl = run_cavity(ca, emit=False)
+            line["cavity"] = {k: cl[k] for k in ("workload", "unit", "value", "best_arm", "steps", "ndof", "arms")}
+        except Exception as e:   # noqa: BLE001
+            line["cavity"] = {"workload": "lid_driven_cavity", "error": str(e)[:200]}
     print(json.dumps(line), flush=True)
 
 
@@ -1398,6 +1408,8 @@ def main():
     ap.add_argument("--no-step-graph", action="store_true",
                     help="host-driven steps (a look at the GMRES state every few columns) instead of one CUDA "
                          "graph launch per step with device-driven Newton and GMRES loops")
+    ap.add_argument("--no-cavity", action="store_true",
+                    help="leave the lid-driven cavity sub-line out of the default line")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched viscous Burgers workload in the default line")
     ap.add_argument("--no-r1-roofline", action="store_true",
